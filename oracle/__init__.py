@@ -1,0 +1,251 @@
+"""FP64 CPU oracle for the hybrid LB / dynamic SCF time step (arXiv:1204.2088).
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline
+leg of ``bench.py`` may import this package.  The product path (the CUDA library and its
+binding) never imports, links or executes anything here, and nothing here imports the
+product.  The arithmetic lives in ``oracle.c`` (plain C, FP64); this module only marshals
+numpy arrays through ctypes.
+
+Parity status of each function (what pins it is in ``tests/test_oracle_pins.py``):
+  sigma, densities, objective, ncg, mu, force, lb_step, cd_step, step, free_energy,
+  order_parameter, segregation: pinned.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c into liboracle.so next to it (gcc, FP64, OpenMP)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        cmd = ["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=c11", _SRC, "-o", _LIB, "-lm"]
+        subprocess.run(cmd, check=True)
+    return _LIB
+
+
+class Params(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
+        ("ns", ctypes.c_int32), ("N", ctypes.c_int32), ("nA", ctypes.c_int32),
+        ("phi_p", ctypes.c_double), ("chi", ctypes.c_double * 9), ("kappa", ctypes.c_double),
+        ("a", ctypes.c_double), ("dt", ctypes.c_double), ("M", ctypes.c_double),
+        ("tau_s", ctypes.c_double), ("tau_b", ctypes.c_double), ("rho0", ctypes.c_double),
+        ("hydro", ctypes.c_int32), ("ncg_iters", ctypes.c_int32), ("cn_sweeps", ctypes.c_int32),
+        ("phi_floor", ctypes.c_double),
+    ]
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = ctypes.CDLL(build())
+        D = ctypes.POINTER(ctypes.c_double)
+        P = ctypes.POINTER(Params)
+        sig = {
+            "or_stencil_weights": (None, [ctypes.c_double, D]),
+            "or_sigma": (None, [P, D, D]),
+            "or_densities": (ctypes.c_double, [P, D, D, D, D]),
+            "or_objective": (ctypes.c_double, [P, D, D]),
+            "or_ncg": (None, [P, D, D, D, D]),
+            "or_mu": (None, [P, D, D, D]),
+            "or_force": (None, [P, D, D, D]),
+            "or_lb_basis": (None, [D, D, D, ctypes.POINTER(ctypes.c_int)]),
+            "or_lb_equilibrium": (None, [ctypes.c_double, D, D]),
+            "or_lb_step": (None, [P, D, D, D, D]),
+            "or_cd_step": (None, [P, D, D, D, D, D]),
+            "or_step": (None, [P, D, D, D, D, D, D, D, D]),
+            "or_free_energy": (ctypes.c_double, [P, D, D]),
+            "or_order_parameter": (ctypes.c_double, [P, D]),
+            "or_segregation": (ctypes.c_double, [P, D]),
+            "or_num_threads": (ctypes.c_int, []),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(_lib, name)
+            fn.restype = res
+            fn.argtypes = args
+    return _lib
+
+
+def make_params(cfg: dict) -> Params:
+    """Build the oracle parameter struct from a plain configuration dictionary."""
+    p = Params()
+    p.nx, p.ny, p.nz = cfg["grid"]
+    p.ns = cfg.get("ns", 2)
+    p.N = cfg["N"]
+    p.nA = cfg["nA"]
+    p.phi_p = cfg.get("phi_p", 1.0)
+    chi = np.zeros((3, 3))
+    for (i, j), v in cfg.get("chi", {}).items():
+        chi[i, j] = chi[j, i] = v
+    for k in range(9):
+        p.chi[k] = float(chi.flat[k])
+    p.kappa = cfg.get("kappa", 10.0)
+    p.a = cfg.get("a", 1.1543)
+    p.dt = cfg.get("dt", 0.4)
+    p.M = cfg.get("M", 1.0)
+    p.tau_s = cfg.get("tau_s", 1.0)
+    p.tau_b = cfg.get("tau_b", 1.0)
+    p.rho0 = cfg.get("rho0", 1.0)
+    p.hydro = cfg.get("hydro", 1)
+    p.ncg_iters = cfg.get("ncg_iters", 4)
+    p.cn_sweeps = cfg.get("cn_sweeps", 8)
+    p.phi_floor = cfg.get("phi_floor", 1e-6)
+    return p
+
+
+def _ptr(a: np.ndarray):
+    assert a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _shape(cfg):
+    nx, ny, nz = cfg["grid"]
+    return (nz, ny, nx)
+
+
+def stencil_weights(a: float) -> np.ndarray:
+    w = np.zeros(4)
+    lib().or_stencil_weights(a, _ptr(w))
+    return w
+
+
+def sigma(cfg: dict, f: np.ndarray) -> np.ndarray:
+    p = make_params(cfg)
+    f = _f64(f)
+    out = np.empty_like(f)
+    lib().or_sigma(ctypes.byref(p), _ptr(f), _ptr(out))
+    return out
+
+
+def densities(cfg: dict, U: np.ndarray, want_stack: bool = False):
+    """phi[U] (shape [ns, nz, ny, nx]), Q, <exp(-U_S)> and optionally G_0..G_N."""
+    p = make_params(cfg)
+    U = _f64(U)
+    phi = np.empty_like(U)
+    qs = ctypes.c_double(1.0)
+    stack = None
+    if want_stack:
+        stack = np.empty((cfg["N"] + 1,) + _shape(cfg))
+    Q = lib().or_densities(ctypes.byref(p), _ptr(U), _ptr(phi), ctypes.byref(qs),
+                           _ptr(stack) if stack is not None else None)
+    if want_stack:
+        return phi, Q, qs.value, stack
+    return phi, Q, qs.value
+
+
+def objective(cfg: dict, U: np.ndarray, phi_target: np.ndarray) -> float:
+    p = make_params(cfg)
+    return lib().or_objective(ctypes.byref(p), _ptr(_f64(U)), _ptr(_f64(phi_target)))
+
+
+def ncg(cfg: dict, phi_target: np.ndarray, U0: np.ndarray):
+    """Fixed-count Fletcher-Reeves inversion.  Returns (U, phi_model, info)."""
+    p = make_params(cfg)
+    U = _f64(U0).copy()
+    phim = np.empty_like(U)
+    info = np.zeros(2 + 4 * max(cfg.get("ncg_iters", 4), 0))
+    lib().or_ncg(ctypes.byref(p), _ptr(_f64(phi_target)), _ptr(U), _ptr(phim), _ptr(info))
+    return U, phim, info
+
+
+def mu(cfg: dict, U: np.ndarray, phi: np.ndarray) -> np.ndarray:
+    p = make_params(cfg)
+    out = np.empty_like(_f64(phi))
+    lib().or_mu(ctypes.byref(p), _ptr(_f64(U)), _ptr(_f64(phi)), _ptr(out))
+    return out
+
+
+def force(cfg: dict, phi: np.ndarray, mu_: np.ndarray) -> np.ndarray:
+    p = make_params(cfg)
+    out = np.empty((3,) + _shape(cfg))
+    lib().or_force(ctypes.byref(p), _ptr(_f64(phi)), _ptr(_f64(mu_)), _ptr(out))
+    return out
+
+
+def lb_basis():
+    """(e[19,19], w[19], b[19], c[19,3]) of Table 1 with the D3Q19 velocities."""
+    e = np.zeros((19, 19)); w = np.zeros(19); b = np.zeros(19)
+    c = np.zeros((19, 3), dtype=np.intc)
+    lib().or_lb_basis(_ptr(e), _ptr(w), _ptr(b), c.ctypes.data_as(ctypes.POINTER(ctypes.c_int)))
+    return e, w, b, c
+
+
+def lb_equilibrium(rho: float, u) -> np.ndarray:
+    out = np.zeros(19)
+    lib().or_lb_equilibrium(float(rho), _ptr(_f64(u)), _ptr(out))
+    return out
+
+
+def lb_step(cfg: dict, n: np.ndarray, f_lat: np.ndarray | None = None):
+    """One collide+stream step.  n: [19, nz, ny, nx] post-streaming populations."""
+    p = make_params(cfg)
+    n = _f64(n)
+    out = np.empty_like(n)
+    u = np.empty((3,) + _shape(cfg))
+    lib().or_lb_step(ctypes.byref(p), _ptr(n), _ptr(_f64(f_lat)) if f_lat is not None else None,
+                     _ptr(out), _ptr(u))
+    return out, u
+
+
+def cd_step(cfg: dict, phi: np.ndarray, mu_: np.ndarray, ulat: np.ndarray | None, mass0) -> np.ndarray:
+    p = make_params(cfg)
+    phi = _f64(phi)
+    out = np.empty_like(phi)
+    lib().or_cd_step(ctypes.byref(p), _ptr(phi), _ptr(_f64(mu_)),
+                     _ptr(_f64(ulat)) if ulat is not None else None,
+                     _ptr(_f64(mass0)) if mass0 is not None else None, _ptr(out))
+    return out
+
+
+def step(cfg: dict, phi: np.ndarray, U: np.ndarray, pop: np.ndarray | None, mass0):
+    """One coupled time step.  Returns a dict with the new state and the step outputs."""
+    p = make_params(cfg)
+    phi = _f64(phi).copy()
+    U = _f64(U).copy()
+    shp = _shape(cfg)
+    if pop is None:
+        pop = np.zeros((19,) + shp)
+        _, w, _, _ = lb_basis()
+        pop += (cfg.get("rho0", 1.0) * w)[:, None, None, None]
+    pop = _f64(pop).copy()
+    mu_ = np.empty_like(phi)
+    ulat = np.empty((3,) + shp)
+    phim = np.empty_like(phi)
+    info = np.zeros(2 + 4 * max(cfg.get("ncg_iters", 4), 0))
+    lib().or_step(ctypes.byref(p), _ptr(phi), _ptr(U), _ptr(pop), _ptr(_f64(mass0)), _ptr(mu_),
+                  _ptr(ulat), _ptr(phim), _ptr(info))
+    return {"phi": phi, "U": U, "pop": pop, "mu": mu_, "ulat": ulat, "phim": phim, "info": info}
+
+
+def free_energy(cfg: dict, U: np.ndarray, phi: np.ndarray) -> float:
+    p = make_params(cfg)
+    return lib().or_free_energy(ctypes.byref(p), _ptr(_f64(U)), _ptr(_f64(phi)))
+
+
+def order_parameter(cfg: dict, phi: np.ndarray) -> float:
+    p = make_params(cfg)
+    return lib().or_order_parameter(ctypes.byref(p), _ptr(_f64(phi)))
+
+
+def segregation(cfg: dict, phi: np.ndarray) -> float:
+    p = make_params(cfg)
+    return lib().or_segregation(ctypes.byref(p), _ptr(_f64(phi)))
+
+
+def num_threads() -> int:
+    return lib().or_num_threads()

@@ -1,0 +1,560 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each test ties one oracle function to something other than itself: a closed form, a
+library routine used as an independent route (FFT convolution), brute-force enumeration of
+chain conformations (Eq. 2 taken literally), a finite-difference derivative, a conservation
+law, or a value the paper prints.  A plausible slip in the oracle (a dropped term, a wrong
+index or sign, a transposed operand) fails at least one of them.
+"""
+import itertools
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1204_2088_gb300 import inputs
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def cfg_small(grid=(5, 6, 7), N=6, nA=2, chi=0.4, ns=2, phi_p=1.0, **kw):
+    c = inputs.melt(grid, N, 0.5, chi * N, **kw)
+    c["nA"] = nA
+    if ns == 3:
+        c["ns"] = 3
+        c["phi_p"] = phi_p
+        c["chi"] = {(0, 1): chi, (1, 2): 1.3 * chi, (0, 2): 0.2 * chi}
+    return c
+
+
+def symbol(a, kvec):
+    """Fourier symbol of the separable moment-matched 27-point stencil."""
+    al = a * a / 6.0
+    return np.prod([1.0 - 2.0 * al + 2.0 * al * np.cos(k) for k in kvec])
+
+
+def kgrid(grid):
+    nx, ny, nz = grid
+    kz, ky, kx = np.meshgrid(2 * np.pi * np.fft.fftfreq(nz), 2 * np.pi * np.fft.fftfreq(ny),
+                             2 * np.pi * np.fft.fftfreq(nx), indexing="ij")
+    return kx, ky, kz
+
+
+# ---------------------------------------------------------------------------------------------
+# Linkage operator (Eq. 17 and the Gaussian kernel after it)
+# ---------------------------------------------------------------------------------------------
+def test_stencil_normalised_and_moment_matched():
+    a = 1.1543
+    w = oracle.stencil_weights(a)
+    counts = np.array([1, 6, 12, 8])
+    assert abs((counts * w).sum() - 1.0) < 1e-15            # sigma[1] = 1
+    # second moment along x: faces +-x (2), edges with x (8), corners (8)
+    m2 = 2 * w[1] + 8 * w[2] + 8 * w[3]
+    assert abs(m2 - a * a / 3.0) < 1e-15                     # per-axis variance of a Gaussian bond
+
+
+def test_sigma_plane_wave_closed_form():
+    cfg = cfg_small(grid=(5, 6, 7))
+    nx, ny, nz = cfg["grid"]
+    k = (2 * np.pi * 1 / nx, 2 * np.pi * 2 / ny, 2 * np.pi * 3 / nz)
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    f = np.cos(k[0] * x + k[1] * y + k[2] * z + 0.3)
+    out = oracle.sigma(cfg, f)
+    assert np.abs(out - symbol(cfg["a"], k) * f).max() < 1e-14
+
+
+def test_sigma_equals_fft_convolution():
+    cfg = cfg_small(grid=(4, 7, 3))   # nx=4, tiny nz=3: periodic wrap on both sides
+    f = inputs.random_field((3, 7, 4), seed=3)
+    kx, ky, kz = kgrid(cfg["grid"])
+    al = cfg["a"] ** 2 / 6.0
+    sym = (1 - 2 * al + 2 * al * np.cos(kx)) * (1 - 2 * al + 2 * al * np.cos(ky)) * (1 - 2 * al + 2 * al * np.cos(kz))
+    ref = np.real(np.fft.ifftn(np.fft.fftn(f) * sym))
+    assert np.abs(oracle.sigma(cfg, f) - ref).max() < 1e-14
+
+
+# ---------------------------------------------------------------------------------------------
+# Propagators, densities, Q (Eq. 2, 16, 17)
+# ---------------------------------------------------------------------------------------------
+def test_homogeneous_field_propagator_is_exponential():
+    cfg = cfg_small(grid=(4, 5, 6), N=7, nA=3)
+    wA, wB = 0.37, -0.21
+    U = np.stack([np.full((6, 5, 4), wA), np.full((6, 5, 4), wB)])
+    phi, Q, _, G = oracle.densities(cfg, U, want_stack=True)
+    for s in range(cfg["N"] + 1):
+        expo = wA * min(s, 3) + wB * max(s - 3, 0)
+        assert np.abs(G[s] - np.exp(-expo)).max() < 1e-14 * max(1.0, np.exp(-expo))
+    assert abs(Q - np.exp(-(3 * wA + 4 * wB))) < 1e-14
+    assert np.abs(phi[0] - 3 / 7).max() < 1e-14 and np.abs(phi[1] - 4 / 7).max() < 1e-14
+
+
+def brute_force_densities(cfg, U):
+    """Eq. 2 taken literally on a tiny lattice: sum over all bead-position paths
+    R_1..R_N of prod_s exp(-U_{I_s}(R_s)) prod_bonds T(R_s - R_{s-1}), where T is the
+    27-point Gaussian bond weight built here from the stencil offsets."""
+    nx, ny, nz = cfg["grid"]
+    V = nx * ny * nz
+    al = cfg["a"] ** 2 / 6.0
+    w1 = {-1: al, 0: 1 - 2 * al, 1: al}
+    T = np.zeros((V, V))
+    for z, y, x in itertools.product(range(nz), range(ny), range(nx)):
+        r = x + nx * (y + ny * z)
+        for dz, dy, dx in itertools.product((-1, 0, 1), repeat=3):
+            r2 = (x + dx) % nx + nx * (((y + dy) % ny) + ny * ((z + dz) % nz))
+            T[r, r2] += w1[dx] * w1[dy] * w1[dz]
+    N, nA = cfg["N"], cfg["nA"]
+    B = [np.exp(-U[0].reshape(-1)) if s < nA else np.exp(-U[1].reshape(-1)) for s in range(N)]
+    # W[r1,...,rN]
+    W = B[0].copy()
+    for s in range(1, N):
+        W = W[..., None] * T.reshape((1,) * (s - 1) + (V, V)) * B[s].reshape((1,) * s + (V,))
+    Phi = W.sum()
+    marg = [W.sum(axis=tuple(a for a in range(N) if a != s)) for s in range(N)]
+    pref = cfg["phi_p"] * V / (N * Phi)
+    phiA = pref * sum(marg[s] for s in range(nA))
+    phiB = pref * sum(marg[s] for s in range(nA, N))
+    return np.stack([phiA, phiB]).reshape(2, nz, ny, nx), Phi / V
+
+
+@pytest.mark.parametrize("grid,N,nA", [((2, 3, 2), 4, 2), ((3, 2, 2), 3, 1), ((1, 3, 4), 4, 3)])
+def test_densities_brute_force_paths(grid, N, nA):
+    cfg = cfg_small(grid=grid, N=N, nA=nA)
+    nx, ny, nz = grid
+    U = inputs.random_field((2, nz, ny, nx), seed=11 + N, scale=0.7)
+    phi, Q, _ = oracle.densities(cfg, U)
+    ref, Qref = brute_force_densities(cfg, U)
+    assert abs(Q - Qref) < 1e-13 * Qref
+    assert np.abs(phi - ref).max() < 1e-13
+
+
+def test_block_masses_and_solvent():
+    cfg = cfg_small(grid=(6, 5, 4), N=9, nA=4, ns=3, phi_p=0.3)
+    U = inputs.random_field((3, 4, 5, 6), seed=5, scale=0.8)
+    phi, Q, qs = oracle.densities(cfg, U)
+    V = 120
+    assert abs(phi[0].sum() - V * 0.3 * 4 / 9) < 1e-12
+    assert abs(phi[1].sum() - V * 0.3 * 5 / 9) < 1e-12
+    es = np.exp(-U[2])
+    assert abs(qs - es.mean()) < 1e-14
+    assert np.abs(phi[2] - 0.7 * es / es.mean()).max() < 1e-14
+
+
+# ---------------------------------------------------------------------------------------------
+# Self-consistent inversion (Fletcher-Reeves NCG on the Legendre functional)
+# ---------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("ns", [2, 3])
+def test_objective_gradient_is_density_deficit(ns):
+    cfg = cfg_small(grid=(4, 3, 5), N=5, nA=2, ns=ns, phi_p=0.4)
+    shp = (ns, 5, 3, 4)
+    U = inputs.random_field(shp, seed=21, scale=0.5)
+    target = 0.2 + 0.1 * inputs.uniform01(22, int(np.prod(shp))).reshape(shp)
+    phi, _, _ = oracle.densities(cfg, U)
+    grad = target - phi
+    h = 1e-5
+    for (I, z, y, x) in [(0, 0, 0, 0), (1, 4, 2, 3), (ns - 1, 2, 1, 1), (0, 3, 0, 2)]:
+        Up = U.copy(); Up[I, z, y, x] += h
+        Um = U.copy(); Um[I, z, y, x] -= h
+        fd = (oracle.objective(cfg, Up, target) - oracle.objective(cfg, Um, target)) / (2 * h)
+        assert abs(fd - grad[I, z, y, x]) < 1e-8
+
+
+def test_ncg_recovers_potentials_up_to_gauge():
+    cfg = cfg_small(grid=(4, 4, 3), N=6, nA=3, ncg_iters=300)
+    Utrue = inputs.random_field((2, 3, 4, 4), seed=31, scale=0.5)
+    target, _, _ = oracle.densities(cfg, Utrue)
+    U, phim, info = oracle.ncg(cfg, target, np.zeros_like(Utrue))
+    assert np.abs(phim - target).max() < 1e-10
+    # the potential is unique up to one constant per species (uniform U_A, U_B are gauges)
+    for I in range(2):
+        dev = U[I] - Utrue[I]
+        assert np.ptp(dev) < 1e-7
+    assert info[-1] < 1e-10
+
+
+def test_ncg_uniform_target_keeps_zero_potential():
+    cfg = cfg_small(grid=(3, 3, 3), N=4, nA=2, ncg_iters=3)
+    target = np.stack([np.full((3, 3, 3), 0.5), np.full((3, 3, 3), 0.5)])
+    U, phim, _ = oracle.ncg(cfg, target, np.zeros_like(target))
+    assert np.abs(U).max() < 1e-13
+    assert np.abs(phim - 0.5).max() < 1e-14
+
+
+# ---------------------------------------------------------------------------------------------
+# Chemical potential (Eq. 4) and force (Eq. 8)
+# ---------------------------------------------------------------------------------------------
+def test_mu_uniform_closed_form():
+    cfg = cfg_small(grid=(3, 4, 5), chi=0.625)
+    phA, phB = 0.37, 0.61
+    phi = np.stack([np.full((5, 4, 3), phA), np.full((5, 4, 3), phB)])
+    mu = oracle.mu(cfg, np.zeros_like(phi), phi)
+    kap = 10.0 * (phA + phB - 1.0)
+    assert np.abs(mu[0] - (0.625 * phB + kap)).max() < 1e-14
+    assert np.abs(mu[1] - (0.625 * phA + kap)).max() < 1e-14
+    assert np.abs((mu[0] - mu[1]) - 0.625 * (phB - phA)).max() < 1e-14
+
+
+def test_mu_general_against_fft():
+    cfg = cfg_small(grid=(6, 5, 4), ns=3, phi_p=0.5, chi=0.3)
+    shp = (3, 4, 5, 6)
+    U = inputs.random_field(shp, seed=41)
+    phi = 0.3 + 0.1 * inputs.random_field(shp, seed=42)
+    kx, ky, kz = kgrid(cfg["grid"])
+    al = cfg["a"] ** 2 / 6.0
+    sym = (1 - 2 * al + 2 * al * np.cos(kx)) * (1 - 2 * al + 2 * al * np.cos(ky)) * (1 - 2 * al + 2 * al * np.cos(kz))
+    sphi = np.stack([np.real(np.fft.ifftn(np.fft.fftn(phi[J]) * sym)) for J in range(3)])
+    chi = np.zeros((3, 3))
+    for (i, j), v in cfg["chi"].items():
+        chi[i, j] = chi[j, i] = v
+    ref = -U + np.einsum("ij,jzyx->izyx", chi, sphi) + 10.0 * (phi.sum(0) - 1.0)[None]
+    assert np.abs(oracle.mu(cfg, U, phi) - ref).max() < 1e-13
+
+
+def test_force_central_difference_closed_form():
+    cfg = cfg_small(grid=(8, 6, 5))
+    z, y, x = np.meshgrid(np.arange(5), np.arange(6), np.arange(8), indexing="ij")
+    k = 2 * np.pi / 8
+    mu = np.stack([np.sin(k * x), 2.0 * np.sin(k * x)])
+    phi = np.stack([np.full_like(mu[0], 0.3), np.full_like(mu[0], 0.7)])
+    f = oracle.force(cfg, phi, mu)
+    ref = -(0.3 + 1.4) * np.sin(k) * np.cos(k * x)     # (sin(k(x+1)) - sin(k(x-1)))/2
+    assert np.abs(f[0] - ref).max() < 1e-14
+    assert np.abs(f[1]).max() == 0.0 and np.abs(f[2]).max() == 0.0
+
+
+# ---------------------------------------------------------------------------------------------
+# Lattice Boltzmann (Eq. 9-15, Table 1)
+# ---------------------------------------------------------------------------------------------
+def test_table1_basis_orthogonal_with_paper_weights():
+    e, w, b, c = oracle.lb_basis()
+    assert abs(w.sum() - 1.0) < 1e-15
+    assert np.abs(np.einsum("i,ia,ib->ab", w, c, c) - np.eye(3) / 3).max() < 1e-15
+    G = np.einsum("i,ki,li->kl", w, e, e)
+    assert np.abs(G - np.diag(np.diag(G))).max() < 1e-15          # mutually orthogonal
+    # norms b_k = sum_i w_i e_ki^2 worked out by hand from Table 1
+    hand = np.array([1, 1 / 3, 1 / 3, 1 / 3, 2 / 3, 4 / 9, 4 / 3, 1 / 9, 1 / 9, 1 / 9,
+                     2 / 3, 2 / 3, 2 / 3, 2 / 9, 2 / 9, 2 / 9, 2, 4 / 9, 4 / 3])
+    assert np.abs(b - hand).max() < 1e-15
+    expect = {(0, 0, 0)}
+    for a in range(3):
+        for sgn in (1, -1):
+            v = [0, 0, 0]; v[a] = sgn
+            expect.add(tuple(v))
+    for a in range(3):
+        for b_ in range(a + 1, 3):
+            for sa in (1, -1):
+                for sb in (1, -1):
+                    v = [0, 0, 0]; v[a] = sa; v[b_] = sb
+                    expect.add(tuple(v))
+    assert set(map(tuple, c.tolist())) == expect and len(expect) == 19
+
+
+def test_equilibrium_moment_constraints():
+    _, w, _, c = oracle.lb_basis()
+    rho, u = 1.07, np.array([0.03, -0.05, 0.02])
+    neq = oracle.lb_equilibrium(rho, u)
+    assert abs(neq.sum() - rho) < 1e-15
+    assert np.abs(neq @ c - rho * u).max() < 1e-15
+    P = np.einsum("i,ia,ib->ab", neq, c, c)
+    assert np.abs(P - (rho * np.outer(u, u) + rho / 3 * np.eye(3))).max() < 1e-15
+
+
+def lb_cfg(grid, tau_s=1.0, tau_b=1.0):  # noqa: E302
+    return cfg_small(grid=grid, tau_s=tau_s, tau_b=tau_b)
+
+
+def test_lb_equilibrium_fixed_point_and_conservation():
+    grid = (5, 4, 6)
+    cfg = lb_cfg(grid, 0.7, 1.3)
+    _, w, _, _ = oracle.lb_basis()
+    u = np.array([0.02, -0.01, 0.015])
+    neq = oracle.lb_equilibrium(1.1, u)
+    n = np.broadcast_to(neq[:, None, None, None], (19, 6, 4, 5)).copy()
+    out, uo = oracle.lb_step(cfg, n)
+    assert np.abs(out - n).max() < 1e-15
+    assert np.abs(uo - u[:, None, None, None]).max() < 1e-15
+    # random state with random force: mass exact, momentum grows by exactly sum f
+    n = w[:, None, None, None] * (1.0 + 0.05 * inputs.random_field((19, 6, 4, 5), seed=51))
+    f = 1e-3 * inputs.random_field((3, 6, 4, 5), seed=52)
+    _, _, _, c = oracle.lb_basis()
+    out, _ = oracle.lb_step(cfg, n, f)
+    assert abs(out.sum() - n.sum()) < 1e-12
+    j0 = np.einsum("izyx,ia->a", n, c)
+    j1 = np.einsum("izyx,ia->a", out, c)
+    assert np.abs(j1 - j0 - f.reshape(3, -1).sum(1)).max() < 1e-13
+
+
+@pytest.mark.parametrize("tau", [0.6, 1.0, 2.0])
+def test_shear_wave_decay_gives_kinematic_viscosity(tau):
+    """u_x = U0 sin(k z) decays as exp(-nu k^2 t) with nu = c_s^2 (tau - 1/2) (Eq. 15 with
+    gamma_s = 1 - 1/tau, lattice units)."""
+    L = 96
+    cfg = lb_cfg((1, 1, L), tau_s=tau, tau_b=1.0)
+    k = 2 * np.pi / L
+    z = np.arange(L)
+    n = np.stack([oracle.lb_equilibrium(1.0, [1e-4 * np.sin(k * zz), 0, 0]) for zz in z], axis=1)
+    n = n.reshape(19, L, 1, 1)
+    amps = []
+    for t in range(400):
+        n, u = oracle.lb_step(cfg, n)
+        amps.append(2.0 / L * (u[0, :, 0, 0] * np.sin(k * z)).sum())
+    t1, t2 = 100, 399
+    rate = -np.log(amps[t2] / amps[t1]) / (t2 - t1)
+    nu = (tau - 0.5) / 3.0
+    # discrete (lattice) wave number of the second-order scheme: k_hat^2 = 2 - 2 cos k
+    assert abs(rate / (nu * (2 - 2 * np.cos(k))) - 1.0) < 2e-3
+
+
+@pytest.mark.parametrize("tau_b", [0.8, 1.5])
+def test_sound_wave_damping_gives_bulk_viscosity(tau_b):
+    """A density wave decays with Gamma = k^2 (4 nu/3 + nu_b)/2, nu_b = (2/3) c_s^2 (tau_b - 1/2),
+    and oscillates at c_s k."""
+    L = 64
+    tau_s = 0.9
+    cfg = lb_cfg((L, 1, 1), tau_s=tau_s, tau_b=tau_b)
+    k = 2 * np.pi / L
+    x = np.arange(L)
+    n = np.stack([oracle.lb_equilibrium(1.0 + 1e-5 * np.cos(k * xx), [0, 0, 0]) for xx in x], axis=1)
+    n = n.reshape(19, 1, 1, L)
+    _, _, _, c = oracle.lb_basis()
+    T = 600
+    rk, jk = [], []
+    for t in range(T):
+        n, u = oracle.lb_step(cfg, n)
+        rho = n.sum(0)[0, 0]
+        jx = np.einsum("i,ix->x", c[:, 0].astype(float), n[:, 0, 0, :])
+        rk.append(2.0 / L * ((rho - 1.0) * np.cos(k * x)).sum())
+        jk.append(2.0 / L * (jx * np.sin(k * x)).sum())
+    rk, jk = np.array(rk), np.array(jk)
+    E = rk ** 2 / 3.0 + jk ** 2                     # acoustic energy of the mode
+    nu, nub = (tau_s - 0.5) / 3.0, 2.0 / 9.0 * (tau_b - 0.5)
+    k2 = 2 - 2 * np.cos(k)
+    gamma = 0.5 * k2 * (4.0 * nu / 3.0 + nub)
+    # average log-energy slope over whole periods
+    period = 2 * np.pi / (np.sqrt(k2 / 3.0))
+    t1 = int(round(period)); t2 = int(round(5 * period))
+    rate = -(np.log(E[t2]) - np.log(E[t1])) / (t2 - t1) / 2.0
+    assert abs(rate / gamma - 1.0) < 2e-2
+    # frequency: zero crossings of the density amplitude
+    s = np.sign(rk)
+    crossings = np.nonzero(s[1:] != s[:-1])[0]
+    w_meas = np.pi / np.mean(np.diff(crossings))
+    assert abs(w_meas / (np.sin(k) / np.sqrt(3.0)) - 1.0) < 3e-2
+
+
+def test_printed_viscosities_back_solve_to_unit_relaxation():
+    """Eq. 15 solved for gamma with the viscosities the paper prints.  With LB mass density 1
+    (m0/h^3) the Fig. 2 values (dt = 0.2 tau, eta_s = 0.83, eta_b = 0.56) give gamma_s and
+    gamma_b within 0.005 of zero, i.e. relaxation times of one LB step -- the unit convention
+    the oracle uses; every printed pair maps to a stable relaxation (|gamma| < 1)."""
+    with open(os.path.join(GOLDEN, "viscosity_pins.json")) as fh:
+        pins = json.load(fh)["pins"]
+    for p in pins:
+        dt, rho = p["dt"], 1.0
+        cs2 = 1.0 / (3.0 * dt * dt)            # (h/dt)^2 / 3 in h^2/tau^2
+        xs = p["eta_s"] / (dt * rho * cs2 / 2.0)
+        xb = p["eta_b"] / (dt * rho * cs2 / 3.0)
+        gs = (xs - 1.0) / (xs + 1.0)
+        gb = (xb - 1.0) / (xb + 1.0)
+        assert -1.0 < gs < 1.0 and -1.0 < gb < 1.0
+        if p["figure"] == "Fig. 2":
+            assert abs(gs) < 5e-3 and abs(gb) < 5e-3
+        # the LB relaxation times that reproduce the printed values, tau = 1/(1 - gamma)
+        tau_s = 1.0 / (1.0 - gs)
+        assert abs(p["eta_s"] - rho * (tau_s - 0.5) / (3.0 * dt)) < 1e-12
+
+
+# ---------------------------------------------------------------------------------------------
+# Convection-diffusion (Eq. 3)
+# ---------------------------------------------------------------------------------------------
+def test_cd_conserves_mass_exactly():
+    cfg = cfg_small(grid=(5, 4, 6), ns=3, phi_p=0.4)
+    shp = (3, 6, 4, 5)
+    phi = 0.2 + 0.1 * inputs.uniform01(61, int(np.prod(shp))).reshape(shp)
+    mu = inputs.random_field(shp, seed=62)
+    u = 0.05 * inputs.random_field((3,) + shp[1:], seed=63)
+    m0 = phi.reshape(3, -1).sum(1)
+    out = oracle.cd_step(cfg, phi, mu, u, m0)
+    assert np.abs(out.reshape(3, -1).sum(1) - m0).max() < 1e-12
+
+
+def test_lax_wendroff_amplification_closed_form():
+    """M = 0 leaves pure two-step Lax-Wendroff: G = 1 - i C sin(t) - C^2 (1 - cos t)."""
+    L = 16
+    cfg = cfg_small(grid=(L, 3, 2))
+    cfg["M"] = 0.0
+    C = 0.3
+    th = 2 * np.pi * 3 / L
+    z, y, x = np.meshgrid(np.arange(2), np.arange(3), np.arange(L), indexing="ij")
+    eps = 1e-3
+    phi = np.stack([0.5 + eps * np.cos(th * x), 0.5 - eps * np.cos(th * x)])
+    u = np.zeros((3, 2, 3, L)); u[0] = C
+    out = oracle.cd_step(cfg, phi, np.zeros_like(phi), u, phi.reshape(2, -1).sum(1))
+    G = 1 - 1j * C * np.sin(th) - C * C * (1 - np.cos(th))
+    ref = 0.5 + eps * np.real(G * np.exp(1j * th * x))
+    assert np.abs(out[0] - ref).max() < 1e-15
+
+
+def test_uniform_state_with_uniform_velocity_is_steady():
+    cfg = cfg_small(grid=(4, 5, 3))
+    phi = np.stack([np.full((3, 5, 4), 0.4), np.full((3, 5, 4), 0.6)])
+    u = np.zeros((3, 3, 5, 4)); u[0], u[1], u[2] = 0.05, -0.02, 0.01
+    out = oracle.cd_step(cfg, phi, np.full_like(phi, 0.3), u, phi.reshape(2, -1).sum(1))
+    assert np.abs(out - phi).max() < 1e-15
+
+
+# ---------------------------------------------------------------------------------------------
+# Whole step: growth of small Fourier modes (linearised, RPA) in diffusion-only mode
+# ---------------------------------------------------------------------------------------------
+def rpa_amplification(cfg, kvec):
+    """Closed-form 2x2 amplification of one step for a Fourier mode about the uniform melt."""
+    N, nA = cfg["N"], cfg["nA"]
+    s_hat = symbol(cfg["a"], kvec)
+    types = [0] * nA + [1] * (N - nA)
+    S = np.zeros((2, 2))
+    for s in range(N):
+        for t in range(N):
+            S[types[s], types[t]] += s_hat ** abs(s - t)
+    S *= cfg["phi_p"] / N
+    chi = np.zeros((2, 2)); chi[0, 1] = chi[1, 0] = cfg["chi"][(0, 1)]
+    kap = cfg["kappa"]
+    ones = np.ones((2, 2))
+    Mmu = np.linalg.inv(S) + s_hat * chi + kap * ones            # d mu / d phi
+    phib = cfg["phi_p"] * np.array([nA / N, 1 - nA / N])
+    Phi = np.diag(phib)
+    k2 = sum(2 - 2 * np.cos(k) for k in kvec)
+    dt, M = cfg["dt"], cfg["M"]
+    c = 0.5 * dt * M
+    H = np.diag(1 / phib) + kap * ones
+    B = np.eye(2) + 6 * c * Phi @ H
+    Binv = np.linalg.inv(B)
+    It = Binv @ (c * (6 - k2) * Phi @ H)
+    P = sum(np.linalg.matrix_power(It, j) for j in range(cfg["cn_sweeps"]))
+    r = -dt * M * k2 * Phi @ Mmu
+    return np.eye(2) + P @ Binv @ r
+
+
+@pytest.mark.parametrize("mode", [(1, 0, 0), (1, 1, 0), (2, 1, 1)])
+def test_rpa_growth_of_small_modes(mode):
+    grid = (8, 8, 8)
+    cfg = inputs.melt(grid, 8, 0.5, 20.0, hydro=0, ncg_iters=60, dt=0.4)
+    cfg["nA"] = 3
+    k = [2 * np.pi * m / 8 for m in mode]
+    z, y, x = np.meshgrid(np.arange(8), np.arange(8), np.arange(8), indexing="ij")
+    wave = np.cos(k[0] * x + k[1] * y + k[2] * z)
+    amp = np.array([1e-6, -0.4e-6])
+    phib = np.array([3 / 8, 5 / 8])
+    phi = phib[:, None, None, None] + amp[:, None, None, None] * wave[None]
+    # start the inversion from the linear-response potential so it converges fully
+    U0 = np.zeros_like(phi)
+    out = oracle.step(cfg, phi, U0, None, phi.reshape(2, -1).sum(1))
+    assert out["info"][-1] < 1e-14
+    new = out["phi"] - phib[:, None, None, None]
+    meas = (new * wave[None]).reshape(2, -1).sum(1) / (wave * wave).sum()
+    A = rpa_amplification(cfg, k)
+    assert np.abs(meas - A @ amp).max() < 1e-5 * np.abs(amp).max()
+
+
+# ---------------------------------------------------------------------------------------------
+# Free energy (Eq. 1) and order parameters (Fig. 1, Fig. 3)
+# ---------------------------------------------------------------------------------------------
+def test_free_energy_uniform_closed_form():
+    cfg = cfg_small(grid=(3, 3, 3), chi=0.8)
+    phi = np.stack([np.full((3, 3, 3), 0.5), np.full((3, 3, 3), 0.5)])
+    assert abs(oracle.free_energy(cfg, np.zeros_like(phi), phi) - 0.8 * 0.25) < 1e-15
+
+
+def test_free_energy_derivative_is_chemical_potential():
+    """dF/dphi_I(r) = mu_I(r) (Eq. 4 is the functional derivative of Eq. 1), checked with a
+    mass-conserving finite difference and fully converged potentials."""
+    cfg = cfg_small(grid=(3, 2, 3), N=4, nA=2, chi=0.7, ncg_iters=200)
+    shp = (2, 3, 2, 3)
+    phi = 0.5 + 0.05 * inputs.random_field(shp, seed=71)
+    phi[1] = 1.0 - phi[0] + 0.01 * inputs.random_field(shp[1:], seed=72)
+    # block masses must equal those of the chains (V phi_p n_A / N each) for a solution to exist
+    phi[0] *= 9.0 / phi[0].sum()
+    phi[1] *= 9.0 / phi[1].sum()
+
+    def F(ph):
+        U, phim, info = oracle.ncg(cfg, ph, np.zeros_like(ph))
+        assert info[-1] < 1e-12
+        return oracle.free_energy(cfg, U, ph) * ph[0].size, U
+
+    _, U = F(phi)
+    mu = oracle.mu(cfg, U, phi)
+    h = 1e-5
+    i, j = (0, 1, 0, 2), (0, 2, 1, 0)
+    pp = phi.copy(); pp[i] += h; pp[j] -= h
+    pm = phi.copy(); pm[i] -= h; pm[j] += h
+    fd = (F(pp)[0] - F(pm)[0]) / (2 * h)
+    assert abs(fd - (mu[i] - mu[j])) < 1e-7
+
+
+def test_order_parameters_closed_form():
+    cfg = cfg_small(grid=(4, 1, 1), ns=3, phi_p=0.5)
+    phi = np.zeros((3, 1, 1, 4))
+    phi[0, 0, 0] = [0.1, 0.3, 0.1, 0.3]
+    phi[1, 0, 0] = [0.2, 0.2, 0.4, 0.4]
+    phi[2] = 1 - phi[0] - phi[1]
+    dA = np.array([-0.1, 0.1, -0.1, 0.1]); dB = np.array([-0.1, -0.1, 0.1, 0.1])
+    S = np.sqrt((dA ** 2 + dB ** 2 + (dA + dB) ** 2).sum() / 4)
+    assert abs(oracle.order_parameter(cfg, phi) - S) < 1e-15
+    assert abs(oracle.segregation(cfg, phi) - np.abs(dA + dB).mean()) < 1e-15
+
+
+def test_mrt_forcing_second_moment_closed_form():
+    """On one site (streaming maps it onto itself) the post-collision momentum flux is
+    rho u u + rho/3 I + gamma_s dev(Pi_neq) + gamma_b tr(Pi_neq)/3 I + Sigma (Eq. 13-14), with u the
+    half-force velocity of Eq. 9, Pi_neq the non-equilibrium second moment and Sigma of Eq. 14."""
+    ts, tb = 0.7, 1.6
+    gs, gb = 1 - 1 / ts, 1 - 1 / tb
+    cfg = lb_cfg((1, 1, 1), ts, tb)
+    _, w, _, c = oracle.lb_basis()
+    rho, u0 = 1.03, np.array([0.02, -0.03, 0.01])
+    n = oracle.lb_equilibrium(rho, u0) + 1e-3 * inputs.random_field((19,), seed=81) * w
+    rho = n.sum()
+    f = np.array([2e-3, 1e-3, -3e-3])
+    out, uo = oracle.lb_step(cfg, n.reshape(19, 1, 1, 1), f.reshape(3, 1, 1, 1))
+    cf = c.astype(float)
+    u = (n @ cf + 0.5 * f) / rho
+    assert np.abs(uo[:, 0, 0, 0] - u).max() < 1e-16
+    Pi = np.einsum("i,ia,ib->ab", n, cf, cf)
+    Pieq = rho * np.outer(u, u) + rho / 3 * np.eye(3)
+    Pn = Pi - Pieq
+    dev = Pn - np.trace(Pn) / 3 * np.eye(3)
+    uf = u @ f
+    Sig = 0.5 * (1 + gs) * (np.outer(u, f) + np.outer(f, u) - 2 / 3 * uf * np.eye(3)) + (1 + gb) / 3 * uf * np.eye(3)
+    expect = Pieq + gs * dev + gb * np.trace(Pn) / 3 * np.eye(3) + Sig
+    got = np.einsum("i,ia,ib->ab", out[:, 0, 0, 0], cf, cf)
+    assert np.abs(got - expect).max() < 1e-15
+    assert abs(out.sum() - rho) < 1e-15
+    assert np.abs(out[:, 0, 0, 0] @ cf - (n @ cf + f)).max() < 1e-16
+
+
+def test_uniform_chemical_potential_without_flow_is_stationary():
+    """Nonuniform compositions at uniform mu feel no diffusive flux (Eq. 3 with u = 0)."""
+    cfg = cfg_small(grid=(5, 4, 3), ns=3, phi_p=0.4)
+    shp = (3, 3, 4, 5)
+    phi = 0.2 + 0.15 * inputs.uniform01(91, int(np.prod(shp))).reshape(shp)
+    mu = np.stack([np.full(shp[1:], v) for v in (0.3, -1.2, 0.7)])
+    out = oracle.cd_step(cfg, phi, mu, None, phi.reshape(3, -1).sum(1))
+    assert np.abs(out - phi).max() < 1e-15
+
+
+def test_converged_crank_nicolson_conserves_mass_by_itself():
+    """The Jacobi sweeps converge to the flux-form Crank-Nicolson solution, which conserves each
+    species exactly (no mass shift applied here); two sweeps do not, which is why the step
+    applies the shift."""
+    shp = (2, 3, 4, 5)
+    phi = 0.35 + 0.3 * inputs.uniform01(95, int(np.prod(shp))).reshape(shp)
+    mu = 0.5 * inputs.random_field(shp, seed=96)
+    m0 = phi.reshape(2, -1).sum(1)
+    drift = {}
+    for K in (2, 400):
+        cfg = cfg_small(grid=(5, 4, 3), cn_sweeps=K)
+        cfg["dt"] = 0.05
+        out = oracle.cd_step(cfg, phi, mu, None, None)
+        drift[K] = np.abs(out.reshape(2, -1).sum(1) - m0).max()
+    assert drift[400] < 1e-13
+    assert drift[2] > 1e-6
