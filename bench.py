@@ -1,0 +1,352 @@
+#!/usr/bin/env python
+"""Benchmark of the coupled LB/DSCF time step on GB300.
+
+Metric: lattice site-updates per second of the whole coupled step (Fletcher-Reeves inversion
+with its propagator sweeps, chemical potential, LB collide-stream, convection-diffusion),
+V * steps / time, on the 128^3 asymmetric melt (f = 0.3, chi N = 25, N = 64), FP32 form, with
+the FP64 form reported beside it.  Inputs are synthetic (seeded noise around the homogeneous
+melt) and resident in HBM; the resident state (about 1.1 GB in FP32) is larger than L2.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 runs under torch.distributed (one process per GPU): every rank advances its own
+replica (different seed), weak scaling, no data-path collective; value = all sites updated
+by all ranks / the slowest rank's time.  --impl reference times the FP64 CPU oracle (the
+baseline arm) on the host cores, rank 0 only.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "site-updates/s per LB+DSCF step, 128^3, FP32 vs FP64 same GB300; % HBM roofline"
+UNIT = "site-updates/s"
+WORKLOAD = "melt128"
+
+
+def args_():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-forms", action="store_true", help="skip the FP64 form")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=20.0, help="seconds of oracle work for cpu_baseline")
+    return ap.parse_args()
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def workload_config(cfg):
+    return {"workload": f"{cfg['name']}: AB diblock melt, {cfg['grid'][0]}x{cfg['grid'][1]}x{cfg['grid'][2]} periodic, "
+                        f"N={cfg['N']}, nA={cfg['nA']}, chi N={cfg['chi'][(0, 1)] * cfg['N']:g}, dt={cfg['dt']} tau, "
+                        f"tau_s={cfg['tau_s']}, tau_b={cfg['tau_b']}, LB coupled",
+            "grid": list(cfg["grid"]), "N": cfg["N"], "nA": cfg["nA"], "ncg_iters": cfg["ncg_iters"],
+            "cn_sweeps": cfg["cn_sweeps"], "hydro": cfg["hydro"],
+            "l2": "no flush: the resident step state (G stack + fields, >1 GB) exceeds the 129 MB L2",
+            "parallelism": "replicas (one per GPU)"}
+
+
+# ---------------------------------------------------------------------------------------------
+# CPU oracle timing (the reference arm and the cpu_baseline leg)
+# ---------------------------------------------------------------------------------------------
+def oracle_sample_rate(cfg, budget_s, steps=None):
+    """Time the FP64 oracle on a cubic sub-box of the workload (same N, nA, chi, dt, relaxation
+    times, inversion and Jacobi counts), sized so that `steps` steps take about budget_s.
+    Returns (site-updates/s, cores, sample description, steps, seconds)."""
+    import numpy as np
+
+    import oracle
+    from paper_1204_2088_gb300 import inputs
+    oracle.build()
+    probe = dict(cfg, grid=(16, 16, 16))
+    phi = inputs.initial_fields(probe)
+    t = time.perf_counter()
+    oracle.step(probe, phi, np.zeros_like(phi), None, phi.reshape(2, -1).sum(1))
+    per_site = (time.perf_counter() - t) / 16 ** 3
+    n = steps or 3
+    L = 16
+    for cand in (24, 32, 40, 48, 64, 80, 96, 128):
+        if per_site * cand ** 3 * n <= budget_s:
+            L = cand
+    sample = dict(cfg, grid=(L, L, L))
+    phi = inputs.initial_fields(sample)
+    U = np.zeros_like(phi)
+    pop = None
+    m0 = phi.reshape(2, -1).sum(1)
+    t = time.perf_counter()
+    for _ in range(n):
+        st = oracle.step(sample, phi, U, pop, m0)
+        phi, U, pop = st["phi"], st["U"], st["pop"]
+    dt = time.perf_counter() - t
+    desc = (f"{n} coupled steps of the workload on a {L}^3 periodic sub-box (same N, nA, chi, dt, "
+            f"tau_s, tau_b, {cfg['ncg_iters']} inversion iterations, {cfg['cn_sweeps']} Jacobi sweeps), "
+            f"rate per site")
+    return L ** 3 * n / dt, oracle.num_threads(), desc, n, dt
+
+
+def _cpu_child(cfg, budget, q):
+    try:
+        q.put(oracle_sample_rate(cfg, budget))
+    except Exception as e:  # reported, not raised
+        q.put(repr(e))
+
+
+def cpu_baseline_spawned(cfg, budget):
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    p = ctx.Process(target=_cpu_child, args=(cfg, budget, q))
+    p.start()
+    res = q.get(timeout=600)
+    p.join(60)
+    if isinstance(res, str):
+        return None
+    rate, cores, desc, _, _ = res
+    return {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc}
+
+
+def run_reference(a):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    from paper_1204_2088_gb300 import inputs
+    cfg = inputs.workload(WORKLOAD)
+    total_budget = 150.0
+    per_step_budget = total_budget / max(1, a.steps + a.warmup)
+    import numpy as np  # noqa: F401
+    # warm-up steps run on the same sample size as the timed ones
+    rate, cores, desc, n, dt = oracle_sample_rate(cfg, per_step_budget * a.steps, steps=a.steps)
+    line = {"metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": a.gpus, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": 1e3 * dt / n, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": workload_config(cfg),
+            "impl": "reference",
+            "cpu_baseline": {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc},
+            "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.index), "-lms", "100"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for ln in open(self.path):
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def ncu_traffic(kernel_src):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on the current
+    source of the kernel (hash match); otherwise None."""
+    import hashlib
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    h = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()[:16]
+    ent = d.get("prop_sweep")
+    if ent and ent.get("source_sha256_16") == h:
+        return ent.get("dram_bytes_per_launch")
+    return None
+
+
+def run_ours(a):
+    import numpy as np
+    import torch
+
+    from paper_1204_2088_gb300 import dscf, inputs
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    cfg = inputs.workload(WORKLOAD, seed=11 + rank)
+    V = int(np.prod(cfg["grid"]))
+    N = cfg["N"]
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    def max_over_ranks(x):
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        return float(t.item())
+
+    phi0 = torch.from_numpy(inputs.initial_fields(cfg)).float().to(dev)
+    ctx = dscf.Context(cfg, dscf.FP32, device=dev)
+    ctx.set(dscf.PHI, phi0)
+    ctx.probe(True)
+    ctx.step(a.warmup)
+    ctx.status()
+    stream = torch.cuda.current_stream(dev)
+    clocks = ClockSampler(local)
+    torch.cuda.synchronize(dev)
+    barrier()
+    torch.cuda.synchronize(dev)
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    ctx.step(a.steps)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    barrier()
+    torch.cuda.synchronize(dev)
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    ctx.status()
+    ms_max = max_over_ranks(ms)
+    sweeps_ms, lb_ms, step_ms = ctx.probe_ms()
+    diag = ctx.diagnostics()
+    launches = ctx.launches_per_step()
+    value = world * V * a.steps / (ms_max * 1e-3)
+
+    # end to end through the C ABI with host buffers: upload phi, one step, read phi back
+    host = torch.empty(tuple(phi0.shape), dtype=torch.float32).pin_memory()
+    ctx.get_host(dscf.PHI, host)
+    ke2e = max(3, min(a.steps, 30))
+    torch.cuda.synchronize(dev)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(ke2e):
+        ctx.set(dscf.PHI, host)
+        ctx.step(1)
+        ctx.get_host(dscf.PHI, host)
+    torch.cuda.synchronize(dev)
+    t_e2e = max_over_ranks(time.perf_counter() - t0)
+    nbytes = host.numel() * host.element_size()
+    e2e = {"value": world * V * ke2e / t_e2e, "unit": UNIT, "h2d_bytes_per_step": nbytes,
+           "d2h_bytes_per_step": nbytes, "steps": ke2e}
+    ctx.close()
+    del ctx
+
+    forms = {}
+    if not a.no_forms:
+        k64 = max(2, min(10, a.steps // 10))
+        c64 = dscf.Context(cfg, dscf.FP64, device=dev)
+        c64.set(dscf.PHI, phi0.double())
+        c64.probe(True)
+        c64.step(2)
+        torch.cuda.synchronize(dev)
+        barrier()
+        e0.record(stream)
+        c64.step(k64)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        m64 = max_over_ranks(e0.elapsed_time(e1))
+        sw64, lb64, st64 = c64.probe_ms()
+        forms["fp64"] = {"value": world * V * k64 / (m64 * 1e-3), "unit": UNIT, "ms_per_step": m64 / k64,
+                         "steps": k64, "prop_sweep_ms_per_launch": sw64 / (2 * N), "lb_ms": lb64}
+        c64.close()
+        del c64
+
+    hbm, peak_kind = peaks()
+    # Dominant kernel: one contour step of the propagator sweeps (k_prop_fwd / k_prop_bwd).
+    # Algorithmic bytes per launch: the store-forward propagator solve must write G_s once and
+    # read it once per gradient evaluation plus read U and write phi: (8N + 16) B per site per
+    # evaluation over its 2N launches, i.e. (4 + 8/N) B per site per launch (FP32).
+    per_launch_s = sweeps_ms * 1e-3 / (2 * N)
+    alg_bytes = (4.0 + 8.0 / N) * V
+    achieved = alg_bytes / per_launch_s / 1e9
+    traffic = ncu_traffic(os.path.join(ROOT, "paper_1204_2088_gb300", "csrc", "dscf_prop.cu"))
+    roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+            "traffic": traffic, "kernel": "k_prop_fwd/k_prop_bwd (one contour step)",
+            "alg_bytes_per_launch": alg_bytes, "ms_per_launch": per_launch_s * 1e3, "peak_kind": peak_kind}
+    lb_alg = 180.0 * V
+    kernels = {"prop_sweep": {"ms_per_launch": per_launch_s * 1e3, "GBps": achieved},
+               "lb_collide_stream": {"ms": lb_ms, "alg_bytes": lb_alg,
+                                     "GBps": lb_alg / (lb_ms * 1e-3) / 1e9 if lb_ms > 0 else None},
+               "step_ms_probe": step_ms}
+
+    cpu = None
+    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+        cpu = cpu_baseline_spawned(cfg, a.cpu_budget)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
+                "warmup": a.warmup, "ms_per_step": ms_max / a.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": workload_config(cfg), "e2e": e2e, "gpu_launches": int(launches * a.steps),
+                "roofline": roof, "cpu_baseline": cpu, "clocks": clk, "forms": forms, "kernels": kernels,
+                "ncg": {"iters": diag["ncg_iters"], "line_search_evals_per_iter": 1,
+                        "gmax_start": diag["gmax_start"], "gmax_end": diag["gmax_end"]},
+                "umax": diag["umax"]}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    a = args_()
+    if a.impl == "reference":
+        return run_reference(a)
+    return run_ours(a)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,179 @@
+/*
+ * dscf.h -- C ABI of the GB300 (sm_103a) hot path of the hybrid lattice-Boltzmann / dynamic
+ * self-consistent-field method (Zhang, Sevink, Schmid, arXiv:1204.2088).
+ *
+ * One time step (Sec. 2, paragraph after Eq. 17: "LB steps alternate with propagations of
+ * Eq. (3)", each propagation needing the self-consistent potentials) is:
+ *   1. potentials U^n from the compositions phi^n by Fletcher-Reeves nonlinear CG on the
+ *      convex functional L(U) = (phi_p V/N) ln Q[U] + phi_s V ln<exp(-U_S)> + sum U phi^n,
+ *      whose gradient is phi^n - phi[U]; every gradient needs the Green propagators of
+ *      Eq. 17 (27-point linkage stencil) and the contour quadrature of Eq. 16;
+ *   2. chemical potentials mu^n, Eq. 4;
+ *   3. (hydro) one D3Q19 MRT lattice-Boltzmann collide-stream, Eq. 9-14 / Table 1, driven by
+ *      the body force f = -sum_I phi_I grad mu_I of Eq. 8;
+ *   4. convection-diffusion update of the compositions, Eq. 3: two-step Lax-Wendroff
+ *      convection by the LB velocity, Crank-Nicolson diffusion (Jacobi sweeps), FP64 mass
+ *      correction.
+ *
+ * Conventions.
+ *   - Lattice spacing h = 1, energies in k_B T, time in tau = h^2/(k_B T M) (Sec. 2 units).
+ *   - Fields are contiguous arrays, x fastest: index x + nx*(y + ny*z); several species are
+ *     stored species-major [I][V] in the order A, B, S.  Several replicas are stored one after
+ *     the other, replica-major, each with its own V = nx*ny*nz.
+ *   - The floating-point type of every field pointer is the context precision: double for
+ *     DSCF_FP64, float for DSCF_FP32.  Scalars, the partition function Q, all mass / momentum
+ *     sums and the line-search dot products are FP64 in both precisions.
+ *   - LB populations are exchanged as deviations n_i - w_i rho0 from the rest equilibrium, in
+ *     D3Q19 order 0:(000), 1..6: +x -x +y -y +z -z, 7..18: (+x+y) (-x-y) (+x-y) (-x+y) (+x+z)
+ *     (-x-z) (+x-z) (-x+z) (+y+z) (-y-z) (+y-z) (-y+z), as the populations n_i(r, t) that enter
+ *     the next collision (Eq. 10 left-hand side).
+ *   - LB runs in lattice units (Delta t_LB = 1, c_s^2 = 1/3); the force enters as dt^2 f and
+ *     the velocity u_lat = dt u is the Courant number the convection step uses.
+ *
+ * Memory and streams.  The library allocates no device memory: the caller passes one device
+ * workspace of at least dscf_workspace_bytes() bytes (256-byte aligned), which must outlive
+ * the context, and a CUDA stream (NULL = legacy default stream).  Every call is asynchronous
+ * on that stream unless stated otherwise.  The library owns only host-side bookkeeping plus
+ * one CUDA graph and one capture stream, released by dscf_free.
+ *
+ * Errors.  Every entry point returns DSCF_OK (0) or a negative code; it never aborts and
+ * never traps.  dscf_last_error() gives a message.  Device-side problems (non-finite sums) set
+ * a device status word that dscf_status() reads.
+ */
+#ifndef DSCF_H
+#define DSCF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    DSCF_OK = 0,
+    DSCF_ERR_ARG = -1,      /* invalid argument or parameter                           */
+    DSCF_ERR_CUDA = -2,     /* a CUDA runtime call failed                             */
+    DSCF_ERR_OOM = -3,      /* the workspace passed is too small                       */
+    DSCF_ERR_TIMEOUT = -4,  /* a bounded device wait gave up                           */
+    DSCF_ERR_NUMERIC = -5,  /* non-finite value in a reduction (status word)           */
+    DSCF_ERR_STATE = -6     /* call not valid in the current context state             */
+};
+
+enum { DSCF_FP64 = 0, DSCF_FP32 = 1 };
+
+/* Field selectors for dscf_get_fields / dscf_set_fields. */
+enum {
+    DSCF_FIELD_PHI = 0,   /* compositions phi_I            [ns][V]                      */
+    DSCF_FIELD_U = 1,     /* potentials U_I                [ns][V]                      */
+    DSCF_FIELD_MU = 2,    /* chemical potentials mu_I      [ns][V]  (get only)          */
+    DSCF_FIELD_VEL = 3,   /* LB velocity u_lat (Eq. 9)     [3][V]   (get only)          */
+    DSCF_FIELD_POP = 4,   /* LB population deviations      [19][V]                      */
+    DSCF_FIELD_PHIM = 5   /* phi[U] of the current U       [ns][V]  (get only)          */
+};
+
+/*
+ * Parameters of one replica (Sec. 2 model and units; Sec. 3 workloads).
+ *   nx, ny, nz   periodic lattice (h = 1), each >= 1
+ *   ns           2 = A,B melt; 3 = A,B copolymer plus single-bead solvent S (Eq. 2, 3rd line)
+ *   N, nA        beads per chain N_p and A-block length n, 1 <= nA < N (bead s is A iff s <= nA)
+ *   phi_p        mean copolymer volume fraction (1 in a melt); the solvent takes 1 - phi_p
+ *   chi[9]       Flory-Huggins chi_IJ (row-major 3x3, symmetric, zero diagonal), Sec. 2
+ *   kappa        Helfand compressibility kappa_H v0 / k_B T (paper: 10)
+ *   a            statistical segment length in h (paper: 1.1543); the 27-point linkage
+ *                stencil is the tensor product of (alpha, 1 - 2 alpha, alpha), alpha = a^2/6,
+ *                which has the per-axis variance a^2/3 of a Gaussian bond; needs alpha < 1/2
+ *   dt, M        time step in tau and mobility (paper: M = 1)
+ *   tau_s, tau_b LB shear / bulk relaxation times; gamma = 1 - 1/tau (Eq. 13, 15); > 1/2
+ *   rho0         LB reference mass density (1)
+ *   hydro        0: diffusion only (u = 0); 1: LB coupled
+ *   ncg_iters    Fletcher-Reeves iterations per step (fixed count, 0..32)
+ *   cn_sweeps    Jacobi sweeps of the Crank-Nicolson system (even, 2..64)
+ *   phi_floor    floor on phi inside the local curvature of mu (e.g. 1e-6)
+ */
+typedef struct {
+    int32_t nx, ny, nz;
+    int32_t ns;
+    int32_t N, nA;
+    double phi_p;
+    double chi[9];
+    double kappa;
+    double a;
+    double dt, M;
+    double tau_s, tau_b, rho0;
+    int32_t hydro;
+    int32_t ncg_iters;
+    int32_t cn_sweeps;
+    double phi_floor;
+} dscf_params;
+
+typedef struct dscf_ctx dscf_ctx;
+
+/* Bytes of device workspace needed for n_replicas replicas with parameters p[0..n-1] in the
+ * given precision.  Returns 0 if the parameters are invalid. */
+size_t dscf_workspace_bytes(const dscf_params* p, int32_t n_replicas, int32_t precision);
+
+/*
+ * Create a context.  p: n_replicas parameter sets (host memory, copied).  workspace: device
+ * pointer (caller-owned, 256-byte aligned, >= dscf_workspace_bytes).  stream: cudaStream_t or
+ * NULL.  The initial state is phi = homogeneous melt/solution, U = 0, LB at rest; set the
+ * compositions with dscf_set_fields before stepping.  Synchronises the stream once.
+ * Errors: DSCF_ERR_ARG (bad parameters), DSCF_ERR_OOM (workspace too small), DSCF_ERR_CUDA.
+ */
+int dscf_init(const dscf_params* p, int32_t n_replicas, int32_t precision, void* workspace,
+              size_t workspace_bytes, void* stream, dscf_ctx** out);
+
+/* Advance every replica by n_steps coupled time steps (steps 1-4 above).  The step sequence
+ * is captured once into a CUDA graph and launched n_steps times on the context stream. */
+int dscf_step(dscf_ctx* ctx, int32_t n_steps);
+
+/* Forward density map alone (Eq. 2 via Eq. 16-17): phi_out = phi[U_in], for every replica.
+ * U_in, phi_out: device pointers, [rep][ns][V] in the context precision.  Does not touch the
+ * context's U or phi (uses its propagator buffers). */
+int dscf_densities(dscf_ctx* ctx, const void* U_in, void* phi_out);
+
+/* n_steps LB collide-stream steps alone (Eq. 9-14).  force: device pointer [rep][3][V] of
+ * lattice-unit body force, or NULL for the thermodynamic force of the current phi and mu. */
+int lb_step(dscf_ctx* ctx, const void* force, int32_t n_steps);
+
+/* Copy a field out of / into the context.  on_host != 0: dst/src is host memory (the call
+ * synchronises the stream before returning for gets); otherwise device memory.  Setting PHI
+ * also sets the per-species mass targets of the mass correction to the new totals; setting U
+ * makes the next step recompute phi[U]. */
+int dscf_get_fields(dscf_ctx* ctx, int32_t which, void* dst, int32_t on_host);
+int dscf_set_fields(dscf_ctx* ctx, int32_t which, const void* src, int32_t on_host);
+
+/* FP64 diagnostics of one replica (synchronises).  out[0..23]:
+ *  0..2  sum_r phi_I after the last step, 3..5 its drift before the mass correction,
+ *  6 LB mass sum_r rho, 7..9 LB momentum after collision, 10 max |u_lat|,
+ *  11 Q of the last gradient evaluation, 12 <exp(-U_S)>, 13 NCG iterations per step,
+ *  14 <g,g> and 15 max|g| at the start of the last inversion, 16 <g,g> and 17 max|g|
+ *  at its end, 18 steps done, 19..23 reserved (0). */
+int dscf_diagnostics(dscf_ctx* ctx, int32_t replica, double* out);
+
+/* Synchronise the stream and return the device status word as an error code (DSCF_OK or
+ * DSCF_ERR_NUMERIC) or DSCF_ERR_CUDA if a kernel failed. */
+int dscf_status(dscf_ctx* ctx);
+
+/* Release host-side state (graph, capture stream).  The workspace stays the caller's. */
+int dscf_free(dscf_ctx* ctx);
+
+/* Message of the last error on this context (or of the last failed dscf_init if ctx NULL). */
+const char* dscf_last_error(const dscf_ctx* ctx);
+
+/* Number of kernels one dscf_step(ctx, 1) launches (for launch accounting). */
+int64_t dscf_launches_per_step(const dscf_ctx* ctx);
+
+/* Timing probe.  enable != 0 makes the next dscf_step capture CUDA events (created by the
+ * library) into the step graph: around the 2N contour-sweep launches of the first gradient
+ * evaluation of the step, around the LB collide-stream launch, and around the whole step.
+ * dscf_probe_ms synchronises the stream and returns, for the most recent step, the elapsed
+ * milliseconds of those three regions (ms[0] sweeps, ms[1] LB, ms[2] step); regions that did
+ * not run read 0.  DSCF_ERR_STATE if the probe is off or no step ran since enabling it. */
+int dscf_probe(dscf_ctx* ctx, int32_t enable);
+int dscf_probe_ms(dscf_ctx* ctx, float* ms);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DSCF_H */

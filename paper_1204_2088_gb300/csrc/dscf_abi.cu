@@ -1,0 +1,562 @@
+// C ABI of the library (declared in include/dscf.h): parameter validation, the layout of the
+// caller's workspace, replica tiling, capture of one time step into a CUDA graph, and the
+// entry points.  Device memory is never allocated here.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/dscf.h"
+#include "dscf_internal.cuh"
+
+using namespace dscf;
+
+namespace {
+
+constexpr int kTX = 32, kTY = 8;   // propagator tile (must match the kernels)
+thread_local std::string g_init_error;
+
+struct Layout {
+    std::vector<Rep> reps;          // host copy, pointers filled by place()
+    std::vector<int> tile2rep, blk2rep;
+    std::vector<int> fwd_grid;      // [s] for s = 1..Nmax (index s), tiles of replicas with N >= s
+    int ntiles = 0, nblk = 0, Nmax = 0;
+    size_t bytes = 0;
+    // offsets of the shared blocks
+    size_t off_reps = 0, off_t2r = 0, off_b2r = 0, off_status = 0;
+};
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+bool validate(const dscf_params* p, int n, std::string& why) {
+    if (!p || n < 1) { why = "no replicas"; return false; }
+    for (int r = 0; r < n; ++r) {
+        const dscf_params& q = p[r];
+        char buf[160];
+        auto bad = [&](const char* m) { snprintf(buf, sizeof buf, "replica %d: %s", r, m); why = buf; return false; };
+        if (q.nx < 1 || q.ny < 1 || q.nz < 1) return bad("grid sizes must be >= 1");
+        if ((long long)q.nx * q.ny * q.nz > (1LL << 31) - 1) return bad("grid too large");
+        if (q.ns != 2 && q.ns != 3) return bad("ns must be 2 or 3");
+        if (q.N < 2 || q.N > 4096 || q.nA < 1 || q.nA >= q.N) return bad("need 1 <= nA < N <= 4096");
+        if (!(q.phi_p > 0.0 && q.phi_p <= 1.0)) return bad("phi_p must be in (0, 1]");
+        if (q.ns == 2 && q.phi_p != 1.0) return bad("a melt (ns = 2) needs phi_p = 1");
+        const double al = q.a * q.a / 6.0;
+        if (!(q.a > 0.0) || !(al < 0.5)) return bad("segment length must satisfy 0 < a^2/6 < 1/2");
+        if (!(q.dt > 0.0) || !(q.M >= 0.0)) return bad("dt > 0 and M >= 0 required");
+        if (!(q.tau_s > 0.5) || !(q.tau_b > 0.5)) return bad("LB relaxation times must exceed 1/2");
+        if (!(q.rho0 > 0.0)) return bad("rho0 must be positive");
+        if (q.ncg_iters < 0 || q.ncg_iters > kMaxNcg) return bad("ncg_iters must be in 0..32");
+        if (q.cn_sweeps < 2 || q.cn_sweeps > 64 || (q.cn_sweeps & 1)) return bad("cn_sweeps must be even, 2..64");
+        if (!(q.phi_floor > 0.0)) return bad("phi_floor must be positive");
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j)
+                if (q.chi[3 * i + j] != q.chi[3 * j + i] || (i == j && q.chi[3 * i + j] != 0.0))
+                    return bad("chi must be symmetric with zero diagonal");
+        if (q.ncg_iters != p[0].ncg_iters || q.cn_sweeps != p[0].cn_sweeps || q.hydro != p[0].hydro)
+            return bad("ncg_iters, cn_sweeps and hydro must be the same for all replicas");
+    }
+    return true;
+}
+
+// Tiling and workspace layout.  With base == nullptr only sizes are computed.
+Layout make_layout(const dscf_params* p, int n, int prec, char* base) {
+    Layout L;
+    const size_t es = (prec == DSCF_FP64) ? sizeof(double) : sizeof(float);
+    L.reps.resize(n);
+    // replicas in order of decreasing chain length own the first tiles (prefix property)
+    std::vector<int> order(n);
+    for (int r = 0; r < n; ++r) order[r] = r;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return p[a].N > p[b].N; });
+    long long ext = 0, vb = 0;
+    for (int r = 0; r < n; ++r) {
+        Rep& R = L.reps[r];
+        std::memset(&R, 0, sizeof(Rep));
+        const dscf_params& q = p[r];
+        R.nx = q.nx; R.ny = q.ny; R.nz = q.nz; R.ns = q.ns; R.N = q.N; R.nA = q.nA;
+        R.V = (long long)q.nx * q.ny * q.nz;
+        R.tiles_x = (q.nx + kTX - 1) / kTX;
+        R.tiles_y = (q.ny + kTY - 1) / kTY;
+        R.zc = q.nz >= 64 ? 16 : std::max(1, std::min(q.nz, std::max(4, q.nz / 4)));
+        R.tiles_z = (q.nz + R.zc - 1) / R.zc;
+        R.ntiles = R.tiles_x * R.tiles_y * R.tiles_z;
+        long long nb = (R.V + kFlatThreads - 1) / kFlatThreads;
+        nb = std::min<long long>(nb, kMaxFlatBlocks);
+        long long chunk = (R.V + nb - 1) / nb;
+        chunk = (chunk + kFlatThreads - 1) / kFlatThreads * kFlatThreads;
+        R.chunk = (int)chunk;
+        R.nblk = (int)((R.V + chunk - 1) / chunk);
+        R.hydro = q.hydro;
+        R.cn_sweeps = q.cn_sweeps;
+        R.phi_p = q.phi_p; R.kappa = q.kappa; R.alpha = q.a * q.a / 6.0; R.dt = q.dt; R.M = q.M;
+        R.gs = 1.0 - 1.0 / q.tau_s; R.gb = 1.0 - 1.0 / q.tau_b; R.rho0 = q.rho0; R.phi_floor = q.phi_floor;
+        for (int i = 0; i < 9; ++i) R.chi[i] = q.chi[i];
+        const double f = (double)q.nA / q.N;
+        R.mass0[0] = (double)R.V * q.phi_p * f;
+        R.mass0[1] = (double)R.V * q.phi_p * (1.0 - f);
+        R.mass0[2] = q.ns == 3 ? (double)R.V * (1.0 - q.phi_p) : 0.0;
+        R.ext_off = ext;
+        R.vbase = vb;
+        ext += (long long)q.ns * R.V;
+        vb += R.V;
+        R.part_stride = std::max(R.ntiles, R.nblk);
+        L.Nmax = std::max(L.Nmax, q.N);
+    }
+    for (int k = 0; k < n; ++k) {
+        Rep& R = L.reps[order[k]];
+        R.tile0 = L.ntiles;
+        for (int t = 0; t < R.ntiles; ++t) L.tile2rep.push_back(order[k]);
+        L.ntiles += R.ntiles;
+        R.blk0 = L.nblk;
+        for (int b = 0; b < R.nblk; ++b) L.blk2rep.push_back(order[k]);
+        L.nblk += R.nblk;
+    }
+    L.fwd_grid.assign(L.Nmax + 2, 0);
+    for (int s = 1; s <= L.Nmax; ++s)
+        for (int r = 0; r < n; ++r)
+            if (L.reps[r].N >= s) L.fwd_grid[s] += L.reps[r].ntiles;
+    // workspace
+    size_t off = 0;
+    auto take = [&](size_t bytes) -> void* {
+        void* ptr = base ? (void*)(base + off) : nullptr;
+        off = align256(off + bytes);
+        return ptr;
+    };
+    for (int r = 0; r < n; ++r) {
+        Rep& R = L.reps[r];
+        const size_t V = (size_t)R.V, ns = (size_t)R.ns;
+        R.phi = take(ns * V * es);
+        R.U = take(ns * V * es);
+        R.mu = take(ns * V * es);
+        R.d = take(ns * V * es);
+        R.phim = take(ns * V * es);
+        R.q = take(2 * V * es);
+        R.E = take(ns * V * es);
+        R.G = take((size_t)R.N * V * es);
+        R.Gp0 = take(V * es);
+        R.Gp1 = take(V * es);
+        R.u = take(3 * V * es);
+        R.pop0 = take(19 * V * es);
+        R.pop1 = take(19 * V * es);
+        R.del0 = take(ns * V * es);
+        R.del1 = take(ns * V * es);
+        R.rhs = take(ns * V * es);
+        R.part = (double*)take((size_t)NPART * R.part_stride * sizeof(double));
+        R.scal = (double*)take((size_t)kScalStride * sizeof(double));
+    }
+    L.off_reps = off; take(sizeof(Rep) * n);
+    L.off_t2r = off; take(sizeof(int) * L.ntiles);
+    L.off_b2r = off; take(sizeof(int) * L.nblk);
+    L.off_status = off; take(sizeof(int) * 64);
+    L.bytes = off;
+    return L;
+}
+
+__global__ void k_fill(double* p, long long n, double v) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) p[i] = v;
+}
+__global__ void k_fillf(float* p, long long n, float v) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) p[i] = v;
+}
+
+}  // namespace
+
+struct dscf_ctx {
+    int nrep = 0, prec = 0, device = 0;
+    std::vector<dscf_params> params;
+    Layout L;
+    char* ws = nullptr;
+    cudaStream_t stream = nullptr, cap = nullptr;
+    Rep* d_reps = nullptr;
+    int* d_t2r = nullptr;
+    int* d_b2r = nullptr;
+    int* d_status = nullptr;
+    int* d_counter = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    bool probe = false, probe_ran = false;
+    cudaEvent_t ev[6] = {};
+    bool phim_stale = true;
+    long long steps = 0;
+    int64_t launches = 0;
+    std::string err;
+};
+
+namespace {
+
+int fail(dscf_ctx* c, int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (c) c->err = buf; else g_init_error = buf;
+    return code;
+}
+
+int cuda_check(dscf_ctx* c, cudaError_t e, const char* what) {
+    if (e == cudaSuccess) return DSCF_OK;
+    return fail(c, DSCF_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+Launch launch_of(dscf_ctx* c, cudaStream_t s) {
+    Launch L;
+    L.reps = c->d_reps;
+    L.tile2rep = c->d_t2r;
+    L.blk2rep = c->d_b2r;
+    L.status = c->d_status;
+    L.counter = c->d_counter;
+    L.nblk_total = c->L.nblk;
+    L.stream = s;
+    return L;
+}
+
+// One gradient evaluation: Boltzmann factors, forward and backward contour sweeps.
+template <typename T>
+int64_t enqueue_eval(dscf_ctx* c, const Launch& L, int exp_mode, int k, const void* Uext) {
+    int64_t n = 0;
+    launch_exp<T>(L, exp_mode, k, Uext); ++n;
+    for (int s = 1; s <= c->L.Nmax; ++s) { launch_prop_fwd<T>(L, s, c->L.fwd_grid[s]); ++n; }
+    for (int j = 0; j < c->L.Nmax; ++j) { launch_prop_bwd<T>(L, j, c->L.fwd_grid[j + 1]); ++n; }
+    return n;
+}
+
+// The launch sequence of one time step (see include/dscf.h, steps 1-4).
+template <typename T>
+int64_t enqueue_step(dscf_ctx* c, const Launch& L) {
+    const int K = c->params[0].ncg_iters;
+    auto mark = [&](int i) { if (c->probe) cudaEventRecordWithFlags(c->ev[i], L.stream, cudaEventRecordExternal); };
+    int64_t n = 0;
+    mark(4);
+    if (K > 0) { launch_dir<T>(L, 0, 0); ++n; }
+    for (int k = 0; k < K; ++k) {
+        launch_exp<T>(L, 1, k, nullptr); ++n;
+        if (k == 0) mark(0);
+        for (int s = 1; s <= c->L.Nmax; ++s) { launch_prop_fwd<T>(L, s, c->L.fwd_grid[s]); ++n; }
+        for (int j = 0; j < c->L.Nmax; ++j) { launch_prop_bwd<T>(L, j, c->L.fwd_grid[j + 1]); ++n; }
+        if (k == 0) mark(1);
+        launch_trial<T>(L); ++n;
+        n += enqueue_eval<T>(c, L, 2, k, nullptr);
+        launch_grad<T>(L, k); ++n;
+        if (k + 1 < K) { launch_dir<T>(L, 1, k); ++n; }
+    }
+    launch_mu<T>(L, K); ++n;
+    if (c->params[0].hydro) {
+        mark(2);
+        launch_lb<T>(L, nullptr); ++n;
+        mark(3);
+        launch_step_end(L); ++n;
+    }
+    launch_cd<T>(L, c->params[0].cn_sweeps);
+    n += 3 + c->params[0].cn_sweeps;
+    mark(5);
+    return n;
+}
+
+template <typename T>
+int refresh_phim(dscf_ctx* c) {
+    const Launch L = launch_of(c, c->stream);
+    enqueue_eval<T>(c, L, 0, 0, nullptr);
+    launch_grad<T>(L, -1);
+    c->phim_stale = false;
+    return cuda_check(c, cudaGetLastError(), "phi[U] refresh");
+}
+
+template <typename T>
+int build_graph(dscf_ctx* c) {
+    cudaGraph_t g = nullptr;
+    int rc = cuda_check(c, cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal), "begin capture");
+    if (rc) return rc;
+    const Launch L = launch_of(c, c->cap);
+    c->launches = enqueue_step<T>(c, L);
+    cudaError_t le = cudaGetLastError();
+    cudaError_t ee = cudaStreamEndCapture(c->cap, &g);
+    if (le != cudaSuccess) { if (g) cudaGraphDestroy(g); return cuda_check(c, le, "kernel launch during capture"); }
+    if (ee != cudaSuccess) return cuda_check(c, ee, "end capture");
+    cudaError_t ie = cudaGraphInstantiate(&c->exec, g, 0);
+    cudaGraphDestroy(g);
+    return cuda_check(c, ie, "graph instantiate");
+}
+
+int set_dev(dscf_ctx* c) { return cuda_check(c, cudaSetDevice(c->device), "cudaSetDevice"); }
+
+}  // namespace
+
+extern "C" {
+
+size_t dscf_workspace_bytes(const dscf_params* p, int32_t n, int32_t precision) {
+    std::string why;
+    if (precision != DSCF_FP64 && precision != DSCF_FP32) return 0;
+    if (!validate(p, n, why)) return 0;
+    return make_layout(p, n, precision, nullptr).bytes;
+}
+
+int dscf_init(const dscf_params* p, int32_t n, int32_t precision, void* workspace, size_t wbytes, void* stream,
+              dscf_ctx** out) {
+    if (!out) return fail(nullptr, DSCF_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    std::string why;
+    if (precision != DSCF_FP64 && precision != DSCF_FP32) return fail(nullptr, DSCF_ERR_ARG, "bad precision");
+    if (!validate(p, n, why)) return fail(nullptr, DSCF_ERR_ARG, "%s", why.c_str());
+    if (!workspace || ((uintptr_t)workspace & 255)) return fail(nullptr, DSCF_ERR_ARG, "workspace must be 256-byte aligned");
+    dscf_ctx* c = new (std::nothrow) dscf_ctx;
+    if (!c) return fail(nullptr, DSCF_ERR_OOM, "host allocation failed");
+    c->nrep = n;
+    c->prec = precision;
+    c->params.assign(p, p + n);
+    c->stream = (cudaStream_t)stream;
+    c->ws = (char*)workspace;
+    cudaPointerAttributes pa;
+    if (cudaPointerGetAttributes(&pa, workspace) != cudaSuccess || pa.type != cudaMemoryTypeDevice) {
+        cudaGetLastError();
+        delete c;
+        return fail(nullptr, DSCF_ERR_ARG, "workspace is not device memory");
+    }
+    c->device = pa.device;
+    if (int rc = set_dev(c)) { g_init_error = c->err; delete c; return rc; }
+    c->L = make_layout(p, n, precision, c->ws);
+    if (wbytes < c->L.bytes) {
+        delete c;
+        return fail(nullptr, DSCF_ERR_OOM, "workspace has %zu bytes, needs %zu", wbytes, c->L.bytes);
+    }
+    c->d_reps = (Rep*)(c->ws + c->L.off_reps);
+    c->d_t2r = (int*)(c->ws + c->L.off_t2r);
+    c->d_b2r = (int*)(c->ws + c->L.off_b2r);
+    c->d_status = (int*)(c->ws + c->L.off_status);
+    c->d_counter = c->d_status + 1;
+    auto chk = [&](cudaError_t e, const char* w) { return cuda_check(c, e, w); };
+    int rc = 0;
+    rc = rc ? rc : chk(cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking), "capture stream");
+    rc = rc ? rc : chk(cudaMemcpyAsync(c->d_reps, c->L.reps.data(), sizeof(Rep) * n, cudaMemcpyHostToDevice, c->stream), "reps");
+    rc = rc ? rc : chk(cudaMemcpyAsync(c->d_t2r, c->L.tile2rep.data(), sizeof(int) * c->L.ntiles, cudaMemcpyHostToDevice, c->stream), "t2r");
+    rc = rc ? rc : chk(cudaMemcpyAsync(c->d_b2r, c->L.blk2rep.data(), sizeof(int) * c->L.nblk, cudaMemcpyHostToDevice, c->stream), "b2r");
+    rc = rc ? rc : chk(cudaMemsetAsync(c->d_status, 0, sizeof(int) * 64, c->stream), "status");
+    const size_t es = precision == DSCF_FP64 ? 8 : 4;
+    for (int r = 0; r < n && !rc; ++r) {
+        const Rep& R = c->L.reps[r];
+        const size_t V = (size_t)R.V;
+        rc = rc ? rc : chk(cudaMemsetAsync(R.U, 0, R.ns * V * es, c->stream), "U");
+        rc = rc ? rc : chk(cudaMemsetAsync(R.d, 0, R.ns * V * es, c->stream), "d");
+        rc = rc ? rc : chk(cudaMemsetAsync(R.mu, 0, R.ns * V * es, c->stream), "mu");
+        rc = rc ? rc : chk(cudaMemsetAsync(R.u, 0, 3 * V * es, c->stream), "u");
+        rc = rc ? rc : chk(cudaMemsetAsync(R.pop0, 0, 19 * V * es, c->stream), "pop0");
+        rc = rc ? rc : chk(cudaMemsetAsync(R.pop1, 0, 19 * V * es, c->stream), "pop1");
+        rc = rc ? rc : chk(cudaMemsetAsync(R.part, 0, (size_t)NPART * R.part_stride * 8, c->stream), "part");
+        rc = rc ? rc : chk(cudaMemsetAsync(R.scal, 0, (size_t)kScalStride * 8, c->stream), "scal");
+        const double f = (double)R.nA / R.N;
+        const double vals[3] = {R.phi_p * f, R.phi_p * (1.0 - f), 1.0 - R.phi_p};
+        for (int I = 0; I < R.ns; ++I) {
+            if (precision == DSCF_FP64)
+                k_fill<<<256, 256, 0, c->stream>>>((double*)R.phi + I * V, (long long)V, vals[I]);
+            else
+                k_fillf<<<256, 256, 0, c->stream>>>((float*)R.phi + I * V, (long long)V, (float)vals[I]);
+        }
+    }
+    rc = rc ? rc : chk(cudaGetLastError(), "fill");
+    rc = rc ? rc : chk(cudaStreamSynchronize(c->stream), "init sync");
+    if (rc) {
+        g_init_error = c->err;
+        if (c->cap) cudaStreamDestroy(c->cap);
+        delete c;
+        return rc;
+    }
+    *out = c;
+    return DSCF_OK;
+}
+
+int dscf_step(dscf_ctx* c, int32_t n_steps) {
+    if (!c) return DSCF_ERR_ARG;
+    if (n_steps < 0) return fail(c, DSCF_ERR_ARG, "n_steps < 0");
+    if (int rc = set_dev(c)) return rc;
+    if (c->phim_stale) {
+        int rc = c->prec == DSCF_FP64 ? refresh_phim<double>(c) : refresh_phim<float>(c);
+        if (rc) return rc;
+    }
+    if (!c->exec) {
+        int rc = c->prec == DSCF_FP64 ? build_graph<double>(c) : build_graph<float>(c);
+        if (rc) return rc;
+    }
+    for (int i = 0; i < n_steps; ++i) {
+        if (int rc = cuda_check(c, cudaGraphLaunch(c->exec, c->stream), "graph launch")) return rc;
+    }
+    c->steps += n_steps;
+    if (n_steps > 0 && c->probe) c->probe_ran = true;
+    return DSCF_OK;
+}
+
+int dscf_densities(dscf_ctx* c, const void* U_in, void* phi_out) {
+    if (!c || !U_in || !phi_out) return c ? fail(c, DSCF_ERR_ARG, "NULL field pointer") : DSCF_ERR_ARG;
+    if (int rc = set_dev(c)) return rc;
+    const Launch L = launch_of(c, c->stream);
+    if (c->prec == DSCF_FP64) {
+        enqueue_eval<double>(c, L, 3, 0, U_in);
+        launch_dens_out<double>(L, phi_out);
+    } else {
+        enqueue_eval<float>(c, L, 3, 0, U_in);
+        launch_dens_out<float>(L, phi_out);
+    }
+    // the propagator buffers no longer hold phi[U] of the context's U
+    c->phim_stale = true;
+    return cuda_check(c, cudaGetLastError(), "densities");
+}
+
+int lb_step(dscf_ctx* c, const void* force, int32_t n_steps) {
+    if (!c) return DSCF_ERR_ARG;
+    if (n_steps < 0) return fail(c, DSCF_ERR_ARG, "n_steps < 0");
+    if (int rc = set_dev(c)) return rc;
+    const Launch L = launch_of(c, c->stream);
+    for (int i = 0; i < n_steps; ++i) {
+        if (c->prec == DSCF_FP64) launch_lb<double>(L, force); else launch_lb<float>(L, force);
+        launch_step_end(L);
+    }
+    return cuda_check(c, cudaGetLastError(), "lb_step");
+}
+
+int dscf_get_fields(dscf_ctx* c, int32_t which, void* dst, int32_t on_host) {
+    if (!c || !dst) return c ? fail(c, DSCF_ERR_ARG, "NULL destination") : DSCF_ERR_ARG;
+    if (int rc = set_dev(c)) return rc;
+    const size_t es = c->prec == DSCF_FP64 ? 8 : 4;
+    const cudaMemcpyKind kind = on_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+    if (which == DSCF_FIELD_POP) {
+        if (on_host) return fail(c, DSCF_ERR_ARG, "populations are exchanged in device memory only");
+        const Launch L = launch_of(c, c->stream);
+        if (c->prec == DSCF_FP64) launch_pop_copy<double>(L, dst, 0); else launch_pop_copy<float>(L, dst, 0);
+        return cuda_check(c, cudaGetLastError(), "get populations");
+    }
+    char* out = (char*)dst;
+    for (int r = 0; r < c->nrep; ++r) {
+        const Rep& R = c->L.reps[r];
+        const size_t V = (size_t)R.V;
+        const void* srcp = nullptr;
+        size_t n = 0, off = 0;
+        switch (which) {
+            case DSCF_FIELD_PHI: srcp = R.phi; n = R.ns * V; off = R.ext_off; break;
+            case DSCF_FIELD_U: srcp = R.U; n = R.ns * V; off = R.ext_off; break;
+            case DSCF_FIELD_MU: srcp = R.mu; n = R.ns * V; off = R.ext_off; break;
+            case DSCF_FIELD_PHIM: srcp = R.phim; n = R.ns * V; off = R.ext_off; break;
+            case DSCF_FIELD_VEL: srcp = R.u; n = 3 * V; off = 3 * R.vbase; break;
+            default: return fail(c, DSCF_ERR_ARG, "unknown field %d", which);
+        }
+        if (int rc = cuda_check(c, cudaMemcpyAsync(out + off * es, srcp, n * es, kind, c->stream), "get field")) return rc;
+    }
+    if (on_host) return cuda_check(c, cudaStreamSynchronize(c->stream), "get field sync");
+    return DSCF_OK;
+}
+
+int dscf_set_fields(dscf_ctx* c, int32_t which, const void* src, int32_t on_host) {
+    if (!c || !src) return c ? fail(c, DSCF_ERR_ARG, "NULL source") : DSCF_ERR_ARG;
+    if (int rc = set_dev(c)) return rc;
+    const size_t es = c->prec == DSCF_FP64 ? 8 : 4;
+    const cudaMemcpyKind kind = on_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+    const Launch L = launch_of(c, c->stream);
+    if (which == DSCF_FIELD_POP) {
+        if (on_host) return fail(c, DSCF_ERR_ARG, "populations are exchanged in device memory only");
+        if (c->prec == DSCF_FP64) launch_pop_copy<double>(L, (void*)src, 1); else launch_pop_copy<float>(L, (void*)src, 1);
+        return cuda_check(c, cudaGetLastError(), "set populations");
+    }
+    if (which != DSCF_FIELD_PHI && which != DSCF_FIELD_U) return fail(c, DSCF_ERR_ARG, "field %d cannot be set", which);
+    const char* in = (const char*)src;
+    for (int r = 0; r < c->nrep; ++r) {
+        const Rep& R = c->L.reps[r];
+        void* dstp = which == DSCF_FIELD_PHI ? R.phi : R.U;
+        if (int rc = cuda_check(c, cudaMemcpyAsync(dstp, in + (size_t)R.ext_off * es, (size_t)R.ns * R.V * es, kind, c->stream),
+                                "set field"))
+            return rc;
+    }
+    if (which == DSCF_FIELD_PHI) {
+        if (c->prec == DSCF_FP64) launch_mass_init<double>(L, c->nrep); else launch_mass_init<float>(L, c->nrep);
+    } else {
+        c->phim_stale = true;
+    }
+    return cuda_check(c, cudaGetLastError(), "set field");
+}
+
+int dscf_diagnostics(dscf_ctx* c, int32_t replica, double* out) {
+    if (!c || !out || replica < 0 || replica >= c->nrep) return c ? fail(c, DSCF_ERR_ARG, "bad replica") : DSCF_ERR_ARG;
+    if (int rc = set_dev(c)) return rc;
+    double s[kScalStride];
+    const Rep& R = c->L.reps[replica];
+    if (int rc = cuda_check(c, cudaMemcpyAsync(s, R.scal, sizeof s, cudaMemcpyDeviceToHost, c->stream), "diag")) return rc;
+    if (int rc = cuda_check(c, cudaStreamSynchronize(c->stream), "diag sync")) return rc;
+    const int K = c->params[0].ncg_iters;
+    std::memset(out, 0, sizeof(double) * 24);
+    for (int I = 0; I < 3; ++I) {
+        out[I] = s[S_MASS0 + I];
+        out[3 + I] = s[S_DRIFT0 + I];
+    }
+    out[6] = s[S_RHO];
+    out[7] = s[S_JX]; out[8] = s[S_JY]; out[9] = s[S_JZ];
+    out[10] = s[S_UMAX];
+    out[11] = s[S_Q];
+    out[12] = s[S_QS];
+    out[13] = K;
+    out[14] = s[S_GG0];
+    out[15] = s[S_GMAX0];
+    out[16] = K > 0 ? s[S_ITER0 + 4 * (K - 1) + 2] : s[S_GG0];
+    out[17] = K > 0 ? s[S_ITER0 + 4 * (K - 1) + 3] : s[S_GMAX0];
+    out[18] = (double)c->steps;
+    return DSCF_OK;
+}
+
+int dscf_status(dscf_ctx* c) {
+    if (!c) return DSCF_ERR_ARG;
+    if (int rc = set_dev(c)) return rc;
+    if (int rc = cuda_check(c, cudaStreamSynchronize(c->stream), "status sync")) return rc;
+    if (int rc = cuda_check(c, cudaGetLastError(), "status")) return rc;
+    int st = 0;
+    if (int rc = cuda_check(c, cudaMemcpy(&st, c->d_status, sizeof(int), cudaMemcpyDeviceToHost), "status read")) return rc;
+    if (st & ST_NONFINITE) return fail(c, DSCF_ERR_NUMERIC, "non-finite value in a reduction");
+    return DSCF_OK;
+}
+
+int dscf_probe(dscf_ctx* c, int32_t enable) {
+    if (!c) return DSCF_ERR_ARG;
+    if (int rc = set_dev(c)) return rc;
+    const bool on = enable != 0;
+    if (on && !c->ev[0]) {
+        for (int i = 0; i < 6; ++i)
+            if (int rc = cuda_check(c, cudaEventCreate(&c->ev[i]), "probe event")) return rc;
+    }
+    if (on != c->probe && c->exec) {
+        if (int rc = cuda_check(c, cudaStreamSynchronize(c->stream), "probe sync")) return rc;
+        cudaGraphExecDestroy(c->exec);
+        c->exec = nullptr;
+    }
+    c->probe = on;
+    c->probe_ran = false;
+    return DSCF_OK;
+}
+
+int dscf_probe_ms(dscf_ctx* c, float* ms) {
+    if (!c || !ms) return DSCF_ERR_ARG;
+    if (!c->probe || !c->probe_ran) return fail(c, DSCF_ERR_STATE, "probe not enabled or no step since enabling it");
+    if (int rc = set_dev(c)) return rc;
+    if (int rc = cuda_check(c, cudaStreamSynchronize(c->stream), "probe sync")) return rc;
+    ms[0] = ms[1] = ms[2] = 0.0f;
+    if (c->params[0].ncg_iters > 0)
+        if (int rc = cuda_check(c, cudaEventElapsedTime(&ms[0], c->ev[0], c->ev[1]), "probe sweeps")) return rc;
+    if (c->params[0].hydro)
+        if (int rc = cuda_check(c, cudaEventElapsedTime(&ms[1], c->ev[2], c->ev[3]), "probe lb")) return rc;
+    return cuda_check(c, cudaEventElapsedTime(&ms[2], c->ev[4], c->ev[5]), "probe step");
+}
+
+int dscf_free(dscf_ctx* c) {
+    if (!c) return DSCF_OK;
+    cudaSetDevice(c->device);
+    for (int i = 0; i < 6; ++i)
+        if (c->ev[i]) cudaEventDestroy(c->ev[i]);
+    if (c->exec) cudaGraphExecDestroy(c->exec);
+    if (c->cap) cudaStreamDestroy(c->cap);
+    delete c;
+    return DSCF_OK;
+}
+
+const char* dscf_last_error(const dscf_ctx* c) { return c ? c->err.c_str() : g_init_error.c_str(); }
+
+int64_t dscf_launches_per_step(const dscf_ctx* c) { return c ? c->launches : 0; }
+
+}  // extern "C"

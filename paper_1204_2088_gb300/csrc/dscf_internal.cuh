@@ -1,0 +1,186 @@
+// Internal declarations of the CUDA library: replica descriptors, partial-sum slots and the
+// deterministic block reductions every kernel uses.  Not part of the public ABI.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace dscf {
+
+constexpr int kFlatThreads = 256;     // threads of every site-parallel ("flat") kernel
+constexpr int kMaxFlatBlocks = 1024;  // flat blocks per replica (= partial sums per replica)
+constexpr int kMaxNcg = 32;           // Fletcher-Reeves iterations per step, upper bound
+constexpr int kScalStride = 192;      // FP64 scalar slots per replica
+
+// Partial-sum slots: one array of per-block FP64 partials per slot and replica.  Reducing a
+// slot is done redundantly, in a fixed order, by every block that needs the total, so the
+// result is bit-identical in all blocks and from run to run.
+enum PartSlot {
+    P_Q = 0,     // sum_r G_N(r)            (written by the last forward contour step)
+    P_ES,        // sum_r exp(-U_S)         (written by the Boltzmann-factor kernel)
+    P_H0,        // <g, d>
+    P_CD,        // <d, phi_m d>
+    P_H1,        // <phi* - phi[U + a1 d], d>
+    P_GG0,       // <g, g>, even iterations
+    P_GG1,       // <g, g>, odd iterations
+    P_GMAX,      // max |g|
+    P_MASS0, P_MASS1, P_MASS2,   // sum_r phi_I after the convection-diffusion update
+    P_RHO, P_JX, P_JY, P_JZ,     // LB mass and momentum
+    P_UMAX,      // max |u_lat|
+    NPART
+};
+
+// Scalar history slots (per replica, FP64).
+enum ScalSlot {
+    S_GG0 = 0, S_GMAX0 = 1,      // start of the inversion
+    S_ITER0 = 2,                 // per iteration k: a1, a, gg, gmax at S_ITER0 + 4k + {0..3}
+    S_Q = 160, S_QS, S_DRIFT0, S_DRIFT1, S_DRIFT2, S_MASS0, S_MASS1, S_MASS2,
+    S_RHO, S_JX, S_JY, S_JZ, S_UMAX
+};
+
+// Device status bits.
+enum { ST_NONFINITE = 1 };
+
+// One replica as the kernels see it.  Pointers are into the caller's workspace; their element
+// type is the context precision (double or float) except part/scal (double).
+struct Rep {
+    int nx, ny, nz, ns, N, nA;
+    long long V;
+    int tiles_x, tiles_y, tiles_z, zc;     // propagator tiling
+    int tile0, ntiles;
+    int blk0, nblk, chunk;                 // flat tiling: nblk blocks of `chunk` sites
+    int hydro, cn_sweeps;
+    double phi_p, kappa, alpha, dt, M, gs, gb, rho0, phi_floor;
+    double chi[9];
+    double mass0[3];
+    long long ext_off;                     // offset of this replica in [rep][ns][V] arrays
+    long long vbase;                       // sites of the replicas before it ([rep][c][V] arrays)
+    void* phi;   // [ns][V] compositions (target of the inversion)
+    void* U;     // [ns][V]
+    void* mu;    // [ns][V]
+    void* d;     // [ns][V] conjugate direction
+    void* phim;  // [ns][V] phi[U]
+    void* q;     // [2][V]  contour quadratures
+    void* E;     // [ns][V] Boltzmann factors exp(-U)
+    void* G;     // [N][V]  forward propagators G_1..G_N
+    void* Gp0;   // [V]     backward propagator ping
+    void* Gp1;   // [V]     backward propagator pong
+    void* u;     // [3][V]  LB velocity (lattice units)
+    void* pop0;  // [19][V] LB population deviations (post-collision), even steps
+    void* pop1;  // [19][V] odd steps
+    void* del0;  // [ns][V] Jacobi iterate ping
+    void* del1;  // [ns][V] Jacobi iterate pong
+    void* rhs;   // [ns][V] right-hand side of the Crank-Nicolson system
+    double* part;   // [NPART][part_stride]
+    int part_stride;
+    double* scal;   // [kScalStride]
+};
+
+// Launch description shared by the host launchers.
+struct Launch {
+    const Rep* reps;         // device table
+    const int* tile2rep;     // device map: propagator tile -> replica
+    const int* blk2rep;      // device map: flat block -> replica
+    int* status;             // device status word
+    int* counter;            // device step counter (selects the LB buffer parity)
+    int nblk_total;          // flat blocks over all replicas
+    cudaStream_t stream;
+};
+
+// ---------------------------------------------------------------------------------------------
+// Deterministic reductions (warp shuffle then one warp over the warp sums).
+// ---------------------------------------------------------------------------------------------
+__device__ __forceinline__ double warp_sum(double v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ double warp_max(double v) {
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// Block-wide sum; the result is returned to every thread.  sh: >= 33 doubles of shared memory.
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nw = (blockDim.x * blockDim.y + 31) >> 5;
+    const int tid = threadIdx.x + threadIdx.y * blockDim.x;
+    const int l = tid & 31, w = tid >> 5;
+    (void)lane; (void)warp;
+    v = warp_sum(v);
+    if (l == 0) sh[w] = v;
+    __syncthreads();
+    if (w == 0) {
+        double x = (l < nw) ? sh[l] : 0.0;
+        x = warp_sum(x);
+        if (l == 0) sh[32] = x;
+    }
+    __syncthreads();
+    double r = sh[32];
+    __syncthreads();
+    return r;
+}
+
+__device__ __forceinline__ double block_max(double v, double* sh) {
+    const int nw = (blockDim.x * blockDim.y + 31) >> 5;
+    const int tid = threadIdx.x + threadIdx.y * blockDim.x;
+    const int l = tid & 31, w = tid >> 5;
+    v = warp_max(v);
+    if (l == 0) sh[w] = v;
+    __syncthreads();
+    if (w == 0) {
+        double x = (l < nw) ? sh[l] : 0.0;
+        x = warp_max(x);
+        if (l == 0) sh[32] = x;
+    }
+    __syncthreads();
+    double r = sh[32];
+    __syncthreads();
+    return r;
+}
+
+// Total of n partials, same fixed order in every block.
+__device__ __forceinline__ double reduce_parts(const double* __restrict__ p, int n, double* sh) {
+    const int tid = threadIdx.x + threadIdx.y * blockDim.x;
+    const int nt = blockDim.x * blockDim.y;
+    double s = 0.0;
+    for (int i = tid; i < n; i += nt) s += p[i];
+    return block_sum(s, sh);
+}
+__device__ __forceinline__ double reduce_parts_max(const double* __restrict__ p, int n, double* sh) {
+    const int tid = threadIdx.x + threadIdx.y * blockDim.x;
+    const int nt = blockDim.x * blockDim.y;
+    double s = 0.0;
+    for (int i = tid; i < n; i += nt) s = fmax(s, p[i]);
+    return block_max(s, sh);
+}
+
+__device__ __forceinline__ double* slot(const Rep& R, int s) { return R.part + (size_t)s * R.part_stride; }
+
+__device__ __forceinline__ int wrapi(int v, int n) {
+    v %= n;
+    return v < 0 ? v + n : v;
+}
+
+// Boltzmann factor exp(-x) in the field precision (CUDA's exp / expf, not re-implemented).
+__device__ __forceinline__ double bexp(double x) { return exp(-x); }
+__device__ __forceinline__ float bexp(float x) { return expf(-x); }
+
+// ---------------------------------------------------------------------------------------------
+// Host launchers (defined in the kernel translation units, explicit per precision).
+// ---------------------------------------------------------------------------------------------
+template <typename T> void launch_prop_fwd(const Launch& L, int s, int grid);
+template <typename T> void launch_prop_bwd(const Launch& L, int j, int grid);
+// mode: 0 exp(-U), 1 trial exp(-(U + a1 d)), 2 commit U += a d then exp(-U), 3 exp(-Uext)
+template <typename T> void launch_exp(const Launch& L, int mode, int k, const void* Uext);
+template <typename T> void launch_trial(const Launch& L);
+template <typename T> void launch_grad(const Launch& L, int k);
+// mode 0: init (d = -g), mode 1: iteration k direction update
+template <typename T> void launch_dir(const Launch& L, int mode, int k);
+template <typename T> void launch_mu(const Launch& L, int K);
+template <typename T> void launch_lb(const Launch& L, const void* force_ext);
+template <typename T> void launch_cd(const Launch& L, int sweeps);
+template <typename T> void launch_dens_out(const Launch& L, void* phi_ext);
+template <typename T> void launch_pop_copy(const Launch& L, void* ext, int dir);  // 0 get, 1 set
+template <typename T> void launch_mass_init(const Launch& L, int nrep);
+void launch_step_end(const Launch& L);
+
+}  // namespace dscf

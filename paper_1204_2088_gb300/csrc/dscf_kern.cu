@@ -1,0 +1,658 @@
+// Site-parallel kernels of the time step: Fletcher-Reeves bookkeeping, chemical potential
+// (Eq. 4), the fused D3Q19 MRT collide-stream with the thermodynamic body force (Eq. 8-14,
+// Table 1) and the convection-diffusion update of the compositions (Eq. 3).
+//
+// Every "flat" kernel runs nblk blocks per replica; block b of replica r covers the sites
+// [b*chunk, (b+1)*chunk) and leaves one FP64 partial per reduction in the replica's slot, so
+// totals are formed deterministically by the kernels that consume them.
+#include "dscf_internal.cuh"
+
+namespace dscf {
+
+#define FLAT_PROLOGUE                                                   \
+    const Rep& R = reps[blk2rep[blockIdx.x]];                           \
+    const int lb = blockIdx.x - R.blk0;                                 \
+    const long long V = R.V;                                            \
+    const long long i0 = (long long)lb * R.chunk;                       \
+    const long long i1 = min(i0 + (long long)R.chunk, V);               \
+    (void)i1;
+
+__device__ __forceinline__ int pslot_gg(int k) { return (k & 1) ? P_GG1 : P_GG0; }
+
+// ---------------------------------------------------------------------------------------------
+// Normalisation of the quadrature (Eq. 2 prefactor):  phi_I = phi_p/(N Q) q_I,
+// phi_S = phi_s exp(-U_S)/<exp(-U_S)>.
+// ---------------------------------------------------------------------------------------------
+struct Norm {
+    double coef, qs, phis;
+};
+__device__ __forceinline__ Norm norm_of(const Rep& R, double* sh) {
+    Norm n;
+    const double Q = reduce_parts(slot(R, P_Q), R.ntiles, sh) / (double)R.V;
+    n.coef = R.phi_p / ((double)R.N * Q);
+    n.qs = (R.ns == 3) ? reduce_parts(slot(R, P_ES), R.nblk, sh) / (double)R.V : 1.0;
+    n.phis = 1.0 - R.phi_p;
+    return n;
+}
+template <typename T>
+__device__ __forceinline__ double model_phi(const Rep& R, const Norm& n, int I, long long i) {
+    if (I < 2) return n.coef * (double)((const T*)R.q)[(long long)I * R.V + i];
+    return n.phis * (double)((const T*)R.E)[2 * R.V + i] / n.qs;
+}
+
+// Directional derivative at the trial point: h1 = <phi* - phi[U + a1 d], d>.
+template <typename T>
+__global__ void __launch_bounds__(kFlatThreads) k_trial(const Rep* __restrict__ reps, const int* __restrict__ blk2rep) {
+    __shared__ double sh[33];
+    FLAT_PROLOGUE
+    const Norm n = norm_of(R, sh);
+    const T* phi = (const T*)R.phi;
+    const T* d = (const T*)R.d;
+    double h1 = 0.0;
+    for (int I = 0; I < R.ns; ++I)
+        for (long long i = i0 + threadIdx.x; i < i1; i += kFlatThreads) {
+            const long long o = (long long)I * V + i;
+            h1 += ((double)phi[o] - model_phi<T>(R, n, I, i)) * (double)d[o];
+        }
+    const double t = block_sum(h1, sh);
+    if (threadIdx.x == 0) slot(R, P_H1)[lb] = t;
+}
+
+// Store phi_m = phi[U] of the committed point; k >= 0 also leaves <g,g> (g = phi* - phi_m) in
+// the parity slot of iteration k+1 and max|g|.
+template <typename T>
+__global__ void __launch_bounds__(kFlatThreads) k_grad(const Rep* __restrict__ reps, const int* __restrict__ blk2rep,
+                                                       int k) {
+    __shared__ double sh[33];
+    FLAT_PROLOGUE
+    const Norm n = norm_of(R, sh);
+    if (lb == 0 && threadIdx.x == 0) {
+        R.scal[S_Q] = n.coef > 0.0 ? R.phi_p / ((double)R.N * n.coef) : 0.0;
+        R.scal[S_QS] = n.qs;
+    }
+    const T* phi = (const T*)R.phi;
+    T* pm = (T*)R.phim;
+    double gg = 0.0, gmax = 0.0;
+    for (int I = 0; I < R.ns; ++I)
+        for (long long i = i0 + threadIdx.x; i < i1; i += kFlatThreads) {
+            const long long o = (long long)I * V + i;
+            const T m = (T)model_phi<T>(R, n, I, i);
+            pm[o] = m;
+            const double g = (double)phi[o] - (double)m;
+            gg += g * g;
+            gmax = fmax(gmax, fabs(g));
+        }
+    if (k >= 0) {
+        const double t = block_sum(gg, sh);
+        const double tm = block_max(gmax, sh);
+        if (threadIdx.x == 0) {
+            slot(R, pslot_gg(k + 1))[lb] = t;
+            slot(R, P_GMAX)[lb] = tm;
+        }
+    }
+}
+
+// Conjugate direction.  mode 0: d = -g (start of an inversion, also <g,g> and max|g|);
+// mode 1 (after iteration k): beta = <g_{k+1},g_{k+1}>/<g_k,g_k> (Fletcher-Reeves),
+// d = -g + beta d.  Leaves h0 = <g,d> and <d, phi_m d> for the next line search.
+template <typename T>
+__global__ void __launch_bounds__(kFlatThreads) k_dir(const Rep* __restrict__ reps, const int* __restrict__ blk2rep,
+                                                      int mode, int k, int* status) {
+    __shared__ double sh[33];
+    FLAT_PROLOGUE
+    double beta = 0.0;
+    if (mode == 1) {
+        const double ggn = reduce_parts(slot(R, pslot_gg(k + 1)), R.nblk, sh);
+        const double ggo = reduce_parts(slot(R, pslot_gg(k)), R.nblk, sh);
+        beta = (ggo > 0.0) ? ggn / ggo : 0.0;
+        if (lb == 0) {
+            const double gm = reduce_parts_max(slot(R, P_GMAX), R.nblk, sh);
+            if (threadIdx.x == 0) {
+                R.scal[S_ITER0 + 4 * k + 2] = ggn;
+                R.scal[S_ITER0 + 4 * k + 3] = gm;
+                if (!isfinite(ggn)) atomicOr(status, (int)ST_NONFINITE);
+            }
+        }
+    }
+    const T* phi = (const T*)R.phi;
+    const T* pm = (const T*)R.phim;
+    T* d = (T*)R.d;
+    double h0 = 0.0, cd = 0.0, gg = 0.0, gmax = 0.0;
+    for (int I = 0; I < R.ns; ++I)
+        for (long long i = i0 + threadIdx.x; i < i1; i += kFlatThreads) {
+            const long long o = (long long)I * V + i;
+            const double g = (double)phi[o] - (double)pm[o];
+            const T dn = (mode == 0) ? (T)(-g) : (T)(-g + beta * (double)d[o]);
+            d[o] = dn;
+            const double dd = (double)dn;
+            h0 += g * dd;
+            cd += dd * (double)pm[o] * dd;
+            gg += g * g;
+            gmax = fmax(gmax, fabs(g));
+        }
+    const double th0 = block_sum(h0, sh);
+    const double tcd = block_sum(cd, sh);
+    if (threadIdx.x == 0) {
+        slot(R, P_H0)[lb] = th0;
+        slot(R, P_CD)[lb] = tcd;
+    }
+    if (mode == 0) {
+        const double tg = block_sum(gg, sh);
+        const double tm = block_max(gmax, sh);
+        if (threadIdx.x == 0) {
+            slot(R, P_GG0)[lb] = tg;
+            slot(R, P_GMAX)[lb] = tm;
+        }
+    }
+}
+
+// sigma[f] at one site, written as the x, y, z passes of the separable 27-point stencil.
+template <typename T>
+__device__ __forceinline__ T sigma_at(const T* __restrict__ f, int x, int y, int z, int nx, int ny, int nz, T al,
+                                      T be) {
+    const int xs[3] = {x == 0 ? nx - 1 : x - 1, x, x == nx - 1 ? 0 : x + 1};
+    const int ys[3] = {y == 0 ? ny - 1 : y - 1, y, y == ny - 1 ? 0 : y + 1};
+    const int zs[3] = {z == 0 ? nz - 1 : z - 1, z, z == nz - 1 ? 0 : z + 1};
+    T zz[3];
+    for (int c = 0; c < 3; ++c) {
+        T yy[3];
+        for (int b = 0; b < 3; ++b) {
+            const long long row = (long long)nx * (ys[b] + (long long)ny * zs[c]);
+            yy[b] = be * f[row + xs[1]] + al * (f[row + xs[0]] + f[row + xs[2]]);
+        }
+        zz[c] = be * yy[1] + al * (yy[0] + yy[2]);
+    }
+    return be * zz[1] + al * (zz[0] + zz[2]);
+}
+
+// Chemical potentials, Eq. 4: mu_I = -U_I + sum_J chi_IJ sigma[phi_J] + kappa (sum_J phi_J - 1).
+// Block 0 of each replica also records the end-of-inversion residual.
+template <typename T>
+__global__ void __launch_bounds__(kFlatThreads) k_mu(const Rep* __restrict__ reps, const int* __restrict__ blk2rep,
+                                                     int K) {
+    __shared__ double sh[33];
+    FLAT_PROLOGUE
+    if (K >= 1 && lb == 0) {
+        const double gg = reduce_parts(slot(R, pslot_gg(K)), R.nblk, sh);
+        const double gm = reduce_parts_max(slot(R, P_GMAX), R.nblk, sh);
+        if (threadIdx.x == 0) {
+            R.scal[S_ITER0 + 4 * (K - 1) + 2] = gg;
+            R.scal[S_ITER0 + 4 * (K - 1) + 3] = gm;
+        }
+    }
+    const int nx = R.nx, ny = R.ny, nz = R.nz, ns = R.ns;
+    const T al = (T)R.alpha, be = (T)(1.0 - 2.0 * R.alpha);
+    const T* phi = (const T*)R.phi;
+    const T* U = (const T*)R.U;
+    T* mu = (T*)R.mu;
+    for (long long i = i0 + threadIdx.x; i < i1; i += kFlatThreads) {
+        const int x = (int)(i % nx);
+        const int y = (int)((i / nx) % ny);
+        const int z = (int)(i / ((long long)nx * ny));
+        T sp[3], tot = T(0);
+        for (int J = 0; J < ns; ++J) {
+            sp[J] = sigma_at(phi + (long long)J * V, x, y, z, nx, ny, nz, al, be);
+            tot += phi[(long long)J * V + i];
+        }
+        for (int I = 0; I < ns; ++I) {
+            T m = -U[(long long)I * V + i];
+            for (int J = 0; J < ns; ++J) m += (T)R.chi[I * 3 + J] * sp[J];
+            m += (T)R.kappa * (tot - T(1));
+            mu[(long long)I * V + i] = m;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// D3Q19 MRT lattice Boltzmann: pull-scheme fused collide-stream.
+// ---------------------------------------------------------------------------------------------
+__constant__ signed char kC[19][3] = {
+    {0, 0, 0}, {1, 0, 0}, {-1, 0, 0}, {0, 1, 0}, {0, -1, 0}, {0, 0, 1}, {0, 0, -1},
+    {1, 1, 0}, {-1, -1, 0}, {1, -1, 0}, {-1, 1, 0}, {1, 0, 1}, {-1, 0, -1},
+    {1, 0, -1}, {-1, 0, 1}, {0, 1, 1}, {0, -1, -1}, {0, 1, -1}, {0, -1, 1}};
+
+template <typename T>
+__device__ __forceinline__ T lbw(int i) {
+    return i == 0 ? T(1.0 / 3.0) : (i <= 6 ? T(1.0 / 18.0) : T(1.0 / 36.0));
+}
+
+// One collide-stream step at every site.  The stored state is the post-collision deviation
+// dn*_i(r) = n*_i(r) - w_i rho0 of the previous step; pulling dn*_i(r - c_i) performs the
+// streaming of Eq. 10, then the collision of Eq. 12-13 (noise amplitude phi_k = 0) with the
+// force term of Eq. 14 writes the new dn*_i(r) to the other buffer.
+//
+// Collision in closed form: modes 0-3 are conserved (gamma = 1) with m_0 = 0 and
+// m_{1..3} = -f/2 (the half-force velocity of Eq. 9), modes 10-18 have gamma = 0, so
+//   n*_i = n_i^eq + Df_i - 3/2 w_i f.c_i + w_i sum_{k=4..9} gamma_k m_k e_ki / b_k,
+// where m_4..m_9 are the Table 1 stress modes of the non-equilibrium second moment
+// Pi^neq = sum_i (n_i - n_i^eq) c_i c_i and Df_i is Eq. 14 (sum_k w_i m^f_k e_ki/b_k = Df_i).
+template <typename T>
+__global__ void __launch_bounds__(kFlatThreads) k_lb(const Rep* __restrict__ reps, const int* __restrict__ blk2rep,
+                                                     const int* __restrict__ counter, const T* __restrict__ fext) {
+    __shared__ double sh[33];
+    FLAT_PROLOGUE
+    const int par = (*counter) & 1;
+    const T* src = (const T*)(par ? R.pop1 : R.pop0);
+    T* dst = (T*)(par ? R.pop0 : R.pop1);
+    const int nx = R.nx, ny = R.ny, nz = R.nz, ns = R.ns;
+    const T rho0 = (T)R.rho0, gs = (T)R.gs, gb = (T)R.gb, dt2 = (T)(R.dt * R.dt);
+    const T* phi = (const T*)R.phi;
+    const T* mu = (const T*)R.mu;
+    T* uo = (T*)R.u;
+    double srho = 0.0, sjx = 0.0, sjy = 0.0, sjz = 0.0, umax = 0.0;
+    for (long long r = i0 + threadIdx.x; r < i1; r += kFlatThreads) {
+        const int x = (int)(r % nx);
+        const int y = (int)((r / nx) % ny);
+        const int z = (int)(r / ((long long)nx * ny));
+        const int xm = x == 0 ? nx - 1 : x - 1, xp = x == nx - 1 ? 0 : x + 1;
+        const int ym = y == 0 ? ny - 1 : y - 1, yp = y == ny - 1 ? 0 : y + 1;
+        const int zm = z == 0 ? nz - 1 : z - 1, zp = z == nz - 1 ? 0 : z + 1;
+        const int X[3] = {xm, x, xp}, Y[3] = {ym, y, yp}, Z[3] = {zm, z, zp};
+        T dn[19];
+#pragma unroll
+        for (int i = 0; i < 19; ++i) {
+            // upstream site r - c_i
+            const long long s = X[1 - kC[i][0]] + (long long)nx * (Y[1 - kC[i][1]] + (long long)ny * Z[1 - kC[i][2]]);
+            dn[i] = src[(long long)i * V + s];
+        }
+        // body force (Eq. 8, central differences), in lattice units dt^2 f
+        T fx = 0, fy = 0, fz = 0;
+        if (fext) {
+            const long long b3 = 3 * R.vbase;
+            fx = fext[b3 + r];
+            fy = fext[b3 + V + r];
+            fz = fext[b3 + 2 * V + r];
+        } else {
+            for (int I = 0; I < ns; ++I) {
+                const T* m = mu + (long long)I * V;
+                const T ph = phi[(long long)I * V + r];
+                const long long row = (long long)nx * (y + (long long)ny * z);
+                fx -= ph * T(0.5) * (m[row + xp] - m[row + xm]);
+                fy -= ph * T(0.5) * (m[x + (long long)nx * (yp + (long long)ny * z)] -
+                                     m[x + (long long)nx * (ym + (long long)ny * z)]);
+                fz -= ph * T(0.5) * (m[x + (long long)nx * (y + (long long)ny * zp)] -
+                                     m[x + (long long)nx * (y + (long long)ny * zm)]);
+            }
+            fx *= dt2;
+            fy *= dt2;
+            fz *= dt2;
+        }
+        // moments (Eq. 9)
+        T drho = 0, jx = 0, jy = 0, jz = 0, pxx = 0, pyy = 0, pzz = 0, pxy = 0, pxz = 0, pyz = 0;
+#pragma unroll
+        for (int i = 0; i < 19; ++i) {
+            const T cx = kC[i][0], cy = kC[i][1], cz = kC[i][2];
+            drho += dn[i];
+            jx += dn[i] * cx;
+            jy += dn[i] * cy;
+            jz += dn[i] * cz;
+            pxx += dn[i] * cx * cx;
+            pyy += dn[i] * cy * cy;
+            pzz += dn[i] * cz * cz;
+            pxy += dn[i] * cx * cy;
+            pxz += dn[i] * cx * cz;
+            pyz += dn[i] * cy * cz;
+        }
+        const T rho = rho0 + drho;
+        jx += T(0.5) * fx;
+        jy += T(0.5) * fy;
+        jz += T(0.5) * fz;
+        const T ux = jx / rho, uy = jy / rho, uz = jz / rho;
+        uo[r] = ux;
+        uo[V + r] = uy;
+        uo[2 * V + r] = uz;
+        const T usq = ux * ux + uy * uy + uz * uz;
+        // non-equilibrium second moment: Pi - rho u u - rho/3 I with Pi = rho0/3 I + sum dn c c
+        const T third = T(1.0 / 3.0);
+        const T nxx = pxx - rho * ux * ux - drho * third;
+        const T nyy = pyy - rho * uy * uy - drho * third;
+        const T nzz = pzz - rho * uz * uz - drho * third;
+        const T nxy = pxy - rho * ux * uy, nxz = pxz - rho * ux * uz, nyz = pyz - rho * uy * uz;
+        const T m4 = nxx + nyy + nzz;
+        const T m5 = nxx - nyy;
+        const T m6 = m4 - T(3) * nzz;
+        // relaxed stress modes divided by their norms b_4 = 2/3, b_5 = 4/9, b_6 = 4/3, b_7..9 = 1/9
+        const T r4 = gb * m4 * T(1.5);
+        const T r5 = gs * m5 * T(2.25);
+        const T r6 = gs * m6 * T(0.75);
+        const T r7 = gs * nxy * T(9), r8 = gs * nxz * T(9), r9 = gs * nyz * T(9);
+        // Sigma of Eq. 14
+        const T uf = ux * fx + uy * fy + uz * fz;
+        const T a1 = T(0.5) * (T(1) + gs), a2 = (T(1) + gb) * third;
+        const T sxx = a1 * (T(2) * ux * fx - T(2.0 / 3.0) * uf) + a2 * uf;
+        const T syy = a1 * (T(2) * uy * fy - T(2.0 / 3.0) * uf) + a2 * uf;
+        const T szz = a1 * (T(2) * uz * fz - T(2.0 / 3.0) * uf) + a2 * uf;
+        const T sxy = a1 * (ux * fy + uy * fx), sxz = a1 * (ux * fz + uz * fx), syz = a1 * (uy * fz + uz * fy);
+        const T trs3 = (sxx + syy + szz) * third;
+#pragma unroll
+        for (int i = 0; i < 19; ++i) {
+            const T cx = kC[i][0], cy = kC[i][1], cz = kC[i][2];
+            const T w = lbw<T>(i);
+            const T c2 = cx * cx + cy * cy + cz * cz;
+            const T uc = ux * cx + uy * cy + uz * cz;
+            const T fc = fx * cx + fy * cy + fz * cz;
+            const T dneq = w * (drho + rho * (T(3) * uc + T(4.5) * uc * uc - T(1.5) * usq));
+            const T scc = sxx * cx * cx + syy * cy * cy + szz * cz * cz +
+                          T(2) * (sxy * cx * cy + sxz * cx * cz + syz * cy * cz);
+            const T df = T(3) * w * (fc + T(1.5) * (scc - trs3));
+            const T rel = w * (r4 * (c2 - T(1)) + r5 * (cx * cx - cy * cy) + r6 * (c2 - T(3) * cz * cz) +
+                               r7 * cx * cy + r8 * cx * cz + r9 * cy * cz);
+            dst[(long long)i * V + r] = dneq + df - T(1.5) * w * fc + rel;
+        }
+        srho += (double)rho;
+        sjx += (double)(jx + T(0.5) * fx);
+        sjy += (double)(jy + T(0.5) * fy);
+        sjz += (double)(jz + T(0.5) * fz);
+        umax = fmax(umax, fmax(fabs((double)ux), fmax(fabs((double)uy), fabs((double)uz))));
+    }
+    const double a = block_sum(srho, sh), bx = block_sum(sjx, sh), by = block_sum(sjy, sh), bz = block_sum(sjz, sh);
+    const double bm = block_max(umax, sh);
+    if (threadIdx.x == 0) {
+        slot(R, P_RHO)[lb] = a;
+        slot(R, P_JX)[lb] = bx;
+        slot(R, P_JY)[lb] = by;
+        slot(R, P_JZ)[lb] = bz;
+        slot(R, P_UMAX)[lb] = bm;
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Convection-diffusion (Eq. 3): two-step Lax-Wendroff convection, Crank-Nicolson diffusion
+// with mu^{n+1} linearised by its local curvature H = diag(1/phi) + kappa 1 1^T, Jacobi
+// sweeps, FP64 mass correction.
+// ---------------------------------------------------------------------------------------------
+struct Nb {
+    long long c, n[6];  // centre and +x -x +y -y +z -z
+};
+__device__ __forceinline__ Nb neighbours(long long i, int nx, int ny, int nz) {
+    const int x = (int)(i % nx);
+    const int y = (int)((i / nx) % ny);
+    const int z = (int)(i / ((long long)nx * ny));
+    const int xm = x == 0 ? nx - 1 : x - 1, xp = x == nx - 1 ? 0 : x + 1;
+    const int ym = y == 0 ? ny - 1 : y - 1, yp = y == ny - 1 ? 0 : y + 1;
+    const int zm = z == 0 ? nz - 1 : z - 1, zp = z == nz - 1 ? 0 : z + 1;
+    const long long sy = nx, sz = (long long)nx * ny;
+    Nb b;
+    b.c = i;
+    b.n[0] = xp + y * sy + z * sz;
+    b.n[1] = xm + y * sy + z * sz;
+    b.n[2] = x + yp * sy + z * sz;
+    b.n[3] = x + ym * sy + z * sz;
+    b.n[4] = x + y * sy + zp * sz;
+    b.n[5] = x + y * sy + zm * sz;
+    return b;
+}
+
+// Explicit part: rhs_I = -sum_axes [F(i+1/2) - F(i-1/2)] + dt M L(phi; mu^n).
+template <typename T>
+__global__ void __launch_bounds__(kFlatThreads) k_cd_rhs(const Rep* __restrict__ reps, const int* __restrict__ blk2rep) {
+    FLAT_PROLOGUE
+    const T* phi = (const T*)R.phi;
+    const T* mu = (const T*)R.mu;
+    const T* u = (const T*)R.u;
+    T* rhs = (T*)R.rhs;
+    const bool hyd = R.hydro != 0;
+    const T dtM = (T)(R.dt * R.M);
+    for (long long i = i0 + threadIdx.x; i < i1; i += kFlatThreads) {
+        const Nb b = neighbours(i, R.nx, R.ny, R.nz);
+        for (int I = 0; I < R.ns; ++I) {
+            const T* ph = phi + (long long)I * V;
+            const T* m = mu + (long long)I * V;
+            T conv = 0, lap = 0;
+            for (int d = 0; d < 3; ++d) {
+                const long long ip = b.n[2 * d], im = b.n[2 * d + 1];
+                T Ci = 0, Cp = 0, Cm = 0;
+                if (hyd) {
+                    const T* C = u + (long long)d * V;
+                    Ci = C[i];
+                    Cp = C[ip];
+                    Cm = C[im];
+                }
+                const T hp = T(0.5) * (ph[i] + ph[ip]) - T(0.5) * (Cp * ph[ip] - Ci * ph[i]);
+                const T Fp = T(0.5) * (Ci + Cp) * hp;
+                const T hm = T(0.5) * (ph[im] + ph[i]) - T(0.5) * (Ci * ph[i] - Cm * ph[im]);
+                const T Fm = T(0.5) * (Cm + Ci) * hm;
+                conv += Fp - Fm;
+                lap += T(0.5) * (ph[i] + ph[ip]) * (m[ip] - m[i]) + T(0.5) * (ph[i] + ph[im]) * (m[im] - m[i]);
+            }
+            rhs[(long long)I * V + i] = -conv + dtM * lap;
+        }
+    }
+}
+
+// One Jacobi sweep k of (I - c L(phi; H .)) delta = rhs, c = dt M / 2; the species block of a
+// site is solved exactly (diagonal plus the rank-one kappa coupling).
+template <typename T>
+__global__ void __launch_bounds__(kFlatThreads) k_cd_jacobi(const Rep* __restrict__ reps, const int* __restrict__ blk2rep,
+                                                            int k) {
+    FLAT_PROLOGUE
+    const T* phi = (const T*)R.phi;
+    const T* rhs = (const T*)R.rhs;
+    const T* dold = (const T*)((k & 1) ? R.del0 : R.del1);
+    T* dnew = (T*)((k & 1) ? R.del1 : R.del0);
+    const int ns = R.ns;
+    const T c = (T)(0.5 * R.dt * R.M);
+    const T kap = (T)R.kappa, fl = (T)R.phi_floor;
+    for (long long i = i0 + threadIdx.x; i < i1; i += kFlatThreads) {
+        const Nb b = neighbours(i, R.nx, R.ny, R.nz);
+        T psi[3][6];
+        if (k == 0) {
+            for (int I = 0; I < 3; ++I)
+                for (int q = 0; q < 6; ++q) psi[I][q] = 0;
+        } else {
+            for (int q = 0; q < 6; ++q) {
+                T sd = 0;
+                for (int J = 0; J < ns; ++J) sd += dold[(long long)J * V + b.n[q]];
+                for (int I = 0; I < ns; ++I) {
+                    T ph = phi[(long long)I * V + b.n[q]];
+                    if (ph < fl) ph = fl;
+                    psi[I][q] = dold[(long long)I * V + b.n[q]] / ph + kap * sd;
+                }
+            }
+        }
+        T rh[3], D[3], A[3];
+        for (int I = 0; I < ns; ++I) {
+            const T* ph = phi + (long long)I * V;
+            T ws = 0, off = 0;
+            for (int q = 0; q < 6; ++q) {
+                const T pf = T(0.5) * (ph[i] + ph[b.n[q]]);
+                ws += pf;
+                off += pf * psi[I][q];
+            }
+            const T phc = ph[i] < fl ? fl : ph[i];
+            rh[I] = rhs[(long long)I * V + i] + c * off;
+            D[I] = T(1) + c * ws / phc;
+            A[I] = c * kap * ws;
+        }
+        T num = 0, den = 1;
+        for (int I = 0; I < ns; ++I) {
+            num += rh[I] / D[I];
+            den += A[I] / D[I];
+        }
+        const T s = num / den;
+        for (int I = 0; I < ns; ++I) dnew[(long long)I * V + i] = (rh[I] - A[I] * s) / D[I];
+    }
+}
+
+// phi <- phi + delta; FP64 partial sums of each species for the mass correction.
+template <typename T>
+__global__ void __launch_bounds__(kFlatThreads) k_cd_finish(const Rep* __restrict__ reps, const int* __restrict__ blk2rep,
+                                                            int sweeps) {
+    __shared__ double sh[33];
+    FLAT_PROLOGUE
+    T* phi = (T*)R.phi;
+    const T* del = (const T*)(((sweeps - 1) & 1) ? R.del1 : R.del0);
+    for (int I = 0; I < R.ns; ++I) {
+        double acc = 0.0;
+        for (long long i = i0 + threadIdx.x; i < i1; i += kFlatThreads) {
+            const long long o = (long long)I * V + i;
+            const T v = phi[o] + del[o];
+            phi[o] = v;
+            acc += (double)v;
+        }
+        const double t = block_sum(acc, sh);
+        if (threadIdx.x == 0) slot(R, P_MASS0 + I)[lb] = t;
+    }
+}
+
+// Shift every species to its prescribed total (FP64); block 0 records the diagnostics.
+template <typename T>
+__global__ void __launch_bounds__(kFlatThreads) k_mass_fix(const Rep* __restrict__ reps, const int* __restrict__ blk2rep,
+                                                           int* status) {
+    __shared__ double sh[33];
+    FLAT_PROLOGUE
+    T* phi = (T*)R.phi;
+    for (int I = 0; I < R.ns; ++I) {
+        const double tot = reduce_parts(slot(R, P_MASS0 + I), R.nblk, sh);
+        const double shift = (R.mass0[I] - tot) / (double)V;
+        if (lb == 0 && threadIdx.x == 0) {
+            R.scal[S_DRIFT0 + I] = tot - R.mass0[I];
+            R.scal[S_MASS0 + I] = R.mass0[I];
+            if (!isfinite(tot)) atomicOr(status, (int)ST_NONFINITE);
+        }
+        const T ts = (T)shift;
+        for (long long i = i0 + threadIdx.x; i < i1; i += kFlatThreads) phi[(long long)I * V + i] += ts;
+    }
+    if (lb == 0 && R.hydro) {
+        const double a = reduce_parts(slot(R, P_RHO), R.nblk, sh);
+        const double bx = reduce_parts(slot(R, P_JX), R.nblk, sh);
+        const double by = reduce_parts(slot(R, P_JY), R.nblk, sh);
+        const double bz = reduce_parts(slot(R, P_JZ), R.nblk, sh);
+        const double bm = reduce_parts_max(slot(R, P_UMAX), R.nblk, sh);
+        if (threadIdx.x == 0) {
+            R.scal[S_RHO] = a;
+            R.scal[S_JX] = bx;
+            R.scal[S_JY] = by;
+            R.scal[S_JZ] = bz;
+            R.scal[S_UMAX] = bm;
+            if (!isfinite(a) || !isfinite(bm)) atomicOr(status, (int)ST_NONFINITE);
+        }
+    }
+}
+
+// Forward map output: phi_ext = phi[U] from the quadrature of the last evaluation.
+template <typename T>
+__global__ void __launch_bounds__(kFlatThreads) k_dens_out(const Rep* __restrict__ reps, const int* __restrict__ blk2rep,
+                                                           T* __restrict__ out) {
+    __shared__ double sh[33];
+    FLAT_PROLOGUE
+    const Norm n = norm_of(R, sh);
+    for (int I = 0; I < R.ns; ++I)
+        for (long long i = i0 + threadIdx.x; i < i1; i += kFlatThreads)
+            out[R.ext_off + (long long)I * V + i] = (T)model_phi<T>(R, n, I, i);
+}
+
+// Populations in / out: the API exchanges n_i(r) before collision, i.e. the stored
+// post-collision deviation streamed: n_i(r) = n*_i(r - c_i).
+template <typename T>
+__global__ void __launch_bounds__(kFlatThreads) k_pop_copy(const Rep* __restrict__ reps, const int* __restrict__ blk2rep,
+                                                           const int* __restrict__ counter, T* __restrict__ ext,
+                                                           int dir) {
+    FLAT_PROLOGUE
+    T* cur = (T*)(((*counter) & 1) ? R.pop1 : R.pop0);
+    const long long b19 = 19 * R.vbase;
+    const int nx = R.nx, ny = R.ny, nz = R.nz;
+    for (long long r = i0 + threadIdx.x; r < i1; r += kFlatThreads) {
+        const int x = (int)(r % nx);
+        const int y = (int)((r / nx) % ny);
+        const int z = (int)(r / ((long long)nx * ny));
+        for (int i = 0; i < 19; ++i) {
+            if (dir == 0) {
+                const long long s = wrapi(x - kC[i][0], nx) +
+                                    (long long)nx * (wrapi(y - kC[i][1], ny) + (long long)ny * wrapi(z - kC[i][2], nz));
+                ext[b19 + (long long)i * V + r] = cur[(long long)i * V + s];
+            } else {
+                const long long s = wrapi(x + kC[i][0], nx) +
+                                    (long long)nx * (wrapi(y + kC[i][1], ny) + (long long)ny * wrapi(z + kC[i][2], nz));
+                cur[(long long)i * V + r] = ext[b19 + (long long)i * V + s];
+            }
+        }
+    }
+}
+
+// Mass targets: partial sums of the current phi, then one block per replica commits them.
+template <typename T>
+__global__ void __launch_bounds__(kFlatThreads) k_mass_parts(const Rep* __restrict__ reps, const int* __restrict__ blk2rep) {
+    __shared__ double sh[33];
+    FLAT_PROLOGUE
+    const T* phi = (const T*)R.phi;
+    for (int I = 0; I < R.ns; ++I) {
+        double acc = 0.0;
+        for (long long i = i0 + threadIdx.x; i < i1; i += kFlatThreads) acc += (double)phi[(long long)I * V + i];
+        const double t = block_sum(acc, sh);
+        if (threadIdx.x == 0) slot(R, P_MASS0 + I)[lb] = t;
+    }
+}
+__global__ void __launch_bounds__(kFlatThreads) k_mass_commit(Rep* reps) {
+    __shared__ double sh[33];
+    Rep& R = reps[blockIdx.x];
+    for (int I = 0; I < R.ns; ++I) {
+        const double t = reduce_parts(slot(R, P_MASS0 + I), R.nblk, sh);
+        if (threadIdx.x == 0) {
+            R.mass0[I] = t;
+            R.scal[S_MASS0 + I] = t;
+        }
+    }
+}
+
+__global__ void k_step_end(int* counter) { *counter += 1; }
+
+// ---------------------------------------------------------------------------------------------
+// Host launchers
+// ---------------------------------------------------------------------------------------------
+template <typename T>
+void launch_trial(const Launch& L) {
+    k_trial<T><<<L.nblk_total, kFlatThreads, 0, L.stream>>>(L.reps, L.blk2rep);
+}
+template <typename T>
+void launch_grad(const Launch& L, int k) {
+    k_grad<T><<<L.nblk_total, kFlatThreads, 0, L.stream>>>(L.reps, L.blk2rep, k);
+}
+template <typename T>
+void launch_dir(const Launch& L, int mode, int k) {
+    k_dir<T><<<L.nblk_total, kFlatThreads, 0, L.stream>>>(L.reps, L.blk2rep, mode, k, L.status);
+}
+template <typename T>
+void launch_mu(const Launch& L, int K) {
+    k_mu<T><<<L.nblk_total, kFlatThreads, 0, L.stream>>>(L.reps, L.blk2rep, K);
+}
+template <typename T>
+void launch_lb(const Launch& L, const void* fext) {
+    k_lb<T><<<L.nblk_total, kFlatThreads, 0, L.stream>>>(L.reps, L.blk2rep, L.counter, (const T*)fext);
+}
+template <typename T>
+void launch_cd(const Launch& L, int sweeps) {
+    k_cd_rhs<T><<<L.nblk_total, kFlatThreads, 0, L.stream>>>(L.reps, L.blk2rep);
+    for (int k = 0; k < sweeps; ++k) k_cd_jacobi<T><<<L.nblk_total, kFlatThreads, 0, L.stream>>>(L.reps, L.blk2rep, k);
+    k_cd_finish<T><<<L.nblk_total, kFlatThreads, 0, L.stream>>>(L.reps, L.blk2rep, sweeps);
+    k_mass_fix<T><<<L.nblk_total, kFlatThreads, 0, L.stream>>>(L.reps, L.blk2rep, L.status);
+}
+template <typename T>
+void launch_dens_out(const Launch& L, void* phi_ext) {
+    k_dens_out<T><<<L.nblk_total, kFlatThreads, 0, L.stream>>>(L.reps, L.blk2rep, (T*)phi_ext);
+}
+template <typename T>
+void launch_pop_copy(const Launch& L, void* ext, int dir) {
+    k_pop_copy<T><<<L.nblk_total, kFlatThreads, 0, L.stream>>>(L.reps, L.blk2rep, L.counter, (T*)ext, dir);
+}
+template <typename T>
+void launch_mass_init(const Launch& L, int nrep) {
+    k_mass_parts<T><<<L.nblk_total, kFlatThreads, 0, L.stream>>>(L.reps, L.blk2rep);
+    k_mass_commit<<<nrep, kFlatThreads, 0, L.stream>>>(const_cast<Rep*>(L.reps));
+}
+void launch_step_end(const Launch& L) { k_step_end<<<1, 1, 0, L.stream>>>(L.counter); }
+
+#define INST(T)                                                        \
+    template void launch_trial<T>(const Launch&);                      \
+    template void launch_grad<T>(const Launch&, int);                  \
+    template void launch_dir<T>(const Launch&, int, int);              \
+    template void launch_mu<T>(const Launch&, int);                    \
+    template void launch_lb<T>(const Launch&, const void*);            \
+    template void launch_cd<T>(const Launch&, int);                    \
+    template void launch_dens_out<T>(const Launch&, void*);            \
+    template void launch_pop_copy<T>(const Launch&, void*, int);       \
+    template void launch_mass_init<T>(const Launch&, int);
+INST(double)
+INST(float)
+
+}  // namespace dscf

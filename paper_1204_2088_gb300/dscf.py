@@ -1,0 +1,238 @@
+"""Python binding of libdscf.so (include/dscf.h): argument marshalling only.
+
+Every step of the method runs in the CUDA library; this module only builds the parameter
+structs, allocates the device workspace with PyTorch (the only allocator), passes raw
+pointers and the current CUDA stream, and wraps results as tensors.  There is no CPU
+fallback: if the library is missing or fails to load, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libdscf.so")
+
+DSCF_OK = 0
+ERRORS = {-1: "DSCF_ERR_ARG", -2: "DSCF_ERR_CUDA", -3: "DSCF_ERR_OOM", -4: "DSCF_ERR_TIMEOUT",
+          -5: "DSCF_ERR_NUMERIC", -6: "DSCF_ERR_STATE"}
+FP64, FP32 = 0, 1
+PHI, U, MU, VEL, POP, PHIM = 0, 1, 2, 3, 4, 5
+
+
+class DSCFError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Params(ctypes.Structure):
+    """Mirror of dscf_params."""
+    _fields_ = [
+        ("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
+        ("ns", ctypes.c_int32), ("N", ctypes.c_int32), ("nA", ctypes.c_int32),
+        ("phi_p", ctypes.c_double), ("chi", ctypes.c_double * 9), ("kappa", ctypes.c_double),
+        ("a", ctypes.c_double), ("dt", ctypes.c_double), ("M", ctypes.c_double),
+        ("tau_s", ctypes.c_double), ("tau_b", ctypes.c_double), ("rho0", ctypes.c_double),
+        ("hydro", ctypes.c_int32), ("ncg_iters", ctypes.c_int32), ("cn_sweeps", ctypes.c_int32),
+        ("phi_floor", ctypes.c_double),
+    ]
+
+
+_lib = None
+
+
+def load():
+    """Load libdscf.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with __graft_entry__.build() "
+                           "(there is no CPU fallback)")
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, i32, sz = ctypes.c_void_p, ctypes.c_int32, ctypes.c_size_t
+    P = ctypes.POINTER(Params)
+    sigs = {
+        "dscf_workspace_bytes": (sz, [P, i32, i32]),
+        "dscf_init": (ctypes.c_int, [P, i32, i32, vp, sz, vp, ctypes.POINTER(vp)]),
+        "dscf_step": (ctypes.c_int, [vp, i32]),
+        "dscf_densities": (ctypes.c_int, [vp, vp, vp]),
+        "lb_step": (ctypes.c_int, [vp, vp, i32]),
+        "dscf_get_fields": (ctypes.c_int, [vp, i32, vp, i32]),
+        "dscf_set_fields": (ctypes.c_int, [vp, i32, vp, i32]),
+        "dscf_diagnostics": (ctypes.c_int, [vp, i32, ctypes.POINTER(ctypes.c_double)]),
+        "dscf_status": (ctypes.c_int, [vp]),
+        "dscf_free": (ctypes.c_int, [vp]),
+        "dscf_last_error": (ctypes.c_char_p, [vp]),
+        "dscf_launches_per_step": (ctypes.c_int64, [vp]),
+        "dscf_probe": (ctypes.c_int, [vp, i32]),
+        "dscf_probe_ms": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_float)]),
+    }
+    for name, (res, args) in sigs.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def make_params(cfg: dict) -> Params:
+    p = Params()
+    p.nx, p.ny, p.nz = cfg["grid"]
+    p.ns = cfg.get("ns", 2)
+    p.N = cfg["N"]
+    p.nA = cfg["nA"]
+    p.phi_p = cfg.get("phi_p", 1.0)
+    chi = np.zeros((3, 3))
+    for (i, j), v in cfg.get("chi", {}).items():
+        chi[i, j] = chi[j, i] = v
+    for k in range(9):
+        p.chi[k] = float(chi.flat[k])
+    p.kappa = cfg.get("kappa", 10.0)
+    p.a = cfg.get("a", 1.1543)
+    p.dt = cfg.get("dt", 0.2)
+    p.M = cfg.get("M", 1.0)
+    p.tau_s = cfg.get("tau_s", 1.0)
+    p.tau_b = cfg.get("tau_b", 1.0)
+    p.rho0 = cfg.get("rho0", 1.0)
+    p.hydro = cfg.get("hydro", 1)
+    p.ncg_iters = cfg.get("ncg_iters", 4)
+    p.cn_sweeps = cfg.get("cn_sweeps", 8)
+    p.phi_floor = cfg.get("phi_floor", 1e-6)
+    return p
+
+
+def workspace_bytes(cfgs, precision=FP64) -> int:
+    cfgs = [cfgs] if isinstance(cfgs, dict) else list(cfgs)
+    arr = (Params * len(cfgs))(*[make_params(c) for c in cfgs])
+    return int(load().dscf_workspace_bytes(arr, len(cfgs), precision))
+
+
+class Context:
+    """One library context: n replicas (a dict or a list of dicts), one precision, one device.
+
+    Field tensors use the layout of include/dscf.h: for one replica [ncomp, nz, ny, nx], for
+    several the replica blocks concatenated into one flat tensor."""
+
+    def __init__(self, cfgs, precision=FP64, device=None, stream=None):
+        self.lib = load()
+        self.cfgs = [cfgs] if isinstance(cfgs, dict) else list(cfgs)
+        self.n = len(self.cfgs)
+        self.precision = precision
+        self.dtype = torch.float64 if precision == FP64 else torch.float32
+        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        self._params = (Params * self.n)(*[make_params(c) for c in self.cfgs])
+        nbytes = self.lib.dscf_workspace_bytes(self._params, self.n, precision)
+        if nbytes == 0:
+            raise DSCFError(-1, "invalid parameters")
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        h = ctypes.c_void_p()
+        rc = self.lib.dscf_init(self._params, self.n, precision, ctypes.c_void_p(self.workspace.data_ptr()),
+                                nbytes, ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h))
+        if rc != DSCF_OK:
+            raise DSCFError(rc, self.lib.dscf_last_error(None).decode())
+        self.h = h
+        self.V = [c["grid"][0] * c["grid"][1] * c["grid"][2] for c in self.cfgs]
+        self.ns = [c.get("ns", 2) for c in self.cfgs]
+
+    # -- helpers ---------------------------------------------------------------------------
+    def _check(self, rc):
+        if rc != DSCF_OK:
+            raise DSCFError(rc, self.lib.dscf_last_error(self.h).decode())
+
+    def _ncomp(self, which):
+        return {VEL: [3] * self.n, POP: [19] * self.n}.get(which, self.ns)
+
+    def _shape(self, which):
+        nc = self._ncomp(which)
+        if self.n == 1:
+            nx, ny, nz = self.cfgs[0]["grid"]
+            return (nc[0], nz, ny, nx)
+        return (sum(c * v for c, v in zip(nc, self.V)),)
+
+    def _as_field(self, t, which):
+        t = torch.as_tensor(t)
+        if t.device.type == "cpu":
+            t = t.to(self.device)
+        t = t.to(self.dtype).contiguous()
+        if t.numel() != int(np.prod(self._shape(which))):
+            raise ValueError(f"field has {t.numel()} elements, expected {int(np.prod(self._shape(which)))}")
+        return t
+
+    # -- API -------------------------------------------------------------------------------
+    def step(self, n_steps=1):
+        self._check(self.lib.dscf_step(self.h, int(n_steps)))
+
+    def densities(self, U):
+        Ud = self._as_field(U, PHI)
+        out = torch.empty(self._shape(PHI), dtype=self.dtype, device=self.device)
+        self._check(self.lib.dscf_densities(self.h, ctypes.c_void_p(Ud.data_ptr()), ctypes.c_void_p(out.data_ptr())))
+        return out
+
+    def lb_step(self, force=None, n_steps=1):
+        ptr = None
+        if force is not None:
+            force = self._as_field(force, VEL)
+            ptr = ctypes.c_void_p(force.data_ptr())
+        self._check(self.lib.lb_step(self.h, ptr, int(n_steps)))
+        self._keep = force
+
+    def get(self, which):
+        out = torch.empty(self._shape(which), dtype=self.dtype, device=self.device)
+        self._check(self.lib.dscf_get_fields(self.h, which, ctypes.c_void_p(out.data_ptr()), 0))
+        return out
+
+    def get_host(self, which, out: torch.Tensor):
+        """Copy a field into a (preferably pinned) host tensor; synchronises."""
+        assert out.device.type == "cpu" and out.dtype == self.dtype and out.is_contiguous()
+        self._check(self.lib.dscf_get_fields(self.h, which, ctypes.c_void_p(out.data_ptr()), 1))
+        return out
+
+    def set(self, which, t):
+        if isinstance(t, torch.Tensor) and t.device.type == "cpu":
+            src = t.to(self.dtype).contiguous()
+            self._check(self.lib.dscf_set_fields(self.h, which, ctypes.c_void_p(src.data_ptr()), 1))
+            torch.cuda.current_stream(self.device).synchronize()
+            return
+        src = self._as_field(t, which)
+        self._check(self.lib.dscf_set_fields(self.h, which, ctypes.c_void_p(src.data_ptr()), 0))
+        self._keep = src
+
+    def diagnostics(self, replica=0):
+        out = (ctypes.c_double * 24)()
+        self._check(self.lib.dscf_diagnostics(self.h, replica, out))
+        v = list(out)
+        return {"mass": v[0:3], "mass_drift": v[3:6], "lb_mass": v[6], "lb_momentum": v[7:10],
+                "umax": v[10], "Q": v[11], "QS": v[12], "ncg_iters": int(v[13]), "gg_start": v[14],
+                "gmax_start": v[15], "gg_end": v[16], "gmax_end": v[17], "steps": int(v[18])}
+
+    def status(self):
+        self._check(self.lib.dscf_status(self.h))
+
+    def probe(self, enable=True):
+        self._check(self.lib.dscf_probe(self.h, 1 if enable else 0))
+
+    def probe_ms(self):
+        """(contour sweeps of one gradient evaluation, LB launch, whole step) of the last step, ms."""
+        out = (ctypes.c_float * 3)()
+        self._check(self.lib.dscf_probe_ms(self.h, out))
+        return tuple(float(v) for v in out)
+
+    def launches_per_step(self):
+        return int(self.lib.dscf_launches_per_step(self.h))
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.dscf_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
