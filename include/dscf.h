@@ -173,6 +173,33 @@ int64_t dscf_launches_per_step(const dscf_ctx* ctx);
 int dscf_probe(dscf_ctx* ctx, int32_t enable);
 int dscf_probe_ms(dscf_ctx* ctx, float* ms);
 
+/*
+ * Forward density map phi_out = phi[U_in] for one replica, for callers that cannot allocate
+ * device memory at all (a host framework that owns every device allocation, a callback in
+ * which allocation is forbidden, a process whose device footprint is fixed after start-up) and
+ * therefore cannot supply the workspace dscf_init needs.  The paper has no counterpart: this
+ * is an interface for such callers, computing the same map as dscf_densities.
+ *
+ * p: parameters of one replica (host memory; only the chain, stencil and composition fields
+ * matter).  U_in, phi_out: device pointers, [ns][V] in the given precision; their device is the
+ * one used.  stream: cudaStream_t or NULL.  Asynchronous on the stream.
+ *
+ * Neither the library nor the caller allocates anything: all scratch (propagator stack,
+ * Boltzmann factors, quadratures, partial sums) lives in one file-scope device array of
+ * DSCF_STATIC_SCRATCH_BYTES, which every GPU that loads the library holds until the process
+ * exits.  A problem needing more returns DSCF_ERR_OOM without launching anything (the
+ * scratch needed is about (ns + N + 4) * V * sizeof(real) bytes; for example 32^3 with N = 64 in
+ * FP64 or 64^3 with N = 48 in FP32 fit).  The first call on a device looks up that device's copy
+ * of the array (a one-time set-up per device); make that first call before any stream capture.
+ * Every call reuses the same array and overwrites what it needs, so calls whose work overlaps on
+ * the GPU (on different streams, or from different threads) race and must be serialised by the
+ * caller.  Errors: DSCF_ERR_ARG, DSCF_ERR_OOM, DSCF_ERR_CUDA; dscf_last_error(NULL) has the
+ * message.
+ */
+#define DSCF_STATIC_SCRATCH_BYTES (64u * 1024u * 1024u)
+int dscf_densities_static(const dscf_params* p, int32_t precision, const void* U_in, void* phi_out,
+                          void* stream);
+
 #ifdef __cplusplus
 }
 #endif

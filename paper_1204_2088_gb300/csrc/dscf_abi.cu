@@ -166,6 +166,11 @@ __global__ void k_fillf(float* p, long long n, float v) {
 
 }  // namespace
 
+namespace dscf {
+// Message for dscf_last_error(NULL) from entry points that have no context.
+void set_thread_error(const char* msg) { g_init_error = msg ? msg : ""; }
+}  // namespace dscf
+
 struct dscf_ctx {
     int nrep = 0, prec = 0, device = 0;
     std::vector<dscf_params> params;

@@ -71,6 +71,7 @@ def load():
         "dscf_launches_per_step": (ctypes.c_int64, [vp]),
         "dscf_probe": (ctypes.c_int, [vp, i32]),
         "dscf_probe_ms": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_float)]),
+        "dscf_densities_static": (ctypes.c_int, [P, i32, vp, vp, vp]),
     }
     for name, (res, args) in sigs.items():
         fn = getattr(lib, name)
@@ -110,6 +111,28 @@ def workspace_bytes(cfgs, precision=FP64) -> int:
     cfgs = [cfgs] if isinstance(cfgs, dict) else list(cfgs)
     arr = (Params * len(cfgs))(*[make_params(c) for c in cfgs])
     return int(load().dscf_workspace_bytes(arr, len(cfgs), precision))
+
+
+STATIC_SCRATCH_BYTES = 64 * 1024 * 1024
+
+
+def densities_static(cfg: dict, U: torch.Tensor, out: torch.Tensor, precision=FP64, stream=None):
+    """phi[U] through dscf_densities_static: for callers that cannot allocate device memory.
+
+    U and out are caller-owned device tensors ([ns, nz, ny, nx], contiguous, in the precision's
+    dtype); nothing is allocated here or in the library.  Raises DSCFError on an error code."""
+    lib = load()
+    want = torch.float64 if precision == FP64 else torch.float32
+    for t in (U, out):
+        if t.device.type != "cuda" or t.dtype != want or not t.is_contiguous():
+            raise ValueError("U and out must be contiguous CUDA tensors of the precision's dtype")
+    p = make_params(cfg)
+    s = stream if stream is not None else torch.cuda.current_stream(U.device)
+    rc = lib.dscf_densities_static(ctypes.byref(p), precision, ctypes.c_void_p(U.data_ptr()),
+                                   ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(s.cuda_stream))
+    if rc != DSCF_OK:
+        raise DSCFError(rc, lib.dscf_last_error(None).decode())
+    return out
 
 
 class Context:
