@@ -148,7 +148,8 @@ int dscf_set_fields(dscf_ctx* ctx, int32_t which, const void* src, int32_t on_ho
  *  6 LB mass sum_r rho, 7..9 LB momentum after collision, 10 max |u_lat|,
  *  11 Q of the last gradient evaluation, 12 <exp(-U_S)>, 13 NCG iterations per step,
  *  14 <g,g> and 15 max|g| at the start of the last inversion, 16 <g,g> and 17 max|g|
- *  at its end, 18 steps done, 19..23 reserved (0). */
+ *  at its end, 18 steps done, 19 z-chunk of the propagator tiles and 20 contour steps fused
+ *  per propagator launch, both chosen by the autotuner at dscf_init, 21..23 reserved (0). */
 int dscf_diagnostics(dscf_ctx* ctx, int32_t replica, double* out);
 
 /* Synchronise the stream and return the device status word as an error code (DSCF_OK or
@@ -163,6 +164,13 @@ const char* dscf_last_error(const dscf_ctx* ctx);
 
 /* Number of kernels one dscf_step(ctx, 1) launches (for launch accounting). */
 int64_t dscf_launches_per_step(const dscf_ctx* ctx);
+
+/* Override the autotuner's choice (for instance with a value cached from an earlier run):
+ * zc = z planes per propagator tile (>= 1), kfuse = contour steps per propagator launch (1..4;
+ * > 1 needs FP32 and nx in {32, 64, 128} for every replica, and kfuse <= N).  Synchronises the
+ * stream; the next dscf_step re-captures its graph.  Results do not depend on either value
+ * beyond rounding. */
+int dscf_set_tuning(dscf_ctx* ctx, int32_t zc, int32_t kfuse);
 
 /* Timing probe.  enable != 0 makes the next dscf_step capture CUDA events (created by the
  * library) into the step graph: around the 2N contour-sweep launches of the first gradient

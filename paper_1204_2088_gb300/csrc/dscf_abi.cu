@@ -19,13 +19,14 @@ using namespace dscf;
 
 namespace {
 
-constexpr int kTX = 32, kTY = 8;   // propagator tile (must match the kernels)
 thread_local std::string g_init_error;
 
 struct Layout {
     std::vector<Rep> reps;          // host copy, pointers filled by place()
     std::vector<int> tile2rep, blk2rep;
     std::vector<int> fwd_grid;      // [s] for s = 1..Nmax (index s), tiles of replicas with N >= s
+    std::vector<size_t> fwd_smem, bwd_smem;   // [s] dynamic shared memory of the contour launches
+    size_t es = 8;
     int ntiles = 0, nblk = 0, Nmax = 0;
     size_t bytes = 0;
     // offsets of the shared blocks
@@ -64,33 +65,62 @@ bool validate(const dscf_params* p, int n, std::string& why) {
     return true;
 }
 
-// Tiling and workspace layout.  With base == nullptr only sizes are computed.
-Layout make_layout(const dscf_params* p, int n, int prec, char* base) {
-    Layout L;
-    const size_t es = (prec == DSCF_FP64) ? sizeof(double) : sizeof(float);
-    L.reps.resize(n);
-    // replicas in order of decreasing chain length own the first tiles (prefix property)
+// Assign tiles (replicas in order of decreasing chain length own the first tiles, so the
+// replicas still active at contour step s are a prefix) and per-step grid sizes, for the
+// current z-chunk of every replica.
+void assign_tiles(Layout& L, const dscf_params* p, int n) {
     std::vector<int> order(n);
     for (int r = 0; r < n; ++r) order[r] = r;
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return p[a].N > p[b].N; });
+    L.tile2rep.clear();
+    L.blk2rep.clear();
+    L.ntiles = 0;
+    L.nblk = 0;
+    for (int k = 0; k < n; ++k) {
+        Rep& R = L.reps[order[k]];
+        R.tile0 = L.ntiles;
+        for (int t = 0; t < R.ntiles; ++t) L.tile2rep.push_back(order[k]);
+        L.ntiles += R.ntiles;
+        R.blk0 = L.nblk;
+        for (int b = 0; b < R.nblk; ++b) L.blk2rep.push_back(order[k]);
+        L.nblk += R.nblk;
+    }
+    L.fwd_grid.assign(L.Nmax + 2, 0);
+    L.fwd_smem.assign(L.Nmax + 2, 0);
+    L.bwd_smem.assign(L.Nmax + 2, 0);
+    for (int s = 1; s <= L.Nmax; ++s)
+        for (int r = 0; r < n; ++r)
+            if (L.reps[r].N >= s) {
+                L.fwd_grid[s] += L.reps[r].ntiles;
+                L.fwd_smem[s] = std::max(L.fwd_smem[s], prop_smem_bytes(L.reps[r].vec, false, L.es));
+                L.bwd_smem[s] = std::max(L.bwd_smem[s], prop_smem_bytes(L.reps[r].vec, true, L.es));
+            }
+}
+
+int default_zc(int nz) { return std::min(nz, 8); }
+
+// Tiling and workspace layout.  With base == nullptr only sizes are computed.  Tile maps and
+// partial-sum slots are sized for the smallest z-chunk the autotuner may choose, so re-tiling
+// never moves anything.
+Layout make_layout(const dscf_params* p, int n, int prec, char* base) {
+    Layout L;
+    const size_t es = (prec == DSCF_FP64) ? sizeof(double) : sizeof(float);
+    L.es = es;
+    L.reps.resize(n);
     long long ext = 0, vb = 0;
+    int max_tiles_total = 0, max_blk_total = 0;
     for (int r = 0; r < n; ++r) {
         Rep& R = L.reps[r];
         std::memset(&R, 0, sizeof(Rep));
         const dscf_params& q = p[r];
         R.nx = q.nx; R.ny = q.ny; R.nz = q.nz; R.ns = q.ns; R.N = q.N; R.nA = q.nA;
         R.V = (long long)q.nx * q.ny * q.nz;
-        R.tiles_x = (q.nx + kTX - 1) / kTX;
-        R.tiles_y = (q.ny + kTY - 1) / kTY;
-        R.zc = q.nz >= 64 ? 16 : std::max(1, std::min(q.nz, std::max(4, q.nz / 4)));
-        R.tiles_z = (q.nz + R.zc - 1) / R.zc;
-        R.ntiles = R.tiles_x * R.tiles_y * R.tiles_z;
-        long long nb = (R.V + kFlatThreads - 1) / kFlatThreads;
-        nb = std::min<long long>(nb, kMaxFlatBlocks);
-        long long chunk = (R.V + nb - 1) / nb;
-        chunk = (chunk + kFlatThreads - 1) / kFlatThreads * kFlatThreads;
-        R.chunk = (int)chunk;
-        R.nblk = (int)((R.V + chunk - 1) / chunk);
+        tile_replica(R, kMinZc);
+        const int max_tiles = R.ntiles;
+        max_tiles_total += max_tiles;
+        max_blk_total += R.nblk;
+        R.part_stride = std::max(max_tiles, R.nblk);
+        tile_replica(R, default_zc(q.nz));
         R.hydro = q.hydro;
         R.cn_sweeps = q.cn_sweeps;
         R.phi_p = q.phi_p; R.kappa = q.kappa; R.alpha = q.a * q.a / 6.0; R.dt = q.dt; R.M = q.M;
@@ -104,22 +134,9 @@ Layout make_layout(const dscf_params* p, int n, int prec, char* base) {
         R.vbase = vb;
         ext += (long long)q.ns * R.V;
         vb += R.V;
-        R.part_stride = std::max(R.ntiles, R.nblk);
         L.Nmax = std::max(L.Nmax, q.N);
     }
-    for (int k = 0; k < n; ++k) {
-        Rep& R = L.reps[order[k]];
-        R.tile0 = L.ntiles;
-        for (int t = 0; t < R.ntiles; ++t) L.tile2rep.push_back(order[k]);
-        L.ntiles += R.ntiles;
-        R.blk0 = L.nblk;
-        for (int b = 0; b < R.nblk; ++b) L.blk2rep.push_back(order[k]);
-        L.nblk += R.nblk;
-    }
-    L.fwd_grid.assign(L.Nmax + 2, 0);
-    for (int s = 1; s <= L.Nmax; ++s)
-        for (int r = 0; r < n; ++r)
-            if (L.reps[r].N >= s) L.fwd_grid[s] += L.reps[r].ntiles;
+    assign_tiles(L, p, n);
     // workspace
     size_t off = 0;
     auto take = [&](size_t bytes) -> void* {
@@ -150,8 +167,8 @@ Layout make_layout(const dscf_params* p, int n, int prec, char* base) {
         R.scal = (double*)take((size_t)kScalStride * sizeof(double));
     }
     L.off_reps = off; take(sizeof(Rep) * n);
-    L.off_t2r = off; take(sizeof(int) * L.ntiles);
-    L.off_b2r = off; take(sizeof(int) * L.nblk);
+    L.off_t2r = off; take(sizeof(int) * max_tiles_total);
+    L.off_b2r = off; take(sizeof(int) * max_blk_total);
     L.off_status = off; take(sizeof(int) * 64);
     L.bytes = off;
     return L;
@@ -186,6 +203,9 @@ struct dscf_ctx {
     bool probe = false, probe_ran = false;
     cudaEvent_t ev[6] = {};
     bool phim_stale = true;
+    int zc = 0;
+    int kfuse = 1;          // contour steps per propagator launch (1 = single-step kernels)
+    bool fusable = false;   // FP32 and every replica in the whole-row layout
     long long steps = 0;
     int64_t launches = 0;
     std::string err;
@@ -220,13 +240,31 @@ Launch launch_of(dscf_ctx* c, cudaStream_t s) {
     return L;
 }
 
+// Forward and backward contour sweeps of one gradient evaluation.
+template <typename T>
+int64_t enqueue_sweeps(dscf_ctx* c, const Launch& L) {
+    int64_t n = 0;
+    const int K = c->kfuse;
+    if (K > 1) {
+        int vmax = 0;
+        for (const Rep& R : c->L.reps) vmax = std::max(vmax, R.vec);
+        const size_t sm = prop_fused_smem_bytes(vmax, K);
+        const int ng = (c->L.Nmax + K - 1) / K;
+        for (int g = 0; g < ng; ++g) { launch_prop_fused(L, false, K, g, c->L.fwd_grid[g * K + 1], sm); ++n; }
+        for (int g = 0; g < ng; ++g) { launch_prop_fused(L, true, K, g, c->L.fwd_grid[g * K + 1], sm); ++n; }
+        return n;
+    }
+    for (int s = 1; s <= c->L.Nmax; ++s) { launch_prop_fwd<T>(L, s, c->L.fwd_grid[s], c->L.fwd_smem[s]); ++n; }
+    for (int j = 0; j < c->L.Nmax; ++j) { launch_prop_bwd<T>(L, j, c->L.fwd_grid[j + 1], c->L.bwd_smem[j + 1]); ++n; }
+    return n;
+}
+
 // One gradient evaluation: Boltzmann factors, forward and backward contour sweeps.
 template <typename T>
 int64_t enqueue_eval(dscf_ctx* c, const Launch& L, int exp_mode, int k, const void* Uext) {
     int64_t n = 0;
     launch_exp<T>(L, exp_mode, k, Uext); ++n;
-    for (int s = 1; s <= c->L.Nmax; ++s) { launch_prop_fwd<T>(L, s, c->L.fwd_grid[s]); ++n; }
-    for (int j = 0; j < c->L.Nmax; ++j) { launch_prop_bwd<T>(L, j, c->L.fwd_grid[j + 1]); ++n; }
+    n += enqueue_sweeps<T>(c, L);
     return n;
 }
 
@@ -241,8 +279,7 @@ int64_t enqueue_step(dscf_ctx* c, const Launch& L) {
     for (int k = 0; k < K; ++k) {
         launch_exp<T>(L, 1, k, nullptr); ++n;
         if (k == 0) mark(0);
-        for (int s = 1; s <= c->L.Nmax; ++s) { launch_prop_fwd<T>(L, s, c->L.fwd_grid[s]); ++n; }
-        for (int j = 0; j < c->L.Nmax; ++j) { launch_prop_bwd<T>(L, j, c->L.fwd_grid[j + 1]); ++n; }
+        n += enqueue_sweeps<T>(c, L);
         if (k == 0) mark(1);
         launch_trial<T>(L); ++n;
         n += enqueue_eval<T>(c, L, 2, k, nullptr);
@@ -289,6 +326,81 @@ int build_graph(dscf_ctx* c) {
 
 int set_dev(dscf_ctx* c) { return cuda_check(c, cudaSetDevice(c->device), "cudaSetDevice"); }
 
+int upload_tiles(dscf_ctx* c) {
+    int rc = cuda_check(c, cudaMemcpyAsync(c->d_reps, c->L.reps.data(), sizeof(Rep) * c->nrep, cudaMemcpyHostToDevice,
+                                           c->stream), "reps");
+    if (rc) return rc;
+    rc = cuda_check(c, cudaMemcpyAsync(c->d_t2r, c->L.tile2rep.data(), sizeof(int) * c->L.ntiles, cudaMemcpyHostToDevice,
+                                       c->stream), "tile map");
+    if (rc) return rc;
+    rc = cuda_check(c, cudaMemcpyAsync(c->d_b2r, c->L.blk2rep.data(), sizeof(int) * c->L.nblk, cudaMemcpyHostToDevice,
+                                       c->stream), "block map");
+    if (rc) return rc;
+    return cuda_check(c, cudaStreamSynchronize(c->stream), "tile upload");
+}
+
+void set_zc(dscf_ctx* c, int zc) {
+    for (int r = 0; r < c->nrep; ++r) tile_replica(c->L.reps[r], std::min(zc, c->L.reps[r].nz));
+    assign_tiles(c->L, c->params.data(), c->nrep);
+}
+
+// Autotuner: pick the z-chunk of the propagator tiles and the number of contour steps fused per
+// launch (one pair for all replicas) by timing forward contour launches on the context's own
+// buffers; the figure of merit is time per contour step.  Small problems keep the defaults.
+int autotune_zc(dscf_ctx* c) {
+    long long Vtot = 0;
+    int Nmin = 1 << 30;
+    for (const Rep& R : c->L.reps) { Vtot += R.V; Nmin = std::min(Nmin, R.N); }
+    int best = default_zc(c->L.reps[0].nz), bestK = 1;
+    c->fusable = (c->prec == DSCF_FP32);
+    for (const Rep& R : c->L.reps) c->fusable = c->fusable && (R.vec > 0);
+    if (c->fusable) {
+        const size_t lim = prop_fused_smem_bytes(4, 4);
+        if (int rc = cuda_check(c, (cudaError_t)prop_fused_set_smem_limit(lim), "fused shared-memory limit")) return rc;
+    }
+    if (Vtot >= 32 * 32 * 32) {
+        cudaEvent_t e0, e1;
+        if (int rc = cuda_check(c, cudaEventCreate(&e0), "tune event")) return rc;
+        if (int rc = cuda_check(c, cudaEventCreate(&e1), "tune event")) { cudaEventDestroy(e0); return rc; }
+        float best_ms = 1e30f;
+        const int cands[] = {4, 5, 6, 8, 11, 16, 22, 32};
+        const int kmax = c->fusable ? std::min(4, Nmin) : 1;
+        for (int zc : cands) {
+            set_zc(c, zc);
+            if (int rc = upload_tiles(c)) { cudaEventDestroy(e0); cudaEventDestroy(e1); return rc; }
+            const Launch L = launch_of(c, c->stream);
+            for (int K = 1; K <= kmax; ++K) {
+                int vmax = 0;
+                for (const Rep& R : c->L.reps) vmax = std::max(vmax, R.vec);
+                auto run = [&]() {
+                    if (K == 1) {
+                        if (c->prec == DSCF_FP64) launch_prop_fwd<double>(L, 2, c->L.fwd_grid[2], c->L.fwd_smem[2]);
+                        else launch_prop_fwd<float>(L, 2, c->L.fwd_grid[2], c->L.fwd_smem[2]);
+                    } else {
+                        launch_prop_fused(L, false, K, 0, c->L.fwd_grid[1], prop_fused_smem_bytes(vmax, K));
+                    }
+                };
+                for (int i = 0; i < 3; ++i) run();
+                cudaEventRecord(e0, c->stream);
+                for (int i = 0; i < 8; ++i) run();
+                cudaEventRecord(e1, c->stream);
+                float ms = 0.f;
+                cudaError_t e = cudaEventSynchronize(e1);
+                if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+                if (e == cudaSuccess) e = cudaGetLastError();
+                if (e != cudaSuccess) { cudaEventDestroy(e0); cudaEventDestroy(e1); return cuda_check(c, e, "tune timing"); }
+                ms /= (float)K;
+                if (ms < best_ms) { best_ms = ms; best = zc; bestK = K; }
+            }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+    }
+    c->zc = best;
+    c->kfuse = bestK;
+    set_zc(c, best);
+    return upload_tiles(c);
+}
 }  // namespace
 
 extern "C" {
@@ -363,6 +475,12 @@ int dscf_init(const dscf_params* p, int32_t n, int32_t precision, void* workspac
     }
     rc = rc ? rc : chk(cudaGetLastError(), "fill");
     rc = rc ? rc : chk(cudaStreamSynchronize(c->stream), "init sync");
+    if (!rc) {
+        const size_t lim = std::max(prop_smem_bytes(4, true, c->L.es), prop_smem_bytes(0, true, c->L.es));
+        const int e = precision == DSCF_FP64 ? prop_set_smem_limit<double>(lim) : prop_set_smem_limit<float>(lim);
+        rc = cuda_check(c, (cudaError_t)e, "propagator shared-memory limit");
+    }
+    rc = rc ? rc : autotune_zc(c);
     if (rc) {
         g_init_error = c->err;
         if (c->cap) cudaStreamDestroy(c->cap);
@@ -504,6 +622,8 @@ int dscf_diagnostics(dscf_ctx* c, int32_t replica, double* out) {
     out[16] = K > 0 ? s[S_ITER0 + 4 * (K - 1) + 2] : s[S_GG0];
     out[17] = K > 0 ? s[S_ITER0 + 4 * (K - 1) + 3] : s[S_GMAX0];
     out[18] = (double)c->steps;
+    out[19] = (double)c->zc;
+    out[20] = (double)c->kfuse;
     return DSCF_OK;
 }
 
@@ -547,6 +667,24 @@ int dscf_probe_ms(dscf_ctx* c, float* ms) {
     if (c->params[0].hydro)
         if (int rc = cuda_check(c, cudaEventElapsedTime(&ms[1], c->ev[2], c->ev[3]), "probe lb")) return rc;
     return cuda_check(c, cudaEventElapsedTime(&ms[2], c->ev[4], c->ev[5]), "probe step");
+}
+
+int dscf_set_tuning(dscf_ctx* c, int32_t zc, int32_t kfuse) {
+    if (!c) return DSCF_ERR_ARG;
+    if (zc < 1 || kfuse < 1 || kfuse > 4) return fail(c, DSCF_ERR_ARG, "need zc >= 1 and 1 <= kfuse <= 4");
+    if (kfuse > 1 && !c->fusable) return fail(c, DSCF_ERR_ARG, "contour fusion needs FP32 and nx in {32, 64, 128}");
+    for (const Rep& R : c->L.reps)
+        if (kfuse > R.N) return fail(c, DSCF_ERR_ARG, "kfuse exceeds a chain length");
+    if (int rc = set_dev(c)) return rc;
+    if (int rc = cuda_check(c, cudaStreamSynchronize(c->stream), "tuning sync")) return rc;
+    if (c->exec) {
+        cudaGraphExecDestroy(c->exec);
+        c->exec = nullptr;
+    }
+    c->zc = zc;
+    c->kfuse = kfuse;
+    set_zc(c, zc);
+    return upload_tiles(c);
 }
 
 int dscf_free(dscf_ctx* c) {

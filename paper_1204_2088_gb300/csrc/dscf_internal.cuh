@@ -10,6 +10,10 @@ constexpr int kFlatThreads = 256;     // threads of every site-parallel ("flat")
 constexpr int kMaxFlatBlocks = 1024;  // flat blocks per replica (= partial sums per replica)
 constexpr int kMaxNcg = 32;           // Fletcher-Reeves iterations per step, upper bound
 constexpr int kScalStride = 192;      // FP64 scalar slots per replica
+constexpr int kPropCols = 30;         // output x columns per propagator CTA (a warp minus 2 halo lanes)
+constexpr int kPropRows = 8;          // output y rows per propagator CTA
+// cp.async ring depth of the propagator kernels for an element size
+__host__ __device__ constexpr int prop_depth(size_t es) { return es == 8 ? 2 : 4; }
 
 // Partial-sum slots: one array of per-block FP64 partials per slot and replica.  Reducing a
 // slot is done redundantly, in a fixed order, by every block that needs the total, so the
@@ -46,6 +50,7 @@ struct Rep {
     int nx, ny, nz, ns, N, nA;
     long long V;
     int tiles_x, tiles_y, tiles_z, zc;     // propagator tiling
+    int vec;                               // 1, 2, 4: whole-row layout with nx = 32 vec; 0: tiled
     int tile0, ntiles;
     int blk0, nblk, chunk;                 // flat tiling: nblk blocks of `chunk` sites
     int hydro, cn_sweeps;
@@ -74,6 +79,24 @@ struct Rep {
     int part_stride;
     double* scal;   // [kScalStride]
 };
+
+// Propagator and flat tiling of one replica for a given z-chunk; the context path and the
+// allocation-free path both use it.
+inline void tile_replica(Rep& R, int zc) {
+    R.vec = (R.nx == 32 || R.nx == 64 || R.nx == 128) ? R.nx / 32 : 0;
+    R.tiles_x = R.vec ? 1 : (R.nx + kPropCols - 1) / kPropCols;
+    R.tiles_y = (R.ny + kPropRows - 1) / kPropRows;
+    R.zc = zc < 1 ? 1 : (zc > R.nz ? R.nz : zc);
+    R.tiles_z = (R.nz + R.zc - 1) / R.zc;
+    R.ntiles = R.tiles_x * R.tiles_y * R.tiles_z;
+    long long nb = (R.V + kFlatThreads - 1) / kFlatThreads;
+    if (nb > kMaxFlatBlocks) nb = kMaxFlatBlocks;
+    long long chunk = (R.V + nb - 1) / nb;
+    chunk = (chunk + kFlatThreads - 1) / kFlatThreads * kFlatThreads;
+    R.chunk = (int)chunk;
+    R.nblk = (int)((R.V + chunk - 1) / chunk);
+}
+constexpr int kMinZc = 4;             // smallest z-chunk the autotuner tries (most tiles)
 
 // Launch description shared by the host launchers.
 struct Launch {
@@ -167,8 +190,14 @@ __device__ __forceinline__ float bexp(float x) { return expf(-x); }
 // ---------------------------------------------------------------------------------------------
 // Host launchers (defined in the kernel translation units, explicit per precision).
 // ---------------------------------------------------------------------------------------------
-template <typename T> void launch_prop_fwd(const Launch& L, int s, int grid);
-template <typename T> void launch_prop_bwd(const Launch& L, int j, int grid);
+template <typename T> void launch_prop_fwd(const Launch& L, int s, int grid, size_t smem);
+template <typename T> void launch_prop_bwd(const Launch& L, int j, int grid, size_t smem);
+template <typename T> int prop_set_smem_limit(size_t bytes);   // returns a cudaError_t
+size_t prop_smem_bytes(int vec, bool bwd, size_t es);           // dynamic shared memory of one CTA
+// fused contour groups of K steps (FP32, whole-row layout only)
+size_t prop_fused_smem_bytes(int vec, int K);
+void launch_prop_fused(const Launch& L, bool bwd, int K, int g, int grid, size_t smem);
+int prop_fused_set_smem_limit(size_t bytes);                    // returns a cudaError_t
 // mode: 0 exp(-U), 1 trial exp(-(U + a1 d)), 2 commit U += a d then exp(-U), 3 exp(-Uext)
 template <typename T> void launch_exp(const Launch& L, int mode, int k, const void* Uext);
 template <typename T> void launch_trial(const Launch& L);

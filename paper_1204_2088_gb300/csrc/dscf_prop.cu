@@ -1,126 +1,539 @@
 // Green-propagator kernels (Eq. 16-17) and Boltzmann factors.
 //
-// One launch = one contour step s for every replica whose chain reaches s.  A CTA owns a
-// TX x TY column of the lattice and a chunk of zc planes; it streams along z, staging one
-// plane (plus a one-site halo in x and y) at a time in shared memory.  The 27-point linkage
-// stencil is the tensor product of the 1-D kernel (alpha, 1 - 2 alpha, alpha), so each plane
-// gets an x pass and a y pass in shared memory and the z pass combines three consecutive
-// planes held in registers.  Inputs of step s are the outputs of step s-1, which at the sizes
-// of interest are still resident in the 129 MB L2; the HBM traffic is the write of G_s in the
-// forward sweep and its read in the backward sweep.
+// One launch = one contour step s for every replica whose chain reaches s.  A CTA owns ROWS
+// lattice rows (plus one halo row on each side, one warp per row) across a range of x and a range
+// of zc planes (zc picked per context by the autotuner at initialisation).  Per plane a thread
+// applies the x pass of the separable 27-point stencil to its sites, writes them to a
+// double-buffered shared row buffer (one barrier per plane), reads the two neighbouring rows for
+// the y pass, and combines three consecutive planes in registers for the z pass.
+//
+// Two row layouts:
+//  - whole-row (nx = 32 VEC, VEC = 1, 2, 4): a warp holds an entire periodic x row, VEC
+//    consecutive sites per lane; the x pass runs in registers plus two wrap-around shuffles, so no
+//    halo is loaded in x and all accesses are VEC-wide vectors;
+//  - tiled (any nx): lane L holds column x0 - 1 + L of a 30-column tile, lanes 0 and 31 being the
+//    x halo.
+//
+// Loads are asynchronous: every thread copies its own input sites of plane j + DEPTH - 1 and the
+// per-site operands (Boltzmann factor, G_s, q) of the matching output plane into a DEPTH-stage
+// shared-memory ring with cp.async, so DEPTH planes per thread are in flight without holding
+// registers; a thread only reads ring slots it filled itself, so the ring needs no barrier.  The
+// inputs of step s are the outputs of step s-1, still resident in the 129 MB L2 at the sizes of
+// interest; the HBM traffic is the write of G_s in the forward sweep and its read in the
+// backward sweep.
 #include "dscf_internal.cuh"
 
 namespace dscf {
 
-constexpr int TX = 32;
-constexpr int TY = 8;
+constexpr int NWARP = kPropRows + 2;   // warps per CTA
 
-template <typename T>
-struct Plane {
-    T in[TY + 2][TX + 2];
-    T xs[TY + 2][TX];
+__device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+template <int BYTES>
+__device__ __forceinline__ void cp_bytes(void* sdst, const void* gsrc) {
+    if constexpr (BYTES <= 16) {
+        asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(smem_addr(sdst)), "l"(gsrc), "n"(BYTES));
+    } else {
+        cp_bytes<16>(sdst, gsrc);
+        cp_bytes<BYTES - 16>((char*)sdst + 16, (const char*)gsrc + 16);
+    }
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
+
+template <typename T, int VEC>
+struct alignas(sizeof(T) * VEC <= 16 ? sizeof(T) * VEC : 16) Vec {
+    T v[VEC];
 };
 
-// xy part of the separable stencil on plane z of `src` (nullptr = the constant field 1) at
-// this thread's (x, y); all threads of the CTA must call it.
+// Per-launch operands of one replica.
 template <typename T>
-__device__ __forceinline__ T xy_pass(const T* __restrict__ src, int z, int x0, int y0, int nx, int ny,
-                                     int nz, Plane<T>& P, T al, T be) {
-    const int tid = threadIdx.x + threadIdx.y * TX;
-    const int zz = wrapi(z, nz);
-    const long long pofs = (long long)zz * nx * ny;
-    for (int i = tid; i < (TY + 2) * (TX + 2); i += TX * TY) {
-        const int ly = i / (TX + 2), lx = i - ly * (TX + 2);
-        const int gx = wrapi(x0 + lx - 1, nx), gy = wrapi(y0 + ly - 1, ny);
-        P.in[ly][lx] = src ? src[pofs + gx + (long long)gy * nx] : T(1);
+struct PropOps {
+    const T* src;   // nullptr = the constant field 1
+    T* dst;
+    const T* E;
+    const T* Gs;
+    T* q;
+    bool lastQ, first, wout;
+    T al, be;
+};
+
+template <typename T, bool BWD>
+__device__ __forceinline__ PropOps<T> prop_ops(const Rep& R, int step) {
+    PropOps<T> o;
+    const size_t V = (size_t)R.V;
+    o.Gs = nullptr;
+    o.q = nullptr;
+    o.lastQ = o.first = false;
+    o.wout = true;
+    if (!BWD) {
+        const int s = step;
+        o.src = (s == 1) ? nullptr : (const T*)R.G + (size_t)(s - 2) * V;
+        o.dst = (T*)R.G + (size_t)(s - 1) * V;
+        o.E = (const T*)R.E + (s <= R.nA ? 0 : V);
+        o.lastQ = (s == R.N);
+    } else {
+        const int s = R.N - step;
+        o.src = (step == 0) ? nullptr : (const T*)(((step - 1) & 1) ? R.Gp1 : R.Gp0);
+        o.dst = (T*)((step & 1) ? R.Gp1 : R.Gp0);
+        o.Gs = (const T*)R.G + (size_t)(s - 1) * V;
+        o.E = (const T*)R.E + (s <= R.nA ? 0 : V);
+        o.q = (T*)R.q + (s <= R.nA ? 0 : V);
+        o.first = (s == R.N) || (s == R.nA);
+        o.wout = (s > 1);
     }
-    __syncthreads();
-    for (int row = threadIdx.y; row < TY + 2; row += TY)
-        P.xs[row][threadIdx.x] =
-            be * P.in[row][threadIdx.x + 1] + al * (P.in[row][threadIdx.x] + P.in[row][threadIdx.x + 2]);
-    __syncthreads();
-    const T v = be * P.xs[threadIdx.y + 1][threadIdx.x] +
-                al * (P.xs[threadIdx.y][threadIdx.x] + P.xs[threadIdx.y + 2][threadIdx.x]);
-    __syncthreads();
-    return v;
+    o.al = (T)R.alpha;
+    o.be = (T)(1.0 - 2.0 * R.alpha);
+    return o;
 }
 
-// Forward recurrence: G_s = exp(-U_{I_s}) sigma[G_{s-1}], G_0 = 1 (Eq. 17).  At s = N each
-// CTA also writes its FP64 partial sum of G_N for Q = V^-1 sum_r G_N(r).
-template <typename T>
-__global__ void __launch_bounds__(TX* TY) k_prop_fwd(const Rep* __restrict__ reps, const int* __restrict__ tile2rep,
-                                                     int s) {
-    __shared__ Plane<T> P;
+// Shared-memory bytes of one CTA for a replica (host and device agree through this function).
+__host__ __device__ constexpr size_t prop_smem(int vec, bool bwd, size_t es) {
+    // row buffer (2) + ring stages (input, E, and G, q in the backward sweep)
+    return (size_t)(2 + prop_depth(es) * (bwd ? 4 : 2)) * NWARP * 32 * (vec > 0 ? vec : 1) * es;
+}
+
+// Whole-row layout: warp w holds row y0 - 1 + w, lane L sites x = VEC L .. VEC L + VEC - 1.
+template <typename T, bool BWD, int VEC>
+__device__ __forceinline__ double prop_row(const Rep& R, int lt, const PropOps<T>& o, unsigned char* smem) {
+    constexpr int D = prop_depth(sizeof(T));
+    constexpr int W = 32 * VEC;
+    using VT = Vec<T, VEC>;
+    T* sX = (T*)smem;                            // [2][NWARP][W]
+    T* sRaw = sX + 2 * NWARP * W;                // [D][NWARP][W]
+    T* sE = sRaw + D * NWARP * W;                // [D][NWARP][W]
+    T* sG = sE + D * NWARP * W;                  // [D][NWARP][W] (backward)
+    T* sQ = sG + D * NWARP * W;                  // [D][NWARP][W] (backward)
+    const int ty = lt % R.tiles_y, tz = lt / R.tiles_y;
+    const int nx = W, ny = R.ny, nz = R.nz;
+    const int plane = nx * ny;
+    const int y0 = ty * kPropRows;
+    const int zb = tz * R.zc, ze = min(zb + R.zc, nz);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int y = y0 - 1 + w;
+    const int rowbase = wrapi(y, ny) * nx + VEC * lane;
+    const bool outw = (w >= 1) && (w <= kPropRows);
+    const bool act = outw && (y < ny);
+    const int np = ze - zb + 2;
+    const int me = w * W + VEC * lane;           // this thread's slot inside a [NWARP][W] block
+
+    auto issue = [&](int j) {
+        if (j < np) {
+            const int st = (j % D) * NWARP * W + me;
+            if (o.src) {
+                int z = zb - 1 + j;
+                z = z < 0 ? z + nz : (z >= nz ? z - nz : z);
+                cp_bytes<sizeof(VT)>(sRaw + st, o.src + rowbase + z * plane);
+            }
+            if (act && j >= 2) {
+                const int i = rowbase + (zb + j - 2) * plane;
+                cp_bytes<sizeof(VT)>(sE + st, o.E + i);
+                if (BWD) {
+                    cp_bytes<sizeof(VT)>(sG + st, o.Gs + i);
+                    if (!o.first) cp_bytes<sizeof(VT)>(sQ + st, o.q + i);
+                }
+            }
+        }
+        cp_commit();
+    };
+#pragma unroll
+    for (int j = 0; j < D - 1; ++j) issue(j);
+
+    const T al = o.al, be = o.be;
+    double qacc = 0.0;
+    T pm[VEC], p0[VEC];
+#pragma unroll
+    for (int k = 0; k < VEC; ++k) pm[k] = p0[k] = T(0);
+    for (int j = 0; j < np; ++j) {
+        issue(j + D - 1);
+        cp_wait<D - 1>();
+        const int st = (j % D) * NWARP * W + me;
+        VT v;
+        if (o.src) {
+            v = *(const VT*)(sRaw + st);
+        } else {
+#pragma unroll
+            for (int k = 0; k < VEC; ++k) v.v[k] = T(1);
+        }
+        const T lv = __shfl_sync(0xffffffffu, v.v[VEC - 1], (lane + 31) & 31);
+        const T rv = __shfl_sync(0xffffffffu, v.v[0], (lane + 1) & 31);
+        VT xf;
+#pragma unroll
+        for (int k = 0; k < VEC; ++k) {
+            const T l = (k == 0) ? lv : v.v[k - 1];
+            const T r = (k == VEC - 1) ? rv : v.v[k + 1];
+            xf.v[k] = be * v.v[k] + al * (l + r);
+        }
+        T* xb = sX + (j & 1) * NWARP * W;
+        *(VT*)(xb + me) = xf;
+        __syncthreads();
+        if (outw) {
+            const VT a = *(const VT*)(xb + me - W);
+            const VT b = *(const VT*)(xb + me);
+            const VT c = *(const VT*)(xb + me + W);
+            T yf[VEC];
+#pragma unroll
+            for (int k = 0; k < VEC; ++k) yf[k] = be * b.v[k] + al * (a.v[k] + c.v[k]);
+            if (j >= 2 && act) {
+                const int i = rowbase + (zb + j - 2) * plane;
+                const VT e = *(const VT*)(sE + st);
+                VT out;
+                if (!BWD) {
+#pragma unroll
+                    for (int k = 0; k < VEC; ++k) {
+                        out.v[k] = e.v[k] * (be * p0[k] + al * (pm[k] + yf[k]));
+                        if (o.lastQ) qacc += (double)out.v[k];
+                    }
+                    *(VT*)(o.dst + i) = out;
+                } else {
+                    const VT g = *(const VT*)(sG + st);
+                    VT qv;
+                    if (o.first) {
+#pragma unroll
+                        for (int k = 0; k < VEC; ++k) qv.v[k] = T(0);
+                    } else {
+                        qv = *(const VT*)(sQ + st);
+                    }
+#pragma unroll
+                    for (int k = 0; k < VEC; ++k) {
+                        const T sig = be * p0[k] + al * (pm[k] + yf[k]);
+                        qv.v[k] = qv.v[k] + g.v[k] * sig;
+                        out.v[k] = e.v[k] * sig;
+                    }
+                    *(VT*)(o.q + i) = qv;
+                    if (o.wout) *(VT*)(o.dst + i) = out;
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < VEC; ++k) {
+                pm[k] = p0[k];
+                p0[k] = yf[k];
+            }
+        }
+    }
+    cp_wait<0>();
+    return qacc;
+}
+
+// Tiled layout (any nx): lane L holds column x0 - 1 + L of a 30-column tile.
+template <typename T, bool BWD>
+__device__ __forceinline__ double prop_tiled(const Rep& R, int lt, const PropOps<T>& o, unsigned char* smem) {
+    constexpr int D = prop_depth(sizeof(T));
+    constexpr int W = 32;
+    T* sX = (T*)smem;
+    T* sRaw = sX + 2 * NWARP * W;
+    T* sE = sRaw + D * NWARP * W;
+    T* sG = sE + D * NWARP * W;
+    T* sQ = sG + D * NWARP * W;
+    const int txy = R.tiles_x * R.tiles_y;
+    const int tz = lt / txy, rem = lt - tz * txy;
+    const int ty = rem / R.tiles_x, tx = rem - ty * R.tiles_x;
+    const int nx = R.nx, ny = R.ny, nz = R.nz;
+    const int plane = nx * ny;
+    const int x0 = tx * kPropCols, y0 = ty * kPropRows;
+    const int zb = tz * R.zc, ze = min(zb + R.zc, nz);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int x = x0 - 1 + lane, y = y0 - 1 + w;
+    const int col = wrapi(x, nx) + wrapi(y, ny) * nx;
+    const bool act = lane >= 1 && lane <= kPropCols && w >= 1 && w <= kPropRows && x < nx && y < ny;
+    const int np = ze - zb + 2;
+    const int me = w * W + lane;
+
+    auto issue = [&](int j) {
+        if (j < np) {
+            const int st = (j % D) * NWARP * W + me;
+            if (o.src) {
+                int z = zb - 1 + j;
+                z = z < 0 ? z + nz : (z >= nz ? z - nz : z);
+                cp_bytes<sizeof(T)>(sRaw + st, o.src + col + z * plane);
+            }
+            if (act && j >= 2) {
+                const int i = col + (zb + j - 2) * plane;
+                cp_bytes<sizeof(T)>(sE + st, o.E + i);
+                if (BWD) {
+                    cp_bytes<sizeof(T)>(sG + st, o.Gs + i);
+                    if (!o.first) cp_bytes<sizeof(T)>(sQ + st, o.q + i);
+                }
+            }
+        }
+        cp_commit();
+    };
+#pragma unroll
+    for (int j = 0; j < D - 1; ++j) issue(j);
+
+    const T al = o.al, be = o.be;
+    double qacc = 0.0;
+    T pm = T(0), p0 = T(0);
+    for (int j = 0; j < np; ++j) {
+        issue(j + D - 1);
+        cp_wait<D - 1>();
+        const int st = (j % D) * NWARP * W + me;
+        const T v = o.src ? sRaw[st] : T(1);
+        const T l = __shfl_up_sync(0xffffffffu, v, 1);
+        const T r = __shfl_down_sync(0xffffffffu, v, 1);
+        T* xb = sX + (j & 1) * NWARP * W;
+        xb[me] = be * v + al * (l + r);
+        __syncthreads();
+        if (w >= 1 && w <= kPropRows) {
+            const T yf = be * xb[me] + al * (xb[me - W] + xb[me + W]);
+            if (j >= 2 && act) {
+                const int i = col + (zb + j - 2) * plane;
+                const T sig = be * p0 + al * (pm + yf);
+                const T e = sE[st];
+                if (!BWD) {
+                    const T g = e * sig;
+                    o.dst[i] = g;
+                    if (o.lastQ) qacc += (double)g;
+                } else {
+                    const T q0 = o.first ? T(0) : sQ[st];
+                    o.q[i] = q0 + sG[st] * sig;
+                    if (o.wout) o.dst[i] = e * sig;
+                }
+            }
+            pm = p0;
+            p0 = yf;
+        }
+    }
+    cp_wait<0>();
+    return qacc;
+}
+
+// Forward (BWD = false): G_s = exp(-U_{I_s}) sigma[G_{s-1}], G_0 = 1 (Eq. 17); at s = N each CTA
+// also writes its FP64 partial sum of G_N for Q = V^-1 sum_r G_N(r).
+// Backward (BWD = true), launch j handles s = N - j (Eq. 16-17):
+//   sig = sigma[G+_{s+1}] (G+_{N+1} = 1);  q_{I_s} += G_s sig;  G+_s = exp(-U_{I_s}) sig.
+// G+ only lives in two ping-pong buffers; q_I is (re)started at the first bead of each block.
+template <typename T, bool BWD>
+__global__ void __launch_bounds__(32 * NWARP) k_prop(const Rep* __restrict__ reps, const int* __restrict__ tile2rep,
+                                                     int step) {
+    extern __shared__ __align__(16) unsigned char smem[];
     __shared__ double sh[33];
     const Rep& R = reps[tile2rep[blockIdx.x]];
     const int lt = blockIdx.x - R.tile0;
-    const int tx = lt % R.tiles_x, ty = (lt / R.tiles_x) % R.tiles_y, tz = lt / (R.tiles_x * R.tiles_y);
-    const int nx = R.nx, ny = R.ny, nz = R.nz;
-    const int x0 = tx * TX, y0 = ty * TY, z0 = tz * R.zc, z1 = min(z0 + R.zc, nz);
-    const long long V = R.V;
-    const T* src = (s == 1) ? nullptr : (const T*)R.G + (long long)(s - 2) * V;
-    T* dst = (T*)R.G + (long long)(s - 1) * V;
-    const T* E = (const T*)R.E + (s <= R.nA ? 0 : V);
-    const T al = (T)R.alpha, be = (T)(1.0 - 2.0 * R.alpha);
-    const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
-    const bool act = (x < nx) && (y < ny);
-    const bool lastQ = (s == R.N);
-    double qacc = 0.0;
-    T pm = xy_pass(src, z0 - 1, x0, y0, nx, ny, nz, P, al, be);
-    T p0 = xy_pass(src, z0, x0, y0, nx, ny, nz, P, al, be);
-    for (int z = z0; z < z1; ++z) {
-        const T pp = xy_pass(src, z + 1, x0, y0, nx, ny, nz, P, al, be);
-        if (act) {
-            const long long i = x + (long long)nx * (y + (long long)ny * z);
-            const T g = E[i] * (be * p0 + al * (pm + pp));
-            dst[i] = g;
-            if (lastQ) qacc += (double)g;
-        }
-        pm = p0;
-        p0 = pp;
+    const PropOps<T> o = prop_ops<T, BWD>(R, step);
+    double qacc;
+    switch (R.vec) {
+        case 4: qacc = prop_row<T, BWD, 4>(R, lt, o, smem); break;
+        case 2: qacc = prop_row<T, BWD, 2>(R, lt, o, smem); break;
+        case 1: qacc = prop_row<T, BWD, 1>(R, lt, o, smem); break;
+        default: qacc = prop_tiled<T, BWD>(R, lt, o, smem); break;
     }
-    if (lastQ) {
+    if (!BWD && o.lastQ) {
         const double t = block_sum(qacc, sh);
-        if (threadIdx.x == 0 && threadIdx.y == 0) slot(R, P_Q)[lt] = t;
+        if (threadIdx.x == 0) slot(R, P_Q)[lt] = t;
     }
 }
 
-// Backward recurrence and contour quadrature (Eq. 16-17), launch j handles s = N - j:
-//   sig = sigma[G+_{s+1}] (G+_{N+1} = 1);  q_{I_s} += G_s * sig;  G+_s = exp(-U_{I_s}) * sig.
-// G+ only lives in two ping-pong buffers; q_I is (re)started at the first bead of each block.
-template <typename T>
-__global__ void __launch_bounds__(TX* TY) k_prop_bwd(const Rep* __restrict__ reps, const int* __restrict__ tile2rep,
-                                                     int j) {
-    __shared__ Plane<T> P;
+// ---------------------------------------------------------------------------------------------
+// Contour-step fusion (whole-row layout, FP32): one launch advances a group of up to K contour
+// steps.  Warp w holds row y0 - K + w (ROWS output rows plus K halo rows on each side); level 0 is
+// the group's input field, level k its k-th step.  The CTA streams the planes of its z range
+// extended by K on each side through a software pipeline: at pipeline step t it x- and y-filters
+// level 0 at plane t, then for k = 1..kg computes level k at plane t - k from the three
+// x/y-filtered planes of level k - 1 kept in registers, and x/y-filters it in turn (one barrier
+// per level, each level with its own double-buffered row buffer).  The halo shrinks by one row
+// and one plane per level, so level kg is exact on the CTA's own rows and planes.
+//   forward group g: steps s = gK + k (k = 1..kg); every level's G_s is stored (interior only);
+//   backward group g: steps s = N - gK - k + 1; q_{I_s} += G_s sig at every level, and only the
+//   last level's G+ is stored.
+// Per contour step this reads the previous propagator from L2 once per group instead of once per
+// step and saves K - 1 launches per group.
+// ---------------------------------------------------------------------------------------------
+template <bool BWD, int VEC, int K>
+__device__ __forceinline__ double prop_fused_row(const Rep& R, int lt, int g, unsigned char* smem) {
+    using T = float;
+    constexpr int D = 4;
+    constexpr int W = 32 * VEC;
+    constexpr int NW = kPropRows + 2 * K;
+    using VT = Vec<T, VEC>;
+    T* sX = (T*)smem;                            // [K][2][NW][W]
+    T* sRaw = sX + K * 2 * NW * W;               // [D][NW][W]
+    const int ty = lt % R.tiles_y, tz = lt / R.tiles_y;
+    const int ny = R.ny, nz = R.nz, N = R.N, nA = R.nA;
+    const int plane = W * ny;
+    const size_t V = (size_t)R.V;
+    const int y0 = ty * kPropRows;
+    const int zb = tz * R.zc, ze = min(zb + R.zc, nz);
+    const int zn = ze - zb;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int y = y0 - K + w;
+    const int rowbase = wrapi(y, ny) * W + VEC * lane;
+    const bool rowout = (w >= K) && (w < K + kPropRows) && (y < ny);
+    const int np = zn + 2 * K;                   // level-0 planes zb - K .. ze + K - 1
+    const int me = w * W + VEC * lane;
+    const T al = (T)R.alpha, be = (T)(1.0 - 2.0 * R.alpha);
+
+    // group geometry
+    int kg, sfirst;   // number of levels, contour index of level 1
+    const T* src;
+    if (!BWD) {
+        sfirst = g * K + 1;
+        kg = min(K, N - g * K);
+        src = (g == 0) ? nullptr : (const T*)R.G + (size_t)(g * K - 1) * V;
+    } else {
+        sfirst = N - g * K;
+        kg = min(K, sfirst);
+        src = (g == 0) ? nullptr : (const T*)(((g - 1) & 1) ? R.Gp1 : R.Gp0);
+    }
+    T* gpout = (T*)((g & 1) ? R.Gp1 : R.Gp0);
+    auto level_s = [&](int k) { return BWD ? sfirst - k + 1 : sfirst + k - 1; };
+    auto wrapz = [&](int z) { return z < 0 ? z + nz : (z >= nz ? z - nz : z); };
+
+    auto issue = [&](int j) {
+        if (j < np && src) {
+            cp_bytes<sizeof(VT)>(sRaw + (j % D) * NW * W + me, src + rowbase + wrapz(zb - K + j) * plane);
+        }
+        cp_commit();
+    };
+#pragma unroll
+    for (int j = 0; j < D - 1; ++j) issue(j);
+
+    // xy[k][m]: x/y-filtered level k at the three most recent planes (m = 0 oldest)
+    T xy[K][3][VEC];
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+#pragma unroll
+        for (int m = 0; m < 3; ++m)
+#pragma unroll
+            for (int c = 0; c < VEC; ++c) xy[k][m][c] = T(0);
+    double qacc = 0.0;
+
+    // x pass of a VEC-vector (periodic row held by the warp) into row buffer `buf`, then barrier,
+    // then the y pass of this warp's row.
+    auto xyfilter = [&](const VT& v, T* buf, T (&out)[VEC]) {
+        const T lv = __shfl_sync(0xffffffffu, v.v[VEC - 1], (lane + 31) & 31);
+        const T rv = __shfl_sync(0xffffffffu, v.v[0], (lane + 1) & 31);
+        VT xf;
+#pragma unroll
+        for (int c = 0; c < VEC; ++c) {
+            const T l = (c == 0) ? lv : v.v[c - 1];
+            const T r = (c == VEC - 1) ? rv : v.v[c + 1];
+            xf.v[c] = be * v.v[c] + al * (l + r);
+        }
+        *(VT*)(buf + me) = xf;
+        __syncthreads();
+        if (w >= 1 && w < NW - 1) {
+            const VT a = *(const VT*)(buf + me - W);
+            const VT c = *(const VT*)(buf + me + W);
+#pragma unroll
+            for (int q = 0; q < VEC; ++q) out[q] = be * xf.v[q] + al * (a.v[q] + c.v[q]);
+        } else {
+#pragma unroll
+            for (int q = 0; q < VEC; ++q) out[q] = T(0);
+        }
+    };
+
+    for (int t = 0; t < np; ++t) {
+        // operands of every level for this pipeline step (level k at plane t - k)
+        VT ev[K], gv[K], qv[K];
+#pragma unroll
+        for (int k = 1; k <= K; ++k) {
+            const int p = t - k;
+            if (k <= kg && p >= 0 && p < np) {
+                const int s = level_s(k);
+                const int i = rowbase + wrapz(zb - K + p) * plane;
+                ev[k - 1] = *(const VT*)((const T*)R.E + (s <= nA ? 0 : V) + i);
+                if (BWD) {
+                    gv[k - 1] = *(const VT*)((const T*)R.G + (size_t)(s - 1) * V + i);
+                    const bool first = (s == N) || (s == nA);
+                    if (!first && rowout && p >= K && p < K + zn) {
+                        qv[k - 1] = *(const VT*)((const T*)R.q + (s <= nA ? 0 : V) + i);
+                    } else {
+#pragma unroll
+                        for (int c = 0; c < VEC; ++c) qv[k - 1].v[c] = T(0);
+                    }
+                }
+            }
+        }
+        // level 0 at plane t
+        issue(t + D - 1);
+        cp_wait<D - 1>();
+        {
+            VT v;
+            if (src && t < np) {
+                v = *(const VT*)(sRaw + (t % D) * NW * W + me);
+            } else {
+#pragma unroll
+                for (int c = 0; c < VEC; ++c) v.v[c] = T(1);
+            }
+            T out[VEC];
+            xyfilter(v, sX + ((0 * 2) + (t & 1)) * NW * W, out);
+#pragma unroll
+            for (int c = 0; c < VEC; ++c) {
+                xy[0][0][c] = xy[0][1][c];
+                xy[0][1][c] = xy[0][2][c];
+                xy[0][2][c] = out[c];
+            }
+        }
+        // levels 1..K
+#pragma unroll
+        for (int k = 1; k <= K; ++k) {
+            const int p = t - k;                           // plane of level k
+            const bool live = (k <= kg);                   // uniform across the CTA
+            if (!live) break;
+            VT val;
+#pragma unroll
+            for (int c = 0; c < VEC; ++c)
+                val.v[c] = ev[k - 1].v[c] * (be * xy[k - 1][1][c] + al * (xy[k - 1][0][c] + xy[k - 1][2][c]));
+            const bool inside = rowout && p >= K && p < K + zn;
+            const int s = level_s(k);
+            if (p >= 0 && p < np) {
+                const int i = rowbase + wrapz(zb - K + p) * plane;
+                if (!BWD) {
+                    if (inside) {
+                        *(VT*)((T*)R.G + (size_t)(s - 1) * V + i) = val;
+                        if (s == N) {
+#pragma unroll
+                            for (int c = 0; c < VEC; ++c) qacc += (double)val.v[c];
+                        }
+                    }
+                } else if (inside) {
+                    // val = E sig  ->  q += G_s sig  with sig = val / E recomputed exactly below
+                    VT qn;
+#pragma unroll
+                    for (int c = 0; c < VEC; ++c) {
+                        const T sig = be * xy[k - 1][1][c] + al * (xy[k - 1][0][c] + xy[k - 1][2][c]);
+                        qn.v[c] = qv[k - 1].v[c] + gv[k - 1].v[c] * sig;
+                    }
+                    *(VT*)((T*)R.q + (s <= nA ? 0 : V) + i) = qn;
+                    if (k == kg && s > 1) *(VT*)(gpout + i) = val;
+                }
+            }
+            if (k < kg) {
+                T out[VEC];
+                xyfilter(val, sX + ((k * 2) + (t & 1)) * NW * W, out);
+#pragma unroll
+                for (int c = 0; c < VEC; ++c) {
+                    xy[k][0][c] = xy[k][1][c];
+                    xy[k][1][c] = xy[k][2][c];
+                    xy[k][2][c] = out[c];
+                }
+            }
+        }
+    }
+    cp_wait<0>();
+    return qacc;
+}
+
+template <bool BWD, int K>
+__global__ void __launch_bounds__(32 * (kPropRows + 2 * K)) k_prop_fused(const Rep* __restrict__ reps,
+                                                                        const int* __restrict__ tile2rep, int g) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ double sh[33];
     const Rep& R = reps[tile2rep[blockIdx.x]];
     const int lt = blockIdx.x - R.tile0;
-    const int tx = lt % R.tiles_x, ty = (lt / R.tiles_x) % R.tiles_y, tz = lt / (R.tiles_x * R.tiles_y);
-    const int nx = R.nx, ny = R.ny, nz = R.nz;
-    const int x0 = tx * TX, y0 = ty * TY, z0 = tz * R.zc, z1 = min(z0 + R.zc, nz);
-    const long long V = R.V;
-    const int s = R.N - j;
-    const T* src = (j == 0) ? nullptr : (const T*)(((j - 1) & 1) ? R.Gp1 : R.Gp0);
-    T* dst = (T*)((j & 1) ? R.Gp1 : R.Gp0);
-    const T* Gs = (const T*)R.G + (long long)(s - 1) * V;
-    const T* E = (const T*)R.E + (s <= R.nA ? 0 : V);
-    T* q = (T*)R.q + (s <= R.nA ? 0 : V);
-    const bool first = (s == R.N) || (s == R.nA);
-    const bool wout = (s > 1);
-    const T al = (T)R.alpha, be = (T)(1.0 - 2.0 * R.alpha);
-    const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
-    const bool act = (x < nx) && (y < ny);
-    T pm = xy_pass(src, z0 - 1, x0, y0, nx, ny, nz, P, al, be);
-    T p0 = xy_pass(src, z0, x0, y0, nx, ny, nz, P, al, be);
-    for (int z = z0; z < z1; ++z) {
-        const T pp = xy_pass(src, z + 1, x0, y0, nx, ny, nz, P, al, be);
-        if (act) {
-            const long long i = x + (long long)nx * (y + (long long)ny * z);
-            const T sig = be * p0 + al * (pm + pp);
-            q[i] = (first ? T(0) : q[i]) + Gs[i] * sig;
-            if (wout) dst[i] = E[i] * sig;
+    double qacc;
+    switch (R.vec) {
+        case 4: qacc = prop_fused_row<BWD, 4, K>(R, lt, g, smem); break;
+        case 2: qacc = prop_fused_row<BWD, 2, K>(R, lt, g, smem); break;
+        default: qacc = prop_fused_row<BWD, 1, K>(R, lt, g, smem); break;
+    }
+    if (!BWD) {
+        const bool lastQ = (g * K + K >= R.N);   // this group reaches s = N
+        if (lastQ) {
+            const double t = block_sum(qacc, sh);
+            if (threadIdx.x == 0) slot(R, P_Q)[lt] = t;
         }
-        pm = p0;
-        p0 = pp;
     }
 }
 
@@ -194,24 +607,64 @@ __global__ void __launch_bounds__(kFlatThreads) k_exp(const Rep* __restrict__ re
 }
 
 template <typename T>
-void launch_prop_fwd(const Launch& L, int s, int grid) {
+void launch_prop_fwd(const Launch& L, int s, int grid, size_t smem) {
     if (grid <= 0) return;
-    k_prop_fwd<T><<<grid, dim3(TX, TY), 0, L.stream>>>(L.reps, L.tile2rep, s);
+    k_prop<T, false><<<grid, 32 * NWARP, smem, L.stream>>>(L.reps, L.tile2rep, s);
 }
 template <typename T>
-void launch_prop_bwd(const Launch& L, int j, int grid) {
+void launch_prop_bwd(const Launch& L, int j, int grid, size_t smem) {
     if (grid <= 0) return;
-    k_prop_bwd<T><<<grid, dim3(TX, TY), 0, L.stream>>>(L.reps, L.tile2rep, j);
+    k_prop<T, true><<<grid, 32 * NWARP, smem, L.stream>>>(L.reps, L.tile2rep, j);
 }
+size_t prop_fused_smem_bytes(int vec, int K) {
+    return (size_t)(K * 2 + 4) * (kPropRows + 2 * K) * 32 * (vec > 0 ? vec : 1) * sizeof(float);
+}
+int prop_fused_threads(int K) { return 32 * (kPropRows + 2 * K); }
+void launch_prop_fused(const Launch& L, bool bwd, int K, int g, int grid, size_t smem) {
+    if (grid <= 0) return;
+    const int th = prop_fused_threads(K);
+    if (K == 2) {
+        if (bwd) k_prop_fused<true, 2><<<grid, th, smem, L.stream>>>(L.reps, L.tile2rep, g);
+        else k_prop_fused<false, 2><<<grid, th, smem, L.stream>>>(L.reps, L.tile2rep, g);
+    } else if (K == 3) {
+        if (bwd) k_prop_fused<true, 3><<<grid, th, smem, L.stream>>>(L.reps, L.tile2rep, g);
+        else k_prop_fused<false, 3><<<grid, th, smem, L.stream>>>(L.reps, L.tile2rep, g);
+    } else {
+        if (bwd) k_prop_fused<true, 4><<<grid, th, smem, L.stream>>>(L.reps, L.tile2rep, g);
+        else k_prop_fused<false, 4><<<grid, th, smem, L.stream>>>(L.reps, L.tile2rep, g);
+    }
+}
+int prop_fused_set_smem_limit(size_t bytes) {
+    cudaError_t e = cudaSuccess;
+    const int b = (int)bytes;
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_prop_fused<false, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_prop_fused<true, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_prop_fused<false, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_prop_fused<true, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_prop_fused<false, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_prop_fused<true, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+    return (int)e;
+}
+
+template <typename T>
+int prop_set_smem_limit(size_t bytes) {
+    cudaError_t e = cudaFuncSetAttribute(k_prop<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_prop<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    return (int)e;
+}
+size_t prop_smem_bytes(int vec, bool bwd, size_t es) { return prop_smem(vec, bwd, es); }
 template <typename T>
 void launch_exp(const Launch& L, int mode, int k, const void* Uext) {
     k_exp<T><<<L.nblk_total, kFlatThreads, 0, L.stream>>>(L.reps, L.blk2rep, mode, k, (const T*)Uext);
 }
 
-template void launch_prop_fwd<double>(const Launch&, int, int);
-template void launch_prop_fwd<float>(const Launch&, int, int);
-template void launch_prop_bwd<double>(const Launch&, int, int);
-template void launch_prop_bwd<float>(const Launch&, int, int);
+template void launch_prop_fwd<double>(const Launch&, int, int, size_t);
+template void launch_prop_fwd<float>(const Launch&, int, int, size_t);
+template void launch_prop_bwd<double>(const Launch&, int, int, size_t);
+template void launch_prop_bwd<float>(const Launch&, int, int, size_t);
+template int prop_set_smem_limit<double>(size_t);
+template int prop_set_smem_limit<float>(size_t);
 template void launch_exp<double>(const Launch&, int, int, const void*);
 template void launch_exp<float>(const Launch&, int, int, const void*);
 

@@ -75,18 +75,7 @@ extern "C" int dscf_densities_static(const dscf_params* p, int32_t precision, co
     std::memset(&R, 0, sizeof R);
     R.nx = p->nx; R.ny = p->ny; R.nz = p->nz; R.ns = p->ns; R.N = p->N; R.nA = p->nA;
     R.V = (long long)p->nx * p->ny * p->nz;
-    R.tiles_x = (p->nx + 31) / 32;
-    R.tiles_y = (p->ny + 7) / 8;
-    R.zc = p->nz >= 64 ? 16 : (p->nz < 4 ? p->nz : (p->nz / 4 > 4 ? p->nz / 4 : 4));
-    if (R.zc > p->nz) R.zc = p->nz;
-    R.tiles_z = (p->nz + R.zc - 1) / R.zc;
-    R.ntiles = R.tiles_x * R.tiles_y * R.tiles_z;
-    long long nb = (R.V + kFlatThreads - 1) / kFlatThreads;
-    if (nb > kMaxFlatBlocks) nb = kMaxFlatBlocks;
-    long long chunk = (R.V + nb - 1) / nb;
-    chunk = (chunk + kFlatThreads - 1) / kFlatThreads * kFlatThreads;
-    R.chunk = (int)chunk;
-    R.nblk = (int)((R.V + chunk - 1) / chunk);
+    tile_replica(R, 8);
     R.phi_p = p->phi_p;
     R.alpha = p->a * p->a / 6.0;
     R.part_stride = R.ntiles > R.nblk ? R.ntiles : R.nblk;
@@ -123,6 +112,13 @@ extern "C" int dscf_densities_static(const dscf_params* p, int32_t precision, co
                 return DSCF_ERR_CUDA;
             }
             g_scratch_dev[dev] = (unsigned char*)ptr;
+            // dynamic shared memory of the propagator kernels, for the largest layout
+            if (prop_set_smem_limit<double>(prop_smem_bytes(4, true, 8)) != 0 ||
+                prop_set_smem_limit<float>(prop_smem_bytes(4, true, 4)) != 0) {
+                g_scratch_dev[dev] = nullptr;
+                set_thread_error("dscf_densities_static: cudaFuncSetAttribute failed");
+                return DSCF_ERR_CUDA;
+            }
         }
         base = g_scratch_dev[dev];
     }
@@ -157,13 +153,13 @@ extern "C" int dscf_densities_static(const dscf_params* p, int32_t precision, co
     k_put_rep<<<1, 1, 0, s>>>((Rep*)(base + o_rep), R);
     if (precision == DSCF_FP64) {
         launch_exp<double>(L, 3, 0, U_in);
-        for (int k = 1; k <= R.N; ++k) launch_prop_fwd<double>(L, k, R.ntiles);
-        for (int j = 0; j < R.N; ++j) launch_prop_bwd<double>(L, j, R.ntiles);
+        for (int k = 1; k <= R.N; ++k) launch_prop_fwd<double>(L, k, R.ntiles, prop_smem_bytes(R.vec, false, 8));
+        for (int j = 0; j < R.N; ++j) launch_prop_bwd<double>(L, j, R.ntiles, prop_smem_bytes(R.vec, true, 8));
         launch_dens_out<double>(L, phi_out);
     } else {
         launch_exp<float>(L, 3, 0, U_in);
-        for (int k = 1; k <= R.N; ++k) launch_prop_fwd<float>(L, k, R.ntiles);
-        for (int j = 0; j < R.N; ++j) launch_prop_bwd<float>(L, j, R.ntiles);
+        for (int k = 1; k <= R.N; ++k) launch_prop_fwd<float>(L, k, R.ntiles, prop_smem_bytes(R.vec, false, 4));
+        for (int j = 0; j < R.N; ++j) launch_prop_bwd<float>(L, j, R.ntiles, prop_smem_bytes(R.vec, true, 4));
         launch_dens_out<float>(L, phi_out);
     }
     e = cudaGetLastError();

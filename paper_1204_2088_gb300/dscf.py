@@ -72,6 +72,7 @@ def load():
         "dscf_probe": (ctypes.c_int, [vp, i32]),
         "dscf_probe_ms": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_float)]),
         "dscf_densities_static": (ctypes.c_int, [P, i32, vp, vp, vp]),
+        "dscf_set_tuning": (ctypes.c_int, [vp, i32, i32]),
     }
     for name, (res, args) in sigs.items():
         fn = getattr(lib, name)
@@ -232,10 +233,14 @@ class Context:
         v = list(out)
         return {"mass": v[0:3], "mass_drift": v[3:6], "lb_mass": v[6], "lb_momentum": v[7:10],
                 "umax": v[10], "Q": v[11], "QS": v[12], "ncg_iters": int(v[13]), "gg_start": v[14],
-                "gmax_start": v[15], "gg_end": v[16], "gmax_end": v[17], "steps": int(v[18])}
+                "gmax_start": v[15], "gg_end": v[16], "gmax_end": v[17], "steps": int(v[18]),
+                "zc": int(v[19]), "kfuse": int(v[20])}
 
     def status(self):
         self._check(self.lib.dscf_status(self.h))
+
+    def set_tuning(self, zc, kfuse):
+        self._check(self.lib.dscf_set_tuning(self.h, int(zc), int(kfuse)))
 
     def probe(self, enable=True):
         self._check(self.lib.dscf_probe(self.h, 1 if enable else 0))

@@ -43,6 +43,9 @@ def solution(grid, N, nA, phi_p=0.3, **kw):
 
 DENSITY_CASES = [
     melt((8, 8, 8), 4, 2),
+    melt((32, 12, 10), 6, 3),          # whole-row layout, 1 site per lane
+    melt((64, 9, 7), 7, 2),            # whole-row layout, 2 sites per lane, ragged y
+    solution((128, 3, 5), 5, 2),       # whole-row layout, 4 sites per lane, solvent
     melt((40, 20, 36), 8, 3),          # several tiles in x, y and z, ragged in each
     solution((33, 17, 9), 7, 4),       # solvent, odd sizes
     melt((1, 3, 70), 5, 2),            # degenerate x, z chunking with a ragged tail
@@ -71,6 +74,45 @@ def test_densities_fp32_within_1e5(cfg):
     ctx = dscf.Context(cfg, dscf.FP32)
     got = t2n(ctx.densities(torch.from_numpy(U)))
     assert rel(got, ref) < 1e-5
+
+
+FUSED_CASES = [
+    (melt((32, 12, 10), 9, 4), 5),
+    (melt((64, 9, 21), 11, 3), 8),
+    (solution((128, 10, 6), 7, 5), 4),
+]
+
+
+@pytest.mark.parametrize("kfuse", [1, 2, 3, 4])
+@pytest.mark.parametrize("case", FUSED_CASES, ids=lambda c: "x".join(map(str, c[0]["grid"])) + f"_zc{c[1]}")
+def test_fused_contour_groups_fp32_within_1e5(case, kfuse):
+    """Every contour-fusion depth (including groups that straddle the A/B junction and short
+    last groups) gives the oracle's densities within the FP32 tolerance."""
+    cfg, zc = case
+    U = inputs.random_field(ncomp_shape(cfg), seed=9, scale=0.5)
+    ref, _, _ = oracle.densities(cfg, U)
+    ctx = dscf.Context(cfg, dscf.FP32)
+    ctx.set_tuning(zc, kfuse)
+    got = t2n(ctx.densities(torch.from_numpy(U)))
+    assert ctx.diagnostics()["kfuse"] == kfuse
+    assert rel(got, ref) < 1e-5
+
+
+def test_fused_step_fp32_matches_single_step():
+    cfg = melt((32, 16, 24), 10, 4, hydro=1, ncg_iters=2, cn_sweeps=4)
+    phi, U, dn = random_state(cfg, 81)
+    outs = []
+    for kfuse in (1, 3):
+        ctx = dscf.Context(cfg, dscf.FP32)
+        ctx.set_tuning(6, kfuse)
+        ctx.set(dscf.PHI, torch.from_numpy(phi).cuda())
+        ctx.set(dscf.U, torch.from_numpy(U).cuda())
+        ctx.set(dscf.POP, torch.from_numpy(dn).cuda())
+        ctx.step(2)
+        outs.append(t2n(ctx.get(dscf.PHI)))
+    o = run_oracle(cfg, phi, U, dn, 2)
+    assert rel(outs[1], outs[0]) < 1e-5
+    assert rel(outs[1], o["phi"]) < 1e-5
 
 
 def random_state(cfg, seed):
@@ -111,6 +153,7 @@ def run_oracle(cfg, phi, U, dn, steps):
 
 STEP_CASES = [
     melt((20, 12, 16), 6, 3, hydro=1, ncg_iters=3, cn_sweeps=4),
+    melt((64, 10, 12), 6, 3, hydro=1, ncg_iters=2, cn_sweeps=4),
     melt((20, 12, 16), 6, 3, hydro=0, ncg_iters=3, cn_sweeps=4),
     solution((18, 10, 34), 5, 2, hydro=1, ncg_iters=2, cn_sweeps=6),
     melt((36, 9, 10), 8, 5, hydro=1, ncg_iters=4, cn_sweeps=8, dt=0.4, tau_s=0.7, tau_b=1.4),
