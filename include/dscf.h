@@ -145,7 +145,8 @@ int dscf_set_fields(dscf_ctx* ctx, int32_t which, const void* src, int32_t on_ho
 
 /* FP64 diagnostics of one replica (synchronises).  out[0..23]:
  *  0..2  sum_r phi_I after the last step, 3..5 its drift before the mass correction,
- *  6 LB mass sum_r rho, 7..9 LB momentum after collision, 10 max |u_lat|,
+ *  6 LB mass sum_r rho, 7..9 LB momentum after the last collision, 10 max |u_lat|
+ *  (6..10 are reduced from the current populations and velocity when this is called),
  *  11 Q of the last gradient evaluation, 12 <exp(-U_S)>, 13 NCG iterations per step,
  *  14 <g,g> and 15 max|g| at the start of the last inversion, 16 <g,g> and 17 max|g|
  *  at its end, 18 steps done, 19 z-chunk of the propagator tiles and 20 contour steps fused

@@ -27,7 +27,7 @@ struct Layout {
     std::vector<int> fwd_grid;      // [s] for s = 1..Nmax (index s), tiles of replicas with N >= s
     std::vector<size_t> fwd_smem, bwd_smem;   // [s] dynamic shared memory of the contour launches
     size_t es = 8;
-    int ntiles = 0, nblk = 0, Nmax = 0;
+    int ntiles = 0, nblk = 0, nlb = 0, Nmax = 0;
     size_t bytes = 0;
     // offsets of the shared blocks
     size_t off_reps = 0, off_t2r = 0, off_b2r = 0, off_status = 0;
@@ -76,6 +76,11 @@ void assign_tiles(Layout& L, const dscf_params* p, int n) {
     L.blk2rep.clear();
     L.ntiles = 0;
     L.nblk = 0;
+    L.nlb = 0;
+    for (int r = 0; r < n; ++r) {
+        L.reps[r].lb_blk0 = L.nlb;
+        L.nlb += L.reps[r].lb_nblk;
+    }
     for (int k = 0; k < n; ++k) {
         Rep& R = L.reps[order[k]];
         R.tile0 = L.ntiles;
@@ -119,7 +124,7 @@ Layout make_layout(const dscf_params* p, int n, int prec, char* base) {
         const int max_tiles = R.ntiles;
         max_tiles_total += max_tiles;
         max_blk_total += R.nblk;
-        R.part_stride = std::max(max_tiles, R.nblk);
+        R.part_stride = std::max(std::max(max_tiles, R.nblk), R.lb_nblk);
         tile_replica(R, default_zc(q.nz));
         R.hydro = q.hydro;
         R.cn_sweeps = q.cn_sweeps;
@@ -236,6 +241,8 @@ Launch launch_of(dscf_ctx* c, cudaStream_t s) {
     L.status = c->d_status;
     L.counter = c->d_counter;
     L.nblk_total = c->L.nblk;
+    L.nlb_total = c->L.nlb;
+    L.nrep = c->nrep;
     L.stream = s;
     return L;
 }
@@ -603,6 +610,11 @@ int dscf_diagnostics(dscf_ctx* c, int32_t replica, double* out) {
     if (int rc = set_dev(c)) return rc;
     double s[kScalStride];
     const Rep& R = c->L.reps[replica];
+    {
+        const Launch L = launch_of(c, c->stream);
+        if (c->prec == DSCF_FP64) launch_lb_diag<double>(L); else launch_lb_diag<float>(L);
+        if (int rc = cuda_check(c, cudaGetLastError(), "LB diagnostics")) return rc;
+    }
     if (int rc = cuda_check(c, cudaMemcpyAsync(s, R.scal, sizeof s, cudaMemcpyDeviceToHost, c->stream), "diag")) return rc;
     if (int rc = cuda_check(c, cudaStreamSynchronize(c->stream), "diag sync")) return rc;
     const int K = c->params[0].ncg_iters;

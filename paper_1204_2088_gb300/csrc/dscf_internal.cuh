@@ -7,7 +7,7 @@
 namespace dscf {
 
 constexpr int kFlatThreads = 256;     // threads of every site-parallel ("flat") kernel
-constexpr int kMaxFlatBlocks = 1024;  // flat blocks per replica (= partial sums per replica)
+constexpr int kMaxFlatBlocks = 304;   // flat blocks per replica (= partial sums per replica)
 constexpr int kMaxNcg = 32;           // Fletcher-Reeves iterations per step, upper bound
 constexpr int kScalStride = 192;      // FP64 scalar slots per replica
 constexpr int kPropCols = 30;         // output x columns per propagator CTA (a warp minus 2 halo lanes)
@@ -53,6 +53,7 @@ struct Rep {
     int vec;                               // 1, 2, 4: whole-row layout with nx = 32 vec; 0: tiled
     int tile0, ntiles;
     int blk0, nblk, chunk;                 // flat tiling: nblk blocks of `chunk` sites
+    int lb_blk0, lb_nblk;                  // LB grid: one site per thread, lb_nblk blocks
     int hydro, cn_sweeps;
     double phi_p, kappa, alpha, dt, M, gs, gb, rho0, phi_floor;
     double chi[9];
@@ -95,6 +96,7 @@ inline void tile_replica(Rep& R, int zc) {
     chunk = (chunk + kFlatThreads - 1) / kFlatThreads * kFlatThreads;
     R.chunk = (int)chunk;
     R.nblk = (int)((R.V + chunk - 1) / chunk);
+    R.lb_nblk = (int)((R.V + kFlatThreads - 1) / kFlatThreads);
 }
 constexpr int kMinZc = 4;             // smallest z-chunk the autotuner tries (most tiles)
 
@@ -106,6 +108,8 @@ struct Launch {
     int* status;             // device status word
     int* counter;            // device step counter (selects the LB buffer parity)
     int nblk_total;          // flat blocks over all replicas
+    int nlb_total;           // LB blocks over all replicas
+    int nrep;
     cudaStream_t stream;
 };
 
@@ -211,5 +215,6 @@ template <typename T> void launch_dens_out(const Launch& L, void* phi_ext);
 template <typename T> void launch_pop_copy(const Launch& L, void* ext, int dir);  // 0 get, 1 set
 template <typename T> void launch_mass_init(const Launch& L, int nrep);
 void launch_step_end(const Launch& L);
+template <typename T> void launch_lb_diag(const Launch& L);
 
 }  // namespace dscf

@@ -12,9 +12,9 @@ namespace dscf {
 #define FLAT_PROLOGUE                                                   \
     const Rep& R = reps[blk2rep[blockIdx.x]];                           \
     const int lb = blockIdx.x - R.blk0;                                 \
-    const long long V = R.V;                                            \
-    const long long i0 = (long long)lb * R.chunk;                       \
-    const long long i1 = min(i0 + (long long)R.chunk, V);               \
+    const int V = (int)R.V;                                             \
+    const int i0 = lb * R.chunk;                                        \
+    const int i1 = min(i0 + R.chunk, V);                                \
     (void)i1;
 
 __device__ __forceinline__ int pslot_gg(int k) { return (k & 1) ? P_GG1 : P_GG0; }
@@ -34,10 +34,11 @@ __device__ __forceinline__ Norm norm_of(const Rep& R, double* sh) {
     n.phis = 1.0 - R.phi_p;
     return n;
 }
+// phi_I[U] at one site in the field precision (FP64 only in the normalisation constants).
 template <typename T>
-__device__ __forceinline__ double model_phi(const Rep& R, const Norm& n, int I, long long i) {
-    if (I < 2) return n.coef * (double)((const T*)R.q)[(long long)I * R.V + i];
-    return n.phis * (double)((const T*)R.E)[2 * R.V + i] / n.qs;
+__device__ __forceinline__ T model_phi(const Rep& R, const Norm& n, int I, int i) {
+    if (I < 2) return (T)n.coef * ((const T*)R.q)[(size_t)I * R.V + i];
+    return (T)n.phis * ((const T*)R.E)[2 * (size_t)R.V + i] / (T)n.qs;
 }
 
 // Directional derivative at the trial point: h1 = <phi* - phi[U + a1 d], d>.
@@ -48,13 +49,13 @@ __global__ void __launch_bounds__(kFlatThreads) k_trial(const Rep* __restrict__ 
     const Norm n = norm_of(R, sh);
     const T* phi = (const T*)R.phi;
     const T* d = (const T*)R.d;
-    double h1 = 0.0;
+    T h1 = T(0);
     for (int I = 0; I < R.ns; ++I)
-        for (long long i = i0 + threadIdx.x; i < i1; i += kFlatThreads) {
-            const long long o = (long long)I * V + i;
-            h1 += ((double)phi[o] - model_phi<T>(R, n, I, i)) * (double)d[o];
+        _Pragma("unroll 4") for (int i = i0 + threadIdx.x; i < i1; i += kFlatThreads) {
+            const size_t o = (size_t)I * V + i;
+            h1 += (phi[o] - model_phi<T>(R, n, I, i)) * d[o];
         }
-    const double t = block_sum(h1, sh);
+    const double t = block_sum((double)h1, sh);
     if (threadIdx.x == 0) slot(R, P_H1)[lb] = t;
 }
 
@@ -72,19 +73,19 @@ __global__ void __launch_bounds__(kFlatThreads) k_grad(const Rep* __restrict__ r
     }
     const T* phi = (const T*)R.phi;
     T* pm = (T*)R.phim;
-    double gg = 0.0, gmax = 0.0;
+    T gg = T(0), gmax = T(0);
     for (int I = 0; I < R.ns; ++I)
-        for (long long i = i0 + threadIdx.x; i < i1; i += kFlatThreads) {
-            const long long o = (long long)I * V + i;
-            const T m = (T)model_phi<T>(R, n, I, i);
+        _Pragma("unroll 4") for (int i = i0 + threadIdx.x; i < i1; i += kFlatThreads) {
+            const size_t o = (size_t)I * V + i;
+            const T m = model_phi<T>(R, n, I, i);
             pm[o] = m;
-            const double g = (double)phi[o] - (double)m;
+            const T g = phi[o] - m;
             gg += g * g;
             gmax = fmax(gmax, fabs(g));
         }
     if (k >= 0) {
-        const double t = block_sum(gg, sh);
-        const double tm = block_max(gmax, sh);
+        const double t = block_sum((double)gg, sh);
+        const double tm = block_max((double)gmax, sh);
         if (threadIdx.x == 0) {
             slot(R, pslot_gg(k + 1))[lb] = t;
             slot(R, P_GMAX)[lb] = tm;
@@ -117,28 +118,28 @@ __global__ void __launch_bounds__(kFlatThreads) k_dir(const Rep* __restrict__ re
     const T* phi = (const T*)R.phi;
     const T* pm = (const T*)R.phim;
     T* d = (T*)R.d;
-    double h0 = 0.0, cd = 0.0, gg = 0.0, gmax = 0.0;
+    const T tb = (T)beta;
+    T h0 = T(0), cd = T(0), gg = T(0), gmax = T(0);
     for (int I = 0; I < R.ns; ++I)
-        for (long long i = i0 + threadIdx.x; i < i1; i += kFlatThreads) {
-            const long long o = (long long)I * V + i;
-            const double g = (double)phi[o] - (double)pm[o];
-            const T dn = (mode == 0) ? (T)(-g) : (T)(-g + beta * (double)d[o]);
+        _Pragma("unroll 4") for (int i = i0 + threadIdx.x; i < i1; i += kFlatThreads) {
+            const size_t o = (size_t)I * V + i;
+            const T g = phi[o] - pm[o];
+            const T dn = (mode == 0) ? -g : -g + tb * d[o];
             d[o] = dn;
-            const double dd = (double)dn;
-            h0 += g * dd;
-            cd += dd * (double)pm[o] * dd;
+            h0 += g * dn;
+            cd += dn * pm[o] * dn;
             gg += g * g;
             gmax = fmax(gmax, fabs(g));
         }
-    const double th0 = block_sum(h0, sh);
-    const double tcd = block_sum(cd, sh);
+    const double th0 = block_sum((double)h0, sh);
+    const double tcd = block_sum((double)cd, sh);
     if (threadIdx.x == 0) {
         slot(R, P_H0)[lb] = th0;
         slot(R, P_CD)[lb] = tcd;
     }
     if (mode == 0) {
-        const double tg = block_sum(gg, sh);
-        const double tm = block_max(gmax, sh);
+        const double tg = block_sum((double)gg, sh);
+        const double tm = block_max((double)gmax, sh);
         if (threadIdx.x == 0) {
             slot(R, P_GG0)[lb] = tg;
             slot(R, P_GMAX)[lb] = tm;
@@ -185,7 +186,7 @@ __global__ void __launch_bounds__(kFlatThreads) k_mu(const Rep* __restrict__ rep
     const T* phi = (const T*)R.phi;
     const T* U = (const T*)R.U;
     T* mu = (T*)R.mu;
-    for (long long i = i0 + threadIdx.x; i < i1; i += kFlatThreads) {
+    _Pragma("unroll 4") for (int i = i0 + threadIdx.x; i < i1; i += kFlatThreads) {
         const int x = (int)(i % nx);
         const int y = (int)((i / nx) % ny);
         const int z = (int)(i / ((long long)nx * ny));
@@ -211,98 +212,106 @@ __constant__ signed char kC[19][3] = {
     {1, 1, 0}, {-1, -1, 0}, {1, -1, 0}, {-1, 1, 0}, {1, 0, 1}, {-1, 0, -1},
     {1, 0, -1}, {-1, 0, 1}, {0, 1, 1}, {0, -1, -1}, {0, 1, -1}, {0, -1, 1}};
 
+// Compile-time D3Q19 velocity components (same order as kC), so unrolled loops fold them.
+__host__ __device__ constexpr int lbc(int i, int a) {
+    constexpr signed char c[19][3] = {
+        {0, 0, 0}, {1, 0, 0}, {-1, 0, 0}, {0, 1, 0}, {0, -1, 0}, {0, 0, 1}, {0, 0, -1},
+        {1, 1, 0}, {-1, -1, 0}, {1, -1, 0}, {-1, 1, 0}, {1, 0, 1}, {-1, 0, -1},
+        {1, 0, -1}, {-1, 0, 1}, {0, 1, 1}, {0, -1, -1}, {0, 1, -1}, {0, -1, 1}};
+    return c[i][a];
+}
+
 template <typename T>
 __device__ __forceinline__ T lbw(int i) {
     return i == 0 ? T(1.0 / 3.0) : (i <= 6 ? T(1.0 / 18.0) : T(1.0 / 36.0));
 }
 
-// One collide-stream step at every site.  The stored state is the post-collision deviation
-// dn*_i(r) = n*_i(r) - w_i rho0 of the previous step; pulling dn*_i(r - c_i) performs the
-// streaming of Eq. 10, then the collision of Eq. 12-13 (noise amplitude phi_k = 0) with the
-// force term of Eq. 14 writes the new dn*_i(r) to the other buffer.
+// One collide-stream step at every site, one site per thread.  The stored state is the
+// post-collision deviation dn*_i(r) = n*_i(r) - w_i rho0 of the previous step; pulling
+// dn*_i(r - c_i) performs the streaming of Eq. 10, then the collision of Eq. 12-13 (noise
+// amplitude phi_k = 0) with the force term of Eq. 14 writes the new dn*_i(r) to the other buffer.
 //
 // Collision in closed form: modes 0-3 are conserved (gamma = 1) with m_0 = 0 and
 // m_{1..3} = -f/2 (the half-force velocity of Eq. 9), modes 10-18 have gamma = 0, so
 //   n*_i = n_i^eq + Df_i - 3/2 w_i f.c_i + w_i sum_{k=4..9} gamma_k m_k e_ki / b_k,
 // where m_4..m_9 are the Table 1 stress modes of the non-equilibrium second moment
 // Pi^neq = sum_i (n_i - n_i^eq) c_i c_i and Df_i is Eq. 14 (sum_k w_i m^f_k e_ki/b_k = Df_i).
+// The incoming populations only enter through their moments, so each outgoing population is
+// formed and stored on its own.
 template <typename T>
-__global__ void __launch_bounds__(kFlatThreads) k_lb(const Rep* __restrict__ reps, const int* __restrict__ blk2rep,
-                                                     const int* __restrict__ counter, const T* __restrict__ fext) {
+__global__ void __launch_bounds__(kFlatThreads, sizeof(T) == 4 ? 4 : 2) k_lb(const Rep* __restrict__ reps, int nrep,
+                                                        const int* __restrict__ counter, const T* __restrict__ fext) {
     __shared__ double sh[33];
-    FLAT_PROLOGUE
+    int r = 0;
+    while (r + 1 < nrep && (int)blockIdx.x >= reps[r + 1].lb_blk0) ++r;
+    const Rep& R = reps[r];
+    const int lbk = blockIdx.x - R.lb_blk0;
+    const int V = (int)R.V;
+    const int site = lbk * kFlatThreads + threadIdx.x;
+    const bool act = site < V;
     const int par = (*counter) & 1;
     const T* src = (const T*)(par ? R.pop1 : R.pop0);
     T* dst = (T*)(par ? R.pop0 : R.pop1);
     const int nx = R.nx, ny = R.ny, nz = R.nz, ns = R.ns;
     const T rho0 = (T)R.rho0, gs = (T)R.gs, gb = (T)R.gb, dt2 = (T)(R.dt * R.dt);
-    const T* phi = (const T*)R.phi;
-    const T* mu = (const T*)R.mu;
-    T* uo = (T*)R.u;
-    double srho = 0.0, sjx = 0.0, sjy = 0.0, sjz = 0.0, umax = 0.0;
-    for (long long r = i0 + threadIdx.x; r < i1; r += kFlatThreads) {
-        const int x = (int)(r % nx);
-        const int y = (int)((r / nx) % ny);
-        const int z = (int)(r / ((long long)nx * ny));
-        const int xm = x == 0 ? nx - 1 : x - 1, xp = x == nx - 1 ? 0 : x + 1;
-        const int ym = y == 0 ? ny - 1 : y - 1, yp = y == ny - 1 ? 0 : y + 1;
-        const int zm = z == 0 ? nz - 1 : z - 1, zp = z == nz - 1 ? 0 : z + 1;
-        const int X[3] = {xm, x, xp}, Y[3] = {ym, y, yp}, Z[3] = {zm, z, zp};
-        T dn[19];
+    if (act) {
+        const int x = site % nx;
+        const int yz = site / nx;
+        const int y = yz % ny;
+        const int z = yz / ny;
+        const int X[3] = {x == 0 ? nx - 1 : x - 1, x, x == nx - 1 ? 0 : x + 1};
+        const int Y[3] = {y == 0 ? ny - 1 : y - 1, y, y == ny - 1 ? 0 : y + 1};
+        const int Z[3] = {z == 0 ? nz - 1 : z - 1, z, z == nz - 1 ? 0 : z + 1};
+        // moments of the pulled populations dn*_i(r - c_i) (Eq. 9, deviation form)
+        T drho = 0, jx = 0, jy = 0, jz = 0, pxx = 0, pyy = 0, pzz = 0, pxy = 0, pxz = 0, pyz = 0;
 #pragma unroll
         for (int i = 0; i < 19; ++i) {
-            // upstream site r - c_i
-            const long long s = X[1 - kC[i][0]] + (long long)nx * (Y[1 - kC[i][1]] + (long long)ny * Z[1 - kC[i][2]]);
-            dn[i] = src[(long long)i * V + s];
+            const int cx = lbc(i, 0), cy = lbc(i, 1), cz = lbc(i, 2);
+            const int s = X[1 - cx] + nx * (Y[1 - cy] + ny * Z[1 - cz]);
+            const T d = src[(size_t)i * V + s];
+            drho += d;
+            if (cx) { jx += cx * d; pxx += d; }
+            if (cy) { jy += cy * d; pyy += d; }
+            if (cz) { jz += cz * d; pzz += d; }
+            if (cx && cy) pxy += (cx * cy) * d;
+            if (cx && cz) pxz += (cx * cz) * d;
+            if (cy && cz) pyz += (cy * cz) * d;
         }
         // body force (Eq. 8, central differences), in lattice units dt^2 f
         T fx = 0, fy = 0, fz = 0;
         if (fext) {
-            const long long b3 = 3 * R.vbase;
-            fx = fext[b3 + r];
-            fy = fext[b3 + V + r];
-            fz = fext[b3 + 2 * V + r];
+            const size_t b3 = 3 * (size_t)R.vbase;
+            fx = fext[b3 + site];
+            fy = fext[b3 + V + site];
+            fz = fext[b3 + 2 * (size_t)V + site];
         } else {
+            const T* phi = (const T*)R.phi;
+            const T* mu = (const T*)R.mu;
+            const int row = nx * (y + ny * z);
+            const int sxp = X[2] + row, sxm = X[0] + row;
+            const int syp = x + nx * (Y[2] + ny * z), sym = x + nx * (Y[0] + ny * z);
+            const int szp = x + nx * (y + ny * Z[2]), szm = x + nx * (y + ny * Z[0]);
             for (int I = 0; I < ns; ++I) {
-                const T* m = mu + (long long)I * V;
-                const T ph = phi[(long long)I * V + r];
-                const long long row = (long long)nx * (y + (long long)ny * z);
-                fx -= ph * T(0.5) * (m[row + xp] - m[row + xm]);
-                fy -= ph * T(0.5) * (m[x + (long long)nx * (yp + (long long)ny * z)] -
-                                     m[x + (long long)nx * (ym + (long long)ny * z)]);
-                fz -= ph * T(0.5) * (m[x + (long long)nx * (y + (long long)ny * zp)] -
-                                     m[x + (long long)nx * (y + (long long)ny * zm)]);
+                const T* m = mu + (size_t)I * V;
+                const T ph = phi[(size_t)I * V + site];
+                fx -= ph * T(0.5) * (m[sxp] - m[sxm]);
+                fy -= ph * T(0.5) * (m[syp] - m[sym]);
+                fz -= ph * T(0.5) * (m[szp] - m[szm]);
             }
             fx *= dt2;
             fy *= dt2;
             fz *= dt2;
-        }
-        // moments (Eq. 9)
-        T drho = 0, jx = 0, jy = 0, jz = 0, pxx = 0, pyy = 0, pzz = 0, pxy = 0, pxz = 0, pyz = 0;
-#pragma unroll
-        for (int i = 0; i < 19; ++i) {
-            const T cx = kC[i][0], cy = kC[i][1], cz = kC[i][2];
-            drho += dn[i];
-            jx += dn[i] * cx;
-            jy += dn[i] * cy;
-            jz += dn[i] * cz;
-            pxx += dn[i] * cx * cx;
-            pyy += dn[i] * cy * cy;
-            pzz += dn[i] * cz * cz;
-            pxy += dn[i] * cx * cy;
-            pxz += dn[i] * cx * cz;
-            pyz += dn[i] * cy * cz;
         }
         const T rho = rho0 + drho;
         jx += T(0.5) * fx;
         jy += T(0.5) * fy;
         jz += T(0.5) * fz;
         const T ux = jx / rho, uy = jy / rho, uz = jz / rho;
-        uo[r] = ux;
-        uo[V + r] = uy;
-        uo[2 * V + r] = uz;
+        T* uo = (T*)R.u;
+        uo[site] = ux;
+        uo[V + site] = uy;
+        uo[2 * (size_t)V + site] = uz;
         const T usq = ux * ux + uy * uy + uz * uz;
-        // non-equilibrium second moment: Pi - rho u u - rho/3 I with Pi = rho0/3 I + sum dn c c
         const T third = T(1.0 / 3.0);
         const T nxx = pxx - rho * ux * ux - drho * third;
         const T nyy = pyy - rho * uy * uy - drho * third;
@@ -326,7 +335,7 @@ __global__ void __launch_bounds__(kFlatThreads) k_lb(const Rep* __restrict__ rep
         const T trs3 = (sxx + syy + szz) * third;
 #pragma unroll
         for (int i = 0; i < 19; ++i) {
-            const T cx = kC[i][0], cy = kC[i][1], cz = kC[i][2];
+            const T cx = (T)lbc(i, 0), cy = (T)lbc(i, 1), cz = (T)lbc(i, 2);
             const T w = lbw<T>(i);
             const T c2 = cx * cx + cy * cy + cz * cz;
             const T uc = ux * cx + uy * cy + uz * cz;
@@ -337,22 +346,57 @@ __global__ void __launch_bounds__(kFlatThreads) k_lb(const Rep* __restrict__ rep
             const T df = T(3) * w * (fc + T(1.5) * (scc - trs3));
             const T rel = w * (r4 * (c2 - T(1)) + r5 * (cx * cx - cy * cy) + r6 * (c2 - T(3) * cz * cz) +
                                r7 * cx * cy + r8 * cx * cz + r9 * cy * cz);
-            dst[(long long)i * V + r] = dneq + df - T(1.5) * w * fc + rel;
+            dst[(size_t)i * V + site] = dneq + df - T(1.5) * w * fc + rel;
         }
-        srho += (double)rho;
-        sjx += (double)(jx + T(0.5) * fx);
-        sjy += (double)(jy + T(0.5) * fy);
-        sjz += (double)(jz + T(0.5) * fz);
-        umax = fmax(umax, fmax(fabs((double)ux), fmax(fabs((double)uy), fabs((double)uz))));
     }
-    const double a = block_sum(srho, sh), bx = block_sum(sjx, sh), by = block_sum(sjy, sh), bz = block_sum(sjz, sh);
-    const double bm = block_max(umax, sh);
+}
+
+// LB diagnostics on demand: mass sum_r rho and post-collision momentum sum_r sum_i n*_i c_i of
+// the stored populations, max |u_lat|; FP64 per-block partials (flat tiling).
+template <typename T>
+__global__ void __launch_bounds__(kFlatThreads) k_lb_diag(const Rep* __restrict__ reps, const int* __restrict__ blk2rep,
+                                                          const int* __restrict__ counter) {
+    __shared__ double sh[33];
+    FLAT_PROLOGUE
+    const T* cur = (const T*)(((*counter) & 1) ? R.pop1 : R.pop0);
+    const T* u = (const T*)R.u;
+    T sr = T(0), sx = T(0), sy = T(0), sz = T(0), um = T(0);
+    for (int i = i0 + threadIdx.x; i < i1; i += kFlatThreads) {
+#pragma unroll
+        for (int k = 0; k < 19; ++k) {
+            const T d = cur[(size_t)k * V + i];
+            sr += d;
+            sx += (T)lbc(k, 0) * d;
+            sy += (T)lbc(k, 1) * d;
+            sz += (T)lbc(k, 2) * d;
+        }
+        um = fmax(um, fmax(fabs(u[i]), fmax(fabs(u[(size_t)V + i]), fabs(u[2 * (size_t)V + i]))));
+    }
+    const double a = block_sum((double)sr, sh), bx = block_sum((double)sx, sh), by = block_sum((double)sy, sh),
+                 bz = block_sum((double)sz, sh), bm = block_max((double)um, sh);
     if (threadIdx.x == 0) {
         slot(R, P_RHO)[lb] = a;
         slot(R, P_JX)[lb] = bx;
         slot(R, P_JY)[lb] = by;
         slot(R, P_JZ)[lb] = bz;
         slot(R, P_UMAX)[lb] = bm;
+    }
+}
+__global__ void __launch_bounds__(kFlatThreads) k_lb_diag_fin(const Rep* __restrict__ reps, int* status) {
+    __shared__ double sh[33];
+    const Rep& R = reps[blockIdx.x];
+    const double a = reduce_parts(slot(R, P_RHO), R.nblk, sh);
+    const double bx = reduce_parts(slot(R, P_JX), R.nblk, sh);
+    const double by = reduce_parts(slot(R, P_JY), R.nblk, sh);
+    const double bz = reduce_parts(slot(R, P_JZ), R.nblk, sh);
+    const double bm = reduce_parts_max(slot(R, P_UMAX), R.nblk, sh);
+    if (threadIdx.x == 0) {
+        R.scal[S_RHO] = a + R.rho0 * (double)R.V;
+        R.scal[S_JX] = bx;
+        R.scal[S_JY] = by;
+        R.scal[S_JZ] = bz;
+        R.scal[S_UMAX] = bm;
+        if (!isfinite(a) || !isfinite(bm)) atomicOr(status, (int)ST_NONFINITE);
     }
 }
 
@@ -393,7 +437,7 @@ __global__ void __launch_bounds__(kFlatThreads) k_cd_rhs(const Rep* __restrict__
     T* rhs = (T*)R.rhs;
     const bool hyd = R.hydro != 0;
     const T dtM = (T)(R.dt * R.M);
-    for (long long i = i0 + threadIdx.x; i < i1; i += kFlatThreads) {
+    _Pragma("unroll 4") for (int i = i0 + threadIdx.x; i < i1; i += kFlatThreads) {
         const Nb b = neighbours(i, R.nx, R.ny, R.nz);
         for (int I = 0; I < R.ns; ++I) {
             const T* ph = phi + (long long)I * V;
@@ -433,44 +477,52 @@ __global__ void __launch_bounds__(kFlatThreads) k_cd_jacobi(const Rep* __restric
     const int ns = R.ns;
     const T c = (T)(0.5 * R.dt * R.M);
     const T kap = (T)R.kappa, fl = (T)R.phi_floor;
-    for (long long i = i0 + threadIdx.x; i < i1; i += kFlatThreads) {
+    for (int i = i0 + threadIdx.x; i < i1; i += kFlatThreads) {
         const Nb b = neighbours(i, R.nx, R.ny, R.nz);
-        T psi[3][6];
-        if (k == 0) {
-            for (int I = 0; I < 3; ++I)
-                for (int q = 0; q < 6; ++q) psi[I][q] = 0;
-        } else {
-            for (int q = 0; q < 6; ++q) {
-                T sd = 0;
-                for (int J = 0; J < ns; ++J) sd += dold[(long long)J * V + b.n[q]];
-                for (int I = 0; I < ns; ++I) {
-                    T ph = phi[(long long)I * V + b.n[q]];
-                    if (ph < fl) ph = fl;
-                    psi[I][q] = dold[(long long)I * V + b.n[q]] / ph + kap * sd;
+        T rh[3], D[3], A[3];
+#pragma unroll
+        for (int I = 0; I < 3; ++I) { rh[I] = T(0); D[I] = T(1); A[I] = T(0); }
+#pragma unroll
+        for (int q = 0; q < 6; ++q) {
+            const int nb = (int)b.n[q];
+            // psi at the neighbour from the previous iterate (zero before the first sweep)
+            T dl[3], sd = T(0);
+#pragma unroll
+            for (int J = 0; J < 3; ++J) {
+                dl[J] = (J < ns && k > 0) ? dold[(size_t)J * V + nb] : T(0);
+                sd += dl[J];
+            }
+#pragma unroll
+            for (int I = 0; I < 3; ++I) {
+                if (I < ns) {
+                    const T phn = phi[(size_t)I * V + nb];
+                    const T phc = phi[(size_t)I * V + i];
+                    const T ph = phn < fl ? fl : phn;
+                    const T psi = (k > 0) ? dl[I] / ph + kap * sd : T(0);
+                    const T pf = T(0.5) * (phc + phn);
+                    A[I] += pf;                  // accumulates the face sum w_I
+                    rh[I] += pf * psi;           // accumulates the off-diagonal term
                 }
             }
         }
-        T rh[3], D[3], A[3];
-        for (int I = 0; I < ns; ++I) {
-            const T* ph = phi + (long long)I * V;
-            T ws = 0, off = 0;
-            for (int q = 0; q < 6; ++q) {
-                const T pf = T(0.5) * (ph[i] + ph[b.n[q]]);
-                ws += pf;
-                off += pf * psi[I][q];
+        T num = T(0), den = T(1);
+#pragma unroll
+        for (int I = 0; I < 3; ++I) {
+            if (I < ns) {
+                const T ws = A[I];
+                const T phc0 = phi[(size_t)I * V + i];
+                const T phc = phc0 < fl ? fl : phc0;
+                rh[I] = rhs[(size_t)I * V + i] + c * rh[I];
+                D[I] = T(1) + c * ws / phc;
+                A[I] = c * kap * ws;
+                num += rh[I] / D[I];
+                den += A[I] / D[I];
             }
-            const T phc = ph[i] < fl ? fl : ph[i];
-            rh[I] = rhs[(long long)I * V + i] + c * off;
-            D[I] = T(1) + c * ws / phc;
-            A[I] = c * kap * ws;
-        }
-        T num = 0, den = 1;
-        for (int I = 0; I < ns; ++I) {
-            num += rh[I] / D[I];
-            den += A[I] / D[I];
         }
         const T s = num / den;
-        for (int I = 0; I < ns; ++I) dnew[(long long)I * V + i] = (rh[I] - A[I] * s) / D[I];
+#pragma unroll
+        for (int I = 0; I < 3; ++I)
+            if (I < ns) dnew[(size_t)I * V + i] = (rh[I] - A[I] * s) / D[I];
     }
 }
 
@@ -483,14 +535,14 @@ __global__ void __launch_bounds__(kFlatThreads) k_cd_finish(const Rep* __restric
     T* phi = (T*)R.phi;
     const T* del = (const T*)(((sweeps - 1) & 1) ? R.del1 : R.del0);
     for (int I = 0; I < R.ns; ++I) {
-        double acc = 0.0;
-        for (long long i = i0 + threadIdx.x; i < i1; i += kFlatThreads) {
-            const long long o = (long long)I * V + i;
+        T acc = T(0);
+        _Pragma("unroll 4") for (int i = i0 + threadIdx.x; i < i1; i += kFlatThreads) {
+            const size_t o = (size_t)I * V + i;
             const T v = phi[o] + del[o];
             phi[o] = v;
-            acc += (double)v;
+            acc += v;
         }
-        const double t = block_sum(acc, sh);
+        const double t = block_sum((double)acc, sh);
         if (threadIdx.x == 0) slot(R, P_MASS0 + I)[lb] = t;
     }
 }
@@ -511,22 +563,7 @@ __global__ void __launch_bounds__(kFlatThreads) k_mass_fix(const Rep* __restrict
             if (!isfinite(tot)) atomicOr(status, (int)ST_NONFINITE);
         }
         const T ts = (T)shift;
-        for (long long i = i0 + threadIdx.x; i < i1; i += kFlatThreads) phi[(long long)I * V + i] += ts;
-    }
-    if (lb == 0 && R.hydro) {
-        const double a = reduce_parts(slot(R, P_RHO), R.nblk, sh);
-        const double bx = reduce_parts(slot(R, P_JX), R.nblk, sh);
-        const double by = reduce_parts(slot(R, P_JY), R.nblk, sh);
-        const double bz = reduce_parts(slot(R, P_JZ), R.nblk, sh);
-        const double bm = reduce_parts_max(slot(R, P_UMAX), R.nblk, sh);
-        if (threadIdx.x == 0) {
-            R.scal[S_RHO] = a;
-            R.scal[S_JX] = bx;
-            R.scal[S_JY] = by;
-            R.scal[S_JZ] = bz;
-            R.scal[S_UMAX] = bm;
-            if (!isfinite(a) || !isfinite(bm)) atomicOr(status, (int)ST_NONFINITE);
-        }
+        _Pragma("unroll 4") for (int i = i0 + threadIdx.x; i < i1; i += kFlatThreads) phi[(long long)I * V + i] += ts;
     }
 }
 
@@ -538,8 +575,8 @@ __global__ void __launch_bounds__(kFlatThreads) k_dens_out(const Rep* __restrict
     FLAT_PROLOGUE
     const Norm n = norm_of(R, sh);
     for (int I = 0; I < R.ns; ++I)
-        for (long long i = i0 + threadIdx.x; i < i1; i += kFlatThreads)
-            out[R.ext_off + (long long)I * V + i] = (T)model_phi<T>(R, n, I, i);
+        _Pragma("unroll 4") for (int i = i0 + threadIdx.x; i < i1; i += kFlatThreads)
+            out[R.ext_off + (size_t)I * V + i] = model_phi<T>(R, n, I, i);
 }
 
 // Populations in / out: the API exchanges n_i(r) before collision, i.e. the stored
@@ -552,7 +589,7 @@ __global__ void __launch_bounds__(kFlatThreads) k_pop_copy(const Rep* __restrict
     T* cur = (T*)(((*counter) & 1) ? R.pop1 : R.pop0);
     const long long b19 = 19 * R.vbase;
     const int nx = R.nx, ny = R.ny, nz = R.nz;
-    for (long long r = i0 + threadIdx.x; r < i1; r += kFlatThreads) {
+    for (int r = i0 + threadIdx.x; r < i1; r += kFlatThreads) {
         const int x = (int)(r % nx);
         const int y = (int)((r / nx) % ny);
         const int z = (int)(r / ((long long)nx * ny));
@@ -577,9 +614,9 @@ __global__ void __launch_bounds__(kFlatThreads) k_mass_parts(const Rep* __restri
     FLAT_PROLOGUE
     const T* phi = (const T*)R.phi;
     for (int I = 0; I < R.ns; ++I) {
-        double acc = 0.0;
-        for (long long i = i0 + threadIdx.x; i < i1; i += kFlatThreads) acc += (double)phi[(long long)I * V + i];
-        const double t = block_sum(acc, sh);
+        T acc = T(0);
+        _Pragma("unroll 4") for (int i = i0 + threadIdx.x; i < i1; i += kFlatThreads) acc += phi[(size_t)I * V + i];
+        const double t = block_sum((double)acc, sh);
         if (threadIdx.x == 0) slot(R, P_MASS0 + I)[lb] = t;
     }
 }
@@ -618,7 +655,7 @@ void launch_mu(const Launch& L, int K) {
 }
 template <typename T>
 void launch_lb(const Launch& L, const void* fext) {
-    k_lb<T><<<L.nblk_total, kFlatThreads, 0, L.stream>>>(L.reps, L.blk2rep, L.counter, (const T*)fext);
+    k_lb<T><<<L.nlb_total, kFlatThreads, 0, L.stream>>>(L.reps, L.nrep, L.counter, (const T*)fext);
 }
 template <typename T>
 void launch_cd(const Launch& L, int sweeps) {
@@ -641,6 +678,11 @@ void launch_mass_init(const Launch& L, int nrep) {
     k_mass_commit<<<nrep, kFlatThreads, 0, L.stream>>>(const_cast<Rep*>(L.reps));
 }
 void launch_step_end(const Launch& L) { k_step_end<<<1, 1, 0, L.stream>>>(L.counter); }
+template <typename T>
+void launch_lb_diag(const Launch& L) {
+    k_lb_diag<T><<<L.nblk_total, kFlatThreads, 0, L.stream>>>(L.reps, L.blk2rep, L.counter);
+    k_lb_diag_fin<<<L.nrep, kFlatThreads, 0, L.stream>>>(L.reps, L.status);
+}
 
 #define INST(T)                                                        \
     template void launch_trial<T>(const Launch&);                      \
@@ -651,7 +693,8 @@ void launch_step_end(const Launch& L) { k_step_end<<<1, 1, 0, L.stream>>>(L.coun
     template void launch_cd<T>(const Launch&, int);                    \
     template void launch_dens_out<T>(const Launch&, void*);            \
     template void launch_pop_copy<T>(const Launch&, void*, int);       \
-    template void launch_mass_init<T>(const Launch&, int);
+    template void launch_mass_init<T>(const Launch&, int);                \
+    template void launch_lb_diag<T>(const Launch&);
 INST(double)
 INST(float)
 

@@ -142,6 +142,8 @@ extern "C" int dscf_densities_static(const dscf_params* p, int32_t precision, co
     L.status = nullptr;
     L.counter = nullptr;
     L.nblk_total = R.nblk;
+    L.nlb_total = R.lb_nblk;
+    L.nrep = 1;
     L.stream = s;
     // the only state that must start at zero: the tile and block maps (one replica, index 0)
     cudaError_t e = cudaMemsetAsync(base + o_t2r, 0, sizeof(int) * R.ntiles, s);
