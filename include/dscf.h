@@ -153,8 +153,9 @@ int dscf_set_fields(dscf_ctx* ctx, int32_t which, const void* src, int32_t on_ho
  *  per propagator launch, both chosen by the autotuner at dscf_init, 21..23 reserved (0). */
 int dscf_diagnostics(dscf_ctx* ctx, int32_t replica, double* out);
 
-/* Synchronise the stream and return the device status word as an error code (DSCF_OK or
- * DSCF_ERR_NUMERIC) or DSCF_ERR_CUDA if a kernel failed. */
+/* Synchronise the stream and return the device status word as an error code (DSCF_OK,
+ * DSCF_ERR_TIMEOUT if a persistent sweep gave up a bounded wait, DSCF_ERR_NUMERIC) or
+ * DSCF_ERR_CUDA if a kernel failed. */
 int dscf_status(dscf_ctx* ctx);
 
 /* Release host-side state (graph, capture stream).  The workspace stays the caller's. */
@@ -168,9 +169,10 @@ int64_t dscf_launches_per_step(const dscf_ctx* ctx);
 
 /* Override the autotuner's choice (for instance with a value cached from an earlier run):
  * zc = z planes per propagator tile (>= 1), kfuse = contour steps per propagator launch (1..4;
- * > 1 needs FP32 and nx in {32, 64, 128} for every replica, and kfuse <= N).  Synchronises the
- * stream; the next dscf_step re-captures its graph.  Results do not depend on either value
- * beyond rounding. */
+ * > 1 needs FP32 and nx in {32, 64, 128} for every replica, and kfuse <= N), or kfuse = 0 for
+ * persistent sweeps (one launch per sweep; one FP32 replica with nx = 128 and ny, nz multiples
+ * of 8, bricks co-resident one per SM).  Synchronises the stream; the next dscf_step re-captures
+ * its graph.  Results do not depend on either value beyond rounding. */
 int dscf_set_tuning(dscf_ctx* ctx, int32_t zc, int32_t kfuse);
 
 /* Timing probe.  enable != 0 makes the next dscf_step capture CUDA events (created by the

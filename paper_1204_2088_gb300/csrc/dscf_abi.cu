@@ -103,6 +103,7 @@ void assign_tiles(Layout& L, const dscf_params* p, int n) {
 }
 
 int default_zc(int nz) { return std::min(nz, 8); }
+constexpr int kPersSpinLimit = 1 << 22;   // polls (~64 ns sleep each) before a persistent sweep gives up
 
 // Tiling and workspace layout.  With base == nullptr only sizes are computed.  Tile maps and
 // partial-sum slots are sized for the smallest z-chunk the autotuner may choose, so re-tiling
@@ -174,7 +175,7 @@ Layout make_layout(const dscf_params* p, int n, int prec, char* base) {
     L.off_reps = off; take(sizeof(Rep) * n);
     L.off_t2r = off; take(sizeof(int) * max_tiles_total);
     L.off_b2r = off; take(sizeof(int) * max_blk_total);
-    L.off_status = off; take(sizeof(int) * 64);
+    L.off_status = off; take(sizeof(int) * (kFlagBase + kMaxBricks));
     L.bytes = off;
     return L;
 }
@@ -209,7 +210,9 @@ struct dscf_ctx {
     cudaEvent_t ev[6] = {};
     bool phim_stale = true;
     int zc = 0;
-    int kfuse = 1;          // contour steps per propagator launch (1 = single-step kernels)
+    int kfuse = 1;          // contour steps per propagator launch (1 = single-step kernels, 0 = persistent)
+    int pers_bz = 0;        // brick depth of the persistent sweeps (0 = not available)
+    int nsm = 0;
     bool fusable = false;   // FP32 and every replica in the whole-row layout
     long long steps = 0;
     int64_t launches = 0;
@@ -252,6 +255,13 @@ template <typename T>
 int64_t enqueue_sweeps(dscf_ctx* c, const Launch& L) {
     int64_t n = 0;
     const int K = c->kfuse;
+    if (K == 0) {
+        const int nb = pers_bricks(c->L.reps[0], c->pers_bz);
+        int* flags = c->d_status + kFlagBase;
+        launch_prop_pers(L, false, c->pers_bz, nb, flags, c->d_status + 2, kPersSpinLimit);
+        launch_prop_pers(L, true, c->pers_bz, nb, flags, c->d_status + 2, kPersSpinLimit);
+        return 2;
+    }
     if (K > 1) {
         int vmax = 0;
         for (const Rep& R : c->L.reps) vmax = std::max(vmax, R.vec);
@@ -403,9 +413,58 @@ int autotune_zc(dscf_ctx* c) {
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
     }
+    // persistent sweeps: one replica, FP32, whole 128-site rows; timed against the best above
+    c->pers_bz = 0;
+    if (c->nrep == 1 && c->prec == DSCF_FP32) {
+        for (int bz : {16, 8}) {
+            if (pers_supported(c->L.reps[0], bz, std::min(c->nsm, kMaxBricks))) { c->pers_bz = bz; break; }
+        }
+    }
+    if (c->pers_bz) {
+        if (int rc = cuda_check(c, (cudaError_t)pers_prepare(c->pers_bz), "persistent sweep set-up")) return rc;
+        if (Vtot >= 32 * 32 * 32 && c->L.reps[0].N >= 2) {
+            // per contour step of the best multi-launch configuration, measured on a forward sweep
+            auto sweep_ms = [&](int K, int zc) -> float {
+                c->kfuse = K;
+                set_zc(c, K == 0 ? c->pers_bz : zc);
+                if (upload_tiles(c)) return 1e30f;
+                const Launch L = launch_of(c, c->stream);
+                cudaEvent_t e0, e1;
+                cudaEventCreate(&e0);
+                cudaEventCreate(&e1);
+                auto run = [&]() {
+                    if (K == 0) {
+                        launch_prop_pers(L, false, c->pers_bz, pers_bricks(c->L.reps[0], c->pers_bz),
+                                         c->d_status + kFlagBase, c->d_status + 2, kPersSpinLimit);
+                    } else if (c->prec == DSCF_FP64) {
+                        enqueue_sweeps<double>(c, L);
+                    } else {
+                        enqueue_sweeps<float>(c, L);
+                    }
+                };
+                run();
+                cudaEventRecord(e0, c->stream);
+                run();
+                run();
+                cudaEventRecord(e1, c->stream);
+                float ms = 1e30f;
+                if (cudaEventSynchronize(e1) == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
+                cudaEventDestroy(e0);
+                cudaEventDestroy(e1);
+                if (cudaGetLastError() != cudaSuccess) return 1e30f;
+                return K == 0 ? ms / 2.0f : ms / 2.0f / 2.0f;   // forward sweep only vs forward + backward
+            };
+            const float tp = sweep_ms(0, 0);
+            const float tm = sweep_ms(bestK, best);
+            int st = 0;
+            cudaMemcpy(&st, c->d_status, sizeof(int), cudaMemcpyDeviceToHost);
+            if (st & ST_TIMEOUT) return fail(c, DSCF_ERR_TIMEOUT, "persistent sweep timed out during tuning");
+            if (tp < tm) bestK = 0;
+        }
+    }
     c->zc = best;
     c->kfuse = bestK;
-    set_zc(c, best);
+    set_zc(c, bestK == 0 ? c->pers_bz : best);
     return upload_tiles(c);
 }
 }  // namespace
@@ -442,6 +501,7 @@ int dscf_init(const dscf_params* p, int32_t n, int32_t precision, void* workspac
     }
     c->device = pa.device;
     if (int rc = set_dev(c)) { g_init_error = c->err; delete c; return rc; }
+    cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, c->device);
     c->L = make_layout(p, n, precision, c->ws);
     if (wbytes < c->L.bytes) {
         delete c;
@@ -458,7 +518,7 @@ int dscf_init(const dscf_params* p, int32_t n, int32_t precision, void* workspac
     rc = rc ? rc : chk(cudaMemcpyAsync(c->d_reps, c->L.reps.data(), sizeof(Rep) * n, cudaMemcpyHostToDevice, c->stream), "reps");
     rc = rc ? rc : chk(cudaMemcpyAsync(c->d_t2r, c->L.tile2rep.data(), sizeof(int) * c->L.ntiles, cudaMemcpyHostToDevice, c->stream), "t2r");
     rc = rc ? rc : chk(cudaMemcpyAsync(c->d_b2r, c->L.blk2rep.data(), sizeof(int) * c->L.nblk, cudaMemcpyHostToDevice, c->stream), "b2r");
-    rc = rc ? rc : chk(cudaMemsetAsync(c->d_status, 0, sizeof(int) * 64, c->stream), "status");
+    rc = rc ? rc : chk(cudaMemsetAsync(c->d_status, 0, sizeof(int) * (kFlagBase + kMaxBricks), c->stream), "status");
     const size_t es = precision == DSCF_FP64 ? 8 : 4;
     for (int r = 0; r < n && !rc; ++r) {
         const Rep& R = c->L.reps[r];
@@ -646,6 +706,7 @@ int dscf_status(dscf_ctx* c) {
     if (int rc = cuda_check(c, cudaGetLastError(), "status")) return rc;
     int st = 0;
     if (int rc = cuda_check(c, cudaMemcpy(&st, c->d_status, sizeof(int), cudaMemcpyDeviceToHost), "status read")) return rc;
+    if (st & ST_TIMEOUT) return fail(c, DSCF_ERR_TIMEOUT, "a persistent contour sweep gave up waiting for a neighbour");
     if (st & ST_NONFINITE) return fail(c, DSCF_ERR_NUMERIC, "non-finite value in a reduction");
     return DSCF_OK;
 }
@@ -683,8 +744,10 @@ int dscf_probe_ms(dscf_ctx* c, float* ms) {
 
 int dscf_set_tuning(dscf_ctx* c, int32_t zc, int32_t kfuse) {
     if (!c) return DSCF_ERR_ARG;
-    if (zc < 1 || kfuse < 1 || kfuse > 4) return fail(c, DSCF_ERR_ARG, "need zc >= 1 and 1 <= kfuse <= 4");
+    if (zc < 1 || kfuse < 0 || kfuse > 4) return fail(c, DSCF_ERR_ARG, "need zc >= 1 and 0 <= kfuse <= 4");
     if (kfuse > 1 && !c->fusable) return fail(c, DSCF_ERR_ARG, "contour fusion needs FP32 and nx in {32, 64, 128}");
+    if (kfuse == 0 && !c->pers_bz)
+        return fail(c, DSCF_ERR_ARG, "persistent sweeps need one FP32 replica with nx = 128, ny % 8 = 0, nz % 8 = 0");
     for (const Rep& R : c->L.reps)
         if (kfuse > R.N) return fail(c, DSCF_ERR_ARG, "kfuse exceeds a chain length");
     if (int rc = set_dev(c)) return rc;
@@ -695,7 +758,7 @@ int dscf_set_tuning(dscf_ctx* c, int32_t zc, int32_t kfuse) {
     }
     c->zc = zc;
     c->kfuse = kfuse;
-    set_zc(c, zc);
+    set_zc(c, kfuse == 0 ? c->pers_bz : zc);
     return upload_tiles(c);
 }
 

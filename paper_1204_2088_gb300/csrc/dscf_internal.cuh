@@ -42,7 +42,11 @@ enum ScalSlot {
 };
 
 // Device status bits.
-enum { ST_NONFINITE = 1 };
+enum { ST_NONFINITE = 1, ST_TIMEOUT = 2 };
+// Layout of the status block: [0] status word, [1] LB step counter, [2] abort flag of the
+// persistent sweeps, [kFlagBase..] one step counter per persistent brick.
+constexpr int kFlagBase = 64;
+constexpr int kMaxBricks = 1024;
 
 // One replica as the kernels see it.  Pointers are into the caller's workspace; their element
 // type is the context precision (double or float) except part/scal (double).
@@ -216,5 +220,11 @@ template <typename T> void launch_pop_copy(const Launch& L, void* ext, int dir);
 template <typename T> void launch_mass_init(const Launch& L, int nrep);
 void launch_step_end(const Launch& L);
 template <typename T> void launch_lb_diag(const Launch& L);
+// persistent contour sweeps (FP32, nx = 128, one replica)
+size_t pers_smem_bytes(int vec, int bz);
+bool pers_supported(const Rep& R, int bz, int nsm);
+int pers_bricks(const Rep& R, int bz);
+int pers_prepare(int bz);                                                                  // cudaError_t
+int launch_prop_pers(const Launch& L, bool bwd, int bz, int nbricks, int* flags, int* abortf, int limit);  // cudaError_t
 
 }  // namespace dscf

@@ -1,0 +1,317 @@
+// Persistent contour sweeps (Eq. 16-17) for one replica in the whole-row layout (FP32).
+//
+// One launch runs a whole forward (or backward) sweep of N contour steps.  The lattice is cut
+// into bricks of nx x 8 x BZ sites, one brick per CTA and at most one CTA per SM (the launch is
+// cooperative, so all CTAs are resident together).  A CTA keeps its brick's x-filtered
+// propagator in shared memory from one contour step to the next; per step it only reads the halo
+// rows and planes of its eight y/z neighbours from L2, after checking with an acquire load that
+// they have published that step.  Per step:
+//   halo rows of the previous step -> x pass -> shared XS (the brick's own rows are already there);
+//   barrier; each warp y-filters its row over its planes (plus one each side) into registers;
+//   barrier; z pass in registers -> sig;
+//   forward:  G_s = exp(-U_{I_s}) sig; brick-boundary values stored to the contour stack;
+//   backward: q_{I_s} += G_s sig in registers (G_s prefetched a step ahead with cp.async),
+//             G+_s = exp(-U_{I_s}) sig, boundary values stored to a ping-pong exchange buffer;
+//   barrier, fence, release store of the brick's step counter; then the forward interior stores
+//   and the x pass of the new values into XS.
+// q is accumulated in registers over a whole block of beads and written once; nothing is
+// read-modify-written per step.  Every wait is bounded: on timeout the CTA sets a status bit and a
+// global abort flag that makes every other CTA stop waiting, so the launch always finishes.
+#include "dscf_internal.cuh"
+
+namespace dscf {
+
+namespace {
+
+constexpr int PBY = 8;                 // brick rows
+constexpr int PWARPS = 16;             // warps per CTA
+constexpr int PTHREADS = 32 * PWARPS;
+
+__device__ __forceinline__ unsigned saddr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void cp16(void* s, const void* g) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(saddr(s)), "l"(g));
+}
+__device__ __forceinline__ void cpc() { asm volatile("cp.async.commit_group;\n" ::); }
+__device__ __forceinline__ void cpw0() { asm volatile("cp.async.wait_group 0;\n" ::); }
+__device__ __forceinline__ int ld_acquire(const int* p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];\n" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release(int* p, int v) {
+    asm volatile("st.release.gpu.global.s32 [%0], %1;\n" ::"l"(p), "r"(v) : "memory");
+}
+
+struct PersCtl {
+    int* flags;     // one step counter per brick
+    int* abort;     // set by a CTA that gave up waiting
+    int* status;    // device status word
+    int limit;      // polls before giving up
+};
+
+// Wait until every neighbour brick has published `target`; threads 0..7 poll one neighbour each.
+__device__ __forceinline__ void wait_nb(const PersCtl& c, const int* nb, int target, bool& aborted) {
+    if (threadIdx.x < 8 && !aborted) {
+        const int* f = c.flags + nb[threadIdx.x];
+        int spins = 0;
+        while (ld_acquire(f) < target) {
+            if (ld_acquire(c.abort) != 0) break;
+            if (++spins > c.limit) {
+                atomicOr(c.status, (int)ST_TIMEOUT);
+                atomicExch(c.abort, 1);
+                break;
+            }
+            __nanosleep(64);
+        }
+    }
+    __syncthreads();
+    if (!aborted && ld_acquire(c.abort) != 0) aborted = true;
+}
+
+template <int BZ>
+struct PersGeom {
+    static constexpr int NH = 2 * (BZ + 2) + 2 * PBY;   // halo rows per step
+    static constexpr int OWN = PBY * BZ / PWARPS;        // consecutive planes per warp (one row)
+};
+
+}  // namespace
+
+size_t pers_smem_bytes(int vec, int bz) {
+    const size_t W = 32 * (size_t)vec;
+    // XS (x-filtered level with halo) + halo staging + backward G_s of the brick
+    return ((size_t)(bz + 2) * (PBY + 2) * W + (size_t)(2 * (bz + 2) + 2 * PBY) * W + (size_t)bz * PBY * W) *
+           sizeof(float);
+}
+
+// Warp w owns row w % 8 and planes [OWN (w / 8), OWN (w / 8 + 1)) of the brick; it y-filters its
+// row over those planes plus one on each side straight into registers, so the z pass needs no
+// second shared buffer.  Brick-boundary values are stored and published first; the rest of the
+// forward G_s follows without a fence (the backward G+ interior is never stored: it stays in XS).
+template <int BZ, bool BWD>
+__global__ void __launch_bounds__(PTHREADS, 1) k_prop_pers(const Rep* __restrict__ reps, PersCtl ctl) {
+    constexpr int VEC = 4, W = 128;
+    using G = PersGeom<BZ>;
+    constexpr int OWN = G::OWN;
+    using VT = float4;
+    extern __shared__ __align__(16) unsigned char smem[];
+    float* XS = (float*)smem;                                  // [BZ+2][PBY+2][W]
+    float* HS = XS + (BZ + 2) * (PBY + 2) * W;                 // [NH][W]
+    float* GS = HS + G::NH * W;                                // [BZ][PBY][W] backward G_s
+    __shared__ double sh[33];
+    __shared__ int nbs[8];
+    const Rep& R = reps[0];
+    const int ny = R.ny, nz = R.nz, N = R.N, nA = R.nA;
+    const int plane = W * ny;
+    const size_t V = (size_t)R.V;
+    const int nby = ny / PBY, nbz = nz / BZ;
+    const int b = blockIdx.x;
+    const int by = b % nby, bz = b / nby;
+    const int y0 = by * PBY, z0 = bz * BZ;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int row = w % PBY, p0 = OWN * (w / PBY);
+    const float al = (float)R.alpha, be = (float)(1.0 - 2.0 * R.alpha);
+    if (threadIdx.x < 8) {
+        const int k = threadIdx.x < 4 ? threadIdx.x : threadIdx.x + 1;   // skip the centre
+        const int dy = k % 3 - 1, dz = k / 3 - 1;
+        nbs[threadIdx.x] = (by + dy + nby) % nby + nby * ((bz + dz + nbz) % nbz);
+    }
+    __shared__ int hoff[2 * (BZ + 2) + 2 * PBY];   // global row offsets of the halo rows (lane 0)
+    for (int h = threadIdx.x; h < G::NH; h += PTHREADS) {
+        int r, pl;
+        if (h < 2 * (BZ + 2)) { r = (h < BZ + 2) ? -1 : PBY; pl = h % (BZ + 2) - 1; }
+        else { const int h2 = h - 2 * (BZ + 2); pl = (h2 < PBY) ? -1 : BZ; r = h2 % PBY; }
+        const int y = (y0 + r + ny) % ny, z = (z0 + pl + nz) % nz;
+        hoff[h] = z * plane + y * W;
+    }
+    const int c0 = ctl.flags[b];       // step counters of all bricks are equal at launch
+    __syncthreads();
+    bool aborted = ld_acquire(ctl.abort) != 0;
+
+    auto xs = [&](int pl, int r) { return XS + ((pl + 1) * (PBY + 2) + (r + 1)) * W + VEC * lane; };
+    auto xpass = [&](VT v) -> VT {      // x pass of a periodic row held by the warp
+        const float lv = __shfl_sync(0xffffffffu, v.w, (lane + 31) & 31);
+        const float rv = __shfl_sync(0xffffffffu, v.x, (lane + 1) & 31);
+        VT o;
+        o.x = be * v.x + al * (lv + v.y);
+        o.y = be * v.y + al * (v.x + v.z);
+        o.z = be * v.z + al * (v.y + v.w);
+        o.w = be * v.w + al * (v.z + rv);
+        return o;
+    };
+    auto is_boundary = [&](int pl) { return row == 0 || row == PBY - 1 || pl == 0 || pl == BZ - 1; };
+    // own planes never wrap: offset of (row, p0 + k) is own0 + k * plane
+    const size_t own0 = (size_t)(z0 + p0) * plane + (size_t)(y0 + row) * W + VEC * lane;
+
+    VT e[OWN];
+    auto load_e = [&](int species) {
+        const float* E = (const float*)R.E + (size_t)species * V;
+#pragma unroll
+        for (int k = 0; k < OWN; ++k) e[k] = *(const VT*)(E + own0 + (size_t)k * plane);
+    };
+    auto prefetch_gs = [&](int s) {   // backward: G_s of this warp's pairs into GS
+        const float* Gs = (const float*)R.G + (size_t)(s - 1) * V;
+#pragma unroll
+        for (int k = 0; k < OWN; ++k) cp16(GS + ((p0 + k) * PBY + row) * W + VEC * lane, Gs + own0 + (size_t)k * plane);
+        cpc();
+    };
+
+    {   // the first input (G_0 = 1, or G+_{N+1} = 1): its x pass is be + 2 al everywhere
+        const float one = be + 2.0f * al;
+        for (int i = threadIdx.x; i < (BZ + 2) * (PBY + 2) * W; i += PTHREADS) XS[i] = one;
+    }
+    VT qacc[BWD ? OWN : 1];
+#pragma unroll
+    for (int k = 0; k < (BWD ? OWN : 1); ++k) qacc[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+    float qsum = 0.f;
+    int species = BWD ? (N <= nA ? 0 : 1) : (1 <= nA ? 0 : 1);
+    load_e(species);
+    if (BWD) prefetch_gs(N);
+    __syncthreads();
+
+    for (int j = 0; j < N; ++j) {
+        const int s = BWD ? N - j : j + 1;
+        const int sp = (s <= nA) ? 0 : 1;
+        if (sp != species) {
+            if (BWD) {   // leaving the B block: its quadrature is complete
+                float* q = (float*)R.q + (size_t)species * V;
+#pragma unroll
+                for (int k = 0; k < OWN; ++k) {
+                    *(VT*)(q + own0 + (size_t)k * plane) = qacc[k];
+                    qacc[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+            }
+            species = sp;
+            load_e(species);
+        }
+        // halo of the previous step
+        if (j > 0) {
+            wait_nb(ctl, nbs, c0 + j, aborted);
+            const float* src = BWD ? (const float*)(((j - 1) & 1) ? R.Gp1 : R.Gp0)
+                                   : (const float*)R.G + (size_t)(s - 2) * V;
+            for (int h = w; h < G::NH; h += PWARPS) cp16(HS + h * W + VEC * lane, src + hoff[h] + VEC * lane);
+            cpc();
+            cpw0();
+            for (int h = w; h < G::NH; h += PWARPS) {
+                int r, pl;
+                if (h < 2 * (BZ + 2)) { r = (h < BZ + 2) ? -1 : PBY; pl = h % (BZ + 2) - 1; }
+                else { const int h2 = h - 2 * (BZ + 2); pl = (h2 < PBY) ? -1 : BZ; r = h2 % PBY; }
+                *(VT*)xs(pl, r) = xpass(*(const VT*)(HS + h * W + VEC * lane));
+            }
+        } else if (BWD) {
+            cpw0();
+        }
+        __syncthreads();
+        // y pass of this warp's row over planes p0 - 1 .. p0 + OWN, into registers
+        VT yf[OWN + 2];
+#pragma unroll
+        for (int k = 0; k < OWN + 2; ++k) {
+            const int pl = p0 - 1 + k;
+            const VT a = *(const VT*)xs(pl, row - 1), c = *(const VT*)xs(pl, row), d = *(const VT*)xs(pl, row + 1);
+            yf[k].x = be * c.x + al * (a.x + d.x);
+            yf[k].y = be * c.y + al * (a.y + d.y);
+            yf[k].z = be * c.z + al * (a.z + d.z);
+            yf[k].w = be * c.w + al * (a.w + d.w);
+        }
+        __syncthreads();   // XS is rewritten below
+        // z pass and step output
+        float* dst = BWD ? (float*)((j & 1) ? R.Gp1 : R.Gp0) : (float*)R.G + (size_t)(s - 1) * V;
+        VT out[OWN];
+#pragma unroll
+        for (int k = 0; k < OWN; ++k) {
+            VT sg;
+            sg.x = be * yf[k + 1].x + al * (yf[k].x + yf[k + 2].x);
+            sg.y = be * yf[k + 1].y + al * (yf[k].y + yf[k + 2].y);
+            sg.z = be * yf[k + 1].z + al * (yf[k].z + yf[k + 2].z);
+            sg.w = be * yf[k + 1].w + al * (yf[k].w + yf[k + 2].w);
+            out[k].x = e[k].x * sg.x;
+            out[k].y = e[k].y * sg.y;
+            out[k].z = e[k].z * sg.z;
+            out[k].w = e[k].w * sg.w;
+            if (BWD) {
+                const VT g = *(const VT*)(GS + ((p0 + k) * PBY + row) * W + VEC * lane);
+                qacc[k].x += g.x * sg.x;
+                qacc[k].y += g.y * sg.y;
+                qacc[k].z += g.z * sg.z;
+                qacc[k].w += g.w * sg.w;
+            } else if (s == N) {
+                qsum += (out[k].x + out[k].y) + (out[k].z + out[k].w);
+            }
+            if (is_boundary(p0 + k) && (!BWD || s > 1)) *(VT*)(dst + own0 + (size_t)k * plane) = out[k];
+        }
+        if (BWD && s > 1) prefetch_gs(s - 1);   // GS slots of this thread were read above
+        // publish the boundary of this step
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            st_release(ctl.flags + b, c0 + j + 1);
+        }
+#pragma unroll
+        for (int k = 0; k < OWN; ++k) {
+            if (!BWD && !is_boundary(p0 + k)) *(VT*)(dst + own0 + (size_t)k * plane) = out[k];
+            *(VT*)xs(p0 + k, row) = xpass(out[k]);
+        }
+    }
+    if (BWD) {   // the A block ends at s = 1
+        float* q = (float*)R.q + (size_t)species * V;
+#pragma unroll
+        for (int k = 0; k < OWN; ++k) *(VT*)(q + own0 + (size_t)k * plane) = qacc[k];
+    } else {
+        const double t = block_sum((double)qsum, sh);
+        if (threadIdx.x == 0) slot(R, P_Q)[b] = t;
+        if (b == 0)
+            for (int i = threadIdx.x + gridDim.x; i < R.ntiles; i += PTHREADS) slot(R, P_Q)[i] = 0.0;
+    }
+}
+
+// Host side ---------------------------------------------------------------------------------
+
+bool pers_supported(const Rep& R, int bz, int nsm) {
+    if (R.nx != 128 || R.ny % PBY || R.nz % bz) return false;
+    const int nb = (R.ny / PBY) * (R.nz / bz);
+    return nb >= 1 && nb <= nsm && (PBY * bz) % PWARPS == 0;
+}
+
+int pers_bricks(const Rep& R, int bz) { return (R.ny / PBY) * (R.nz / bz); }
+
+int pers_prepare(int bz) {
+    const int sm = (int)pers_smem_bytes(4, bz);
+    cudaError_t e = cudaSuccess;
+    if (bz == 16) {
+        e = cudaFuncSetAttribute(k_prop_pers<16, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_prop_pers<16, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    } else if (bz == 8) {
+        e = cudaFuncSetAttribute(k_prop_pers<8, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_prop_pers<8, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    } else {
+        return (int)cudaErrorInvalidValue;
+    }
+    return (int)e;
+}
+
+int launch_prop_pers(const Launch& L, bool bwd, int bz, int nbricks, int* flags, int* abortf, int limit) {
+    PersCtl ctl;
+    ctl.flags = flags;
+    ctl.abort = abortf;
+    ctl.status = L.status;
+    ctl.limit = limit;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(nbricks);
+    cfg.blockDim = dim3(PTHREADS);
+    cfg.dynamicSmemBytes = pers_smem_bytes(4, bz);
+    cfg.stream = L.stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaError_t e;
+    if (bz == 16)
+        e = bwd ? cudaLaunchKernelEx(&cfg, k_prop_pers<16, true>, L.reps, ctl)
+                : cudaLaunchKernelEx(&cfg, k_prop_pers<16, false>, L.reps, ctl);
+    else
+        e = bwd ? cudaLaunchKernelEx(&cfg, k_prop_pers<8, true>, L.reps, ctl)
+                : cudaLaunchKernelEx(&cfg, k_prop_pers<8, false>, L.reps, ctl);
+    return (int)e;
+}
+
+}  // namespace dscf
