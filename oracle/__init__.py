@@ -69,6 +69,8 @@ def lib():
             "or_order_parameter": (ctypes.c_double, [P, D]),
             "or_segregation": (ctypes.c_double, [P, D]),
             "or_num_threads": (ctypes.c_int, []),
+            "or_conv3d": (None, [ctypes.c_int] * 6 + [D, D, D, D]),
+            "or_conv3d_bwd": (None, [ctypes.c_int] * 6 + [D, D, D, D, D, D]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(_lib, name)
@@ -249,3 +251,68 @@ def segregation(cfg: dict, phi: np.ndarray) -> float:
 
 def num_threads() -> int:
     return lib().or_num_threads()
+
+
+# ---------------------------------------------------------------------------------------------
+# Learned predictor: FP64 reference of the 3-layer circular 5^3 convolution network
+# (conv primitives in oracle.c, the composition below in numpy).
+# ---------------------------------------------------------------------------------------------
+NET_LAYERS = ((2, 32), (32, 32), (32, 2))
+
+
+def conv3d(grid, batch, W, b, x):
+    """x: [batch, cin, nz, ny, nx] -> [batch, cout, nz, ny, nx]."""
+    nx, ny, nz = grid
+    cout, cin = W.shape[0], W.shape[1]
+    x = _f64(x)
+    out = np.empty((batch, cout, nz, ny, nx))
+    lib().or_conv3d(nx, ny, nz, batch, cin, cout, _ptr(_f64(W)), _ptr(_f64(b)) if b is not None else None,
+                    _ptr(x), _ptr(out))
+    return out
+
+
+def conv3d_bwd(grid, batch, W, x, dout, want_din=True):
+    nx, ny, nz = grid
+    cout, cin = W.shape[0], W.shape[1]
+    dW = np.empty(W.shape)
+    db = np.empty(cout)
+    din = np.empty((batch, cin, nz, ny, nx)) if want_din else None
+    lib().or_conv3d_bwd(nx, ny, nz, batch, cin, cout, _ptr(_f64(W)), _ptr(_f64(x)), _ptr(_f64(dout)),
+                        _ptr(dW), _ptr(db), _ptr(din) if want_din else None)
+    return dW, db, din
+
+
+def net_input(U):
+    """U: [batch, 2, ...] -> per-sample, per-species mean-free potentials (the gauge-free input)."""
+    U = _f64(U)
+    return U - U.mean(axis=(2, 3, 4), keepdims=True)
+
+
+def net_forward(grid, params, U, phibar):
+    """phi_hat = phibar_I + y_I - <y_I>, y = conv3(tanh(conv2(tanh(conv1(U - <U>)))))."""
+    (W1, b1), (W2, b2), (W3, b3) = params
+    B = U.shape[0]
+    x = net_input(U)
+    h1 = np.tanh(conv3d(grid, B, W1, b1, x))
+    h2 = np.tanh(conv3d(grid, B, W2, b2, h1))
+    y = conv3d(grid, B, W3, b3, h2)
+    phi = y - y.mean(axis=(2, 3, 4), keepdims=True) + np.asarray(phibar, dtype=np.float64)[None, :, None, None, None]
+    return phi, (x, h1, h2)
+
+
+def net_loss_grad(grid, params, U, phi_target, phibar):
+    """Loss 0.5 * mean((phi_hat - phi*)^2) over all sites, species and samples, and its gradient."""
+    (W1, b1), (W2, b2), (W3, b3) = params
+    B = U.shape[0]
+    phi, (x, h1, h2) = net_forward(grid, params, U, phibar)
+    diff = phi - _f64(phi_target)
+    n = diff.size
+    loss = 0.5 * float((diff * diff).sum()) / n
+    g = diff / n
+    dy = g - g.mean(axis=(2, 3, 4), keepdims=True)            # through the mean removal
+    dW3, db3, dh2 = conv3d_bwd(grid, B, W3, h2, dy)
+    dz2 = dh2 * (1.0 - h2 * h2)
+    dW2, db2, dh1 = conv3d_bwd(grid, B, W2, h1, dz2)
+    dz1 = dh1 * (1.0 - h1 * h1)
+    dW1, db1, _ = conv3d_bwd(grid, B, W1, x, dz1, want_din=False)
+    return loss, ((dW1, db1), (dW2, db2), (dW3, db3))

@@ -636,3 +636,100 @@ int or_num_threads(void) {
     return 1;
 #endif
 }
+
+/* ------------------------------------------------------------------------------------ */
+/* Learned predictor (a small translation-invariant 3-D convolution network standing in  */
+/* for the density map phi[U]; not part of the paper, see the package for its use).       */
+/* Circular 3-D correlation with a 5^3 kernel centred on the site:                        */
+/*   out[co][r] = b[co] + sum_ci sum_{o in [-2,2]^3} W[co][ci][o] in[ci][r + o]           */
+/* W is [cout][cin][125] with offset index (oz+2)*25 + (oy+2)*5 + (ox+2); fields are     */
+/* [c][V] for each of `batch` samples (sample-major), each sample periodic on its own.    */
+/* ------------------------------------------------------------------------------------ */
+void or_conv3d(int nx, int ny, int nz, int batch, int cin, int cout, const double* W, const double* b,
+               const double* in, double* out) {
+    const int64_t V = (int64_t)nx * ny * nz;
+    for (int n = 0; n < batch; ++n) {
+        const double* inn = in + (int64_t)n * cin * V;
+        double* outn = out + (int64_t)n * cout * V;
+#pragma omp parallel for schedule(static)
+        for (int z = 0; z < nz; ++z)
+            for (int y = 0; y < ny; ++y)
+                for (int x = 0; x < nx; ++x) {
+                    const int64_t r = x + (int64_t)nx * (y + (int64_t)ny * z);
+                    for (int co = 0; co < cout; ++co) {
+                        double acc = b ? b[co] : 0.0;
+                        for (int ci = 0; ci < cin; ++ci)
+                            for (int oz = -2; oz <= 2; ++oz)
+                                for (int oy = -2; oy <= 2; ++oy)
+                                    for (int ox = -2; ox <= 2; ++ox) {
+                                        const int o = (oz + 2) * 25 + (oy + 2) * 5 + (ox + 2);
+                                        const int xs = ((x + ox) % nx + nx) % nx;
+                                        const int ys = ((y + oy) % ny + ny) % ny;
+                                        const int zs = ((z + oz) % nz + nz) % nz;
+                                        acc += W[((int64_t)co * cin + ci) * 125 + o] *
+                                               inn[(int64_t)ci * V + xs + (int64_t)nx * (ys + (int64_t)ny * zs)];
+                                    }
+                        outn[(int64_t)co * V + r] = acc;
+                    }
+                }
+    }
+}
+
+/* Gradients of or_conv3d for an upstream gradient dout: dW (summed over sites and samples),
+ * db, and din (NULL = not wanted):
+ *   dW[co][ci][o] = sum_n sum_r dout[co][r] in[ci][r + o],  db[co] = sum_n sum_r dout[co][r],
+ *   din[ci][r] = sum_co sum_o W[co][ci][o] dout[co][r - o]. */
+void or_conv3d_bwd(int nx, int ny, int nz, int batch, int cin, int cout, const double* W, const double* in,
+                   const double* dout, double* dW, double* db, double* din) {
+    const int64_t V = (int64_t)nx * ny * nz;
+    for (int64_t i = 0; i < (int64_t)cout * cin * 125; ++i) dW[i] = 0.0;
+    for (int co = 0; co < cout; ++co) db[co] = 0.0;
+    for (int n = 0; n < batch; ++n) {
+        const double* inn = in + (int64_t)n * cin * V;
+        const double* dn = dout + (int64_t)n * cout * V;
+        for (int co = 0; co < cout; ++co)
+            for (int64_t r = 0; r < V; ++r) db[co] += dn[(int64_t)co * V + r];
+#pragma omp parallel for schedule(static)
+        for (int co = 0; co < cout; ++co)
+            for (int ci = 0; ci < cin; ++ci)
+                for (int oz = -2; oz <= 2; ++oz)
+                    for (int oy = -2; oy <= 2; ++oy)
+                        for (int ox = -2; ox <= 2; ++ox) {
+                            const int o = (oz + 2) * 25 + (oy + 2) * 5 + (ox + 2);
+                            double acc = 0.0;
+                            for (int z = 0; z < nz; ++z)
+                                for (int y = 0; y < ny; ++y)
+                                    for (int x = 0; x < nx; ++x) {
+                                        const int xs = ((x + ox) % nx + nx) % nx;
+                                        const int ys = ((y + oy) % ny + ny) % ny;
+                                        const int zs = ((z + oz) % nz + nz) % nz;
+                                        acc += dn[(int64_t)co * V + x + (int64_t)nx * (y + (int64_t)ny * z)] *
+                                               inn[(int64_t)ci * V + xs + (int64_t)nx * (ys + (int64_t)ny * zs)];
+                                    }
+                            dW[((int64_t)co * cin + ci) * 125 + o] += acc;
+                        }
+        if (din) {
+            double* dinn = din + (int64_t)n * cin * V;
+#pragma omp parallel for schedule(static)
+            for (int z = 0; z < nz; ++z)
+                for (int y = 0; y < ny; ++y)
+                    for (int x = 0; x < nx; ++x) {
+                        for (int ci = 0; ci < cin; ++ci) {
+                            double acc = 0.0;
+                            for (int co = 0; co < cout; ++co)
+                                for (int oz = -2; oz <= 2; ++oz)
+                                    for (int oy = -2; oy <= 2; ++oy)
+                                        for (int ox = -2; ox <= 2; ++ox) {
+                                            const int o = (oz + 2) * 25 + (oy + 2) * 5 + (ox + 2);
+                                            const int xs = ((x - ox) % nx + nx) % nx;
+                                            const int ys = ((y - oy) % ny + ny) % ny;
+                                            const int zs = ((z - oz) % nz + nz) % nz;
+                                            acc += W[((int64_t)co * cin + ci) * 125 + o] *
+                                                   dn[(int64_t)co * V + xs + (int64_t)nx * (ys + (int64_t)ny * zs)];
+                                        }
+                            dinn[(int64_t)ci * V + x + (int64_t)nx * (y + (int64_t)ny * z)] = acc;
+                        }
+                    }
+        }
+    }
+}

@@ -558,3 +558,71 @@ def test_converged_crank_nicolson_conserves_mass_by_itself():
         drift[K] = np.abs(out.reshape(2, -1).sum(1) - m0).max()
     assert drift[400] < 1e-13
     assert drift[2] > 1e-6
+
+
+# ---------------------------------------------------------------------------------------------
+# Learned-predictor network reference (circular 5^3 convolutions)
+# ---------------------------------------------------------------------------------------------
+def test_conv3d_equals_fft_correlation():
+    grid = (6, 5, 7)
+    nx, ny, nz = grid
+    W = inputs.random_field((3, 2, 125), seed=101)
+    b = inputs.random_field((3,), seed=102)
+    x = inputs.random_field((2, 2, nz, ny, nx), seed=103)
+    out = oracle.conv3d(grid, 2, W, b, x)
+    # correlation theorem: out[co] = b + sum_ci ifft(fft(x_ci) * conj(fft(kernel_co_ci)))
+    for n in range(2):
+        for co in range(3):
+            acc = np.full((nz, ny, nx), b[co])
+            for ci in range(2):
+                k = np.zeros((nz, ny, nx))
+                for o in range(125):
+                    oz, oy, ox = o // 25 - 2, (o // 5) % 5 - 2, o % 5 - 2
+                    k[oz % nz, oy % ny, ox % nx] += W[co, ci, o]
+                acc += np.real(np.fft.ifftn(np.fft.fftn(x[n, ci]) * np.conj(np.fft.fftn(k))))
+            assert np.abs(out[n, co] - acc).max() < 1e-12
+
+
+def test_conv3d_backward_finite_differences():
+    grid = (5, 4, 6)
+    nx, ny, nz = grid
+    W = inputs.random_field((2, 3, 125), seed=111)
+    b = inputs.random_field((2,), seed=112)
+    x = inputs.random_field((1, 3, nz, ny, nx), seed=113)
+    dout = inputs.random_field((1, 2, nz, ny, nx), seed=114)
+    dW, db, din = oracle.conv3d_bwd(grid, 1, W, x, dout)
+    f = lambda W_, b_, x_: float((oracle.conv3d(grid, 1, W_, b_, x_) * dout).sum())
+    h = 1e-6
+    for idx in [(0, 0, 0), (1, 2, 62), (0, 1, 124)]:
+        Wp = W.copy(); Wp[idx] += h
+        Wm = W.copy(); Wm[idx] -= h
+        assert abs((f(Wp, b, x) - f(Wm, b, x)) / (2 * h) - dW[idx]) < 1e-7 * max(1.0, abs(dW[idx]))
+    bp = b.copy(); bp[1] += h
+    bm = b.copy(); bm[1] -= h
+    assert abs((f(W, bp, x) - f(W, bm, x)) / (2 * h) - db[1]) < 1e-7
+    for idx in [(0, 0, 0, 0, 0), (0, 2, 5, 3, 4), (0, 1, 2, 1, 3)]:
+        xp = x.copy(); xp[idx] += h
+        xm = x.copy(); xm[idx] -= h
+        assert abs((f(W, b, xp) - f(W, b, xm)) / (2 * h) - din[idx]) < 1e-7 * max(1.0, abs(din[idx]))
+
+
+def test_net_gradient_finite_differences():
+    """Whole-network gradient (mean removal, tanh layers) against central differences (1e-6 rel)."""
+    grid = (4, 4, 4)
+    rng = [inputs.random_field(s, seed=120 + i, scale=0.3) for i, s in
+           enumerate([(4, 2, 125), (4,), (4, 4, 125), (4,), (2, 4, 125), (2,)])]
+    params = [[rng[0], rng[1]], [rng[2], rng[3]], [rng[4], rng[5]]]
+    U = inputs.random_field((2, 2, 4, 4, 4), seed=130, scale=0.5)
+    tgt = 0.5 + 0.05 * inputs.random_field((2, 2, 4, 4, 4), seed=131)
+    phibar = [0.5, 0.5]
+    loss, grads = oracle.net_loss_grad(grid, params, U, tgt, phibar)
+    h = 1e-6
+    for (li, pi, idx) in [(0, 0, (1, 0, 17)), (1, 0, (2, 3, 99)), (2, 0, (1, 2, 60)), (0, 1, (3,)), (2, 1, (0,))]:
+        P = [[a.copy(), b_.copy()] for a, b_ in params]
+        P[li][pi][idx] += h
+        lp = oracle.net_loss_grad(grid, P, U, tgt, phibar)[0]
+        P[li][pi][idx] -= 2 * h
+        lm = oracle.net_loss_grad(grid, P, U, tgt, phibar)[0]
+        fd = (lp - lm) / (2 * h)
+        g = grads[li][pi][idx]
+        assert abs(fd - g) <= 1e-6 * max(abs(g), 1e-3 * abs(loss))
