@@ -211,6 +211,40 @@ int dscf_probe_ms(dscf_ctx* ctx, float* ms);
 int dscf_densities_static(const dscf_params* p, int32_t precision, const void* U_in, void* phi_out,
                           void* stream);
 
+/*
+ * Learned predictor of the density map (row "learned predictor" of this library; the paper has
+ * no such component).  A translation-invariant 3-D network maps the two potentials to the two
+ * densities of an A-B melt:
+ *   phi_hat_I = phibar_I + y_I - <y_I>,  y = conv3(tanh(conv2(tanh(conv1(U - <U>))))),
+ * with circular 5^3 convolutions 2 -> 32 -> 32 -> 2 channels (U - <U> and the output mean removal
+ * are per sample and per species, so the input is gauge-free and the output has the exact block
+ * masses).  All convolutions run on BF16 tensor cores with FP32 accumulation; FP32 master
+ * weights, Adam.  Parameters are one FP32 vector: W1[32][2][125], b1[32], W2[32][32][125], b2[32],
+ * W3[2][32][125], b3[2] (kernel offset index (oz+2)*25 + (oy+2)*5 + (ox+2)).
+ *
+ * A network context works on `batch` samples of an nx x ny x nz periodic grid (nx a multiple of
+ * 16); fields are [batch][2][V] float, device memory.  The workspace is caller-owned like the
+ * DSCF one.  phibar: host array of the two mean volume fractions.
+ */
+typedef struct dscf_net dscf_net;
+size_t dscf_net_workspace_bytes(int32_t nx, int32_t ny, int32_t nz, int32_t batch);
+int dscf_net_init(int32_t nx, int32_t ny, int32_t nz, int32_t batch, uint64_t seed, void* workspace,
+                  size_t workspace_bytes, void* stream, dscf_net** out);
+int dscf_net_forward(dscf_net* net, const float* U, const double* phibar, float* phi_out);
+/* Loss 0.5 mean((phi_hat - phi_target)^2) over all samples, species and sites (returned in *loss,
+ * synchronising, if loss != NULL) and its gradient (copied to grads_out if not NULL);
+ * phi_work receives phi_hat. */
+int dscf_net_gradient(dscf_net* net, const float* U, const float* phi_target, const double* phibar,
+                      float* phi_work, double* loss, float* grads_out);
+/* One Adam step (lr, beta1 = 0.9, beta2 = 0.999) on the gradient above. */
+int dscf_net_train_step(dscf_net* net, const float* U, const float* phi_target, const double* phibar,
+                        float* phi_work, float lr, double* loss);
+int dscf_net_get_params(dscf_net* net, float* dst);        /* dst: device or host */
+int dscf_net_set_params(dscf_net* net, const float* src);  /* resets the Adam moments */
+int64_t dscf_net_num_params(void);
+int dscf_net_free(dscf_net* net);
+const char* dscf_net_last_error(const dscf_net* net);
+
 #ifdef __cplusplus
 }
 #endif

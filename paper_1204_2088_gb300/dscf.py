@@ -73,6 +73,18 @@ def load():
         "dscf_probe_ms": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_float)]),
         "dscf_densities_static": (ctypes.c_int, [P, i32, vp, vp, vp]),
         "dscf_set_tuning": (ctypes.c_int, [vp, i32, i32]),
+        "dscf_net_workspace_bytes": (sz, [i32, i32, i32, i32]),
+        "dscf_net_init": (ctypes.c_int, [i32, i32, i32, i32, ctypes.c_uint64, vp, sz, vp, ctypes.POINTER(vp)]),
+        "dscf_net_forward": (ctypes.c_int, [vp, vp, ctypes.POINTER(ctypes.c_double), vp]),
+        "dscf_net_gradient": (ctypes.c_int, [vp, vp, vp, ctypes.POINTER(ctypes.c_double), vp,
+                                             ctypes.POINTER(ctypes.c_double), vp]),
+        "dscf_net_train_step": (ctypes.c_int, [vp, vp, vp, ctypes.POINTER(ctypes.c_double), vp, ctypes.c_float,
+                                               ctypes.POINTER(ctypes.c_double)]),
+        "dscf_net_get_params": (ctypes.c_int, [vp, vp]),
+        "dscf_net_set_params": (ctypes.c_int, [vp, vp]),
+        "dscf_net_num_params": (ctypes.c_int64, []),
+        "dscf_net_free": (ctypes.c_int, [vp]),
+        "dscf_net_last_error": (ctypes.c_char_p, [vp]),
     }
     for name, (res, args) in sigs.items():
         fn = getattr(lib, name)
@@ -264,3 +276,99 @@ class Context:
             self.close()
         except Exception:
             pass
+
+
+class Net:
+    """Learned density-map predictor (see include/dscf.h): batch x [2][nz][ny][nx] FP32 fields."""
+
+    def __init__(self, grid, batch=1, seed=1, device=None, stream=None):
+        self.lib = load()
+        self.grid = tuple(int(g) for g in grid)
+        self.batch = int(batch)
+        nx, ny, nz = self.grid
+        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        nbytes = self.lib.dscf_net_workspace_bytes(nx, ny, nz, self.batch)
+        if nbytes == 0:
+            raise DSCFError(-1, "network grid needs nx a multiple of 16")
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        h = ctypes.c_void_p()
+        rc = self.lib.dscf_net_init(nx, ny, nz, self.batch, seed, ctypes.c_void_p(self.workspace.data_ptr()), nbytes,
+                                    ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h))
+        if rc != DSCF_OK:
+            raise DSCFError(rc, self.lib.dscf_net_last_error(None).decode())
+        self.h = h
+        self.nparam = int(self.lib.dscf_net_num_params())
+        self.shape = (self.batch, 2, nz, ny, nx)
+        self._work = torch.empty(self.shape, dtype=torch.float32, device=self.device)
+
+    def _check(self, rc):
+        if rc != DSCF_OK:
+            raise DSCFError(rc, self.lib.dscf_net_last_error(self.h).decode())
+
+    def _f32(self, t):
+        t = torch.as_tensor(t).to(self.device, torch.float32).contiguous()
+        if t.numel() != int(np.prod(self.shape)):
+            raise ValueError("field shape does not match the network context")
+        return t
+
+    @staticmethod
+    def _pb(phibar):
+        return (ctypes.c_double * 2)(float(phibar[0]), float(phibar[1]))
+
+    def forward(self, U, phibar):
+        U = self._f32(U)
+        out = torch.empty(self.shape, dtype=torch.float32, device=self.device)
+        self._check(self.lib.dscf_net_forward(self.h, ctypes.c_void_p(U.data_ptr()), self._pb(phibar),
+                                              ctypes.c_void_p(out.data_ptr())))
+        return out
+
+    def gradient(self, U, target, phibar):
+        U, target = self._f32(U), self._f32(target)
+        g = torch.empty(self.nparam, dtype=torch.float32, device=self.device)
+        loss = ctypes.c_double()
+        self._check(self.lib.dscf_net_gradient(self.h, ctypes.c_void_p(U.data_ptr()), ctypes.c_void_p(target.data_ptr()),
+                                               self._pb(phibar), ctypes.c_void_p(self._work.data_ptr()),
+                                               ctypes.byref(loss), ctypes.c_void_p(g.data_ptr())))
+        return loss.value, g
+
+    def train_step(self, U, target, phibar, lr=1e-3, want_loss=False):
+        U, target = self._f32(U), self._f32(target)
+        loss = ctypes.c_double()
+        self._check(self.lib.dscf_net_train_step(self.h, ctypes.c_void_p(U.data_ptr()), ctypes.c_void_p(target.data_ptr()),
+                                                 self._pb(phibar), ctypes.c_void_p(self._work.data_ptr()), float(lr),
+                                                 ctypes.byref(loss) if want_loss else None))
+        self._keep = (U, target)
+        return loss.value if want_loss else None
+
+    def get_params(self):
+        p = torch.empty(self.nparam, dtype=torch.float32, device=self.device)
+        self._check(self.lib.dscf_net_get_params(self.h, ctypes.c_void_p(p.data_ptr())))
+        return p
+
+    def set_params(self, p):
+        p = torch.as_tensor(p).to(self.device, torch.float32).contiguous()
+        self._check(self.lib.dscf_net_set_params(self.h, ctypes.c_void_p(p.data_ptr())))
+        self._keep = p
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.dscf_net_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def net_params_split(p):
+    """FP32 parameter vector -> [(W1, b1), (W2, b2), (W3, b3)] numpy arrays."""
+    p = np.asarray(p, dtype=np.float64)
+    out, off = [], 0
+    for cin, cout in ((2, 32), (32, 32), (32, 2)):
+        n = cout * cin * 125
+        out.append([p[off:off + n].reshape(cout, cin, 125), p[off + n:off + n + cout]])
+        off += n + cout
+    return out
