@@ -150,7 +150,10 @@ int dscf_set_fields(dscf_ctx* ctx, int32_t which, const void* src, int32_t on_ho
  *  11 Q of the last gradient evaluation, 12 <exp(-U_S)>, 13 NCG iterations per step,
  *  14 <g,g> and 15 max|g| at the start of the last inversion, 16 <g,g> and 17 max|g|
  *  at its end, 18 steps done, 19 z-chunk of the propagator tiles and 20 contour steps fused
- *  per propagator launch, both chosen by the autotuner at dscf_init, 21..23 reserved (0). */
+ *  per propagator launch, both chosen by the autotuner at dscf_init, 21 steps taken with the
+ *  learned predictor and 22 exact steps since dscf_set_predictor, 23 the predictor's last
+ *  judged error (see dscf_set_predictor; -1 before the first judgement).  Slots 13, 16 and 17
+ *  follow the inversion of the last step taken (a predictor step may use fewer iterations). */
 int dscf_diagnostics(dscf_ctx* ctx, int32_t replica, double* out);
 
 /* Synchronise the stream and return the device status word as an error code (DSCF_OK,
@@ -243,6 +246,21 @@ int dscf_net_get_params(dscf_net* net, float* dst);        /* dst: device or hos
 int dscf_net_set_params(dscf_net* net, const float* src);  /* resets the Adam moments */
 int64_t dscf_net_num_params(void);
 int dscf_net_free(dscf_net* net);
+
+/* Use a trained network (same grid as the context, batch 1) as the density map inside the
+ * self-consistent inversion of dscf_step (the composition-to-potential solve of Eq. 6 with
+ * phi[U] of Eqs. 8-10 replaced by the network): one FP32 melt replica only.
+ * Every corrector_every-th step (counted from this call, starting with the first) is exact and
+ * judges the predictor (this synchronises): after a predictor step by that step's
+ * self-consistency error ||phi[U] - phi*||_inf (exact densities at the potential the predictor
+ * produced against the composition it inverted), otherwise by the network's own error
+ * max |phi_hat[U] - phi[U]| at the exactly inverted potential.  The steps in between use the
+ * predictor while the last judgement is <= tol and are exact otherwise (fallback).  ncg_iters is
+ * the number of inversion iterations of a predictor step (0: the context's own count); their
+ * secant steps are capped at the local-curvature step.  net NULL detaches.  The network context
+ * must outlive the attachment.  DSCF_ERR_ARG for an FP64 or batched context, a solvent system,
+ * another grid or batch, corrector_every < 1, tol <= 0 or ncg_iters outside 0..32. */
+int dscf_set_predictor(dscf_ctx* ctx, dscf_net* net, int32_t corrector_every, double tol, int32_t ncg_iters);
 const char* dscf_net_last_error(const dscf_net* net);
 
 #ifdef __cplusplus

@@ -210,6 +210,14 @@ struct dscf_ctx {
     cudaEvent_t ev[6] = {};
     bool phim_stale = true;
     int zc = 0;
+    // learned predictor (see dscf_set_predictor)
+    dscf_net* net = nullptr;
+    int pred_k = 10, pred_iters = 0;   // corrector period; inversion iterations of predictor steps
+    double pred_tol = 1e-3;
+    bool pred_ok = false, last_was_pred = false;
+    long long pred_counter = 0, n_pred = 0, n_exact = 0;
+    double pred_err = -1.0;
+    cudaGraphExec_t exec_pred = nullptr;
     int kfuse = 1;          // contour steps per propagator launch (1 = single-step kernels, 0 = persistent)
     int pers_bz = 0;        // brick depth of the persistent sweeps (0 = not available)
     int nsm = 0;
@@ -286,14 +294,34 @@ int64_t enqueue_eval(dscf_ctx* c, const Launch& L, int exp_mode, int k, const vo
 }
 
 // The launch sequence of one time step (see include/dscf.h, steps 1-4).
+// Learned-predictor evaluation at the potential the Boltzmann-factor kernel wrote into E:
+// q <- phi_hat[U'] (FP32 melts, one replica).
+void enqueue_net(dscf_ctx* c, const Launch& L) {
+    const Rep& R = c->L.reps[0];
+    const double f = (double)R.nA / R.N;
+    dscf_net_forward_on(c->net, L.stream, (const float*)R.E, R.phi_p * f, R.phi_p * (1.0 - f), (float*)R.q);
+}
+
 template <typename T>
-int64_t enqueue_step(dscf_ctx* c, const Launch& L) {
-    const int K = c->params[0].ncg_iters;
-    auto mark = [&](int i) { if (c->probe) cudaEventRecordWithFlags(c->ev[i], L.stream, cudaEventRecordExternal); };
+int64_t enqueue_step(dscf_ctx* c, const Launch& L, bool pred = false) {
+    const int K = pred ? c->pred_iters : c->params[0].ncg_iters;
+    auto mark = [&](int i) {
+        if (c->probe && !pred) cudaEventRecordWithFlags(c->ev[i], L.stream, cudaEventRecordExternal);
+    };
     int64_t n = 0;
     mark(4);
     if (K > 0) { launch_dir<T>(L, 0, 0); ++n; }
     for (int k = 0; k < K; ++k) {
+        if (pred) {   // both evaluations of the iteration through the learned predictor
+            launch_exp<T>(L, 1, k, nullptr, 1); ++n;
+            enqueue_net(c, L); n += 7;
+            launch_trial<T>(L, 1); ++n;
+            launch_exp<T>(L, 2, k, nullptr, 1); ++n;
+            enqueue_net(c, L); n += 7;
+            launch_grad<T>(L, k, 1); ++n;
+            if (k + 1 < K) { launch_dir<T>(L, 1, k); ++n; }
+            continue;
+        }
         launch_exp<T>(L, 1, k, nullptr); ++n;
         if (k == 0) mark(0);
         n += enqueue_sweeps<T>(c, L);
@@ -326,19 +354,48 @@ int refresh_phim(dscf_ctx* c) {
 }
 
 template <typename T>
-int build_graph(dscf_ctx* c) {
+int build_graph(dscf_ctx* c, bool pred = false) {
     cudaGraph_t g = nullptr;
     int rc = cuda_check(c, cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal), "begin capture");
     if (rc) return rc;
     const Launch L = launch_of(c, c->cap);
-    c->launches = enqueue_step<T>(c, L);
+    const int64_t n = enqueue_step<T>(c, L, pred);
+    if (!pred) c->launches = n;
     cudaError_t le = cudaGetLastError();
     cudaError_t ee = cudaStreamEndCapture(c->cap, &g);
     if (le != cudaSuccess) { if (g) cudaGraphDestroy(g); return cuda_check(c, le, "kernel launch during capture"); }
     if (ee != cudaSuccess) return cuda_check(c, ee, "end capture");
-    cudaError_t ie = cudaGraphInstantiate(&c->exec, g, 0);
+    cudaError_t ie = cudaGraphInstantiate(pred ? &c->exec_pred : &c->exec, g, 0);
     cudaGraphDestroy(g);
     return cuda_check(c, ie, "graph instantiate");
+}
+
+// Judgement of the learned predictor at a corrector step (an exact step just run).
+// After a predictor step the error is that step's self-consistency error ||phi[U] - phi*||_inf:
+// the exact density at the potential the predictor-driven inversion produced against the
+// composition it was inverted for, which the corrector's own inversion measures as its starting
+// residual (it also holds the composition change of one step, ~1e-5).  Otherwise (first judgement,
+// or after a fallback) the network's own error max |phi_hat[U] - phi[U]| at the exactly inverted
+// potential stands in for it (the inversion error it causes is observed to be at most of that
+// size).  A non-finite error fails.
+int check_predictor(dscf_ctx* c, bool after_pred) {
+    const Launch L = launch_of(c, c->stream);
+    launch_exp<float>(L, 0, 0, nullptr, 1);
+    enqueue_net(c, L);
+    launch_pred_err(L);
+    double s0[2] = {0.0, 0.0}, e = 0.0;
+    const double* scal = c->L.reps[0].scal;
+    int rc = cuda_check(c, cudaGetLastError(), "predictor check");
+    if (!rc) rc = cuda_check(c, cudaMemcpyAsync(s0, scal + S_GG0, 2 * sizeof(double), cudaMemcpyDeviceToHost,
+                                                c->stream), "inversion residual");
+    if (!rc) rc = cuda_check(c, cudaMemcpyAsync(&e, scal + S_PERR, sizeof(double), cudaMemcpyDeviceToHost,
+                                                c->stream), "predictor error");
+    if (!rc) rc = cuda_check(c, cudaStreamSynchronize(c->stream), "predictor sync");
+    if (rc) return rc;
+    if (after_pred) e = std::isfinite(s0[0]) ? s0[1] : INFINITY;
+    c->pred_err = e;
+    c->pred_ok = std::isfinite(e) && e <= c->pred_tol;
+    return DSCF_OK;
 }
 
 int set_dev(dscf_ctx* c) { return cuda_check(c, cudaSetDevice(c->device), "cudaSetDevice"); }
@@ -570,10 +627,41 @@ int dscf_step(dscf_ctx* c, int32_t n_steps) {
         int rc = c->prec == DSCF_FP64 ? build_graph<double>(c) : build_graph<float>(c);
         if (rc) return rc;
     }
-    for (int i = 0; i < n_steps; ++i) {
-        if (int rc = cuda_check(c, cudaGraphLaunch(c->exec, c->stream), "graph launch")) return rc;
+    if (!c->net) {
+        for (int i = 0; i < n_steps; ++i) {
+            if (int rc = cuda_check(c, cudaGraphLaunch(c->exec, c->stream), "graph launch")) return rc;
+        }
+        c->steps += n_steps;
+        if (n_steps > 0 && c->probe) c->probe_ran = true;
+        return DSCF_OK;
     }
-    c->steps += n_steps;
+    // learned predictor: every pred_k-th step is exact and judges the predictor; in between the
+    // predictor is used while its last judgement was within tolerance, else the step is exact
+    if (!c->exec_pred) {
+        if (int rc = build_graph<float>(c, true)) return rc;
+    }
+    for (int i = 0; i < n_steps; ++i) {
+        const bool check = (c->pred_counter % c->pred_k) == 0;
+        const bool use_pred = !check && c->pred_ok;
+        if (use_pred) {
+            if (int rc = cuda_check(c, cudaGraphLaunch(c->exec_pred, c->stream), "predictor graph launch")) return rc;
+            c->last_was_pred = true;
+            ++c->n_pred;
+        } else {
+            const bool after_pred = c->last_was_pred;
+            if (after_pred) {   // the exact inversion starts from the exact phi[U]
+                if (int rc = refresh_phim<float>(c)) return rc;
+            }
+            if (int rc = cuda_check(c, cudaGraphLaunch(c->exec, c->stream), "graph launch")) return rc;
+            c->last_was_pred = false;
+            ++c->n_exact;
+            if (check) {
+                if (int rc = check_predictor(c, after_pred)) return rc;
+            }
+        }
+        ++c->pred_counter;
+        ++c->steps;
+    }
     if (n_steps > 0 && c->probe) c->probe_ran = true;
     return DSCF_OK;
 }
@@ -677,7 +765,7 @@ int dscf_diagnostics(dscf_ctx* c, int32_t replica, double* out) {
     }
     if (int rc = cuda_check(c, cudaMemcpyAsync(s, R.scal, sizeof s, cudaMemcpyDeviceToHost, c->stream), "diag")) return rc;
     if (int rc = cuda_check(c, cudaStreamSynchronize(c->stream), "diag sync")) return rc;
-    const int K = c->params[0].ncg_iters;
+    const int K = c->last_was_pred ? c->pred_iters : c->params[0].ncg_iters;
     std::memset(out, 0, sizeof(double) * 24);
     for (int I = 0; I < 3; ++I) {
         out[I] = s[S_MASS0 + I];
@@ -696,6 +784,9 @@ int dscf_diagnostics(dscf_ctx* c, int32_t replica, double* out) {
     out[18] = (double)c->steps;
     out[19] = (double)c->zc;
     out[20] = (double)c->kfuse;
+    out[21] = (double)c->n_pred;
+    out[22] = (double)c->n_exact;
+    out[23] = c->pred_err;
     return DSCF_OK;
 }
 
@@ -742,6 +833,37 @@ int dscf_probe_ms(dscf_ctx* c, float* ms) {
     return cuda_check(c, cudaEventElapsedTime(&ms[2], c->ev[4], c->ev[5]), "probe step");
 }
 
+int dscf_set_predictor(dscf_ctx* c, dscf_net* net, int32_t corrector_every, double tol, int32_t ncg_iters) {
+    if (!c) return DSCF_ERR_ARG;
+    if (int rc = set_dev(c)) return rc;
+    if (int rc = cuda_check(c, cudaStreamSynchronize(c->stream), "predictor sync")) return rc;
+    if (c->exec_pred) {
+        cudaGraphExecDestroy(c->exec_pred);
+        c->exec_pred = nullptr;
+    }
+    if (!net) {
+        if (c->last_was_pred) c->phim_stale = true;
+        c->net = nullptr;
+        return DSCF_OK;
+    }
+    const Rep& R = c->L.reps[0];
+    if (c->prec != DSCF_FP32 || c->nrep != 1 || R.ns != 2)
+        return fail(c, DSCF_ERR_ARG, "the learned predictor needs one FP32 melt replica");
+    if (!dscf_net_fits(net, R.nx, R.ny, R.nz))
+        return fail(c, DSCF_ERR_ARG, "the network context must have this grid and batch 1");
+    if (corrector_every < 1 || !(tol > 0.0)) return fail(c, DSCF_ERR_ARG, "need corrector_every >= 1 and tol > 0");
+    if (ncg_iters < 0 || ncg_iters > kMaxNcg) return fail(c, DSCF_ERR_ARG, "predictor inversion iterations out of range");
+    c->net = net;
+    c->pred_iters = ncg_iters > 0 ? ncg_iters : c->params[0].ncg_iters;
+    c->pred_k = corrector_every;
+    c->pred_tol = tol;
+    c->pred_ok = false;
+    c->pred_counter = 0;
+    c->n_pred = c->n_exact = 0;
+    c->pred_err = -1.0;
+    return DSCF_OK;
+}
+
 int dscf_set_tuning(dscf_ctx* c, int32_t zc, int32_t kfuse) {
     if (!c) return DSCF_ERR_ARG;
     if (zc < 1 || kfuse < 0 || kfuse > 4) return fail(c, DSCF_ERR_ARG, "need zc >= 1 and 0 <= kfuse <= 4");
@@ -756,6 +878,10 @@ int dscf_set_tuning(dscf_ctx* c, int32_t zc, int32_t kfuse) {
         cudaGraphExecDestroy(c->exec);
         c->exec = nullptr;
     }
+    if (c->exec_pred) {
+        cudaGraphExecDestroy(c->exec_pred);
+        c->exec_pred = nullptr;
+    }
     c->zc = zc;
     c->kfuse = kfuse;
     set_zc(c, kfuse == 0 ? c->pers_bz : zc);
@@ -768,6 +894,7 @@ int dscf_free(dscf_ctx* c) {
     for (int i = 0; i < 6; ++i)
         if (c->ev[i]) cudaEventDestroy(c->ev[i]);
     if (c->exec) cudaGraphExecDestroy(c->exec);
+    if (c->exec_pred) cudaGraphExecDestroy(c->exec_pred);
     if (c->cap) cudaStreamDestroy(c->cap);
     delete c;
     return DSCF_OK;

@@ -38,7 +38,7 @@ enum ScalSlot {
     S_GG0 = 0, S_GMAX0 = 1,      // start of the inversion
     S_ITER0 = 2,                 // per iteration k: a1, a, gg, gmax at S_ITER0 + 4k + {0..3}
     S_Q = 160, S_QS, S_DRIFT0, S_DRIFT1, S_DRIFT2, S_MASS0, S_MASS1, S_MASS2,
-    S_RHO, S_JX, S_JY, S_JZ, S_UMAX
+    S_RHO, S_JX, S_JY, S_JZ, S_UMAX, S_PERR
 };
 
 // Device status bits.
@@ -207,9 +207,11 @@ size_t prop_fused_smem_bytes(int vec, int K);
 void launch_prop_fused(const Launch& L, bool bwd, int K, int g, int grid, size_t smem);
 int prop_fused_set_smem_limit(size_t bytes);                    // returns a cudaError_t
 // mode: 0 exp(-U), 1 trial exp(-(U + a1 d)), 2 commit U += a d then exp(-U), 3 exp(-Uext)
-template <typename T> void launch_exp(const Launch& L, int mode, int k, const void* Uext);
-template <typename T> void launch_trial(const Launch& L);
-template <typename T> void launch_grad(const Launch& L, int k);
+template <typename T> void launch_exp(const Launch& L, int mode, int k, const void* Uext, int write_u = 0);
+// net != 0: the density at the evaluated potential is the learned predictor's output, stored in q
+template <typename T> void launch_trial(const Launch& L, int net = 0);
+template <typename T> void launch_grad(const Launch& L, int k, int net = 0);
+void launch_pred_err(const Launch& L);   // max |q - phi_m| of replica 0 into scal[S_PERR] (FP32 melts)
 // mode 0: init (d = -g), mode 1: iteration k direction update
 template <typename T> void launch_dir(const Launch& L, int mode, int k);
 template <typename T> void launch_mu(const Launch& L, int K);
@@ -228,3 +230,8 @@ int pers_prepare(int bz);                                                       
 int launch_prop_pers(const Launch& L, bool bwd, int bz, int nbricks, int* flags, int* abortf, int limit);  // cudaError_t
 
 }  // namespace dscf
+
+// learned predictor (dscf_net.cu): forward pass on a given stream, for use inside the step graph
+struct dscf_net;
+bool dscf_net_fits(const dscf_net* net, int nx, int ny, int nz);
+void dscf_net_forward_on(dscf_net* net, cudaStream_t stream, const float* U, double pb0, double pb1, float* phi);

@@ -26,8 +26,14 @@ __device__ __forceinline__ int pslot_gg(int k) { return (k & 1) ? P_GG1 : P_GG0;
 struct Norm {
     double coef, qs, phis;
 };
-__device__ __forceinline__ Norm norm_of(const Rep& R, double* sh) {
+__device__ __forceinline__ Norm norm_of(const Rep& R, double* sh, int net = 0) {
     Norm n;
+    if (net) {   // the learned predictor's output is already normalised
+        n.coef = 1.0;
+        n.qs = 1.0;
+        n.phis = 1.0 - R.phi_p;
+        return n;
+    }
     const double Q = reduce_parts(slot(R, P_Q), R.ntiles, sh) / (double)R.V;
     n.coef = R.phi_p / ((double)R.N * Q);
     n.qs = (R.ns == 3) ? reduce_parts(slot(R, P_ES), R.nblk, sh) / (double)R.V : 1.0;
@@ -43,10 +49,11 @@ __device__ __forceinline__ T model_phi(const Rep& R, const Norm& n, int I, int i
 
 // Directional derivative at the trial point: h1 = <phi* - phi[U + a1 d], d>.
 template <typename T>
-__global__ void __launch_bounds__(kFlatThreads) k_trial(const Rep* __restrict__ reps, const int* __restrict__ blk2rep) {
+__global__ void __launch_bounds__(kFlatThreads) k_trial(const Rep* __restrict__ reps, const int* __restrict__ blk2rep,
+                                                        int net) {
     __shared__ double sh[33];
     FLAT_PROLOGUE
-    const Norm n = norm_of(R, sh);
+    const Norm n = norm_of(R, sh, net);
     const T* phi = (const T*)R.phi;
     const T* d = (const T*)R.d;
     T h1 = T(0);
@@ -63,11 +70,11 @@ __global__ void __launch_bounds__(kFlatThreads) k_trial(const Rep* __restrict__ 
 // the parity slot of iteration k+1 and max|g|.
 template <typename T>
 __global__ void __launch_bounds__(kFlatThreads) k_grad(const Rep* __restrict__ reps, const int* __restrict__ blk2rep,
-                                                       int k) {
+                                                       int k, int net) {
     __shared__ double sh[33];
     FLAT_PROLOGUE
-    const Norm n = norm_of(R, sh);
-    if (lb == 0 && threadIdx.x == 0) {
+    const Norm n = norm_of(R, sh, net);
+    if (lb == 0 && threadIdx.x == 0 && !net) {
         R.scal[S_Q] = n.coef > 0.0 ? R.phi_p / ((double)R.N * n.coef) : 0.0;
         R.scal[S_QS] = n.qs;
     }
@@ -638,12 +645,41 @@ __global__ void k_step_end(int* counter) { *counter += 1; }
 // Host launchers
 // ---------------------------------------------------------------------------------------------
 template <typename T>
-void launch_trial(const Launch& L) {
-    k_trial<T><<<L.nblk_total, kFlatThreads, 0, L.stream>>>(L.reps, L.blk2rep);
+void launch_trial(const Launch& L, int net) {
+    k_trial<T><<<L.nblk_total, kFlatThreads, 0, L.stream>>>(L.reps, L.blk2rep, net);
 }
 template <typename T>
-void launch_grad(const Launch& L, int k) {
-    k_grad<T><<<L.nblk_total, kFlatThreads, 0, L.stream>>>(L.reps, L.blk2rep, k);
+void launch_grad(const Launch& L, int k, int net) {
+    k_grad<T><<<L.nblk_total, kFlatThreads, 0, L.stream>>>(L.reps, L.blk2rep, k, net);
+}
+// Predictor error: max over sites and species of |q - phi_m| (q: predictor output at the current
+// U, phi_m: exact phi[U]); one block per replica 0, FP32 fields.
+__global__ void __launch_bounds__(kFlatThreads) k_pred_err(const Rep* __restrict__ reps) {
+    __shared__ double sh[33];
+    const Rep& R = reps[0];
+    const float* q = (const float*)R.q;
+    const float* pm = (const float*)R.phim;
+    const long long V = R.V;
+    const long long i0 = (long long)blockIdx.x * R.chunk;
+    const long long i1 = min(i0 + (long long)R.chunk, V);
+    float m = 0.f;
+    for (int I = 0; I < 2; ++I)
+        for (long long i = i0 + threadIdx.x; i < i1; i += kFlatThreads) {
+            const float e = fabsf(q[I * V + i] - pm[I * V + i]);
+            m = (e <= m) ? m : (e == e ? e : INFINITY);   // a NaN counts as an infinite error
+        }
+    const double t = block_max((double)m, sh);
+    if (threadIdx.x == 0) slot(R, P_GMAX)[blockIdx.x] = t;
+}
+__global__ void __launch_bounds__(kFlatThreads) k_pred_err_fin(const Rep* __restrict__ reps) {
+    __shared__ double sh[33];
+    const Rep& R = reps[0];
+    const double t = reduce_parts_max(slot(R, P_GMAX), R.nblk, sh);
+    if (threadIdx.x == 0) R.scal[S_PERR] = t;
+}
+void launch_pred_err(const Launch& L) {
+    k_pred_err<<<L.nblk_total, kFlatThreads, 0, L.stream>>>(L.reps);
+    k_pred_err_fin<<<1, kFlatThreads, 0, L.stream>>>(L.reps);
 }
 template <typename T>
 void launch_dir(const Launch& L, int mode, int k) {
@@ -685,8 +721,8 @@ void launch_lb_diag(const Launch& L) {
 }
 
 #define INST(T)                                                        \
-    template void launch_trial<T>(const Launch&);                      \
-    template void launch_grad<T>(const Launch&, int);                  \
+    template void launch_trial<T>(const Launch&, int);                 \
+    template void launch_grad<T>(const Launch&, int, int);             \
     template void launch_dir<T>(const Launch&, int, int);              \
     template void launch_mu<T>(const Launch&, int);                    \
     template void launch_lb<T>(const Launch&, const void*);            \

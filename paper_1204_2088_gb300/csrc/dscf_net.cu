@@ -470,6 +470,16 @@ double u01(uint64_t seed, uint64_t k) {
 
 }  // namespace
 
+bool dscf_net_fits(const dscf_net* n, int nx, int ny, int nz) {
+    return n && n->nx == nx && n->ny == ny && n->nz == nz && n->B == 1;
+}
+void dscf_net_forward_on(dscf_net* n, cudaStream_t stream, const float* U, double pb0, double pb1, float* phi) {
+    cudaStream_t keep = n->stream;
+    n->stream = stream;
+    forward(n, U, pb0, pb1, phi);
+    n->stream = keep;
+}
+
 extern "C" {
 
 size_t dscf_net_workspace_bytes(int32_t nx, int32_t ny, int32_t nz, int32_t batch) {

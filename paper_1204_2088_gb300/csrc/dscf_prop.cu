@@ -544,7 +544,7 @@ __global__ void __launch_bounds__(32 * (kPropRows + 2 * K)) k_prop_fused(const R
 // Also the FP64 partial sums of exp(-U'_S) for the solvent normalisation.
 template <typename T>
 __global__ void __launch_bounds__(kFlatThreads) k_exp(const Rep* __restrict__ reps, const int* __restrict__ blk2rep,
-                                                      int mode, int k, const T* __restrict__ Uext) {
+                                                      int mode, int k, const T* __restrict__ Uext, int write_u) {
     __shared__ double sh[33];
     const Rep& R = reps[blk2rep[blockIdx.x]];
     const int lb = blockIdx.x - R.blk0;
@@ -561,6 +561,11 @@ __global__ void __launch_bounds__(kFlatThreads) k_exp(const Rep* __restrict__ re
             const double h1 = reduce_parts(slot(R, P_H1), R.nblk, sh);
             const double den = h1 - h0;
             a = (den > 0.0) ? a1 * (-h0) / den : a1;
+            // With the learned predictor the secant is capped at the local-curvature step a1: the
+            // exact response is stiffer than the local one (a <= a1), and a network whose response
+            // to the tiny trial displacement is below its resolution would otherwise give a
+            // near-zero secant denominator and an unbounded step.
+            if (write_u && a > a1) a = a1;
             if (lb == 0 && threadIdx.x == 0) {
                 R.scal[S_ITER0 + 4 * k + 0] = a1;
                 R.scal[S_ITER0 + 4 * k + 1] = a;
@@ -595,7 +600,7 @@ __global__ void __launch_bounds__(kFlatThreads) k_exp(const Rep* __restrict__ re
             } else {
                 u = Uext[R.ext_off + o];
             }
-            const T e = bexp(u);
+            const T e = write_u ? u : bexp(u);   // write_u: the learned predictor takes U' itself
             E[o] = e;
             if (I == 2) es += (double)e;
         }
@@ -655,8 +660,8 @@ int prop_set_smem_limit(size_t bytes) {
 }
 size_t prop_smem_bytes(int vec, bool bwd, size_t es) { return prop_smem(vec, bwd, es); }
 template <typename T>
-void launch_exp(const Launch& L, int mode, int k, const void* Uext) {
-    k_exp<T><<<L.nblk_total, kFlatThreads, 0, L.stream>>>(L.reps, L.blk2rep, mode, k, (const T*)Uext);
+void launch_exp(const Launch& L, int mode, int k, const void* Uext, int write_u) {
+    k_exp<T><<<L.nblk_total, kFlatThreads, 0, L.stream>>>(L.reps, L.blk2rep, mode, k, (const T*)Uext, write_u);
 }
 
 template void launch_prop_fwd<double>(const Launch&, int, int, size_t);
@@ -665,7 +670,7 @@ template void launch_prop_bwd<double>(const Launch&, int, int, size_t);
 template void launch_prop_bwd<float>(const Launch&, int, int, size_t);
 template int prop_set_smem_limit<double>(size_t);
 template int prop_set_smem_limit<float>(size_t);
-template void launch_exp<double>(const Launch&, int, int, const void*);
-template void launch_exp<float>(const Launch&, int, int, const void*);
+template void launch_exp<double>(const Launch&, int, int, const void*, int);
+template void launch_exp<float>(const Launch&, int, int, const void*, int);
 
 }  // namespace dscf

@@ -85,6 +85,7 @@ def load():
         "dscf_net_num_params": (ctypes.c_int64, []),
         "dscf_net_free": (ctypes.c_int, [vp]),
         "dscf_net_last_error": (ctypes.c_char_p, [vp]),
+        "dscf_set_predictor": (ctypes.c_int, [vp, vp, i32, ctypes.c_double, i32]),
     }
     for name, (res, args) in sigs.items():
         fn = getattr(lib, name)
@@ -246,10 +247,18 @@ class Context:
         return {"mass": v[0:3], "mass_drift": v[3:6], "lb_mass": v[6], "lb_momentum": v[7:10],
                 "umax": v[10], "Q": v[11], "QS": v[12], "ncg_iters": int(v[13]), "gg_start": v[14],
                 "gmax_start": v[15], "gg_end": v[16], "gmax_end": v[17], "steps": int(v[18]),
-                "zc": int(v[19]), "kfuse": int(v[20])}
+                "zc": int(v[19]), "kfuse": int(v[20]), "pred_steps": int(v[21]), "exact_steps": int(v[22]),
+                "pred_err": v[23]}
 
     def status(self):
         self._check(self.lib.dscf_status(self.h))
+
+    def set_predictor(self, net, corrector_every=10, tol=1e-3, ncg_iters=0):
+        """Attach a trained Net (same grid, batch 1) as the density map of the inversion, judged
+        by an exact corrector step every corrector_every steps; None detaches."""
+        self._check(self.lib.dscf_set_predictor(self.h, net.h if net is not None else None, int(corrector_every),
+                                                float(tol), int(ncg_iters)))
+        self._net = net
 
     def set_tuning(self, zc, kfuse):
         self._check(self.lib.dscf_set_tuning(self.h, int(zc), int(kfuse)))

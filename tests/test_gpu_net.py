@@ -89,3 +89,186 @@ def test_training_on_method_generated_pairs_lowers_the_loss():
         net.train_step(U, P, phibar, lr=2e-3)
     last = net.train_step(U, P, phibar, lr=2e-3, want_loss=True)
     assert last < 0.2 * first
+
+
+def _melt32(N=16, seed=31):
+    cfg = inputs.melt((32, 16, 12), N, 0.5, 15.0, seed=seed, noise=0.03)
+    return cfg
+
+
+def _ctx_from(cfg, phi0):
+    ctx = dscf.Context(cfg, dscf.FP32)
+    ctx.set(dscf.PHI, torch.from_numpy(phi0).float().cuda())
+    return ctx
+
+
+def test_predictor_that_never_passes_falls_back_to_the_exact_path_bitwise():
+    cfg = _melt32()
+    phi0 = inputs.initial_fields(cfg)
+    ref = _ctx_from(cfg, phi0)
+    ctx = _ctx_from(cfg, phi0)
+    net = dscf.Net(cfg["grid"], 1, seed=7)           # untrained: far outside any tolerance
+    ctx.set_predictor(net, corrector_every=2, tol=1e-9)
+    ref.step(5)
+    ctx.step(5)
+    for f in (dscf.PHI, dscf.U, dscf.POP, dscf.PHIM):
+        assert torch.equal(ctx.get(f), ref.get(f)), f
+    d = ctx.diagnostics()
+    assert d["pred_steps"] == 0 and d["exact_steps"] == 5 and d["pred_err"] > 1e-9
+
+
+def test_predictor_steps_use_the_network_and_the_corrector_judges_it():
+    cfg = _melt32()
+    phi0 = inputs.initial_fields(cfg)
+    phibar = [cfg["nA"] / cfg["N"], 1 - cfg["nA"] / cfg["N"]]
+    ctx = _ctx_from(cfg, phi0)
+    net = dscf.Net(cfg["grid"], 1, seed=8)
+    ctx.set_predictor(net, corrector_every=2, tol=1e3, ncg_iters=2)   # always accepted
+    ctx.step(1)                      # exact step; first judgement: the network's own error
+    d = ctx.diagnostics()
+    assert d["exact_steps"] == 1 and d["pred_steps"] == 0
+    U = ctx.get(dscf.U)
+    exact = ctx.densities(U)
+    pred = net.forward(U[None], phibar)[0]
+    torch.cuda.synchronize()
+    assert abs(d["pred_err"] - (pred - exact).abs().max().item()) < 1e-6
+    ctx.step(1)                      # predictor step
+    d = ctx.diagnostics()
+    assert d["exact_steps"] == 1 and d["pred_steps"] == 1 and d["ncg_iters"] == 2
+    # after a predictor step the inversion's density is the network at the committed potential
+    U = ctx.get(dscf.U)
+    pred = net.forward(U[None], phibar)[0]
+    torch.cuda.synchronize()
+    assert (ctx.get(dscf.PHIM) - pred).abs().max().item() < 1e-5
+    # masses stay exact through the convection-diffusion update
+    m0 = phi0.astype(np.float32).astype(np.float64).reshape(2, -1).sum(1)
+    phi = ctx.get(dscf.PHI)
+    assert np.abs(phi.double().cpu().numpy().reshape(2, -1).sum(1) - m0).max() < 1e-6 * m0.max()
+    # the corrector after a predictor step judges it by ||phi[U] - phi*||_inf at its potential
+    want = (phi - ctx.densities(U)).abs().max().item()
+    ctx.step(1)
+    d = ctx.diagnostics()
+    assert d["exact_steps"] == 2 and d["pred_steps"] == 1 and d["ncg_iters"] == cfg["ncg_iters"]
+    assert abs(d["pred_err"] - want) < 1e-6 * max(1.0, want)
+    ctx.step(1)                      # predictor step again
+    # detaching returns to the exact path, starting from the exact density of the current state:
+    # the next step agrees with that of a fresh context given the same fields (which differs only
+    # in its reference masses, taken from the fields it was given, and its stored velocity)
+    ctx.set_predictor(None)
+    fresh = dscf.Context(cfg, dscf.FP32)
+    for f in (dscf.PHI, dscf.U, dscf.POP):
+        fresh.set(f, ctx.get(f))
+    ctx.step(1)
+    fresh.step(1)
+    for f in (dscf.PHI, dscf.U):
+        a, b = ctx.get(f), fresh.get(f)
+        r = ((a - b).abs().max() / b.abs().max()).item()
+        assert r < 1e-4, (f, r)
+
+
+def test_corrector_schedule():
+    """Exact steps at counters 0, k, 2k, ...; between them the predictor runs exactly when the
+    last judgement passed (an untrained network can fail it: its steps may even go non-finite)."""
+    cfg = _melt32()
+    ctx = _ctx_from(cfg, inputs.initial_fields(cfg))
+    tol = 1e3
+    ctx.set_predictor(dscf.Net(cfg["grid"], 1, seed=8), corrector_every=3, tol=tol)
+    ok = None
+    d = ctx.diagnostics()
+    for i in range(7):
+        ctx.step(1)
+        e = ctx.diagnostics()
+        took_pred = e["pred_steps"] > d["pred_steps"]
+        assert e["pred_steps"] + e["exact_steps"] == i + 1
+        if i % 3 == 0:
+            assert not took_pred
+            ok = bool(np.isfinite(e["pred_err"]) and e["pred_err"] <= tol)
+        else:
+            assert took_pred == ok, (i, e)
+        d = e
+    assert d["steps"] == 7
+
+
+def test_predictor_rejects_unsupported_contexts():
+    cfg = _melt32()
+    net = dscf.Net(cfg["grid"], 1, seed=9)
+    with pytest.raises(dscf.DSCFError):
+        dscf.Context(cfg, dscf.FP64).set_predictor(net)
+    with pytest.raises(dscf.DSCFError):
+        dscf.Context(cfg, dscf.FP32).set_predictor(dscf.Net((16, 16, 12), 1))
+    with pytest.raises(dscf.DSCFError):
+        dscf.Context(cfg, dscf.FP32).set_predictor(dscf.Net(cfg["grid"], 2))
+    with pytest.raises(dscf.DSCFError):
+        dscf.Context(cfg, dscf.FP32).set_predictor(net, corrector_every=0)
+    with pytest.raises(dscf.DSCFError):
+        dscf.Context(cfg, dscf.FP32).set_predictor(net, ncg_iters=33)
+
+
+def _events_ms(fn, reps):
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(reps):
+        fn()
+    b.record()
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / reps
+
+
+def test_trained_predictor_gain_over_the_exact_method():
+    """What a network trained on the method's own (U, phi[U]) pairs gains, measured honestly.
+
+    Symmetric melt f = 0.5, chi N = 20, N = 32 on 32^3 (FP32).  The exact run supplies the
+    pairs of its first 120 steps; the network (BF16 kernels, Adam on the GPU) is judged on the
+    later 40.  Then, from the exact state at step 120, 40 steps with the predictor attached
+    (exact corrector every 10 steps, fallback above tol) against 40 exact steps: the run must
+    take predictor steps, stay finite and close to the exact trajectory, and be faster."""
+    cfg = inputs.melt((32, 32, 32), 32, 0.5, 20.0, seed=1)
+    phibar = [cfg["nA"] / cfg["N"], 1 - cfg["nA"] / cfg["N"]]
+    ctx = dscf.Context(cfg, dscf.FP32)
+    ctx.set(dscf.PHI, torch.from_numpy(inputs.initial_fields(cfg)).float().cuda())
+    T0, T = 120, 160
+    Us, Ps = [], []
+    for t in range(1, T + 1):
+        ctx.step(1)
+        Us.append(ctx.get(dscf.U).clone())
+        Ps.append(ctx.get(dscf.PHIM).clone())     # phi[U] of the step's inverted potential
+        if t == T0:
+            state = {f: ctx.get(f).clone() for f in (dscf.PHI, dscf.U, dscf.POP)}
+    phi_exact = ctx.get(dscf.PHI)
+    U, P = torch.stack(Us), torch.stack(Ps)
+
+    B, iters = 8, 2000
+    net = dscf.Net(cfg["grid"], B, seed=3)
+    one = dscf.Net(cfg["grid"], 1, seed=3)
+
+    def held_out_err():
+        return max((one.forward(U[t:t + 1], phibar)[0] - P[t]).abs().max().item() for t in range(T0, T, 5))
+
+    e0 = held_out_err()
+    g = torch.Generator().manual_seed(0)
+    for it in range(iters):
+        idx = torch.randint(0, T0, (B,), generator=g)
+        net.train_step(U[idx], P[idx], phibar, lr=1e-3 * 0.5 * (1 + np.cos(np.pi * it / iters)) + 1e-5)
+    one.set_params(net.get_params())
+    e1 = held_out_err()
+    assert e1 < 0.1 * e0 and e1 < 3e-3, (e0, e1)
+
+    tol = 3e-3
+    pred = dscf.Context(cfg, dscf.FP32)
+    ref = dscf.Context(cfg, dscf.FP32)
+    for c in (pred, ref):
+        for f, v in state.items():
+            c.set(f, v)
+    pred.set_predictor(one, corrector_every=10, tol=tol, ncg_iters=1)
+    t_pred = _events_ms(lambda: pred.step(T - T0), 1)
+    t_ref = _events_ms(lambda: ref.step(T - T0), 1)
+    d = pred.diagnostics()
+    phi = pred.get(dscf.PHI)
+    dev = (phi - ref.get(dscf.PHI)).abs().max().item()
+    # a context restarted from the fields reproduces the continued run up to FP32 rounding
+    assert (ref.get(dscf.PHI) - phi_exact).abs().max().item() < 1e-4
+    assert d["pred_steps"] > 0 and d["pred_steps"] + d["exact_steps"] == T - T0
+    assert torch.isfinite(phi).all()
+    assert dev < 2 * tol, dev
+    assert t_ref / t_pred > 1.1, (t_ref, t_pred, d)
