@@ -39,7 +39,8 @@ def args_():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--no-forms", action="store_true", help="skip the FP64 form")
+    ap.add_argument("--no-forms", action="store_true", help="skip the FP64, learned and batched forms")
+    ap.add_argument("--forms", default="fp64,fp32_learned,batch48", help="comma-separated forms to report")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=20.0, help="seconds of oracle work for cpu_baseline")
     return ap.parse_args()
@@ -210,11 +211,98 @@ def ncu_traffic(kernel_src):
     return None
 
 
+def learned_form(cfg, dev, phi0, timed, world, steps):
+    """FP32 step with the learned predictor: a network trained on the GPU (the library's BF16
+    kernels, Adam) on (U, phi[U]) pairs of the same physics generated by the exact method on a
+    32^3 box, then attached to the full-size context (the network is translation invariant with
+    periodic padding).  Exact corrector every 10 steps, fallback above 1e-3, one inversion
+    iteration per predictor step.  The timed region includes the correctors and judgements."""
+    import numpy as np
+    import torch
+
+    from paper_1204_2088_gb300 import dscf, inputs, replicas
+
+    t_start = time.perf_counter()
+    small = dict(cfg, grid=(32, 32, 32), name=cfg["name"] + "-train32")
+    ctx = dscf.Context(small, dscf.FP32, device=dev)
+    ctx.set(dscf.PHI, torch.from_numpy(inputs.initial_fields(small)).float().to(dev))
+    T, T0 = 160, 120
+    Us, Ps = [], []
+    for _ in range(T):
+        ctx.step(1)
+        Us.append(ctx.get(dscf.U).clone())
+        Ps.append(ctx.get(dscf.PHIM).clone())
+    ctx.close()
+    U, P = torch.stack(Us), torch.stack(Ps)
+    f = cfg["nA"] / cfg["N"]
+    phibar = [cfg["phi_p"] * f, cfg["phi_p"] * (1 - f)]
+    B, iters = 8, 2000
+    net = dscf.Net(small["grid"], B, seed=3, device=dev)
+    one = dscf.Net(small["grid"], 1, seed=3, device=dev)
+    err = lambda: max((one.forward(U[t:t + 1], phibar)[0] - P[t]).abs().max().item() for t in range(T0, T, 5))
+    e_untrained = err()
+    g = torch.Generator().manual_seed(0)
+    for it in range(iters):
+        idx = torch.randint(0, T0, (B,), generator=g)
+        net.train_step(U[idx], P[idx], phibar, lr=1e-3 * 0.5 * (1 + np.cos(np.pi * it / iters)) + 1e-5)
+    one.set_params(net.get_params())
+    e_trained = err()
+    t_train = time.perf_counter() - t_start
+    big = dscf.Net(cfg["grid"], 1, seed=3, device=dev)
+    big.set_params(net.get_params())
+    del net, one
+    c = dscf.Context(cfg, dscf.FP32, device=dev)
+    c.set(dscf.PHI, phi0)
+    c.set_predictor(big, corrector_every=10, tol=1e-3, ncg_iters=1)
+    c.step(3)
+    d0 = c.diagnostics()
+    ms = timed(lambda: c.step(steps))
+    d = c.diagnostics()
+    c.status()
+    V = int(np.prod(cfg["grid"]))
+    out = {"value": replicas.aggregate_rate([V * steps] * world, [ms]), "unit": UNIT, "ms_per_step": ms / steps,
+           "steps": steps, "predictor_steps": d["pred_steps"] - d0["pred_steps"],
+           "exact_steps": d["exact_steps"] - d0["exact_steps"], "last_judged_error": d["pred_err"],
+           "tol": 1e-3, "corrector_every": 10, "predictor_ncg_iters": 1,
+           "training": {"pairs": T0, "grid": list(small["grid"]), "iters": iters, "batch": B,
+                        "held_out_max_err_untrained": e_untrained, "held_out_max_err_trained": e_trained,
+                        "seconds": t_train}}
+    c.close()
+    big.close()
+    return out
+
+
+def batch48_form(dev, timed, rank, world, steps):
+    """The 48 mixed-size melts (24 x 48^3, 16 x 64^3, 8 x 96^3) in one FP32 context per rank
+    (the replicas split across ranks by site count), one captured graph per step."""
+    import numpy as np
+    import torch
+
+    from paper_1204_2088_gb300 import dscf, inputs, replicas
+
+    cfgs = inputs.batch48()
+    sites = [int(np.prod(c["grid"])) for c in cfgs]
+    mine = replicas.partition(sites, world)[rank]
+    if not mine:
+        ms = timed(lambda: None)
+        return None
+    sub = [cfgs[i] for i in mine]
+    c = dscf.Context(sub, dscf.FP32, device=dev)
+    c.set(dscf.PHI, torch.cat([torch.from_numpy(inputs.initial_fields(x)).float().reshape(-1) for x in sub]).to(dev))
+    c.step(2)
+    ms = timed(lambda: c.step(steps))
+    c.status()
+    diag = c.diagnostics(0)
+    c.close()
+    return {"value": replicas.aggregate_rate([sum(sites) * steps], [ms]), "unit": UNIT, "ms_per_step": ms / steps,
+            "steps": steps, "replicas": len(cfgs), "sites": sum(sites), "zc": diag["zc"], "kfuse": diag["kfuse"]}
+
+
 def run_ours(a):
     import numpy as np
     import torch
 
-    from paper_1204_2088_gb300 import dscf, inputs
+    from paper_1204_2088_gb300 import dscf, inputs, replicas
 
     rank, world, local = dist_env()
     if world > 1:
@@ -222,7 +310,7 @@ def run_ours(a):
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    cfg = inputs.workload(WORKLOAD, seed=11 + rank)
+    cfg = inputs.workload(WORKLOAD, seed=replicas.rank_seed(11, rank))
     V = int(np.prod(cfg["grid"]))
     N = cfg["N"]
 
@@ -263,7 +351,7 @@ def run_ours(a):
     sweeps_ms, lb_ms, step_ms = ctx.probe_ms()
     diag = ctx.diagnostics()
     launches = ctx.launches_per_step()
-    value = world * V * a.steps / (ms_max * 1e-3)
+    value = replicas.aggregate_rate([V * a.steps] * world, [ms_max])
 
     # end to end through the C ABI with host buffers: upload phi, one step, read phi back
     host = torch.empty(tuple(phi0.shape), dtype=torch.float32).pin_memory()
@@ -285,24 +373,34 @@ def run_ours(a):
     del ctx
 
     forms = {}
-    if not a.no_forms:
+    want = set() if a.no_forms else set(f for f in a.forms.split(",") if f)
+
+    def timed(fn):
+        torch.cuda.synchronize(dev)
+        barrier()
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        return max_over_ranks(e0.elapsed_time(e1))
+
+    if "fp64" in want:
         k64 = max(2, min(10, a.steps // 10))
         c64 = dscf.Context(cfg, dscf.FP64, device=dev)
         c64.set(dscf.PHI, phi0.double())
         c64.probe(True)
         c64.step(2)
-        torch.cuda.synchronize(dev)
-        barrier()
-        e0.record(stream)
-        c64.step(k64)
-        e1.record(stream)
-        torch.cuda.synchronize(dev)
-        m64 = max_over_ranks(e0.elapsed_time(e1))
+        m64 = timed(lambda: c64.step(k64))
         sw64, lb64, st64 = c64.probe_ms()
-        forms["fp64"] = {"value": world * V * k64 / (m64 * 1e-3), "unit": UNIT, "ms_per_step": m64 / k64,
-                         "steps": k64, "prop_sweep_ms_per_launch": sw64 / (2 * N), "lb_ms": lb64}
+        forms["fp64"] = {"value": replicas.aggregate_rate([V * k64] * world, [m64]), "unit": UNIT,
+                         "ms_per_step": m64 / k64, "steps": k64, "prop_sweep_ms_per_launch": sw64 / (2 * N),
+                         "lb_ms": lb64}
         c64.close()
         del c64
+    if "fp32_learned" in want:
+        forms["fp32_learned"] = learned_form(cfg, dev, phi0, timed, world, max(20, min(a.steps, 40)))
+    if "batch48" in want:
+        forms["batch48"] = batch48_form(dev, timed, rank, world, max(3, min(a.steps // 10, 10)))
 
     hbm, peak_kind = peaks()
     # Dominant kernel: one contour step of the propagator sweeps (k_prop_fwd / k_prop_bwd).
