@@ -196,9 +196,9 @@ def peaks():
     return 6800.0, "fallback"
 
 
-def ncu_traffic(kernel_src):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken on the current
-    source of the kernel (hash match); otherwise None."""
+def ncu_traffic(kernel_src, N):
+    """DRAM bytes per contour step of the propagator sweep from the committed ncu summary, if it
+    was taken on the current source of the kernel (hash match); otherwise None."""
     import hashlib
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
@@ -206,8 +206,8 @@ def ncu_traffic(kernel_src):
     d = json.load(open(p))
     h = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()[:16]
     ent = d.get("prop_sweep")
-    if ent and ent.get("source_sha256_16") == h:
-        return ent.get("dram_bytes_per_launch")
+    if ent and ent.get("source_sha256_16") == h and ent.get("N") == N:
+        return ent.get("dram_bytes_per_contour_step")
     return None
 
 
@@ -338,10 +338,14 @@ def run_ours(a):
     torch.cuda.synchronize(dev)
     clocks.start()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    # the profiler range (a no-op unless a profiler runs with profiling from start off) holds
+    # exactly the timed steps
+    torch.cuda.profiler.start()
     e0.record(stream)
     ctx.step(a.steps)
     e1.record(stream)
     torch.cuda.synchronize(dev)
+    torch.cuda.profiler.stop()
     barrier()
     torch.cuda.synchronize(dev)
     clk = clocks.stop()
@@ -403,16 +407,20 @@ def run_ours(a):
         forms["batch48"] = batch48_form(dev, timed, rank, world, max(3, min(a.steps // 10, 10)))
 
     hbm, peak_kind = peaks()
-    # Dominant kernel: one contour step of the propagator sweeps (k_prop_fwd / k_prop_bwd).
-    # Algorithmic bytes per launch: the store-forward propagator solve must write G_s once and
-    # read it once per gradient evaluation plus read U and write phi: (8N + 16) B per site per
-    # evaluation over its 2N launches, i.e. (4 + 8/N) B per site per launch (FP32).
+    # Dominant kernel: the propagator sweeps.  The unit is one contour step (the autotuner runs
+    # N of them per launch in the persistent kernel, K per launch in the fused one, one in the
+    # single-step kernels).  Algorithmic bytes per contour step: the store-forward propagator
+    # solve must write G_s once and read it once per density evaluation plus read U and write
+    # phi: (8N + 16) B per site per evaluation over its 2N contour steps, i.e. (4 + 8/N) B per
+    # site per step (FP32).
     per_launch_s = sweeps_ms * 1e-3 / (2 * N)
     alg_bytes = (4.0 + 8.0 / N) * V
     achieved = alg_bytes / per_launch_s / 1e9
-    traffic = ncu_traffic(os.path.join(ROOT, "paper_1204_2088_gb300", "csrc", "dscf_prop.cu"))
+    traffic = ncu_traffic(os.path.join(ROOT, "paper_1204_2088_gb300", "csrc", "dscf_pers.cu"), N)
     roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-            "traffic": traffic, "kernel": "k_prop_fwd/k_prop_bwd (one contour step)",
+            "traffic": traffic,
+            "kernel": {0: "k_prop_pers (persistent sweep)", 1: "k_prop (single step)"}.get(
+                diag["kfuse"], f"k_prop_fused (K={diag['kfuse']})") + "; unit = one contour step",
             "alg_bytes_per_launch": alg_bytes, "ms_per_launch": per_launch_s * 1e3, "peak_kind": peak_kind}
     lb_alg = 180.0 * V
     kernels = {"prop_sweep": {"ms_per_launch": per_launch_s * 1e3, "GBps": achieved},

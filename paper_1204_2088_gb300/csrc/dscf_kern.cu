@@ -19,6 +19,15 @@ namespace dscf {
 
 __device__ __forceinline__ int pslot_gg(int k) { return (k & 1) ? P_GG1 : P_GG0; }
 
+// Site coordinates from the flat index (32-bit unsigned division: the flat index of a replica
+// fits in an int).
+__device__ __forceinline__ void site_xyz(int i, int nx, int ny, int& x, int& y, int& z) {
+    const unsigned q = (unsigned)i / (unsigned)nx;
+    x = i - (int)q * nx;
+    z = (int)(q / (unsigned)ny);
+    y = (int)q - z * ny;
+}
+
 // ---------------------------------------------------------------------------------------------
 // Normalisation of the quadrature (Eq. 2 prefactor):  phi_I = phi_p/(N Q) q_I,
 // phi_S = phi_s exp(-U_S)/<exp(-U_S)>.
@@ -165,7 +174,7 @@ __device__ __forceinline__ T sigma_at(const T* __restrict__ f, int x, int y, int
     for (int c = 0; c < 3; ++c) {
         T yy[3];
         for (int b = 0; b < 3; ++b) {
-            const long long row = (long long)nx * (ys[b] + (long long)ny * zs[c]);
+            const int row = nx * (ys[b] + ny * zs[c]);
             yy[b] = be * f[row + xs[1]] + al * (f[row + xs[0]] + f[row + xs[2]]);
         }
         zz[c] = be * yy[1] + al * (yy[0] + yy[2]);
@@ -193,20 +202,19 @@ __global__ void __launch_bounds__(kFlatThreads) k_mu(const Rep* __restrict__ rep
     const T* phi = (const T*)R.phi;
     const T* U = (const T*)R.U;
     T* mu = (T*)R.mu;
-    _Pragma("unroll 4") for (int i = i0 + threadIdx.x; i < i1; i += kFlatThreads) {
-        const int x = (int)(i % nx);
-        const int y = (int)((i / nx) % ny);
-        const int z = (int)(i / ((long long)nx * ny));
+    for (int i = i0 + threadIdx.x; i < i1; i += kFlatThreads) {
+        int x, y, z;
+        site_xyz(i, nx, ny, x, y, z);
         T sp[3], tot = T(0);
         for (int J = 0; J < ns; ++J) {
-            sp[J] = sigma_at(phi + (long long)J * V, x, y, z, nx, ny, nz, al, be);
-            tot += phi[(long long)J * V + i];
+            sp[J] = sigma_at(phi + (size_t)J * V, x, y, z, nx, ny, nz, al, be);
+            tot += phi[(size_t)J * V + i];
         }
         for (int I = 0; I < ns; ++I) {
-            T m = -U[(long long)I * V + i];
+            T m = -U[(size_t)I * V + i];
             for (int J = 0; J < ns; ++J) m += (T)R.chi[I * 3 + J] * sp[J];
             m += (T)R.kappa * (tot - T(1));
-            mu[(long long)I * V + i] = m;
+            mu[(size_t)I * V + i] = m;
         }
     }
 }
@@ -413,28 +421,25 @@ __global__ void __launch_bounds__(kFlatThreads) k_lb_diag_fin(const Rep* __restr
 // sweeps, FP64 mass correction.
 // ---------------------------------------------------------------------------------------------
 struct Nb {
-    long long c, n[6];  // centre and +x -x +y -y +z -z
+    int n[6];  // +x -x +y -y +z -z
 };
-__device__ __forceinline__ Nb neighbours(long long i, int nx, int ny, int nz) {
-    const int x = (int)(i % nx);
-    const int y = (int)((i / nx) % ny);
-    const int z = (int)(i / ((long long)nx * ny));
-    const int xm = x == 0 ? nx - 1 : x - 1, xp = x == nx - 1 ? 0 : x + 1;
-    const int ym = y == 0 ? ny - 1 : y - 1, yp = y == ny - 1 ? 0 : y + 1;
-    const int zm = z == 0 ? nz - 1 : z - 1, zp = z == nz - 1 ? 0 : z + 1;
-    const long long sy = nx, sz = (long long)nx * ny;
+__device__ __forceinline__ Nb neighbours(int i, int nx, int ny, int nz) {
+    int x, y, z;
+    site_xyz(i, nx, ny, x, y, z);
+    const int sy = nx, sz = nx * ny;
     Nb b;
-    b.c = i;
-    b.n[0] = xp + y * sy + z * sz;
-    b.n[1] = xm + y * sy + z * sz;
-    b.n[2] = x + yp * sy + z * sz;
-    b.n[3] = x + ym * sy + z * sz;
-    b.n[4] = x + y * sy + zp * sz;
-    b.n[5] = x + y * sy + zm * sz;
+    b.n[0] = i + (x == nx - 1 ? 1 - nx : 1);
+    b.n[1] = i + (x == 0 ? nx - 1 : -1);
+    b.n[2] = i + (y == ny - 1 ? sy - sz : sy);
+    b.n[3] = i + (y == 0 ? sz - sy : -sy);
+    b.n[4] = i + (z == nz - 1 ? sz - nz * sz : sz);
+    b.n[5] = i + (z == 0 ? nz * sz - sz : -sz);
     return b;
 }
 
-// Explicit part: rhs_I = -sum_axes [F(i+1/2) - F(i-1/2)] + dt M L(phi; mu^n).
+// Explicit part: rhs_I = -sum_axes [F(i+1/2) - F(i-1/2)] + dt M L(phi; mu^n).  Also stores
+// 1/max(phi_I, floor) for the Jacobi sweeps in the Boltzmann-factor buffer, which is free from
+// the end of the inversion to the start of the next one.
 template <typename T>
 __global__ void __launch_bounds__(kFlatThreads) k_cd_rhs(const Rep* __restrict__ reps, const int* __restrict__ blk2rep) {
     FLAT_PROLOGUE
@@ -442,56 +447,72 @@ __global__ void __launch_bounds__(kFlatThreads) k_cd_rhs(const Rep* __restrict__
     const T* mu = (const T*)R.mu;
     const T* u = (const T*)R.u;
     T* rhs = (T*)R.rhs;
+    T* inv = (T*)R.E;
     const bool hyd = R.hydro != 0;
     const T dtM = (T)(R.dt * R.M);
-    _Pragma("unroll 4") for (int i = i0 + threadIdx.x; i < i1; i += kFlatThreads) {
+    const T fl = (T)R.phi_floor;
+    for (int i = i0 + threadIdx.x; i < i1; i += kFlatThreads) {
         const Nb b = neighbours(i, R.nx, R.ny, R.nz);
-        for (int I = 0; I < R.ns; ++I) {
-            const T* ph = phi + (long long)I * V;
-            const T* m = mu + (long long)I * V;
-            T conv = 0, lap = 0;
-            for (int d = 0; d < 3; ++d) {
-                const long long ip = b.n[2 * d], im = b.n[2 * d + 1];
-                T Ci = 0, Cp = 0, Cm = 0;
-                if (hyd) {
-                    const T* C = u + (long long)d * V;
-                    Ci = C[i];
-                    Cp = C[ip];
-                    Cm = C[im];
-                }
-                const T hp = T(0.5) * (ph[i] + ph[ip]) - T(0.5) * (Cp * ph[ip] - Ci * ph[i]);
-                const T Fp = T(0.5) * (Ci + Cp) * hp;
-                const T hm = T(0.5) * (ph[im] + ph[i]) - T(0.5) * (Ci * ph[i] - Cm * ph[im]);
-                const T Fm = T(0.5) * (Cm + Ci) * hm;
-                conv += Fp - Fm;
-                lap += T(0.5) * (ph[i] + ph[ip]) * (m[ip] - m[i]) + T(0.5) * (ph[i] + ph[im]) * (m[im] - m[i]);
+        T Ci[3], Cp[3], Cm[3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            Ci[d] = Cp[d] = Cm[d] = T(0);
+            if (hyd) {
+                const T* C = u + (size_t)d * V;
+                Ci[d] = C[i];
+                Cp[d] = C[b.n[2 * d]];
+                Cm[d] = C[b.n[2 * d + 1]];
             }
-            rhs[(long long)I * V + i] = -conv + dtM * lap;
+        }
+        for (int I = 0; I < R.ns; ++I) {
+            const T* ph = phi + (size_t)I * V;
+            const T* m = mu + (size_t)I * V;
+            const T pc = ph[i], mc = m[i];
+            T conv = 0, lap = 0;
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                const int ip = b.n[2 * d], im = b.n[2 * d + 1];
+                const T pp = ph[ip], pm = ph[im];
+                const T hp = T(0.5) * (pc + pp) - T(0.5) * (Cp[d] * pp - Ci[d] * pc);
+                const T Fp = T(0.5) * (Ci[d] + Cp[d]) * hp;
+                const T hm = T(0.5) * (pm + pc) - T(0.5) * (Ci[d] * pc - Cm[d] * pm);
+                const T Fm = T(0.5) * (Cm[d] + Ci[d]) * hm;
+                conv += Fp - Fm;
+                lap += T(0.5) * (pc + pp) * (m[ip] - mc) + T(0.5) * (pc + pm) * (m[im] - mc);
+            }
+            rhs[(size_t)I * V + i] = -conv + dtM * lap;
+            inv[(size_t)I * V + i] = T(1) / (pc < fl ? fl : pc);
         }
     }
 }
 
 // One Jacobi sweep k of (I - c L(phi; H .)) delta = rhs, c = dt M / 2; the species block of a
-// site is solved exactly (diagonal plus the rank-one kappa coupling).
+// site is solved exactly (diagonal plus the rank-one kappa coupling).  inv = 1/max(phi, floor)
+// from k_cd_rhs.
 template <typename T>
 __global__ void __launch_bounds__(kFlatThreads) k_cd_jacobi(const Rep* __restrict__ reps, const int* __restrict__ blk2rep,
                                                             int k) {
     FLAT_PROLOGUE
     const T* phi = (const T*)R.phi;
+    const T* inv = (const T*)R.E;
     const T* rhs = (const T*)R.rhs;
     const T* dold = (const T*)((k & 1) ? R.del0 : R.del1);
     T* dnew = (T*)((k & 1) ? R.del1 : R.del0);
     const int ns = R.ns;
     const T c = (T)(0.5 * R.dt * R.M);
-    const T kap = (T)R.kappa, fl = (T)R.phi_floor;
+    const T kap = (T)R.kappa;
     for (int i = i0 + threadIdx.x; i < i1; i += kFlatThreads) {
         const Nb b = neighbours(i, R.nx, R.ny, R.nz);
-        T rh[3], D[3], A[3];
+        T rh[3], w[3], phc[3];
 #pragma unroll
-        for (int I = 0; I < 3; ++I) { rh[I] = T(0); D[I] = T(1); A[I] = T(0); }
+        for (int I = 0; I < 3; ++I) {
+            rh[I] = T(0);
+            w[I] = T(0);
+            phc[I] = (I < ns) ? phi[(size_t)I * V + i] : T(0);
+        }
 #pragma unroll
         for (int q = 0; q < 6; ++q) {
-            const int nb = (int)b.n[q];
+            const int nb = b.n[q];
             // psi at the neighbour from the previous iterate (zero before the first sweep)
             T dl[3], sd = T(0);
 #pragma unroll
@@ -502,26 +523,19 @@ __global__ void __launch_bounds__(kFlatThreads) k_cd_jacobi(const Rep* __restric
 #pragma unroll
             for (int I = 0; I < 3; ++I) {
                 if (I < ns) {
-                    const T phn = phi[(size_t)I * V + nb];
-                    const T phc = phi[(size_t)I * V + i];
-                    const T ph = phn < fl ? fl : phn;
-                    const T psi = (k > 0) ? dl[I] / ph + kap * sd : T(0);
-                    const T pf = T(0.5) * (phc + phn);
-                    A[I] += pf;                  // accumulates the face sum w_I
-                    rh[I] += pf * psi;           // accumulates the off-diagonal term
+                    const T pf = T(0.5) * (phc[I] + phi[(size_t)I * V + nb]);
+                    w[I] += pf;                                   // face sum w_I
+                    if (k > 0) rh[I] += pf * (dl[I] * inv[(size_t)I * V + nb] + kap * sd);
                 }
             }
         }
-        T num = T(0), den = T(1);
+        T num = T(0), den = T(1), D[3], A[3];
 #pragma unroll
         for (int I = 0; I < 3; ++I) {
             if (I < ns) {
-                const T ws = A[I];
-                const T phc0 = phi[(size_t)I * V + i];
-                const T phc = phc0 < fl ? fl : phc0;
                 rh[I] = rhs[(size_t)I * V + i] + c * rh[I];
-                D[I] = T(1) + c * ws / phc;
-                A[I] = c * kap * ws;
+                D[I] = T(1) + c * w[I] * inv[(size_t)I * V + i];
+                A[I] = c * kap * w[I];
                 num += rh[I] / D[I];
                 den += A[I] / D[I];
             }
