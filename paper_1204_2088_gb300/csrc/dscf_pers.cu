@@ -238,13 +238,14 @@ __global__ void __launch_bounds__(PTHREADS, 1) k_prop_pers(const Rep* __restrict
             }
             if (is_boundary(p0 + k) && (!BWD || s > 1)) *(VT*)(dst + own0 + (size_t)k * plane) = out[k];
         }
-        if (BWD && s > 1) prefetch_gs(s - 1);   // GS slots of this thread were read above
-        // publish the boundary of this step
+        // publish the boundary of this step; the fence waits for every memory operation the SM
+        // has in flight, so nothing else is issued before it
         __syncthreads();
         if (threadIdx.x == 0) {
             __threadfence();
             st_release(ctl.flags + b, c0 + j + 1);
         }
+        if (BWD && s > 1) prefetch_gs(s - 1);   // GS slots of this thread were read above
 #pragma unroll
         for (int k = 0; k < OWN; ++k) {
             if (!BWD && !is_boundary(p0 + k)) *(VT*)(dst + own0 + (size_t)k * plane) = out[k];
