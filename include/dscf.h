@@ -178,6 +178,20 @@ int64_t dscf_launches_per_step(const dscf_ctx* ctx);
  * its graph.  Results do not depend on either value beyond rounding. */
 int dscf_set_tuning(dscf_ctx* ctx, int32_t zc, int32_t kfuse);
 
+/* Failure detection of the persistent sweeps.  Every wait of a persistent sweep on a
+ * neighbouring brick is bounded by `polls` polls (default 4194304, several seconds; each poll is
+ * an acquire load of the neighbour's step counter followed by a short sleep).  A CTA that runs out
+ * sets the status bit and a global abort flag; every other CTA then stops waiting, all launches
+ * finish, and dscf_status reports DSCF_ERR_TIMEOUT.  That call also re-arms the step counters, so
+ * the context stays usable once the caller has restored its fields (they are invalid after a
+ * timeout).  dscf_set_wait_limit synchronises and re-captures the step graph.
+ * dscf_inject_lag (test hook, host side: one 4-byte copy) sets brick `brick`'s step counter far
+ * behind the others, so that during the next persistent sweep its neighbours wait for values it
+ * never publishes and run out of polls.  DSCF_ERR_STATE unless the context uses persistent
+ * sweeps (kfuse 0), DSCF_ERR_ARG for a brick outside 0 .. bricks-1 or polls < 1. */
+int dscf_set_wait_limit(dscf_ctx* ctx, int32_t polls);
+int dscf_inject_lag(dscf_ctx* ctx, int32_t brick);
+
 /* Timing probe.  enable != 0 makes the next dscf_step capture CUDA events (created by the
  * library) into the step graph: around the 2N contour-sweep launches of the first gradient
  * evaluation of the step, around the LB collide-stream launch, and around the whole step.

@@ -220,6 +220,7 @@ struct dscf_ctx {
     cudaGraphExec_t exec_pred = nullptr;
     int kfuse = 1;          // contour steps per propagator launch (1 = single-step kernels, 0 = persistent)
     int pers_bz = 0;        // brick depth of the persistent sweeps (0 = not available)
+    int wait_limit = kPersSpinLimit;   // polls before a persistent sweep gives up on a neighbour
     int nsm = 0;
     bool fusable = false;   // FP32 and every replica in the whole-row layout
     long long steps = 0;
@@ -266,8 +267,8 @@ int64_t enqueue_sweeps(dscf_ctx* c, const Launch& L) {
     if (K == 0) {
         const int nb = pers_bricks(c->L.reps[0], c->pers_bz);
         int* flags = c->d_status + kFlagBase;
-        launch_prop_pers(L, false, c->pers_bz, nb, flags, c->d_status + 2, kPersSpinLimit);
-        launch_prop_pers(L, true, c->pers_bz, nb, flags, c->d_status + 2, kPersSpinLimit);
+        launch_prop_pers(L, false, c->pers_bz, nb, flags, c->d_status + 2, c->wait_limit);
+        launch_prop_pers(L, true, c->pers_bz, nb, flags, c->d_status + 2, c->wait_limit);
         return 2;
     }
     if (K > 1) {
@@ -797,9 +798,52 @@ int dscf_status(dscf_ctx* c) {
     if (int rc = cuda_check(c, cudaGetLastError(), "status")) return rc;
     int st = 0;
     if (int rc = cuda_check(c, cudaMemcpy(&st, c->d_status, sizeof(int), cudaMemcpyDeviceToHost), "status read")) return rc;
-    if (st & ST_TIMEOUT) return fail(c, DSCF_ERR_TIMEOUT, "a persistent contour sweep gave up waiting for a neighbour");
+    if (st & ST_TIMEOUT) {
+        // The sweeps that ran since the timeout skipped their waits (the abort flag was set), so
+        // the fields are invalid, but every launch has finished.  Re-arm the brick step counters,
+        // the abort flag and the status bit so that the context can be used again once the
+        // caller has restored its fields.
+        cudaError_t e = cudaMemsetAsync(c->d_status + kFlagBase, 0, sizeof(int) * kMaxBricks, c->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(c->d_status + 2, 0, sizeof(int), c->stream);
+        const int clear = st & ~(int)ST_TIMEOUT;
+        if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_status, &clear, sizeof(int), cudaMemcpyHostToDevice, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        if (int rc = cuda_check(c, e, "re-arming after a timeout")) return rc;
+        return fail(c, DSCF_ERR_TIMEOUT, "a persistent contour sweep gave up waiting for a neighbour");
+    }
     if (st & ST_NONFINITE) return fail(c, DSCF_ERR_NUMERIC, "non-finite value in a reduction");
     return DSCF_OK;
+}
+
+int dscf_set_wait_limit(dscf_ctx* c, int32_t polls) {
+    if (!c) return DSCF_ERR_ARG;
+    if (polls < 1) return fail(c, DSCF_ERR_ARG, "polls must be >= 1");
+    if (int rc = set_dev(c)) return rc;
+    if (int rc = cuda_check(c, cudaStreamSynchronize(c->stream), "wait-limit sync")) return rc;
+    if (c->exec) {
+        cudaGraphExecDestroy(c->exec);
+        c->exec = nullptr;
+    }
+    if (c->exec_pred) {
+        cudaGraphExecDestroy(c->exec_pred);
+        c->exec_pred = nullptr;
+    }
+    c->wait_limit = polls;
+    return DSCF_OK;
+}
+
+int dscf_inject_lag(dscf_ctx* c, int32_t brick) {
+    if (!c) return DSCF_ERR_ARG;
+    if (!c->pers_bz || c->kfuse != 0) return fail(c, DSCF_ERR_STATE, "the context does not run persistent sweeps");
+    const int nb = pers_bricks(c->L.reps[0], c->pers_bz);
+    if (brick < 0 || brick >= nb) return fail(c, DSCF_ERR_ARG, "brick index out of range");
+    if (int rc = set_dev(c)) return rc;
+    // a counter far behind the others: the brick's neighbours wait for step values it never
+    // publishes during the next sweep, the brick itself sees its neighbours ahead and runs through
+    const int lag = -(1 << 24);
+    cudaError_t e = cudaMemcpyAsync(c->d_status + kFlagBase + brick, &lag, sizeof(int), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    return cuda_check(c, e, "inject lag");
 }
 
 int dscf_probe(dscf_ctx* c, int32_t enable) {

@@ -86,6 +86,8 @@ def load():
         "dscf_net_free": (ctypes.c_int, [vp]),
         "dscf_net_last_error": (ctypes.c_char_p, [vp]),
         "dscf_set_predictor": (ctypes.c_int, [vp, vp, i32, ctypes.c_double, i32]),
+        "dscf_set_wait_limit": (ctypes.c_int, [vp, i32]),
+        "dscf_inject_lag": (ctypes.c_int, [vp, i32]),
     }
     for name, (res, args) in sigs.items():
         fn = getattr(lib, name)
@@ -259,6 +261,14 @@ class Context:
         self._check(self.lib.dscf_set_predictor(self.h, net.h if net is not None else None, int(corrector_every),
                                                 float(tol), int(ncg_iters)))
         self._net = net
+
+    def set_wait_limit(self, polls):
+        """Polls a persistent sweep spends on a neighbour before it reports DSCF_ERR_TIMEOUT."""
+        self._check(self.lib.dscf_set_wait_limit(self.h, int(polls)))
+
+    def inject_lag(self, brick):
+        """Test hook: make brick's step counter lag so the next persistent sweep times out."""
+        self._check(self.lib.dscf_inject_lag(self.h, int(brick)))
 
     def set_tuning(self, zc, kfuse):
         self._check(self.lib.dscf_set_tuning(self.h, int(zc), int(kfuse)))

@@ -115,6 +115,36 @@ def test_persistent_sweeps_fp32_within_1e5(cfg):
         assert rel(got, ref) < 1e-5
 
 
+def test_persistent_sweep_timeout_is_reported_and_the_context_recovers():
+    """Failure detection without a GPU fault: one brick's step counter is set far behind (host
+    side), so its neighbours wait for a value nobody publishes; their bounded waits run out, the
+    abort flag releases every other CTA, the launch finishes and the host reads DSCF_ERR_TIMEOUT.
+    The same context then computes correct densities again."""
+    import time
+    cfg = PERSISTENT_CASES[0]
+    U = torch.from_numpy(inputs.random_field(ncomp_shape(cfg), seed=12, scale=0.5))
+    ctx = dscf.Context(cfg, dscf.FP32)
+    ctx.set_tuning(8, 0)
+    good = ctx.densities(U)
+    ctx.status()
+    ctx.set_wait_limit(2000)
+    ctx.inject_lag(0)
+    t0 = time.perf_counter()
+    ctx.densities(U)
+    with pytest.raises(dscf.DSCFError) as err:
+        ctx.status()
+    assert err.value.code == -4
+    assert time.perf_counter() - t0 < 30.0
+    ctx.status()                    # re-armed by the call that reported the timeout
+    again = ctx.densities(U)
+    ctx.status()
+    assert torch.equal(again, good)
+    with pytest.raises(dscf.DSCFError):
+        ctx.inject_lag(1000)
+    with pytest.raises(dscf.DSCFError):
+        ctx.set_wait_limit(0)
+
+
 def test_persistent_step_matches_multi_launch():
     cfg = melt((128, 16, 16), 8, 3, hydro=1, ncg_iters=2, cn_sweeps=4)
     phi, U, dn = random_state(cfg, 91)
