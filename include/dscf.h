@@ -259,6 +259,17 @@ int dscf_net_train_step(dscf_net* net, const float* U, const float* phi_target, 
 int dscf_net_get_params(dscf_net* net, float* dst);        /* dst: device or host */
 int dscf_net_set_params(dscf_net* net, const float* src);  /* resets the Adam moments */
 int64_t dscf_net_num_params(void);
+
+/* Tensor-core path of the network's forward convolutions.  path 0 (default): tcgen05 MMAs with
+ * operands in shared memory and accumulators in tensor memory where the grid allows it (nx a
+ * multiple of 128, ny of 4, sm_103 device), warp-level mma.sync otherwise; path 1: mma.sync
+ * always (the backward pass always uses mma.sync).  dscf_net_tensor_path returns 2 when the
+ * forward runs on tcgen05, 1 for mma.sync.  dscf_net_status synchronises and returns
+ * DSCF_ERR_TIMEOUT if a tcgen05 convolution gave up waiting for its MMAs (bounded wait; the
+ * output of that call is invalid), then clears the condition. */
+int dscf_net_set_tensor_path(dscf_net* net, int32_t path);
+int32_t dscf_net_tensor_path(const dscf_net* net);
+int dscf_net_status(dscf_net* net);
 int dscf_net_free(dscf_net* net);
 
 /* Use a trained network (same grid as the context, batch 1) as the density map inside the

@@ -315,10 +315,10 @@ int64_t enqueue_step(dscf_ctx* c, const Launch& L, bool pred = false) {
     for (int k = 0; k < K; ++k) {
         if (pred) {   // both evaluations of the iteration through the learned predictor
             launch_exp<T>(L, 1, k, nullptr, 1); ++n;
-            enqueue_net(c, L); n += 7;
+            enqueue_net(c, L); n += dscf_net_forward_launches(c->net);
             launch_trial<T>(L, 1); ++n;
             launch_exp<T>(L, 2, k, nullptr, 1); ++n;
-            enqueue_net(c, L); n += 7;
+            enqueue_net(c, L); n += dscf_net_forward_launches(c->net);
             launch_grad<T>(L, k, 1); ++n;
             if (k + 1 < K) { launch_dir<T>(L, 1, k); ++n; }
             continue;

@@ -231,7 +231,17 @@ int launch_prop_pers(const Launch& L, bool bwd, int bz, int nbricks, int* flags,
 
 }  // namespace dscf
 
+namespace dscf {
+// tcgen05 forward convolution of the predictor network (dscf_tc.cu)
+bool tc_conv_supported(int nx, int ny);
+size_t tc_conv_smem(int ci, int co);
+int tc_conv_prepare();   // cudaError_t
+int tc_conv_blocks(int nx, int ny, int nz);   // CTAs per sample
+void launch_conv_tc(int layer, const void* in, const void* wt, const float* bias, int cout, void* out, int nx, int ny,
+                    int nz, int B, double* part, int* err, cudaStream_t s);
+}  // namespace dscf
 // learned predictor (dscf_net.cu): forward pass on a given stream, for use inside the step graph
 struct dscf_net;
 bool dscf_net_fits(const dscf_net* net, int nx, int ny, int nz);
+int dscf_net_forward_launches(const dscf_net* n);   // kernels one forward pass launches
 void dscf_net_forward_on(dscf_net* net, cudaStream_t stream, const float* U, double pb0, double pb1, float* phi);

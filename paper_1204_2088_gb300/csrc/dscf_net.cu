@@ -4,8 +4,10 @@
 // in for the propagator solve inside the self-consistent inversion).
 //
 // Tensor cores: every convolution (forward, and backward with respect to the input) is one
-// implicit GEMM over (offset, input channel) in BF16 with FP32 accumulation (mma.sync
-// m16n8k16); weight gradients are per-offset GEMMs over sites.  Activations are stored
+// implicit GEMM over (offset, input channel) in BF16 with FP32 accumulation; weight gradients are
+// per-offset GEMMs over sites.  The forward convolutions run on tcgen05 (operands in shared
+// memory, accumulators in tensor memory; dscf_tc.cu) when nx is a multiple of 128 and ny of 4,
+// and with warp-level mma.sync m16n8k16 otherwise (and for the backward pass).  Activations are stored
 // channel-last in BF16 with channel counts padded to multiples of 16 (zero weights in the pad).
 // Training keeps FP32 master weights and Adam moments.
 #include <cuda_bf16.h>
@@ -223,21 +225,24 @@ __global__ void k_chan_parts_cl(const float* __restrict__ f, int C, int CS, int 
     const double t = block_sum((double)acc, sh);
     if (threadIdx.x == 0) part[((size_t)b * C + c) * gridDim.x + blockIdx.x] = t;
 }
-__device__ __forceinline__ double chan_mean(const double* part, int nb, int V) {
-    double s = 0.0;
-    for (int i = 0; i < nb; ++i) s += part[i];
-    return s / (double)V;
+// means[p] = (sum of the nb partials of pair p, fixed order) / V, one block per pair.
+__global__ void k_chan_final(const double* __restrict__ part, int nb, int V, double* __restrict__ means) {
+    __shared__ double sh[33];
+    const double* q = part + (size_t)blockIdx.x * nb;
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) acc += q[i];
+    const double t = block_sum(acc, sh);
+    if (threadIdx.x == 0) means[blockIdx.x] = t / (double)V;
 }
 
 // Network input: x[r][c] = U_c[r] - <U_c> (c < 2), zero in the padded channels.
-__global__ void k_net_in(const float* __restrict__ U, const double* __restrict__ part, int nb, int V, int B,
+__global__ void k_net_in(const float* __restrict__ U, const double* __restrict__ means, int V, int B,
                          bf16* __restrict__ x) {
     const size_t r = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
     if (r >= (size_t)B * V) return;
     const int b = (int)(r / V);
     const size_t i = r - (size_t)b * V;
-    const float m0 = (float)chan_mean(part + (size_t)(2 * b) * nb, nb, V);
-    const float m1 = (float)chan_mean(part + (size_t)(2 * b + 1) * nb, nb, V);
+    const float m0 = (float)means[2 * b], m1 = (float)means[2 * b + 1];
     __align__(16) bf16 v[16];
 #pragma unroll
     for (int c = 0; c < 16; ++c) v[c] = __float2bfloat16(0.f);
@@ -249,14 +254,13 @@ __global__ void k_net_in(const float* __restrict__ U, const double* __restrict__
 }
 
 // Network output: phi_c[r] = phibar_c + y[r][c] - <y_c>  ([B][2][V] float).
-__global__ void k_net_out(const float* __restrict__ y, const double* __restrict__ part, int nb, int V, int B,
-                          double pb0, double pb1, float* __restrict__ phi) {
+__global__ void k_net_out(const float* __restrict__ y, const double* __restrict__ means, int V, int B, double pb0,
+                          double pb1, float* __restrict__ phi) {
     const size_t r = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
     if (r >= (size_t)B * V) return;
     const int b = (int)(r / V);
     const size_t i = r - (size_t)b * V;
-    const double m0 = chan_mean(part + (size_t)(2 * b) * nb, nb, V);
-    const double m1 = chan_mean(part + (size_t)(2 * b + 1) * nb, nb, V);
+    const double m0 = means[2 * b], m1 = means[2 * b + 1];
     phi[((size_t)2 * b) * V + i] = (float)(pb0 - m0) + y[r * 16];
     phi[((size_t)2 * b + 1) * V + i] = (float)(pb1 - m1) + y[r * 16 + 1];
 }
@@ -275,14 +279,13 @@ __global__ void k_loss_g(const float* __restrict__ phi, const float* __restrict_
     const double t = block_sum((double)acc, sh);
     if (threadIdx.x == 0) lpart[blockIdx.x] = t;
 }
-__global__ void k_dy(const float* __restrict__ g, const double* __restrict__ part, int nb, int V, int B,
+__global__ void k_dy(const float* __restrict__ g, const double* __restrict__ means, int V, int B,
                      bf16* __restrict__ dy) {
     const size_t r = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
     if (r >= (size_t)B * V) return;
     const int b = (int)(r / V);
     const size_t i = r - (size_t)b * V;
-    const float m0 = (float)chan_mean(part + (size_t)(2 * b) * nb, nb, V);
-    const float m1 = (float)chan_mean(part + (size_t)(2 * b + 1) * nb, nb, V);
+    const float m0 = (float)means[2 * b], m1 = (float)means[2 * b + 1];
     __align__(16) bf16 v[16];
 #pragma unroll
     for (int c = 0; c < 16; ++c) v[c] = __float2bfloat16(0.f);
@@ -315,6 +318,20 @@ __global__ void k_prep_w(const float* __restrict__ W, int cin, int cout, int cin
     }
 }
 
+// BF16 weights of layer l in the tcgen05 operand layout Wt[o][ci / 8][co][ci % 8] (zero in
+// padded channels): for each offset and group of 8 input channels, 8 output channels x 16 bytes
+// form one contiguous core matrix.
+__global__ void k_prep_wt(const float* __restrict__ W, int cin, int cout, int cinp, int coutp, bf16* __restrict__ Wt) {
+    const int n = KVOL * coutp * cinp;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int o = i / (coutp * cinp), rem = i % (coutp * cinp);
+        const int kc = rem / (coutp * 8), r2 = rem % (coutp * 8);
+        const int co = r2 / 8, ci = kc * 8 + r2 % 8;
+        const float v = (co < cout && ci < cin) ? W[((size_t)co * cin + ci) * KVOL + o] : 0.f;
+        Wt[i] = __float2bfloat16(v);
+    }
+}
+
 // Adam (FP32 master weights).
 __global__ void k_adam(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m, float* __restrict__ v,
                        int n, float lr, float b1, float b2, float eps, float c1, float c2) {
@@ -331,9 +348,10 @@ __global__ void k_adam(float* __restrict__ p, const float* __restrict__ g, float
 size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct NetLayout {
-    size_t params, grads, m, v, wf[NL], wb[NL], x16, h1, h2, y16, dy16, dz2, dz1, gtmp, part, lpart, bytes;
+    size_t params, grads, m, v, wf[NL], wb[NL], wt[NL], x16, h1, h2, y16, dy16, dz2, dz1, gtmp, part, means, lpart, err,
+        bytes;
 };
-constexpr int kPartBlocks = 64;
+constexpr int kPartBlocks = 512;   // partial sums per channel and sample
 
 NetLayout net_layout(int nx, int ny, int nz, int B) {
     NetLayout L;
@@ -347,6 +365,7 @@ NetLayout net_layout(int nx, int ny, int nz, int B) {
     for (int l = 0; l < NL; ++l) {
         L.wf[l] = take((size_t)KVOL * COUTP[l] * CINP[l] * 2);
         L.wb[l] = take((size_t)KVOL * COUTP[l] * CINP[l] * 2);
+        L.wt[l] = take((size_t)KVOL * COUTP[l] * CINP[l] * 2);
     }
     L.x16 = take(S * 16 * 2);
     L.h1 = take(S * 32 * 2);
@@ -356,8 +375,11 @@ NetLayout net_layout(int nx, int ny, int nz, int B) {
     L.dz2 = take(S * 32 * 2);
     L.dz1 = take(S * 32 * 2);
     L.gtmp = take(S * 2 * 4);
-    L.part = take((size_t)B * 2 * kPartBlocks * 8);
+    const size_t ntc = tc_conv_supported(nx, ny) ? (size_t)tc_conv_blocks(nx, ny, nz) : 0;
+    L.part = take((size_t)B * 2 * (ntc > (size_t)kPartBlocks ? ntc : (size_t)kPartBlocks) * 8);
+    L.means = take((size_t)B * 2 * 8);
     L.lpart = take((size_t)1024 * 8);
+    L.err = take(sizeof(int));
     L.bytes = off;
     return L;
 }
@@ -379,7 +401,10 @@ struct dscf_net {
     char* ws;
     NetLayout L;
     int adam_t = 0;
+    int path = 0;          // 0: tcgen05 forward where the grid allows it, 1: mma.sync only
+    bool tc_ok = false;    // grid and device allow the tcgen05 forward
     std::string err;
+    bool use_tc() const { return tc_ok && path == 0; }
     template <typename P> P* at(size_t off) { return (P*)(ws + off); }
 };
 
@@ -399,10 +424,17 @@ void prep_weights(dscf_net* n) {
     for (int l = 0; l < NL; ++l)
         k_prep_w<<<64, 256, 0, n->stream>>>(n->at<float>(n->L.params) + poff(l), CIN[l], COUT[l], CINP[l], COUTP[l],
                                               n->at<bf16>(n->L.wf[l]), l > 0 ? n->at<bf16>(n->L.wb[l]) : nullptr);
+    if (n->tc_ok)
+        for (int l = 0; l < NL; ++l)
+            k_prep_wt<<<64, 256, 0, n->stream>>>(n->at<float>(n->L.params) + poff(l), CIN[l], COUT[l], CINP[l], COUTP[l],
+                                                   n->at<bf16>(n->L.wt[l]));
 }
 
+// means of C = 2 channels of a [B][C][V] field into L.means
 void chan_means(dscf_net* n, const float* f, int C) {
     k_chan_parts<<<dim3(kPartBlocks, C, n->B), 256, 0, n->stream>>>(f, C, (int)n->V, n->at<double>(n->L.part));
+    k_chan_final<<<C * n->B, 256, 0, n->stream>>>(n->at<double>(n->L.part), kPartBlocks, (int)n->V,
+                                                  n->at<double>(n->L.means));
 }
 
 // forward pass from U ([B][2][V] float, device) to phi ([B][2][V] float, device)
@@ -412,20 +444,31 @@ void forward(dscf_net* n, const float* U, double pb0, double pb1, float* phi) {
     const int blocks = (ntiles + 3) / 4;
     const int eb = (int)((n->V * B + 255) / 256);
     chan_means(n, U, 2);
-    k_net_in<<<eb, 256, 0, n->stream>>>(U, n->at<double>(n->L.part), kPartBlocks, V, B, n->at<bf16>(n->L.x16));
-    k_conv<16, 32, EPI_TANH><<<blocks, 128, 0, n->stream>>>(n->at<bf16>(n->L.x16), n->at<bf16>(n->L.wf[0]),
-        n->at<float>(n->L.params) + poff(0) + wcount(0), 32, nullptr, n->at<bf16>(n->L.h1), n->nx, n->ny, n->nz, ntiles,
-        nullptr);
-    k_conv<32, 32, EPI_TANH><<<blocks, 128, 0, n->stream>>>(n->at<bf16>(n->L.h1), n->at<bf16>(n->L.wf[1]),
-        n->at<float>(n->L.params) + poff(1) + wcount(1), 32, nullptr, n->at<bf16>(n->L.h2), n->nx, n->ny, n->nz, ntiles,
-        nullptr);
-    k_conv<32, 16, EPI_LIN_F32><<<blocks, 128, 0, n->stream>>>(n->at<bf16>(n->L.h2), n->at<bf16>(n->L.wf[2]),
-        n->at<float>(n->L.params) + poff(2) + wcount(2), 2, nullptr, n->at<float>(n->L.y16), n->nx, n->ny, n->nz, ntiles,
-        nullptr);
-    k_chan_parts_cl<<<dim3(kPartBlocks, 2, B), 256, 0, n->stream>>>(n->at<float>(n->L.y16), 2, 16, V,
-                                                                     n->at<double>(n->L.part));
-    k_net_out<<<eb, 256, 0, n->stream>>>(n->at<float>(n->L.y16), n->at<double>(n->L.part), kPartBlocks, V, B, pb0, pb1,
-                                         phi);
+    k_net_in<<<eb, 256, 0, n->stream>>>(U, n->at<double>(n->L.means), V, B, n->at<bf16>(n->L.x16));
+    if (n->use_tc()) {
+        const size_t act[NL + 1] = {n->L.x16, n->L.h1, n->L.h2, n->L.y16};
+        for (int l = 0; l < NL; ++l)
+            launch_conv_tc(l, n->ws + act[l], n->ws + n->L.wt[l], n->at<float>(n->L.params) + poff(l) + wcount(l),
+                           COUT[l], n->ws + act[l + 1], n->nx, n->ny, n->nz, B, n->at<double>(n->L.part),
+                           n->at<int>(n->L.err), n->stream);
+        // the output layer left per-CTA sums of its two channels
+        k_chan_final<<<2 * B, 256, 0, n->stream>>>(n->at<double>(n->L.part), tc_conv_blocks(n->nx, n->ny, n->nz), V,
+                                                   n->at<double>(n->L.means));
+    } else {
+        k_conv<16, 32, EPI_TANH><<<blocks, 128, 0, n->stream>>>(n->at<bf16>(n->L.x16), n->at<bf16>(n->L.wf[0]),
+            n->at<float>(n->L.params) + poff(0) + wcount(0), 32, nullptr, n->at<bf16>(n->L.h1), n->nx, n->ny, n->nz, ntiles,
+            nullptr);
+        k_conv<32, 32, EPI_TANH><<<blocks, 128, 0, n->stream>>>(n->at<bf16>(n->L.h1), n->at<bf16>(n->L.wf[1]),
+            n->at<float>(n->L.params) + poff(1) + wcount(1), 32, nullptr, n->at<bf16>(n->L.h2), n->nx, n->ny, n->nz, ntiles,
+            nullptr);
+        k_conv<32, 16, EPI_LIN_F32><<<blocks, 128, 0, n->stream>>>(n->at<bf16>(n->L.h2), n->at<bf16>(n->L.wf[2]),
+            n->at<float>(n->L.params) + poff(2) + wcount(2), 2, nullptr, n->at<float>(n->L.y16), n->nx, n->ny, n->nz, ntiles,
+            nullptr);
+        k_chan_parts_cl<<<dim3(kPartBlocks, 2, B), 256, 0, n->stream>>>(n->at<float>(n->L.y16), 2, 16, V,
+                                                                         n->at<double>(n->L.part));
+        k_chan_final<<<2 * B, 256, 0, n->stream>>>(n->at<double>(n->L.part), kPartBlocks, V, n->at<double>(n->L.means));
+    }
+    k_net_out<<<eb, 256, 0, n->stream>>>(n->at<float>(n->L.y16), n->at<double>(n->L.means), V, B, pb0, pb1, phi);
 }
 
 // gradient of 0.5 mean((phi - target)^2) with respect to all parameters, into grads
@@ -439,8 +482,7 @@ void backward(dscf_net* n, const float* phi, const float* tgt) {
     cudaMemsetAsync(grads, 0, NPARAM * 4, n->stream);
     k_loss_g<<<1024, 256, 0, n->stream>>>(phi, tgt, S * 2, n->at<float>(n->L.gtmp), n->at<double>(n->L.lpart));
     chan_means(n, n->at<float>(n->L.gtmp), 2);
-    k_dy<<<eb, 256, 0, n->stream>>>(n->at<float>(n->L.gtmp), n->at<double>(n->L.part), kPartBlocks, V, B,
-                                    n->at<bf16>(n->L.dy16));
+    k_dy<<<eb, 256, 0, n->stream>>>(n->at<float>(n->L.gtmp), n->at<double>(n->L.means), V, B, n->at<bf16>(n->L.dy16));
     const int chunk = 8;
     const int wblocks = (ntiles + 4 * chunk - 1) / (4 * chunk);
     // layer 3
@@ -473,6 +515,7 @@ double u01(uint64_t seed, uint64_t k) {
 bool dscf_net_fits(const dscf_net* n, int nx, int ny, int nz) {
     return n && n->nx == nx && n->ny == ny && n->nz == nz && n->B == 1;
 }
+int dscf_net_forward_launches(const dscf_net* n) { return n->use_tc() ? 8 : 9; }
 void dscf_net_forward_on(dscf_net* n, cudaStream_t stream, const float* U, double pb0, double pb1, float* phi) {
     cudaStream_t keep = n->stream;
     n->stream = stream;
@@ -508,6 +551,13 @@ int dscf_net_init(int32_t nx, int32_t ny, int32_t nz, int32_t batch, uint64_t se
     n->ws = (char*)workspace;
     n->L = net_layout(nx, ny, nz, batch);
     cudaSetDevice(n->device);
+    {
+        int major = 0, minor = 0;
+        cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, n->device);
+        cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, n->device);
+        n->tc_ok = tc_conv_supported(nx, ny) && major == 10 && minor == 3 && tc_conv_prepare() == 0;
+        cudaGetLastError();
+    }
     // Glorot-like normal initial weights, zero biases
     std::vector<float> p(NPARAM, 0.f);
     uint64_t k = 0;
@@ -522,6 +572,7 @@ int dscf_net_init(int32_t nx, int32_t ny, int32_t nz, int32_t batch, uint64_t se
     int rc = ncheck(n, cudaMemcpy(n->at<float>(n->L.params), p.data(), NPARAM * 4, cudaMemcpyHostToDevice), "params");
     if (!rc) rc = ncheck(n, cudaMemset(n->at<float>(n->L.m), 0, NPARAM * 4), "m");
     if (!rc) rc = ncheck(n, cudaMemset(n->at<float>(n->L.v), 0, NPARAM * 4), "v");
+    if (!rc) rc = ncheck(n, cudaMemset(n->at<int>(n->L.err), 0, sizeof(int)), "error word");
     if (!rc) {
         prep_weights(n);
         rc = ncheck(n, cudaStreamSynchronize(n->stream), "init");
@@ -592,6 +643,32 @@ int dscf_net_set_params(dscf_net* n, const float* src) {
 }
 
 int64_t dscf_net_num_params(void) { return (int64_t)NPARAM; }
+
+int dscf_net_set_tensor_path(dscf_net* n, int32_t path) {
+    if (!n) return DSCF_ERR_ARG;
+    if (path != 0 && path != 1) return nfail(n, DSCF_ERR_ARG, "path must be 0 (tcgen05 where possible) or 1 (mma.sync)");
+    cudaSetDevice(n->device);
+    int rc = ncheck(n, cudaStreamSynchronize(n->stream), "path sync");
+    if (rc) return rc;
+    n->path = path;
+    return DSCF_OK;
+}
+
+int32_t dscf_net_tensor_path(const dscf_net* n) { return n ? (n->use_tc() ? 2 : 1) : 0; }
+
+int dscf_net_status(dscf_net* n) {
+    if (!n) return DSCF_ERR_ARG;
+    cudaSetDevice(n->device);
+    int e = 0;
+    int rc = ncheck(n, cudaStreamSynchronize(n->stream), "status sync");
+    if (!rc) rc = ncheck(n, cudaMemcpy(&e, n->at<int>(n->L.err), sizeof(int), cudaMemcpyDeviceToHost), "status read");
+    if (rc) return rc;
+    if (e) {
+        cudaMemset(n->at<int>(n->L.err), 0, sizeof(int));
+        return nfail(n, DSCF_ERR_TIMEOUT, "a tensor-core convolution gave up waiting for its MMAs");
+    }
+    return DSCF_OK;
+}
 
 int dscf_net_free(dscf_net* n) {
     delete n;

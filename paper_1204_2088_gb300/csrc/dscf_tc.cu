@@ -1,0 +1,351 @@
+// Forward 5^3 circular convolution of the learned predictor on the 5th-generation tensor cores
+// (tcgen05: operands in shared memory, FP32 accumulators in tensor memory), for grids whose x
+// extent is a multiple of 128.
+//
+// GEMM view: for an output row of 128 sites along x, D[x][co] = sum over the 125 offsets
+// (dz, dy, dx) and input channels ci of A[x][ci] B[co][ci] with A the input row (y+dy, z+dz)
+// shifted by dx.  One CTA computes 4 output rows (y0..y0+3, z, x0..x0+127) into 4 TMEM
+// accumulators of 128 lanes x CO columns.  For each dz it stages the 8 input rows y0-2..y0+5 of
+// plane z+dz (periodic) in shared memory in the no-swizzle K-major operand layout
+//   [row][channel group of 8][x' = 0..131][8 channels]  (x' = x - x0 + 2),
+// in which 8 consecutive sites of one channel group form a contiguous 128-byte core matrix: the
+// descriptor has 128 B between core matrices along M (sites) and 132 x 16 B between channel
+// groups along K, and the shift by dx is just 16 dx bytes added to its start address.  The
+// weights of the (dy, dx) offsets of that dz are staged in two halves (dy 0..2, dy 3..4) as
+// [offset][channel group][co][8], the same layout for the N x K operand; the smaller footprint
+// lets two CTAs share an SM, one staging while the other's MMAs run.  One thread issues the M = 128, N = CO, K = 16 MMAs; a
+// tcgen05.commit on an mbarrier tells the CTA when the staged operands may be overwritten, and
+// after the last dz when the accumulators are complete.  The epilogue (bias, tanh, BF16 or FP32
+// channel-last stores) reads each warp's quarter of the TMEM lanes with tcgen05.ld.
+//
+// Every wait is bounded; a CTA that gives up sets the error word, frees its tensor memory and
+// returns.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "dscf_internal.cuh"
+
+namespace dscf {
+
+namespace {
+
+typedef __nv_bfloat16 bf16;
+
+constexpr int TC_R = 4;            // output rows per CTA
+constexpr int TC_XP = 132;         // staged row length (128 + 2 on each side)
+constexpr int TC_THREADS = 256;  // 8 warps: staging; epilogue pairs of warps per TMEM lane quarter
+constexpr int TC_TMEM_COLS = 128;  // >= TC_R * CO for CO <= 32
+constexpr long long kTcSpinLimit = 1ll << 20;   // try_wait polls (each may suspend ~1 us)
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void cp16(void* s, const void* g) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_u32(s)), "l"(g));
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+__device__ __forceinline__ void cp_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// Shared-memory matrix descriptor (no swizzle): start address, leading-dimension byte offset
+// (between core matrices along K), stride-dimension byte offset (between 8-row core-matrix
+// groups along M or N), descriptor version 1 in bits 46-47.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 46;
+    return d;
+}
+
+// Instruction descriptor of kind::f16: FP32 accumulator (bits 4-5 = 1), BF16 A and B (bits 7-9
+// and 10-12 = 1), both K-major, N >> 3 in bits 17-22, M >> 4 in bits 24-28.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc, int accum) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(dtmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum));
+}
+__device__ __forceinline__ void mma_commit(uint64_t* mbar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                     smem_u32(mbar))
+                 : "memory");
+}
+__device__ __forceinline__ void fence_before_sync() { asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory"); }
+__device__ __forceinline__ void fence_after_sync() { asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* mbar, int count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(mbar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ int mbar_try_wait(uint64_t* mbar, uint32_t parity) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred P1;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 P1, [%1], %2;\n\t"
+        "selp.b32 %0, 1, 0, P1;\n\t}\n"
+        : "=r"(done)
+        : "r"(smem_u32(mbar)), "r"(parity)
+        : "memory");
+    return (int)done;
+}
+// Bounded wait on an mbarrier phase; false if the limit ran out.
+__device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity) {
+    for (long long i = 0; i < kTcSpinLimit; ++i)
+        if (mbar_try_wait(mbar, parity)) return true;
+    return false;
+}
+
+// 32 consecutive FP32 columns of this warp's 32 TMEM lanes (one lane per thread).
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+          "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15}, [%16];\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ int wrapi_(int v, int n) {
+    v %= n;
+    return v < 0 ? v + n : v;
+}
+
+// EPI 0: tanh(acc + bias) -> BF16 [site][CO]; EPI 1: acc + bias -> FP32 [site][16] (CO = 16),
+// and the CTA's FP64 sums of channels 0 and 1 into part[(b * 2 + c) * nblk + i] (i: the CTA's
+// index within its sample, nblk: CTAs per sample), for the network's mean removal.
+// in: [B][V][CI] BF16 channel-last; wt: [125][CI/8][CO][8] BF16; bias: cout values.
+template <int CI, int CO, int EPI>
+__global__ void __launch_bounds__(TC_THREADS, 2)
+    k_conv_tc(const bf16* __restrict__ in, const bf16* __restrict__ wt, const float* __restrict__ bias, int cout,
+              void* __restrict__ out, int nx, int ny, int nz, double* __restrict__ part, int* __restrict__ err) {
+    constexpr int G = CI / 8;                       // channel groups of 16 bytes
+    constexpr int ROWB = G * TC_XP * 16;            // bytes of one staged row
+    constexpr int ABYTES = (TC_R + 4) * ROWB;
+    constexpr int OFFB = G * CO * 16;               // bytes of the weights of one offset
+    constexpr uint32_t IDESC = idesc_bf16(128, CO);
+    static_assert(TC_R * CO <= TC_TMEM_COLS, "accumulators exceed the tensor-memory allocation");
+    static_assert(CO == 16 || CO == 32, "CO");
+    static_assert(CI % 16 == 0, "CI");
+    extern __shared__ __align__(1024) unsigned char smem[];
+    unsigned char* As = smem;
+    unsigned char* Ws = smem + ABYTES;
+    __shared__ __align__(8) uint64_t mbar;
+    __shared__ uint32_t tmem_slot;
+    __shared__ float csum[TC_THREADS / 32][2];
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int nxt = nx / 128, nyb = ny / TC_R;
+    int blk = blockIdx.x;
+    const int xt = blk % nxt;
+    blk /= nxt;
+    const int yb = blk % nyb;
+    blk /= nyb;
+    const int z = blk % nz, b = blk / nz;
+    const int x0 = xt * 128, y0 = yb * TC_R;
+    const size_t V = (size_t)nx * ny * nz;
+    const bf16* inb = in + (size_t)b * V * CI;
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(&tmem_slot)),
+                     "r"(TC_TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+    }
+    if (tid == 0) {
+        mbar_init(&mbar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+    const uint32_t tmem = tmem_slot;
+
+    // this thread's staging slots within a row: chunk c = tid + k * TC_THREADS of the
+    // TC_XP * G chunks; consecutive threads read consecutive 16-byte channel groups of one site
+    constexpr int RCH = TC_XP * G;
+    constexpr int KCH = (RCH + TC_THREADS - 1) / TC_THREADS;
+    int soff[KCH], goff[KCH];
+#pragma unroll
+    for (int k = 0; k < KCH; ++k) {
+        const int c = tid + k * TC_THREADS;
+        const int g = c % G, xp = c / G;
+        int x = x0 - 2 + xp;
+        x = x < 0 ? x + nx : (x >= nx ? x - nx : x);
+        soff[k] = c < RCH ? (g * TC_XP + xp) * 16 : -1;
+        goff[k] = x * CI + g * 8;
+    }
+
+    bool ok = true;
+    int phase = 0;
+    for (int dzi = 0; dzi < 5 && ok; ++dzi) {
+        int zin = z + dzi - 2;
+        zin = zin < 0 ? zin + nz : (zin >= nz ? zin - nz : zin);
+        // the 8 input rows y0-2 .. y0+5 of plane zin
+#pragma unroll 1
+        for (int i = 0; i < TC_R + 4; ++i) {
+            const int yin = wrapi_(y0 - 2 + i, ny);
+            const bf16* src = inb + ((size_t)zin * ny + yin) * nx * CI;
+            unsigned char* dst = As + i * ROWB;
+#pragma unroll
+            for (int k = 0; k < KCH; ++k)
+                if (soff[k] >= 0) cp16(dst + soff[k], src + goff[k]);
+        }
+        // two halves of the 25 (dy, dx) offsets: dy 0..2, then dy 3..4
+#pragma unroll 1
+        for (int h = 0; h < 2 && ok; ++h) {
+            const int dy0 = h ? 3 : 0, dy1 = h ? 5 : 3;
+            const bf16* wsrc = wt + ((size_t)dzi * 25 + dy0 * 5) * G * CO * 8;
+            const int nbytes = (dy1 - dy0) * 5 * OFFB;
+            for (int c = tid; c < nbytes / 16; c += TC_THREADS) cp16(Ws + (size_t)c * 16, wsrc + (size_t)c * 8);
+            cp_commit();
+            cp_wait_all();
+            fence_proxy_async();   // the tensor cores read shared memory through the async proxy
+            __syncthreads();
+            if (tid == 0) {
+                fence_after_sync();
+                const uint32_t a0 = smem_u32(As), w0 = smem_u32(Ws);
+                for (int r = 0; r < TC_R; ++r)
+                    for (int dyi = dy0; dyi < dy1; ++dyi)
+                        for (int dxi = 0; dxi < 5; ++dxi)
+#pragma unroll
+                            for (int kk = 0; kk < CI / 16; ++kk) {
+                                const uint32_t aaddr = a0 + (uint32_t)(((r + dyi) * G + 2 * kk) * TC_XP + dxi) * 16u;
+                                const uint32_t baddr =
+                                    w0 + (uint32_t)((((dyi - dy0) * 5 + dxi) * G + 2 * kk) * CO) * 16u;
+                                mma_bf16(tmem + (uint32_t)(r * CO), smem_desc(aaddr, TC_XP * 16, 128),
+                                         smem_desc(baddr, CO * 16, 128), IDESC, (dzi | dyi | dxi | kk) != 0);
+                            }
+                mma_commit(&mbar);   // arrives once every MMA above has completed
+            }
+            const bool done = mbar_wait(&mbar, (uint32_t)(phase & 1));
+            ++phase;
+            if (!done) atomicOr(err, 1);
+            ok = __syncthreads_and(done ? 1 : 0) != 0;
+        }
+    }
+    fence_after_sync();
+    float s0 = 0.f, s1 = 0.f;
+    if (ok) {
+        // warps w and w + 4 share TMEM lane quarter w % 4 and take half of the rows each
+        const int q = warp & 3;
+        const int x = x0 + q * 32 + lane;
+        const uint32_t tq = tmem + ((uint32_t)(q * 32) << 16);
+#pragma unroll 1
+        for (int r = (warp >> 2) * (TC_R / 2); r < ((warp >> 2) + 1) * (TC_R / 2); ++r) {
+            float v[CO];
+            if (CO == 32) tmem_ld32(tq + (uint32_t)(r * CO), v);
+            else tmem_ld16(tq + (uint32_t)(r * CO), v);
+            const size_t site = (size_t)b * V + ((size_t)z * ny + (y0 + r)) * nx + x;
+#pragma unroll
+            for (int co = 0; co < CO; ++co) v[co] += (co < cout) ? bias[co] : 0.f;
+            if (EPI == 0) {
+                __align__(16) bf16 hv[CO];
+#pragma unroll
+                for (int co = 0; co < CO; ++co) hv[co] = __float2bfloat16(tanhf(v[co]));
+                uint4* dst = (uint4*)((bf16*)out + site * CO);
+#pragma unroll
+                for (int k = 0; k < CO / 8; ++k) dst[k] = ((const uint4*)hv)[k];
+            } else {
+                float4* dst = (float4*)((float*)out + site * 16);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) dst[k] = make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+                s0 += v[0];
+                s1 += v[1];
+            }
+        }
+    }
+    if (EPI == 1) {   // fixed-order CTA sums of the two output channels
+#pragma unroll
+        for (int m = 16; m > 0; m >>= 1) {
+            s0 += __shfl_xor_sync(0xffffffffu, s0, m);
+            s1 += __shfl_xor_sync(0xffffffffu, s1, m);
+        }
+        if (lane == 0) {
+            csum[warp][0] = s0;
+            csum[warp][1] = s1;
+        }
+        __syncthreads();
+        if (tid < 2) {
+            double t = 0.0;
+            for (int w = 0; w < TC_THREADS / 32; ++w) t += (double)csum[w][tid];
+            const int nblk = nz * nyb * nxt;
+            part[((size_t)b * 2 + tid) * nblk + (blockIdx.x - (size_t)b * nblk)] = t;
+        }
+    }
+    fence_before_sync();
+    __syncthreads();
+    if (warp == 0) {
+        fence_after_sync();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(TC_TMEM_COLS)
+                     : "memory");
+    }
+}
+
+}  // namespace
+
+// Bytes of dynamic shared memory of the kernel for CI input and CO output channels: the staged
+// input rows and the staged weights of half a dz (every operand address the MMAs form lies inside
+// them: the A walk ends at the last staged row, the B walk at the last offset's weights).
+size_t tc_conv_smem(int ci, int co) {
+    const size_t a = (size_t)(TC_R + 4) * (ci / 8) * TC_XP * 16;
+    const size_t w = (size_t)15 * (ci / 8) * co * 16;   // the larger half (dy 0..2) of one dz
+    return a + w;
+}
+
+bool tc_conv_supported(int nx, int ny) { return nx % 128 == 0 && ny % TC_R == 0; }
+
+int tc_conv_prepare() {
+    cudaError_t e = cudaFuncSetAttribute(k_conv_tc<16, 32, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)tc_conv_smem(16, 32));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_conv_tc<32, 32, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)tc_conv_smem(32, 32));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_conv_tc<32, 16, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)tc_conv_smem(32, 16));
+    return (int)e;
+}
+
+// Layer l of the predictor network (0: 16 -> 32 tanh, 1: 32 -> 32 tanh, 2: 32 -> 16 linear FP32)
+// over B samples of an nx x ny x nz grid (tc_conv_supported must hold).
+int tc_conv_blocks(int nx, int ny, int nz) { return nz * (ny / TC_R) * (nx / 128); }
+
+void launch_conv_tc(int layer, const void* in, const void* wt, const float* bias, int cout, void* out, int nx, int ny,
+                    int nz, int B, double* part, int* err, cudaStream_t s) {
+    const int blocks = B * nz * (ny / TC_R) * (nx / 128);
+    if (layer == 0)
+        k_conv_tc<16, 32, 0><<<blocks, TC_THREADS, tc_conv_smem(16, 32), s>>>((const bf16*)in, (const bf16*)wt, bias,
+                                                                              cout, out, nx, ny, nz, part, err);
+    else if (layer == 1)
+        k_conv_tc<32, 32, 0><<<blocks, TC_THREADS, tc_conv_smem(32, 32), s>>>((const bf16*)in, (const bf16*)wt, bias,
+                                                                              cout, out, nx, ny, nz, part, err);
+    else
+        k_conv_tc<32, 16, 1><<<blocks, TC_THREADS, tc_conv_smem(32, 16), s>>>((const bf16*)in, (const bf16*)wt, bias,
+                                                                              cout, out, nx, ny, nz, part, err);
+}
+
+}  // namespace dscf

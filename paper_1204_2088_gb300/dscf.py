@@ -87,6 +87,9 @@ def load():
         "dscf_net_last_error": (ctypes.c_char_p, [vp]),
         "dscf_set_predictor": (ctypes.c_int, [vp, vp, i32, ctypes.c_double, i32]),
         "dscf_set_wait_limit": (ctypes.c_int, [vp, i32]),
+        "dscf_net_set_tensor_path": (ctypes.c_int, [vp, i32]),
+        "dscf_net_tensor_path": (i32, [vp]),
+        "dscf_net_status": (ctypes.c_int, [vp]),
         "dscf_inject_lag": (ctypes.c_int, [vp, i32]),
     }
     for name, (res, args) in sigs.items():
@@ -359,6 +362,17 @@ class Net:
                                                  ctypes.byref(loss) if want_loss else None))
         self._keep = (U, target)
         return loss.value if want_loss else None
+
+    def set_tensor_path(self, path):
+        """0: tcgen05 forward where the grid allows it (default), 1: mma.sync only."""
+        self._check(self.lib.dscf_net_set_tensor_path(self.h, int(path)))
+
+    def tensor_path(self):
+        """2 if the forward convolutions run on tcgen05, 1 for mma.sync."""
+        return int(self.lib.dscf_net_tensor_path(self.h))
+
+    def status(self):
+        self._check(self.lib.dscf_net_status(self.h))
 
     def get_params(self):
         p = torch.empty(self.nparam, dtype=torch.float32, device=self.device)

@@ -272,3 +272,48 @@ def test_trained_predictor_gain_over_the_exact_method():
     assert torch.isfinite(phi).all()
     assert dev < 2 * tol, dev
     assert t_ref / t_pred > 1.1, (t_ref, t_pred, d)
+
+
+def test_tcgen05_forward_matches_mma_sync_and_fp64_network():
+    """Forward convolutions on tcgen05 (operands in shared memory, accumulators in tensor memory)
+    on a 128-wide grid: the same network on the warp-level mma.sync path agrees up to FP32
+    summation order and the BF16 rounding it can flip, and both match the FP64 CPU network within
+    the BF16 bound."""
+    grid, B = (128, 8, 6), 2
+    net = dscf.Net(grid, B, seed=13)
+    assert net.tensor_path() == 2
+    params = dscf.net_params_split(net.get_params().cpu().numpy())
+    nx, ny, nz = grid
+    U = inputs.random_field((B, 2, nz, ny, nx), seed=301, scale=0.6)
+    phibar = [0.3, 0.7]
+    Ut = torch.from_numpy(U).float()
+    tc = net.forward(Ut, phibar).cpu().numpy()
+    net.status()
+    net.set_tensor_path(1)
+    assert net.tensor_path() == 1
+    ms = net.forward(Ut, phibar).cpu().numpy()
+    net.set_tensor_path(0)
+    pb = np.array(phibar)[None, :, None, None, None]
+    dev = ms - pb
+    assert np.abs(tc - ms).max() < 2e-2 * np.abs(dev).max(), np.abs(tc - ms).max()
+    assert rel_l2(tc - pb, dev) < 2e-3
+    ref, _ = oracle.net_forward(grid, params, U.astype(np.float32).astype(np.float64), phibar)
+    assert rel_l2(tc - pb, ref - pb) < 3e-2
+    assert np.abs(tc.reshape(B, 2, -1).mean(2) - np.array(phibar)[None]).max() < 1e-6
+
+
+def test_tcgen05_training_forward_gives_the_same_gradient():
+    """Training at a 128-wide grid runs its forward pass on tcgen05; the gradient agrees with the
+    one taken with the mma.sync forward."""
+    grid, B = (128, 4, 4), 1
+    net = dscf.Net(grid, B, seed=14)
+    nx, ny, nz = grid
+    U = torch.from_numpy(inputs.random_field((B, 2, nz, ny, nx), seed=311, scale=0.6)).float()
+    tgt = torch.from_numpy(np.array([0.4, 0.6])[None, :, None, None, None]
+                           + 0.05 * inputs.random_field((B, 2, nz, ny, nx), seed=312)).float()
+    l0, g0 = net.gradient(U, tgt, [0.4, 0.6])
+    net.status()
+    net.set_tensor_path(1)
+    l1, g1 = net.gradient(U, tgt, [0.4, 0.6])
+    assert abs(l0 - l1) < 1e-3 * l1
+    assert rel_l2(g0.cpu().numpy(), g1.cpu().numpy()) < 2e-2
