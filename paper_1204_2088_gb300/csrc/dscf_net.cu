@@ -253,6 +253,33 @@ __global__ void k_net_in(const float* __restrict__ U, const double* __restrict__
     dst[1] = *(const uint4*)&v[8];
 }
 
+// Network input with the five x offsets folded into the channels (tcgen05 first layer):
+// xf[r][2 dx + c] = U_c[r + dx - 2 along x] - <U_c> for dx = 0..4, zero in channels 10..15.
+__global__ void k_net_in_fold(const float* __restrict__ U, const double* __restrict__ means, int nx, int V, int B,
+                              bf16* __restrict__ xf) {
+    const size_t r = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    if (r >= (size_t)B * V) return;
+    const int b = (int)(r / V);
+    const int i = (int)(r - (size_t)b * V);
+    const int x = i % nx, row = i - x;
+    const float m0 = (float)means[2 * b], m1 = (float)means[2 * b + 1];
+    const float* U0 = U + ((size_t)2 * b) * V + row;
+    const float* U1 = U + ((size_t)2 * b + 1) * V + row;
+    __align__(16) bf16 v[16];
+#pragma unroll
+    for (int dx = 0; dx < 5; ++dx) {
+        int xs = x + dx - 2;
+        xs = xs < 0 ? xs + nx : (xs >= nx ? xs - nx : xs);
+        v[2 * dx] = __float2bfloat16(U0[xs] - m0);
+        v[2 * dx + 1] = __float2bfloat16(U1[xs] - m1);
+    }
+#pragma unroll
+    for (int c = 10; c < 16; ++c) v[c] = __float2bfloat16(0.f);
+    uint4* dst = (uint4*)(xf + r * 16);
+    dst[0] = *(const uint4*)&v[0];
+    dst[1] = *(const uint4*)&v[8];
+}
+
 // Network output: phi_c[r] = phibar_c + y[r][c] - <y_c>  ([B][2][V] float).
 __global__ void k_net_out(const float* __restrict__ y, const double* __restrict__ means, int V, int B, double pb0,
                           double pb1, float* __restrict__ phi) {
@@ -332,6 +359,43 @@ __global__ void k_prep_wt(const float* __restrict__ W, int cin, int cout, int ci
     }
 }
 
+// Weights of a stacked tcgen05 layer: Wt[dz][dx][ci / 8][4 - dy][co][ci % 8] (zero in padded
+// channels): per (dz, dx, 8 input channels) the five dy offsets' output channels, last dy first,
+// form the rows of one N = 5 CO operand.
+__global__ void k_prep_wt_stk(const float* __restrict__ W, int cin, int cout, int cinp, int coutp, bf16* __restrict__ Wt) {
+    const int n = KVOL * coutp * cinp;
+    const int G = cinp / 8;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        int t = i;
+        const int j8 = t % 8;
+        t /= 8;
+        const int co = t % coutp;
+        t /= coutp;
+        const int k = t % 5;
+        t /= 5;
+        const int kc = t % G;
+        t /= G;
+        const int dx = t % 5, dz = t / 5;
+        const int ci = kc * 8 + j8, o = dz * 25 + (4 - k) * 5 + dx;
+        const float v = (co < cout && ci < cin) ? W[((size_t)co * cin + ci) * KVOL + o] : 0.f;
+        Wt[i] = __float2bfloat16(v);
+    }
+}
+
+// First-layer weights for the folded input: Wt[dz][dy][k / 8][co][k % 8] with k = 2 dx + ci
+// (k < 10), zero for k >= 10.
+__global__ void k_prep_wt_fold(const float* __restrict__ W, bf16* __restrict__ Wt) {
+    const int n = 25 * 2 * 32 * 8;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int o2 = i / 512, rem = i % 512;
+        const int kc = rem / 256, r2 = rem % 256;
+        const int co = r2 / 8, k = kc * 8 + r2 % 8;
+        float v = 0.f;
+        if (k < 10) v = W[((size_t)co * 2 + (k & 1)) * KVOL + o2 * 5 + (k >> 1)];
+        Wt[i] = __float2bfloat16(v);
+    }
+}
+
 // Adam (FP32 master weights).
 __global__ void k_adam(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m, float* __restrict__ v,
                        int n, float lr, float b1, float b2, float eps, float c1, float c2) {
@@ -348,8 +412,8 @@ __global__ void k_adam(float* __restrict__ p, const float* __restrict__ g, float
 size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct NetLayout {
-    size_t params, grads, m, v, wf[NL], wb[NL], wt[NL], x16, h1, h2, y16, dy16, dz2, dz1, gtmp, part, means, lpart, err,
-        bytes;
+    size_t params, grads, m, v, wf[NL], wb[NL], wt[NL], x16, x16f, h1, h2, y16, dy16, dz2, dz1, gtmp, part, means, lpart,
+        err, bytes;
 };
 constexpr int kPartBlocks = 512;   // partial sums per channel and sample
 
@@ -368,6 +432,7 @@ NetLayout net_layout(int nx, int ny, int nz, int B) {
         L.wt[l] = take((size_t)KVOL * COUTP[l] * CINP[l] * 2);
     }
     L.x16 = take(S * 16 * 2);
+    L.x16f = tc_conv_supported(nx, ny) ? take(S * 16 * 2) : 0;
     L.h1 = take(S * 32 * 2);
     L.h2 = take(S * 32 * 2);
     L.y16 = take(S * 16 * 4);
@@ -424,10 +489,12 @@ void prep_weights(dscf_net* n) {
     for (int l = 0; l < NL; ++l)
         k_prep_w<<<64, 256, 0, n->stream>>>(n->at<float>(n->L.params) + poff(l), CIN[l], COUT[l], CINP[l], COUTP[l],
                                               n->at<bf16>(n->L.wf[l]), l > 0 ? n->at<bf16>(n->L.wb[l]) : nullptr);
-    if (n->tc_ok)
-        for (int l = 0; l < NL; ++l)
-            k_prep_wt<<<64, 256, 0, n->stream>>>(n->at<float>(n->L.params) + poff(l), CIN[l], COUT[l], CINP[l], COUTP[l],
-                                                   n->at<bf16>(n->L.wt[l]));
+    if (n->tc_ok) {
+        k_prep_wt_fold<<<64, 256, 0, n->stream>>>(n->at<float>(n->L.params) + poff(0), n->at<bf16>(n->L.wt[0]));
+        for (int l = 1; l < NL; ++l)
+            k_prep_wt_stk<<<64, 256, 0, n->stream>>>(n->at<float>(n->L.params) + poff(l), CIN[l], COUT[l], CINP[l],
+                                                       COUTP[l], n->at<bf16>(n->L.wt[l]));
+    }
 }
 
 // means of C = 2 channels of a [B][C][V] field into L.means
@@ -446,7 +513,8 @@ void forward(dscf_net* n, const float* U, double pb0, double pb1, float* phi) {
     chan_means(n, U, 2);
     k_net_in<<<eb, 256, 0, n->stream>>>(U, n->at<double>(n->L.means), V, B, n->at<bf16>(n->L.x16));
     if (n->use_tc()) {
-        const size_t act[NL + 1] = {n->L.x16, n->L.h1, n->L.h2, n->L.y16};
+        k_net_in_fold<<<eb, 256, 0, n->stream>>>(U, n->at<double>(n->L.means), n->nx, V, B, n->at<bf16>(n->L.x16f));
+        const size_t act[NL + 1] = {n->L.x16f, n->L.h1, n->L.h2, n->L.y16};
         for (int l = 0; l < NL; ++l)
             launch_conv_tc(l, n->ws + act[l], n->ws + n->L.wt[l], n->at<float>(n->L.params) + poff(l) + wcount(l),
                            COUT[l], n->ws + act[l + 1], n->nx, n->ny, n->nz, B, n->at<double>(n->L.part),
@@ -515,7 +583,7 @@ double u01(uint64_t seed, uint64_t k) {
 bool dscf_net_fits(const dscf_net* n, int nx, int ny, int nz) {
     return n && n->nx == nx && n->ny == ny && n->nz == nz && n->B == 1;
 }
-int dscf_net_forward_launches(const dscf_net* n) { return n->use_tc() ? 8 : 9; }
+int dscf_net_forward_launches(const dscf_net* n) { return 9; }
 void dscf_net_forward_on(dscf_net* n, cudaStream_t stream, const float* U, double pb0, double pb1, float* phi) {
     cudaStream_t keep = n->stream;
     n->stream = stream;

@@ -138,7 +138,10 @@ __device__ __forceinline__ int wrapi_(int v, int n) {
 // and the CTA's FP64 sums of channels 0 and 1 into part[(b * 2 + c) * nblk + i] (i: the CTA's
 // index within its sample, nblk: CTAs per sample), for the network's mean removal.
 // in: [B][V][CI] BF16 channel-last; wt: [125][CI/8][CO][8] BF16; bias: cout values.
-template <int CI, int CO, int EPI>
+// FOLD: the input holds, in channels 2 dx + ci (dx = 0..4, ci = 0..1), the two real input channels
+// at x + dx - 2 (zero in channels 10..15), so one K = 16 step covers all five x offsets: the
+// offsets are (dz, dy) only, with weights [dz][dy][k / 8][co][k % 8].
+template <int CI, int CO, int EPI, bool FOLD>
 __global__ void __launch_bounds__(TC_THREADS, 2)
     k_conv_tc(const bf16* __restrict__ in, const bf16* __restrict__ wt, const float* __restrict__ bias, int cout,
               void* __restrict__ out, int nx, int ny, int nz, double* __restrict__ part, int* __restrict__ err) {
@@ -146,6 +149,8 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
     constexpr int ROWB = G * TC_XP * 16;            // bytes of one staged row
     constexpr int ABYTES = (TC_R + 4) * ROWB;
     constexpr int OFFB = G * CO * 16;               // bytes of the weights of one offset
+    constexpr int NDX = FOLD ? 1 : 5;               // x offsets per (dz, dy)
+    constexpr int DXS = FOLD ? 2 : 0;               // x' of the first x offset minus x - x0
     constexpr uint32_t IDESC = idesc_bf16(128, CO);
     static_assert(TC_R * CO <= TC_TMEM_COLS, "accumulators exceed the tensor-memory allocation");
     static_assert(CO == 16 || CO == 32, "CO");
@@ -218,8 +223,8 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
 #pragma unroll 1
         for (int h = 0; h < 2 && ok; ++h) {
             const int dy0 = h ? 3 : 0, dy1 = h ? 5 : 3;
-            const bf16* wsrc = wt + ((size_t)dzi * 25 + dy0 * 5) * G * CO * 8;
-            const int nbytes = (dy1 - dy0) * 5 * OFFB;
+            const bf16* wsrc = wt + ((size_t)dzi * 5 + dy0) * NDX * G * CO * 8;
+            const int nbytes = (dy1 - dy0) * NDX * OFFB;
             for (int c = tid; c < nbytes / 16; c += TC_THREADS) cp16(Ws + (size_t)c * 16, wsrc + (size_t)c * 8);
             cp_commit();
             cp_wait_all();
@@ -230,12 +235,13 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
                 const uint32_t a0 = smem_u32(As), w0 = smem_u32(Ws);
                 for (int r = 0; r < TC_R; ++r)
                     for (int dyi = dy0; dyi < dy1; ++dyi)
-                        for (int dxi = 0; dxi < 5; ++dxi)
+                        for (int dxi = 0; dxi < NDX; ++dxi)
 #pragma unroll
                             for (int kk = 0; kk < CI / 16; ++kk) {
-                                const uint32_t aaddr = a0 + (uint32_t)(((r + dyi) * G + 2 * kk) * TC_XP + dxi) * 16u;
+                                const uint32_t aaddr =
+                                    a0 + (uint32_t)(((r + dyi) * G + 2 * kk) * TC_XP + dxi + DXS) * 16u;
                                 const uint32_t baddr =
-                                    w0 + (uint32_t)((((dyi - dy0) * 5 + dxi) * G + 2 * kk) * CO) * 16u;
+                                    w0 + (uint32_t)((((dyi - dy0) * NDX + dxi) * G + 2 * kk) * CO) * 16u;
                                 mma_bf16(tmem + (uint32_t)(r * CO), smem_desc(aaddr, TC_XP * 16, 128),
                                          smem_desc(baddr, CO * 16, 128), IDESC, (dzi | dyi | dxi | kk) != 0);
                             }
@@ -305,6 +311,182 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
     }
 }
 
+// Zero NC (multiple of 32) TMEM columns of this warp's lane quarter.
+__device__ __forceinline__ void tmem_zero(uint32_t taddr, int nc) {
+    const uint32_t z = 0u;
+    for (int c = 0; c < nc; c += 32)
+        asm volatile(
+            "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, "
+            "%1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1};\n" ::"r"(taddr + (uint32_t)c),
+            "r"(z)
+            : "memory");
+    asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory");
+}
+
+// Stacked variant: one MMA per (staged input row j, dx, 16-channel step) with the weights of the
+// five dy offsets stacked along N in reverse order, n = (4 - dy) CO + co, so that its 5 CO output
+// columns land on the accumulators of output rows j - 4 .. j, which sit side by side when the
+// accumulator of output row r starts at column (r + 4) CO.  Each staged A tile is read once for
+// five offsets instead of once per offset; the accumulators of the 8 halo rows (r < 0, r >= R)
+// collect unused sums.  TMEM is zeroed first so that every MMA accumulates.
+// wt: [dz][dx][ci / 8][4 - dy][co][ci % 8].  R output rows per CTA, TMEM_COLS >= (R + 8) CO.
+template <int CI, int CO, int EPI, int R, int TMEM_COLS, int MINB>
+__global__ void __launch_bounds__(TC_THREADS, MINB)
+    k_conv_tc_stk(const bf16* __restrict__ in, const bf16* __restrict__ wt, const float* __restrict__ bias, int cout,
+                  void* __restrict__ out, int nx, int ny, int nz, double* __restrict__ part, int* __restrict__ err) {
+    constexpr int G = CI / 8;
+    constexpr int ROWB = G * TC_XP * 16;
+    constexpr int ABYTES = (R + 4) * ROWB;
+    constexpr int NS = 5 * CO;                      // stacked N
+    constexpr int WBYTES = 5 * G * NS * 16;         // weights of one dz
+    constexpr uint32_t IDESC = idesc_bf16(128, NS);
+    static_assert((R + 8) * CO <= TMEM_COLS, "accumulators exceed the tensor-memory allocation");
+    static_assert(NS % 16 == 0 && NS <= 256, "stacked N");
+    static_assert(R % 2 == 0, "R");
+    extern __shared__ __align__(1024) unsigned char smem[];
+    unsigned char* As = smem;
+    unsigned char* Ws = smem + ABYTES;
+    __shared__ __align__(8) uint64_t mbar;
+    __shared__ uint32_t tmem_slot;
+    __shared__ float csum[TC_THREADS / 32][2];
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int nxt = nx / 128, nyb = ny / R;
+    int blk = blockIdx.x;
+    const int xt = blk % nxt;
+    blk /= nxt;
+    const int yb = blk % nyb;
+    blk /= nyb;
+    const int z = blk % nz, b = blk / nz;
+    const int x0 = xt * 128, y0 = yb * R;
+    const size_t V = (size_t)nx * ny * nz;
+    const bf16* inb = in + (size_t)b * V * CI;
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(&tmem_slot)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+    }
+    if (tid == 0) {
+        mbar_init(&mbar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+    const uint32_t tmem = tmem_slot;
+    if (warp < 4) tmem_zero(tmem + ((uint32_t)(warp * 32) << 16), (R + 8) * CO);
+
+    constexpr int RCH = TC_XP * G;
+    constexpr int KCH = (RCH + TC_THREADS - 1) / TC_THREADS;
+    int soff[KCH], goff[KCH];
+#pragma unroll
+    for (int k = 0; k < KCH; ++k) {
+        const int c = tid + k * TC_THREADS;
+        const int g = c % G, xp = c / G;
+        int x = x0 - 2 + xp;
+        x = x < 0 ? x + nx : (x >= nx ? x - nx : x);
+        soff[k] = c < RCH ? (g * TC_XP + xp) * 16 : -1;
+        goff[k] = x * CI + g * 8;
+    }
+
+    bool ok = true;
+    for (int dzi = 0; dzi < 5 && ok; ++dzi) {
+        int zin = z + dzi - 2;
+        zin = zin < 0 ? zin + nz : (zin >= nz ? zin - nz : zin);
+#pragma unroll 1
+        for (int i = 0; i < R + 4; ++i) {
+            const int yin = wrapi_(y0 - 2 + i, ny);
+            const bf16* src = inb + ((size_t)zin * ny + yin) * nx * CI;
+            unsigned char* dst = As + i * ROWB;
+#pragma unroll
+            for (int k = 0; k < KCH; ++k)
+                if (soff[k] >= 0) cp16(dst + soff[k], src + goff[k]);
+        }
+        const bf16* wsrc = wt + (size_t)dzi * (WBYTES / 2);
+        for (int c = tid; c < WBYTES / 16; c += TC_THREADS) cp16(Ws + (size_t)c * 16, wsrc + (size_t)c * 8);
+        cp_commit();
+        cp_wait_all();
+        fence_proxy_async();
+        fence_before_sync();   // orders the TMEM zeroing before the MMAs
+        __syncthreads();
+        if (tid == 0) {
+            fence_after_sync();
+            const uint32_t a0 = smem_u32(As), w0 = smem_u32(Ws);
+            for (int j = 0; j < R + 4; ++j)
+                for (int dxi = 0; dxi < 5; ++dxi)
+#pragma unroll
+                    for (int kk = 0; kk < CI / 16; ++kk) {
+                        const uint32_t aaddr = a0 + (uint32_t)((j * G + 2 * kk) * TC_XP + dxi) * 16u;
+                        const uint32_t baddr = w0 + (uint32_t)((dxi * G + 2 * kk) * NS) * 16u;
+                        mma_bf16(tmem + (uint32_t)(j * CO), smem_desc(aaddr, TC_XP * 16, 128),
+                                 smem_desc(baddr, NS * 16, 128), IDESC, 1);
+                    }
+            mma_commit(&mbar);
+        }
+        const bool done = mbar_wait(&mbar, (uint32_t)(dzi & 1));
+        if (!done) atomicOr(err, 1);
+        ok = __syncthreads_and(done ? 1 : 0) != 0;
+    }
+    fence_after_sync();
+    float s0 = 0.f, s1 = 0.f;
+    if (ok) {
+        const int q = warp & 3;
+        const int x = x0 + q * 32 + lane;
+        const uint32_t tq = tmem + ((uint32_t)(q * 32) << 16);
+#pragma unroll 1
+        for (int r = (warp >> 2) * (R / 2); r < ((warp >> 2) + 1) * (R / 2); ++r) {
+            float v[CO];
+            const uint32_t col = (uint32_t)((r + 4) * CO);
+            if (CO == 32) tmem_ld32(tq + col, v);
+            else tmem_ld16(tq + col, v);
+            const size_t site = (size_t)b * V + ((size_t)z * ny + (y0 + r)) * nx + x;
+#pragma unroll
+            for (int co = 0; co < CO; ++co) v[co] += (co < cout) ? bias[co] : 0.f;
+            if (EPI == 0) {
+                __align__(16) bf16 hv[CO];
+#pragma unroll
+                for (int co = 0; co < CO; ++co) hv[co] = __float2bfloat16(tanhf(v[co]));
+                uint4* dst = (uint4*)((bf16*)out + site * CO);
+#pragma unroll
+                for (int k = 0; k < CO / 8; ++k) dst[k] = ((const uint4*)hv)[k];
+            } else {
+                float4* dst = (float4*)((float*)out + site * 16);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) dst[k] = make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+                s0 += v[0];
+                s1 += v[1];
+            }
+        }
+    }
+    if (EPI == 1) {
+#pragma unroll
+        for (int m = 16; m > 0; m >>= 1) {
+            s0 += __shfl_xor_sync(0xffffffffu, s0, m);
+            s1 += __shfl_xor_sync(0xffffffffu, s1, m);
+        }
+        if (lane == 0) {
+            csum[warp][0] = s0;
+            csum[warp][1] = s1;
+        }
+        __syncthreads();
+        if (tid < 2) {
+            double t = 0.0;
+            for (int w = 0; w < TC_THREADS / 32; ++w) t += (double)csum[w][tid];
+            const int nblk = nz * nyb * nxt;
+            part[((size_t)b * 2 + tid) * nblk + (blockIdx.x - (size_t)b * nblk)] = t;
+        }
+    }
+    fence_before_sync();
+    __syncthreads();
+    if (warp == 0) {
+        fence_after_sync();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(TMEM_COLS)
+                     : "memory");
+    }
+}
+
 }  // namespace
 
 // Bytes of dynamic shared memory of the kernel for CI input and CO output channels: the staged
@@ -315,37 +497,50 @@ size_t tc_conv_smem(int ci, int co) {
     const size_t w = (size_t)15 * (ci / 8) * co * 16;   // the larger half (dy 0..2) of one dz
     return a + w;
 }
+// the stacked variant: R + 4 staged rows and the weights of one whole dz
+constexpr size_t stk_smem(int ci, int co, int r) {
+    return (size_t)(r + 4) * (ci / 8) * TC_XP * 16 + (size_t)25 * (ci / 8) * co * 16;
+}
+constexpr int kR2 = 8, kR3 = 4;   // output rows per CTA of the second and third layer
 
-bool tc_conv_supported(int nx, int ny) { return nx % 128 == 0 && ny % TC_R == 0; }
+bool tc_conv_supported(int nx, int ny) { return nx % 128 == 0 && ny % kR2 == 0; }
 
 int tc_conv_prepare() {
-    cudaError_t e = cudaFuncSetAttribute(k_conv_tc<16, 32, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    // the whole unified L1/shared array as shared memory, so that several CTAs fit per SM
+    cudaFuncSetAttribute(k_conv_tc<16, 32, 0, true>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    cudaFuncSetAttribute(k_conv_tc_stk<32, 32, 0, kR2, 512, 1>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    cudaFuncSetAttribute(k_conv_tc_stk<32, 16, 1, kR3, 256, 2>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    cudaError_t e = cudaFuncSetAttribute(k_conv_tc<16, 32, 0, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)tc_conv_smem(16, 32));
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_conv_tc<32, 32, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)tc_conv_smem(32, 32));
+        e = cudaFuncSetAttribute(k_conv_tc_stk<32, 32, 0, kR2, 512, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)stk_smem(32, 32, kR2));
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_conv_tc<32, 16, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)tc_conv_smem(32, 16));
+        e = cudaFuncSetAttribute(k_conv_tc_stk<32, 16, 1, kR3, 256, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)stk_smem(32, 16, kR3));
     return (int)e;
 }
 
-// Layer l of the predictor network (0: 16 -> 32 tanh, 1: 32 -> 32 tanh, 2: 32 -> 16 linear FP32)
-// over B samples of an nx x ny x nz grid (tc_conv_supported must hold).
-int tc_conv_blocks(int nx, int ny, int nz) { return nz * (ny / TC_R) * (nx / 128); }
+// CTAs per sample of the output layer (the number of its channel partial sums).
+int tc_conv_blocks(int nx, int ny, int nz) { return nz * (ny / kR3) * (nx / 128); }
 
+// Layer l of the predictor network (0: 2 -> 32 tanh with the x offsets folded into 16 input
+// channels, weights [dz][dy][k / 8][co][k % 8]; 1: 32 -> 32 tanh and 2: 32 -> 16 linear FP32, both
+// stacked, weights [dz][dx][ci / 8][4 - dy][co][ci % 8]) over B samples of an nx x ny x nz grid
+// (tc_conv_supported must hold).
 void launch_conv_tc(int layer, const void* in, const void* wt, const float* bias, int cout, void* out, int nx, int ny,
                     int nz, int B, double* part, int* err, cudaStream_t s) {
-    const int blocks = B * nz * (ny / TC_R) * (nx / 128);
+    const bf16* x = (const bf16*)in;
+    const bf16* w = (const bf16*)wt;
     if (layer == 0)
-        k_conv_tc<16, 32, 0><<<blocks, TC_THREADS, tc_conv_smem(16, 32), s>>>((const bf16*)in, (const bf16*)wt, bias,
-                                                                              cout, out, nx, ny, nz, part, err);
+        k_conv_tc<16, 32, 0, true><<<B * nz * (ny / TC_R) * (nx / 128), TC_THREADS, tc_conv_smem(16, 32), s>>>(
+            x, w, bias, cout, out, nx, ny, nz, part, err);
     else if (layer == 1)
-        k_conv_tc<32, 32, 0><<<blocks, TC_THREADS, tc_conv_smem(32, 32), s>>>((const bf16*)in, (const bf16*)wt, bias,
-                                                                              cout, out, nx, ny, nz, part, err);
+        k_conv_tc_stk<32, 32, 0, kR2, 512, 1><<<B * nz * (ny / kR2) * (nx / 128), TC_THREADS, stk_smem(32, 32, kR2), s>>>(
+            x, w, bias, cout, out, nx, ny, nz, part, err);
     else
-        k_conv_tc<32, 16, 1><<<blocks, TC_THREADS, tc_conv_smem(32, 16), s>>>((const bf16*)in, (const bf16*)wt, bias,
-                                                                              cout, out, nx, ny, nz, part, err);
+        k_conv_tc_stk<32, 16, 1, kR3, 256, 2><<<B * nz * (ny / kR3) * (nx / 128), TC_THREADS, stk_smem(32, 16, kR3), s>>>(
+            x, w, bias, cout, out, nx, ny, nz, part, err);
 }
 
 }  // namespace dscf

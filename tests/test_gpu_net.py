@@ -305,8 +305,9 @@ def test_tcgen05_forward_matches_mma_sync_and_fp64_network():
 def test_tcgen05_training_forward_gives_the_same_gradient():
     """Training at a 128-wide grid runs its forward pass on tcgen05; the gradient agrees with the
     one taken with the mma.sync forward."""
-    grid, B = (128, 4, 4), 1
+    grid, B = (128, 8, 4), 1
     net = dscf.Net(grid, B, seed=14)
+    assert net.tensor_path() == 2
     nx, ny, nz = grid
     U = torch.from_numpy(inputs.random_field((B, 2, nz, ny, nx), seed=311, scale=0.6)).float()
     tgt = torch.from_numpy(np.array([0.4, 0.6])[None, :, None, None, None]
