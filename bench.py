@@ -212,63 +212,79 @@ def ncu_traffic(kernel_src, N):
 
 
 def learned_form(cfg, dev, phi0, timed, world, steps):
-    """FP32 step with the learned predictor: a network trained on the GPU (the library's BF16
-    kernels, Adam) on (U, phi[U]) pairs of the same physics generated by the exact method on a
-    32^3 box, then attached to the full-size context (the network is translation invariant with
-    periodic padding).  Exact corrector every 10 steps, fallback above 1e-3, one inversion
-    iteration per predictor step.  The timed region includes the correctors and judgements."""
+    """FP32 step with the learned predictor.  The network is trained on the GPU (the library's
+    kernels, Adam) on (U, phi[U]) pairs generated by the exact method on 32^3 boxes of the same
+    physics (three seeds, the first 120 steps of each), then attached to the full-size context
+    (translation invariant, periodic padding).  The full-size run first takes 12 exact steps
+    through the quench transient, then the timed steps run with the predictor attached: exact
+    corrector every 10 steps, one inversion iteration per predictor step, fallback above the
+    tolerance (1e-3; a second run at 2e-3 shows what an accepted predictor gains).  The timed
+    region includes the correctors and judgements."""
     import numpy as np
     import torch
 
     from paper_1204_2088_gb300 import dscf, inputs, replicas
 
     t_start = time.perf_counter()
-    small = dict(cfg, grid=(32, 32, 32), name=cfg["name"] + "-train32")
-    ctx = dscf.Context(small, dscf.FP32, device=dev)
-    ctx.set(dscf.PHI, torch.from_numpy(inputs.initial_fields(small)).float().to(dev))
-    T, T0 = 160, 120
-    Us, Ps = [], []
-    for _ in range(T):
-        ctx.step(1)
-        Us.append(ctx.get(dscf.U).clone())
-        Ps.append(ctx.get(dscf.PHIM).clone())
-    ctx.close()
-    U, P = torch.stack(Us), torch.stack(Ps)
     f = cfg["nA"] / cfg["N"]
     phibar = [cfg["phi_p"] * f, cfg["phi_p"] * (1 - f)]
-    B, iters = 8, 2000
-    net = dscf.Net(small["grid"], B, seed=3, device=dev)
-    one = dscf.Net(small["grid"], 1, seed=3, device=dev)
-    err = lambda: max((one.forward(U[t:t + 1], phibar)[0] - P[t]).abs().max().item() for t in range(T0, T, 5))
+    Us, Ps, held = [], [], None
+    for seed in (101, 102, 103, 104):
+        small = dict(cfg, grid=(32, 32, 32), seed=seed, name=cfg["name"] + "-train32")
+        ctx = dscf.Context(small, dscf.FP32, device=dev)
+        ctx.set(dscf.PHI, torch.from_numpy(inputs.initial_fields(small)).float().to(dev))
+        u, p = [], []
+        for _ in range(120):
+            ctx.step(1)
+            u.append(ctx.get(dscf.U).clone())
+            p.append(ctx.get(dscf.PHIM).clone())
+        ctx.close()
+        if seed == 104:
+            held = (torch.stack(u), torch.stack(p))
+        else:
+            Us += u
+            Ps += p
+    U, P = torch.stack(Us), torch.stack(Ps)
+    B, iters, lr = 8, 6000, 1e-4
+    net = dscf.Net((32, 32, 32), B, seed=3, device=dev)
+    one = dscf.Net((32, 32, 32), 1, seed=3, device=dev)
+    err = lambda: max((one.forward(held[0][t:t + 1], phibar)[0] - held[1][t]).abs().max().item()
+                      for t in range(10, 120, 10))
     e_untrained = err()
     g = torch.Generator().manual_seed(0)
     for it in range(iters):
-        idx = torch.randint(0, T0, (B,), generator=g)
-        net.train_step(U[idx], P[idx], phibar, lr=1e-3 * 0.5 * (1 + np.cos(np.pi * it / iters)) + 1e-5)
+        idx = torch.randint(0, U.shape[0], (B,), generator=g)
+        net.train_step(U[idx], P[idx], phibar, lr=lr * 0.5 * (1 + np.cos(np.pi * it / iters)) + 1e-6)
     one.set_params(net.get_params())
     e_trained = err()
     t_train = time.perf_counter() - t_start
     big = dscf.Net(cfg["grid"], 1, seed=3, device=dev)
     big.set_params(net.get_params())
     del net, one
-    c = dscf.Context(cfg, dscf.FP32, device=dev)
-    c.set(dscf.PHI, phi0)
-    c.set_predictor(big, corrector_every=10, tol=1e-3, ncg_iters=1)
-    c.step(3)
-    d0 = c.diagnostics()
-    ms = timed(lambda: c.step(steps))
-    d = c.diagnostics()
-    c.status()
     V = int(np.prod(cfg["grid"]))
-    out = {"value": replicas.aggregate_rate([V * steps] * world, [ms]), "unit": UNIT, "ms_per_step": ms / steps,
-           "steps": steps, "predictor_steps": d["pred_steps"] - d0["pred_steps"],
-           "exact_steps": d["exact_steps"] - d0["exact_steps"], "last_judged_error": d["pred_err"],
-           "tol": 1e-3, "corrector_every": 10, "predictor_ncg_iters": 1,
-           "training": {"pairs": T0, "grid": list(small["grid"]), "iters": iters, "batch": B,
-                        "held_out_max_err_untrained": e_untrained, "held_out_max_err_trained": e_trained,
-                        "seconds": t_train}}
-    c.close()
+    runs = {}
+    for tol in (1e-3, 2e-3):
+        c = dscf.Context(cfg, dscf.FP32, device=dev)
+        c.set(dscf.PHI, phi0)
+        c.step(12)
+        c.set_predictor(big, corrector_every=10, tol=tol, ncg_iters=1)
+        c.step(3)
+        d0 = c.diagnostics()
+        ms = timed(lambda: c.step(steps))
+        d = c.diagnostics()
+        c.status()
+        runs[tol] = {"value": replicas.aggregate_rate([V * steps] * world, [ms]), "ms_per_step": ms / steps,
+                     "predictor_steps": d["pred_steps"] - d0["pred_steps"],
+                     "exact_steps": d["exact_steps"] - d0["exact_steps"], "last_judged_error": d["pred_err"],
+                     "tensor_path": "tcgen05" if big.tensor_path() == 2 else "mma.sync"}
+        c.close()
     big.close()
+    out = dict(runs[1e-3])
+    out.update({"unit": UNIT, "steps": steps, "tol": 1e-3, "corrector_every": 10, "predictor_ncg_iters": 1,
+                "exact_warmup_steps": 12, "at_tol_2e-3": runs[2e-3],
+                "training": {"pairs": int(U.shape[0]), "grid": [32, 32, 32], "seeds": 3, "iters": iters, "batch": B,
+                             "lr": lr, "held_out_max_err_untrained": e_untrained,
+                             "held_out_max_err_trained": e_trained, "seconds": t_train}})
     return out
 
 
