@@ -7,7 +7,7 @@
 namespace dscf {
 
 constexpr int kFlatThreads = 256;     // threads of every site-parallel ("flat") kernel
-constexpr int kMaxFlatBlocks = 1216;  // flat blocks per replica (= partial sums per replica): 8 per SM
+constexpr int kMaxFlatBlocks = 608;   // flat blocks per replica (= partial sums per replica): 4 per SM, one wave
 constexpr int kMaxNcg = 32;           // Fletcher-Reeves iterations per step, upper bound
 constexpr int kScalStride = 192;      // FP64 scalar slots per replica
 constexpr int kPropCols = 30;         // output x columns per propagator CTA (a warp minus 2 halo lanes)

@@ -56,6 +56,25 @@ __device__ __forceinline__ T model_phi(const Rep& R, const Norm& n, int I, int i
     return (T)n.phis * ((const T*)R.E)[2 * (size_t)R.V + i] / (T)n.qs;
 }
 
+// FP32 fields with V a multiple of 4 are also walked as float4 (4 consecutive sites per thread and
+// iteration: 16-byte accesses, every species offset stays 16-byte aligned).
+template <typename T>
+__device__ __forceinline__ bool flat_vec(int V) {
+    if constexpr (sizeof(T) == 4) return (V & 3) == 0;
+    return false;
+}
+__device__ __forceinline__ float4 ld4(const float* p) { return *(const float4*)p; }
+// Scale and source of the model density of species I as a float4 stream: coef q_I, or for the
+// solvent phis E_S / qs.
+__device__ __forceinline__ const float* model_src(const Rep& R, const Norm& n, int I, float& sc) {
+    if (I < 2) {
+        sc = (float)n.coef;
+        return (const float*)R.q + (size_t)I * R.V;
+    }
+    sc = (float)(n.phis / n.qs);
+    return (const float*)R.E + 2 * (size_t)R.V;
+}
+
 // Directional derivative at the trial point: h1 = <phi* - phi[U + a1 d], d>.
 template <typename T>
 __global__ void __launch_bounds__(kFlatThreads) k_trial(const Rep* __restrict__ reps, const int* __restrict__ blk2rep,
@@ -66,11 +85,24 @@ __global__ void __launch_bounds__(kFlatThreads) k_trial(const Rep* __restrict__ 
     const T* phi = (const T*)R.phi;
     const T* d = (const T*)R.d;
     T h1 = T(0);
-    for (int I = 0; I < R.ns; ++I)
-        _Pragma("unroll 4") for (int i = i0 + threadIdx.x; i < i1; i += kFlatThreads) {
-            const size_t o = (size_t)I * V + i;
-            h1 += (phi[o] - model_phi<T>(R, n, I, i)) * d[o];
+    if (flat_vec<T>(V)) {
+        for (int I = 0; I < R.ns; ++I) {
+            float sc;
+            const float* src = model_src(R, n, I, sc);
+            _Pragma("unroll 2") for (int i = i0 + 4 * (int)threadIdx.x; i < i1; i += 4 * kFlatThreads) {
+                const size_t o = (size_t)I * V + i;
+                const float4 p = ld4((const float*)phi + o), dd = ld4((const float*)d + o), q = ld4(src + i);
+                h1 += (T)((p.x - sc * q.x) * dd.x + (p.y - sc * q.y) * dd.y + (p.z - sc * q.z) * dd.z +
+                          (p.w - sc * q.w) * dd.w);
+            }
         }
+    } else {
+        for (int I = 0; I < R.ns; ++I)
+            _Pragma("unroll 4") for (int i = i0 + threadIdx.x; i < i1; i += kFlatThreads) {
+                const size_t o = (size_t)I * V + i;
+                h1 += (phi[o] - model_phi<T>(R, n, I, i)) * d[o];
+            }
+    }
     const double t = block_sum((double)h1, sh);
     if (threadIdx.x == 0) slot(R, P_H1)[lb] = t;
 }
@@ -90,15 +122,31 @@ __global__ void __launch_bounds__(kFlatThreads) k_grad(const Rep* __restrict__ r
     const T* phi = (const T*)R.phi;
     T* pm = (T*)R.phim;
     T gg = T(0), gmax = T(0);
-    for (int I = 0; I < R.ns; ++I)
-        _Pragma("unroll 4") for (int i = i0 + threadIdx.x; i < i1; i += kFlatThreads) {
-            const size_t o = (size_t)I * V + i;
-            const T m = model_phi<T>(R, n, I, i);
-            pm[o] = m;
-            const T g = phi[o] - m;
-            gg += g * g;
-            gmax = fmax(gmax, fabs(g));
+    if (flat_vec<T>(V)) {
+        for (int I = 0; I < R.ns; ++I) {
+            float sc;
+            const float* src = model_src(R, n, I, sc);
+            _Pragma("unroll 2") for (int i = i0 + 4 * (int)threadIdx.x; i < i1; i += 4 * kFlatThreads) {
+                const size_t o = (size_t)I * V + i;
+                const float4 q = ld4(src + i), p = ld4((const float*)phi + o);
+                const float4 m = make_float4(sc * q.x, sc * q.y, sc * q.z, sc * q.w);
+                *(float4*)((float*)pm + o) = m;
+                const float g0 = p.x - m.x, g1 = p.y - m.y, g2 = p.z - m.z, g3 = p.w - m.w;
+                gg += (T)(g0 * g0 + g1 * g1 + g2 * g2 + g3 * g3);
+                gmax = fmax(gmax, (T)fmaxf(fmaxf(fabsf(g0), fabsf(g1)), fmaxf(fabsf(g2), fabsf(g3))));
+            }
         }
+    } else {
+        for (int I = 0; I < R.ns; ++I)
+            _Pragma("unroll 4") for (int i = i0 + threadIdx.x; i < i1; i += kFlatThreads) {
+                const size_t o = (size_t)I * V + i;
+                const T m = model_phi<T>(R, n, I, i);
+                pm[o] = m;
+                const T g = phi[o] - m;
+                gg += g * g;
+                gmax = fmax(gmax, fabs(g));
+            }
+    }
     if (k >= 0) {
         const double t = block_sum((double)gg, sh);
         const double tm = block_max((double)gmax, sh);
@@ -136,17 +184,41 @@ __global__ void __launch_bounds__(kFlatThreads) k_dir(const Rep* __restrict__ re
     T* d = (T*)R.d;
     const T tb = (T)beta;
     T h0 = T(0), cd = T(0), gg = T(0), gmax = T(0);
-    for (int I = 0; I < R.ns; ++I)
-        _Pragma("unroll 4") for (int i = i0 + threadIdx.x; i < i1; i += kFlatThreads) {
-            const size_t o = (size_t)I * V + i;
-            const T g = phi[o] - pm[o];
-            const T dn = (mode == 0) ? -g : -g + tb * d[o];
-            d[o] = dn;
-            h0 += g * dn;
-            cd += dn * pm[o] * dn;
-            gg += g * g;
-            gmax = fmax(gmax, fabs(g));
+    if (flat_vec<T>(V)) {
+        const float fb = (float)tb;
+        _Pragma("unroll 2") for (int i = i0 + 4 * (int)threadIdx.x; i < i1; i += 4 * kFlatThreads) {
+            for (int I = 0; I < R.ns; ++I) {
+                const size_t o = (size_t)I * V + i;
+                const float4 p = ld4((const float*)phi + o), m = ld4((const float*)pm + o);
+                float4 dn = make_float4(m.x - p.x, m.y - p.y, m.z - p.z, m.w - p.w);   // -g
+                if (mode != 0) {
+                    const float4 dd = ld4((const float*)d + o);
+                    dn.x += fb * dd.x;
+                    dn.y += fb * dd.y;
+                    dn.z += fb * dd.z;
+                    dn.w += fb * dd.w;
+                }
+                *(float4*)((float*)d + o) = dn;
+                const float g0 = p.x - m.x, g1 = p.y - m.y, g2 = p.z - m.z, g3 = p.w - m.w;
+                h0 += (T)(g0 * dn.x + g1 * dn.y + g2 * dn.z + g3 * dn.w);
+                cd += (T)(dn.x * m.x * dn.x + dn.y * m.y * dn.y + dn.z * m.z * dn.z + dn.w * m.w * dn.w);
+                gg += (T)(g0 * g0 + g1 * g1 + g2 * g2 + g3 * g3);
+                gmax = fmax(gmax, (T)fmaxf(fmaxf(fabsf(g0), fabsf(g1)), fmaxf(fabsf(g2), fabsf(g3))));
+            }
         }
+    } else {
+        for (int I = 0; I < R.ns; ++I)
+            _Pragma("unroll 4") for (int i = i0 + threadIdx.x; i < i1; i += kFlatThreads) {
+                const size_t o = (size_t)I * V + i;
+                const T g = phi[o] - pm[o];
+                const T dn = (mode == 0) ? -g : -g + tb * d[o];
+                d[o] = dn;
+                h0 += g * dn;
+                cd += dn * pm[o] * dn;
+                gg += g * g;
+                gmax = fmax(gmax, fabs(g));
+            }
+    }
     const double th0 = block_sum((double)h0, sh);
     const double tcd = block_sum((double)cd, sh);
     if (threadIdx.x == 0) {
