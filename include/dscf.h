@@ -174,7 +174,9 @@ int64_t dscf_launches_per_step(const dscf_ctx* ctx);
  * zc = z planes per propagator tile (>= 1), kfuse = contour steps per propagator launch (1..4;
  * > 1 needs FP32 and nx in {32, 64, 128} for every replica, and kfuse <= N), or kfuse = 0 for
  * persistent sweeps (one launch per sweep; one FP32 replica with nx = 128 and ny, nz multiples
- * of 8, bricks co-resident one per SM).  Synchronises the stream; the next dscf_step re-captures
+ * of 8; bricks of 128 x 8 x 16 sites, one CTA of 16 warps per SM, or of 128 x 8 x 8 sites, two
+ * CTAs of 8 warps per SM, all co-resident).  With kfuse = 0, zc = 16 or 8 selects the brick depth
+ * (DSCF_ERR_ARG if the grid does not allow it), any other zc keeps the autotuner's choice.  Synchronises the stream; the next dscf_step re-captures
  * its graph.  Results do not depend on either value beyond rounding. */
 int dscf_set_tuning(dscf_ctx* ctx, int32_t zc, int32_t kfuse);
 

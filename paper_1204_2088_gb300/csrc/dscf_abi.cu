@@ -220,6 +220,7 @@ struct dscf_ctx {
     cudaGraphExec_t exec_pred = nullptr;
     int kfuse = 1;          // contour steps per propagator launch (1 = single-step kernels, 0 = persistent)
     int pers_bz = 0;        // brick depth of the persistent sweeps (0 = not available)
+    int pers_nw = 16;       // warps per CTA of the persistent sweeps
     int wait_limit = kPersSpinLimit;   // polls before a persistent sweep gives up on a neighbour
     int nsm = 0;
     bool fusable = false;   // FP32 and every replica in the whole-row layout
@@ -259,6 +260,13 @@ Launch launch_of(dscf_ctx* c, cudaStream_t s) {
     return L;
 }
 
+// The persistent sweeps require equal step counters of all bricks at launch: re-arm them whenever
+// the brick decomposition changes.
+int reset_pers_flags(dscf_ctx* c) {
+    return cuda_check(c, cudaMemsetAsync(c->d_status + kFlagBase, 0, sizeof(int) * kMaxBricks, c->stream),
+                      "re-arming the brick counters");
+}
+
 // Forward and backward contour sweeps of one gradient evaluation.
 template <typename T>
 int64_t enqueue_sweeps(dscf_ctx* c, const Launch& L) {
@@ -267,8 +275,8 @@ int64_t enqueue_sweeps(dscf_ctx* c, const Launch& L) {
     if (K == 0) {
         const int nb = pers_bricks(c->L.reps[0], c->pers_bz);
         int* flags = c->d_status + kFlagBase;
-        launch_prop_pers(L, false, c->pers_bz, nb, flags, c->d_status + 2, c->wait_limit);
-        launch_prop_pers(L, true, c->pers_bz, nb, flags, c->d_status + 2, c->wait_limit);
+        launch_prop_pers(L, false, c->pers_bz, c->pers_nw, nb, flags, c->d_status + 2, c->wait_limit);
+        launch_prop_pers(L, true, c->pers_bz, c->pers_nw, nb, flags, c->d_status + 2, c->wait_limit);
         return 2;
     }
     if (K > 1) {
@@ -472,14 +480,21 @@ int autotune_zc(dscf_ctx* c) {
         cudaEventDestroy(e1);
     }
     // persistent sweeps: one replica, FP32, whole 128-site rows; timed against the best above
+    // Candidates: bricks of 16 planes (16 warps, one CTA per SM) or, where the depth does not
+    // divide, of 8 planes; and bricks of 8 planes with 8 warps, two CTAs per SM.
     c->pers_bz = 0;
+    std::vector<std::pair<int, int>> pcand;
     if (c->nrep == 1 && c->prec == DSCF_FP32) {
-        for (int bz : {16, 8}) {
-            if (pers_supported(c->L.reps[0], bz, std::min(c->nsm, kMaxBricks))) { c->pers_bz = bz; break; }
-        }
+        const int nsm = std::min(c->nsm, kMaxBricks / 2);
+        if (pers_supported(c->L.reps[0], 16, 16, nsm)) pcand.push_back({16, 16});
+        else if (pers_supported(c->L.reps[0], 8, 16, nsm)) pcand.push_back({8, 16});
+        if (pers_supported(c->L.reps[0], 8, 8, nsm)) pcand.push_back({8, 8});
     }
-    if (c->pers_bz) {
-        if (int rc = cuda_check(c, (cudaError_t)pers_prepare(c->pers_bz), "persistent sweep set-up")) return rc;
+    for (auto& pc : pcand)
+        if (int rc = cuda_check(c, (cudaError_t)pers_prepare(pc.first, pc.second), "persistent sweep set-up")) return rc;
+    if (!pcand.empty()) {
+        c->pers_bz = pcand[0].first;
+        c->pers_nw = pcand[0].second;
         if (Vtot >= 32 * 32 * 32 && c->L.reps[0].N >= 2) {
             // per contour step of the best multi-launch configuration, measured on a forward sweep
             auto sweep_ms = [&](int K, int zc) -> float {
@@ -492,7 +507,7 @@ int autotune_zc(dscf_ctx* c) {
                 cudaEventCreate(&e1);
                 auto run = [&]() {
                     if (K == 0) {
-                        launch_prop_pers(L, false, c->pers_bz, pers_bricks(c->L.reps[0], c->pers_bz),
+                        launch_prop_pers(L, false, c->pers_bz, c->pers_nw, pers_bricks(c->L.reps[0], c->pers_bz),
                                          c->d_status + kFlagBase, c->d_status + 2, kPersSpinLimit);
                     } else if (c->prec == DSCF_FP64) {
                         enqueue_sweeps<double>(c, L);
@@ -512,7 +527,18 @@ int autotune_zc(dscf_ctx* c) {
                 if (cudaGetLastError() != cudaSuccess) return 1e30f;
                 return K == 0 ? ms / 2.0f : ms / 2.0f / 2.0f;   // forward sweep only vs forward + backward
             };
-            const float tp = sweep_ms(0, 0);
+            float tp = 1e30f;
+            std::pair<int, int> pbest = pcand[0];
+            for (auto& pc : pcand) {
+                c->pers_bz = pc.first;
+                c->pers_nw = pc.second;
+                if (int rc = reset_pers_flags(c)) return rc;
+                const float t = sweep_ms(0, 0);
+                if (t < tp) { tp = t; pbest = pc; }
+            }
+            c->pers_bz = pbest.first;
+            c->pers_nw = pbest.second;
+            if (int rc = reset_pers_flags(c)) return rc;
             const float tm = sweep_ms(bestK, best);
             int st = 0;
             cudaMemcpy(&st, c->d_status, sizeof(int), cudaMemcpyDeviceToHost);
@@ -914,6 +940,14 @@ int dscf_set_tuning(dscf_ctx* c, int32_t zc, int32_t kfuse) {
     if (kfuse > 1 && !c->fusable) return fail(c, DSCF_ERR_ARG, "contour fusion needs FP32 and nx in {32, 64, 128}");
     if (kfuse == 0 && !c->pers_bz)
         return fail(c, DSCF_ERR_ARG, "persistent sweeps need one FP32 replica with nx = 128, ny % 8 = 0, nz % 8 = 0");
+    int pbz = c->pers_bz, pnw = c->pers_nw;
+    if (kfuse == 0 && (zc == 8 || zc == 16)) {   // brick depth requested
+        const int nsm = std::min(c->nsm, kMaxBricks / 2);
+        if (zc == 16 && pers_supported(c->L.reps[0], 16, 16, nsm)) { pbz = 16; pnw = 16; }
+        else if (zc == 8 && pers_supported(c->L.reps[0], 8, 8, nsm)) { pbz = 8; pnw = 8; }
+        else if (zc == 8 && pers_supported(c->L.reps[0], 8, 16, nsm)) { pbz = 8; pnw = 16; }
+        else return fail(c, DSCF_ERR_ARG, "no persistent sweep with bricks of %d planes for this grid", zc);
+    }
     for (const Rep& R : c->L.reps)
         if (kfuse > R.N) return fail(c, DSCF_ERR_ARG, "kfuse exceeds a chain length");
     if (int rc = set_dev(c)) return rc;
@@ -925,6 +959,12 @@ int dscf_set_tuning(dscf_ctx* c, int32_t zc, int32_t kfuse) {
     if (c->exec_pred) {
         cudaGraphExecDestroy(c->exec_pred);
         c->exec_pred = nullptr;
+    }
+    if (kfuse == 0 && (pbz != c->pers_bz || pnw != c->pers_nw)) {
+        if (int rc = cuda_check(c, (cudaError_t)pers_prepare(pbz, pnw), "persistent sweep set-up")) return rc;
+        c->pers_bz = pbz;
+        c->pers_nw = pnw;
+        if (int rc = reset_pers_flags(c)) return rc;
     }
     c->zc = zc;
     c->kfuse = kfuse;

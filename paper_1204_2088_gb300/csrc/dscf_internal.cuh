@@ -224,10 +224,10 @@ void launch_step_end(const Launch& L);
 template <typename T> void launch_lb_diag(const Launch& L);
 // persistent contour sweeps (FP32, nx = 128, one replica)
 size_t pers_smem_bytes(int vec, int bz);
-bool pers_supported(const Rep& R, int bz, int nsm);
+bool pers_supported(const Rep& R, int bz, int nw, int nsm);   // nw: warps per CTA (16, or 8 with 2 CTAs per SM)
 int pers_bricks(const Rep& R, int bz);
-int pers_prepare(int bz);                                                                  // cudaError_t
-int launch_prop_pers(const Launch& L, bool bwd, int bz, int nbricks, int* flags, int* abortf, int limit);  // cudaError_t
+int pers_prepare(int bz, int nw);                                                                  // cudaError_t
+int launch_prop_pers(const Launch& L, bool bwd, int bz, int nw, int nbricks, int* flags, int* abortf, int limit);  // cudaError_t
 
 }  // namespace dscf
 

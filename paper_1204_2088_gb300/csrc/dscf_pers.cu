@@ -24,8 +24,8 @@ namespace dscf {
 namespace {
 
 constexpr int PBY = 8;                 // brick rows
-constexpr int PWARPS = 16;             // warps per CTA
-constexpr int PTHREADS = 32 * PWARPS;
+// Warps per CTA: 16 for bricks of 16 planes (one CTA per SM), 8 for bricks of 8 planes, which
+// fit two CTAs per SM so that one brick computes while the other waits on its neighbours.
 
 __device__ __forceinline__ unsigned saddr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
 __device__ __forceinline__ void cp16(void* s, const void* g) {
@@ -68,10 +68,10 @@ __device__ __forceinline__ void wait_nb(const PersCtl& c, const int* nb, int tar
     if (!aborted && ld_acquire(c.abort) != 0) aborted = true;
 }
 
-template <int BZ>
+template <int BZ, int NW>
 struct PersGeom {
     static constexpr int NH = 2 * (BZ + 2) + 2 * PBY;   // halo rows per step
-    static constexpr int OWN = PBY * BZ / PWARPS;        // consecutive planes per warp (one row)
+    static constexpr int OWN = PBY * BZ / NW;            // consecutive planes per warp (one row)
 };
 
 }  // namespace
@@ -87,10 +87,11 @@ size_t pers_smem_bytes(int vec, int bz) {
 // row over those planes plus one on each side straight into registers, so the z pass needs no
 // second shared buffer.  Brick-boundary values are stored and published first; the rest of the
 // forward G_s follows without a fence (the backward G+ interior is never stored: it stays in XS).
-template <int BZ, bool BWD>
-__global__ void __launch_bounds__(PTHREADS, 1) k_prop_pers(const Rep* __restrict__ reps, PersCtl ctl) {
+template <int BZ, bool BWD, int NW>
+__global__ void __launch_bounds__(32 * NW, 16 / NW) k_prop_pers(const Rep* __restrict__ reps, PersCtl ctl) {
+    constexpr int PWARPS = NW, PTHREADS = 32 * NW;
     constexpr int VEC = 4, W = 128;
-    using G = PersGeom<BZ>;
+    using G = PersGeom<BZ, NW>;
     constexpr int OWN = G::OWN;
     using VT = float4;
     extern __shared__ __align__(16) unsigned char smem[];
@@ -266,30 +267,37 @@ __global__ void __launch_bounds__(PTHREADS, 1) k_prop_pers(const Rep* __restrict
 
 // Host side ---------------------------------------------------------------------------------
 
-bool pers_supported(const Rep& R, int bz, int nsm) {
+bool pers_supported(const Rep& R, int bz, int nw, int nsm) {
     if (R.nx != 128 || R.ny % PBY || R.nz % bz) return false;
+    if (!((bz == 16 && nw == 16) || (bz == 8 && (nw == 16 || nw == 8)))) return false;
     const int nb = (R.ny / PBY) * (R.nz / bz);
-    return nb >= 1 && nb <= nsm && (PBY * bz) % PWARPS == 0;
+    return nb >= 1 && nb <= nsm * (nw == 8 ? 2 : 1);   // all bricks co-resident
 }
 
 int pers_bricks(const Rep& R, int bz) { return (R.ny / PBY) * (R.nz / bz); }
 
-int pers_prepare(int bz) {
-    const int sm = (int)pers_smem_bytes(4, bz);
-    cudaError_t e = cudaSuccess;
-    if (bz == 16) {
-        e = cudaFuncSetAttribute(k_prop_pers<16, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_prop_pers<16, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-    } else if (bz == 8) {
-        e = cudaFuncSetAttribute(k_prop_pers<8, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_prop_pers<8, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-    } else {
-        return (int)cudaErrorInvalidValue;
-    }
-    return (int)e;
+namespace {
+template <int BZ, int NW>
+cudaError_t pers_attr() {
+    const int sm = (int)pers_smem_bytes(4, BZ);
+    cudaError_t e = cudaFuncSetAttribute(k_prop_pers<BZ, false, NW>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_prop_pers<BZ, true, NW>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_prop_pers<BZ, false, NW>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_prop_pers<BZ, true, NW>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    return e;
+}
+}  // namespace
+
+int pers_prepare(int bz, int nw) {
+    if (bz == 16 && nw == 16) return (int)pers_attr<16, 16>();
+    if (bz == 8 && nw == 16) return (int)pers_attr<8, 16>();
+    if (bz == 8 && nw == 8) return (int)pers_attr<8, 8>();
+    return (int)cudaErrorInvalidValue;
 }
 
-int launch_prop_pers(const Launch& L, bool bwd, int bz, int nbricks, int* flags, int* abortf, int limit) {
+int launch_prop_pers(const Launch& L, bool bwd, int bz, int nw, int nbricks, int* flags, int* abortf, int limit) {
     PersCtl ctl;
     ctl.flags = flags;
     ctl.abort = abortf;
@@ -297,7 +305,7 @@ int launch_prop_pers(const Launch& L, bool bwd, int bz, int nbricks, int* flags,
     ctl.limit = limit;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(nbricks);
-    cfg.blockDim = dim3(PTHREADS);
+    cfg.blockDim = dim3(32 * nw);
     cfg.dynamicSmemBytes = pers_smem_bytes(4, bz);
     cfg.stream = L.stream;
     cudaLaunchAttribute attr[1];
@@ -307,11 +315,14 @@ int launch_prop_pers(const Launch& L, bool bwd, int bz, int nbricks, int* flags,
     cfg.numAttrs = 1;
     cudaError_t e;
     if (bz == 16)
-        e = bwd ? cudaLaunchKernelEx(&cfg, k_prop_pers<16, true>, L.reps, ctl)
-                : cudaLaunchKernelEx(&cfg, k_prop_pers<16, false>, L.reps, ctl);
+        e = bwd ? cudaLaunchKernelEx(&cfg, k_prop_pers<16, true, 16>, L.reps, ctl)
+                : cudaLaunchKernelEx(&cfg, k_prop_pers<16, false, 16>, L.reps, ctl);
+    else if (nw == 16)
+        e = bwd ? cudaLaunchKernelEx(&cfg, k_prop_pers<8, true, 16>, L.reps, ctl)
+                : cudaLaunchKernelEx(&cfg, k_prop_pers<8, false, 16>, L.reps, ctl);
     else
-        e = bwd ? cudaLaunchKernelEx(&cfg, k_prop_pers<8, true>, L.reps, ctl)
-                : cudaLaunchKernelEx(&cfg, k_prop_pers<8, false>, L.reps, ctl);
+        e = bwd ? cudaLaunchKernelEx(&cfg, k_prop_pers<8, true, 8>, L.reps, ctl)
+                : cudaLaunchKernelEx(&cfg, k_prop_pers<8, false, 8>, L.reps, ctl);
     return (int)e;
 }
 

@@ -101,13 +101,17 @@ def test_fused_contour_groups_fp32_within_1e5(case, kfuse):
 PERSISTENT_CASES = [melt((128, 16, 32), 7, 3), solution((128, 8, 24), 6, 4), melt((128, 24, 16), 12, 5)]
 
 
+@pytest.mark.parametrize("depth", [8, 16])
 @pytest.mark.parametrize("cfg", PERSISTENT_CASES, ids=lambda c: "x".join(map(str, c["grid"])) + f"_ns{c['ns']}")
-def test_persistent_sweeps_fp32_within_1e5(cfg):
-    """One-launch-per-sweep contour kernel (bricks exchanging halos through L2) against the oracle."""
+def test_persistent_sweeps_fp32_within_1e5(cfg, depth):
+    """One-launch-per-sweep contour kernel (bricks exchanging halos through L2) against the oracle,
+    with bricks of 16 planes (one CTA per SM) and of 8 planes (two CTAs per SM)."""
+    if cfg["grid"][2] % depth:
+        pytest.skip("brick depth does not divide nz")
     U = inputs.random_field(ncomp_shape(cfg), seed=10, scale=0.5)
     ref, _, _ = oracle.densities(cfg, U)
     ctx = dscf.Context(cfg, dscf.FP32)
-    ctx.set_tuning(8, 0)
+    ctx.set_tuning(depth, 0)
     assert ctx.diagnostics()["kfuse"] == 0
     for _ in range(2):      # twice: the brick step counters carry over between launches
         got = t2n(ctx.densities(torch.from_numpy(U)))
@@ -149,16 +153,16 @@ def test_persistent_step_matches_multi_launch():
     cfg = melt((128, 16, 16), 8, 3, hydro=1, ncg_iters=2, cn_sweeps=4)
     phi, U, dn = random_state(cfg, 91)
     outs = []
-    for kfuse in (1, 0):
+    for kfuse, zc in ((1, 8), (0, 8), (0, 16)):
         ctx = dscf.Context(cfg, dscf.FP32)
-        ctx.set_tuning(8, kfuse)
+        ctx.set_tuning(zc, kfuse)
         ctx.set(dscf.PHI, torch.from_numpy(phi).cuda())
         ctx.set(dscf.U, torch.from_numpy(U).cuda())
         ctx.set(dscf.POP, torch.from_numpy(dn).cuda())
         ctx.step(3)
         ctx.status()
         outs.append(t2n(ctx.get(dscf.PHI)))
-    assert rel(outs[1], outs[0]) < 1e-5
+    assert rel(outs[1], outs[0]) < 1e-5 and rel(outs[2], outs[0]) < 1e-5
 
 
 def test_fused_step_fp32_matches_single_step():
