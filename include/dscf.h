@@ -159,6 +159,16 @@ int dscf_diagnostics(dscf_ctx* ctx, int32_t replica, double* out);
 /* Synchronise the stream and return the device status word as an error code (DSCF_OK,
  * DSCF_ERR_TIMEOUT if a persistent sweep gave up a bounded wait, DSCF_ERR_NUMERIC) or
  * DSCF_ERR_CUDA if a kernel failed. */
+/* Observables of replica `replica` at the current state (Sec. 3; Eq. 1 restated in volume
+ * fractions with constants dropped): out[0] free energy per site
+ *   F = -(phi_p / N) ln Q - (1 - phi_p) ln <e^{-U_S}> - <sum_I U_I phi_I>
+ *       + <1/2 sum_IJ chi_IJ phi_I sigma[phi_J] + kappa/2 (sum_I phi_I - 1)^2>
+ * with Q from an exact density evaluation at the current U (the solvent term only with three
+ * species); out[1] order parameter S = sqrt(<sum_I (phi_I - <phi_I>)^2>) (Fig. 1); out[2]
+ * segregation <|phi_A + phi_B - <phi_A> - <phi_B>|> (Fig. 3).  Sums in FP64 from per-block
+ * partials in a fixed order.  Runs one density evaluation and synchronises the stream. */
+int dscf_observables(dscf_ctx* ctx, int32_t replica, double* out);
+
 int dscf_status(dscf_ctx* ctx);
 
 /* Release host-side state (graph, capture stream).  The workspace stays the caller's. */

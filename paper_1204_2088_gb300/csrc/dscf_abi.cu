@@ -780,6 +780,52 @@ int dscf_set_fields(dscf_ctx* c, int32_t which, const void* src, int32_t on_host
     return cuda_check(c, cudaGetLastError(), "set field");
 }
 
+int dscf_observables(dscf_ctx* c, int32_t replica, double* out) {
+    if (!c || !out) return c ? fail(c, DSCF_ERR_ARG, "NULL output") : DSCF_ERR_ARG;
+    if (replica < 0 || replica >= c->nrep) return fail(c, DSCF_ERR_ARG, "replica out of range");
+    if (int rc = set_dev(c)) return rc;
+    // exact densities at the current potentials: Q (and the solvent sum) of Eq. 2
+    int rc = c->prec == DSCF_FP64 ? refresh_phim<double>(c) : refresh_phim<float>(c);
+    if (rc) return rc;
+    const Launch L = launch_of(c, c->stream);
+    const Rep& R = c->L.reps[replica];
+    const int nb = R.nblk;
+    std::vector<double> h((size_t)5 * nb);
+    double qq[2] = {0.0, 0.0};
+    if (c->prec == DSCF_FP64) launch_obs1<double>(L); else launch_obs1<float>(L);
+    for (int k = 0; k < 5 && !rc; ++k)
+        rc = cuda_check(c, cudaMemcpyAsync(h.data() + (size_t)k * nb, R.part + (size_t)(P_OBS0 + k) * R.part_stride,
+                                           sizeof(double) * nb, cudaMemcpyDeviceToHost, c->stream), "observables");
+    if (!rc) rc = cuda_check(c, cudaMemcpyAsync(qq, R.scal + S_Q, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->stream),
+                             "observables");
+    if (!rc) rc = cuda_check(c, cudaStreamSynchronize(c->stream), "observables sync");
+    if (rc) return rc;
+    double sum[5] = {0, 0, 0, 0, 0};
+    for (int k = 0; k < 5; ++k)
+        for (int i = 0; i < nb; ++i) sum[k] += h[(size_t)k * nb + i];   // fixed order
+    const double V = (double)R.V;
+    const double m[3] = {sum[0] / V, sum[1] / V, sum[2] / V};
+    if (c->prec == DSCF_FP64) launch_obs2<double>(L, m[0], m[1], m[2]); else launch_obs2<float>(L, m[0], m[1], m[2]);
+    for (int k = 0; k < 2 && !rc; ++k)
+        rc = cuda_check(c, cudaMemcpyAsync(h.data() + (size_t)k * nb, R.part + (size_t)(P_OBS0 + k) * R.part_stride,
+                                           sizeof(double) * nb, cudaMemcpyDeviceToHost, c->stream), "observables");
+    if (!rc) rc = cuda_check(c, cudaStreamSynchronize(c->stream), "observables sync");
+    if (rc) return rc;
+    double s2 = 0.0, seg = 0.0;
+    for (int i = 0; i < nb; ++i) {
+        s2 += h[i];
+        seg += h[(size_t)nb + i];
+    }
+    const dscf_params& p = c->params[replica];
+    double F = -p.phi_p / (double)p.N * std::log(qq[0]);
+    if (p.ns == 3) F -= (1.0 - p.phi_p) * std::log(qq[1]);
+    F += (-sum[3] + sum[4]) / V;
+    out[0] = F;
+    out[1] = std::sqrt(s2 / V);
+    out[2] = seg / V;
+    return DSCF_OK;
+}
+
 int dscf_diagnostics(dscf_ctx* c, int32_t replica, double* out) {
     if (!c || !out || replica < 0 || replica >= c->nrep) return c ? fail(c, DSCF_ERR_ARG, "bad replica") : DSCF_ERR_ARG;
     if (int rc = set_dev(c)) return rc;

@@ -30,6 +30,7 @@ enum PartSlot {
     P_MASS0, P_MASS1, P_MASS2,   // sum_r phi_I after the convection-diffusion update
     P_RHO, P_JX, P_JY, P_JZ,     // LB mass and momentum
     P_UMAX,      // max |u_lat|
+    P_OBS0, P_OBS1, P_OBS2, P_OBS3, P_OBS4, P_OBS5,   // observables (dscf_observables)
     NPART
 };
 
@@ -212,6 +213,13 @@ template <typename T> void launch_exp(const Launch& L, int mode, int k, const vo
 template <typename T> void launch_trial(const Launch& L, int net = 0);
 template <typename T> void launch_grad(const Launch& L, int k, int net = 0);
 void launch_pred_err(const Launch& L);   // max |q - phi_m| of replica 0 into scal[S_PERR] (FP32 melts)
+// Observables: pass 1 leaves per-block sums of phi_I (slots P_OBS0..2), U.phi (P_OBS3) and the
+// interaction energy density (P_OBS4); pass 2, given the species means, sum (phi_I - <phi_I>)^2
+// over I (P_OBS0) and |phi_A + phi_B - <phi_A> - <phi_B>| (P_OBS1).
+template <typename T>
+void launch_obs1(const Launch& L);
+template <typename T>
+void launch_obs2(const Launch& L, double mA, double mB, double mS);
 // mode 0: init (d = -g), mode 1: iteration k direction update
 template <typename T> void launch_dir(const Launch& L, int mode, int k);
 template <typename T> void launch_mu(const Launch& L, int K);

@@ -863,6 +863,77 @@ __global__ void __launch_bounds__(kFlatThreads) k_pred_err_fin(const Rep* __rest
     const double t = reduce_parts_max(slot(R, P_GMAX), R.nblk, sh);
     if (threadIdx.x == 0) R.scal[S_PERR] = t;
 }
+// Free-energy terms and composition sums (Eq. 1 in volume-fraction units, constants dropped):
+// per block, sum_r phi_I, sum_r sum_I U_I phi_I and sum_r [1/2 sum_IJ chi_IJ phi_I sigma[phi_J] +
+// kappa/2 (sum_I phi_I - 1)^2].
+template <typename T>
+__global__ void __launch_bounds__(kFlatThreads) k_obs1(const Rep* __restrict__ reps, const int* __restrict__ blk2rep) {
+    __shared__ double sh[33];
+    FLAT_PROLOGUE
+    const int nx = R.nx, ny = R.ny, nz = R.nz, ns = R.ns;
+    const T al = (T)R.alpha, be = (T)(1.0 - 2.0 * R.alpha);
+    const T* phi = (const T*)R.phi;
+    const T* U = (const T*)R.U;
+    T sp[3] = {T(0), T(0), T(0)}, up = T(0), inter = T(0);
+    for (int i = i0 + threadIdx.x; i < i1; i += kFlatThreads) {
+        int x, y, z;
+        site_xyz(i, nx, ny, x, y, z);
+        T sg[3], ph[3], tot = T(0);
+        for (int J = 0; J < ns; ++J) {
+            ph[J] = phi[(size_t)J * V + i];
+            sg[J] = sigma_at(phi + (size_t)J * V, x, y, z, nx, ny, nz, al, be);
+            tot += ph[J];
+            sp[J] += ph[J];
+            up += U[(size_t)J * V + i] * ph[J];
+        }
+        T e = T(0);
+        for (int I = 0; I < ns; ++I)
+            for (int J = 0; J < ns; ++J) e += T(0.5) * (T)R.chi[I * 3 + J] * ph[I] * sg[J];
+        e += T(0.5) * (T)R.kappa * (tot - T(1)) * (tot - T(1));
+        inter += e;
+    }
+    const double vals[5] = {(double)sp[0], (double)sp[1], (double)sp[2], (double)up, (double)inter};
+    for (int k = 0; k < 5; ++k) {
+        const double t = block_sum(vals[k], sh);
+        if (threadIdx.x == 0) slot(R, P_OBS0 + k)[lb] = t;
+    }
+}
+// Order parameters of Fig. 1 and Fig. 3 given the species means.
+template <typename T>
+__global__ void __launch_bounds__(kFlatThreads) k_obs2(const Rep* __restrict__ reps, const int* __restrict__ blk2rep,
+                                                      double mA, double mB, double mS) {
+    __shared__ double sh[33];
+    FLAT_PROLOGUE
+    const T* phi = (const T*)R.phi;
+    const double m[3] = {mA, mB, mS};
+    double s2 = 0.0, seg = 0.0;
+    for (int i = i0 + threadIdx.x; i < i1; i += kFlatThreads) {
+        for (int I = 0; I < R.ns; ++I) {
+            const double d = (double)phi[(size_t)I * V + i] - m[I];
+            s2 += d * d;
+        }
+        seg += fabs((double)phi[i] + (double)phi[(size_t)V + i] - mA - mB);
+    }
+    const double t2 = block_sum(s2, sh);
+    const double ts = block_sum(seg, sh);
+    if (threadIdx.x == 0) {
+        slot(R, P_OBS0)[lb] = t2;
+        slot(R, P_OBS1)[lb] = ts;
+    }
+}
+template <typename T>
+void launch_obs1(const Launch& L) {
+    k_obs1<T><<<L.nblk_total, kFlatThreads, 0, L.stream>>>(L.reps, L.blk2rep);
+}
+template <typename T>
+void launch_obs2(const Launch& L, double mA, double mB, double mS) {
+    k_obs2<T><<<L.nblk_total, kFlatThreads, 0, L.stream>>>(L.reps, L.blk2rep, mA, mB, mS);
+}
+template void launch_obs1<float>(const Launch&);
+template void launch_obs1<double>(const Launch&);
+template void launch_obs2<float>(const Launch&, double, double, double);
+template void launch_obs2<double>(const Launch&, double, double, double);
+
 void launch_pred_err(const Launch& L) {
     k_pred_err<<<L.nblk_total, kFlatThreads, 0, L.stream>>>(L.reps);
     k_pred_err_fin<<<1, kFlatThreads, 0, L.stream>>>(L.reps);

@@ -87,6 +87,7 @@ def load():
         "dscf_net_last_error": (ctypes.c_char_p, [vp]),
         "dscf_set_predictor": (ctypes.c_int, [vp, vp, i32, ctypes.c_double, i32]),
         "dscf_set_wait_limit": (ctypes.c_int, [vp, i32]),
+        "dscf_observables": (ctypes.c_int, [vp, i32, ctypes.POINTER(ctypes.c_double)]),
         "dscf_net_set_tensor_path": (ctypes.c_int, [vp, i32]),
         "dscf_net_tensor_path": (i32, [vp]),
         "dscf_net_status": (ctypes.c_int, [vp]),
@@ -257,6 +258,12 @@ class Context:
 
     def status(self):
         self._check(self.lib.dscf_status(self.h))
+
+    def observables(self, replica=0):
+        """Free energy per site, order parameter S and segregation of a replica (synchronises)."""
+        out = (ctypes.c_double * 3)()
+        self._check(self.lib.dscf_observables(self.h, int(replica), out))
+        return {"free_energy": out[0], "order_parameter": out[1], "segregation": out[2]}
 
     def set_predictor(self, net, corrector_every=10, tol=1e-3, ncg_iters=0):
         """Attach a trained Net (same grid, batch 1) as the density map of the inversion, judged

@@ -249,7 +249,7 @@ def test_trained_predictor_gain_over_the_exact_method():
     g = torch.Generator().manual_seed(0)
     for it in range(iters):
         idx = torch.randint(0, T0, (B,), generator=g)
-        net.train_step(U[idx], P[idx], phibar, lr=1e-3 * 0.5 * (1 + np.cos(np.pi * it / iters)) + 1e-5)
+        net.train_step(U[idx], P[idx], phibar, lr=3e-4 * 0.5 * (1 + np.cos(np.pi * it / iters)) + 1e-6)
     one.set_params(net.get_params())
     e1 = held_out_err()
     assert e1 < 0.1 * e0 and e1 < 3e-3, (e0, e1)

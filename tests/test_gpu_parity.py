@@ -282,6 +282,31 @@ def test_batched_replicas_bit_identical_to_solo():
         off += n
 
 
+@pytest.mark.parametrize("cfg", [STEP_CASES[0], STEP_CASES[3]], ids=["melt", "solution"])
+def test_observables_match_oracle(cfg):
+    """Free energy (Eq. 1), order parameter (Fig. 1) and segregation (Fig. 3) of the GPU's own
+    state after two steps against the oracle's functions of the same fields: FP64 to 1e-10, FP32
+    to the FP32 bound."""
+    phi, U, dn = random_state(cfg, 71)
+    for prec, tol in ((dscf.FP64, 1e-10), (dscf.FP32, 2e-5)):
+        ctx = dscf.Context(cfg, prec)
+        ctx.set(dscf.PHI, torch.from_numpy(phi).cuda())
+        ctx.set(dscf.U, torch.from_numpy(U).cuda())
+        ctx.set(dscf.POP, torch.from_numpy(dn).cuda())
+        ctx.step(2)
+        obs = ctx.observables()
+        ctx.status()
+        gphi, gU = t2n(ctx.get(dscf.PHI)), t2n(ctx.get(dscf.U))
+        F = oracle.free_energy(cfg, gU, gphi)
+        S = oracle.order_parameter(cfg, gphi)
+        seg = oracle.segregation(cfg, gphi)
+        # F is a difference of O(1) terms: compare on the scale of its largest term
+        scale = max(abs(F), float(np.abs(gU * gphi).sum(0).mean()), 1.0)
+        assert abs(obs["free_energy"] - F) < tol * scale, (prec, obs["free_energy"], F)
+        assert abs(obs["order_parameter"] - S) < tol * S + 1e-12, (prec, obs["order_parameter"], S)
+        assert abs(obs["segregation"] - seg) < tol * max(seg, 1e-3), (prec, obs["segregation"], seg)
+
+
 def test_lb_step_alone_with_external_force():
     cfg = melt((14, 9, 11), 4, 2, tau_s=0.65, tau_b=1.7)
     _, w, _, _ = oracle.lb_basis()
