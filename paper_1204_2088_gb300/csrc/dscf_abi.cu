@@ -175,7 +175,7 @@ Layout make_layout(const dscf_params* p, int n, int prec, char* base) {
     L.off_reps = off; take(sizeof(Rep) * n);
     L.off_t2r = off; take(sizeof(int) * max_tiles_total);
     L.off_b2r = off; take(sizeof(int) * max_blk_total);
-    L.off_status = off; take(sizeof(int) * (kFlagBase + kMaxBricks));
+    L.off_status = off; take(sizeof(int) * (kFlagBase + 2 * kMaxBricks));
     L.bytes = off;
     return L;
 }
@@ -221,6 +221,7 @@ struct dscf_ctx {
     int kfuse = 1;          // contour steps per propagator launch (1 = single-step kernels, 0 = persistent)
     int pers_bz = 0;        // brick depth of the persistent sweeps (0 = not available)
     int pers_nw = 16;       // warps per CTA of the persistent sweeps
+    bool pers_perm = false; // brick placement table in use
     int wait_limit = kPersSpinLimit;   // polls before a persistent sweep gives up on a neighbour
     int nsm = 0;
     bool fusable = false;   // FP32 and every replica in the whole-row layout
@@ -267,6 +268,32 @@ int reset_pers_flags(dscf_ctx* c) {
                       "re-arming the brick counters");
 }
 
+// Brick placement: the CTAs of a sweep-shaped cooperative launch land on SMs in a fixed pattern
+// that scatters consecutive CTA indices over the GPCs (and both dies).  Bricks are given to the
+// CTAs in the order of their SM ids instead, so that the bricks of one z slab (consecutive brick
+// indices, y fastest) share a GPC and neighbouring slabs sit on neighbouring GPCs.  The table is
+// a permutation: correctness does not depend on the placement actually repeating.
+int place_bricks(dscf_ctx* c) {
+    c->pers_perm = false;
+    const int nb = pers_bricks(c->L.reps[0], c->pers_bz);
+    int* d_perm = c->d_status + kFlagBase + kMaxBricks;
+    int rc = cuda_check(c, (cudaError_t)pers_placement(c->pers_bz, c->pers_nw, nb, d_perm, c->stream), "placement probe");
+    std::vector<int> smid(nb), order(nb), perm(nb);
+    if (!rc) rc = cuda_check(c, cudaMemcpyAsync(smid.data(), d_perm, sizeof(int) * nb, cudaMemcpyDeviceToHost, c->stream),
+                             "placement probe");
+    if (!rc) rc = cuda_check(c, cudaStreamSynchronize(c->stream), "placement probe");
+    if (rc) return rc;
+    for (int i = 0; i < nb; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return smid[a] < smid[b]; });
+    for (int r = 0; r < nb; ++r) perm[order[r]] = r;
+    rc = cuda_check(c, cudaMemcpyAsync(d_perm, perm.data(), sizeof(int) * nb, cudaMemcpyHostToDevice, c->stream),
+                    "placement table");
+    if (!rc) rc = cuda_check(c, cudaStreamSynchronize(c->stream), "placement table");
+    if (!rc) c->pers_perm = true;
+    return rc;
+}
+const int* perm_of(const dscf_ctx* c) { return c->pers_perm ? c->d_status + kFlagBase + kMaxBricks : nullptr; }
+
 // Forward and backward contour sweeps of one gradient evaluation.
 template <typename T>
 int64_t enqueue_sweeps(dscf_ctx* c, const Launch& L) {
@@ -275,8 +302,8 @@ int64_t enqueue_sweeps(dscf_ctx* c, const Launch& L) {
     if (K == 0) {
         const int nb = pers_bricks(c->L.reps[0], c->pers_bz);
         int* flags = c->d_status + kFlagBase;
-        launch_prop_pers(L, false, c->pers_bz, c->pers_nw, nb, flags, c->d_status + 2, c->wait_limit);
-        launch_prop_pers(L, true, c->pers_bz, c->pers_nw, nb, flags, c->d_status + 2, c->wait_limit);
+        launch_prop_pers(L, false, c->pers_bz, c->pers_nw, nb, flags, c->d_status + 2, c->wait_limit, perm_of(c));
+        launch_prop_pers(L, true, c->pers_bz, c->pers_nw, nb, flags, c->d_status + 2, c->wait_limit, perm_of(c));
         return 2;
     }
     if (K > 1) {
@@ -508,7 +535,7 @@ int autotune_zc(dscf_ctx* c) {
                 auto run = [&]() {
                     if (K == 0) {
                         launch_prop_pers(L, false, c->pers_bz, c->pers_nw, pers_bricks(c->L.reps[0], c->pers_bz),
-                                         c->d_status + kFlagBase, c->d_status + 2, kPersSpinLimit);
+                                         c->d_status + kFlagBase, c->d_status + 2, kPersSpinLimit, perm_of(c));
                     } else if (c->prec == DSCF_FP64) {
                         enqueue_sweeps<double>(c, L);
                     } else {
@@ -533,12 +560,14 @@ int autotune_zc(dscf_ctx* c) {
                 c->pers_bz = pc.first;
                 c->pers_nw = pc.second;
                 if (int rc = reset_pers_flags(c)) return rc;
+                if (int rc = place_bricks(c)) return rc;
                 const float t = sweep_ms(0, 0);
                 if (t < tp) { tp = t; pbest = pc; }
             }
             c->pers_bz = pbest.first;
             c->pers_nw = pbest.second;
             if (int rc = reset_pers_flags(c)) return rc;
+            if (int rc = place_bricks(c)) return rc;
             const float tm = sweep_ms(bestK, best);
             int st = 0;
             cudaMemcpy(&st, c->d_status, sizeof(int), cudaMemcpyDeviceToHost);
@@ -602,7 +631,7 @@ int dscf_init(const dscf_params* p, int32_t n, int32_t precision, void* workspac
     rc = rc ? rc : chk(cudaMemcpyAsync(c->d_reps, c->L.reps.data(), sizeof(Rep) * n, cudaMemcpyHostToDevice, c->stream), "reps");
     rc = rc ? rc : chk(cudaMemcpyAsync(c->d_t2r, c->L.tile2rep.data(), sizeof(int) * c->L.ntiles, cudaMemcpyHostToDevice, c->stream), "t2r");
     rc = rc ? rc : chk(cudaMemcpyAsync(c->d_b2r, c->L.blk2rep.data(), sizeof(int) * c->L.nblk, cudaMemcpyHostToDevice, c->stream), "b2r");
-    rc = rc ? rc : chk(cudaMemsetAsync(c->d_status, 0, sizeof(int) * (kFlagBase + kMaxBricks), c->stream), "status");
+    rc = rc ? rc : chk(cudaMemsetAsync(c->d_status, 0, sizeof(int) * (kFlagBase + 2 * kMaxBricks), c->stream), "status");
     const size_t es = precision == DSCF_FP64 ? 8 : 4;
     for (int r = 0; r < n && !rc; ++r) {
         const Rep& R = c->L.reps[r];
@@ -1011,6 +1040,7 @@ int dscf_set_tuning(dscf_ctx* c, int32_t zc, int32_t kfuse) {
         c->pers_bz = pbz;
         c->pers_nw = pnw;
         if (int rc = reset_pers_flags(c)) return rc;
+        if (int rc = place_bricks(c)) return rc;
     }
     c->zc = zc;
     c->kfuse = kfuse;

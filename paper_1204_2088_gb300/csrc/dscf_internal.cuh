@@ -235,7 +235,10 @@ size_t pers_smem_bytes(int vec, int bz);
 bool pers_supported(const Rep& R, int bz, int nw, int nsm);   // nw: warps per CTA (16, or 8 with 2 CTAs per SM)
 int pers_bricks(const Rep& R, int bz);
 int pers_prepare(int bz, int nw);                                                                  // cudaError_t
-int launch_prop_pers(const Launch& L, bool bwd, int bz, int nw, int nbricks, int* flags, int* abortf, int limit);  // cudaError_t
+int launch_prop_pers(const Launch& L, bool bwd, int bz, int nw, int nbricks, int* flags, int* abortf, int limit,
+                     const int* perm);  // cudaError_t
+// SM id of each CTA of a sweep-shaped cooperative launch (cudaError_t)
+int pers_placement(int bz, int nw, int nbricks, int* d_smid, cudaStream_t stream);
 
 }  // namespace dscf
 

@@ -43,10 +43,11 @@ __device__ __forceinline__ void st_release(int* p, int v) {
 }
 
 struct PersCtl {
-    int* flags;     // one step counter per brick
-    int* abort;     // set by a CTA that gave up waiting
-    int* status;    // device status word
-    int limit;      // polls before giving up
+    int* flags;        // one step counter per brick
+    int* abort;        // set by a CTA that gave up waiting
+    int* status;       // device status word
+    const int* perm;   // brick of each CTA (NULL: brick = CTA index)
+    int limit;         // polls before giving up
 };
 
 // Wait until every neighbour brick has published `target`; threads 0..7 poll one neighbour each.
@@ -105,7 +106,7 @@ __global__ void __launch_bounds__(32 * NW, 16 / NW) k_prop_pers(const Rep* __res
     const int plane = W * ny;
     const size_t V = (size_t)R.V;
     const int nby = ny / PBY, nbz = nz / BZ;
-    const int b = blockIdx.x;
+    const int b = ctl.perm ? ctl.perm[blockIdx.x] : (int)blockIdx.x;
     const int by = b % nby, bz = b / nby;
     const int y0 = by * PBY, z0 = bz * BZ;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -297,11 +298,49 @@ int pers_prepare(int bz, int nw) {
     return (int)cudaErrorInvalidValue;
 }
 
-int launch_prop_pers(const Launch& L, bool bwd, int bz, int nw, int nbricks, int* flags, int* abortf, int limit) {
+namespace {
+// The SM that runs each CTA of a launch shaped like the sweep (same block size, shared memory
+// and cooperative attribute), for the placement of bricks on SMs.
+template <int NW>
+__global__ void __launch_bounds__(32 * NW, 16 / NW) k_pers_place(int* smid) {
+    if (threadIdx.x == 0) {
+        unsigned id;
+        asm volatile("mov.u32 %0, %%smid;" : "=r"(id));
+        smid[blockIdx.x] = (int)id;
+    }
+}
+}  // namespace
+
+int pers_placement(int bz, int nw, int nbricks, int* d_smid, cudaStream_t stream) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(nbricks);
+    cfg.blockDim = dim3(32 * nw);
+    cfg.dynamicSmemBytes = pers_smem_bytes(4, bz);
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaError_t e;
+    if (nw == 16) {
+        e = cudaFuncSetAttribute(k_pers_place<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cfg.dynamicSmemBytes);
+        if (e == cudaSuccess) e = cudaLaunchKernelEx(&cfg, k_pers_place<16>, d_smid);
+    } else {
+        e = cudaFuncSetAttribute(k_pers_place<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cfg.dynamicSmemBytes);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_pers_place<8>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+        if (e == cudaSuccess) e = cudaLaunchKernelEx(&cfg, k_pers_place<8>, d_smid);
+    }
+    return (int)e;
+}
+
+int launch_prop_pers(const Launch& L, bool bwd, int bz, int nw, int nbricks, int* flags, int* abortf, int limit,
+                     const int* perm) {
     PersCtl ctl;
     ctl.flags = flags;
     ctl.abort = abortf;
     ctl.status = L.status;
+    ctl.perm = perm;
     ctl.limit = limit;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(nbricks);
