@@ -175,7 +175,7 @@ Layout make_layout(const dscf_params* p, int n, int prec, char* base) {
     L.off_reps = off; take(sizeof(Rep) * n);
     L.off_t2r = off; take(sizeof(int) * max_tiles_total);
     L.off_b2r = off; take(sizeof(int) * max_blk_total);
-    L.off_status = off; take(sizeof(int) * (kFlagBase + 2 * kMaxBricks));
+    L.off_status = off; take(sizeof(int) * ((size_t)kFlagBase + (size_t)kMaxBricks * (kFlagStride + 1)));
     L.bytes = off;
     return L;
 }
@@ -264,7 +264,7 @@ Launch launch_of(dscf_ctx* c, cudaStream_t s) {
 // The persistent sweeps require equal step counters of all bricks at launch: re-arm them whenever
 // the brick decomposition changes.
 int reset_pers_flags(dscf_ctx* c) {
-    return cuda_check(c, cudaMemsetAsync(c->d_status + kFlagBase, 0, sizeof(int) * kMaxBricks, c->stream),
+    return cuda_check(c, cudaMemsetAsync(c->d_status + kFlagBase, 0, sizeof(int) * (size_t)kMaxBricks * kFlagStride, c->stream),
                       "re-arming the brick counters");
 }
 
@@ -276,7 +276,7 @@ int reset_pers_flags(dscf_ctx* c) {
 int place_bricks(dscf_ctx* c) {
     c->pers_perm = false;
     const int nb = pers_bricks(c->L.reps[0], c->pers_bz);
-    int* d_perm = c->d_status + kFlagBase + kMaxBricks;
+    int* d_perm = c->d_status + kFlagBase + (size_t)kMaxBricks * kFlagStride;
     int rc = cuda_check(c, (cudaError_t)pers_placement(c->pers_bz, c->pers_nw, nb, d_perm, c->stream), "placement probe");
     std::vector<int> smid(nb), order(nb), perm(nb);
     if (!rc) rc = cuda_check(c, cudaMemcpyAsync(smid.data(), d_perm, sizeof(int) * nb, cudaMemcpyDeviceToHost, c->stream),
@@ -292,7 +292,9 @@ int place_bricks(dscf_ctx* c) {
     if (!rc) c->pers_perm = true;
     return rc;
 }
-const int* perm_of(const dscf_ctx* c) { return c->pers_perm ? c->d_status + kFlagBase + kMaxBricks : nullptr; }
+const int* perm_of(const dscf_ctx* c) {
+    return c->pers_perm ? c->d_status + kFlagBase + (size_t)kMaxBricks * kFlagStride : nullptr;
+}
 
 // Forward and backward contour sweeps of one gradient evaluation.
 template <typename T>
@@ -631,7 +633,7 @@ int dscf_init(const dscf_params* p, int32_t n, int32_t precision, void* workspac
     rc = rc ? rc : chk(cudaMemcpyAsync(c->d_reps, c->L.reps.data(), sizeof(Rep) * n, cudaMemcpyHostToDevice, c->stream), "reps");
     rc = rc ? rc : chk(cudaMemcpyAsync(c->d_t2r, c->L.tile2rep.data(), sizeof(int) * c->L.ntiles, cudaMemcpyHostToDevice, c->stream), "t2r");
     rc = rc ? rc : chk(cudaMemcpyAsync(c->d_b2r, c->L.blk2rep.data(), sizeof(int) * c->L.nblk, cudaMemcpyHostToDevice, c->stream), "b2r");
-    rc = rc ? rc : chk(cudaMemsetAsync(c->d_status, 0, sizeof(int) * (kFlagBase + 2 * kMaxBricks), c->stream), "status");
+    rc = rc ? rc : chk(cudaMemsetAsync(c->d_status, 0, sizeof(int) * ((size_t)kFlagBase + (size_t)kMaxBricks * (kFlagStride + 1)), c->stream), "status");
     const size_t es = precision == DSCF_FP64 ? 8 : 4;
     for (int r = 0; r < n && !rc; ++r) {
         const Rep& R = c->L.reps[r];
@@ -904,7 +906,7 @@ int dscf_status(dscf_ctx* c) {
         // the fields are invalid, but every launch has finished.  Re-arm the brick step counters,
         // the abort flag and the status bit so that the context can be used again once the
         // caller has restored its fields.
-        cudaError_t e = cudaMemsetAsync(c->d_status + kFlagBase, 0, sizeof(int) * kMaxBricks, c->stream);
+        cudaError_t e = cudaMemsetAsync(c->d_status + kFlagBase, 0, sizeof(int) * (size_t)kMaxBricks * kFlagStride, c->stream);
         if (e == cudaSuccess) e = cudaMemsetAsync(c->d_status + 2, 0, sizeof(int), c->stream);
         const int clear = st & ~(int)ST_TIMEOUT;
         if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_status, &clear, sizeof(int), cudaMemcpyHostToDevice, c->stream);
@@ -942,7 +944,8 @@ int dscf_inject_lag(dscf_ctx* c, int32_t brick) {
     // a counter far behind the others: the brick's neighbours wait for step values it never
     // publishes during the next sweep, the brick itself sees its neighbours ahead and runs through
     const int lag = -(1 << 24);
-    cudaError_t e = cudaMemcpyAsync(c->d_status + kFlagBase + brick, &lag, sizeof(int), cudaMemcpyHostToDevice, c->stream);
+    cudaError_t e = cudaMemcpyAsync(c->d_status + kFlagBase + (size_t)brick * kFlagStride, &lag, sizeof(int),
+                                    cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     return cuda_check(c, e, "inject lag");
 }

@@ -43,7 +43,7 @@ __device__ __forceinline__ void st_release(int* p, int v) {
 }
 
 struct PersCtl {
-    int* flags;        // one step counter per brick
+    int* flags;        // one step counter per brick, kFlagStride ints apart
     int* abort;        // set by a CTA that gave up waiting
     int* status;       // device status word
     const int* perm;   // brick of each CTA (NULL: brick = CTA index)
@@ -53,7 +53,7 @@ struct PersCtl {
 // Wait until every neighbour brick has published `target`; threads 0..7 poll one neighbour each.
 __device__ __forceinline__ void wait_nb(const PersCtl& c, const int* nb, int target, bool& aborted) {
     if (threadIdx.x < 8 && !aborted) {
-        const int* f = c.flags + nb[threadIdx.x];
+        const int* f = c.flags + (size_t)nb[threadIdx.x] * kFlagStride;
         int spins = 0;
         while (ld_acquire(f) < target) {
             if (ld_acquire(c.abort) != 0) break;
@@ -125,7 +125,7 @@ __global__ void __launch_bounds__(32 * NW, 16 / NW) k_prop_pers(const Rep* __res
         const int y = (y0 + r + ny) % ny, z = (z0 + pl + nz) % nz;
         hoff[h] = z * plane + y * W;
     }
-    const int c0 = ctl.flags[b];       // step counters of all bricks are equal at launch
+    const int c0 = ctl.flags[(size_t)b * kFlagStride];   // step counters of all bricks are equal at launch
     __syncthreads();
     bool aborted = ld_acquire(ctl.abort) != 0;
 
@@ -245,7 +245,7 @@ __global__ void __launch_bounds__(32 * NW, 16 / NW) k_prop_pers(const Rep* __res
         __syncthreads();
         if (threadIdx.x == 0) {
             __threadfence();
-            st_release(ctl.flags + b, c0 + j + 1);
+            st_release(ctl.flags + (size_t)b * kFlagStride, c0 + j + 1);
         }
         if (BWD && s > 1) prefetch_gs(s - 1);   // GS slots of this thread were read above
 #pragma unroll
