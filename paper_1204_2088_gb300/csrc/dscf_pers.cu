@@ -50,23 +50,30 @@ struct PersCtl {
     int limit;         // polls before giving up
 };
 
-// Wait until every neighbour brick has published `target`; threads 0..7 poll one neighbour each.
+// Wait until every neighbour brick has published `target`; threads 0..7 poll one neighbour each
+// (each counter on its own cache line).  Only the pollers look at the shared abort flag, and only
+// every 32 polls, so that the waits of all CTAs do not contend on one line.
 __device__ __forceinline__ void wait_nb(const PersCtl& c, const int* nb, int target, bool& aborted) {
     if (threadIdx.x < 8 && !aborted) {
         const int* f = c.flags + (size_t)nb[threadIdx.x] * kFlagStride;
         int spins = 0;
         while (ld_acquire(f) < target) {
-            if (ld_acquire(c.abort) != 0) break;
-            if (++spins > c.limit) {
-                atomicOr(c.status, (int)ST_TIMEOUT);
-                atomicExch(c.abort, 1);
-                break;
+            if ((++spins & 31) == 0) {
+                if (ld_acquire(c.abort) != 0) {
+                    aborted = true;
+                    break;
+                }
+                if (spins > c.limit) {
+                    atomicOr(c.status, (int)ST_TIMEOUT);
+                    atomicExch(c.abort, 1);
+                    aborted = true;
+                    break;
+                }
             }
-            __nanosleep(64);
+            __nanosleep(32);
         }
     }
     __syncthreads();
-    if (!aborted && ld_acquire(c.abort) != 0) aborted = true;
 }
 
 template <int BZ, int NW>
