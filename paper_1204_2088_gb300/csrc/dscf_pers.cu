@@ -247,13 +247,12 @@ __global__ void __launch_bounds__(32 * NW, 16 / NW) k_prop_pers(const Rep* __res
             }
             if (is_boundary(p0 + k) && (!BWD || s > 1)) *(VT*)(dst + own0 + (size_t)k * plane) = out[k];
         }
-        // publish the boundary of this step; the fence waits for every memory operation the SM
-        // has in flight, so nothing else is issued before it
+        // publish the boundary of this step: the CTA barrier orders every thread's boundary stores
+        // before thread 0's release store, and release is cumulative, so a CTA whose acquire load
+        // reads the new counter sees them.  The release waits for the memory operations the SM
+        // has in flight, so nothing else is issued before it.
         __syncthreads();
-        if (threadIdx.x == 0) {
-            __threadfence();
-            st_release(ctl.flags + (size_t)b * kFlagStride, c0 + j + 1);
-        }
+        if (threadIdx.x == 0) st_release(ctl.flags + (size_t)b * kFlagStride, c0 + j + 1);
         if (BWD && s > 1) prefetch_gs(s - 1);   // GS slots of this thread were read above
 #pragma unroll
         for (int k = 0; k < OWN; ++k) {

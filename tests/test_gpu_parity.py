@@ -119,6 +119,21 @@ def test_persistent_sweeps_fp32_within_1e5(cfg, depth):
         assert rel(got, ref) < 1e-5
 
 
+@pytest.mark.parametrize("depth", [8, 16])
+def test_persistent_sweeps_are_deterministic(depth):
+    """Race check of the brick handshake (release store after the CTA barrier, acquire loads of
+    the neighbours' counters): the density map of the persistent sweep, repeated, is bitwise the
+    same every time (a halo row read before its neighbour published it would perturb it)."""
+    cfg = PERSISTENT_CASES[0]
+    U = torch.from_numpy(inputs.random_field(ncomp_shape(cfg), seed=13, scale=0.5))
+    ctx = dscf.Context(cfg, dscf.FP32)
+    ctx.set_tuning(depth, 0)
+    first = ctx.densities(U)
+    for _ in range(20):
+        assert torch.equal(ctx.densities(U), first)
+    ctx.status()
+
+
 def test_persistent_sweep_timeout_is_reported_and_the_context_recovers():
     """Failure detection without a GPU fault: one brick's step counter is set far behind (host
     side), so its neighbours wait for a value nobody publishes; their bounded waits run out, the
