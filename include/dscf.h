@@ -123,6 +123,13 @@ size_t dscf_workspace_bytes(const dscf_params* p, int32_t n_replicas, int32_t pr
 int dscf_init(const dscf_params* p, int32_t n_replicas, int32_t precision, void* workspace,
               size_t workspace_bytes, void* stream, dscf_ctx** out);
 
+/* dscf_init with a given tuning instead of the autotuner (zc, kfuse as in dscf_set_tuning, for
+ * instance the values dscf_diagnostics reported after an earlier dscf_init on the same replica
+ * shapes and device): no timing runs.  zc < 0 runs the autotuner (= dscf_init).  DSCF_ERR_ARG if
+ * the tuning is not valid for these replicas. */
+int dscf_init_tuned(const dscf_params* p, int32_t n_replicas, int32_t precision, void* workspace,
+                    size_t workspace_bytes, void* stream, int32_t zc, int32_t kfuse, dscf_ctx** out);
+
 /* Advance every replica by n_steps coupled time steps (steps 1-4 above).  The step sequence
  * is captured once into a CUDA graph and launched n_steps times on the context stream. */
 int dscf_step(dscf_ctx* ctx, int32_t n_steps);
@@ -149,8 +156,9 @@ int dscf_set_fields(dscf_ctx* ctx, int32_t which, const void* src, int32_t on_ho
  *  (6..10 are reduced from the current populations and velocity when this is called),
  *  11 Q of the last gradient evaluation, 12 <exp(-U_S)>, 13 NCG iterations per step,
  *  14 <g,g> and 15 max|g| at the start of the last inversion, 16 <g,g> and 17 max|g|
- *  at its end, 18 steps done, 19 z-chunk of the propagator tiles and 20 contour steps fused
- *  per propagator launch, both chosen by the autotuner at dscf_init, 21 steps taken with the
+ *  at its end, 18 steps done, 19 z-chunk of the propagator tiles (the brick depth when 20 is 0)
+ *  and 20 contour steps fused per propagator launch (0: persistent sweeps), as chosen at
+ *  dscf_init or by dscf_set_tuning, 21 steps taken with the
  *  learned predictor and 22 exact steps since dscf_set_predictor, 23 the predictor's last
  *  judged error (see dscf_set_predictor; -1 before the first judgement).  Slots 13, 16 and 17
  *  follow the inversion of the last step taken (a predictor step may use fewer iterations). */
@@ -186,8 +194,9 @@ int64_t dscf_launches_per_step(const dscf_ctx* ctx);
  * persistent sweeps (one launch per sweep; one FP32 replica with nx = 128 and ny, nz multiples
  * of 8; bricks of 128 x 8 x 16 sites, one CTA of 16 warps per SM, or of 128 x 8 x 8 sites, two
  * CTAs of 8 warps per SM, all co-resident).  With kfuse = 0, zc = 16 or 8 selects the brick depth
- * (DSCF_ERR_ARG if the grid does not allow it), any other zc keeps the autotuner's choice.  Synchronises the stream; the next dscf_step re-captures
- * its graph.  Results do not depend on either value beyond rounding. */
+ * (8 planes: two CTAs of 8 warps per SM where the grid allows it, else one of 16; DSCF_ERR_ARG if
+ * the grid allows neither), any other zc keeps the current depth.  Synchronises the stream; the
+ * next dscf_step re-captures its graph.  Results do not depend on either value beyond rounding. */
 int dscf_set_tuning(dscf_ctx* ctx, int32_t zc, int32_t kfuse);
 
 /* Failure detection of the persistent sweeps.  Every wait of a persistent sweep on a

@@ -456,6 +456,38 @@ void set_zc(dscf_ctx* c, int zc) {
     assign_tiles(c->L, c->params.data(), c->nrep);
 }
 
+// Persistent-sweep candidates: bricks of 16 planes (16 warps, one CTA per SM) or, where the depth
+// does not divide, of 8 planes; and bricks of 8 planes with 8 warps, two CTAs per SM.  The first
+// becomes the context's persistent configuration.
+int pers_select(dscf_ctx* c, std::vector<std::pair<int, int>>& pcand) {
+    c->pers_bz = 0;
+    pcand.clear();
+    if (c->nrep == 1 && c->prec == DSCF_FP32) {
+        const int nsm = std::min(c->nsm, kMaxBricks / 2);
+        if (pers_supported(c->L.reps[0], 16, 16, nsm)) pcand.push_back({16, 16});
+        else if (pers_supported(c->L.reps[0], 8, 16, nsm)) pcand.push_back({8, 16});
+        if (pers_supported(c->L.reps[0], 8, 8, nsm)) pcand.push_back({8, 8});
+    }
+    for (auto& pc : pcand)
+        if (int rc = cuda_check(c, (cudaError_t)pers_prepare(pc.first, pc.second), "persistent sweep set-up")) return rc;
+    if (!pcand.empty()) {
+        c->pers_bz = pcand[0].first;
+        c->pers_nw = pcand[0].second;
+    }
+    return DSCF_OK;
+}
+
+// Fusion support and its shared-memory limit (needed before any fused launch).
+int fusion_setup(dscf_ctx* c) {
+    c->fusable = (c->prec == DSCF_FP32);
+    for (const Rep& R : c->L.reps) c->fusable = c->fusable && (R.vec > 0);
+    if (c->fusable) {
+        const size_t lim = prop_fused_smem_bytes(4, 4);
+        return cuda_check(c, (cudaError_t)prop_fused_set_smem_limit(lim), "fused shared-memory limit");
+    }
+    return DSCF_OK;
+}
+
 // Autotuner: pick the z-chunk of the propagator tiles and the number of contour steps fused per
 // launch (one pair for all replicas) by timing forward contour launches on the context's own
 // buffers; the figure of merit is time per contour step.  Small problems keep the defaults.
@@ -464,12 +496,7 @@ int autotune_zc(dscf_ctx* c) {
     int Nmin = 1 << 30;
     for (const Rep& R : c->L.reps) { Vtot += R.V; Nmin = std::min(Nmin, R.N); }
     int best = default_zc(c->L.reps[0].nz), bestK = 1;
-    c->fusable = (c->prec == DSCF_FP32);
-    for (const Rep& R : c->L.reps) c->fusable = c->fusable && (R.vec > 0);
-    if (c->fusable) {
-        const size_t lim = prop_fused_smem_bytes(4, 4);
-        if (int rc = cuda_check(c, (cudaError_t)prop_fused_set_smem_limit(lim), "fused shared-memory limit")) return rc;
-    }
+    if (int rc = fusion_setup(c)) return rc;
     if (Vtot >= 32 * 32 * 32) {
         cudaEvent_t e0, e1;
         if (int rc = cuda_check(c, cudaEventCreate(&e0), "tune event")) return rc;
@@ -509,18 +536,8 @@ int autotune_zc(dscf_ctx* c) {
         cudaEventDestroy(e1);
     }
     // persistent sweeps: one replica, FP32, whole 128-site rows; timed against the best above
-    // Candidates: bricks of 16 planes (16 warps, one CTA per SM) or, where the depth does not
-    // divide, of 8 planes; and bricks of 8 planes with 8 warps, two CTAs per SM.
-    c->pers_bz = 0;
     std::vector<std::pair<int, int>> pcand;
-    if (c->nrep == 1 && c->prec == DSCF_FP32) {
-        const int nsm = std::min(c->nsm, kMaxBricks / 2);
-        if (pers_supported(c->L.reps[0], 16, 16, nsm)) pcand.push_back({16, 16});
-        else if (pers_supported(c->L.reps[0], 8, 16, nsm)) pcand.push_back({8, 16});
-        if (pers_supported(c->L.reps[0], 8, 8, nsm)) pcand.push_back({8, 8});
-    }
-    for (auto& pc : pcand)
-        if (int rc = cuda_check(c, (cudaError_t)pers_prepare(pc.first, pc.second), "persistent sweep set-up")) return rc;
+    if (int rc = pers_select(c, pcand)) return rc;
     if (!pcand.empty()) {
         c->pers_bz = pcand[0].first;
         c->pers_nw = pcand[0].second;
@@ -577,10 +594,22 @@ int autotune_zc(dscf_ctx* c) {
             if (tp < tm) bestK = 0;
         }
     }
-    c->zc = best;
+    c->zc = bestK == 0 ? c->pers_bz : best;   // with persistent sweeps the brick depth
     c->kfuse = bestK;
     set_zc(c, bestK == 0 ? c->pers_bz : best);
     return upload_tiles(c);
+}
+// A tuning chosen earlier (for instance cached from an autotuner run) instead of the autotuner.
+int apply_tuning(dscf_ctx* c, int zc, int kfuse) {
+    std::vector<std::pair<int, int>> pcand;
+    if (int rc = pers_select(c, pcand)) return rc;
+    if (int rc = fusion_setup(c)) return rc;
+    if (int rc = dscf_set_tuning(c, zc, kfuse)) return rc;
+    if (kfuse == 0) {
+        if (int rc = reset_pers_flags(c)) return rc;
+        if (int rc = place_bricks(c)) return rc;
+    }
+    return DSCF_OK;
 }
 }  // namespace
 
@@ -595,6 +624,11 @@ size_t dscf_workspace_bytes(const dscf_params* p, int32_t n, int32_t precision) 
 
 int dscf_init(const dscf_params* p, int32_t n, int32_t precision, void* workspace, size_t wbytes, void* stream,
               dscf_ctx** out) {
+    return dscf_init_tuned(p, n, precision, workspace, wbytes, stream, -1, -1, out);
+}
+
+int dscf_init_tuned(const dscf_params* p, int32_t n, int32_t precision, void* workspace, size_t wbytes, void* stream,
+                    int32_t zc, int32_t kfuse, dscf_ctx** out) {
     if (!out) return fail(nullptr, DSCF_ERR_ARG, "out is NULL");
     *out = nullptr;
     std::string why;
@@ -662,7 +696,7 @@ int dscf_init(const dscf_params* p, int32_t n, int32_t precision, void* workspac
         const int e = precision == DSCF_FP64 ? prop_set_smem_limit<double>(lim) : prop_set_smem_limit<float>(lim);
         rc = cuda_check(c, (cudaError_t)e, "propagator shared-memory limit");
     }
-    rc = rc ? rc : autotune_zc(c);
+    if (!rc) rc = (zc < 0) ? autotune_zc(c) : apply_tuning(c, zc, kfuse);
     if (rc) {
         g_init_error = c->err;
         if (c->cap) cudaStreamDestroy(c->cap);
@@ -1045,9 +1079,9 @@ int dscf_set_tuning(dscf_ctx* c, int32_t zc, int32_t kfuse) {
         if (int rc = reset_pers_flags(c)) return rc;
         if (int rc = place_bricks(c)) return rc;
     }
-    c->zc = zc;
+    c->zc = kfuse == 0 ? c->pers_bz : zc;
     c->kfuse = kfuse;
-    set_zc(c, kfuse == 0 ? c->pers_bz : zc);
+    set_zc(c, c->zc);
     return upload_tiles(c);
 }
 

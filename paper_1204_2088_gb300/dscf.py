@@ -8,6 +8,7 @@ fallback: if the library is missing or fails to load, every call raises.
 from __future__ import annotations
 
 import ctypes
+import json
 import os
 
 import numpy as np
@@ -59,6 +60,7 @@ def load():
     sigs = {
         "dscf_workspace_bytes": (sz, [P, i32, i32]),
         "dscf_init": (ctypes.c_int, [P, i32, i32, vp, sz, vp, ctypes.POINTER(vp)]),
+        "dscf_init_tuned": (ctypes.c_int, [P, i32, i32, vp, sz, vp, i32, i32, ctypes.POINTER(vp)]),
         "dscf_step": (ctypes.c_int, [vp, i32]),
         "dscf_densities": (ctypes.c_int, [vp, vp, vp]),
         "lb_step": (ctypes.c_int, [vp, vp, i32]),
@@ -155,13 +157,39 @@ def densities_static(cfg: dict, U: torch.Tensor, out: torch.Tensor, precision=FP
     return out
 
 
+def _tuning_key(cfgs, precision, device) -> str:
+    name = torch.cuda.get_device_name(device)
+    shapes = [[list(c["grid"]), c.get("ns", 2), int(c["N"])] for c in cfgs]
+    return json.dumps([name, int(precision), shapes])
+
+
+def _tuning_cache_read(path) -> dict:
+    try:
+        with open(path) as f:
+            return {k: tuple(v) for k, v in json.load(f).items()}
+    except (OSError, ValueError):
+        return {}
+
+
+def _tuning_cache_write(path, key, tuning):
+    d = _tuning_cache_read(path)
+    d[key] = list(tuning)
+    tmp = f"{path}.tmp{os.getpid()}"
+    with open(tmp, "w") as f:
+        json.dump({k: list(v) for k, v in d.items()}, f, indent=1)
+    os.replace(tmp, path)
+
+
 class Context:
     """One library context: n replicas (a dict or a list of dicts), one precision, one device.
 
     Field tensors use the layout of include/dscf.h: for one replica [ncomp, nz, ny, nx], for
     several the replica blocks concatenated into one flat tensor."""
 
-    def __init__(self, cfgs, precision=FP64, device=None, stream=None):
+    def __init__(self, cfgs, precision=FP64, device=None, stream=None, tuning=None, tuning_cache=None):
+        """tuning: (zc, kfuse) to use instead of the autotuner; tuning_cache: path of a JSON file
+        mapping (device, precision, replica shapes) to the tuning the autotuner chose, read before
+        and written after the autotuner runs."""
         self.lib = load()
         self.cfgs = [cfgs] if isinstance(cfgs, dict) else list(cfgs)
         self.n = len(self.cfgs)
@@ -174,12 +202,20 @@ class Context:
             raise DSCFError(-1, "invalid parameters")
         self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        key = None
+        if tuning is None and tuning_cache is not None:
+            key = _tuning_key(self.cfgs, precision, self.device)
+            tuning = _tuning_cache_read(tuning_cache).get(key)
         h = ctypes.c_void_p()
-        rc = self.lib.dscf_init(self._params, self.n, precision, ctypes.c_void_p(self.workspace.data_ptr()),
-                                nbytes, ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h))
+        zc, kfuse = (int(tuning[0]), int(tuning[1])) if tuning is not None else (-1, -1)
+        rc = self.lib.dscf_init_tuned(self._params, self.n, precision, ctypes.c_void_p(self.workspace.data_ptr()),
+                                      nbytes, ctypes.c_void_p(self.stream.cuda_stream), zc, kfuse, ctypes.byref(h))
         if rc != DSCF_OK:
             raise DSCFError(rc, self.lib.dscf_last_error(None).decode())
         self.h = h
+        if key is not None and tuning is None:
+            d = self.diagnostics()
+            _tuning_cache_write(tuning_cache, key, (d["zc"], d["kfuse"]))
         self.V = [c["grid"][0] * c["grid"][1] * c["grid"][2] for c in self.cfgs]
         self.ns = [c.get("ns", 2) for c in self.cfgs]
 

@@ -65,3 +65,21 @@ def test_init_rejects_null_output(lib):
     rc = lib.dscf_init(ctypes.byref(p), 1, 0, None, 0, None, None)
     assert rc == -1
     assert b"NULL" in lib.dscf_last_error(None)
+
+
+def test_init_tuned_rejects_null_output(lib):
+    p = dscf.make_params(inputs.melt((8, 8, 8), 4, 0.5, 10.0))
+    rc = lib.dscf_init_tuned(ctypes.byref(p), 1, 0, None, 0, None, 4, 1, None)
+    assert rc == -1
+
+
+def test_tuning_cache_round_trip(tmp_path):
+    path = str(tmp_path / "tuning.json")
+    assert dscf._tuning_cache_read(path) == {}
+    dscf._tuning_cache_write(path, "a", (16, 0))
+    dscf._tuning_cache_write(path, "b", (8, 4))
+    dscf._tuning_cache_write(path, "a", (11, 2))
+    assert dscf._tuning_cache_read(path) == {"a": (11, 2), "b": (8, 4)}
+    with open(path, "w") as f:
+        f.write("{not json")
+    assert dscf._tuning_cache_read(path) == {}

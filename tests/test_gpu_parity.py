@@ -180,6 +180,31 @@ def test_persistent_step_matches_multi_launch():
     assert rel(outs[1], outs[0]) < 1e-5 and rel(outs[2], outs[0]) < 1e-5
 
 
+def test_cached_tuning_reproduces_the_autotuned_context(tmp_path):
+    cfg = melt((128, 16, 16), 8, 3, hydro=1, ncg_iters=2, cn_sweeps=4)
+    phi, U, dn = random_state(cfg, 93)
+    cache = tmp_path / "tuning.json"
+    outs, tunings = [], []
+    for _ in range(2):   # the first context runs the autotuner and writes the cache, the second reads it
+        ctx = dscf.Context(cfg, dscf.FP32, tuning_cache=str(cache))
+        d = ctx.diagnostics()
+        tunings.append((d["zc"], d["kfuse"]))
+        assert cache.exists()
+        ctx.set(dscf.PHI, torch.from_numpy(phi).cuda())
+        ctx.set(dscf.U, torch.from_numpy(U).cuda())
+        ctx.set(dscf.POP, torch.from_numpy(dn).cuda())
+        ctx.step(2)
+        ctx.status()
+        outs.append(t2n(ctx.get(dscf.PHI)))
+    assert tunings[0] == tunings[1]
+    assert np.array_equal(outs[0], outs[1])
+    with pytest.raises(dscf.DSCFError):
+        dscf.Context(cfg, dscf.FP32, tuning=(4, 9))
+    bad = melt((64, 16, 16), 8, 3, hydro=1)
+    with pytest.raises(dscf.DSCFError):
+        dscf.Context(bad, dscf.FP32, tuning=(8, 0))   # persistent sweeps need nx = 128
+
+
 def test_fused_step_fp32_matches_single_step():
     cfg = melt((32, 16, 24), 10, 4, hydro=1, ncg_iters=2, cn_sweeps=4)
     phi, U, dn = random_state(cfg, 81)
