@@ -39,7 +39,7 @@ class Params(ctypes.Structure):
         ("a", ctypes.c_double), ("dt", ctypes.c_double), ("M", ctypes.c_double),
         ("tau_s", ctypes.c_double), ("tau_b", ctypes.c_double), ("rho0", ctypes.c_double),
         ("hydro", ctypes.c_int32), ("ncg_iters", ctypes.c_int32), ("cn_sweeps", ctypes.c_int32),
-        ("phi_floor", ctypes.c_double),
+        ("phi_floor", ctypes.c_double), ("ncg_tol", ctypes.c_double),
     ]
 
 
@@ -57,7 +57,7 @@ def lib():
             "or_sigma": (None, [P, D, D]),
             "or_densities": (ctypes.c_double, [P, D, D, D, D]),
             "or_objective": (ctypes.c_double, [P, D, D]),
-            "or_ncg": (None, [P, D, D, D, D]),
+            "or_ncg": (ctypes.c_int, [P, D, D, D, D]),
             "or_mu": (None, [P, D, D, D]),
             "or_force": (None, [P, D, D, D]),
             "or_lb_basis": (None, [D, D, D, ctypes.POINTER(ctypes.c_int)]),
@@ -103,6 +103,7 @@ def make_params(cfg: dict) -> Params:
     p.ncg_iters = cfg.get("ncg_iters", 4)
     p.cn_sweeps = cfg.get("cn_sweeps", 8)
     p.phi_floor = cfg.get("phi_floor", 1e-6)
+    p.ncg_tol = cfg.get("ncg_tol", 0.0)
     return p
 
 
@@ -156,13 +157,20 @@ def objective(cfg: dict, U: np.ndarray, phi_target: np.ndarray) -> float:
 
 
 def ncg(cfg: dict, phi_target: np.ndarray, U0: np.ndarray):
-    """Fixed-count Fletcher-Reeves inversion.  Returns (U, phi_model, info)."""
+    """Fletcher-Reeves inversion: at most ncg_iters iterations, fewer once max|g| < ncg_tol
+    (if ncg_tol > 0).  Returns (U, phi_model, info); ncg_run also gives the iterations run."""
+    U, phim, info, _ = ncg_run(cfg, phi_target, U0)
+    return U, phim, info
+
+
+def ncg_run(cfg: dict, phi_target: np.ndarray, U0: np.ndarray):
+    """As ncg, also returning the number of iterations run."""
     p = make_params(cfg)
     U = _f64(U0).copy()
     phim = np.empty_like(U)
     info = np.zeros(2 + 4 * max(cfg.get("ncg_iters", 4), 0))
-    lib().or_ncg(ctypes.byref(p), _ptr(_f64(phi_target)), _ptr(U), _ptr(phim), _ptr(info))
-    return U, phim, info
+    k = lib().or_ncg(ctypes.byref(p), _ptr(_f64(phi_target)), _ptr(U), _ptr(phim), _ptr(info))
+    return U, phim, info, k
 
 
 def mu(cfg: dict, U: np.ndarray, phi: np.ndarray) -> np.ndarray:

@@ -43,6 +43,7 @@ typedef struct {
     int32_t ncg_iters;   /* Fletcher-Reeves iterations per time step                     */
     int32_t cn_sweeps;   /* Jacobi sweeps for the Crank-Nicolson system                  */
     double phi_floor;    /* floor on phi inside the local curvature of mu              */
+    double ncg_tol;      /* > 0: stop the inversion once max|phi* - phi[U]| < ncg_tol    */
 } or_params;
 
 static inline int64_t nsites(const or_params* p) { return (int64_t)p->nx * p->ny * p->nz; }
@@ -179,17 +180,19 @@ static double dotv(const double* a, const double* b, int64_t n) {
 
 /* ------------------------------------------------------------------------------------ */
 /* Fletcher-Reeves nonlinear conjugate gradient on L(U) (Sec. 2, last paragraph).        */
-/* Fixed iteration count (no data-dependent exit), secant line search with one trial      */
-/* point whose step comes from the local curvature <d, phi[U] d> (the large-wavevector     */
-/* limit of the Hessian of L).  Per iteration k:                                           */
+/* At most ncg_iters iterations; with ncg_tol > 0 the inversion also stops before an       */
+/* iteration whose starting residual max|g| is below ncg_tol (or not a number).  Secant    */
+/* line search with one trial point whose step comes from the local curvature             */
+/* <d, phi[U] d> (the large-wavevector limit of the Hessian of L).  Per iteration k:       */
 /*   h0 = <g,d>, c = <d, phi_m d>, a1 = -h0/c                   (trial step)             */
 /*   h1 = <phi* - phi[U + a1 d], d>                                                        */
 /*   a  = a1 * (-h0) / (h1 - h0)                                (secant root)             */
 /*   U += a d;  g' = phi* - phi[U];  beta = <g',g'>/<g,g>;  d = -g' + beta d              */
 /* U is updated in place; phi_model receives phi[U] at the final U.                       */
-/* info (length 2 + 4*K): gg0, max|g0|, then per iteration a1, a, gg, max|g|.             */
+/* info (length 2 + 4*K): gg0, max|g0|, then per iteration a1, a, gg, max|g|; the entries  */
+/* of iterations not run are left untouched.  Returns the number of iterations run.       */
 /* ------------------------------------------------------------------------------------ */
-void or_ncg(const or_params* p, const double* phi_target, double* U, double* phi_model, double* info) {
+int or_ncg(const or_params* p, const double* phi_target, double* U, double* phi_model, double* info) {
     const int64_t V = nsites(p);
     const int64_t n = (int64_t)p->ns * V;
     double* g = (double*)malloc(sizeof(double) * (size_t)n);
@@ -207,7 +210,9 @@ void or_ncg(const or_params* p, const double* phi_target, double* U, double* phi
     double gg = dotv(g, g, n);
     if (info) { info[0] = gg; info[1] = gmax; }
 
-    for (int k = 0; k < p->ncg_iters; ++k) {
+    int k = 0;
+    for (; k < p->ncg_iters; ++k) {
+        if (p->ncg_tol > 0.0 && !(gmax >= p->ncg_tol)) break;
         double h0 = dotv(g, d, n);
         double c = 0.0;
         for (int64_t i = 0; i < n; ++i) c += d[i] * phi_model[i] * d[i];
@@ -237,6 +242,7 @@ void or_ncg(const or_params* p, const double* phi_target, double* U, double* phi
         }
     }
     free(g); free(d); free(Ut); free(pt);
+    return k;
 }
 
 /* ------------------------------------------------------------------------------------ */

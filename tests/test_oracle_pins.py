@@ -181,6 +181,53 @@ def test_ncg_uniform_target_keeps_zero_potential():
     assert np.abs(phim - 0.5).max() < 1e-14
 
 
+def _residual_history(info, K):
+    """max|g| at the start of iterations 0..K (info layout of oracle.ncg)."""
+    return [info[1]] + [info[2 + 4 * k + 3] for k in range(K)]
+
+
+def test_ncg_tolerance_stop_is_a_truncated_fixed_count_run():
+    cfg = cfg_small(grid=(4, 5, 3), N=6, nA=3, ncg_iters=8)
+    Utrue = inputs.random_field((2, 3, 5, 4), seed=33, scale=0.4)
+    target, _, _ = oracle.densities(cfg, Utrue)
+    U0 = np.zeros_like(Utrue)
+    _, _, info_full = oracle.ncg(cfg, target, U0)
+    r = _residual_history(info_full, 8)
+    j = 3
+    assert min(r[:j]) > 1.01 * r[j]
+    tol = 1.005 * r[j]
+    Ut, pt, info_t, k = oracle.ncg_run(dict(cfg, ncg_tol=tol), target, U0)
+    Uf, pf, info_f, kf = oracle.ncg_run(dict(cfg, ncg_iters=j), target, U0)
+    assert k == j and kf == j
+    assert np.array_equal(Ut, Uf) and np.array_equal(pt, pf)
+    assert np.array_equal(info_t[:2 + 4 * j], info_f)
+    assert np.all(info_t[2 + 4 * j:] == 0.0)   # iterations not run leave their entries untouched
+
+
+def test_ncg_tolerance_above_the_start_residual_runs_no_iteration():
+    cfg = cfg_small(grid=(3, 4, 3), N=4, nA=2, ncg_iters=5)
+    target = 0.5 + 0.05 * inputs.random_field((2, 3, 4, 3), seed=35, scale=1.0)
+    U0 = inputs.random_field((2, 3, 4, 3), seed=36, scale=0.1)
+    phi0, _, _ = oracle.densities(cfg, U0)
+    gmax0 = np.abs(target - phi0).max()
+    U, phim, info, k = oracle.ncg_run(dict(cfg, ncg_tol=1.5 * gmax0), target, U0)
+    assert k == 0
+    assert np.array_equal(U, U0)
+    assert np.abs(phim - phi0).max() < 1e-15
+    assert abs(info[1] - gmax0) < 1e-15
+
+
+def test_ncg_tolerance_stop_meets_the_tolerance():
+    cfg = dict(cfg_small(grid=(4, 4, 3), N=6, nA=3, ncg_iters=300), ncg_tol=1e-9)
+    Utrue = inputs.random_field((2, 3, 4, 4), seed=31, scale=0.5)
+    target, _, _ = oracle.densities(cfg, Utrue)
+    U, phim, info, k = oracle.ncg_run(cfg, target, np.zeros_like(Utrue))
+    assert 0 < k < 300
+    assert np.abs(phim - target).max() < 1e-9              # the exit residual is the true one
+    r = _residual_history(info, k)
+    assert r[k] < 1e-9 and min(r[:k]) >= 1e-9               # and it stopped at the first crossing
+
+
 # ---------------------------------------------------------------------------------------------
 # Chemical potential (Eq. 4) and force (Eq. 8)
 # ---------------------------------------------------------------------------------------------
