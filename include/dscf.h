@@ -199,6 +199,19 @@ int64_t dscf_launches_per_step(const dscf_ctx* ctx);
  * next dscf_step re-captures its graph.  Results do not depend on either value beyond rounding. */
 int dscf_set_tuning(dscf_ctx* ctx, int32_t zc, int32_t kfuse);
 
+/* Residual stop of the inversion (step 1): with tol > 0 the Fletcher-Reeves iterations of each
+ * exact step stop before iteration k once max_r |phi*_I(r) - phi_I[U](r)| < tol for every replica
+ * (or the residual is not finite, which also sets the non-finite status bit), and after at most
+ * ncg_iters iterations in any case; tol = 0 (the default) runs exactly ncg_iters iterations.  The
+ * decision is taken on the device: every iteration is an IF node of the step's CUDA graph whose
+ * condition a one-block kernel sets from the residual the previous iteration left, so a step still
+ * costs one graph launch and no host synchronisation.  Diagnostics slot 13 then reports the
+ * iterations run in the last step; dscf_launches_per_step counts every possible launch, and the
+ * probe's sweep time (dscf_probe_ms, ms[0]) is not measured.  Steps of the learned predictor
+ * keep their fixed count.  Synchronises and re-captures the step graph.  DSCF_ERR_ARG for a
+ * negative or non-finite tol, DSCF_ERR_CUDA if the graph cannot be built. */
+int dscf_set_inversion_tol(dscf_ctx* ctx, double tol);
+
 /* Failure detection of the persistent sweeps.  Every wait of a persistent sweep on a
  * neighbouring brick is bounded by `polls` polls (default 4194304, several seconds; each poll is
  * an acquire load of the neighbour's step counter followed by a short sleep).  A CTA that runs out

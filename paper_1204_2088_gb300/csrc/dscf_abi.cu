@@ -199,7 +199,7 @@ struct dscf_ctx {
     std::vector<dscf_params> params;
     Layout L;
     char* ws = nullptr;
-    cudaStream_t stream = nullptr, cap = nullptr;
+    cudaStream_t stream = nullptr, cap = nullptr, cap_body = nullptr;   // graph capture; conditional bodies
     Rep* d_reps = nullptr;
     int* d_t2r = nullptr;
     int* d_b2r = nullptr;
@@ -223,6 +223,9 @@ struct dscf_ctx {
     int pers_nw = 16;       // warps per CTA of the persistent sweeps
     bool pers_perm = false; // brick placement table in use
     int wait_limit = kPersSpinLimit;   // polls before a persistent sweep gives up on a neighbour
+    double ncg_tol = 0.0;   // > 0: residual stop of the inversion (conditional graph nodes)
+    cudaError_t cap_err = cudaSuccess;   // first graph-construction error of a capture
+    const char* cap_what = "";
     int nsm = 0;
     bool fusable = false;   // FP32 and every replica in the whole-row layout
     long long steps = 0;
@@ -340,16 +343,89 @@ void enqueue_net(dscf_ctx* c, const Launch& L) {
     dscf_net_forward_on(c->net, L.stream, (const float*)R.E, R.phi_p * f, R.phi_p * (1.0 - f), (float*)R.q);
 }
 
+// Conditional graph nodes for the residual stop of the inversion.  During a capture on c->cap,
+// cond_begin appends an IF node on `h` after the captured work and starts capturing its body on
+// c->cap_body; cond_end ends the body, and later work on c->cap follows the IF node.
+cudaError_t cond_handle(dscf_ctx* c, cudaGraphConditionalHandle* h) {
+    cudaStreamCaptureStatus st;
+    cudaGraph_t g = nullptr;
+    c->cap_what = "capture info";
+    cudaError_t e = cudaStreamGetCaptureInfo(c->cap, &st, nullptr, &g, nullptr, nullptr, nullptr);
+    if (e != cudaSuccess) return e;
+    c->cap_what = "conditional handle";
+    return cudaGraphConditionalHandleCreate(h, g, 0, cudaGraphCondAssignDefault);
+}
+
+cudaError_t cond_begin(dscf_ctx* c, cudaGraphConditionalHandle h) {
+    cudaStreamCaptureStatus st;
+    cudaGraph_t g = nullptr;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t nd = 0;
+    c->cap_what = "capture info (dependencies)";
+    cudaError_t e = cudaStreamGetCaptureInfo(c->cap, &st, nullptr, &g, &deps, nullptr, &nd);
+    if (e != cudaSuccess) return e;
+    cudaGraphNodeParams np = {};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = h;
+    np.conditional.type = cudaGraphCondTypeIf;
+    np.conditional.size = 1;
+    cudaGraphNode_t node;
+    c->cap_what = "add IF node";
+    e = cudaGraphAddNode(&node, g, deps, nullptr, nd, &np);
+    if (e != cudaSuccess) return e;
+    c->cap_what = "capture dependencies";
+    e = cudaStreamUpdateCaptureDependencies(c->cap, &node, nullptr, 1, cudaStreamSetCaptureDependencies);
+    if (e != cudaSuccess) return e;
+    c->cap_what = "begin body capture";
+    return cudaStreamBeginCaptureToGraph(c->cap_body, np.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                         cudaStreamCaptureModeThreadLocal);
+}
+
+cudaError_t cond_end(dscf_ctx* c) {
+    c->cap_what = "launch in IF body";
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    c->cap_what = "end body capture";
+    return cudaStreamEndCapture(c->cap_body, nullptr);
+}
+
 template <typename T>
 int64_t enqueue_step(dscf_ctx* c, const Launch& L, bool pred = false) {
     const int K = pred ? c->pred_iters : c->params[0].ncg_iters;
+    // residual stop: each exact iteration k sits in an IF node whose condition (a handle of its
+    // own: a handle belongs to one conditional node) the gate kernel before it sets from the
+    // residual the previous iteration left (a skipped iteration leaves it unchanged, so once
+    // closed every later gate stays closed)
+    const bool gate = !pred && K > 0 && c->ncg_tol > 0.0;
     auto mark = [&](int i) {
-        if (c->probe && !pred) cudaEventRecordWithFlags(c->ev[i], L.stream, cudaEventRecordExternal);
+        if (c->probe && !pred && !(gate && i < 2)) cudaEventRecordWithFlags(c->ev[i], L.stream, cudaEventRecordExternal);
+    };
+    auto note = [&](cudaError_t e) {
+        if (c->cap_err == cudaSuccess && e != cudaSuccess) c->cap_err = e;
     };
     int64_t n = 0;
     mark(4);
     if (K > 0) { launch_dir<T>(L, 0, 0); ++n; }
     for (int k = 0; k < K; ++k) {
+        if (gate && c->cap_err == cudaSuccess) {
+            cudaGraphConditionalHandle h = 0;
+            note(cond_handle(c, &h));
+            if (c->cap_err != cudaSuccess) break;
+            launch_ncg_gate(L, k, c->ncg_tol, (unsigned long long)h); ++n;
+            c->cap_what = "gate launch";
+            note(cudaGetLastError());
+            note(cond_begin(c, h));
+            if (c->cap_err != cudaSuccess) break;
+            const Launch Lb = launch_of(c, c->cap_body);
+            launch_exp<T>(Lb, 1, k, nullptr); ++n;
+            n += enqueue_sweeps<T>(c, Lb);
+            launch_trial<T>(Lb); ++n;
+            n += enqueue_eval<T>(c, Lb, 2, k, nullptr);
+            launch_grad<T>(Lb, k); ++n;
+            if (k + 1 < K) { launch_dir<T>(Lb, 1, k); ++n; }
+            note(cond_end(c));
+            continue;
+        }
         if (pred) {   // both evaluations of the iteration through the learned predictor
             launch_exp<T>(L, 1, k, nullptr, 1); ++n;
             enqueue_net(c, L); n += dscf_net_forward_launches(c->net);
@@ -369,7 +445,7 @@ int64_t enqueue_step(dscf_ctx* c, const Launch& L, bool pred = false) {
         launch_grad<T>(L, k); ++n;
         if (k + 1 < K) { launch_dir<T>(L, 1, k); ++n; }
     }
-    launch_mu<T>(L, K); ++n;
+    launch_mu<T>(L, gate ? -1 : K); ++n;
     if (c->params[0].hydro) {
         mark(2);
         launch_lb<T>(L, nullptr); ++n;
@@ -397,10 +473,16 @@ int build_graph(dscf_ctx* c, bool pred = false) {
     int rc = cuda_check(c, cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal), "begin capture");
     if (rc) return rc;
     const Launch L = launch_of(c, c->cap);
+    c->cap_err = cudaSuccess;
     const int64_t n = enqueue_step<T>(c, L, pred);
     if (!pred) c->launches = n;
     cudaError_t le = cudaGetLastError();
     cudaError_t ee = cudaStreamEndCapture(c->cap, &g);
+    if (c->cap_err != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        const std::string what = std::string("inversion residual stop: ") + c->cap_what;
+        return cuda_check(c, c->cap_err, what.c_str());
+    }
     if (le != cudaSuccess) { if (g) cudaGraphDestroy(g); return cuda_check(c, le, "kernel launch during capture"); }
     if (ee != cudaSuccess) return cuda_check(c, ee, "end capture");
     cudaError_t ie = cudaGraphInstantiate(pred ? &c->exec_pred : &c->exec, g, 0);
@@ -664,6 +746,7 @@ int dscf_init_tuned(const dscf_params* p, int32_t n, int32_t precision, void* wo
     auto chk = [&](cudaError_t e, const char* w) { return cuda_check(c, e, w); };
     int rc = 0;
     rc = rc ? rc : chk(cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking), "capture stream");
+    rc = rc ? rc : chk(cudaStreamCreateWithFlags(&c->cap_body, cudaStreamNonBlocking), "capture stream");
     rc = rc ? rc : chk(cudaMemcpyAsync(c->d_reps, c->L.reps.data(), sizeof(Rep) * n, cudaMemcpyHostToDevice, c->stream), "reps");
     rc = rc ? rc : chk(cudaMemcpyAsync(c->d_t2r, c->L.tile2rep.data(), sizeof(int) * c->L.ntiles, cudaMemcpyHostToDevice, c->stream), "t2r");
     rc = rc ? rc : chk(cudaMemcpyAsync(c->d_b2r, c->L.blk2rep.data(), sizeof(int) * c->L.nblk, cudaMemcpyHostToDevice, c->stream), "b2r");
@@ -700,6 +783,7 @@ int dscf_init_tuned(const dscf_params* p, int32_t n, int32_t precision, void* wo
     if (rc) {
         g_init_error = c->err;
         if (c->cap) cudaStreamDestroy(c->cap);
+        if (c->cap_body) cudaStreamDestroy(c->cap_body);
         delete c;
         return rc;
     }
@@ -903,7 +987,8 @@ int dscf_diagnostics(dscf_ctx* c, int32_t replica, double* out) {
     }
     if (int rc = cuda_check(c, cudaMemcpyAsync(s, R.scal, sizeof s, cudaMemcpyDeviceToHost, c->stream), "diag")) return rc;
     if (int rc = cuda_check(c, cudaStreamSynchronize(c->stream), "diag sync")) return rc;
-    const int K = c->last_was_pred ? c->pred_iters : c->params[0].ncg_iters;
+    const int K = c->last_was_pred ? c->pred_iters
+                  : (c->ncg_tol > 0.0 && c->params[0].ncg_iters > 0) ? (int)s[S_NITER] : c->params[0].ncg_iters;
     std::memset(out, 0, sizeof(double) * 24);
     for (int I = 0; I < 3; ++I) {
         out[I] = s[S_MASS0 + I];
@@ -949,6 +1034,19 @@ int dscf_status(dscf_ctx* c) {
         return fail(c, DSCF_ERR_TIMEOUT, "a persistent contour sweep gave up waiting for a neighbour");
     }
     if (st & ST_NONFINITE) return fail(c, DSCF_ERR_NUMERIC, "non-finite value in a reduction");
+    return DSCF_OK;
+}
+
+int dscf_set_inversion_tol(dscf_ctx* c, double tol) {
+    if (!c) return DSCF_ERR_ARG;
+    if (!(tol >= 0.0) || !std::isfinite(tol)) return fail(c, DSCF_ERR_ARG, "tol must be finite and >= 0");
+    if (int rc = set_dev(c)) return rc;
+    if (int rc = cuda_check(c, cudaStreamSynchronize(c->stream), "inversion-tolerance sync")) return rc;
+    if (c->exec) {
+        cudaGraphExecDestroy(c->exec);
+        c->exec = nullptr;
+    }
+    c->ncg_tol = tol;
     return DSCF_OK;
 }
 
@@ -1008,7 +1106,7 @@ int dscf_probe_ms(dscf_ctx* c, float* ms) {
     if (int rc = set_dev(c)) return rc;
     if (int rc = cuda_check(c, cudaStreamSynchronize(c->stream), "probe sync")) return rc;
     ms[0] = ms[1] = ms[2] = 0.0f;
-    if (c->params[0].ncg_iters > 0)
+    if (c->params[0].ncg_iters > 0 && !(c->ncg_tol > 0.0))
         if (int rc = cuda_check(c, cudaEventElapsedTime(&ms[0], c->ev[0], c->ev[1]), "probe sweeps")) return rc;
     if (c->params[0].hydro)
         if (int rc = cuda_check(c, cudaEventElapsedTime(&ms[1], c->ev[2], c->ev[3]), "probe lb")) return rc;
@@ -1093,6 +1191,7 @@ int dscf_free(dscf_ctx* c) {
     if (c->exec) cudaGraphExecDestroy(c->exec);
     if (c->exec_pred) cudaGraphExecDestroy(c->exec_pred);
     if (c->cap) cudaStreamDestroy(c->cap);
+    if (c->cap_body) cudaStreamDestroy(c->cap_body);
     delete c;
     return DSCF_OK;
 }

@@ -39,7 +39,8 @@ enum ScalSlot {
     S_GG0 = 0, S_GMAX0 = 1,      // start of the inversion
     S_ITER0 = 2,                 // per iteration k: a1, a, gg, gmax at S_ITER0 + 4k + {0..3}
     S_Q = 160, S_QS, S_DRIFT0, S_DRIFT1, S_DRIFT2, S_MASS0, S_MASS1, S_MASS2,
-    S_RHO, S_JX, S_JY, S_JZ, S_UMAX, S_PERR
+    S_RHO, S_JX, S_JY, S_JZ, S_UMAX, S_PERR,
+    S_NITER                      // inversion iterations run in the last step (residual stop)
 };
 
 // Device status bits.
@@ -213,6 +214,10 @@ template <typename T> void launch_exp(const Launch& L, int mode, int k, const vo
 // net != 0: the density at the evaluated potential is the learned predictor's output, stored in q
 template <typename T> void launch_trial(const Launch& L, int net = 0);
 template <typename T> void launch_grad(const Launch& L, int k, int net = 0);
+// Residual stop of the inversion before iteration k: sets the graph condition `handle` to 1 while
+// max|g| >= tol for some replica (0 otherwise, also for a non-finite residual) and records the
+// iterations run in scal[S_NITER]; k = 0 also records the start-of-inversion residual.
+void launch_ncg_gate(const Launch& L, int k, double tol, unsigned long long handle);
 void launch_pred_err(const Launch& L);   // max |q - phi_m| of replica 0 into scal[S_PERR] (FP32 melts)
 // Observables: pass 1 leaves per-block sums of phi_I (slots P_OBS0..2), U.phi (P_OBS3) and the
 // interaction energy density (P_OBS4); pass 2, given the species means, sum (phi_I - <phi_I>)^2
@@ -223,7 +228,7 @@ template <typename T>
 void launch_obs2(const Launch& L, double mA, double mB, double mS);
 // mode 0: init (d = -g), mode 1: iteration k direction update
 template <typename T> void launch_dir(const Launch& L, int mode, int k);
-template <typename T> void launch_mu(const Launch& L, int K);
+template <typename T> void launch_mu(const Launch& L, int K);   // K < 0: iterations from scal[S_NITER]
 template <typename T> void launch_lb(const Launch& L, const void* force_ext);
 template <typename T> void launch_cd(const Launch& L, int sweeps);
 template <typename T> void launch_dens_out(const Launch& L, void* phi_ext);

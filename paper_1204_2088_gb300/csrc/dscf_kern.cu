@@ -261,6 +261,7 @@ __global__ void __launch_bounds__(kFlatThreads) k_mu(const Rep* __restrict__ rep
                                                      int K) {
     __shared__ double sh[33];
     FLAT_PROLOGUE
+    if (K < 0) K = (int)R.scal[S_NITER];   // iterations the residual stop let run
     if (K >= 1 && lb == 0) {
         const double gg = reduce_parts(slot(R, pslot_gg(K)), R.nblk, sh);
         const double gm = reduce_parts_max(slot(R, P_GMAX), R.nblk, sh);
@@ -933,6 +934,38 @@ template void launch_obs1<float>(const Launch&);
 template void launch_obs1<double>(const Launch&);
 template void launch_obs2<float>(const Launch&, double, double, double);
 template void launch_obs2<double>(const Launch&, double, double, double);
+
+// One block.  Every replica's residual is reduced in the same fixed order as the kernels that
+// record it, so the decision is reproducible; a non-finite residual closes the gate.
+// A non-finite <g,g> closes the gate and sets the non-finite status bit.
+__global__ void __launch_bounds__(kFlatThreads) k_ncg_gate(const Rep* __restrict__ reps, int nrep, int k, double tol,
+                                                           cudaGraphConditionalHandle handle, int* status) {
+    __shared__ double sh[33];
+    bool open = false, bad = false;
+    for (int r = 0; r < nrep; ++r) {
+        const Rep& R = reps[r];
+        const double gm = reduce_parts_max(slot(R, P_GMAX), R.nblk, sh);
+        const double gg = reduce_parts(slot(R, pslot_gg(k)), R.nblk, sh);
+        bad = bad || !isfinite(gg);
+        open = open || (gm >= tol);
+        if (k == 0 && threadIdx.x == 0) {
+            R.scal[S_GG0] = gg;
+            R.scal[S_GMAX0] = gm;
+        }
+    }
+    open = open && !bad;
+    if (threadIdx.x == 0) {
+        if (bad) atomicOr(status, (int)ST_NONFINITE);
+        for (int r = 0; r < nrep; ++r)
+            if (open || k == 0) reps[r].scal[S_NITER] = open ? (double)(k + 1) : 0.0;
+        cudaGraphSetConditional(handle, open ? 1u : 0u);
+    }
+}
+
+void launch_ncg_gate(const Launch& L, int k, double tol, unsigned long long handle) {
+    k_ncg_gate<<<1, kFlatThreads, 0, L.stream>>>(L.reps, L.nrep, k, tol, (cudaGraphConditionalHandle)handle,
+                                                 L.status);
+}
 
 void launch_pred_err(const Launch& L) {
     k_pred_err<<<L.nblk_total, kFlatThreads, 0, L.stream>>>(L.reps);

@@ -89,6 +89,7 @@ def load():
         "dscf_net_last_error": (ctypes.c_char_p, [vp]),
         "dscf_set_predictor": (ctypes.c_int, [vp, vp, i32, ctypes.c_double, i32]),
         "dscf_set_wait_limit": (ctypes.c_int, [vp, i32]),
+        "dscf_set_inversion_tol": (ctypes.c_int, [vp, ctypes.c_double]),
         "dscf_observables": (ctypes.c_int, [vp, i32, ctypes.POINTER(ctypes.c_double)]),
         "dscf_net_set_tensor_path": (ctypes.c_int, [vp, i32]),
         "dscf_net_tensor_path": (i32, [vp]),
@@ -315,6 +316,11 @@ class Context:
     def inject_lag(self, brick):
         """Test hook: make brick's step counter lag so the next persistent sweep times out."""
         self._check(self.lib.dscf_inject_lag(self.h, int(brick)))
+
+    def set_inversion_tol(self, tol):
+        """Residual stop of the inversion: at most ncg_iters iterations, fewer once max|phi* - phi[U]|
+        < tol (0: fixed count)."""
+        self._check(self.lib.dscf_set_inversion_tol(self.h, float(tol)))
 
     def set_tuning(self, zc, kfuse):
         self._check(self.lib.dscf_set_tuning(self.h, int(zc), int(kfuse)))

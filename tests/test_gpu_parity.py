@@ -292,6 +292,76 @@ def test_ncg_history_matches_oracle():
     assert abs(g["diag"]["gmax_end"] - info[-1]) < 1e-10 * max(info[-1], 1e-300) + 1e-16
 
 
+def _stop_point(info, K, margin):
+    """An iteration j and a tolerance that stops the inversion there with relative margin
+    `margin` on both sides (residuals r_0..r_{j-1} above it, r_j below it)."""
+    r = [info[1]] + [info[2 + 4 * k + 3] for k in range(K)]
+    for j in (3, 2, 4, 1, 5):
+        tol = (1.0 + margin) * r[j]
+        if min(r[:j]) > (1.0 + margin) * tol:
+            return j, tol
+    raise AssertionError(f"no clean stop point in {r}")
+
+
+def _iters_run(info, K, tol):
+    r = [info[1]] + [info[2 + 4 * k + 3] for k in range(K)]
+    k = next((k for k in range(K) if not r[k] >= tol), K)
+    return k, min(abs(x / tol - 1.0) for x in r[:k + 1] if x != 0.0)
+
+
+def test_residual_stop_fp64_matches_oracle():
+    cfg = melt((20, 12, 16), 6, 3, hydro=1, ncg_iters=8, cn_sweeps=4)
+    phi, U, dn = random_state(cfg, 61)
+    j, tol = _stop_point(run_oracle(cfg, phi, U, dn, 1)["info"], 8, 0.01)
+    for t in (tol, 10.0):   # a stop inside the inversion; a tolerance no residual reaches
+        ctx = dscf.Context(cfg, dscf.FP64)
+        ctx.set_inversion_tol(t)
+        ctx.set(dscf.PHI, torch.from_numpy(phi).cuda())
+        ctx.set(dscf.U, torch.from_numpy(U).cuda())
+        ctx.set(dscf.POP, torch.from_numpy(dn).cuda())
+        ocfg = dict(cfg, ncg_tol=t)
+        _, w, _, _ = oracle.lb_basis()
+        oph, oU, opop = phi, U, dn + w[:, None, None, None]
+        m0 = phi.reshape(phi.shape[0], -1).sum(1)
+        for step in range(3):
+            ctx.step(1)
+            ctx.status()
+            st = oracle.step(ocfg, oph, oU, opop, m0)
+            oph, oU, opop = st["phi"], st["U"], st["pop"]
+            k, gap = _iters_run(st["info"], 8, t)
+            assert gap > 1e-6   # the FP64 decision cannot flip on rounding
+            d = ctx.diagnostics()
+            assert d["ncg_iters"] == k
+            if step == 0:
+                assert k == (j if t == tol else 0)
+            for name, which, ref in (("phi", dscf.PHI, oph), ("U", dscf.U, oU), ("phim", dscf.PHIM, st["phim"]),
+                                     ("mu", dscf.MU, st["mu"])):
+                assert rel(t2n(ctx.get(which)), ref) < 1e-10, (t, step, name)
+        ctx.close()
+
+
+def test_residual_stop_with_persistent_and_multi_launch_sweeps():
+    cfg = melt((128, 16, 16), 8, 3, hydro=1, ncg_iters=6, cn_sweeps=4)
+    phi, U, dn = random_state(cfg, 63)
+    j, tol = _stop_point(run_oracle(cfg, phi, U, dn, 1)["info"], 6, 0.05)
+    o = run_oracle(dict(cfg, ncg_tol=tol), phi, U, dn, 1)
+    for zc, kfuse in ((16, 0), (8, 1), (8, 4)):
+        ctx = dscf.Context(cfg, dscf.FP32, tuning=(zc, kfuse))
+        ctx.set_inversion_tol(tol)
+        ctx.set(dscf.PHI, torch.from_numpy(phi).cuda())
+        ctx.set(dscf.U, torch.from_numpy(U).cuda())
+        ctx.set(dscf.POP, torch.from_numpy(dn).cuda())
+        ctx.step(1)
+        ctx.status()
+        assert ctx.diagnostics()["ncg_iters"] == j, (zc, kfuse)
+        assert rel(t2n(ctx.get(dscf.PHI)), o["phi"]) < 1e-5
+        assert rel(t2n(ctx.get(dscf.U)), o["U"]) < 1e-5
+        ctx.close()
+    with pytest.raises(dscf.DSCFError):
+        ctx = dscf.Context(cfg, dscf.FP32)
+        ctx.set_inversion_tol(-1.0)
+
+
 def test_step_fp32_within_tolerance():
     cfg = STEP_CASES[0]
     phi, U, dn = random_state(cfg, 51)
