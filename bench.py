@@ -40,7 +40,7 @@ def args_():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-forms", action="store_true", help="skip the FP64, learned and batched forms")
-    ap.add_argument("--forms", default="fp64,fp32_learned,batch48", help="comma-separated forms to report")
+    ap.add_argument("--forms", default="fp64,fp32_residual_stop,fp32_learned,batch48", help="comma-separated forms to report")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=20.0, help="seconds of oracle work for cpu_baseline")
     return ap.parse_args()
@@ -288,6 +288,32 @@ def learned_form(cfg, dev, phi0, timed, world, steps):
     return out
 
 
+def residual_stop_form(cfg, dev, phi0, timed, world, steps):
+    """The FP32 step with the inversion stopped on its residual (at most ncg_iters iterations,
+    fewer once max|phi* - phi[U]| < tol), after 30 fixed-count steps from the quench."""
+    from paper_1204_2088_gb300 import dscf, replicas
+    V = int(cfg["grid"][0] * cfg["grid"][1] * cfg["grid"][2])
+    ctx = dscf.Context(cfg, dscf.FP32, device=dev)
+    ctx.set(dscf.PHI, phi0)
+    ctx.step(30)
+    out = {"unit": UNIT, "steps": steps, "warmup_fixed_steps": 30}
+    for tol in (1e-4, 3e-5):
+        ctx.set_inversion_tol(tol)
+        ctx.step(3)
+        ms = timed(lambda: ctx.step(steps))
+        its, gend = [], []
+        for _ in range(steps):   # iterations actually run, one step at a time (untimed)
+            ctx.step(1)
+            d = ctx.diagnostics()
+            its.append(d["ncg_iters"])
+            gend.append(d["gmax_end"])
+        ctx.status()
+        out[f"tol_{tol:g}"] = {"value": replicas.aggregate_rate([V * steps] * world, [ms]), "ms_per_step": ms / steps,
+                               "mean_ncg_iters": sum(its) / len(its), "max_gmax_end": max(gend)}
+    ctx.close()
+    return out
+
+
 def batch48_form(dev, timed, rank, world, steps):
     """The 48 mixed-size melts (24 x 48^3, 16 x 64^3, 8 x 96^3) in one FP32 context per rank
     (the replicas split across ranks by site count), one captured graph per step."""
@@ -417,6 +443,8 @@ def run_ours(a):
                          "lb_ms": lb64}
         c64.close()
         del c64
+    if "fp32_residual_stop" in want:
+        forms["fp32_residual_stop"] = residual_stop_form(cfg, dev, phi0, timed, world, max(10, min(a.steps, 20)))
     if "fp32_learned" in want:
         forms["fp32_learned"] = learned_form(cfg, dev, phi0, timed, world, max(20, min(a.steps, 40)))
     if "batch48" in want:

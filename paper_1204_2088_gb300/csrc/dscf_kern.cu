@@ -325,9 +325,10 @@ __device__ __forceinline__ T lbw(int i) {
 // where m_4..m_9 are the Table 1 stress modes of the non-equilibrium second moment
 // Pi^neq = sum_i (n_i - n_i^eq) c_i c_i and Df_i is Eq. 14 (sum_k w_i m^f_k e_ki/b_k = Df_i).
 // The incoming populations only enter through their moments, so each outgoing population is
-// formed and stored on its own.
+// formed and stored on its own.  FP32: three CTAs per SM, so that the 19 pulled populations and
+// the force inputs stay in registers (at four the compiler spills).
 template <typename T>
-__global__ void __launch_bounds__(kFlatThreads, sizeof(T) == 4 ? 4 : 2) k_lb(const Rep* __restrict__ reps, int nrep,
+__global__ void __launch_bounds__(kFlatThreads, sizeof(T) == 4 ? 3 : 2) k_lb(const Rep* __restrict__ reps, int nrep,
                                                         const int* __restrict__ counter, const T* __restrict__ fext) {
     __shared__ double sh[33];
     int r = 0;
@@ -421,20 +422,30 @@ __global__ void __launch_bounds__(kFlatThreads, sizeof(T) == 4 ? 4 : 2) k_lb(con
         const T szz = a1 * (T(2) * uz * fz - T(2.0 / 3.0) * uf) + a2 * uf;
         const T sxy = a1 * (ux * fy + uy * fx), sxz = a1 * (ux * fz + uz * fx), syz = a1 * (uy * fz + uz * fy);
         const T trs3 = (sxx + syy + szz) * third;
+        // Every outgoing population is w_i times a quadratic form in c_i: the equilibrium
+        // (constant, linear 3 rho u.c, quadratic 9/2 rho (u.c)^2), the forcing (3/2 f.c and
+        // 9/2 (c.Sigma.c - tr Sigma / 3)) and the relaxed stress modes (quadratic in c, r_4
+        // constant).  Its ten coefficients are formed once per site; per population only the
+        // terms with non-zero velocity components remain (c_i in {0, +-1}, known at compile time).
+        const T A = drho - T(1.5) * rho * usq - T(4.5) * trs3 - r4;
+        const T Bx = T(3) * rho * ux + T(1.5) * fx, By = T(3) * rho * uy + T(1.5) * fy,
+                Bz = T(3) * rho * uz + T(1.5) * fz;
+        const T Cxx = T(4.5) * (rho * ux * ux + sxx) + r4 + r5 + r6;
+        const T Cyy = T(4.5) * (rho * uy * uy + syy) + r4 - r5 + r6;
+        const T Czz = T(4.5) * (rho * uz * uz + szz) + r4 - T(2) * r6;
+        const T Dxy = T(9) * (rho * ux * uy + sxy) + r7, Dxz = T(9) * (rho * ux * uz + sxz) + r8,
+                Dyz = T(9) * (rho * uy * uz + syz) + r9;
 #pragma unroll
         for (int i = 0; i < 19; ++i) {
-            const T cx = (T)lbc(i, 0), cy = (T)lbc(i, 1), cz = (T)lbc(i, 2);
-            const T w = lbw<T>(i);
-            const T c2 = cx * cx + cy * cy + cz * cz;
-            const T uc = ux * cx + uy * cy + uz * cz;
-            const T fc = fx * cx + fy * cy + fz * cz;
-            const T dneq = w * (drho + rho * (T(3) * uc + T(4.5) * uc * uc - T(1.5) * usq));
-            const T scc = sxx * cx * cx + syy * cy * cy + szz * cz * cz +
-                          T(2) * (sxy * cx * cy + sxz * cx * cz + syz * cy * cz);
-            const T df = T(3) * w * (fc + T(1.5) * (scc - trs3));
-            const T rel = w * (r4 * (c2 - T(1)) + r5 * (cx * cx - cy * cy) + r6 * (c2 - T(3) * cz * cz) +
-                               r7 * cx * cy + r8 * cx * cz + r9 * cy * cz);
-            dst[(size_t)i * V + site] = dneq + df - T(1.5) * w * fc + rel;
+            const int cx = lbc(i, 0), cy = lbc(i, 1), cz = lbc(i, 2);
+            T v = A;
+            if (cx) v += (cx > 0 ? Bx : -Bx) + Cxx;
+            if (cy) v += (cy > 0 ? By : -By) + Cyy;
+            if (cz) v += (cz > 0 ? Bz : -Bz) + Czz;
+            if (cx && cy) v += (cx == cy) ? Dxy : -Dxy;
+            if (cx && cz) v += (cx == cz) ? Dxz : -Dxz;
+            if (cy && cz) v += (cy == cz) ? Dyz : -Dyz;
+            dst[(size_t)i * V + site] = lbw<T>(i) * v;
         }
     }
 }
