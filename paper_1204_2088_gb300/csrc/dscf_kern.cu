@@ -257,7 +257,7 @@ __device__ __forceinline__ T sigma_at(const T* __restrict__ f, int x, int y, int
 // Chemical potentials, Eq. 4: mu_I = -U_I + sum_J chi_IJ sigma[phi_J] + kappa (sum_J phi_J - 1).
 // Block 0 of each replica also records the end-of-inversion residual.
 template <typename T>
-__global__ void __launch_bounds__(kFlatThreads) k_mu(const Rep* __restrict__ reps, const int* __restrict__ blk2rep,
+__global__ void __launch_bounds__(kFlatThreads, sizeof(T) == 4 ? 3 : 1) k_mu(const Rep* __restrict__ reps, const int* __restrict__ blk2rep,
                                                      int K) {
     __shared__ double sh[33];
     FLAT_PROLOGUE
@@ -275,6 +275,64 @@ __global__ void __launch_bounds__(kFlatThreads) k_mu(const Rep* __restrict__ rep
     const T* phi = (const T*)R.phi;
     const T* U = (const T*)R.U;
     T* mu = (T*)R.mu;
+    if constexpr (sizeof(T) == 4) {
+        if (nx == 128) {   // whole 128-site rows: one warp per row, four sites per lane
+            const int lane = threadIdx.x & 31;
+            // x pass of a periodic row held as float4 per lane (neighbours by shuffles)
+            auto xpass = [&](float4 v) {
+                const float lv = __shfl_sync(0xffffffffu, v.w, (lane + 31) & 31);
+                const float rv = __shfl_sync(0xffffffffu, v.x, (lane + 1) & 31);
+                return make_float4(be * v.x + al * (lv + v.y), be * v.y + al * (v.x + v.z),
+                                   be * v.z + al * (v.y + v.w), be * v.w + al * (v.z + rv));
+            };
+            auto mix = [&](float4 a, float4 c, float4 d) {   // be c + al (a + d)
+                return make_float4(be * c.x + al * (a.x + d.x), be * c.y + al * (a.y + d.y),
+                                   be * c.z + al * (a.z + d.z), be * c.w + al * (a.w + d.w));
+            };
+            // chunks are whole rows (a multiple of 256 sites; nx = 128 divides V)
+            for (int rw = i0 / 128 + (int)(threadIdx.x >> 5); rw < i1 / 128; rw += kFlatThreads / 32) {
+                const int y = rw % ny, z = rw / ny;
+                const int oy0 = 128 * (y == 0 ? ny - 1 : y - 1), oy1 = 128 * y, oy2 = 128 * (y == ny - 1 ? 0 : y + 1);
+                const int pz0 = 128 * ny * (z == 0 ? nz - 1 : z - 1), pz1 = 128 * ny * z,
+                          pz2 = 128 * ny * (z == nz - 1 ? 0 : z + 1);
+                const int i = 128 * rw + 4 * lane;
+                // species by species: sigma[phi_J] goes straight into every mu_I
+                float4 m[3], tot = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+                for (int I = 0; I < 3; ++I) m[I] = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll 1
+                for (int J = 0; J < ns; ++J) {
+                    const float* f = (const float*)phi + (size_t)J * V + 4 * lane;
+                    auto plane = [&](int pz) {
+                        const float4 a = ld4(f + pz + oy0), c = ld4(f + pz + oy1), d = ld4(f + pz + oy2);
+                        if (pz == pz1) tot = make_float4(tot.x + c.x, tot.y + c.y, tot.z + c.z, tot.w + c.w);
+                        return mix(xpass(a), xpass(c), xpass(d));
+                    };
+                    const float4 z0 = plane(pz0), z1 = plane(pz1), z2 = plane(pz2);
+                    const float4 sp = mix(z0, z1, z2);
+#pragma unroll
+                    for (int I = 0; I < 3; ++I) {
+                        if (I >= ns) break;
+                        const float ch = (float)R.chi[I * 3 + J];
+                        m[I].x += ch * sp.x; m[I].y += ch * sp.y; m[I].z += ch * sp.z; m[I].w += ch * sp.w;
+                    }
+                }
+                const float kap = (float)R.kappa;
+#pragma unroll
+                for (int I = 0; I < 3; ++I) {
+                    if (I >= ns) break;
+                    const float4 u = ld4((const float*)U + (size_t)I * V + i);
+                    float4 o;
+                    o.x = -u.x + m[I].x + kap * (tot.x - 1.f);
+                    o.y = -u.y + m[I].y + kap * (tot.y - 1.f);
+                    o.z = -u.z + m[I].z + kap * (tot.z - 1.f);
+                    o.w = -u.w + m[I].w + kap * (tot.w - 1.f);
+                    *(float4*)((float*)mu + (size_t)I * V + i) = o;
+                }
+            }
+            return;
+        }
+    }
     for (int i = i0 + threadIdx.x; i < i1; i += kFlatThreads) {
         int x, y, z;
         site_xyz(i, nx, ny, x, y, z);
@@ -574,6 +632,9 @@ __global__ void __launch_bounds__(kFlatThreads) k_cd_rhs(const Rep* __restrict__
 // thread: float4 loads at the site and its y and z neighbours, the x neighbours assembled from
 // the site's own float4 and the two scalars at x0-1 and x0+4 (periodic).  Same arithmetic per
 // site as the scalar sweep.
+// SHFL: every warp holds whole x rows (nx divides 128, V a multiple of 128, chunks of whole
+// warps), so the x neighbours just outside a thread's four sites come from the adjacent lanes.
+template <bool SHFL>
 __device__ __forceinline__ void jacobi4(const Rep& R, const float* __restrict__ phi, const float* __restrict__ inv,
                                         const float* __restrict__ rhs, const float* __restrict__ dold,
                                         float* __restrict__ dnew, float c, float kap, int k, int i0, int i1) {
@@ -631,9 +692,22 @@ __device__ __forceinline__ void jacobi4(const Rep& R, const float* __restrict__ 
                 const size_t oI = (size_t)I * V;
                 const float4 ic = ld4(inv + oI + i);
                 const float4 dc = (k > 0) ? ld4(dold + oI + i) : make_float4(0.f, 0.f, 0.f, 0.f);
-                const float pl = phi[oI + ixm], pr = phi[oI + ixp];
-                const float il = inv[oI + ixm], ir = inv[oI + ixp];
-                const float dl = (k > 0) ? dold[oI + ixm] : 0.f, dr = (k > 0) ? dold[oI + ixp] : 0.f;
+                float pl, pr, il, ir, dl, dr;
+                if constexpr (SHFL) {
+                    const int lane = threadIdx.x & 31, L = R.nx >> 2;   // lanes per row
+                    const int lm = (lane % L == 0) ? lane + L - 1 : lane - 1;
+                    const int lp = (lane % L == L - 1) ? lane - L + 1 : lane + 1;
+                    pl = __shfl_sync(0xffffffffu, pc[I].w, lm);
+                    pr = __shfl_sync(0xffffffffu, pc[I].x, lp);
+                    il = __shfl_sync(0xffffffffu, ic.w, lm);
+                    ir = __shfl_sync(0xffffffffu, ic.x, lp);
+                    dl = __shfl_sync(0xffffffffu, dc.w, lm);
+                    dr = __shfl_sync(0xffffffffu, dc.x, lp);
+                } else {
+                    pl = phi[oI + ixm]; pr = phi[oI + ixp];
+                    il = inv[oI + ixm]; ir = inv[oI + ixp];
+                    dl = (k > 0) ? dold[oI + ixm] : 0.f; dr = (k > 0) ? dold[oI + ixp] : 0.f;
+                }
                 pm_[I][0] = pl; pm_[I][1] = pc[I].x; pm_[I][2] = pc[I].y; pm_[I][3] = pc[I].z;
                 pp_[I][0] = pc[I].y; pp_[I][1] = pc[I].z; pp_[I][2] = pc[I].w; pp_[I][3] = pr;
                 im_[I][0] = il; im_[I][1] = ic.x; im_[I][2] = ic.y; im_[I][3] = ic.z;
@@ -667,7 +741,7 @@ __device__ __forceinline__ void jacobi4(const Rep& R, const float* __restrict__ 
 // site is solved exactly (diagonal plus the rank-one kappa coupling).  inv = 1/max(phi, floor)
 // from k_cd_rhs.
 template <typename T>
-__global__ void __launch_bounds__(kFlatThreads) k_cd_jacobi(const Rep* __restrict__ reps, const int* __restrict__ blk2rep,
+__global__ void __launch_bounds__(kFlatThreads, sizeof(T) == 4 ? 4 : 3) k_cd_jacobi(const Rep* __restrict__ reps, const int* __restrict__ blk2rep,
                                                             int k) {
     FLAT_PROLOGUE
     const T* phi = (const T*)R.phi;
@@ -680,8 +754,13 @@ __global__ void __launch_bounds__(kFlatThreads) k_cd_jacobi(const Rep* __restric
     const T kap = (T)R.kappa;
     if constexpr (sizeof(T) == 4) {
         if (ns == 2 && (R.nx & 3) == 0) {   // FP32 melt: 4 consecutive sites of an x row per thread
-            jacobi4(R, (const float*)phi, (const float*)inv, (const float*)rhs, (const float*)dold, (float*)dnew,
-                    (float)c, (float)kap, k, i0, i1);
+            // chunks are multiples of 256 sites, so with V a multiple of 128 every warp is whole
+            if (R.nx <= 128 && 128 % R.nx == 0 && V % 128 == 0)
+                jacobi4<true>(R, (const float*)phi, (const float*)inv, (const float*)rhs, (const float*)dold,
+                              (float*)dnew, (float)c, (float)kap, k, i0, i1);
+            else
+                jacobi4<false>(R, (const float*)phi, (const float*)inv, (const float*)rhs, (const float*)dold,
+                               (float*)dnew, (float)c, (float)kap, k, i0, i1);
             return;
         }
     }

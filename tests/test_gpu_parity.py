@@ -362,6 +362,25 @@ def test_residual_stop_with_persistent_and_multi_launch_sweeps():
         ctx.set_inversion_tol(-1.0)
 
 
+ROW_CASES = [
+    melt((128, 8, 6), 6, 3, hydro=1, ncg_iters=2, cn_sweeps=4),
+    solution((128, 6, 4), 5, 2, hydro=1, ncg_iters=2, cn_sweeps=4),
+    melt((64, 10, 12), 6, 3, hydro=1, ncg_iters=2, cn_sweeps=6),
+    melt((32, 12, 8), 6, 3, hydro=0, ncg_iters=2, cn_sweeps=6),
+]
+
+
+@pytest.mark.parametrize("cfg", ROW_CASES, ids=lambda c: "x".join(map(str, c["grid"])) + f"_ns{c['ns']}")
+def test_step_fp32_row_kernels_within_tolerance(cfg):
+    """FP32 step on grids whose x rows fill whole warps (nx = 128: chemical potentials one warp per
+    row; nx dividing 128: Jacobi x neighbours by shuffles), melt and solution, two steps."""
+    phi, U, dn = random_state(cfg, 57)
+    g = run_gpu(cfg, dscf.FP32, phi, U, dn, 2)
+    o = run_oracle(cfg, phi, U, dn, 2)
+    for k in ("phi", "U", "mu", "phim"):
+        assert rel(g[k], o[k]) < 1e-5, (k, rel(g[k], o[k]))
+
+
 def test_step_fp32_within_tolerance():
     cfg = STEP_CASES[0]
     phi, U, dn = random_state(cfg, 51)
