@@ -153,6 +153,33 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
     return r;
 }
 
+// NV block-wide sums in one pass (same order per value as block_sum, so the same results).
+// sh: >= 33 NV doubles of shared memory.
+template <int NV>
+__device__ __forceinline__ void block_sum_n(double (&v)[NV], double* sh) {
+    const int nw = (blockDim.x * blockDim.y + 31) >> 5;
+    const int tid = threadIdx.x + threadIdx.y * blockDim.x;
+    const int l = tid & 31, w = tid >> 5;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        v[k] = warp_sum(v[k]);
+        if (l == 0) sh[33 * k + w] = v[k];
+    }
+    __syncthreads();
+    if (w == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            double x = (l < nw) ? sh[33 * k + l] : 0.0;
+            x = warp_sum(x);
+            if (l == 0) sh[33 * k + 32] = x;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < NV; ++k) v[k] = sh[33 * k + 32];
+    __syncthreads();
+}
+
 __device__ __forceinline__ double block_max(double v, double* sh) {
     const int nw = (blockDim.x * blockDim.y + 31) >> 5;
     const int tid = threadIdx.x + threadIdx.y * blockDim.x;
@@ -178,6 +205,22 @@ __device__ __forceinline__ double reduce_parts(const double* __restrict__ p, int
     double s = 0.0;
     for (int i = tid; i < n; i += nt) s += p[i];
     return block_sum(s, sh);
+}
+// Totals of NV partial arrays of n entries each, in one pass (same results as reduce_parts).
+template <int NV>
+struct Parts {
+    const double* p[NV];
+};
+template <int NV>
+__device__ __forceinline__ void reduce_parts_n(const Parts<NV> p, int n, double (&out)[NV], double* sh) {
+    const int tid = threadIdx.x + threadIdx.y * blockDim.x;
+    const int nt = blockDim.x * blockDim.y;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) out[k] = 0.0;
+    for (int i = tid; i < n; i += nt)
+#pragma unroll
+        for (int k = 0; k < NV; ++k) out[k] += p.p[k][i];
+    block_sum_n<NV>(out, sh);
 }
 __device__ __forceinline__ double reduce_parts_max(const double* __restrict__ p, int n, double* sh) {
     const int tid = threadIdx.x + threadIdx.y * blockDim.x;

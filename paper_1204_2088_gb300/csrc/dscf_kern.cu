@@ -163,12 +163,14 @@ __global__ void __launch_bounds__(kFlatThreads) k_grad(const Rep* __restrict__ r
 template <typename T>
 __global__ void __launch_bounds__(kFlatThreads) k_dir(const Rep* __restrict__ reps, const int* __restrict__ blk2rep,
                                                       int mode, int k, int* status) {
-    __shared__ double sh[33];
+    __shared__ double sh[3 * 33];
     FLAT_PROLOGUE
     double beta = 0.0;
     if (mode == 1) {
-        const double ggn = reduce_parts(slot(R, pslot_gg(k + 1)), R.nblk, sh);
-        const double ggo = reduce_parts(slot(R, pslot_gg(k)), R.nblk, sh);
+        const Parts<2> ps = {slot(R, pslot_gg(k + 1)), slot(R, pslot_gg(k))};
+        double t[2];
+        reduce_parts_n<2>(ps, R.nblk, t, sh);
+        const double ggn = t[0], ggo = t[1];
         beta = (ggo > 0.0) ? ggn / ggo : 0.0;
         if (lb == 0) {
             const double gm = reduce_parts_max(slot(R, P_GMAX), R.nblk, sh);
@@ -219,18 +221,22 @@ __global__ void __launch_bounds__(kFlatThreads) k_dir(const Rep* __restrict__ re
                 gmax = fmax(gmax, fabs(g));
             }
     }
-    const double th0 = block_sum((double)h0, sh);
-    const double tcd = block_sum((double)cd, sh);
-    if (threadIdx.x == 0) {
-        slot(R, P_H0)[lb] = th0;
-        slot(R, P_CD)[lb] = tcd;
-    }
     if (mode == 0) {
-        const double tg = block_sum((double)gg, sh);
+        double t[3] = {(double)h0, (double)cd, (double)gg};
+        block_sum_n<3>(t, sh);
         const double tm = block_max((double)gmax, sh);
         if (threadIdx.x == 0) {
-            slot(R, P_GG0)[lb] = tg;
+            slot(R, P_H0)[lb] = t[0];
+            slot(R, P_CD)[lb] = t[1];
+            slot(R, P_GG0)[lb] = t[2];
             slot(R, P_GMAX)[lb] = tm;
+        }
+    } else {
+        double t[2] = {(double)h0, (double)cd};
+        block_sum_n<2>(t, sh);
+        if (threadIdx.x == 0) {
+            slot(R, P_H0)[lb] = t[0];
+            slot(R, P_CD)[lb] = t[1];
         }
     }
 }
@@ -583,7 +589,7 @@ __device__ __forceinline__ Nb neighbours(int i, int nx, int ny, int nz) {
 // 1/max(phi_I, floor) for the Jacobi sweeps in the Boltzmann-factor buffer, which is free from
 // the end of the inversion to the start of the next one.
 template <typename T>
-__global__ void __launch_bounds__(kFlatThreads) k_cd_rhs(const Rep* __restrict__ reps, const int* __restrict__ blk2rep) {
+__global__ void __launch_bounds__(kFlatThreads, sizeof(T) == 4 ? 4 : 1) k_cd_rhs(const Rep* __restrict__ reps, const int* __restrict__ blk2rep) {
     FLAT_PROLOGUE
     const T* phi = (const T*)R.phi;
     const T* mu = (const T*)R.mu;
@@ -593,6 +599,87 @@ __global__ void __launch_bounds__(kFlatThreads) k_cd_rhs(const Rep* __restrict__
     const bool hyd = R.hydro != 0;
     const T dtM = (T)(R.dt * R.M);
     const T fl = (T)R.phi_floor;
+    if constexpr (sizeof(T) == 4) {
+        const int nx = R.nx, ny = R.ny, nz = R.nz;
+        if ((nx & 3) == 0 && nx <= 128 && 128 % nx == 0 && V % 128 == 0) {
+            // x rows fill whole warps (chunks are multiples of 256 sites): four consecutive sites
+            // per lane, y and z neighbours as float4, x neighbours from the adjacent lanes; the
+            // same arithmetic per site as below
+            const int lane = threadIdx.x & 31, L = nx >> 2;
+            const int lm = (lane % L == 0) ? lane + L - 1 : lane - 1;
+            const int lp = (lane % L == L - 1) ? lane - L + 1 : lane + 1;
+            const int sy = nx, sz = nx * ny;
+            // the field at the x neighbours (-1: q - 1, +1: q + 1) of the four sites
+            auto xs = [&](const float4 v, float (&m_)[4], float (&p_)[4]) {
+                const float l = __shfl_sync(0xffffffffu, v.w, lm), r = __shfl_sync(0xffffffffu, v.x, lp);
+                m_[0] = l; m_[1] = v.x; m_[2] = v.y; m_[3] = v.z;
+                p_[0] = v.y; p_[1] = v.z; p_[2] = v.w; p_[3] = r;
+            };
+            auto arr = [](const float4 v, float (&a)[4]) { a[0] = v.x; a[1] = v.y; a[2] = v.z; a[3] = v.w; };
+            for (int i = i0 + 4 * (int)threadIdx.x; i < i1; i += 4 * kFlatThreads) {
+                int x, y, z;
+                site_xyz(i, nx, ny, x, y, z);
+                const int nyp = i + (y == ny - 1 ? sy - sz : sy), nym = i + (y == 0 ? sz - sy : -sy);
+                const int nzp = i + (z == nz - 1 ? sz - nz * sz : sz), nzm = i + (z == 0 ? nz * sz - sz : -sz);
+                const int np_[3] = {0, nyp, nzp}, nm_[3] = {0, nym, nzm};
+                for (int I = 0; I < R.ns; ++I) {
+                    const float* ph = (const float*)phi + (size_t)I * V;
+                    const float* m = (const float*)mu + (size_t)I * V;
+                    const float4 pc4 = ld4(ph + i), mc4 = ld4(m + i);
+                    float pc[4], mc[4], conv[4] = {0.f, 0.f, 0.f, 0.f}, lap[4] = {0.f, 0.f, 0.f, 0.f};
+                    arr(pc4, pc);
+                    arr(mc4, mc);
+                    // axis by axis: Courant numbers at the site and its two neighbours, phi and mu
+                    // at the neighbours
+#pragma unroll
+                    for (int d = 0; d < 3; ++d) {
+                        float Ci[4], Cp[4], Cm[4], pp[4], pm[4], mp[4], mm[4];
+                        if (hyd) {
+                            const float* C = (const float*)u + (size_t)d * V;
+                            const float4 c4 = ld4(C + i);
+                            arr(c4, Ci);
+                            if (d == 0) {
+                                xs(c4, Cm, Cp);
+                            } else {
+                                arr(ld4(C + np_[d]), Cp);
+                                arr(ld4(C + nm_[d]), Cm);
+                            }
+                        } else {
+#pragma unroll
+                            for (int q = 0; q < 4; ++q) Ci[q] = Cp[q] = Cm[q] = 0.f;
+                        }
+                        if (d == 0) {
+                            xs(pc4, pm, pp);
+                            xs(mc4, mm, mp);
+                        } else {
+                            arr(ld4(ph + np_[d]), pp);
+                            arr(ld4(ph + nm_[d]), pm);
+                            arr(ld4(m + np_[d]), mp);
+                            arr(ld4(m + nm_[d]), mm);
+                        }
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            const float hp = 0.5f * (pc[q] + pp[q]) - 0.5f * (Cp[q] * pp[q] - Ci[q] * pc[q]);
+                            const float Fp = 0.5f * (Ci[q] + Cp[q]) * hp;
+                            const float hm = 0.5f * (pm[q] + pc[q]) - 0.5f * (Ci[q] * pc[q] - Cm[q] * pm[q]);
+                            const float Fm = 0.5f * (Cm[q] + Ci[q]) * hm;
+                            conv[q] += Fp - Fm;
+                            lap[q] += 0.5f * (pc[q] + pp[q]) * (mp[q] - mc[q]) + 0.5f * (pc[q] + pm[q]) * (mm[q] - mc[q]);
+                        }
+                    }
+                    float4 ro, io;
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        (&ro.x)[q] = -conv[q] + (float)dtM * lap[q];
+                        (&io.x)[q] = 1.f / (pc[q] < (float)fl ? (float)fl : pc[q]);
+                    }
+                    *(float4*)((float*)rhs + (size_t)I * V + i) = ro;
+                    *(float4*)((float*)inv + (size_t)I * V + i) = io;
+                }
+            }
+            return;
+        }
+    }
     for (int i = i0 + threadIdx.x; i < i1; i += kFlatThreads) {
         const Nb b = neighbours(i, R.nx, R.ny, R.nz);
         T Ci[3], Cp[3], Cm[3];
@@ -820,11 +907,21 @@ __global__ void __launch_bounds__(kFlatThreads) k_cd_finish(const Rep* __restric
     const T* del = (const T*)(((sweeps - 1) & 1) ? R.del1 : R.del0);
     for (int I = 0; I < R.ns; ++I) {
         T acc = T(0);
-        _Pragma("unroll 4") for (int i = i0 + threadIdx.x; i < i1; i += kFlatThreads) {
-            const size_t o = (size_t)I * V + i;
-            const T v = phi[o] + del[o];
-            phi[o] = v;
-            acc += v;
+        if (flat_vec<T>(V)) {
+            _Pragma("unroll 2") for (int i = i0 + 4 * (int)threadIdx.x; i < i1; i += 4 * kFlatThreads) {
+                const size_t o = (size_t)I * V + i;
+                const float4 p = ld4((const float*)phi + o), d = ld4((const float*)del + o);
+                const float4 v = make_float4(p.x + d.x, p.y + d.y, p.z + d.z, p.w + d.w);
+                *(float4*)((float*)phi + o) = v;
+                acc += (T)((v.x + v.y) + (v.z + v.w));
+            }
+        } else {
+            _Pragma("unroll 4") for (int i = i0 + threadIdx.x; i < i1; i += kFlatThreads) {
+                const size_t o = (size_t)I * V + i;
+                const T v = phi[o] + del[o];
+                phi[o] = v;
+                acc += v;
+            }
         }
         const double t = block_sum((double)acc, sh);
         if (threadIdx.x == 0) slot(R, P_MASS0 + I)[lb] = t;
@@ -847,7 +944,16 @@ __global__ void __launch_bounds__(kFlatThreads) k_mass_fix(const Rep* __restrict
             if (!isfinite(tot)) atomicOr(status, (int)ST_NONFINITE);
         }
         const T ts = (T)shift;
-        _Pragma("unroll 4") for (int i = i0 + threadIdx.x; i < i1; i += kFlatThreads) phi[(long long)I * V + i] += ts;
+        if (flat_vec<T>(V)) {
+            const float fs = (float)ts;
+            _Pragma("unroll 2") for (int i = i0 + 4 * (int)threadIdx.x; i < i1; i += 4 * kFlatThreads) {
+                float4* p = (float4*)((float*)phi + (size_t)I * V + i);
+                const float4 v = *p;
+                *p = make_float4(v.x + fs, v.y + fs, v.z + fs, v.w + fs);
+            }
+        } else {
+            _Pragma("unroll 4") for (int i = i0 + threadIdx.x; i < i1; i += kFlatThreads) phi[(long long)I * V + i] += ts;
+        }
     }
 }
 

@@ -545,7 +545,7 @@ __global__ void __launch_bounds__(32 * (kPropRows + 2 * K)) k_prop_fused(const R
 template <typename T>
 __global__ void __launch_bounds__(kFlatThreads) k_exp(const Rep* __restrict__ reps, const int* __restrict__ blk2rep,
                                                       int mode, int k, const T* __restrict__ Uext, int write_u) {
-    __shared__ double sh[33];
+    __shared__ double sh[3 * 33];
     const Rep& R = reps[blk2rep[blockIdx.x]];
     const int lb = blockIdx.x - R.blk0;
     const long long V = R.V;
@@ -553,12 +553,22 @@ __global__ void __launch_bounds__(kFlatThreads) k_exp(const Rep* __restrict__ re
     const long long i1 = min(i0 + (long long)R.chunk, V);
     double a = 0.0;
     if (mode == 1 || mode == 2) {
-        const double h0 = reduce_parts(slot(R, P_H0), R.nblk, sh);
-        const double cd = reduce_parts(slot(R, P_CD), R.nblk, sh);
+        double t[3];
+        if (mode == 2) {
+            const Parts<3> ps = {slot(R, P_H0), slot(R, P_CD), slot(R, P_H1)};
+            reduce_parts_n<3>(ps, R.nblk, t, sh);
+        } else {
+            const Parts<2> ps = {slot(R, P_H0), slot(R, P_CD)};
+            double t2[2];
+            reduce_parts_n<2>(ps, R.nblk, t2, sh);
+            t[0] = t2[0];
+            t[1] = t2[1];
+        }
+        const double h0 = t[0], cd = t[1];
         const double a1 = (cd > 0.0 && isfinite(h0 / cd)) ? -h0 / cd : 0.0;
         a = a1;
         if (mode == 2) {
-            const double h1 = reduce_parts(slot(R, P_H1), R.nblk, sh);
+            const double h1 = t[2];
             const double den = h1 - h0;
             a = (den > 0.0) ? a1 * (-h0) / den : a1;
             // With the learned predictor the secant is capped at the local-curvature step a1: the
@@ -570,7 +580,7 @@ __global__ void __launch_bounds__(kFlatThreads) k_exp(const Rep* __restrict__ re
                 R.scal[S_ITER0 + 4 * k + 0] = a1;
                 R.scal[S_ITER0 + 4 * k + 1] = a;
             }
-        } else if (k == 0) {
+        } else if (k == 0 && lb == 0) {
             // start-of-inversion residual (partials written by the direction kernel)
             const double gg = reduce_parts(slot(R, P_GG0), R.nblk, sh);
             const double gm = reduce_parts_max(slot(R, P_GMAX), R.nblk, sh);
