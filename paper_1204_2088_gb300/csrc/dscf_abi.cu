@@ -69,6 +69,24 @@ bool validate(const dscf_params* p, int n, std::string& why) {
 // replicas still active at contour step s are a prefix) and per-step grid sizes, for the
 // current z-chunk of every replica.
 void assign_tiles(Layout& L, const dscf_params* p, int n) {
+    // Flat kernels: about kMaxFlatBlocks blocks over the whole batch (one wave of four per SM).  A
+    // replica whose own tiling would give it smaller chunks takes the batch's common chunk, so a
+    // batch of many replicas does not launch tens of thousands of short blocks.  (A single
+    // replica, or a batch of fewer than kMaxFlatBlocks x kFlatThreads sites, keeps its own tiling
+    // and so its solo reduction order.)
+    {
+        long long Vtot = 0;
+        for (int r = 0; r < n; ++r) Vtot += L.reps[r].V;
+        long long common = (Vtot + kMaxFlatBlocks - 1) / kMaxFlatBlocks;
+        common = (common + kFlatThreads - 1) / kFlatThreads * kFlatThreads;
+        for (int r = 0; r < n; ++r) {
+            Rep& R = L.reps[r];
+            if (common > R.chunk) {
+                R.chunk = (int)common;
+                R.nblk = (int)((R.V + common - 1) / common);
+            }
+        }
+    }
     std::vector<int> order(n);
     for (int r = 0; r < n; ++r) order[r] = r;
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return p[a].N > p[b].N; });

@@ -411,6 +411,29 @@ def test_batched_replicas_bit_identical_to_solo():
         off += n
 
 
+def test_large_batch_matches_solo_to_rounding():
+    """A batch large enough to take a common flat chunk (here 2 x 48^3 + 32^3 sites) regroups
+    the FP64 block partials, so it matches the solo runs to rounding rather than bit for bit."""
+    cfgs = [melt((48, 48, 48), 6, 3, hydro=1, ncg_iters=2, cn_sweeps=4),
+            melt((48, 48, 48), 8, 3, hydro=1, ncg_iters=2, cn_sweeps=4, tau_s=0.8),
+            solution((32, 32, 32), 5, 2, hydro=1, ncg_iters=2, cn_sweeps=4)]
+    states = [random_state(c, 70 + 3 * i) for i, c in enumerate(cfgs)]
+    ctx = dscf.Context(cfgs, dscf.FP64)
+    ctx.set(dscf.PHI, torch.from_numpy(np.concatenate([s[0].ravel() for s in states])).cuda())
+    ctx.set(dscf.U, torch.from_numpy(np.concatenate([s[1].ravel() for s in states])).cuda())
+    ctx.set(dscf.POP, torch.from_numpy(np.concatenate([s[2].ravel() for s in states])).cuda())
+    ctx.step(2)
+    ctx.status()
+    phi_b, U_b = t2n(ctx.get(dscf.PHI)), t2n(ctx.get(dscf.U))
+    off = 0
+    for c, (phi, U, dn) in zip(cfgs, states):
+        solo = run_gpu(c, dscf.FP64, phi, U, dn, 2)
+        n = phi.size
+        assert rel(phi_b[off:off + n], solo["phi"].ravel()) < 1e-12
+        assert rel(U_b[off:off + n], solo["U"].ravel()) < 1e-10
+        off += n
+
+
 @pytest.mark.parametrize("cfg", [STEP_CASES[0], STEP_CASES[3]], ids=["melt", "solution"])
 def test_observables_match_oracle(cfg):
     """Free energy (Eq. 1), order parameter (Fig. 1) and segregation (Fig. 3) of the GPU's own
