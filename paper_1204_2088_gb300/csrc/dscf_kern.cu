@@ -86,14 +86,20 @@ __global__ void __launch_bounds__(kFlatThreads) k_trial(const Rep* __restrict__ 
     const T* d = (const T*)R.d;
     T h1 = T(0);
     if (flat_vec<T>(V)) {
-        for (int I = 0; I < R.ns; ++I) {
-            float sc;
-            const float* src = model_src(R, n, I, sc);
-            _Pragma("unroll 2") for (int i = i0 + 4 * (int)threadIdx.x; i < i1; i += 4 * kFlatThreads) {
+        const int ns = R.ns;
+        float sc[3];
+        const float* src[3];
+#pragma unroll
+        for (int I = 0; I < 3; ++I) src[I] = I < ns ? model_src(R, n, I, sc[I]) : nullptr;
+        // sites outer, species inner: every load of an iteration is issued together
+        _Pragma("unroll 4") for (int i = i0 + 4 * (int)threadIdx.x; i < i1; i += 4 * kFlatThreads) {
+#pragma unroll
+            for (int I = 0; I < 3; ++I) {
+                if (I >= ns) break;
                 const size_t o = (size_t)I * V + i;
-                const float4 p = ld4((const float*)phi + o), dd = ld4((const float*)d + o), q = ld4(src + i);
-                h1 += (T)((p.x - sc * q.x) * dd.x + (p.y - sc * q.y) * dd.y + (p.z - sc * q.z) * dd.z +
-                          (p.w - sc * q.w) * dd.w);
+                const float4 p = ld4((const float*)phi + o), dd = ld4((const float*)d + o), q = ld4(src[I] + i);
+                h1 += (T)((p.x - sc[I] * q.x) * dd.x + (p.y - sc[I] * q.y) * dd.y + (p.z - sc[I] * q.z) * dd.z +
+                          (p.w - sc[I] * q.w) * dd.w);
             }
         }
     } else {
@@ -119,14 +125,22 @@ __global__ void __launch_bounds__(kFlatThreads) k_grad(const Rep* __restrict__ r
         R.scal[S_Q] = n.coef > 0.0 ? R.phi_p / ((double)R.N * n.coef) : 0.0;
         R.scal[S_QS] = n.qs;
     }
-    const T* phi = (const T*)R.phi;
-    T* pm = (T*)R.phim;
+    const T* __restrict__ phi = (const T*)R.phi;
+    T* __restrict__ pm = (T*)R.phim;   // written only here: loads may move past its stores
     T gg = T(0), gmax = T(0);
     if (flat_vec<T>(V)) {
-        for (int I = 0; I < R.ns; ++I) {
-            float sc;
-            const float* src = model_src(R, n, I, sc);
-            _Pragma("unroll 2") for (int i = i0 + 4 * (int)threadIdx.x; i < i1; i += 4 * kFlatThreads) {
+        const int ns = R.ns;
+        float scs[3];
+        const float* srcs[3];
+#pragma unroll
+        for (int I = 0; I < 3; ++I) srcs[I] = I < ns ? model_src(R, n, I, scs[I]) : nullptr;
+        // sites outer, species inner: every load of an iteration is issued together
+        _Pragma("unroll 4") for (int i = i0 + 4 * (int)threadIdx.x; i < i1; i += 4 * kFlatThreads) {
+#pragma unroll
+            for (int I = 0; I < 3; ++I) {
+                if (I >= ns) break;
+                const float sc = scs[I];
+                const float* src = srcs[I];
                 const size_t o = (size_t)I * V + i;
                 const float4 q = ld4(src + i), p = ld4((const float*)phi + o);
                 const float4 m = make_float4(sc * q.x, sc * q.y, sc * q.z, sc * q.w);
@@ -181,14 +195,14 @@ __global__ void __launch_bounds__(kFlatThreads) k_dir(const Rep* __restrict__ re
             }
         }
     }
-    const T* phi = (const T*)R.phi;
-    const T* pm = (const T*)R.phim;
-    T* d = (T*)R.d;
+    const T* __restrict__ phi = (const T*)R.phi;
+    const T* __restrict__ pm = (const T*)R.phim;
+    T* __restrict__ d = (T*)R.d;
     const T tb = (T)beta;
     T h0 = T(0), cd = T(0), gg = T(0), gmax = T(0);
     if (flat_vec<T>(V)) {
         const float fb = (float)tb;
-        _Pragma("unroll 2") for (int i = i0 + 4 * (int)threadIdx.x; i < i1; i += 4 * kFlatThreads) {
+        _Pragma("unroll 4") for (int i = i0 + 4 * (int)threadIdx.x; i < i1; i += 4 * kFlatThreads) {
             for (int I = 0; I < R.ns; ++I) {
                 const size_t o = (size_t)I * V + i;
                 const float4 p = ld4((const float*)phi + o), m = ld4((const float*)pm + o);
@@ -903,8 +917,8 @@ __global__ void __launch_bounds__(kFlatThreads) k_cd_finish(const Rep* __restric
                                                             int sweeps) {
     __shared__ double sh[33];
     FLAT_PROLOGUE
-    T* phi = (T*)R.phi;
-    const T* del = (const T*)(((sweeps - 1) & 1) ? R.del1 : R.del0);
+    T* __restrict__ phi = (T*)R.phi;
+    const T* __restrict__ del = (const T*)(((sweeps - 1) & 1) ? R.del1 : R.del0);
     for (int I = 0; I < R.ns; ++I) {
         T acc = T(0);
         if (flat_vec<T>(V)) {

@@ -23,6 +23,8 @@
 // backward sweep.
 #include "dscf_internal.cuh"
 
+#include <type_traits>
+
 namespace dscf {
 
 constexpr int NWARP = kPropRows + 2;   // warps per CTA
@@ -591,39 +593,63 @@ __global__ void __launch_bounds__(kFlatThreads) k_exp(const Rep* __restrict__ re
         }
     }
     const int ns = R.ns;
-    T* U = (T*)R.U;
-    const T* d = (const T*)R.d;
-    T* E = (T*)R.E;
+    // distinct fields: no store below can change a value loaded from another of them
+    T* __restrict__ U = (T*)R.U;
+    const T* __restrict__ d = (const T*)R.d;
+    T* __restrict__ E = (T*)R.E;
     const T ta = (T)a;
     double es = 0.0;
     bool vec = false;
     if constexpr (sizeof(T) == 4) vec = (V & 3) == 0 && (mode != 3 || (R.ext_off & 3) == 0);
     if (vec) {   // FP32, 4 consecutive sites per thread and iteration (16-byte accesses)
         const float fa = (float)ta;
-        for (int I = 0; I < ns; ++I) {
-            float es4 = 0.f;
-            for (long long i = i0 + 4 * threadIdx.x; i < i1; i += 4 * kFlatThreads) {
-                const long long o = (long long)I * V + i;
-                float4 u;
-                if (mode == 3) {
-                    u = *(const float4*)((const float*)Uext + R.ext_off + o);
-                } else {
-                    u = *(const float4*)((const float*)U + o);
-                    if (mode != 0) {
-                        const float4 dd = *(const float4*)((const float*)d + o);
-                        u.x += fa * dd.x;
-                        u.y += fa * dd.y;
-                        u.z += fa * dd.z;
-                        u.w += fa * dd.w;
-                        if (mode == 2) *(float4*)((float*)U + o) = u;
+        float es4 = 0.f;
+        const int j0 = (int)i0, j1 = (int)i1;
+        constexpr int S = 4 * kFlatThreads;   // sites per block-wide iteration
+        // UB iterations of NS species at a time: every load of the batch is issued before the
+        // first use (a thread has only a few iterations, so a plain loop would wait for each)
+        auto run = [&](auto nsc, auto ubc) {
+            constexpr int NS = decltype(nsc)::value, UB = decltype(ubc)::value;
+            for (int ib = j0 + 4 * (int)threadIdx.x; ib < j1; ib += UB * S) {
+                float4 uu[UB][NS], dv[UB][NS];
+#pragma unroll
+                for (int it = 0; it < UB; ++it)
+#pragma unroll
+                    for (int I = 0; I < NS; ++I) {
+                        const int i = ib + it * S;
+                        if (i < j1) {
+                            const size_t o = (size_t)I * V + i;
+                            uu[it][I] = (mode == 3) ? *(const float4*)((const float*)Uext + R.ext_off + o)
+                                                    : *(const float4*)((const float*)U + o);
+                            if (mode == 1 || mode == 2) dv[it][I] = *(const float4*)((const float*)d + o);
+                        }
                     }
-                }
-                const float4 e = write_u ? u : make_float4(bexp(u.x), bexp(u.y), bexp(u.z), bexp(u.w));
-                *(float4*)((float*)E + o) = e;
-                if (I == 2) es4 += (e.x + e.y) + (e.z + e.w);
+#pragma unroll
+                for (int it = 0; it < UB; ++it)
+#pragma unroll
+                    for (int I = 0; I < NS; ++I) {
+                        const int i = ib + it * S;
+                        if (i < j1) {
+                            const size_t o = (size_t)I * V + i;
+                            float4 u = uu[it][I];
+                            if (mode == 1 || mode == 2) {
+                                const float4 dd = dv[it][I];
+                                u.x += fa * dd.x;
+                                u.y += fa * dd.y;
+                                u.z += fa * dd.z;
+                                u.w += fa * dd.w;
+                                if (mode == 2) *(float4*)((float*)U + o) = u;
+                            }
+                            const float4 e = write_u ? u : make_float4(bexp(u.x), bexp(u.y), bexp(u.z), bexp(u.w));
+                            *(float4*)((float*)E + o) = e;
+                            if (I == 2) es4 += (e.x + e.y) + (e.z + e.w);
+                        }
+                    }
             }
-            if (I == 2) es += (double)es4;
-        }
+        };
+        if (ns == 2) run(std::integral_constant<int, 2>{}, std::integral_constant<int, 2>{});
+        else run(std::integral_constant<int, 3>{}, std::integral_constant<int, 1>{});
+        es += (double)es4;
     }
     for (int I = 0; I < ns && !vec; ++I) {
         for (long long i = i0 + threadIdx.x; i < i1; i += kFlatThreads) {
