@@ -193,9 +193,9 @@ int64_t dscf_launches_per_step(const dscf_ctx* ctx);
  * > 1 needs FP32 and nx in {32, 64, 128} for every replica, and kfuse <= N), or kfuse = 0 for
  * persistent sweeps (one launch per sweep; one FP32 replica with nx = 128 and ny, nz multiples
  * of 8; bricks of 128 x 8 x 16 sites, one CTA of 16 warps per SM, or of 128 x 8 x 8 sites, two
- * CTAs of 8 warps per SM, all co-resident).  With kfuse = 0, zc = 16 or 8 selects the brick depth
- * (8 planes: two CTAs of 8 warps per SM where the grid allows it, else one of 16; DSCF_ERR_ARG if
- * the grid allows neither), any other zc keeps the current depth.  Synchronises the stream; the
+ * CTAs of 8 warps per SM, all co-resident; one warp per plane).  With kfuse = 0, zc = 16 or 8
+ * selects the brick depth (DSCF_ERR_ARG if the grid does not allow it), any other zc keeps the
+ * current depth.  Synchronises the stream; the
  * next dscf_step re-captures its graph.  Results do not depend on either value beyond rounding. */
 int dscf_set_tuning(dscf_ctx* ctx, int32_t zc, int32_t kfuse);
 

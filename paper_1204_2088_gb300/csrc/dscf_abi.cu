@@ -556,16 +556,15 @@ void set_zc(dscf_ctx* c, int zc) {
     assign_tiles(c->L, c->params.data(), c->nrep);
 }
 
-// Persistent-sweep candidates: bricks of 16 planes (16 warps, one CTA per SM) or, where the depth
-// does not divide, of 8 planes; and bricks of 8 planes with 8 warps, two CTAs per SM.  The first
-// becomes the context's persistent configuration.
+// Persistent-sweep candidates (one warp per plane of the brick): bricks of 16 planes (one CTA per
+// SM) and bricks of 8 planes (two CTAs per SM).  The first becomes the context's persistent
+// configuration.
 int pers_select(dscf_ctx* c, std::vector<std::pair<int, int>>& pcand) {
     c->pers_bz = 0;
     pcand.clear();
     if (c->nrep == 1 && c->prec == DSCF_FP32) {
         const int nsm = std::min(c->nsm, kMaxBricks / 2);
         if (pers_supported(c->L.reps[0], 16, 16, nsm)) pcand.push_back({16, 16});
-        else if (pers_supported(c->L.reps[0], 8, 16, nsm)) pcand.push_back({8, 16});
         if (pers_supported(c->L.reps[0], 8, 8, nsm)) pcand.push_back({8, 8});
     }
     for (auto& pc : pcand)
@@ -1173,7 +1172,6 @@ int dscf_set_tuning(dscf_ctx* c, int32_t zc, int32_t kfuse) {
         const int nsm = std::min(c->nsm, kMaxBricks / 2);
         if (zc == 16 && pers_supported(c->L.reps[0], 16, 16, nsm)) { pbz = 16; pnw = 16; }
         else if (zc == 8 && pers_supported(c->L.reps[0], 8, 8, nsm)) { pbz = 8; pnw = 8; }
-        else if (zc == 8 && pers_supported(c->L.reps[0], 8, 16, nsm)) { pbz = 8; pnw = 16; }
         else return fail(c, DSCF_ERR_ARG, "no persistent sweep with bricks of %d planes for this grid", zc);
     }
     for (const Rep& R : c->L.reps)

@@ -1,19 +1,20 @@
 // Persistent contour sweeps (Eq. 16-17) for one replica in the whole-row layout (FP32).
 //
 // One launch runs a whole forward (or backward) sweep of N contour steps.  The lattice is cut
-// into bricks of nx x 8 x BZ sites, one brick per CTA and at most one CTA per SM (the launch is
-// cooperative, so all CTAs are resident together).  A CTA keeps its brick's x-filtered
-// propagator in shared memory from one contour step to the next; per step it only reads the halo
-// rows and planes of its eight y/z neighbours from L2, after checking with an acquire load that
-// they have published that step.  Per step:
-//   halo rows of the previous step -> x pass -> shared XS (the brick's own rows are already there);
-//   barrier; each warp y-filters its row over its planes (plus one each side) into registers;
-//   barrier; z pass in registers -> sig;
+// into bricks of nx x 8 x BZ sites, one brick per CTA (one CTA per SM for BZ = 16, two for
+// BZ = 8; the launch is cooperative, so all CTAs are resident together), one warp per plane of
+// the brick.  A warp keeps its plane's x-filtered rows in registers from one contour step to the
+// next; per step the CTA only reads the halo rows and planes of its eight y/z neighbours from L2,
+// after checking with an acquire load that they have published that step.  Per step:
+//   halo rows of the previous step -> x pass -> shared XH (y-halo rows) and ZH (z-halo planes);
+//   barrier; each warp y-filters its plane in registers (two halo rows from XH) into shared YS,
+//   and one row of a z-halo plane;
+//   barrier; z pass (the neighbouring planes from YS) -> sig;
 //   forward:  G_s = exp(-U_{I_s}) sig; brick-boundary values stored to the contour stack;
 //   backward: q_{I_s} += G_s sig in registers (G_s prefetched a step ahead with cp.async),
 //             G+_s = exp(-U_{I_s}) sig, boundary values stored to a ping-pong exchange buffer;
-//   barrier, fence, release store of the brick's step counter; then the forward interior stores
-//   and the x pass of the new values into XS.
+//   barrier, release store of the brick's step counter; then the forward interior stores and the
+//   x pass of the new values, in registers.
 // q is accumulated in registers over a whole block of beads and written once; nothing is
 // read-modify-written per step.  Every wait is bounded: on timeout the CTA sets a status bit and a
 // global abort flag that makes every other CTA stop waiting, so the launch always finishes.
@@ -79,32 +80,37 @@ __device__ __forceinline__ void wait_nb(const PersCtl& c, const int* nb, int tar
 template <int BZ, int NW>
 struct PersGeom {
     static constexpr int NH = 2 * (BZ + 2) + 2 * PBY;   // halo rows per step
-    static constexpr int OWN = PBY * BZ / NW;            // consecutive planes per warp (one row)
 };
 
 }  // namespace
 
 size_t pers_smem_bytes(int vec, int bz) {
     const size_t W = 32 * (size_t)vec;
-    // XS (x-filtered level with halo) + halo staging + backward G_s of the brick
-    return ((size_t)(bz + 2) * (PBY + 2) * W + (size_t)(2 * (bz + 2) + 2 * PBY) * W + (size_t)bz * PBY * W) *
-           sizeof(float);
+    // YS (y-filtered level, planes -1..bz) + XH (x-filtered y-halo rows of the own planes) + ZH
+    // (x-filtered z-halo planes, rows -1..8) + halo staging + backward G_s of the brick
+    const size_t rows = (size_t)(bz + 2) * PBY + 2 * (size_t)bz + 2 * (PBY + 2) + (2 * (bz + 2) + 2 * PBY) +
+                        (size_t)bz * PBY;
+    return rows * W * sizeof(float);
 }
 
-// Warp w owns row w % 8 and planes [OWN (w / 8), OWN (w / 8 + 1)) of the brick; it y-filters its
-// row over those planes plus one on each side straight into registers, so the z pass needs no
-// second shared buffer.  Brick-boundary values are stored and published first; the rest of the
-// forward G_s follows without a fence (the backward G+ interior is never stored: it stays in XS).
+// Warp w owns plane w of the brick, all PBY rows, four sites of each row per lane; the x-filtered
+// rows of the previous level stay in its registers, so the y pass runs in registers (only the two
+// y-halo rows of the plane come from shared memory) and only the y-filtered rows go through
+// shared memory, for the z pass of the neighbouring planes.  The z-halo planes are y-filtered one
+// row per warp.  Brick-boundary values are stored and published first; the rest of the forward
+// G_s follows without a fence (the backward G+ interior is never stored: it stays in registers).
 template <int BZ, bool BWD, int NW>
 __global__ void __launch_bounds__(32 * NW, 16 / NW) k_prop_pers(const Rep* __restrict__ reps, PersCtl ctl) {
+    static_assert(NW == BZ, "one warp per plane");
     constexpr int PWARPS = NW, PTHREADS = 32 * NW;
     constexpr int VEC = 4, W = 128;
     using G = PersGeom<BZ, NW>;
-    constexpr int OWN = G::OWN;
     using VT = float4;
     extern __shared__ __align__(16) unsigned char smem[];
-    float* XS = (float*)smem;                                  // [BZ+2][PBY+2][W]
-    float* HS = XS + (BZ + 2) * (PBY + 2) * W;                 // [NH][W]
+    float* YS = (float*)smem;                                  // [BZ+2][PBY][W]
+    float* XH = YS + (BZ + 2) * PBY * W;                       // [2][BZ][W]   rows -1 and PBY
+    float* ZH = XH + 2 * BZ * W;                               // [2][PBY+2][W] planes -1 and BZ
+    float* HS = ZH + 2 * (PBY + 2) * W;                        // [NH][W]
     float* GS = HS + G::NH * W;                                // [BZ][PBY][W] backward G_s
     __shared__ double sh[33];
     __shared__ int nbs[8];
@@ -117,26 +123,32 @@ __global__ void __launch_bounds__(32 * NW, 16 / NW) k_prop_pers(const Rep* __res
     const int by = b % nby, bz = b / nby;
     const int y0 = by * PBY, z0 = bz * BZ;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int row = w % PBY, p0 = OWN * (w / PBY);
     const float al = (float)R.alpha, be = (float)(1.0 - 2.0 * R.alpha);
     if (threadIdx.x < 8) {
         const int k = threadIdx.x < 4 ? threadIdx.x : threadIdx.x + 1;   // skip the centre
         const int dy = k % 3 - 1, dz = k / 3 - 1;
         nbs[threadIdx.x] = (by + dy + nby) % nby + nby * ((bz + dz + nbz) % nbz);
     }
-    __shared__ int hoff[2 * (BZ + 2) + 2 * PBY];   // global row offsets of the halo rows (lane 0)
-    for (int h = threadIdx.x; h < G::NH; h += PTHREADS) {
-        int r, pl;
+    // halo row h -> (row r, plane pl) of the brick's frame, r in -1..PBY, pl in -1..BZ
+    auto halo_rp = [&](int h, int& r, int& pl) {
         if (h < 2 * (BZ + 2)) { r = (h < BZ + 2) ? -1 : PBY; pl = h % (BZ + 2) - 1; }
         else { const int h2 = h - 2 * (BZ + 2); pl = (h2 < PBY) ? -1 : BZ; r = h2 % PBY; }
+    };
+    // where the x-filtered halo row lives: a y-halo row of an own plane, or a z-halo plane row
+    auto halo_dst = [&](int r, int pl) -> float* {
+        if (pl >= 0 && pl < BZ) return XH + ((r < 0 ? 0 : 1) * BZ + pl) * W;
+        return ZH + ((pl < 0 ? 0 : 1) * (PBY + 2) + (r + 1)) * W;
+    };
+    __shared__ int hoff[2 * (BZ + 2) + 2 * PBY];   // global row offsets of the halo rows
+    for (int h = threadIdx.x; h < G::NH; h += PTHREADS) {
+        int r, pl;
+        halo_rp(h, r, pl);
         const int y = (y0 + r + ny) % ny, z = (z0 + pl + nz) % nz;
         hoff[h] = z * plane + y * W;
     }
     const int c0 = ctl.flags[(size_t)b * kFlagStride];   // step counters of all bricks are equal at launch
-    __syncthreads();
     bool aborted = ld_acquire(ctl.abort) != 0;
 
-    auto xs = [&](int pl, int r) { return XS + ((pl + 1) * (PBY + 2) + (r + 1)) * W + VEC * lane; };
     auto xpass = [&](VT v) -> VT {      // x pass of a periodic row held by the warp
         const float lv = __shfl_sync(0xffffffffu, v.w, (lane + 31) & 31);
         const float rv = __shfl_sync(0xffffffffu, v.x, (lane + 1) & 31);
@@ -147,30 +159,42 @@ __global__ void __launch_bounds__(32 * NW, 16 / NW) k_prop_pers(const Rep* __res
         o.w = be * v.w + al * (v.z + rv);
         return o;
     };
-    auto is_boundary = [&](int pl) { return row == 0 || row == PBY - 1 || pl == 0 || pl == BZ - 1; };
-    // own planes never wrap: offset of (row, p0 + k) is own0 + k * plane
-    const size_t own0 = (size_t)(z0 + p0) * plane + (size_t)(y0 + row) * W + VEC * lane;
+    auto mix = [&](VT a, VT c, VT d) -> VT {   // be c + al (a + d)
+        VT o;
+        o.x = be * c.x + al * (a.x + d.x);
+        o.y = be * c.y + al * (a.y + d.y);
+        o.z = be * c.z + al * (a.z + d.z);
+        o.w = be * c.w + al * (a.w + d.w);
+        return o;
+    };
+    auto ys = [&](int pl, int r) { return YS + ((pl + 1) * PBY + r) * W + VEC * lane; };
+    const bool face_plane = (w == 0 || w == BZ - 1);
+    auto is_boundary = [&](int r) { return face_plane || r == 0 || r == PBY - 1; };
+    // own plane never wraps: offset of (row r, plane w) is own0 + r * W
+    const size_t own0 = (size_t)(z0 + w) * plane + (size_t)y0 * W + VEC * lane;
 
-    VT e[OWN];
+    VT e[PBY];
     auto load_e = [&](int species) {
         const float* E = (const float*)R.E + (size_t)species * V;
 #pragma unroll
-        for (int k = 0; k < OWN; ++k) e[k] = *(const VT*)(E + own0 + (size_t)k * plane);
+        for (int r = 0; r < PBY; ++r) e[r] = *(const VT*)(E + own0 + (size_t)r * W);
     };
-    auto prefetch_gs = [&](int s) {   // backward: G_s of this warp's pairs into GS
+    auto prefetch_gs = [&](int s) {   // backward: G_s of this warp's plane into GS
         const float* Gs = (const float*)R.G + (size_t)(s - 1) * V;
 #pragma unroll
-        for (int k = 0; k < OWN; ++k) cp16(GS + ((p0 + k) * PBY + row) * W + VEC * lane, Gs + own0 + (size_t)k * plane);
+        for (int r = 0; r < PBY; ++r) cp16(GS + (w * PBY + r) * W + VEC * lane, Gs + own0 + (size_t)r * W);
         cpc();
     };
 
-    {   // the first input (G_0 = 1, or G+_{N+1} = 1): its x pass is be + 2 al everywhere
-        const float one = be + 2.0f * al;
-        for (int i = threadIdx.x; i < (BZ + 2) * (PBY + 2) * W; i += PTHREADS) XS[i] = one;
-    }
-    VT qacc[BWD ? OWN : 1];
+    // the first input (G_0 = 1, or G+_{N+1} = 1): its x pass is be + 2 al everywhere
+    const float one = be + 2.0f * al;
+    VT xf[PBY];
 #pragma unroll
-    for (int k = 0; k < (BWD ? OWN : 1); ++k) qacc[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int r = 0; r < PBY; ++r) xf[r] = make_float4(one, one, one, one);
+    for (int i = threadIdx.x; i < (2 * BZ + 2 * (PBY + 2)) * W; i += PTHREADS) XH[i] = one;   // XH and ZH
+    VT qacc[BWD ? PBY : 1];
+#pragma unroll
+    for (int r = 0; r < (BWD ? PBY : 1); ++r) qacc[r] = make_float4(0.f, 0.f, 0.f, 0.f);
     float qsum = 0.f;
     int species = BWD ? (N <= nA ? 0 : 1) : (1 <= nA ? 0 : 1);
     load_e(species);
@@ -184,15 +208,15 @@ __global__ void __launch_bounds__(32 * NW, 16 / NW) k_prop_pers(const Rep* __res
             if (BWD) {   // leaving the B block: its quadrature is complete
                 float* q = (float*)R.q + (size_t)species * V;
 #pragma unroll
-                for (int k = 0; k < OWN; ++k) {
-                    *(VT*)(q + own0 + (size_t)k * plane) = qacc[k];
-                    qacc[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+                for (int r = 0; r < PBY; ++r) {
+                    *(VT*)(q + own0 + (size_t)r * W) = qacc[r];
+                    qacc[r] = make_float4(0.f, 0.f, 0.f, 0.f);
                 }
             }
             species = sp;
             load_e(species);
         }
-        // halo of the previous step
+        // halo of the previous step, x-filtered into XH / ZH
         if (j > 0) {
             wait_nb(ctl, nbs, c0 + j, aborted);
             const float* src = BWD ? (const float*)(((j - 1) & 1) ? R.Gp1 : R.Gp0)
@@ -202,68 +226,72 @@ __global__ void __launch_bounds__(32 * NW, 16 / NW) k_prop_pers(const Rep* __res
             cpw0();
             for (int h = w; h < G::NH; h += PWARPS) {
                 int r, pl;
-                if (h < 2 * (BZ + 2)) { r = (h < BZ + 2) ? -1 : PBY; pl = h % (BZ + 2) - 1; }
-                else { const int h2 = h - 2 * (BZ + 2); pl = (h2 < PBY) ? -1 : BZ; r = h2 % PBY; }
-                *(VT*)xs(pl, r) = xpass(*(const VT*)(HS + h * W + VEC * lane));
+                halo_rp(h, r, pl);
+                *(VT*)(halo_dst(r, pl) + VEC * lane) = xpass(*(const VT*)(HS + h * W + VEC * lane));
             }
         } else if (BWD) {
             cpw0();
         }
         __syncthreads();
-        // y pass of this warp's row over planes p0 - 1 .. p0 + OWN, into registers
-        VT yf[OWN + 2];
+        // y pass of the own plane in registers (its two y-halo rows from XH), into YS
+        {
+            const VT top = *(const VT*)(XH + w * W + VEC * lane);          // row -1
+            const VT bot = *(const VT*)(XH + (BZ + w) * W + VEC * lane);   // row PBY
+            VT prev = top;
 #pragma unroll
-        for (int k = 0; k < OWN + 2; ++k) {
-            const int pl = p0 - 1 + k;
-            const VT a = *(const VT*)xs(pl, row - 1), c = *(const VT*)xs(pl, row), d = *(const VT*)xs(pl, row + 1);
-            yf[k].x = be * c.x + al * (a.x + d.x);
-            yf[k].y = be * c.y + al * (a.y + d.y);
-            yf[k].z = be * c.z + al * (a.z + d.z);
-            yf[k].w = be * c.w + al * (a.w + d.w);
+            for (int r = 0; r < PBY; ++r) {
+                const VT nxt = (r + 1 < PBY) ? xf[r + 1] : bot;
+                const VT yv = mix(prev, xf[r], nxt);
+                prev = xf[r];
+                xf[r] = yv;   // xf now holds the y-filtered rows
+                *(VT*)ys(w, r) = yv;
+            }
         }
-        __syncthreads();   // XS is rewritten below
+        // y pass of the z-halo planes, one row per warp (PBY rows of each of the two planes)
+        for (int t = w; t < 2 * PBY; t += PWARPS) {
+            const int side = t / PBY, r = t % PBY;
+            const float* zr = ZH + (side * (PBY + 2) + r + 1) * W + VEC * lane;
+            *(VT*)ys(side ? BZ : -1, r) = mix(*(const VT*)(zr - W), *(const VT*)zr, *(const VT*)(zr + W));
+        }
+        __syncthreads();
         // z pass and step output
         float* dst = BWD ? (float*)((j & 1) ? R.Gp1 : R.Gp0) : (float*)R.G + (size_t)(s - 1) * V;
-        VT out[OWN];
+        VT out[PBY];
 #pragma unroll
-        for (int k = 0; k < OWN; ++k) {
-            VT sg;
-            sg.x = be * yf[k + 1].x + al * (yf[k].x + yf[k + 2].x);
-            sg.y = be * yf[k + 1].y + al * (yf[k].y + yf[k + 2].y);
-            sg.z = be * yf[k + 1].z + al * (yf[k].z + yf[k + 2].z);
-            sg.w = be * yf[k + 1].w + al * (yf[k].w + yf[k + 2].w);
-            out[k].x = e[k].x * sg.x;
-            out[k].y = e[k].y * sg.y;
-            out[k].z = e[k].z * sg.z;
-            out[k].w = e[k].w * sg.w;
+        for (int r = 0; r < PBY; ++r) {
+            const VT sg = mix(*(const VT*)ys(w - 1, r), xf[r], *(const VT*)ys(w + 1, r));
+            out[r].x = e[r].x * sg.x;
+            out[r].y = e[r].y * sg.y;
+            out[r].z = e[r].z * sg.z;
+            out[r].w = e[r].w * sg.w;
             if (BWD) {
-                const VT g = *(const VT*)(GS + ((p0 + k) * PBY + row) * W + VEC * lane);
-                qacc[k].x += g.x * sg.x;
-                qacc[k].y += g.y * sg.y;
-                qacc[k].z += g.z * sg.z;
-                qacc[k].w += g.w * sg.w;
+                const VT g = *(const VT*)(GS + (w * PBY + r) * W + VEC * lane);
+                qacc[r].x += g.x * sg.x;
+                qacc[r].y += g.y * sg.y;
+                qacc[r].z += g.z * sg.z;
+                qacc[r].w += g.w * sg.w;
             } else if (s == N) {
-                qsum += (out[k].x + out[k].y) + (out[k].z + out[k].w);
+                qsum += (out[r].x + out[r].y) + (out[r].z + out[r].w);
             }
-            if (is_boundary(p0 + k) && (!BWD || s > 1)) *(VT*)(dst + own0 + (size_t)k * plane) = out[k];
+            if (is_boundary(r) && (!BWD || s > 1)) *(VT*)(dst + own0 + (size_t)r * W) = out[r];
         }
         // publish the boundary of this step: the CTA barrier orders every thread's boundary stores
         // before thread 0's release store, and release is cumulative, so a CTA whose acquire load
-        // reads the new counter sees them.  The release waits for the memory operations the SM
-        // has in flight, so nothing else is issued before it.
+        // reads the new counter sees them.  The barrier also ends every warp's reads of YS, XH
+        // and ZH for this step.
         __syncthreads();
         if (threadIdx.x == 0) st_release(ctl.flags + (size_t)b * kFlagStride, c0 + j + 1);
         if (BWD && s > 1) prefetch_gs(s - 1);   // GS slots of this thread were read above
 #pragma unroll
-        for (int k = 0; k < OWN; ++k) {
-            if (!BWD && !is_boundary(p0 + k)) *(VT*)(dst + own0 + (size_t)k * plane) = out[k];
-            *(VT*)xs(p0 + k, row) = xpass(out[k]);
+        for (int r = 0; r < PBY; ++r) {
+            if (!BWD && !is_boundary(r)) *(VT*)(dst + own0 + (size_t)r * W) = out[r];
+            xf[r] = xpass(out[r]);
         }
     }
     if (BWD) {   // the A block ends at s = 1
         float* q = (float*)R.q + (size_t)species * V;
 #pragma unroll
-        for (int k = 0; k < OWN; ++k) *(VT*)(q + own0 + (size_t)k * plane) = qacc[k];
+        for (int r = 0; r < PBY; ++r) *(VT*)(q + own0 + (size_t)r * W) = qacc[r];
     } else {
         const double t = block_sum((double)qsum, sh);
         if (threadIdx.x == 0) slot(R, P_Q)[b] = t;
@@ -276,7 +304,7 @@ __global__ void __launch_bounds__(32 * NW, 16 / NW) k_prop_pers(const Rep* __res
 
 bool pers_supported(const Rep& R, int bz, int nw, int nsm) {
     if (R.nx != 128 || R.ny % PBY || R.nz % bz) return false;
-    if (!((bz == 16 && nw == 16) || (bz == 8 && (nw == 16 || nw == 8)))) return false;
+    if (!((bz == 16 && nw == 16) || (bz == 8 && nw == 8))) return false;   // one warp per plane
     const int nb = (R.ny / PBY) * (R.nz / bz);
     return nb >= 1 && nb <= nsm * (nw == 8 ? 2 : 1);   // all bricks co-resident
 }
@@ -299,7 +327,6 @@ cudaError_t pers_attr() {
 
 int pers_prepare(int bz, int nw) {
     if (bz == 16 && nw == 16) return (int)pers_attr<16, 16>();
-    if (bz == 8 && nw == 16) return (int)pers_attr<8, 16>();
     if (bz == 8 && nw == 8) return (int)pers_attr<8, 8>();
     return (int)cudaErrorInvalidValue;
 }
@@ -359,15 +386,14 @@ int launch_prop_pers(const Launch& L, bool bwd, int bz, int nw, int nbricks, int
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     cudaError_t e;
-    if (bz == 16)
+    if (bz == 16 && nw == 16)
         e = bwd ? cudaLaunchKernelEx(&cfg, k_prop_pers<16, true, 16>, L.reps, ctl)
                 : cudaLaunchKernelEx(&cfg, k_prop_pers<16, false, 16>, L.reps, ctl);
-    else if (nw == 16)
-        e = bwd ? cudaLaunchKernelEx(&cfg, k_prop_pers<8, true, 16>, L.reps, ctl)
-                : cudaLaunchKernelEx(&cfg, k_prop_pers<8, false, 16>, L.reps, ctl);
-    else
+    else if (bz == 8 && nw == 8)
         e = bwd ? cudaLaunchKernelEx(&cfg, k_prop_pers<8, true, 8>, L.reps, ctl)
                 : cudaLaunchKernelEx(&cfg, k_prop_pers<8, false, 8>, L.reps, ctl);
+    else
+        e = cudaErrorInvalidValue;
     return (int)e;
 }
 
