@@ -40,6 +40,8 @@ class Params(ctypes.Structure):
         ("tau_s", ctypes.c_double), ("tau_b", ctypes.c_double), ("rho0", ctypes.c_double),
         ("hydro", ctypes.c_int32), ("ncg_iters", ctypes.c_int32), ("cn_sweeps", ctypes.c_int32),
         ("phi_floor", ctypes.c_double), ("ncg_tol", ctypes.c_double),
+        ("omega", ctypes.c_double), ("lb_noise", ctypes.c_int32), ("pad_", ctypes.c_int32),
+        ("seed", ctypes.c_uint64), ("step", ctypes.c_int64),
     ]
 
 
@@ -58,6 +60,10 @@ def lib():
             "or_densities": (ctypes.c_double, [P, D, D, D, D]),
             "or_objective": (ctypes.c_double, [P, D, D]),
             "or_ncg": (ctypes.c_int, [P, D, D, D, D]),
+            "or_philox4x32": (None, [ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(ctypes.c_uint32),
+                                     ctypes.POINTER(ctypes.c_uint32)]),
+            "or_normals4": (None, [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, D]),
+            "or_cd_noise": (None, [P, D, D]),
             "or_mu": (None, [P, D, D, D]),
             "or_force": (None, [P, D, D, D]),
             "or_lb_basis": (None, [D, D, D, ctypes.POINTER(ctypes.c_int)]),
@@ -104,6 +110,10 @@ def make_params(cfg: dict) -> Params:
     p.cn_sweeps = cfg.get("cn_sweeps", 8)
     p.phi_floor = cfg.get("phi_floor", 1e-6)
     p.ncg_tol = cfg.get("ncg_tol", 0.0)
+    p.omega = cfg.get("omega", 0.0)          # thermal noise (0: none)
+    p.lb_noise = cfg.get("lb_noise", 0)
+    p.seed = cfg.get("noise_seed", 0)
+    p.step = cfg.get("noise_step", 0)
     return p
 
 
@@ -171,6 +181,29 @@ def ncg_run(cfg: dict, phi_target: np.ndarray, U0: np.ndarray):
     info = np.zeros(2 + 4 * max(cfg.get("ncg_iters", 4), 0))
     k = lib().or_ncg(ctypes.byref(p), _ptr(_f64(phi_target)), _ptr(U), _ptr(phim), _ptr(info))
     return U, phim, info, k
+
+
+def philox4x32(ctr, key):
+    """Philox4x32-10 of a counter (4 words) and key (2 words): 4 output words."""
+    c = (ctypes.c_uint32 * 4)(*ctr)
+    k = (ctypes.c_uint32 * 2)(*key)
+    o = (ctypes.c_uint32 * 4)()
+    lib().or_philox4x32(c, k, o)
+    return list(o)
+
+
+def normals4(seed: int, site: int, step: int, stream: int) -> np.ndarray:
+    out = np.zeros(4)
+    lib().or_normals4(seed, site, step, stream, _ptr(out))
+    return out
+
+
+def cd_noise(cfg: dict, phi: np.ndarray) -> np.ndarray:
+    """The composition noise increment of one step (cfg: omega, noise_seed, noise_step)."""
+    p = make_params(cfg)
+    out = np.empty_like(_f64(phi))
+    lib().or_cd_noise(ctypes.byref(p), _ptr(_f64(phi)), _ptr(out))
+    return out
 
 
 def mu(cfg: dict, U: np.ndarray, phi: np.ndarray) -> np.ndarray:

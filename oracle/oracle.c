@@ -44,6 +44,11 @@ typedef struct {
     int32_t cn_sweeps;   /* Jacobi sweeps for the Crank-Nicolson system                  */
     double phi_floor;    /* floor on phi inside the local curvature of mu              */
     double ncg_tol;      /* > 0: stop the inversion once max|phi* - phi[U]| < ncg_tol    */
+    double omega;        /* > 0: thermal noise with noise parameter Omega = h^3/v0        */
+    int32_t lb_noise;    /* with omega > 0: also the fluctuating LB modes (Eq. 13)       */
+    int32_t pad_;
+    uint64_t seed;       /* key of the counter-based generator                           */
+    int64_t step;        /* step index (counter word 1) of the noise of this call        */
 } or_params;
 
 static inline int64_t nsites(const or_params* p) { return (int64_t)p->nx * p->ny * p->nz; }
@@ -290,6 +295,91 @@ void or_force(const or_params* p, const double* phi, const double* mu, double* f
 }
 
 /* ------------------------------------------------------------------------------------ */
+/* Thermal noise (Sec. 2: Eq. 5 for the compositions, phi_k r_k in Eq. 13 for the LB).     */
+/* Random numbers: Philox4x32-10, the counter-based generator of Salmon, Moraes, Dror and  */
+/* Shaw (SC'11): ten rounds of two 32x32 -> 64-bit products of counter words with the      */
+/* multipliers 0xD2511F53 and 0xCD9E8D57, the high halves XORed with the other two counter */
+/* words and the key, the key bumped by the Weyl constants 0x9E3779B9, 0xBB67AE85 between  */
+/* rounds.  Key = (seed low 32 bits, seed high 32 bits).  Counter words (site, step,      */
+/* stream, 0): stream 1 + I for the composition noise of species I, 16 + c (c = 0..3) for */
+/* the LB modes.  Each output word gives a uniform u = (top 24 bits + 1/2) / 2^24 in       */
+/* (0, 1); words (0, 1) and (2, 3) give two Box-Muller pairs                               */
+/*   n = sqrt(-2 ln u_a) cos(2 pi u_b),  n' = sqrt(-2 ln u_a) sin(2 pi u_b).               */
+/* ------------------------------------------------------------------------------------ */
+void or_philox4x32(const uint32_t ctr_in[4], const uint32_t key_in[2], uint32_t out[4]) {
+    uint32_t c[4] = {ctr_in[0], ctr_in[1], ctr_in[2], ctr_in[3]};
+    uint32_t k0 = key_in[0], k1 = key_in[1];
+    for (int round = 0; round < 10; ++round) {
+        if (round > 0) { k0 += 0x9E3779B9u; k1 += 0xBB67AE85u; }
+        const uint64_t p0 = (uint64_t)0xD2511F53u * c[0];
+        const uint64_t p1 = (uint64_t)0xCD9E8D57u * c[2];
+        const uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        const uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        const uint32_t n0 = hi1 ^ c[1] ^ k0, n1 = lo1, n2 = hi0 ^ c[3] ^ k1, n3 = lo0;
+        c[0] = n0; c[1] = n1; c[2] = n2; c[3] = n3;
+    }
+    for (int i = 0; i < 4; ++i) out[i] = c[i];
+}
+
+/* Four standard normals of counter (site, step, stream, 0). */
+void or_normals4(uint64_t seed, uint32_t site, uint32_t step, uint32_t stream, double n[4]) {
+    const uint32_t ctr[4] = {site, step, stream, 0u};
+    const uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    uint32_t r[4];
+    or_philox4x32(ctr, key, r);
+    double u[4];
+    for (int i = 0; i < 4; ++i) u[i] = ((double)(r[i] >> 8) + 0.5) / 16777216.0;
+    const double two_pi = 6.283185307179586476925286766559;
+    for (int pr = 0; pr < 2; ++pr) {
+        const double rad = sqrt(-2.0 * log(u[2 * pr]));
+        n[2 * pr] = rad * cos(two_pi * u[2 * pr + 1]);
+        n[2 * pr + 1] = rad * sin(two_pi * u[2 * pr + 1]);
+    }
+}
+
+/* Composition noise of one step (Eq. 5), reading of the van Vlimmeren-Fraaije construction */
+/* on the lattice: a random flux on every face, J_a(r) between r and r + e_a with variance   */
+/* 2 M phi_face / (Omega dt) (phi_face the mean of the two sites, clipped at 0; the         */
+/* 1/Omega = v0/h^3 turns bead densities into volume fractions), and the increment of the    */
+/* step is minus its divergence,                                                              */
+/*   dphi_I(r) = dt sum_a [J_a(r - e_a) - J_a(r)],                                            */
+/* so its covariance is -(2/Omega) M dt div(phi grad delta) and every species' total is kept. */
+/* J_a(r) = sqrt(2 M phi_face dt / Omega) n_a / dt with n_a the a-th normal of stream 1 + I.  */
+void or_cd_noise(const or_params* p, const double* phi, double* dphi) {
+    const int64_t V = nsites(p);
+    const double amp2 = 2.0 * p->M * p->dt / p->omega;
+    for (int I = 0; I < p->ns; ++I) {
+        const double* ph = phi + I * V;
+        double* J = (double*)malloc(sizeof(double) * 3 * (size_t)V);   /* dt * J_a(r), [a][V] */
+#pragma omp parallel for schedule(static)
+        for (int z = 0; z < p->nz; ++z)
+            for (int y = 0; y < p->ny; ++y)
+                for (int x = 0; x < p->nx; ++x) {
+                    const int64_t i = sidx(p, x, y, z);
+                    double n[4];
+                    or_normals4(p->seed, (uint32_t)i, (uint32_t)p->step, 1u + (uint32_t)I, n);
+                    const int64_t nb[3] = {sidx(p, x + 1, y, z), sidx(p, x, y + 1, z), sidx(p, x, y, z + 1)};
+                    for (int a = 0; a < 3; ++a) {
+                        double face = 0.5 * (ph[i] + ph[nb[a]]);
+                        if (face < 0.0) face = 0.0;
+                        J[a * V + i] = sqrt(amp2 * face) * n[a];
+                    }
+                }
+#pragma omp parallel for schedule(static)
+        for (int z = 0; z < p->nz; ++z)
+            for (int y = 0; y < p->ny; ++y)
+                for (int x = 0; x < p->nx; ++x) {
+                    const int64_t i = sidx(p, x, y, z);
+                    const int64_t lo[3] = {sidx(p, x - 1, y, z), sidx(p, x, y - 1, z), sidx(p, x, y, z - 1)};
+                    double d = 0.0;
+                    for (int a = 0; a < 3; ++a) d += J[a * V + lo[a]] - J[a * V + i];
+                    dphi[I * V + i] = d;
+                }
+        free(J);
+    }
+}
+
+/* ------------------------------------------------------------------------------------ */
 /* D3Q19 multiple-relaxation-time lattice Boltzmann (Eq. 9-14, Table 1).                  */
 /* ------------------------------------------------------------------------------------ */
 static const int OR_C[19][3] = {
@@ -406,7 +496,7 @@ void or_lb_step(const or_params* p, const double* n_in, const double* f, double*
                             ss += Sig[a][bb] * (c[i][a] * c[i][bb] - cs2 * (a == bb ? 1.0 : 0.0));
                     Df[i] = w[i] / cs2 * (fc + 0.5 / cs2 * ss);
                 }
-                /* modes, Eq. 12; relaxation, Eq. 13 (no noise); reconstruction */
+                /* modes, Eq. 12; relaxation, Eq. 13; reconstruction */
                 double ms[19];
                 for (int k = 0; k < 19; ++k) {
                     double mk = 0.0, mf = 0.0;
@@ -415,6 +505,17 @@ void or_lb_step(const or_params* p, const double* n_in, const double* f, double*
                         mf += Df[i] * e[k][i];
                     }
                     ms[k] = gam[k] * mk + mf;
+                }
+                if (p->omega > 0.0 && p->lb_noise) {
+                    /* phi_k r_k of Eq. 13 for the non-conserved modes k = 4..18, with the
+                     * lattice-unit temperature kT = dt^2 / Omega (energy kT per bead, Omega
+                     * beads of mass m0 per voxel, m0 = kT tau^2 / h^2) and c_s^2 = 1/3 */
+                    const double kT = p->dt * p->dt / p->omega;
+                    double g[16];
+                    for (int cc = 0; cc < 4; ++cc)
+                        or_normals4(p->seed, (uint32_t)r, (uint32_t)p->step, 16u + (uint32_t)cc, g + 4 * cc);
+                    for (int k = 4; k < 19; ++k)
+                        ms[k] += sqrt(rho * kT * b[k] * (1.0 - gam[k] * gam[k]) / cs2) * g[k - 4];
                 }
                 for (int i = 0; i < 19; ++i) {
                     double acc = 0.0;
@@ -482,6 +583,12 @@ void or_cd_step(const or_params* p, const double* phi, const double* mu, const d
                     r[I * V + i] = -conv + p->dt * p->M * lap;
                 }
             }
+    if (p->omega > 0.0) {   /* thermal noise of the step enters the explicit part */
+        double* dn = (double*)malloc(sizeof(double) * (size_t)ns * (size_t)V);
+        or_cd_noise(p, phi, dn);
+        for (int64_t k = 0; k < (int64_t)ns * V; ++k) r[k] += dn[k];
+        free(dn);
+    }
 
     for (int sweep = 0; sweep < p->cn_sweeps; ++sweep) {
 #pragma omp parallel for schedule(static)

@@ -673,3 +673,73 @@ def test_net_gradient_finite_differences():
         fd = (lp - lm) / (2 * h)
         g = grads[li][pi][idx]
         assert abs(fd - g) <= 1e-6 * max(abs(g), 1e-3 * abs(loss))
+
+
+# ---------------------------------------------------------------------------------------------
+# Thermal noise (Eq. 5, Eq. 13): the counter-based generator and the two noise terms
+# ---------------------------------------------------------------------------------------------
+def test_philox_known_answers():
+    """The oracle's Philox4x32-10 reproduces the generator's published known-answer vectors."""
+    kat = json.load(open(os.path.join(GOLDEN, "philox4x32_10_kat.json")))
+    for v in kat["vectors"]:
+        out = oracle.philox4x32([int(x, 16) for x in v["ctr"]], [int(x, 16) for x in v["key"]])
+        assert out == [int(x, 16) for x in v["out"]]
+
+
+def test_normals_are_standard():
+    """Box-Muller normals of distinct counters: mean 0, variance 1, kurtosis 3, pairs uncorrelated."""
+    n = np.array([oracle.normals4(12345, site, 7, 3) for site in range(40000)])
+    x = n.ravel()
+    assert abs(x.mean()) < 0.01
+    assert abs(x.var() - 1.0) < 0.02
+    assert abs((x ** 4).mean() / x.var() ** 2 - 3.0) < 0.08
+    assert abs(np.corrcoef(n[:, 0], n[:, 1])[0, 1]) < 0.02
+    assert abs(np.corrcoef(n[:, 0], n[:, 2])[0, 1]) < 0.02
+    # different streams and steps give different numbers
+    assert not np.allclose(oracle.normals4(1, 5, 0, 1), oracle.normals4(1, 5, 0, 2))
+    assert not np.allclose(oracle.normals4(1, 5, 0, 1), oracle.normals4(1, 5, 1, 1))
+
+
+def test_cd_noise_fluctuation_dissipation():
+    """Composition noise of Eq. 5 as a random face flux: every species' total is kept exactly;
+    for a uniform phi the increment has variance 12 M phi dt / Omega (six faces of variance
+    2 M phi dt / Omega each) and neighbours along an axis share one face (covariance -1/6 of it)."""
+    cfg = dict(cfg_small(grid=(24, 24, 24), N=4, nA=2), omega=100.0, noise_seed=99, noise_step=4)
+    phi = np.stack([np.full((24, 24, 24), 0.3), np.full((24, 24, 24), 0.7)])
+    dn = oracle.cd_noise(cfg, phi)
+    assert np.abs(dn.reshape(2, -1).sum(1)).max() < 1e-12
+    M, dt, om = cfg["M"], cfg["dt"], cfg["omega"]
+    for I, ph in enumerate((0.3, 0.7)):
+        var = 12 * M * ph * dt / om
+        assert abs(dn[I].var() / var - 1.0) < 0.04
+        for ax in range(3):
+            cov = (dn[I] * np.roll(dn[I], -1, axis=ax)).mean()
+            assert abs(cov / var + 1.0 / 6.0) < 0.03
+    # species are independent, and a field-dependent amplitude follows phi_face
+    assert abs(np.corrcoef(dn[0].ravel(), dn[1].ravel())[0, 1]) < 0.03
+    phi2 = phi.copy()
+    phi2[0] = 0.0
+    assert np.abs(oracle.cd_noise(cfg, phi2)[0]).max() == 0.0
+
+
+def test_lb_noise_conserves_and_has_the_mode_variances():
+    """Fluctuating collision (Eq. 13): from rest, one step conserves mass and momentum at every
+    site, and each non-conserved mode k = 4..18 of the post-collision populations has variance
+    phi_k^2 = rho kT b_k (1 - gamma_k^2) / c_s^2 with kT = dt^2 / Omega."""
+    g = (20, 20, 20)
+    cfg = dict(cfg_small(grid=g, N=4, nA=2, tau_s=0.9, tau_b=1.3), omega=50.0, lb_noise=1,
+               noise_seed=7, noise_step=2)
+    e, w, b, c = oracle.lb_basis()
+    n0 = np.broadcast_to(w[:, None, None, None], (19,) + g[::-1]).copy()
+    out, _ = oracle.lb_step(cfg, n0)
+    # undo the streaming: post-collision populations at each site
+    post = np.stack([np.roll(out[i], shift=(-c[i][2], -c[i][1], -c[i][0]), axis=(0, 1, 2)) for i in range(19)])
+    m = np.tensordot(e, post - w[:, None, None, None], axes=(1, 0))
+    assert np.abs(m[0]).max() < 1e-14 and np.abs(m[1:4]).max() < 1e-14
+    kT = cfg["dt"] ** 2 / cfg["omega"]
+    gs, gb = 1 - 1 / cfg["tau_s"], 1 - 1 / cfg["tau_b"]
+    gam = [gb] + [gs] * 5 + [0.0] * 9
+    for k in range(4, 19):
+        expect = kT * b[k] * (1 - gam[k - 4] ** 2) * 3.0
+        assert abs(m[k].var() / expect - 1.0) < 0.06, k
+        assert abs(m[k].mean()) < 4 * np.sqrt(expect / m[k].size)
