@@ -199,6 +199,20 @@ int64_t dscf_launches_per_step(const dscf_ctx* ctx);
  * next dscf_step re-captures its graph.  Results do not depend on either value beyond rounding. */
 int dscf_set_tuning(dscf_ctx* ctx, int32_t zc, int32_t kfuse);
 
+/* Thermal noise (Sec. 2: the stochastic term of Eq. 3 with the covariance of Eq. 5, and phi_k r_k in
+ * the relaxation of the LB modes, Eq. 13).  omega = 0 (the default) turns it off; omega > 0 is
+ * the noise parameter Omega = h^3 / v0 (paper: 400, or 100).  Compositions: minus the divergence of
+ * a random flux on every lattice face, variance 2 M phi_face / (Omega dt), added to the explicit
+ * part of the Crank-Nicolson step (every species' total is kept).  lb_noise != 0 also draws the
+ * fluctuating collision: every non-conserved mode k = 4..18 gains sqrt(rho kT b_k (1 - gamma_k^2)
+ * / c_s^2) r_k with the lattice temperature kT = dt^2 / Omega.  Normals: Philox4x32-10 keyed by
+ * seed (low word, high word), counter (site, step, stream, replica) with stream 1 + I for species
+ * I and 16..19 for the LB modes, uniforms (top 24 bits + 1/2) / 2^24, Box-Muller; the step index
+ * is the context's step counter (it starts at 0 and advances once per coupled step and per
+ * lb_step).  Synchronises and re-captures the step graph.  DSCF_ERR_ARG for a negative or
+ * non-finite omega. */
+int dscf_set_noise(dscf_ctx* ctx, double omega, int32_t lb_noise, uint64_t seed);
+
 /* Residual stop of the inversion (step 1): with tol > 0 the Fletcher-Reeves iterations of each
  * exact step stop before iteration k once max_r |phi*_I(r) - phi_I[U](r)| < tol for every replica
  * (or the residual is not finite, which also sets the non-finite status bit), and after at most

@@ -136,6 +136,7 @@ Layout make_layout(const dscf_params* p, int n, int prec, char* base) {
     for (int r = 0; r < n; ++r) {
         Rep& R = L.reps[r];
         std::memset(&R, 0, sizeof(Rep));
+        R.rep_index = r;
         const dscf_params& q = p[r];
         R.nx = q.nx; R.ny = q.ny; R.nz = q.nz; R.ns = q.ns; R.N = q.N; R.nA = q.nA;
         R.V = (long long)q.nx * q.ny * q.nz;
@@ -242,6 +243,7 @@ struct dscf_ctx {
     bool pers_perm = false; // brick placement table in use
     int wait_limit = kPersSpinLimit;   // polls before a persistent sweep gives up on a neighbour
     double ncg_tol = 0.0;   // > 0: residual stop of the inversion (conditional graph nodes)
+    int noise = 0;          // thermal noise (dscf_set_noise): 1 compositions, 2 LB modes
     cudaError_t cap_err = cudaSuccess;   // first graph-construction error of a capture
     const char* cap_what = "";
     int nsm = 0;
@@ -278,6 +280,7 @@ Launch launch_of(dscf_ctx* c, cudaStream_t s) {
     L.nblk_total = c->L.nblk;
     L.nlb_total = c->L.nlb;
     L.nrep = c->nrep;
+    L.noise = c->noise;
     L.stream = s;
     return L;
 }
@@ -469,6 +472,8 @@ int64_t enqueue_step(dscf_ctx* c, const Launch& L, bool pred = false) {
         launch_lb<T>(L, nullptr); ++n;
         mark(3);
         launch_step_end(L); ++n;
+    } else if (c->noise) {
+        launch_step_end(L); ++n;   // the step counter indexes the noise
     }
     launch_cd<T>(L, c->params[0].cn_sweeps);
     n += 3 + c->params[0].cn_sweeps;
@@ -1051,6 +1056,34 @@ int dscf_status(dscf_ctx* c) {
         return fail(c, DSCF_ERR_TIMEOUT, "a persistent contour sweep gave up waiting for a neighbour");
     }
     if (st & ST_NONFINITE) return fail(c, DSCF_ERR_NUMERIC, "non-finite value in a reduction");
+    return DSCF_OK;
+}
+
+int dscf_set_noise(dscf_ctx* c, double omega, int32_t lb_noise, uint64_t seed) {
+    if (!c) return DSCF_ERR_ARG;
+    if (!(omega >= 0.0) || !std::isfinite(omega)) return fail(c, DSCF_ERR_ARG, "omega must be finite and >= 0");
+    if (int rc = set_dev(c)) return rc;
+    if (int rc = cuda_check(c, cudaStreamSynchronize(c->stream), "noise sync")) return rc;
+    for (int r = 0; r < c->nrep; ++r) {
+        Rep& R = c->L.reps[r];
+        const dscf_params& q = c->params[r];
+        R.noise_amp2 = omega > 0.0 ? 2.0 * q.M * q.dt / omega : 0.0;
+        R.noise_kT = (omega > 0.0 && lb_noise) ? q.dt * q.dt / omega : 0.0;
+        R.noise_seed = seed;
+    }
+    if (int rc = cuda_check(c, cudaMemcpyAsync(c->d_reps, c->L.reps.data(), sizeof(Rep) * c->nrep,
+                                               cudaMemcpyHostToDevice, c->stream), "noise parameters"))
+        return rc;
+    if (int rc = cuda_check(c, cudaStreamSynchronize(c->stream), "noise parameters")) return rc;
+    c->noise = omega > 0.0 ? (1 | (lb_noise ? 2 : 0)) : 0;
+    if (c->exec) {
+        cudaGraphExecDestroy(c->exec);
+        c->exec = nullptr;
+    }
+    if (c->exec_pred) {
+        cudaGraphExecDestroy(c->exec_pred);
+        c->exec_pred = nullptr;
+    }
     return DSCF_OK;
 }
 

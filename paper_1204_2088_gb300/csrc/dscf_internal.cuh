@@ -83,6 +83,11 @@ struct Rep {
     void* del0;  // [ns][V] Jacobi iterate ping
     void* del1;  // [ns][V] Jacobi iterate pong
     void* rhs;   // [ns][V] right-hand side of the Crank-Nicolson system
+    // thermal noise (dscf_set_noise): composition flux variance 2 M dt / Omega per unit phi,
+    // LB temperature dt^2 / Omega (0: off), generator key
+    double noise_amp2, noise_kT;
+    unsigned long long noise_seed;
+    int rep_index;                         // counter word 3 of the noise (replica in the batch)
     double* part;   // [NPART][part_stride]
     int part_stride;
     double* scal;   // [kScalStride]
@@ -117,6 +122,7 @@ struct Launch {
     int nblk_total;          // flat blocks over all replicas
     int nlb_total;           // LB blocks over all replicas
     int nrep;
+    int noise;               // thermal noise: 1 compositions, 2 LB modes
     cudaStream_t stream;
 };
 
@@ -238,6 +244,45 @@ __device__ __forceinline__ int wrapi(int v, int n) {
 }
 
 // Boltzmann factor exp(-x) in the field precision (CUDA's exp / expf, not re-implemented).
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds; each multiplies counter words 0
+// and 2 by 0xD2511F53 and 0xCD9E8D57 (32 x 32 -> 64 bits), XORs the high halves into words 1 and
+// 3 with the key, and swaps; the key advances by the Weyl constants 0x9E3779B9, 0xBB67AE85.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, unsigned k0, unsigned k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) { k0 += 0x9E3779B9u; k1 += 0xBB67AE85u; }
+        const unsigned lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+        const unsigned lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+    }
+    return c;
+}
+// Four standard normals of counter (site, step, stream, replica): uniforms (top 24 bits + 1/2) /
+// 2^24, Box-Muller on words (0, 1) and (2, 3).
+template <typename T>
+__device__ __forceinline__ void normals4(unsigned long long seed, unsigned site, unsigned step, unsigned stream,
+                                         unsigned rep, T (&n)[4]) {
+    const uint4 r = philox4x32_10(make_uint4(site, step, stream, rep), (unsigned)seed, (unsigned)(seed >> 32));
+    const unsigned w[4] = {r.x, r.y, r.z, r.w};
+#pragma unroll
+    for (int pr = 0; pr < 2; ++pr) {
+        const T ua = ((T)(w[2 * pr] >> 8) + T(0.5)) * T(1.0 / 16777216.0);
+        const T ub = ((T)(w[2 * pr + 1] >> 8) + T(0.5)) * T(1.0 / 16777216.0);
+        T sn, cs;
+        if constexpr (sizeof(T) == 4) {
+            const float rad = sqrtf(-2.f * logf(ua));
+            sincospif(2.f * ub, &sn, &cs);
+            n[2 * pr] = rad * cs;
+            n[2 * pr + 1] = rad * sn;
+        } else {
+            const double rad = sqrt(-2.0 * log(ua));
+            sincospi(2.0 * ub, &sn, &cs);
+            n[2 * pr] = rad * cs;
+            n[2 * pr + 1] = rad * sn;
+        }
+    }
+}
+
 __device__ __forceinline__ double bexp(double x) { return exp(-x); }
 __device__ __forceinline__ float bexp(float x) { return expf(-x); }
 

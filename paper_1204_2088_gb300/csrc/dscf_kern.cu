@@ -405,7 +405,39 @@ __device__ __forceinline__ T lbw(int i) {
 // The incoming populations only enter through their moments, so each outgoing population is
 // formed and stored on its own.  FP32: three CTAs per SM, so that the 19 pulled populations and
 // the force inputs stay in registers (at four the compiler spills).
-template <typename T>
+// Ghost modes 10-18 of the D3Q19 basis (Table 1) at velocity c, and their norms
+// b_k = sum_i w_i e_ki^2 (only the fluctuating collision needs them: they carry no other signal).
+__host__ __device__ constexpr int lb_ghost(int k, int cx, int cy, int cz) {
+    const int c2 = cx * cx + cy * cy + cz * cz;
+    switch (k) {
+        case 10: return (3 * c2 - 5) * cx;
+        case 11: return (3 * c2 - 5) * cy;
+        case 12: return (3 * c2 - 5) * cz;
+        case 13: return (cy * cy - cz * cz) * cx;
+        case 14: return (cz * cz - cx * cx) * cy;
+        case 15: return (cx * cx - cy * cy) * cz;
+        case 16: return 3 * c2 * c2 - 6 * c2 + 1;
+        case 17: return (2 * c2 - 3) * (cx * cx - cy * cy);
+        default: return (2 * c2 - 3) * (c2 - 3 * cz * cz);
+    }
+}
+__host__ __device__ constexpr double lb_ghost_norm(int k) {
+    double b = 0.0;
+    for (int i = 0; i < 19; ++i) {
+        const int cx = lbc(i, 0), cy = lbc(i, 1), cz = lbc(i, 2);
+        const int c2 = cx * cx + cy * cy + cz * cz;
+        const double w = c2 == 0 ? 1.0 / 3.0 : (c2 == 1 ? 1.0 / 18.0 : 1.0 / 36.0);
+        const int e = lb_ghost(k, cx, cy, cz);
+        b += w * e * e;
+    }
+    return b;
+}
+
+// NOISE: the fluctuating collision of Eq. 13: every non-conserved mode k = 4..18 gains
+// phi_k r_k, phi_k = sqrt(rho kT b_k (1 - gamma_k^2) / c_s^2) with the lattice temperature
+// kT = dt^2 / Omega; r_k the normals of counters (site, step, 16..19, replica), the step index
+// being the device step counter.
+template <typename T, bool NOISE>
 __global__ void __launch_bounds__(kFlatThreads, sizeof(T) == 4 ? 3 : 2) k_lb(const Rep* __restrict__ reps, int nrep,
                                                         const int* __restrict__ counter, const T* __restrict__ fext) {
     __shared__ double sh[33];
@@ -488,10 +520,33 @@ __global__ void __launch_bounds__(kFlatThreads, sizeof(T) == 4 ? 3 : 2) k_lb(con
         const T m5 = nxx - nyy;
         const T m6 = m4 - T(3) * nzz;
         // relaxed stress modes divided by their norms b_4 = 2/3, b_5 = 4/9, b_6 = 4/3, b_7..9 = 1/9
-        const T r4 = gb * m4 * T(1.5);
-        const T r5 = gs * m5 * T(2.25);
-        const T r6 = gs * m6 * T(0.75);
-        const T r7 = gs * nxy * T(9), r8 = gs * nxz * T(9), r9 = gs * nyz * T(9);
+        T r4 = gb * m4 * T(1.5);
+        T r5 = gs * m5 * T(2.25);
+        T r6 = gs * m6 * T(0.75);
+        T r7 = gs * nxy * T(9), r8 = gs * nxz * T(9), r9 = gs * nyz * T(9);
+        T gk[9];   // ghost modes m*_k / b_k (noise only)
+        if constexpr (NOISE) {
+            T g[16];
+            const unsigned st = (unsigned)(*counter);
+#pragma unroll
+            for (int cc = 0; cc < 4; ++cc) {
+                T n4[4];
+                normals4<T>(R.noise_seed, (unsigned)site, st, 16u + (unsigned)cc, (unsigned)R.rep_index, n4);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) g[4 * cc + q] = n4[q];
+            }
+            // m*_k / b_k gains phi_k r_k / b_k = sqrt(3 rho kT (1 - gamma_k^2) / b_k) r_k
+            const T t3 = T(3) * rho * (T)R.noise_kT;
+            const T ab = sqrt(t3 * (T(1) - gb * gb)), as = sqrt(t3 * (T(1) - gs * gs));
+            r4 += ab * sqrt(T(1.5)) * g[0];    // b_4 = 2/3
+            r5 += as * sqrt(T(2.25)) * g[1];   // b_5 = 4/9
+            r6 += as * sqrt(T(0.75)) * g[2];   // b_6 = 4/3
+            r7 += as * T(3) * g[3];            // b_7..9 = 1/9
+            r8 += as * T(3) * g[4];
+            r9 += as * T(3) * g[5];
+#pragma unroll
+            for (int k = 10; k < 19; ++k) gk[k - 10] = sqrt(t3 / (T)lb_ghost_norm(k)) * g[k - 4];
+        }
         // Sigma of Eq. 14
         const T uf = ux * fx + uy * fy + uz * fz;
         const T a1 = T(0.5) * (T(1) + gs), a2 = (T(1) + gb) * third;
@@ -523,6 +578,13 @@ __global__ void __launch_bounds__(kFlatThreads, sizeof(T) == 4 ? 3 : 2) k_lb(con
             if (cx && cy) v += (cx == cy) ? Dxy : -Dxy;
             if (cx && cz) v += (cx == cz) ? Dxz : -Dxz;
             if (cy && cz) v += (cy == cz) ? Dyz : -Dyz;
+            if constexpr (NOISE) {
+#pragma unroll
+                for (int k = 10; k < 19; ++k) {
+                    const int e = lb_ghost(k, cx, cy, cz);
+                    if (e) v += T(e) * gk[k - 10];
+                }
+            }
             dst[(size_t)i * V + site] = lbw<T>(i) * v;
         }
     }
@@ -602,9 +664,16 @@ __device__ __forceinline__ Nb neighbours(int i, int nx, int ny, int nz) {
 // Explicit part: rhs_I = -sum_axes [F(i+1/2) - F(i-1/2)] + dt M L(phi; mu^n).  Also stores
 // 1/max(phi_I, floor) for the Jacobi sweeps in the Boltzmann-factor buffer, which is free from
 // the end of the inversion to the start of the next one.
-template <typename T>
-__global__ void __launch_bounds__(kFlatThreads, sizeof(T) == 4 ? 4 : 1) k_cd_rhs(const Rep* __restrict__ reps, const int* __restrict__ blk2rep) {
+// NOISE: the composition noise of Eq. 5 joins the explicit part: minus the divergence of a random
+// flux on every face, J_a(r) = sqrt(2 M dt / Omega * max(phi_face, 0)) n_a(r), n_a(r) the a-th
+// normal of counter (r, step, 1 + I, replica); the step index is the device step counter (the
+// step-end kernel of this step has already advanced it).
+template <typename T, bool NOISE>
+__global__ void __launch_bounds__(kFlatThreads, sizeof(T) == 4 ? (NOISE ? 2 : 4) : 1) k_cd_rhs(const Rep* __restrict__ reps, const int* __restrict__ blk2rep,
+                                                                        const int* __restrict__ counter) {
     FLAT_PROLOGUE
+    const unsigned nstep = NOISE ? (unsigned)(*counter - 1) : 0u;
+    const T amp2 = (T)R.noise_amp2;
     const T* phi = (const T*)R.phi;
     const T* mu = (const T*)R.mu;
     const T* u = (const T*)R.u;
@@ -643,6 +712,12 @@ __global__ void __launch_bounds__(kFlatThreads, sizeof(T) == 4 ? 4 : 1) k_cd_rhs
                     float pc[4], mc[4], conv[4] = {0.f, 0.f, 0.f, 0.f}, lap[4] = {0.f, 0.f, 0.f, 0.f};
                     arr(pc4, pc);
                     arr(mc4, mc);
+                    float nown[4][4], noise[4] = {0.f, 0.f, 0.f, 0.f};
+                    if constexpr (NOISE)
+#pragma unroll
+                        for (int q = 0; q < 4; ++q)
+                            normals4<float>(R.noise_seed, (unsigned)(i + q), nstep, 1u + (unsigned)I, (unsigned)R.rep_index,
+                                            nown[q]);
                     // axis by axis: Courant numbers at the site and its two neighbours, phi and mu
                     // at the neighbours
 #pragma unroll
@@ -680,11 +755,33 @@ __global__ void __launch_bounds__(kFlatThreads, sizeof(T) == 4 ? 4 : 1) k_cd_rhs
                             conv[q] += Fp - Fm;
                             lap[q] += 0.5f * (pc[q] + pp[q]) * (mp[q] - mc[q]) + 0.5f * (pc[q] + pm[q]) * (mm[q] - mc[q]);
                         }
+                        if constexpr (NOISE) {
+                            // flux through the lower face comes from the neighbour's normals
+                            float nlo[4];
+                            if (d == 0) {
+                                nlo[0] = __shfl_sync(0xffffffffu, nown[3][0], lm);
+                                nlo[1] = nown[0][0];
+                                nlo[2] = nown[1][0];
+                                nlo[3] = nown[2][0];
+                            } else {
+#pragma unroll
+                                for (int q = 0; q < 4; ++q) {
+                                    float g[4];
+                                    normals4<float>(R.noise_seed, (unsigned)(nm_[d] + q), nstep, 1u + (unsigned)I,
+                                                    (unsigned)R.rep_index, g);
+                                    nlo[q] = g[d];
+                                }
+                            }
+#pragma unroll
+                            for (int q = 0; q < 4; ++q)
+                                noise[q] += sqrtf((float)amp2 * fmaxf(0.5f * (pm[q] + pc[q]), 0.f)) * nlo[q] -
+                                            sqrtf((float)amp2 * fmaxf(0.5f * (pc[q] + pp[q]), 0.f)) * nown[q][d];
+                        }
                     }
                     float4 ro, io;
 #pragma unroll
                     for (int q = 0; q < 4; ++q) {
-                        (&ro.x)[q] = -conv[q] + (float)dtM * lap[q];
+                        (&ro.x)[q] = -conv[q] + (float)dtM * lap[q] + noise[q];
                         (&io.x)[q] = 1.f / (pc[q] < (float)fl ? (float)fl : pc[q]);
                     }
                     *(float4*)((float*)rhs + (size_t)I * V + i) = ro;
@@ -711,7 +808,10 @@ __global__ void __launch_bounds__(kFlatThreads, sizeof(T) == 4 ? 4 : 1) k_cd_rhs
             const T* ph = phi + (size_t)I * V;
             const T* m = mu + (size_t)I * V;
             const T pc = ph[i], mc = m[i];
-            T conv = 0, lap = 0;
+            T conv = 0, lap = 0, noise = 0;
+            T nown[4];
+            if constexpr (NOISE)
+                normals4<T>(R.noise_seed, (unsigned)i, nstep, 1u + (unsigned)I, (unsigned)R.rep_index, nown);
 #pragma unroll
             for (int d = 0; d < 3; ++d) {
                 const int ip = b.n[2 * d], im = b.n[2 * d + 1];
@@ -722,8 +822,14 @@ __global__ void __launch_bounds__(kFlatThreads, sizeof(T) == 4 ? 4 : 1) k_cd_rhs
                 const T Fm = T(0.5) * (Cm[d] + Ci[d]) * hm;
                 conv += Fp - Fm;
                 lap += T(0.5) * (pc + pp) * (m[ip] - mc) + T(0.5) * (pc + pm) * (m[im] - mc);
+                if constexpr (NOISE) {
+                    T g[4];
+                    normals4<T>(R.noise_seed, (unsigned)im, nstep, 1u + (unsigned)I, (unsigned)R.rep_index, g);
+                    noise += sqrt(amp2 * fmax(T(0.5) * (pm + pc), T(0))) * g[d] -
+                             sqrt(amp2 * fmax(T(0.5) * (pc + pp), T(0))) * nown[d];
+                }
             }
-            rhs[(size_t)I * V + i] = -conv + dtM * lap;
+            rhs[(size_t)I * V + i] = -conv + dtM * lap + noise;
             inv[(size_t)I * V + i] = T(1) / (pc < fl ? fl : pc);
         }
     }
@@ -1191,11 +1297,13 @@ void launch_mu(const Launch& L, int K) {
 }
 template <typename T>
 void launch_lb(const Launch& L, const void* fext) {
-    k_lb<T><<<L.nlb_total, kFlatThreads, 0, L.stream>>>(L.reps, L.nrep, L.counter, (const T*)fext);
+    if (L.noise & 2) k_lb<T, true><<<L.nlb_total, kFlatThreads, 0, L.stream>>>(L.reps, L.nrep, L.counter, (const T*)fext);
+    else k_lb<T, false><<<L.nlb_total, kFlatThreads, 0, L.stream>>>(L.reps, L.nrep, L.counter, (const T*)fext);
 }
 template <typename T>
 void launch_cd(const Launch& L, int sweeps) {
-    k_cd_rhs<T><<<L.nblk_total, kFlatThreads, 0, L.stream>>>(L.reps, L.blk2rep);
+    if (L.noise & 1) k_cd_rhs<T, true><<<L.nblk_total, kFlatThreads, 0, L.stream>>>(L.reps, L.blk2rep, L.counter);
+    else k_cd_rhs<T, false><<<L.nblk_total, kFlatThreads, 0, L.stream>>>(L.reps, L.blk2rep, L.counter);
     for (int k = 0; k < sweeps; ++k) k_cd_jacobi<T><<<L.nblk_total, kFlatThreads, 0, L.stream>>>(L.reps, L.blk2rep, k);
     k_cd_finish<T><<<L.nblk_total, kFlatThreads, 0, L.stream>>>(L.reps, L.blk2rep, sweeps);
     k_mass_fix<T><<<L.nblk_total, kFlatThreads, 0, L.stream>>>(L.reps, L.blk2rep, L.status);

@@ -90,6 +90,7 @@ def load():
         "dscf_set_predictor": (ctypes.c_int, [vp, vp, i32, ctypes.c_double, i32]),
         "dscf_set_wait_limit": (ctypes.c_int, [vp, i32]),
         "dscf_set_inversion_tol": (ctypes.c_int, [vp, ctypes.c_double]),
+        "dscf_set_noise": (ctypes.c_int, [vp, ctypes.c_double, i32, ctypes.c_uint64]),
         "dscf_observables": (ctypes.c_int, [vp, i32, ctypes.POINTER(ctypes.c_double)]),
         "dscf_net_set_tensor_path": (ctypes.c_int, [vp, i32]),
         "dscf_net_tensor_path": (i32, [vp]),
@@ -316,6 +317,10 @@ class Context:
     def inject_lag(self, brick):
         """Test hook: make brick's step counter lag so the next persistent sweep times out."""
         self._check(self.lib.dscf_inject_lag(self.h, int(brick)))
+
+    def set_noise(self, omega, lb_noise=True, seed=0):
+        """Thermal noise with noise parameter Omega (0: off); lb_noise also the LB modes."""
+        self._check(self.lib.dscf_set_noise(self.h, float(omega), int(bool(lb_noise)), int(seed)))
 
     def set_inversion_tol(self, tol):
         """Residual stop of the inversion: at most ncg_iters iterations, fewer once max|phi* - phi[U]|

@@ -381,6 +381,50 @@ def test_step_fp32_row_kernels_within_tolerance(cfg):
         assert rel(g[k], o[k]) < 1e-5, (k, rel(g[k], o[k]))
 
 
+NOISE_CASES = [
+    (melt((20, 12, 16), 6, 3, hydro=1, ncg_iters=2, cn_sweeps=4), dscf.FP64),
+    (melt((20, 12, 16), 6, 3, hydro=0, ncg_iters=2, cn_sweeps=4), dscf.FP64),
+    (solution((18, 10, 14), 5, 2, hydro=1, ncg_iters=2, cn_sweeps=4), dscf.FP64),
+    (melt((128, 8, 6), 6, 3, hydro=1, ncg_iters=2, cn_sweeps=4), dscf.FP32),
+    (solution((128, 6, 4), 5, 2, hydro=1, ncg_iters=2, cn_sweeps=4), dscf.FP32),
+    (melt((20, 12, 16), 6, 3, hydro=1, ncg_iters=2, cn_sweeps=4), dscf.FP32),
+]
+
+
+@pytest.mark.parametrize("cfg,prec", NOISE_CASES,
+                         ids=lambda v: "x".join(map(str, v["grid"])) + f"_ns{v['ns']}_h{v['hydro']}" if isinstance(v, dict) else ("fp64" if v == dscf.FP64 else "fp32"))
+def test_thermal_noise_step_matches_oracle(cfg, prec):
+    """Steps with thermal noise (Eq. 5 compositions, Eq. 13 LB modes, Omega = 100) against the
+    oracle drawing the same Philox normals: FP64 within 1e-10, FP32 within 1e-5, three steps;
+    the noise changes the result and keeps every species' mass."""
+    seed, omega = 0x1234_5678_9ABC, 100.0
+    phi, U, dn = random_state(cfg, 97)
+    ctx = dscf.Context(cfg, prec)
+    ctx.set_noise(omega, lb_noise=True, seed=seed)
+    ctx.set(dscf.PHI, torch.from_numpy(phi).cuda())
+    ctx.set(dscf.U, torch.from_numpy(U).cuda())
+    ctx.set(dscf.POP, torch.from_numpy(dn).cuda())
+    _, w, _, _ = oracle.lb_basis()
+    oph, oU, opop = phi, U, dn + w[:, None, None, None]
+    m0 = phi.reshape(phi.shape[0], -1).sum(1)
+    tol = 1e-10 if prec == dscf.FP64 else 1e-5
+    for step in range(3):
+        ctx.step(1)
+        ctx.status()
+        ocfg = dict(cfg, omega=omega, lb_noise=1, noise_seed=seed, noise_step=step)
+        st = oracle.step(ocfg, oph, oU, opop, m0)
+        oph, oU, opop = st["phi"], st["U"], st["pop"]
+        assert rel(t2n(ctx.get(dscf.PHI)), oph) < tol, step
+        assert rel(t2n(ctx.get(dscf.U)), oU) < tol, step
+        if cfg["hydro"]:
+            assert rel(t2n(ctx.get(dscf.POP)), opop - w[:, None, None, None]) < tol, step
+    got = t2n(ctx.get(dscf.PHI))
+    mtol = 1e-9 if prec == dscf.FP64 else 1e-6   # FP32 storage of the fields
+    assert np.abs(got.reshape(phi.shape[0], -1).sum(1) - m0).max() < mtol * m0.max()
+    quiet = run_oracle(cfg, phi, U, dn, 3)
+    assert rel(got, quiet["phi"]) > 10 * tol   # the noise is there
+
+
 def test_step_fp32_within_tolerance():
     cfg = STEP_CASES[0]
     phi, U, dn = random_state(cfg, 51)
