@@ -40,7 +40,7 @@ def args_():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-forms", action="store_true", help="skip the FP64, learned and batched forms")
-    ap.add_argument("--forms", default="fp64,fp32_residual_stop,fp32_learned,batch48", help="comma-separated forms to report")
+    ap.add_argument("--forms", default="fp64,fp32_noise,fp32_residual_stop,fp32_learned,batch48", help="comma-separated forms to report")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=20.0, help="seconds of oracle work for cpu_baseline")
     return ap.parse_args()
@@ -322,6 +322,23 @@ def residual_stop_form(cfg, dev, phi0, timed, world, steps):
     return out
 
 
+def noise_form(cfg, dev, phi0, timed, world, steps):
+    """The FP32 step with thermal noise (Omega = 400 as in the paper's runs): the composition flux
+    noise of Eq. 5 and the fluctuating LB collision of Eq. 13."""
+    from paper_1204_2088_gb300 import dscf, replicas
+    V = int(cfg["grid"][0] * cfg["grid"][1] * cfg["grid"][2])
+    ctx = dscf.Context(cfg, dscf.FP32, device=dev)
+    ctx.set_noise(400.0, lb_noise=True, seed=2012)
+    ctx.set(dscf.PHI, phi0)
+    ctx.step(3)
+    ms = timed(lambda: ctx.step(steps))
+    ctx.status()
+    d = ctx.diagnostics()
+    ctx.close()
+    return {"value": replicas.aggregate_rate([V * steps] * world, [ms]), "unit": UNIT, "ms_per_step": ms / steps,
+            "steps": steps, "omega": 400.0, "lb_noise": True, "lb_momentum": d["lb_momentum"]}
+
+
 def batch48_form(dev, timed, rank, world, steps):
     """The 48 mixed-size melts (24 x 48^3, 16 x 64^3, 8 x 96^3) in one FP32 context per rank
     (the replicas split across ranks by site count), one captured graph per step."""
@@ -451,6 +468,8 @@ def run_ours(a):
                          "lb_ms": lb64}
         c64.close()
         del c64
+    if "fp32_noise" in want:
+        forms["fp32_noise"] = noise_form(cfg, dev, phi0, timed, world, max(10, min(a.steps, 20)))
     if "fp32_residual_stop" in want:
         forms["fp32_residual_stop"] = residual_stop_form(cfg, dev, phi0, timed, world, max(10, min(a.steps, 20)))
     if "fp32_learned" in want:

@@ -188,3 +188,32 @@ def test_melt256_learned_predictor_runs_on_tcgen05():
         assert np.abs(phi.reshape(2, -1).sum(1) - m0).max() < 1e-6 * m0.max()
         assert np.isfinite(phi).all()
         ctx.close()
+
+
+def test_melt128_with_thermal_noise_full_size():
+    """The bench workload with thermal noise at the paper's Omega = 400 (compositions and LB
+    modes): steps keep each species' mass and the LB mass, and the fields stay finite and near
+    the quiet run (the noise's exact conservation of mass and momentum per site is pinned in the
+    oracle and checked against it on smaller grids)."""
+    cfg = inputs.workload("melt128")
+    nx, ny, nz = cfg["grid"]
+    phi0 = inputs.initial_fields(cfg)
+    outs = []
+    for omega in (0.0, 400.0):
+        ctx = dscf.Context(cfg, dscf.FP32, tuning=(16, 0))
+        ctx.set_noise(omega, lb_noise=True, seed=77)
+        ctx.set(dscf.PHI, torch.from_numpy(phi0).float().cuda())
+        ctx.step(3)
+        ctx.status()
+        d = ctx.diagnostics()
+        phi = t2n(ctx.get(dscf.PHI))
+        m0 = phi0.astype(np.float32).astype(np.float64).reshape(2, -1).sum(1)
+        assert np.abs(phi.reshape(2, -1).sum(1) - m0).max() < 1e-6 * m0.max()
+        assert abs(d["lb_mass"] - nx * ny * nz) < 1e-6 * nx * ny * nz
+        assert np.isfinite(phi).all()
+        outs.append(phi)
+        ctx.close()
+    # present, and of the expected size: per step the increment has standard deviation
+    # sqrt(12 M phi dt / Omega) = 0.04-0.07 here, partly smoothed by the implicit diffusion
+    diff = outs[1] - outs[0]
+    assert 0.01 < diff.std() < 0.2 and np.abs(diff).max() < 1.0
