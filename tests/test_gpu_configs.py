@@ -217,3 +217,15 @@ def test_melt128_with_thermal_noise_full_size():
     # sqrt(12 M phi dt / Omega) = 0.04-0.07 here, partly smoothed by the implicit diffusion
     diff = outs[1] - outs[0]
     assert 0.01 < diff.std() < 0.2 and np.abs(diff).max() < 1.0
+
+
+def test_quench_driver_records_ordering():
+    """The ordering-run driver: records every `every` steps with finite F, S and segregation;
+    the symmetric melt quenched to chi N = 16 starts to order (S grows), with and without
+    hydrodynamics."""
+    from paper_1204_2088_gb300 import quench
+    for hydro in (0, 1):
+        recs = list(quench.run("A8B8", 16, 2000, 1000, 1, hydro))   # 200 tau
+        assert [r["step"] for r in recs] == [0, 1000, 2000]
+        assert all("error" not in r and np.isfinite([r["F"], r["S"], r["segregation"]]).all() for r in recs)
+        assert recs[-1]["S"] > 10 * recs[0]["S"] and recs[-1]["F"] < recs[0]["F"]
