@@ -64,6 +64,8 @@ def lib():
                                      ctypes.POINTER(ctypes.c_uint32)]),
             "or_normals4": (None, [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, D]),
             "or_cd_noise": (None, [P, D, D]),
+            "or_minkowski_counts": (None, [ctypes.c_int, ctypes.c_int, ctypes.c_int, D, ctypes.c_double,
+                                           ctypes.POINTER(ctypes.c_int64)]),
             "or_mu": (None, [P, D, D, D]),
             "or_force": (None, [P, D, D, D]),
             "or_lb_basis": (None, [D, D, D, ctypes.POINTER(ctypes.c_int)]),
@@ -204,6 +206,21 @@ def cd_noise(cfg: dict, phi: np.ndarray) -> np.ndarray:
     out = np.empty_like(_f64(phi))
     lib().or_cd_noise(ctypes.byref(p), _ptr(_f64(phi)), _ptr(out))
     return out
+
+
+def minkowski_counts(field: np.ndarray, threshold: float):
+    """(n_c, n_f, n_e, n_v) of the union of cubes where field > threshold; field [nz, ny, nx]."""
+    f = _f64(field)
+    nz, ny, nx = f.shape
+    out = (ctypes.c_int64 * 4)()
+    lib().or_minkowski_counts(nx, ny, nz, _ptr(f), threshold, out)
+    return tuple(out)
+
+
+def minkowski(field: np.ndarray, threshold: float) -> dict:
+    """Volume, surface, 2 x integral mean curvature and Euler characteristic (voxel union)."""
+    nc, nf, ne, nv = minkowski_counts(field, threshold)
+    return {"V": nc, "S": -6 * nc + 2 * nf, "B2": 3 * nc - 2 * nf + ne, "chi": -nc + nf - ne + nv}
 
 
 def mu(cfg: dict, U: np.ndarray, phi: np.ndarray) -> np.ndarray:

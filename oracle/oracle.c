@@ -683,6 +683,52 @@ void or_step(const or_params* p, double* phi, double* U, double* pop, const doub
 }
 
 /* ------------------------------------------------------------------------------------ */
+/* Minkowski functionals of a thresholded field (Sec. 3, morphology of the aggregates;    */
+/* the algorithm of Michielsen and De Raedt for a union of lattice cubes).  The body is   */
+/* the union of the closed unit cubes at the sites where field > threshold (periodic      */
+/* box).  Counting the distinct cubes n_c, faces n_f, edges n_e and vertices n_v of that   */
+/* union,                                                                                  */
+/*   V = n_c,  S = -6 n_c + 2 n_f,  2B = 3 n_c - 2 n_f + n_e,  chi = -n_c + n_f - n_e + n_v */
+/* (volume, surface area, twice the integral mean curvature over pi in the lattice        */
+/* normalisation, Euler characteristic of the body; a closed surface's own Euler number is */
+/* 2 chi).  A face, edge or vertex belongs to the union when one of the 2, 4 or 8 cubes    */
+/* that share it does; each is identified by the lattice point at its lower corner and an  */
+/* orientation.  counts = {n_c, n_f, n_e, n_v}.                                           */
+/* ------------------------------------------------------------------------------------ */
+void or_minkowski_counts(int nx, int ny, int nz, const double* field, double threshold, int64_t counts[4]) {
+    or_params p;
+    memset(&p, 0, sizeof p);
+    p.nx = nx; p.ny = ny; p.nz = nz;
+    int64_t nc = 0, nf = 0, ne = 0, nv = 0;
+    for (int z = 0; z < nz; ++z)
+        for (int y = 0; y < ny; ++y)
+            for (int x = 0; x < nx; ++x) {
+                /* in[dx][dy][dz]: the cube at (x - dx, y - dy, z - dz) is in the body */
+                int in[2][2][2];
+                for (int dx = 0; dx < 2; ++dx)
+                    for (int dy = 0; dy < 2; ++dy)
+                        for (int dz = 0; dz < 2; ++dz)
+                            in[dx][dy][dz] = field[sidx(&p, x - dx, y - dy, z - dz)] > threshold;
+                nc += in[0][0][0];
+                /* faces at this lattice point, normal to x, y, z: shared with the cube below */
+                nf += in[0][0][0] || in[1][0][0];
+                nf += in[0][0][0] || in[0][1][0];
+                nf += in[0][0][0] || in[0][0][1];
+                /* edges from this lattice point along z, y, x: the four cubes around each */
+                ne += in[0][0][0] || in[1][0][0] || in[0][1][0] || in[1][1][0];
+                ne += in[0][0][0] || in[1][0][0] || in[0][0][1] || in[1][0][1];
+                ne += in[0][0][0] || in[0][1][0] || in[0][0][1] || in[0][1][1];
+                /* the vertex at this lattice point: the eight cubes around it */
+                int any = 0;
+                for (int dx = 0; dx < 2; ++dx)
+                    for (int dy = 0; dy < 2; ++dy)
+                        for (int dz = 0; dz < 2; ++dz) any |= in[dx][dy][dz];
+                nv += any;
+            }
+    counts[0] = nc; counts[1] = nf; counts[2] = ne; counts[3] = nv;
+}
+
+/* ------------------------------------------------------------------------------------ */
 /* Diagnostics.                                                                          */
 /* Free-energy density v0 F/(k_B T V) of Eq. 1 in volume fractions (constants ln n!,      */
 /* ln V and Omega dropped):                                                               */

@@ -743,3 +743,54 @@ def test_lb_noise_conserves_and_has_the_mode_variances():
         expect = kT * b[k] * (1 - gam[k - 4] ** 2) * 3.0
         assert abs(m[k].var() / expect - 1.0) < 0.06, k
         assert abs(m[k].mean()) < 4 * np.sqrt(expect / m[k].size)
+
+
+# ---------------------------------------------------------------------------------------------
+# Minkowski functionals of a thresholded field (Sec. 3; Michielsen-De Raedt voxel counting)
+# ---------------------------------------------------------------------------------------------
+def _body(shape, cells):
+    g = np.zeros(shape)
+    for c in cells:
+        g[c] = 1.0
+    return g
+
+
+def test_minkowski_closed_forms():
+    """Volume, area, mean-breadth term and Euler characteristic of bodies whose values are known:
+    a unit cube (1, 6, 3, 1), two disjoint cubes (additive), a 3^3 cube with a central cavity
+    (a hollow ball: chi = 2; area 54 outside + 6 inside), a ring (solid torus: chi = 0), a rod
+    closing on itself through the periodic box (chi = 0), the filled box (a 3-torus: 0, no
+    surface), cubes touching at a corner (one connected closed body: chi = 1)."""
+    cube = oracle.minkowski(_body((8, 8, 8), [(3, 3, 3)]), 0.5)
+    assert cube == {"V": 1, "S": 6, "B2": 3, "chi": 1}
+    two = oracle.minkowski(_body((8, 8, 8), [(1, 1, 1), (5, 5, 5)]), 0.5)
+    assert two == {"V": 2, "S": 12, "B2": 6, "chi": 2}
+    g = np.zeros((9, 9, 9))
+    g[2:5, 2:5, 2:5] = 1.0
+    g[3, 3, 3] = 0.0
+    shell = oracle.minkowski(g, 0.5)
+    assert shell["V"] == 26 and shell["S"] == 60 and shell["chi"] == 2
+    ring = np.zeros((8, 8, 8))
+    ring[3, 2:5, 2:5] = 1.0
+    ring[3, 3, 3] = 0.0
+    assert oracle.minkowski(ring, 0.5)["chi"] == 0
+    rod = np.zeros((8, 8, 8))
+    rod[:, 3, 3] = 1.0
+    assert oracle.minkowski(rod, 0.5) == {"V": 8, "S": 32, "B2": 8, "chi": 0}
+    assert oracle.minkowski(np.ones((6, 6, 6)), 0.5) == {"V": 216, "S": 0, "B2": 0, "chi": 0}
+    assert oracle.minkowski(_body((8, 8, 8), [(3, 3, 3), (4, 4, 4)]), 0.5)["chi"] == 1
+
+
+def test_minkowski_invariances():
+    """A random body: the counts do not change under periodic translation or under axis
+    permutations, the threshold is strict, and a scaled copy scales V by 8 and S by 4."""
+    rng = np.random.default_rng(5)
+    f = rng.random((10, 12, 14))
+    c0 = oracle.minkowski_counts(f, 0.6)
+    assert oracle.minkowski_counts(np.roll(f, (3, -5, 7), axis=(0, 1, 2)), 0.6) == c0
+    assert oracle.minkowski_counts(np.ascontiguousarray(f.transpose(2, 0, 1)), 0.6) == c0
+    assert oracle.minkowski_counts(np.full((4, 4, 4), 0.6), 0.6)[0] == 0
+    b = (rng.random((5, 6, 7)) > 0.7).astype(float)
+    big = np.kron(b, np.ones((2, 2, 2)))
+    m1, m2 = oracle.minkowski(b, 0.5), oracle.minkowski(big, 0.5)
+    assert m2["V"] == 8 * m1["V"] and m2["S"] == 4 * m1["S"] and m2["chi"] == m1["chi"]
