@@ -177,6 +177,15 @@ int dscf_diagnostics(dscf_ctx* ctx, int32_t replica, double* out);
  * partials in a fixed order.  Runs one density evaluation and synchronises the stream. */
 int dscf_observables(dscf_ctx* ctx, int32_t replica, double* out);
 
+/* Minkowski functionals of the morphology (Sec. 3, the algorithm of Michielsen and De Raedt): the
+ * body is the union of the closed unit cubes of the sites where phi_species > threshold (compared
+ * in the context precision; periodic box).  counts[0..3] (host memory) receive its numbers of
+ * distinct cubes n_c, faces n_f, edges n_e and vertices n_v, from which V = n_c,
+ * S = -6 n_c + 2 n_f, 2B = 3 n_c - 2 n_f + n_e and chi = -n_c + n_f - n_e + n_v (the Euler
+ * number of the bounding surfaces, the paper's convention, is 2 chi).  Integer counts, exact.
+ * Synchronises.  DSCF_ERR_ARG for a bad replica, species or threshold. */
+int dscf_minkowski(dscf_ctx* ctx, int32_t replica, int32_t species, double threshold, int64_t* counts);
+
 int dscf_status(dscf_ctx* ctx);
 
 /* Release host-side state (graph, capture stream).  The workspace stays the caller's. */

@@ -997,6 +997,32 @@ int dscf_observables(dscf_ctx* c, int32_t replica, double* out) {
     return DSCF_OK;
 }
 
+int dscf_minkowski(dscf_ctx* c, int32_t replica, int32_t species, double threshold, int64_t* counts) {
+    if (!c || !counts) return c ? fail(c, DSCF_ERR_ARG, "NULL output") : DSCF_ERR_ARG;
+    if (replica < 0 || replica >= c->nrep) return fail(c, DSCF_ERR_ARG, "replica out of range");
+    const Rep& R = c->L.reps[replica];
+    if (species < 0 || species >= R.ns) return fail(c, DSCF_ERR_ARG, "species out of range");
+    if (!std::isfinite(threshold)) return fail(c, DSCF_ERR_ARG, "threshold must be finite");
+    if (int rc = set_dev(c)) return rc;
+    const Launch L = launch_of(c, c->stream);
+    if (c->prec == DSCF_FP64) launch_minkowski<double>(L, replica, species, threshold);
+    else launch_minkowski<float>(L, replica, species, threshold);
+    const int nb = R.nblk;
+    std::vector<double> h((size_t)4 * nb);
+    int rc = cuda_check(c, cudaGetLastError(), "minkowski");
+    for (int k = 0; k < 4 && !rc; ++k)
+        rc = cuda_check(c, cudaMemcpyAsync(h.data() + (size_t)k * nb, R.part + (size_t)(P_OBS0 + k) * R.part_stride,
+                                           sizeof(double) * nb, cudaMemcpyDeviceToHost, c->stream), "minkowski");
+    if (!rc) rc = cuda_check(c, cudaStreamSynchronize(c->stream), "minkowski sync");
+    if (rc) return rc;
+    for (int k = 0; k < 4; ++k) {
+        long long s = 0;
+        for (int b = 0; b < nb; ++b) s += (long long)h[(size_t)k * nb + b];
+        counts[k] = s;
+    }
+    return DSCF_OK;
+}
+
 int dscf_diagnostics(dscf_ctx* c, int32_t replica, double* out) {
     if (!c || !out || replica < 0 || replica >= c->nrep) return c ? fail(c, DSCF_ERR_ARG, "bad replica") : DSCF_ERR_ARG;
     if (int rc = set_dev(c)) return rc;

@@ -314,6 +314,8 @@ template <typename T>
 void launch_obs1(const Launch& L);
 template <typename T>
 void launch_obs2(const Launch& L, double mA, double mB, double mS);
+// per-block counts of cubes, faces, edges, vertices of {phi_species > threshold} into P_OBS0..3
+template <typename T> void launch_minkowski(const Launch& L, int replica, int species, double threshold);
 // mode 0: init (d = -g), mode 1: iteration k direction update
 template <typename T> void launch_dir(const Launch& L, int mode, int k);
 template <typename T> void launch_mu(const Launch& L, int K);   // K < 0: iterations from scal[S_NITER]

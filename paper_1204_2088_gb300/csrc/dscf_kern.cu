@@ -1251,6 +1251,56 @@ template void launch_obs1<double>(const Launch&);
 template void launch_obs2<float>(const Launch&, double, double, double);
 template void launch_obs2<double>(const Launch&, double, double, double);
 
+// Minkowski functionals of species I of one replica at a threshold: the body is the union of the
+// closed unit cubes of the sites where phi_I > threshold (compared in the field's precision).  Per
+// lattice point the kernel counts its cube, the three faces, three edges and the vertex whose lower
+// corner it is, each present when one of the 2, 4 or 8 cubes sharing it is in the body; per-block
+// integer counts go to partial slots P_OBS0..3 (exact in FP64).
+template <typename T>
+__global__ void __launch_bounds__(kFlatThreads) k_minkowski(const Rep* __restrict__ reps, const int* __restrict__ blk2rep,
+                                                            int replica, int species, T threshold) {
+    __shared__ double sh[4 * 33];
+    const Rep& R = reps[blk2rep[blockIdx.x]];
+    if (R.rep_index != replica) return;
+    const int lb = blockIdx.x - R.blk0;
+    const int V = (int)R.V;
+    const int i0 = lb * R.chunk, i1 = min(i0 + R.chunk, V);
+    const int nx = R.nx, ny = R.ny, nz = R.nz;
+    const T* f = (const T*)R.phi + (size_t)species * V;
+    long long nc = 0, nf = 0, ne = 0, nv = 0;
+    for (int i = i0 + threadIdx.x; i < i1; i += kFlatThreads) {
+        int x, y, z;
+        site_xyz(i, nx, ny, x, y, z);
+        const int xm = x == 0 ? nx - 1 : x - 1, ym = y == 0 ? ny - 1 : y - 1, zm = z == 0 ? nz - 1 : z - 1;
+        const int X[2] = {x, xm}, Y[2] = {y, ym}, Z[2] = {z, zm};
+        bool in[2][2][2];   // the cube at (x - dx, y - dy, z - dz)
+#pragma unroll
+        for (int dx = 0; dx < 2; ++dx)
+#pragma unroll
+            for (int dy = 0; dy < 2; ++dy)
+#pragma unroll
+                for (int dz = 0; dz < 2; ++dz) in[dx][dy][dz] = f[X[dx] + nx * (Y[dy] + ny * Z[dz])] > threshold;
+        nc += in[0][0][0];
+        nf += (in[0][0][0] | in[1][0][0]) + (in[0][0][0] | in[0][1][0]) + (in[0][0][0] | in[0][0][1]);
+        ne += (in[0][0][0] | in[1][0][0] | in[0][1][0] | in[1][1][0]) +
+              (in[0][0][0] | in[1][0][0] | in[0][0][1] | in[1][0][1]) +
+              (in[0][0][0] | in[0][1][0] | in[0][0][1] | in[0][1][1]);
+        nv += in[0][0][0] | in[1][0][0] | in[0][1][0] | in[1][1][0] | in[0][0][1] | in[1][0][1] | in[0][1][1] |
+              in[1][1][1];
+    }
+    double t[4] = {(double)nc, (double)nf, (double)ne, (double)nv};
+    block_sum_n<4>(t, sh);
+    if (threadIdx.x == 0)
+        for (int k = 0; k < 4; ++k) slot(R, P_OBS0 + k)[lb] = t[k];
+}
+
+template <typename T>
+void launch_minkowski(const Launch& L, int replica, int species, double threshold) {
+    k_minkowski<T><<<L.nblk_total, kFlatThreads, 0, L.stream>>>(L.reps, L.blk2rep, replica, species, (T)threshold);
+}
+template void launch_minkowski<float>(const Launch&, int, int, double);
+template void launch_minkowski<double>(const Launch&, int, int, double);
+
 // One block.  Every replica's residual is reduced in the same fixed order as the kernels that
 // record it, so the decision is reproducible; a non-finite residual closes the gate.
 // A non-finite <g,g> closes the gate and sets the non-finite status bit.

@@ -91,6 +91,7 @@ def load():
         "dscf_set_wait_limit": (ctypes.c_int, [vp, i32]),
         "dscf_set_inversion_tol": (ctypes.c_int, [vp, ctypes.c_double]),
         "dscf_set_noise": (ctypes.c_int, [vp, ctypes.c_double, i32, ctypes.c_uint64]),
+        "dscf_minkowski": (ctypes.c_int, [vp, i32, i32, ctypes.c_double, ctypes.POINTER(ctypes.c_int64)]),
         "dscf_observables": (ctypes.c_int, [vp, i32, ctypes.POINTER(ctypes.c_double)]),
         "dscf_net_set_tensor_path": (ctypes.c_int, [vp, i32]),
         "dscf_net_tensor_path": (i32, [vp]),
@@ -302,6 +303,17 @@ class Context:
         out = (ctypes.c_double * 3)()
         self._check(self.lib.dscf_observables(self.h, int(replica), out))
         return {"free_energy": out[0], "order_parameter": out[1], "segregation": out[2]}
+
+    def minkowski_counts(self, species, threshold=0.2, replica=0):
+        """(n_c, n_f, n_e, n_v) of the body {phi_species > threshold}."""
+        out = (ctypes.c_int64 * 4)()
+        self._check(self.lib.dscf_minkowski(self.h, int(replica), int(species), float(threshold), out))
+        return tuple(out)
+
+    def minkowski(self, species, threshold=0.2, replica=0):
+        """Volume, surface, 2 x integral mean curvature (lattice units) and Euler characteristic."""
+        nc, nf, ne, nv = self.minkowski_counts(species, threshold, replica)
+        return {"V": nc, "S": -6 * nc + 2 * nf, "B2": 3 * nc - 2 * nf + ne, "chi": -nc + nf - ne + nv}
 
     def set_predictor(self, net, corrector_every=10, tol=1e-3, ncg_iters=0):
         """Attach a trained Net (same grid, batch 1) as the density map of the inversion, judged

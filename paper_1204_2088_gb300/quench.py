@@ -17,8 +17,9 @@ unstable with hydrodynamics at dt = 0.2 tau even without noise; with noise (Omeg
 the explicit noise step drives the minority composition of a strongly segregated 48^3 box through
 zero within a few thousand steps, where the inversion cannot follow.  A run that breaks down ends
 with an "error" record.
-Every record is one JSON line: system, hydro, seed, step, time (tau), F, S, segregation,
-and the mean milliseconds per step of the segment before it.
+Every record is one JSON line: system, hydro, seed, step, time (tau), F, S, segregation, the
+Minkowski functionals of the B beads at threshold 0.2 (V, S, 2B, chi), and the mean milliseconds
+per step of the segment before it.
 """
 from __future__ import annotations
 
@@ -62,8 +63,9 @@ def run(name: str, grid: int, steps: int, every: int, seed: int, hydro: int, ome
     try:
         while True:
             ob = ctx.observables()
+            mk = ctx.minkowski(1, 0.2)   # the B beads at the paper's threshold
             rec = dict(base, step=done, time=done * cfg["dt"], F=ob["free_energy"], S=ob["order_parameter"],
-                       segregation=ob["segregation"])
+                       segregation=ob["segregation"], minkowski_B=mk)
             if ms is not None:
                 rec["ms_per_step"] = ms
             yield rec

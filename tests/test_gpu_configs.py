@@ -229,3 +229,34 @@ def test_quench_driver_records_ordering():
         assert [r["step"] for r in recs] == [0, 1000, 2000]
         assert all("error" not in r and np.isfinite([r["F"], r["S"], r["segregation"]]).all() for r in recs)
         assert recs[-1]["S"] > 10 * recs[0]["S"] and recs[-1]["F"] < recs[0]["F"]
+
+
+@pytest.mark.parametrize("prec", [dscf.FP64, dscf.FP32], ids=["fp64", "fp32"])
+def test_minkowski_counts_match_oracle(prec):
+    """Cube, face, edge and vertex counts of {phi_I > threshold} are integers: bit-exact against
+    the oracle on the same field (for FP32 the oracle gets the stored float values and the float
+    threshold, so both sides take the same decision), on small grids, in a batch (one replica
+    picked out), and on the 128^3 workload after a few steps at the paper's threshold 0.2."""
+    cfgs = [inputs.melt((20, 12, 16), 6, 0.5, 12.0), inputs.solution((18, 10, 14), 5, 0.3, 0.3, 20.0, 24.0, 3.0)]
+    fields = [inputs.random_field((c["ns"],) + tuple(c["grid"][::-1]), seed=40 + k, scale=0.5) + 0.5
+              for k, c in enumerate(cfgs)]
+    ctx = dscf.Context(cfgs, prec)
+    dt = torch.float64 if prec == dscf.FP64 else torch.float32
+    ctx.set(dscf.PHI, torch.cat([torch.from_numpy(f).to(dt).reshape(-1) for f in fields]).cuda())
+    for r, f in enumerate(fields):
+        stored = f.astype(np.float32).astype(np.float64) if prec == dscf.FP32 else f
+        for I in range(f.shape[0]):
+            for th in (0.2, 0.5, 0.83):
+                t = float(np.float32(th)) if prec == dscf.FP32 else th
+                assert ctx.minkowski_counts(I, th, replica=r) == oracle.minkowski_counts(stored[I], t), (r, I, th)
+    ctx.close()
+    if prec == dscf.FP32:
+        cfg = inputs.workload("melt128")
+        big = dscf.Context(cfg, dscf.FP32, tuning=(16, 0))
+        big.set(dscf.PHI, torch.from_numpy(inputs.initial_fields(cfg)).float().cuda())
+        big.step(5)
+        big.status()
+        phi = t2n(big.get(dscf.PHI))
+        assert big.minkowski_counts(1, 0.2) == oracle.minkowski_counts(phi[1], float(np.float32(0.2)))
+        assert big.minkowski_counts(0, 0.3) == oracle.minkowski_counts(phi[0], float(np.float32(0.3)))
+        big.close()
