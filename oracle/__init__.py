@@ -66,6 +66,8 @@ def lib():
             "or_cd_noise": (None, [P, D, D]),
             "or_minkowski_counts": (None, [ctypes.c_int, ctypes.c_int, ctypes.c_int, D, ctypes.c_double,
                                            ctypes.POINTER(ctypes.c_int64)]),
+            "or_trapped_solvent": (ctypes.c_double, [ctypes.c_int, ctypes.c_int, ctypes.c_int, D, D, ctypes.c_double,
+                                                     ctypes.POINTER(ctypes.c_int64)]),
             "or_mu": (None, [P, D, D, D]),
             "or_force": (None, [P, D, D, D]),
             "or_lb_basis": (None, [D, D, D, ctypes.POINTER(ctypes.c_int)]),
@@ -221,6 +223,15 @@ def minkowski(field: np.ndarray, threshold: float) -> dict:
     """Volume, surface, 2 x integral mean curvature and Euler characteristic (voxel union)."""
     nc, nf, ne, nv = minkowski_counts(field, threshold)
     return {"V": nc, "S": -6 * nc + 2 * nf, "B2": 3 * nc - 2 * nf + ne, "chi": -nc + nf - ne + nv}
+
+
+def trapped_solvent(phiB: np.ndarray, phiS: np.ndarray, threshold: float = 0.2):
+    """(f_trap, number of components of the complement of {phi_B > threshold})."""
+    b, s_ = _f64(phiB), _f64(phiS)
+    nz, ny, nx = b.shape
+    n = ctypes.c_int64()
+    f = lib().or_trapped_solvent(nx, ny, nz, _ptr(b), _ptr(s_), threshold, ctypes.byref(n))
+    return f, n.value
 
 
 def mu(cfg: dict, U: np.ndarray, phi: np.ndarray) -> np.ndarray:

@@ -729,6 +729,56 @@ void or_minkowski_counts(int nx, int ny, int nz, const double* field, double thr
 }
 
 /* ------------------------------------------------------------------------------------ */
+/* Trapped solvent (Sec. 3: the solvent inside the vesicles, interior bulk solvent plus the */
+/* hydration solvent of the inner leaflets, as a fraction of all solvent).  Reading: the   */
+/* aggregates are the body {phi_B > threshold} (the hydrophobic cores, as for the         */
+/* Minkowski functionals); its complement splits into face-connected components of the     */
+/* periodic lattice; the largest is the bulk solvent outside, every other one is enclosed.  */
+/* f_trap = sum of phi_S over the enclosed components / sum of phi_S over the box.         */
+/* Components by breadth-first search; ties for the largest go to the one found first      */
+/* (lowest site index).  Returns f_trap; *ncomp receives the number of complement         */
+/* components.                                                                             */
+/* ------------------------------------------------------------------------------------ */
+double or_trapped_solvent(int nx, int ny, int nz, const double* phiB, const double* phiS, double threshold,
+                          int64_t* ncomp) {
+    or_params p;
+    memset(&p, 0, sizeof p);
+    p.nx = nx; p.ny = ny; p.nz = nz;
+    const int64_t V = (int64_t)nx * ny * nz;
+    int64_t* comp = (int64_t*)malloc(sizeof(int64_t) * (size_t)V);
+    int64_t* queue = (int64_t*)malloc(sizeof(int64_t) * (size_t)V);
+    int64_t nc = 0, best = -1, best_size = -1;
+    for (int64_t i = 0; i < V; ++i) comp[i] = (phiB[i] > threshold) ? -2 : -1;   /* -2 body, -1 unvisited */
+    int64_t* sizes = (int64_t*)malloc(sizeof(int64_t) * (size_t)V);
+    for (int64_t s0 = 0; s0 < V; ++s0) {
+        if (comp[s0] != -1) continue;
+        int64_t head = 0, tail = 0, size = 0;
+        queue[tail++] = s0;
+        comp[s0] = nc;
+        while (head < tail) {
+            const int64_t i = queue[head++];
+            ++size;
+            const int x = (int)(i % nx), y = (int)((i / nx) % ny), z = (int)(i / ((int64_t)nx * ny));
+            const int64_t nb[6] = {sidx(&p, x + 1, y, z), sidx(&p, x - 1, y, z), sidx(&p, x, y + 1, z),
+                                   sidx(&p, x, y - 1, z), sidx(&p, x, y, z + 1), sidx(&p, x, y, z - 1)};
+            for (int k = 0; k < 6; ++k)
+                if (comp[nb[k]] == -1) { comp[nb[k]] = nc; queue[tail++] = nb[k]; }
+        }
+        sizes[nc] = size;
+        if (size > best_size) { best_size = size; best = nc; }
+        ++nc;
+    }
+    double trapped = 0.0, total = 0.0;
+    for (int64_t i = 0; i < V; ++i) {
+        total += phiS[i];
+        if (comp[i] >= 0 && comp[i] != best) trapped += phiS[i];
+    }
+    if (ncomp) *ncomp = nc;
+    free(comp); free(queue); free(sizes);
+    return total > 0.0 ? trapped / total : 0.0;
+}
+
+/* ------------------------------------------------------------------------------------ */
 /* Diagnostics.                                                                          */
 /* Free-energy density v0 F/(k_B T V) of Eq. 1 in volume fractions (constants ln n!,      */
 /* ln V and Omega dropped):                                                               */

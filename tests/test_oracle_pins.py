@@ -794,3 +794,35 @@ def test_minkowski_invariances():
     big = np.kron(b, np.ones((2, 2, 2)))
     m1, m2 = oracle.minkowski(b, 0.5), oracle.minkowski(big, 0.5)
     assert m2["V"] == 8 * m1["V"] and m2["S"] == 4 * m1["S"] and m2["chi"] == m1["chi"]
+
+
+def test_trapped_solvent_closed_forms():
+    """Trapped solvent: the solvent inside closed B shells, as a fraction of all solvent.  One
+    hollow cube traps exactly its cavity; two shells trap both cavities; an open cup, a slab and
+    an empty box trap nothing; the result does not depend on where the box is cut."""
+    shape = (12, 12, 12)
+    phiS = 0.5 + 0.1 * inputs.uniform01(3, 12 ** 3).reshape(shape)
+    B = np.zeros(shape)
+    B[2:7, 2:7, 2:7] = 1.0
+    B[3:6, 3:6, 3:6] = 0.0        # cavity of 27 sites
+    f, n = oracle.trapped_solvent(B, phiS)
+    cav = np.zeros(shape, bool)
+    cav[3:6, 3:6, 3:6] = True
+    assert n == 2 and abs(f - phiS[cav].sum() / phiS.sum()) < 1e-14
+    B2 = B.copy()
+    B2[8:11, 8:11, 8:11] = 1.0
+    B2[9, 9, 9] = 0.0              # a second shell, cavity of one site
+    cav2 = cav.copy()
+    cav2[9, 9, 9] = True
+    f2, n2 = oracle.trapped_solvent(B2, phiS)
+    assert n2 == 3 and abs(f2 - phiS[cav2].sum() / phiS.sum()) < 1e-14
+    cup = B.copy()
+    cup[6, 4, 4] = 0.0             # a hole in the lid: the cavity joins the bulk
+    assert oracle.trapped_solvent(cup, phiS)[0] == 0.0
+    slab = np.zeros(shape)
+    slab[:, :, 5] = 1.0            # the complement stays connected through the periodic box
+    assert oracle.trapped_solvent(slab, phiS) == (0.0, 1)
+    assert oracle.trapped_solvent(np.zeros(shape), phiS) == (0.0, 1)
+    sh = (4, -3, 5)
+    fr, nr = oracle.trapped_solvent(np.roll(B2, sh, axis=(0, 1, 2)), np.roll(phiS, sh, axis=(0, 1, 2)))
+    assert nr == n2 and abs(fr - f2) < 1e-14
