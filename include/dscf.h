@@ -186,6 +186,17 @@ int dscf_observables(dscf_ctx* ctx, int32_t replica, double* out);
  * Synchronises.  DSCF_ERR_ARG for a bad replica, species or threshold. */
 int dscf_minkowski(dscf_ctx* ctx, int32_t replica, int32_t species, double threshold, int64_t* counts);
 
+/* Trapped solvent (Sec. 3, solvent enclosed by the vesicles as a fraction of all solvent): the
+ * aggregates are the body {phi_B > threshold}; its complement splits into face-connected
+ * components of the periodic box (found on the device by label propagation to a fixed point);
+ * the largest is the bulk outside (ties: the one containing the smallest site index), the others
+ * are enclosed.  out[0] = sum of phi_S over the enclosed components / sum of phi_S, out[1] = the
+ * number of components.  Solutions only (three species).  Uses the contour stack (recomputed by
+ * every density evaluation) as scratch.
+ * Synchronises.  DSCF_ERR_ARG without solvent, DSCF_ERR_TIMEOUT if the labelling does not
+ * settle within 64 (nx + ny + nz) + 1024 sweeps. */
+int dscf_trapped_solvent(dscf_ctx* ctx, int32_t replica, double threshold, double* out);
+
 int dscf_status(dscf_ctx* ctx);
 
 /* Release host-side state (graph, capture stream).  The workspace stays the caller's. */

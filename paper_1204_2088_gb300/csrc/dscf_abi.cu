@@ -1023,6 +1023,67 @@ int dscf_minkowski(dscf_ctx* c, int32_t replica, int32_t species, double thresho
     return DSCF_OK;
 }
 
+int dscf_trapped_solvent(dscf_ctx* c, int32_t replica, double threshold, double* out) {
+    if (!c || !out) return c ? fail(c, DSCF_ERR_ARG, "NULL output") : DSCF_ERR_ARG;
+    if (replica < 0 || replica >= c->nrep) return fail(c, DSCF_ERR_ARG, "replica out of range");
+    const Rep& R = c->L.reps[replica];
+    if (R.ns != 3) return fail(c, DSCF_ERR_ARG, "the replica has no solvent");
+    if (!std::isfinite(threshold)) return fail(c, DSCF_ERR_ARG, "threshold must be finite");
+    if (int rc = set_dev(c)) return rc;
+    const Launch L = launch_of(c, c->stream);
+    // scratch: the contour stack (recomputed by every density evaluation) holds 2 V ints
+    int* lab = (int*)R.G;
+    int* cnt = lab + R.V;
+    int* changed = c->d_status + 3;
+    if (c->prec == DSCF_FP64) launch_cc_init<double>(L, replica, threshold, lab, cnt);
+    else launch_cc_init<float>(L, replica, threshold, lab, cnt);
+    int rc = cuda_check(c, cudaGetLastError(), "trapped solvent");
+    // label propagation to the fixed point, checked every 8 sweeps; bounded
+    const long long max_sweeps = 64LL * ((long long)R.nx + R.ny + R.nz) + 1024;
+    long long sweeps = 0;
+    int ch = 1;
+    while (!rc && ch) {
+        if (sweeps > max_sweeps) return fail(c, DSCF_ERR_TIMEOUT, "component labelling did not settle");
+        rc = cuda_check(c, cudaMemsetAsync(changed, 0, sizeof(int), c->stream), "trapped solvent");
+        for (int k = 0; k < 8 && !rc; ++k) launch_cc_step(L, replica, lab, changed);
+        sweeps += 8;
+        if (!rc) rc = cuda_check(c, cudaMemcpyAsync(&ch, changed, sizeof(int), cudaMemcpyDeviceToHost, c->stream),
+                                 "trapped solvent");
+        if (!rc) rc = cuda_check(c, cudaStreamSynchronize(c->stream), "trapped solvent");
+    }
+    if (rc) return rc;
+    launch_cc_count(L, replica, lab, cnt);
+    const int nb = R.nblk;
+    std::vector<double> h((size_t)3 * nb);
+    const int sl[3] = {P_OBS0, P_OBS1, P_OBS4};
+    for (int k = 0; k < 3 && !rc; ++k)
+        rc = cuda_check(c, cudaMemcpyAsync(h.data() + (size_t)k * nb, R.part + (size_t)sl[k] * R.part_stride,
+                                           sizeof(double) * nb, cudaMemcpyDeviceToHost, c->stream), "trapped solvent");
+    if (!rc) rc = cuda_check(c, cudaStreamSynchronize(c->stream), "trapped solvent");
+    if (rc) return rc;
+    double bsize = -1.0, broot = -1.0, ncomp = 0.0;
+    for (int b = 0; b < nb; ++b) {
+        const double sz = h[b], rt = h[(size_t)nb + b];
+        if (sz > bsize || (sz == bsize && rt < broot)) { bsize = sz; broot = rt; }
+        ncomp += h[(size_t)2 * nb + b];
+    }
+    if (c->prec == DSCF_FP64) launch_cc_solvent<double>(L, replica, lab, (int)broot);
+    else launch_cc_solvent<float>(L, replica, lab, (int)broot);
+    for (int k = 0; k < 2 && !rc; ++k)
+        rc = cuda_check(c, cudaMemcpyAsync(h.data() + (size_t)k * nb, R.part + (size_t)(P_OBS2 + k) * R.part_stride,
+                                           sizeof(double) * nb, cudaMemcpyDeviceToHost, c->stream), "trapped solvent");
+    if (!rc) rc = cuda_check(c, cudaStreamSynchronize(c->stream), "trapped solvent");
+    if (rc) return rc;
+    double tr = 0.0, tot = 0.0;
+    for (int b = 0; b < nb; ++b) {
+        tr += h[b];
+        tot += h[(size_t)nb + b];
+    }
+    out[0] = tot > 0.0 ? tr / tot : 0.0;
+    out[1] = ncomp;
+    return DSCF_OK;
+}
+
 int dscf_diagnostics(dscf_ctx* c, int32_t replica, double* out) {
     if (!c || !out || replica < 0 || replica >= c->nrep) return c ? fail(c, DSCF_ERR_ARG, "bad replica") : DSCF_ERR_ARG;
     if (int rc = set_dev(c)) return rc;

@@ -316,6 +316,11 @@ template <typename T>
 void launch_obs2(const Launch& L, double mA, double mB, double mS);
 // per-block counts of cubes, faces, edges, vertices of {phi_species > threshold} into P_OBS0..3
 template <typename T> void launch_minkowski(const Launch& L, int replica, int species, double threshold);
+// trapped solvent: component labels of the complement of {phi_B > threshold} (lab, cnt: V ints)
+template <typename T> void launch_cc_init(const Launch& L, int replica, double threshold, int* lab, int* cnt);
+void launch_cc_step(const Launch& L, int replica, int* lab, int* changed);
+void launch_cc_count(const Launch& L, int replica, const int* lab, int* cnt);   // P_OBS0/1 largest size/root, P_OBS4 roots
+template <typename T> void launch_cc_solvent(const Launch& L, int replica, const int* lab, int bulk);   // P_OBS2, 3
 // mode 0: init (d = -g), mode 1: iteration k direction update
 template <typename T> void launch_dir(const Launch& L, int mode, int k);
 template <typename T> void launch_mu(const Launch& L, int K);   // K < 0: iterations from scal[S_NITER]

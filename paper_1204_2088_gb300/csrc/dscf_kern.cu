@@ -1301,6 +1301,135 @@ void launch_minkowski(const Launch& L, int replica, int species, double threshol
 template void launch_minkowski<float>(const Launch&, int, int, double);
 template void launch_minkowski<double>(const Launch&, int, int, double);
 
+// Trapped solvent, step 1: labels of the complement of {phi_B > threshold}: every complement
+// site starts with its own index, body sites with -1 (lab and cnt: 2 V ints of scratch).
+template <typename T>
+__global__ void __launch_bounds__(kFlatThreads) k_cc_init(const Rep* __restrict__ reps, const int* __restrict__ blk2rep,
+                                                          int replica, T threshold, int* __restrict__ lab,
+                                                          int* __restrict__ cnt) {
+    FLAT_PROLOGUE
+    if (R.rep_index != replica) return;
+    const T* pb = (const T*)R.phi + (size_t)V;   // species B
+    for (int i = i0 + threadIdx.x; i < i1; i += kFlatThreads) {
+        lab[i] = pb[i] > threshold ? -1 : i;
+        cnt[i] = 0;
+    }
+}
+// Step 2, repeated until nothing changes: each complement site takes the smallest label among
+// itself and its face neighbours in the complement, then jumps to the label of its label (labels
+// only decrease and always name a site of the same component, so concurrent updates are safe);
+// at the fixed point every site carries the smallest index of its component.
+__global__ void __launch_bounds__(kFlatThreads) k_cc_step(const Rep* __restrict__ reps, const int* __restrict__ blk2rep,
+                                                          int replica, int* __restrict__ lab, int* __restrict__ changed) {
+    FLAT_PROLOGUE
+    if (R.rep_index != replica) return;
+    const int nx = R.nx, ny = R.ny, nz = R.nz;
+    int any = 0;
+    for (int i = i0 + threadIdx.x; i < i1; i += kFlatThreads) {
+        const int l0 = lab[i];
+        if (l0 < 0) continue;
+        int x, y, z;
+        site_xyz(i, nx, ny, x, y, z);
+        const int sy = nx, sz = nx * ny;
+        const int nb[6] = {i + (x == nx - 1 ? 1 - nx : 1), i + (x == 0 ? nx - 1 : -1),
+                           i + (y == ny - 1 ? sy - sz : sy), i + (y == 0 ? sz - sy : -sy),
+                           i + (z == nz - 1 ? sz - nz * sz : sz), i + (z == 0 ? nz * sz - sz : -sz)};
+        int m = l0;
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            const int ln = lab[nb[k]];
+            if (ln >= 0 && ln < m) m = ln;
+        }
+        const int lj = lab[m];
+        if (lj >= 0 && lj < m) m = lj;
+        if (m < l0) {
+            lab[i] = m;
+            any = 1;
+        }
+    }
+    if (__syncthreads_or(any) && threadIdx.x == 0) *changed = 1;
+}
+// Step 3: component sizes at their roots (the smallest index), then per block: the largest
+// component (ties to the smaller root), the number of roots, and the solvent sums.
+__global__ void __launch_bounds__(kFlatThreads) k_cc_count(const Rep* __restrict__ reps, const int* __restrict__ blk2rep,
+                                                           int replica, const int* __restrict__ lab, int* __restrict__ cnt) {
+    FLAT_PROLOGUE
+    if (R.rep_index != replica) return;
+    for (int i = i0 + threadIdx.x; i < i1; i += kFlatThreads)
+        if (lab[i] >= 0) atomicAdd(&cnt[lab[i]], 1);
+}
+__global__ void __launch_bounds__(kFlatThreads) k_cc_best(const Rep* __restrict__ reps, const int* __restrict__ blk2rep,
+                                                          int replica, const int* __restrict__ lab,
+                                                          const int* __restrict__ cnt) {
+    __shared__ double sh[33];
+    __shared__ long long bk[kFlatThreads];
+    FLAT_PROLOGUE
+    if (R.rep_index != replica) return;
+    // key = size * 2^32 + (2^31 - 1 - root): its maximum is the largest component, ties going to
+    // the smallest root
+    long long best = -1;
+    double roots = 0.0;
+    for (int i = i0 + threadIdx.x; i < i1; i += kFlatThreads)
+        if (lab[i] == i) {
+            roots += 1.0;
+            const long long key = ((long long)cnt[i] << 32) | (long long)(0x7fffffff - i);
+            if (key > best) best = key;
+        }
+    bk[threadIdx.x] = best;
+    __syncthreads();
+    for (int o = kFlatThreads / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o && bk[threadIdx.x + o] > bk[threadIdx.x]) bk[threadIdx.x] = bk[threadIdx.x + o];
+        __syncthreads();
+    }
+    const double nr = block_sum(roots, sh);
+    if (threadIdx.x == 0) {
+        const long long k = bk[0];
+        slot(R, P_OBS0)[lb] = k < 0 ? -1.0 : (double)(k >> 32);                          // size
+        slot(R, P_OBS1)[lb] = k < 0 ? -1.0 : (double)(0x7fffffff - (int)(k & 0xffffffffLL));   // root
+        slot(R, P_OBS4)[lb] = nr;
+    }
+}
+template <typename T>
+__global__ void __launch_bounds__(kFlatThreads) k_cc_solvent(const Rep* __restrict__ reps, const int* __restrict__ blk2rep,
+                                                             int replica, const int* __restrict__ lab, int bulk) {
+    __shared__ double sh[2 * 33];
+    FLAT_PROLOGUE
+    if (R.rep_index != replica) return;
+    const T* ps = (const T*)R.phi + 2 * (size_t)V;
+    double tr = 0.0, tot = 0.0;
+    for (int i = i0 + threadIdx.x; i < i1; i += kFlatThreads) {
+        const double v = (double)ps[i];
+        tot += v;
+        if (lab[i] >= 0 && lab[i] != bulk) tr += v;
+    }
+    double t[2] = {tr, tot};
+    block_sum_n<2>(t, sh);
+    if (threadIdx.x == 0) {
+        slot(R, P_OBS2)[lb] = t[0];
+        slot(R, P_OBS3)[lb] = t[1];
+    }
+}
+
+template <typename T>
+void launch_cc_init(const Launch& L, int replica, double threshold, int* lab, int* cnt) {
+    k_cc_init<T><<<L.nblk_total, kFlatThreads, 0, L.stream>>>(L.reps, L.blk2rep, replica, (T)threshold, lab, cnt);
+}
+void launch_cc_step(const Launch& L, int replica, int* lab, int* changed) {
+    k_cc_step<<<L.nblk_total, kFlatThreads, 0, L.stream>>>(L.reps, L.blk2rep, replica, lab, changed);
+}
+void launch_cc_count(const Launch& L, int replica, const int* lab, int* cnt) {
+    k_cc_count<<<L.nblk_total, kFlatThreads, 0, L.stream>>>(L.reps, L.blk2rep, replica, lab, cnt);
+    k_cc_best<<<L.nblk_total, kFlatThreads, 0, L.stream>>>(L.reps, L.blk2rep, replica, lab, cnt);
+}
+template <typename T>
+void launch_cc_solvent(const Launch& L, int replica, const int* lab, int bulk) {
+    k_cc_solvent<T><<<L.nblk_total, kFlatThreads, 0, L.stream>>>(L.reps, L.blk2rep, replica, lab, bulk);
+}
+template void launch_cc_init<float>(const Launch&, int, double, int*, int*);
+template void launch_cc_init<double>(const Launch&, int, double, int*, int*);
+template void launch_cc_solvent<float>(const Launch&, int, const int*, int);
+template void launch_cc_solvent<double>(const Launch&, int, const int*, int);
+
 // One block.  Every replica's residual is reduced in the same fixed order as the kernels that
 // record it, so the decision is reproducible; a non-finite residual closes the gate.
 // A non-finite <g,g> closes the gate and sets the non-finite status bit.

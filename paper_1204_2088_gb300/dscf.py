@@ -92,6 +92,7 @@ def load():
         "dscf_set_inversion_tol": (ctypes.c_int, [vp, ctypes.c_double]),
         "dscf_set_noise": (ctypes.c_int, [vp, ctypes.c_double, i32, ctypes.c_uint64]),
         "dscf_minkowski": (ctypes.c_int, [vp, i32, i32, ctypes.c_double, ctypes.POINTER(ctypes.c_int64)]),
+        "dscf_trapped_solvent": (ctypes.c_int, [vp, i32, ctypes.c_double, ctypes.POINTER(ctypes.c_double)]),
         "dscf_observables": (ctypes.c_int, [vp, i32, ctypes.POINTER(ctypes.c_double)]),
         "dscf_net_set_tensor_path": (ctypes.c_int, [vp, i32]),
         "dscf_net_tensor_path": (i32, [vp]),
@@ -314,6 +315,12 @@ class Context:
         """Volume, surface, 2 x integral mean curvature (lattice units) and Euler characteristic."""
         nc, nf, ne, nv = self.minkowski_counts(species, threshold, replica)
         return {"V": nc, "S": -6 * nc + 2 * nf, "B2": 3 * nc - 2 * nf + ne, "chi": -nc + nf - ne + nv}
+
+    def trapped_solvent(self, threshold=0.2, replica=0):
+        """(fraction of the solvent enclosed by {phi_B > threshold}, number of components)."""
+        out = (ctypes.c_double * 2)()
+        self._check(self.lib.dscf_trapped_solvent(self.h, int(replica), float(threshold), out))
+        return out[0], int(out[1])
 
     def set_predictor(self, net, corrector_every=10, tol=1e-3, ncg_iters=0):
         """Attach a trained Net (same grid, batch 1) as the density map of the inversion, judged

@@ -18,8 +18,9 @@ the explicit noise step drives the minority composition of a strongly segregated
 zero within a few thousand steps, where the inversion cannot follow.  A run that breaks down ends
 with an "error" record.
 Every record is one JSON line: system, hydro, seed, step, time (tau), F, S, segregation, the
-Minkowski functionals of the B beads at threshold 0.2 (V, S, 2B, chi), and the mean milliseconds
-per step of the segment before it.
+Minkowski functionals of the B beads at threshold 0.2 (V, S, 2B, chi), for the solution the
+fraction of the solvent enclosed by {phi_B > 0.2} and the number of solvent components, and the
+mean milliseconds per step of the segment before it.
 """
 from __future__ import annotations
 
@@ -66,6 +67,8 @@ def run(name: str, grid: int, steps: int, every: int, seed: int, hydro: int, ome
             mk = ctx.minkowski(1, 0.2)   # the B beads at the paper's threshold
             rec = dict(base, step=done, time=done * cfg["dt"], F=ob["free_energy"], S=ob["order_parameter"],
                        segregation=ob["segregation"], minkowski_B=mk)
+            if cfg["ns"] == 3:
+                rec["trapped_solvent"], rec["solvent_components"] = ctx.trapped_solvent(0.2)
             if ms is not None:
                 rec["ms_per_step"] = ms
             yield rec

@@ -229,6 +229,9 @@ def test_quench_driver_records_ordering():
         assert [r["step"] for r in recs] == [0, 1000, 2000]
         assert all("error" not in r and np.isfinite([r["F"], r["S"], r["segregation"]]).all() for r in recs)
         assert recs[-1]["S"] > 10 * recs[0]["S"] and recs[-1]["F"] < recs[0]["F"]
+    recs = list(quench.run("A2B8S", 16, 200, 100, 1, 0))   # the solution also records trapped solvent
+    assert all("error" not in r and 0.0 <= r["trapped_solvent"] <= 1.0 and r["solvent_components"] >= 1
+               for r in recs)
 
 
 @pytest.mark.parametrize("prec", [dscf.FP64, dscf.FP32], ids=["fp64", "fp32"])
@@ -259,4 +262,63 @@ def test_minkowski_counts_match_oracle(prec):
         phi = t2n(big.get(dscf.PHI))
         assert big.minkowski_counts(1, 0.2) == oracle.minkowski_counts(phi[1], float(np.float32(0.2)))
         assert big.minkowski_counts(0, 0.3) == oracle.minkowski_counts(phi[0], float(np.float32(0.3)))
+        big.close()
+
+
+def _shells(shape, centres, r_in, r_out):
+    """phi_B = 1 on spherical shells r_in <= |x - c| <= r_out (periodic distances), else 0."""
+    nz, ny, nx = shape
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    b = np.zeros(shape)
+    for c in centres:
+        d = [np.minimum(abs(a - c0), n - abs(a - c0)) for a, c0, n in ((z, c[0], nz), (y, c[1], ny), (x, c[2], nx))]
+        r = np.sqrt(d[0] ** 2 + d[1] ** 2 + d[2] ** 2)
+        b[(r >= r_in) & (r <= r_out)] = 1.0
+    return b
+
+
+@pytest.mark.parametrize("prec", [dscf.FP64, dscf.FP32], ids=["fp64", "fp32"])
+def test_trapped_solvent_matches_oracle(prec):
+    """The number of solvent components is an integer (exact against the oracle) and the enclosed
+    fraction a ratio of sums (FP64 1e-12, FP32 fields summed in FP64: 1e-12 as well, since both
+    sides sum the same stored values): random fields with many components, two hollow vesicles
+    (their cores are the enclosed solvent), a batch with the solution picked out, and the 128^3
+    solution after a few steps.  A melt (no solvent) is refused."""
+    shape = (20, 18, 22)
+    ves = _shells(shape, [(5, 5, 6), (14, 12, 15)], 2.5, 4.0)
+    rng = np.random.default_rng(7)
+    phis = 0.3 + 0.4 * rng.random(shape)
+    rnd = inputs.random_field((3,) + shape, seed=91, scale=0.5) + 0.5
+    cases = [np.stack([1.0 - ves - 0.5 * (1 - ves) * phis, ves, 0.5 * (1 - ves) * phis + 0.01]), rnd]
+    cfgs = [inputs.melt((12, 10, 8), 6, 0.5, 12.0)] + [inputs.solution(shape[::-1], 5, 0.3, 0.3, 20.0, 24.0, 3.0)] * 2
+    ctx = dscf.Context(cfgs, prec)
+    dt = torch.float64 if prec == dscf.FP64 else torch.float32
+    melt = np.full((2, 8, 10, 12), 0.5)
+    ctx.set(dscf.PHI, torch.cat([torch.from_numpy(f).to(dt).reshape(-1) for f in [melt] + cases]).cuda())
+    with pytest.raises(dscf.DSCFError):
+        ctx.trapped_solvent(0.2, replica=0)
+    seen = []
+    for r, f in enumerate(cases, start=1):
+        stored = f.astype(np.float32).astype(np.float64) if prec == dscf.FP32 else f
+        for th in (0.2, 0.5, 0.75):
+            t = float(np.float32(th)) if prec == dscf.FP32 else th
+            want = oracle.trapped_solvent(stored[1], stored[2], t)
+            got = ctx.trapped_solvent(th, replica=r)
+            assert got[1] == want[1], (r, th, got, want)
+            assert got[0] == pytest.approx(want[0], rel=1e-12, abs=1e-15), (r, th, got, want)
+            seen.append(want)
+    assert seen[0][1] == 3 and seen[0][0] > 0.01       # outside + two cores
+    assert max(n for _, n in seen[3:]) > 20            # random fields: many components
+    ctx.close()
+    if prec == dscf.FP32:
+        cfg = inputs.workload("solution128")
+        big = dscf.Context(cfg, dscf.FP32, tuning=(16, 0))
+        big.set(dscf.PHI, torch.from_numpy(inputs.initial_fields(cfg)).float().cuda())
+        big.step(5)
+        big.status()
+        phi = t2n(big.get(dscf.PHI))
+        for th in (0.12, 0.2):
+            want = oracle.trapped_solvent(phi[1], phi[2], float(np.float32(th)))
+            got = big.trapped_solvent(th)
+            assert got[1] == want[1] and got[0] == pytest.approx(want[0], rel=1e-10, abs=1e-15)
         big.close()
