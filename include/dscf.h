@@ -57,7 +57,8 @@ enum {
     DSCF_ERR_OOM = -3,      /* the workspace passed is too small                       */
     DSCF_ERR_TIMEOUT = -4,  /* a bounded device wait gave up                           */
     DSCF_ERR_NUMERIC = -5,  /* non-finite value in a reduction (status word)           */
-    DSCF_ERR_STATE = -6     /* call not valid in the current context state             */
+    DSCF_ERR_STATE = -6,    /* call not valid in the current context state             */
+    DSCF_ERR_NOCONVERGE = -7 /* a bounded host-driven iteration did not settle          */
 };
 
 enum { DSCF_FP64 = 0, DSCF_FP32 = 1 };
@@ -193,7 +194,7 @@ int dscf_minkowski(dscf_ctx* ctx, int32_t replica, int32_t species, double thres
  * are enclosed.  out[0] = sum of phi_S over the enclosed components / sum of phi_S, out[1] = the
  * number of components.  Solutions only (three species).  Uses the contour stack (recomputed by
  * every density evaluation) as scratch.
- * Synchronises.  DSCF_ERR_ARG without solvent, DSCF_ERR_TIMEOUT if the labelling does not
+ * Synchronises.  DSCF_ERR_ARG without solvent, DSCF_ERR_NOCONVERGE if the labelling does not
  * settle within 64 (nx + ny + nz) + 1024 sweeps. */
 int dscf_trapped_solvent(dscf_ctx* ctx, int32_t replica, double threshold, double* out);
 

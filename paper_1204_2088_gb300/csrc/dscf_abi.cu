@@ -1043,7 +1043,7 @@ int dscf_trapped_solvent(dscf_ctx* c, int32_t replica, double threshold, double*
     long long sweeps = 0;
     int ch = 1;
     while (!rc && ch) {
-        if (sweeps > max_sweeps) return fail(c, DSCF_ERR_TIMEOUT, "component labelling did not settle");
+        if (sweeps > max_sweeps) return fail(c, DSCF_ERR_NOCONVERGE, "component labelling did not settle");
         rc = cuda_check(c, cudaMemsetAsync(changed, 0, sizeof(int), c->stream), "trapped solvent");
         for (int k = 0; k < 8 && !rc; ++k) launch_cc_step(L, replica, lab, changed);
         sweeps += 8;

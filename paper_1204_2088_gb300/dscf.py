@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(_HERE, "libdscf.so")
 
 DSCF_OK = 0
 ERRORS = {-1: "DSCF_ERR_ARG", -2: "DSCF_ERR_CUDA", -3: "DSCF_ERR_OOM", -4: "DSCF_ERR_TIMEOUT",
-          -5: "DSCF_ERR_NUMERIC", -6: "DSCF_ERR_STATE"}
+          -5: "DSCF_ERR_NUMERIC", -6: "DSCF_ERR_STATE", -7: "DSCF_ERR_NOCONVERGE"}
 FP64, FP32 = 0, 1
 PHI, U, MU, VEL, POP, PHIM = 0, 1, 2, 3, 4, 5
 
