@@ -11,7 +11,8 @@
 //   and one row of a z-halo plane;
 //   barrier; z pass (the neighbouring planes from YS) -> sig;
 //   forward:  G_s = exp(-U_{I_s}) sig; brick-boundary values stored to the contour stack;
-//   backward: q_{I_s} += G_s sig in registers (G_s prefetched a step ahead with cp.async),
+//   backward: q_{I_s} += G_s sig in registers (G_s prefetched a step ahead by bulk copies that
+//             complete on an mbarrier, so the halo wait never waits for them),
 //             G+_s = exp(-U_{I_s}) sig, boundary values stored to a ping-pong exchange buffer;
 //   barrier, release store of the brick's step counter; then the forward interior stores and the
 //   x pass of the new values, in registers.
@@ -25,6 +26,10 @@ namespace dscf {
 namespace {
 
 constexpr int PBY = 8;                 // brick rows
+// Polls of the backward G_s prefetch's mbarrier before giving up.  The copies depend on no other
+// CTA, so this bound is fixed and far above any real copy time (a shorter neighbour-wait limit set
+// for failure tests must not abandon a copy that is still landing in this CTA's shared memory).
+constexpr long long kGsSpinLimit = 1LL << 26;
 // Warps per CTA: 16 for bricks of 16 planes (one CTA per SM), 8 for bricks of 8 planes, which
 // fit two CTAs per SM so that one brick computes while the other waits on its neighbours.
 
@@ -41,6 +46,31 @@ __device__ __forceinline__ int ld_acquire(const int* p) {
 }
 __device__ __forceinline__ void st_release(int* p, int v) {
     asm volatile("st.release.gpu.global.s32 [%0], %1;\n" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ void bar_init(unsigned long long* bar) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(saddr(bar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+}
+__device__ __forceinline__ void bar_expect(unsigned long long* bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(saddr(bar)), "r"(bytes) : "memory");
+}
+// bulk copy global -> shared (both 16-byte aligned, bytes a multiple of 16) completing on bar
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                     saddr(dst)),
+                 "l"(src), "r"(bytes), "r"(saddr(bar))
+                 : "memory");
+}
+__device__ __forceinline__ bool bar_test(unsigned long long* bar, unsigned parity) {
+    unsigned done;
+    asm volatile(
+        "{\n\t.reg .pred P1;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 P1, [%1], %2;\n\t"
+        "selp.b32 %0, 1, 0, P1;\n\t}\n"
+        : "=r"(done)
+        : "r"(saddr(bar)), "r"(parity)
+        : "memory");
+    return done != 0;
 }
 
 struct PersCtl {
@@ -114,6 +144,7 @@ __global__ void __launch_bounds__(32 * NW, 16 / NW) k_prop_pers(const Rep* __res
     float* GS = HS + G::NH * W;                                // [BZ][PBY][W] backward G_s
     __shared__ double sh[33];
     __shared__ int nbs[8];
+    __shared__ __align__(8) unsigned long long gs_bar;   // backward: completion of the G_s prefetch
     const Rep& R = reps[0];
     const int ny = R.ny, nz = R.nz, N = R.N, nA = R.nA;
     const int plane = W * ny;
@@ -179,11 +210,36 @@ __global__ void __launch_bounds__(32 * NW, 16 / NW) k_prop_pers(const Rep* __res
 #pragma unroll
         for (int r = 0; r < PBY; ++r) e[r] = *(const VT*)(E + own0 + (size_t)r * W);
     };
-    auto prefetch_gs = [&](int s) {   // backward: G_s of this warp's plane into GS
-        const float* Gs = (const float*)R.G + (size_t)(s - 1) * V;
-#pragma unroll
-        for (int r = 0; r < PBY; ++r) cp16(GS + (w * PBY + r) * W + VEC * lane, Gs + own0 + (size_t)r * W);
-        cpc();
+    // backward: G_s of the brick into GS, issued by thread 0 as one bulk copy per plane (the
+    // plane's PBY rows are contiguous in memory and in GS); the copies complete on gs_bar
+    unsigned gs_phase = 0;
+    bool gs_pending = false, gs_dead = false;
+    auto prefetch_gs = [&](int s) {
+        if (gs_dead) return;   // a copy that never completed: issue no more
+        if (threadIdx.x == 0) {
+            asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");   // after the generic reads of GS
+            const float* Gs = (const float*)R.G + (size_t)(s - 1) * V + (size_t)z0 * plane + (size_t)y0 * W;
+            bar_expect(&gs_bar, (unsigned)(BZ * PBY * W * sizeof(float)));
+            for (int pl = 0; pl < BZ; ++pl)
+                bulk_g2s(GS + pl * PBY * W, Gs + (size_t)pl * plane, (unsigned)(PBY * W * sizeof(float)), &gs_bar);
+        }
+        gs_pending = true;
+    };
+    // bounded wait for the pending prefetch; on timeout the CTA reports it, raises the abort and
+    // stops prefetching (the copy stays pending for the last wait at the end of the sweep)
+    auto wait_gs = [&]() {
+        if (!gs_pending || gs_dead) return;
+        for (long long spins = 0; !bar_test(&gs_bar, gs_phase); ++spins) {
+            if (spins > kGsSpinLimit) {
+                atomicOr(ctl.status, (int)ST_TIMEOUT);
+                atomicExch(ctl.abort, 1);
+                aborted = true;
+                gs_dead = true;
+                return;
+            }
+        }
+        gs_phase ^= 1u;
+        gs_pending = false;
     };
 
     // the first input (G_0 = 1, or G+_{N+1} = 1): its x pass is be + 2 al everywhere
@@ -198,7 +254,11 @@ __global__ void __launch_bounds__(32 * NW, 16 / NW) k_prop_pers(const Rep* __res
     float qsum = 0.f;
     int species = BWD ? (N <= nA ? 0 : 1) : (1 <= nA ? 0 : 1);
     load_e(species);
-    if (BWD) prefetch_gs(N);
+    if (BWD) {
+        if (threadIdx.x == 0) bar_init(&gs_bar);
+        __syncthreads();
+        prefetch_gs(N);
+    }
     __syncthreads();
 
     for (int j = 0; j < N; ++j) {
@@ -229,8 +289,6 @@ __global__ void __launch_bounds__(32 * NW, 16 / NW) k_prop_pers(const Rep* __res
                 halo_rp(h, r, pl);
                 *(VT*)(halo_dst(r, pl) + VEC * lane) = xpass(*(const VT*)(HS + h * W + VEC * lane));
             }
-        } else if (BWD) {
-            cpw0();
         }
         __syncthreads();
         // y pass of the own plane in registers (its two y-halo rows from XH), into YS
@@ -256,6 +314,7 @@ __global__ void __launch_bounds__(32 * NW, 16 / NW) k_prop_pers(const Rep* __res
         __syncthreads();
         // z pass and step output
         float* dst = BWD ? (float*)((j & 1) ? R.Gp1 : R.Gp0) : (float*)R.G + (size_t)(s - 1) * V;
+        if (BWD) wait_gs();
         VT out[PBY];
 #pragma unroll
         for (int r = 0; r < PBY; ++r) {
@@ -289,6 +348,10 @@ __global__ void __launch_bounds__(32 * NW, 16 / NW) k_prop_pers(const Rep* __res
         }
     }
     if (BWD) {   // the A block ends at s = 1
+        if (gs_dead) {   // one more bounded wait for a copy still in flight
+            for (long long spins = 0; spins <= kGsSpinLimit && !bar_test(&gs_bar, gs_phase); ++spins) {
+            }
+        }
         float* q = (float*)R.q + (size_t)species * V;
 #pragma unroll
         for (int r = 0; r < PBY; ++r) *(VT*)(q + own0 + (size_t)r * W) = qacc[r];
