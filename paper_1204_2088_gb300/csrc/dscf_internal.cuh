@@ -40,7 +40,12 @@ enum ScalSlot {
     S_ITER0 = 2,                 // per iteration k: a1, a, gg, gmax at S_ITER0 + 4k + {0..3}
     S_Q = 160, S_QS, S_DRIFT0, S_DRIFT1, S_DRIFT2, S_MASS0, S_MASS1, S_MASS2,
     S_RHO, S_JX, S_JY, S_JZ, S_UMAX, S_PERR,
-    S_NITER                      // inversion iterations run in the last step (residual stop)
+    S_NITER,                     // inversion iterations run in the last step (residual stop)
+    // totals of partial sums, formed once by the last block of the kernel that wrote them:
+    S_H0S, S_CDS, S_H1S,         // line search: <g,d>, <d, phi_m d>, h1
+    S_GGS0, S_GGS1,              // <g,g> in the parity slots of the iterations
+    S_TOT0, S_TOT1, S_TOT2,      // sum_r phi_I before the mass correction
+    S_FIN = kScalStride - 1      // finished-block count (an unsigned in this slot's bytes)
 };
 
 // Device status bits.
@@ -228,6 +233,26 @@ __device__ __forceinline__ void reduce_parts_n(const Parts<NV> p, int n, double 
         for (int k = 0; k < NV; ++k) out[k] += p.p[k][i];
     block_sum_n<NV>(out, sh);
 }
+// The same totals read through L2 (ld.global.cg), for partials that other blocks of the running
+// kernel have just written.
+__device__ __forceinline__ double reduce_parts_cg(const double* p, int n, double* sh) {
+    const int tid = threadIdx.x + threadIdx.y * blockDim.x;
+    const int nt = blockDim.x * blockDim.y;
+    double s = 0.0;
+    for (int i = tid; i < n; i += nt) s += __ldcg(p + i);
+    return block_sum(s, sh);
+}
+template <int NV>
+__device__ __forceinline__ void reduce_parts_n_cg(const Parts<NV> p, int n, double (&out)[NV], double* sh) {
+    const int tid = threadIdx.x + threadIdx.y * blockDim.x;
+    const int nt = blockDim.x * blockDim.y;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) out[k] = 0.0;
+    for (int i = tid; i < n; i += nt)
+#pragma unroll
+        for (int k = 0; k < NV; ++k) out[k] += __ldcg(p.p[k] + i);
+    block_sum_n<NV>(out, sh);
+}
 __device__ __forceinline__ double reduce_parts_max(const double* __restrict__ p, int n, double* sh) {
     const int tid = threadIdx.x + threadIdx.y * blockDim.x;
     const int nt = blockDim.x * blockDim.y;
@@ -237,6 +262,24 @@ __device__ __forceinline__ double reduce_parts_max(const double* __restrict__ p,
 }
 
 __device__ __forceinline__ double* slot(const Rep& R, int s) { return R.part + (size_t)s * R.part_stride; }
+
+// Fence-and-count: after thread 0 of every block of the replica has written its partials, true in
+// the one block that finishes last, where every block's partials are visible.  The count wraps
+// to zero at R.nblk, so it is ready for the next launch without a reset.  The last block forms
+// the totals once (in the same order as reduce_parts), instead of every block of the consuming
+// kernel re-reading all partials of one L2 line set.
+__device__ __forceinline__ bool last_block_of(const Rep& R, int* flag_sh) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned old = atomicInc((unsigned*)(R.scal + S_FIN), (unsigned)R.nblk - 1u);
+        *flag_sh = (old == (unsigned)R.nblk - 1u);
+    }
+    __syncthreads();
+    const bool last = *flag_sh != 0;
+    if (last) __threadfence();
+    return last;
+}
 
 __device__ __forceinline__ int wrapi(int v, int n) {
     v %= n;

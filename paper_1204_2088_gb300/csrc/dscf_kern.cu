@@ -111,6 +111,11 @@ __global__ void __launch_bounds__(kFlatThreads) k_trial(const Rep* __restrict__ 
     }
     const double t = block_sum((double)h1, sh);
     if (threadIdx.x == 0) slot(R, P_H1)[lb] = t;
+    __shared__ int fin;
+    if (last_block_of(R, &fin)) {
+        const double h1s = reduce_parts_cg(slot(R, P_H1), R.nblk, sh);
+        if (threadIdx.x == 0) R.scal[S_H1S] = h1s;
+    }
 }
 
 // Store phi_m = phi[U] of the committed point; k >= 0 also leaves <g,g> (g = phi* - phi_m) in
@@ -168,6 +173,11 @@ __global__ void __launch_bounds__(kFlatThreads) k_grad(const Rep* __restrict__ r
             slot(R, pslot_gg(k + 1))[lb] = t;
             slot(R, P_GMAX)[lb] = tm;
         }
+        __shared__ int fin;
+        if (last_block_of(R, &fin)) {
+            const double ggs = reduce_parts_cg(slot(R, pslot_gg(k + 1)), R.nblk, sh);
+            if (threadIdx.x == 0) R.scal[S_GGS0 + ((k + 1) & 1)] = ggs;
+        }
     }
 }
 
@@ -181,10 +191,8 @@ __global__ void __launch_bounds__(kFlatThreads) k_dir(const Rep* __restrict__ re
     FLAT_PROLOGUE
     double beta = 0.0;
     if (mode == 1) {
-        const Parts<2> ps = {slot(R, pslot_gg(k + 1)), slot(R, pslot_gg(k))};
-        double t[2];
-        reduce_parts_n<2>(ps, R.nblk, t, sh);
-        const double ggn = t[0], ggo = t[1];
+        // <g,g> of iterations k+1 and k, totalled by the last blocks of their producers
+        const double ggn = R.scal[S_GGS0 + ((k + 1) & 1)], ggo = R.scal[S_GGS0 + (k & 1)];
         beta = (ggo > 0.0) ? ggn / ggo : 0.0;
         if (lb == 0) {
             const double gm = reduce_parts_max(slot(R, P_GMAX), R.nblk, sh);
@@ -251,6 +259,18 @@ __global__ void __launch_bounds__(kFlatThreads) k_dir(const Rep* __restrict__ re
         if (threadIdx.x == 0) {
             slot(R, P_H0)[lb] = t[0];
             slot(R, P_CD)[lb] = t[1];
+        }
+    }
+    __shared__ int fin;
+    if (last_block_of(R, &fin)) {
+        const Parts<2> ps = {slot(R, P_H0), slot(R, P_CD)};
+        double t[2];
+        reduce_parts_n_cg<2>(ps, R.nblk, t, sh);
+        const double gg0 = mode == 0 ? reduce_parts_cg(slot(R, P_GG0), R.nblk, sh) : 0.0;
+        if (threadIdx.x == 0) {
+            R.scal[S_H0S] = t[0];
+            R.scal[S_CDS] = t[1];
+            if (mode == 0) R.scal[S_GGS0] = gg0;
         }
     }
 }
@@ -1046,6 +1066,12 @@ __global__ void __launch_bounds__(kFlatThreads) k_cd_finish(const Rep* __restric
         const double t = block_sum((double)acc, sh);
         if (threadIdx.x == 0) slot(R, P_MASS0 + I)[lb] = t;
     }
+    __shared__ int fin;
+    if (last_block_of(R, &fin))
+        for (int I = 0; I < R.ns; ++I) {
+            const double tot = reduce_parts_cg(slot(R, P_MASS0 + I), R.nblk, sh);
+            if (threadIdx.x == 0) R.scal[S_TOT0 + I] = tot;
+        }
 }
 
 // Shift every species to its prescribed total (FP64); block 0 records the diagnostics.
@@ -1056,7 +1082,7 @@ __global__ void __launch_bounds__(kFlatThreads) k_mass_fix(const Rep* __restrict
     FLAT_PROLOGUE
     T* phi = (T*)R.phi;
     for (int I = 0; I < R.ns; ++I) {
-        const double tot = reduce_parts(slot(R, P_MASS0 + I), R.nblk, sh);
+        const double tot = R.scal[S_TOT0 + I];   // totalled by the last block of k_cd_finish
         const double shift = (R.mass0[I] - tot) / (double)V;
         if (lb == 0 && threadIdx.x == 0) {
             R.scal[S_DRIFT0 + I] = tot - R.mass0[I];

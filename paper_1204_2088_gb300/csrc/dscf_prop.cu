@@ -555,17 +555,8 @@ __global__ void __launch_bounds__(kFlatThreads) k_exp(const Rep* __restrict__ re
     const long long i1 = min(i0 + (long long)R.chunk, V);
     double a = 0.0;
     if (mode == 1 || mode == 2) {
-        double t[3];
-        if (mode == 2) {
-            const Parts<3> ps = {slot(R, P_H0), slot(R, P_CD), slot(R, P_H1)};
-            reduce_parts_n<3>(ps, R.nblk, t, sh);
-        } else {
-            const Parts<2> ps = {slot(R, P_H0), slot(R, P_CD)};
-            double t2[2];
-            reduce_parts_n<2>(ps, R.nblk, t2, sh);
-            t[0] = t2[0];
-            t[1] = t2[1];
-        }
+        // totals of the direction and trial kernels' partials, formed by their last blocks
+        const double t[3] = {R.scal[S_H0S], R.scal[S_CDS], mode == 2 ? R.scal[S_H1S] : 0.0};
         const double h0 = t[0], cd = t[1];
         const double a1 = (cd > 0.0 && isfinite(h0 / cd)) ? -h0 / cd : 0.0;
         a = a1;
