@@ -17,6 +17,10 @@ unstable with hydrodynamics at dt = 0.2 tau even without noise; with noise (Omeg
 the explicit noise step drives the minority composition of a strongly segregated 48^3 box through
 zero within a few thousand steps, where the inversion cannot follow.  A run that breaks down ends
 with an "error" record.
+With --batch every seed and every (tau_s, tau_b) pair of --viscosities runs as one replica of a
+single context (all replicas in the same launches and one CUDA graph per step), so a protocol of
+several seeds and viscosities costs about one larger run; each replica's record carries its seed
+and relaxation times.
 Every record is one JSON line: system, hydro, seed, step, time (tau), F, S, segregation, the
 Minkowski functionals of the B beads at threshold 0.2 (V, S, 2B, chi), for the solution the
 fraction of the solvent enclosed by {phi_B > 0.2} and the number of solvent components, and the
@@ -49,10 +53,13 @@ def system_cfg(name: str, grid: int, seed: int, hydro: int) -> dict:
 
 
 def run(name: str, grid: int, steps: int, every: int, seed: int, hydro: int, omega: float = 0.0,
-        lb_noise: bool = False, precision=dscf.FP32, sink=None):
+        lb_noise: bool = False, precision=dscf.FP32, viscosity=None):
     """Yields one record per `every` steps (and the initial state); a record with "error" ends a
-    run that broke down (a non-finite value, reported by the library's status check)."""
+    run that broke down (a non-finite value, reported by the library's status check).
+    viscosity: (tau_s, tau_b) in place of the system's relaxation times."""
     cfg = system_cfg(name, grid, seed, hydro)
+    if viscosity is not None:
+        cfg = dict(cfg, tau_s=float(viscosity[0]), tau_b=float(viscosity[1]))
     ctx = dscf.Context(cfg, precision)
     ctx.set_noise(omega, lb_noise=bool(hydro and lb_noise), seed=1000 + seed)
     dt = torch.float32 if precision == dscf.FP32 else torch.float64
@@ -88,6 +95,52 @@ def run(name: str, grid: int, steps: int, every: int, seed: int, hydro: int, ome
         ctx.close()
 
 
+def run_batch(name: str, grid: int, steps: int, every: int, seeds, hydro: int, viscosities=((1.0, 1.0),),
+              omega: float = 0.0, lb_noise: bool = False, precision=dscf.FP32):
+    """As run(), for every (seed, (tau_s, tau_b)) pair at once as the replicas of one context.
+    Yields one record per replica per `every` steps; an "error" record (one per replica) ends the
+    batch."""
+    cfgs, tags = [], []
+    for ts, tb in viscosities:
+        for seed in seeds:
+            cfg = dict(system_cfg(name, grid, seed, hydro), tau_s=float(ts), tau_b=float(tb))
+            cfgs.append(cfg)
+            tags.append({"system": name, "grid": grid, "hydro": hydro, "seed": seed, "omega": omega,
+                         "tau_s": float(ts), "tau_b": float(tb)})
+    ctx = dscf.Context(cfgs, precision)
+    ctx.set_noise(omega, lb_noise=bool(hydro and lb_noise), seed=1000 + int(seeds[0]))
+    dt = torch.float32 if precision == dscf.FP32 else torch.float64
+    ctx.set(dscf.PHI, torch.cat([torch.from_numpy(inputs.initial_fields(c)).to(dt).reshape(-1) for c in cfgs]).cuda())
+    done, ms = 0, None
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    try:
+        while True:
+            for r, (cfg, tag) in enumerate(zip(cfgs, tags)):
+                ob = ctx.observables(r)
+                rec = dict(tag, step=done, time=done * cfg["dt"], F=ob["free_energy"], S=ob["order_parameter"],
+                           segregation=ob["segregation"], minkowski_B=ctx.minkowski(1, 0.2, replica=r))
+                if cfg["ns"] == 3:
+                    rec["trapped_solvent"], rec["solvent_components"] = ctx.trapped_solvent(0.2, replica=r)
+                if ms is not None:
+                    rec["ms_per_step"] = ms
+                yield rec
+            if done >= steps:
+                break
+            k = min(every, steps - done)
+            e0.record()
+            ctx.step(k)
+            e1.record()
+            torch.cuda.synchronize()
+            ctx.status()
+            ms = e0.elapsed_time(e1) / k
+            done += k
+    except dscf.DSCFError as e:
+        for tag in tags:
+            yield dict(tag, step=done, error=str(e))
+    finally:
+        ctx.close()
+
+
 def main(argv=None) -> int:
     ap = argparse.ArgumentParser()
     ap.add_argument("--system", default="A8B8", choices=["A8B8", "A5B11", "A2B8S"])
@@ -97,14 +150,25 @@ def main(argv=None) -> int:
     ap.add_argument("--seeds", type=int, nargs="+", default=[1])
     ap.add_argument("--omega", type=float, default=0.0, help="noise parameter (0: no thermal noise)")
     ap.add_argument("--lb-noise", action="store_true")
+    ap.add_argument("--batch", action="store_true", help="all seeds and viscosities as replicas of one context")
+    ap.add_argument("--viscosities", type=float, nargs="+", default=[1.0, 1.0],
+                    help="tau_s tau_b pairs for the hydrodynamic runs of --batch")
     ap.add_argument("--out", default="-")
     a = ap.parse_args(argv)
+    if len(a.viscosities) % 2:
+        ap.error("--viscosities takes tau_s tau_b pairs")
+    visc = list(zip(a.viscosities[0::2], a.viscosities[1::2]))
     out = sys.stdout if a.out == "-" else open(a.out, "w")
-    for seed in a.seeds:
-        for hydro in (0, 1):
-            for r in run(a.system, a.grid, a.steps, a.every, seed, hydro, a.omega, a.lb_noise):
-                out.write(json.dumps(r) + "\n")
-                out.flush()
+    if a.batch:
+        runs = [run_batch(a.system, a.grid, a.steps, a.every, a.seeds, 0, visc[:1], a.omega, a.lb_noise),
+                run_batch(a.system, a.grid, a.steps, a.every, a.seeds, 1, visc, a.omega, a.lb_noise)]
+    else:
+        runs = [run(a.system, a.grid, a.steps, a.every, seed, hydro, a.omega, a.lb_noise)
+                for seed in a.seeds for hydro in (0, 1)]
+    for it in runs:
+        for r in it:
+            out.write(json.dumps(r) + "\n")
+            out.flush()
     if out is not sys.stdout:
         out.close()
     return 0

@@ -322,3 +322,28 @@ def test_trapped_solvent_matches_oracle(prec):
             got = big.trapped_solvent(th)
             assert got[1] == want[1] and got[0] == pytest.approx(want[0], rel=1e-10, abs=1e-15)
         big.close()
+
+
+def test_quench_batch_matches_solo_runs():
+    """The batched quench protocol (every seed and every (tau_s, tau_b) pair as a replica of one
+    context) reproduces the solo runs record by record (FP64: the replicas of a small batch keep
+    their solo tiling and reduction order)."""
+    from paper_1204_2088_gb300 import quench
+    visc = [(1.0, 1.0), (0.7, 1.5)]
+    for hydro in (0, 1):
+        batch = list(quench.run_batch("A8B8", 12, 40, 20, [1, 2], hydro, visc if hydro else visc[:1],
+                                      precision=dscf.FP64))
+        nrep = 4 if hydro else 2
+        assert len(batch) == 3 * nrep and all("error" not in r for r in batch)
+        for ts, tb in (visc if hydro else visc[:1]):
+            for seed in (1, 2):
+                solo = list(quench.run("A8B8", 12, 40, 20, seed, hydro, precision=dscf.FP64, viscosity=(ts, tb)))
+                mine = [r for r in batch if r["seed"] == seed and r["tau_s"] == ts and r["tau_b"] == tb]
+                assert [r["step"] for r in mine] == [r["step"] for r in solo] == [0, 20, 40]
+                for a, b in zip(mine, solo):
+                    for key in ("F", "S", "segregation"):
+                        assert a[key] == pytest.approx(b[key], rel=1e-9, abs=1e-14), (hydro, ts, seed, key)
+                    assert a["minkowski_B"] == b["minkowski_B"]
+        if hydro:   # the shear relaxation time changes the hydrodynamic run
+            f = {r["tau_s"]: r["F"] for r in batch if r["seed"] == 1 and r["step"] == 40}
+            assert f[1.0] != f[0.7]
