@@ -99,7 +99,9 @@ def run_batch(name: str, grid: int, steps: int, every: int, seeds, hydro: int, v
               omega: float = 0.0, lb_noise: bool = False, precision=dscf.FP32):
     """As run(), for every (seed, (tau_s, tau_b)) pair at once as the replicas of one context.
     Yields one record per replica per `every` steps; an "error" record (one per replica) ends the
-    batch."""
+    batch.  Without noise each replica follows its solo run; with noise every replica draws its
+    own stream (keyed by its place in the batch), so noisy batch runs are other samples than the
+    solo runs of the same seeds."""
     cfgs, tags = [], []
     for ts, tb in viscosities:
         for seed in seeds:
