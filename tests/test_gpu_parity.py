@@ -119,12 +119,13 @@ def test_persistent_sweeps_fp32_within_1e5(cfg, depth):
         assert rel(got, ref) < 1e-5
 
 
-@pytest.mark.parametrize("depth", [8, 16])
-def test_persistent_sweeps_are_deterministic(depth):
+@pytest.mark.parametrize("depth,case", [(8, 0), (16, 0), (16, 2)])
+def test_persistent_sweeps_are_deterministic(depth, case):
     """Race check of the brick handshake (release store after the CTA barrier, acquire loads of
     the neighbours' counters): the density map of the persistent sweep, repeated, is bitwise the
-    same every time (a halo row read before its neighbour published it would perturb it)."""
-    cfg = PERSISTENT_CASES[0]
+    same every time (a halo row read before its neighbour published it would perturb it); also
+    with a single brick along z, its own z-neighbour."""
+    cfg = PERSISTENT_CASES[case]
     U = torch.from_numpy(inputs.random_field(ncomp_shape(cfg), seed=13, scale=0.5))
     ctx = dscf.Context(cfg, dscf.FP32)
     ctx.set_tuning(depth, 0)
@@ -134,7 +135,8 @@ def test_persistent_sweeps_are_deterministic(depth):
     ctx.status()
 
 
-def test_persistent_sweep_timeout_is_reported_and_the_context_recovers():
+@pytest.mark.parametrize("depth", [8, 16])
+def test_persistent_sweep_timeout_is_reported_and_the_context_recovers(depth):
     """Failure detection without a GPU fault: one brick's step counter is set far behind (host
     side), so its neighbours wait for a value nobody publishes; their bounded waits run out, the
     abort flag releases every other CTA, the launch finishes and the host reads DSCF_ERR_TIMEOUT.
@@ -143,7 +145,7 @@ def test_persistent_sweep_timeout_is_reported_and_the_context_recovers():
     cfg = PERSISTENT_CASES[0]
     U = torch.from_numpy(inputs.random_field(ncomp_shape(cfg), seed=12, scale=0.5))
     ctx = dscf.Context(cfg, dscf.FP32)
-    ctx.set_tuning(8, 0)
+    ctx.set_tuning(depth, 0)
     good = ctx.densities(U)
     ctx.status()
     ctx.set_wait_limit(2000)
