@@ -826,3 +826,42 @@ def test_trapped_solvent_closed_forms():
     sh = (4, -3, 5)
     fr, nr = oracle.trapped_solvent(np.roll(B2, sh, axis=(0, 1, 2)), np.roll(phiS, sh, axis=(0, 1, 2)))
     assert nr == n2 and abs(fr - f2) < 1e-14
+
+
+def test_trapped_solvent_against_library_labelling():
+    """The oracle's breadth-first components against an independent labelling: scipy's
+    face-connected labels of the complement in the open box, joined across the periodic faces by
+    a union-find, on random fields at several thresholds (component count, largest component and
+    the enclosed solvent fraction)."""
+    ndimage = pytest.importorskip("scipy.ndimage")
+    rng = np.random.default_rng(2024)
+    for shape in [(9, 11, 13), (16, 8, 12)]:
+        phiB = rng.random(shape)
+        phiS = 0.2 + rng.random(shape)
+        for th in (0.35, 0.5, 0.62):
+            comp = phiB <= th
+            lab, n = ndimage.label(comp, structure=ndimage.generate_binary_structure(3, 1))
+            parent = list(range(n + 1))
+
+            def find(a):
+                while parent[a] != a:
+                    parent[a] = parent[parent[a]]
+                    a = parent[a]
+                return a
+            for ax in range(3):
+                lo = np.take(lab, 0, axis=ax)
+                hi = np.take(lab, shape[ax] - 1, axis=ax)
+                for a, b in zip(lo.ravel(), hi.ravel()):
+                    if a and b:
+                        ra, rb = find(a), find(b)
+                        if ra != rb:
+                            parent[max(ra, rb)] = min(ra, rb)
+            roots = np.array([find(a) if a else 0 for a in lab.ravel()]).reshape(shape)
+            ids, sizes = np.unique(roots[roots > 0], return_counts=True)
+            # the bulk: largest, ties to the component holding the smallest site index
+            first = {i: np.flatnonzero(roots.ravel() == i)[0] for i in ids}
+            bulk = min(ids, key=lambda i: (-sizes[list(ids).index(i)], first[i]))
+            want = phiS[(roots > 0) & (roots != bulk)].sum() / phiS.sum()
+            f, nc = oracle.trapped_solvent(phiB, phiS, th)
+            assert nc == len(ids), (shape, th)
+            assert abs(f - want) < 1e-13, (shape, th)
