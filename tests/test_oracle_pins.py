@@ -865,3 +865,33 @@ def test_trapped_solvent_against_library_labelling():
             f, nc = oracle.trapped_solvent(phiB, phiS, th)
             assert nc == len(ids), (shape, th)
             assert abs(f - want) < 1e-13, (shape, th)
+
+
+def test_minkowski_counts_against_enumeration():
+    """The cube, face, edge and vertex counts of the body (the union of closed unit voxels of the
+    periodic box) against a plain enumeration: every voxel contributes its 6 faces, 12 edges and 8
+    corners, each named by its lattice position (wrapped), and the distinct ones are counted."""
+    rng = np.random.default_rng(77)
+    for shape, th in [((7, 9, 8), 0.55), ((6, 6, 10), 0.8), ((8, 5, 7), 0.3)]:
+        f = rng.random(shape)
+        nz, ny, nx = shape
+        body = np.argwhere(f > th)
+        faces, edges, verts = set(), set(), set()
+        for z, y, x in body:
+            for dz in (0, 1):
+                for dy in (0, 1):
+                    for dx in (0, 1):
+                        verts.add(((z + dz) % nz, (y + dy) % ny, (x + dx) % nx))
+            # edges along x, y, z: the two other coordinates take both corner offsets
+            for a in (0, 1):
+                for c in (0, 1):
+                    edges.add(("x", (z + a) % nz, (y + c) % ny, x % nx))
+                    edges.add(("y", (z + a) % nz, y % ny, (x + c) % nx))
+                    edges.add(("z", z % nz, (y + a) % ny, (x + c) % nx))
+            for a in (0, 1):
+                faces.add(("x", z, y, (x + a) % nx))
+                faces.add(("y", z, (y + a) % ny, x))
+                faces.add(("z", (z + a) % nz, y, x))
+        want = (len(body), len(faces), len(edges), len(verts))
+        got = oracle.minkowski_counts(f, th)
+        assert tuple(got) == want, (shape, got, want)
