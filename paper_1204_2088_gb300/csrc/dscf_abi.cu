@@ -1031,7 +1031,8 @@ int dscf_trapped_solvent(dscf_ctx* c, int32_t replica, double threshold, double*
     if (!std::isfinite(threshold)) return fail(c, DSCF_ERR_ARG, "threshold must be finite");
     if (int rc = set_dev(c)) return rc;
     const Launch L = launch_of(c, c->stream);
-    // scratch: the contour stack (recomputed by every density evaluation) holds 2 V ints
+    // scratch: the contour stack (recomputed by every density evaluation; N >= 2 levels of at least
+    // 4 bytes per site) holds the 2 V ints of labels and counts
     int* lab = (int*)R.G;
     int* cnt = lab + R.V;
     int* changed = c->d_status + 3;

@@ -51,7 +51,8 @@ enum ScalSlot {
 // Device status bits.
 enum { ST_NONFINITE = 1, ST_TIMEOUT = 2 };
 // Layout of the status block: [0] status word, [1] LB step counter, [2] abort flag of the
-// persistent sweeps, [kFlagBase..] one step counter per persistent brick.
+// persistent sweeps, [3] change flag of the solvent-component labelling, [kFlagBase..] one step
+// counter per persistent brick.
 constexpr int kFlagBase = 64;
 constexpr int kFlagStride = 32;   // ints between brick step counters: one 128-byte line each
 constexpr int kMaxBricks = 1024;
