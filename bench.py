@@ -196,6 +196,26 @@ def peaks():
     return 6800.0, "fallback"
 
 
+FP64_NOMINAL_TFLOPS = 1.25   # GB300 FP64 (non-tensor), nominal
+
+
+def step_bytes_per_site(N, ncg_iters, cn_sweeps, hydro, es=4, evals_per_iter=2):
+    """Algorithmic bytes per site of one coupled step (FP32 figures scaled by es / 4): per density
+    evaluation the store-forward propagator solve (G_s written and read once, U in, phi out:
+    8N + 16) and the inversion's flat passes (about 48); chemical potentials 24; LB collide-stream
+    180 with hydrodynamics; convection-diffusion 44 + 40 per Jacobi sweep."""
+    b = evals_per_iter * ncg_iters * (8 * N + 16 + 48) + 24 + 44 + 40 * cn_sweeps + (180 if hydro else 0)
+    return b * es / 4.0
+
+
+def step_prop_flops_per_site(N, ncg_iters, evals_per_iter=2):
+    """Floating-point operations per site of one step's propagator sweeps (a lower bound of the
+    step's arithmetic): per contour step the x, y and z passes of the separable stencil (4 each)
+    and the Boltzmann factor (1), and in the backward sweep the quadrature (2): 28 N per density
+    evaluation."""
+    return evals_per_iter * ncg_iters * 28 * N
+
+
 def ncu_traffic(kernel_src, N):
     """DRAM bytes per contour step of the propagator sweep from the committed ncu summary, if it
     was taken on the current source of the kernel (hash match); otherwise None."""
@@ -463,9 +483,17 @@ def run_ours(a):
         c64.step(2)
         m64 = timed(lambda: c64.step(k64))
         sw64, lb64, st64 = c64.probe_ms()
+        b64 = step_bytes_per_site(N, cfg["ncg_iters"], cfg["cn_sweeps"], cfg["hydro"], es=8)
+        f64 = step_prop_flops_per_site(N, cfg["ncg_iters"])
+        s64 = m64 / k64 * 1e-3
         forms["fp64"] = {"value": replicas.aggregate_rate([V * k64] * world, [m64]), "unit": UNIT,
                          "ms_per_step": m64 / k64, "steps": k64, "prop_sweep_ms_per_launch": sw64 / (2 * N),
-                         "lb_ms": lb64}
+                         "lb_ms": lb64,
+                         "hbm": {"alg_bytes_per_site": b64, "GBps": b64 * V / s64 / 1e9,
+                                 "frac": b64 * V / s64 / 1e9 / peaks()[0]},
+                         "fp64_alu": {"prop_flops_per_site": f64, "TFLOPs": f64 * V / s64 / 1e12,
+                                      "frac_of_nominal": f64 * V / s64 / 1e12 / FP64_NOMINAL_TFLOPS,
+                                      "nominal_TFLOPs": FP64_NOMINAL_TFLOPS}}
         c64.close()
         del c64
     if "fp32_noise" in want:
@@ -494,7 +522,11 @@ def run_ours(a):
                 diag["kfuse"], f"k_prop_fused (K={diag['kfuse']})") + "; unit = one contour step",
             "alg_bytes_per_launch": alg_bytes, "ms_per_launch": per_launch_s * 1e3, "peak_kind": peak_kind}
     lb_alg = 180.0 * V
-    kernels = {"prop_sweep": {"ms_per_launch": per_launch_s * 1e3, "GBps": achieved},
+    bstep = step_bytes_per_site(N, cfg["ncg_iters"], cfg["cn_sweeps"], cfg["hydro"])
+    sstep = ms_max / a.steps * 1e-3
+    kernels = {"step": {"alg_bytes_per_site": bstep, "GBps": bstep * V / sstep / 1e9,
+                        "hbm_frac": bstep * V / sstep / 1e9 / hbm},
+               "prop_sweep": {"ms_per_launch": per_launch_s * 1e3, "GBps": achieved},
                "lb_collide_stream": {"ms": lb_ms, "alg_bytes": lb_alg,
                                      "GBps": lb_alg / (lb_ms * 1e-3) / 1e9 if lb_ms > 0 else None},
                "step_ms_probe": step_ms}
