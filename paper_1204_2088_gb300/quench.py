@@ -143,6 +143,28 @@ def run_batch(name: str, grid: int, steps: int, every: int, seeds, hydro: int, v
         ctx.close()
 
 
+def summarize(records):
+    """Mean and sample standard deviation over seeds of F, S and segregation, per condition
+    (system, grid, hydro, tau_s, tau_b, omega) and time; runs that ended in an "error" record are
+    left out from that record on.  Returns a list of dicts sorted by condition and time."""
+    groups = {}
+    for r in records:
+        if "error" in r:
+            continue
+        key = (r["system"], r["grid"], r["hydro"], r.get("tau_s"), r.get("tau_b"), r.get("omega", 0.0), r["time"])
+        groups.setdefault(key, []).append(r)
+    out = []
+    for key in sorted(groups, key=lambda k: tuple((x is None, x) for x in k)):
+        rs = groups[key]
+        row = dict(zip(("system", "grid", "hydro", "tau_s", "tau_b", "omega", "time"), key), seeds=len(rs))
+        for q in ("F", "S", "segregation"):
+            v = np.array([r[q] for r in rs], dtype=np.float64)
+            row[q] = float(v.mean())
+            row[q + "_std"] = float(v.std(ddof=1)) if len(v) > 1 else 0.0
+        out.append(row)
+    return out
+
+
 def main(argv=None) -> int:
     ap = argparse.ArgumentParser()
     ap.add_argument("--system", default="A8B8", choices=["A8B8", "A5B11", "A2B8S"])
@@ -156,7 +178,14 @@ def main(argv=None) -> int:
     ap.add_argument("--viscosities", type=float, nargs="+", default=[1.0, 1.0],
                     help="tau_s tau_b pairs for the hydrodynamic runs of --batch")
     ap.add_argument("--out", default="-")
+    ap.add_argument("--summarize", metavar="JSONL", help="print mean and spread over seeds of a finished run file")
     a = ap.parse_args(argv)
+    if a.summarize:
+        with open(a.summarize) as f:
+            recs = [json.loads(line) for line in f if line.strip()]
+        for row in summarize(recs):
+            print(json.dumps(row))
+        return 0
     if len(a.viscosities) % 2:
         ap.error("--viscosities takes tau_s tau_b pairs")
     visc = list(zip(a.viscosities[0::2], a.viscosities[1::2]))
