@@ -84,3 +84,10 @@ def test_tuning_cache_round_trip(tmp_path):
     with open(path, "w") as f:
         f.write("{not json")
     assert dscf._tuning_cache_read(path) == {}
+
+
+def test_binding_names_every_declared_error_code():
+    """The status codes of include/dscf.h and the binding's table of names agree."""
+    text = open(os.path.join(ROOT, "include", "dscf.h")).read()
+    codes = {int(v): n for n, v in re.findall(r"\b(DSCF_ERR_\w+)\s*=\s*(-\d+)", text)}
+    assert codes and codes == dscf.ERRORS
