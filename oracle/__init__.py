@@ -8,7 +8,11 @@ numpy arrays through ctypes.
 
 Parity status of each function (what pins it is in ``tests/test_oracle_pins.py``):
   sigma, densities, objective, ncg, mu, force, lb_step, cd_step, step, free_energy,
-  order_parameter, segregation: pinned.
+  order_parameter, segregation: pinned.  The coupling inside ``step`` (the force of Eq. 8 in
+  lattice units, dt^2 f, and the LB velocity handed to the convection step as the Courant number
+  dt u) is pinned by Newton's law for a fluid starting from rest with the continuity equation,
+  by the gradient form of the linearised force (transverse velocity of second order) and by the
+  decrease of F, and of F plus the LB fluid's kinetic and compressional energy.
 """
 from __future__ import annotations
 

@@ -895,3 +895,136 @@ def test_minkowski_counts_against_enumeration():
         want = (len(body), len(faces), len(edges), len(verts))
         got = oracle.minkowski_counts(f, th)
         assert tuple(got) == want, (shape, got, want)
+
+
+# ---------------------------------------------------------------------------------------------
+# Coupling of the two solvers (Sec. 2: the force of Eq. 8 drives the LB of Eq. 9-14, whose
+# velocity advects the compositions in Eq. 3).  These pin the unit conversion between the
+# Brownian time step dt and the LB step (force dt^2 f in lattice units, velocity u_lat = dt u
+# handed to the convection step as a Courant number) with physics, not with the oracle's own
+# formula: Newton's second law for a fluid starting from rest, the continuity equation, the
+# gradient form of the linearised force, and the dissipation of the total energy.
+# ---------------------------------------------------------------------------------------------
+def _lb_energies(pop, dt):
+    """Kinetic and compressional energy per site of the LB fluid in k_B T (rho0 = 1 m0/h^3, so
+    m0 h^2/tau^2 = k_B T): (1/2) j^2/rho in physical velocity j/(rho dt), and c_s^2 drho^2/2
+    with the physical sound speed c_s^2 = h^2/(3 dt^2)."""
+    _, _, _, c = oracle.lb_basis()
+    rho = pop.sum(0)
+    j = np.einsum("izyx,ia->azyx", pop, c.astype(float))
+    return (0.5 * (j * j).sum(0) / rho).mean() / dt ** 2, ((rho - 1.0) ** 2).mean() / (6.0 * dt * dt)
+
+
+def _spectral_divergence(flux):
+    """div of flux [I][3][nz][ny][nx] (components x, y, z) by FFT: the continuum operator."""
+    out = np.zeros((flux.shape[0],) + flux.shape[2:])
+    for a, ax in ((0, 3), (1, 2), (2, 1)):
+        n = flux.shape[ax + 1]
+        kk = (2j * np.pi * np.fft.fftfreq(n)).reshape([n if d == ax else 1 for d in range(4)])
+        out += np.real(np.fft.ifftn(np.fft.fftn(flux[:, a], axes=(1, 2, 3)) * kk, axes=(1, 2, 3)))
+    return out
+
+
+@pytest.mark.parametrize("dt", [0.1, 0.05])
+def test_hydro_first_step_from_rest_obeys_newton_and_advects(dt):
+    """A fluid at rest under the body force f of Eq. 8 moves during the first step with the mean
+    velocity dt f/(2 rho0) (Newton; Eq. 9's half-force velocity is that mean), so the Courant
+    number the step reports is dt^2 f/(2 rho0), and with M = 0 the compositions change only by
+    the continuity equation, -dt div(phi u) (Eq. 3), here compared with the continuum
+    divergence (tolerance: the O((k h)^2) difference of the lattice fluxes, about 2.5% for these
+    wavelengths).  A force scaled by dt instead of dt^2, or a velocity handed to the convection
+    step in other units than the Courant number, is off by a factor 1/dt."""
+    grid = (32, 32, 2)
+    cfg = inputs.melt(grid, 8, 0.5, 12.0, hydro=1, ncg_iters=40, dt=dt)
+    cfg["M"] = 0.0
+    z, y, x = np.meshgrid(np.arange(2), np.arange(32), np.arange(32), indexing="ij")
+    k = 2 * np.pi / 32
+    w1, w2 = np.cos(k * x), np.cos(k * (x + 2 * y) + 0.3)
+    phi = np.stack([0.5 + 0.02 * (w1 + 0.5 * w2), 0.5 - 0.02 * (w1 + 0.5 * w2) + 0.01 * w2])
+    out = oracle.step(cfg, phi, np.zeros_like(phi), None, phi.reshape(2, -1).sum(1))
+    assert out["info"][-1] < 1e-8
+    f = oracle.force(cfg, phi, out["mu"])
+    ubar = dt * f / (2.0 * cfg["rho0"])                      # physical mean velocity, h/tau
+    assert np.abs(out["ulat"] - dt * ubar).max() <= 1e-12 * np.abs(dt * ubar).max()
+    dphi = out["phi"] - phi
+    cont = -dt * _spectral_divergence(phi[:, None] * ubar[None])
+    assert np.abs(dphi - cont).max() <= 0.05 * np.abs(cont).max()
+    assert np.abs(cont).max() > 1e-3 * dt * dt          # the advection is resolved
+
+
+def _helmholtz(u):
+    """Longitudinal and transverse parts of a periodic vector field [3][nz][ny][nx]."""
+    nz, ny, nx = u.shape[1:]
+    kz, ky, kx = np.meshgrid(np.fft.fftfreq(nz), np.fft.fftfreq(ny), np.fft.fftfreq(nx), indexing="ij")
+    K = np.stack([kx, ky, kz])
+    k2 = (K * K).sum(0)
+    k2[0, 0, 0] = 1.0
+    Uk = np.fft.fftn(u, axes=(1, 2, 3))
+    UL = K * (K * Uk).sum(0) / k2
+    return np.real(np.fft.ifftn(UL, axes=(1, 2, 3))), np.real(np.fft.ifftn(Uk - UL, axes=(1, 2, 3)))
+
+
+def test_hydro_transverse_velocity_is_second_order():
+    """Linearised about the uniform melt, f = -sum_I phi_I grad mu_I = -grad(sum_I phibar_I dmu_I)
+    + O(delta^2) is a gradient (Eq. 8), so it drives only the longitudinal (sound) part of the LB
+    velocity: over a few coupled steps the longitudinal velocity grows linearly with the amplitude
+    delta of a two-mode perturbation and the transverse one quadratically (the modes have
+    different |k|, so the second-order force has a curl).  A force whose components pair with the
+    wrong derivatives, or any non-gradient linear term, makes the transverse part linear."""
+    L = 16
+    grid = (L, L, 2)
+    z, y, x = np.meshgrid(np.arange(2), np.arange(L), np.arange(L), indexing="ij")
+    k = 2 * np.pi / L
+    w1, w2 = np.cos(k * x), np.cos(2 * k * y + 0.4)
+    parts = {}
+    for amp in (1e-3, 2e-3):
+        cfg = inputs.melt(grid, 8, 0.5, 12.0, hydro=1, ncg_iters=40, dt=0.1)
+        phi = np.stack([0.5 + amp * (w1 + w2), 0.5 - amp * w1 + 0.5 * amp * w2])
+        U, pop, m0 = np.zeros_like(phi), None, phi.reshape(2, -1).sum(1)
+        for _ in range(6):
+            o = oracle.step(cfg, phi, U, pop, m0)
+            phi, U, pop = o["phi"], o["U"], o["pop"]
+        uL, uT = _helmholtz(o["ulat"])
+        parts[amp] = (np.abs(uL).max(), np.abs(uT).max())
+    (l1, t1), (l2, t2) = parts[1e-3], parts[2e-3]
+    assert abs(l2 / l1 - 2.0) < 2e-3
+    assert abs(t2 / t1 - 4.0) < 2e-2
+    assert t1 < 1e-3 * l1
+
+
+def test_diffusion_only_free_energy_is_non_increasing():
+    """Without flow, Eq. 3 is a gradient flow of the free energy of Eq. 1 (dF/dt = -int M phi
+    |grad mu|^2 <= 0): F(t) of a quenched melt must not increase from step to step at dt = 0.1."""
+    cfg = inputs.melt((12, 12, 12), 8, 0.5, 16.0, noise=0.05, seed=7, dt=0.1, hydro=0, ncg_iters=30)
+    phi = inputs.initial_fields(cfg)
+    U, m0 = np.zeros_like(phi), phi.reshape(2, -1).sum(1)
+    F = []
+    for _ in range(30):
+        o = oracle.step(cfg, phi, U, None, m0)
+        F.append(oracle.free_energy(cfg, o["U"], phi))      # F of phi^n at its potentials U^n
+        phi, U = o["phi"], o["U"]
+    assert np.diff(F).max() < 0.0
+    assert F[0] - F[-1] > 1e-3
+
+
+def test_hydro_total_energy_is_non_increasing():
+    """With the LB coupled, the free energy released by advection is the work the force of Eq. 8
+    does on the fluid, so F + (kinetic + compressional energy of the LB fluid) is what decreases
+    (diffusive and viscous dissipation).  From a quench with a compressive perturbation, where
+    the flow carries energy comparable to the changes of F, the total must not increase at
+    dt = 0.1.  A force in lattice units too large by 1/dt pumps energy in and fails at once."""
+    grid = (16, 16, 16)
+    cfg = inputs.melt(grid, 8, 0.5, 16.0, noise=0.03, seed=5, dt=0.1, hydro=1, ncg_iters=30)
+    phi = inputs.initial_fields(cfg)
+    z, y, x = np.meshgrid(np.arange(16), np.arange(16), np.arange(16), indexing="ij")
+    phi[1] += 0.03 * np.cos(2 * np.pi * x / 16) * np.cos(2 * np.pi * y / 16)
+    U, pop, m0 = np.zeros_like(phi), None, phi.reshape(2, -1).sum(1)
+    E, kin = [], []
+    for _ in range(40):
+        o = oracle.step(cfg, phi, U, pop, m0)
+        ke, pe = _lb_energies(pop, cfg["dt"]) if pop is not None else (0.0, 0.0)
+        E.append(oracle.free_energy(cfg, o["U"], phi) + ke + pe)
+        kin.append(ke + pe)
+        phi, U, pop = o["phi"], o["U"], o["pop"]
+    assert np.diff(E).max() < 0.0
+    assert max(kin) > 1e-5          # the flow matters in this run
