@@ -40,9 +40,8 @@ def args_():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-forms", action="store_true", help="skip the FP64, learned and batched forms")
-    ap.add_argument("--forms", default="fp64,fp32_noise,fp32_residual_stop,fp32_learned,batch48", help="comma-separated forms to report")
+    ap.add_argument("--forms", default="fp64,fp32_noise,fp32_residual_stop,fp32_self_consistent,fp32_learned,batch48,solution128,net_forward", help="comma-separated forms to report")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-budget", type=float, default=20.0, help="seconds of oracle work for cpu_baseline")
     return ap.parse_args()
 
 
@@ -64,34 +63,32 @@ def workload_config(cfg):
 # ---------------------------------------------------------------------------------------------
 # CPU oracle timing (the reference arm and the cpu_baseline leg)
 # ---------------------------------------------------------------------------------------------
-def oracle_sample_rate(cfg, budget_s, steps=None):
-    """Time the FP64 oracle on a cubic sub-box of the workload (same N, nA, chi, dt, relaxation
-    times, inversion and Jacobi counts), sized so that `steps` steps take about budget_s.
-    Returns (site-updates/s, cores, sample description, steps, seconds)."""
+CPU_SAMPLE_L = 48   # edge of the periodic sub-box both CPU legs time
+
+
+def oracle_sample_rate(cfg, steps, L=CPU_SAMPLE_L, budget_s=None):
+    """Time the FP64 oracle on an L^3 periodic sub-box of the workload (same N, nA, chi, dt,
+    relaxation times, inversion and Jacobi counts) for `steps` coupled steps from the seeded
+    initial state, stopping early once budget_s seconds have passed (if given).
+    Returns (site-updates/s, threads, sample description, steps timed, seconds)."""
     import numpy as np
 
     import oracle
     from paper_1204_2088_gb300 import inputs
     oracle.build()
-    probe = dict(cfg, grid=(16, 16, 16))
-    phi = inputs.initial_fields(probe)
-    t = time.perf_counter()
-    oracle.step(probe, phi, np.zeros_like(phi), None, phi.reshape(2, -1).sum(1))
-    per_site = (time.perf_counter() - t) / 16 ** 3
-    n = steps or 3
-    L = 16
-    for cand in (24, 32, 40, 48, 64, 80, 96, 128):
-        if per_site * cand ** 3 * n <= budget_s:
-            L = cand
     sample = dict(cfg, grid=(L, L, L))
     phi = inputs.initial_fields(sample)
     U = np.zeros_like(phi)
     pop = None
     m0 = phi.reshape(2, -1).sum(1)
+    n = 0
     t = time.perf_counter()
-    for _ in range(n):
+    while n < steps:
         st = oracle.step(sample, phi, U, pop, m0)
         phi, U, pop = st["phi"], st["U"], st["pop"]
+        n += 1
+        if budget_s is not None and time.perf_counter() - t > budget_s:
+            break
     dt = time.perf_counter() - t
     desc = (f"{n} coupled steps of the workload on a {L}^3 periodic sub-box (same N, nA, chi, dt, "
             f"tau_s, tau_b, {cfg['ncg_iters']} inversion iterations, {cfg['cn_sweeps']} Jacobi sweeps), "
@@ -99,25 +96,38 @@ def oracle_sample_rate(cfg, budget_s, steps=None):
     return L ** 3 * n / dt, oracle.num_threads(), desc, n, dt
 
 
-def _cpu_child(cfg, budget, q):
+def _cpu_child(cfg, steps, threads, q):
     try:
-        q.put(oracle_sample_rate(cfg, budget))
+        if threads:
+            os.environ["OMP_NUM_THREADS"] = str(threads)
+        q.put(oracle_sample_rate(cfg, steps))
     except Exception as e:  # reported, not raised
         q.put(repr(e))
 
 
-def cpu_baseline_spawned(cfg, budget):
+def _cpu_spawned(cfg, steps, threads=None):
     import multiprocessing as mp
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
-    p = ctx.Process(target=_cpu_child, args=(cfg, budget, q))
+    p = ctx.Process(target=_cpu_child, args=(cfg, steps, threads, q))
     p.start()
-    res = q.get(timeout=600)
+    res = q.get(timeout=900)
     p.join(60)
-    if isinstance(res, str):
+    return None if isinstance(res, str) else res
+
+
+def cpu_baseline_spawned(cfg, steps=10):
+    """The oracle on the host cores, all threads, and on one thread (one step), on the same sub-box
+    the reference arm times (processes started with spawn, after the GPU work)."""
+    res = _cpu_spawned(cfg, steps)
+    if res is None:
         return None
     rate, cores, desc, _, _ = res
-    return {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc}
+    out = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc}
+    one = _cpu_spawned(cfg, 1, threads=1)
+    if one is not None:
+        out["single_thread"] = {"value": one[0], "unit": UNIT, "cores": one[1], "sample": one[2]}
+    return out
 
 
 def run_reference(a):
@@ -126,15 +136,16 @@ def run_reference(a):
         return 0
     from paper_1204_2088_gb300 import inputs
     cfg = inputs.workload(WORKLOAD)
-    total_budget = 150.0
-    per_step_budget = total_budget / max(1, a.steps + a.warmup)
-    import numpy as np  # noqa: F401
-    # warm-up steps run on the same sample size as the timed ones
-    rate, cores, desc, n, dt = oracle_sample_rate(cfg, per_step_budget * a.steps, steps=a.steps)
+    # warm-up steps are not needed by the CPU code; the timed steps run on the same sub-box as the
+    # cpu_baseline leg, within about 150 s in all
+    rate, cores, desc, n, dt = oracle_sample_rate(cfg, a.steps, budget_s=150.0)
+    V = int(cfg["grid"][0] * cfg["grid"][1] * cfg["grid"][2])
     line = {"metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": a.gpus, "steps": a.steps,
-            "warmup": a.warmup, "ms_per_step": 1e3 * dt / n, "higher_is_better": True, "scaling": "weak",
+            "warmup": a.warmup, "ms_per_step": 1e3 * V / rate, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": workload_config(cfg),
             "impl": "reference",
+            "sample": {"edge": CPU_SAMPLE_L, "steps_timed": n, "ms_per_step": 1e3 * dt / n,
+                       "note": "ms_per_step above is the full-size step at the sample's rate per site"},
             "cpu_baseline": {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc},
             "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -342,6 +353,58 @@ def residual_stop_form(cfg, dev, phi0, timed, world, steps):
     return out
 
 
+def self_consistent_form(cfg, dev, phi0, timed, world, steps, tol=1e-5, cap=32):
+    """The FP32 step with the inversion run to self-consistency: residual stop at the FP32
+    tolerance max|phi* - phi[U]| < 1e-5 with a cap of 32 iterations.  Measured early after the quench
+    (the first steps, from the cold start U = 0, need the cap) and from step 30 and step 300 on;
+    the iterations actually run and the largest residual at the end of a step are reported."""
+    from paper_1204_2088_gb300 import dscf, replicas
+    V = int(cfg["grid"][0] * cfg["grid"][1] * cfg["grid"][2])
+    ctx = dscf.Context(dict(cfg, ncg_iters=cap), dscf.FP32, device=dev)
+    ctx.set(dscf.PHI, phi0)
+    ctx.set_inversion_tol(tol)
+    out = {"unit": UNIT, "steps": steps, "tol": tol, "ncg_cap": cap}
+    done = 0
+    for start in (30, 300):
+        ctx.step(start - done)
+        ms = timed(lambda: ctx.step(steps))
+        its, gend = [], []
+        for _ in range(steps):   # iterations actually run, one step at a time (untimed)
+            ctx.step(1)
+            d = ctx.diagnostics()
+            its.append(d["ncg_iters"])
+            gend.append(d["gmax_end"])
+        ctx.status()
+        done = start + 2 * steps
+        out[f"from_step_{start}"] = {"value": replicas.aggregate_rate([V * steps] * world, [ms]),
+                                     "ms_per_step": ms / steps, "mean_ncg_iters": sum(its) / len(its),
+                                     "max_ncg_iters": max(its), "max_gmax_end": max(gend)}
+    ctx.close()
+    return out
+
+
+def solution_form(dev, timed, rank, world, steps):
+    """The amphiphilic diblock in solvent at 128^3 (phi_p = 0.12, f_A = 0.3, N = 48, chi_AB N = 30,
+    chi_BS N = 35, tau_s = 0.8, tau_b = 1.2, three species), FP32, with the tuning the autotuner
+    picks for it."""
+    import numpy as np
+    import torch
+
+    from paper_1204_2088_gb300 import dscf, inputs, replicas
+    cfg = inputs.workload("solution128", seed=replicas.rank_seed(4, rank))
+    V = int(np.prod(cfg["grid"]))
+    ctx = dscf.Context(cfg, dscf.FP32, device=dev)
+    ctx.set(dscf.PHI, torch.from_numpy(inputs.initial_fields(cfg)).float().to(dev))
+    ctx.step(3)
+    ms = timed(lambda: ctx.step(steps))
+    ctx.status()
+    d = ctx.diagnostics()
+    ctx.close()
+    return {"value": replicas.aggregate_rate([V * steps] * world, [ms]), "unit": UNIT, "ms_per_step": ms / steps,
+            "steps": steps, "workload": "solution128: 128^3, N=48, nA=14, phi_p=0.12, three species",
+            "zc": d["zc"], "kfuse": d["kfuse"], "ncg_iters": cfg["ncg_iters"]}
+
+
 def noise_form(cfg, dev, phi0, timed, world, steps):
     """The FP32 step with thermal noise (Omega = 400 as in the paper's runs): the composition flux
     noise of Eq. 5 and the fluctuating LB collision of Eq. 13."""
@@ -357,6 +420,34 @@ def noise_form(cfg, dev, phi0, timed, world, steps):
     ctx.close()
     return {"value": replicas.aggregate_rate([V * steps] * world, [ms]), "unit": UNIT, "ms_per_step": ms / steps,
             "steps": steps, "omega": 400.0, "lb_noise": True, "lb_momentum": d["lb_momentum"]}
+
+
+def net_forward_form(dev, timed, reps=10):
+    """The predictor network's forward pass alone at 128^3 (batch 1), on the tcgen05 path and on
+    the mma.sync path: mean time of one forward (CUDA events, after a warm-up pass) and the rate in
+    TFLOP/s counted on the useful channels (2 x 125 x (2 x 32 + 32 x 32 + 32 x 2) FLOP per site)
+    and on the padded ones the kernels compute (2 x 125 x (16 x 32 + 32 x 32 + 32 x 16))."""
+    import torch
+
+    from paper_1204_2088_gb300 import dscf
+    nx = ny = nz = 128
+    net = dscf.Net((nx, ny, nz), 1, seed=1, device=dev)
+    g = torch.Generator(device=dev).manual_seed(1)
+    U = (torch.randn(1, 2, nz, ny, nx, device=dev, generator=g) * 0.1).float()
+    phibar = [0.5, 0.5]
+    V = nx * ny * nz
+    useful = 2.0 * V * 125 * (2 * 32 + 32 * 32 + 32 * 2)
+    padded = 2.0 * V * 125 * (16 * 32 + 32 * 32 + 32 * 16)
+    out = {"grid": [nx, ny, nz], "reps": reps}
+    for path in (0, 1):
+        net.set_tensor_path(path)
+        net.forward(U, phibar)
+        ms = timed(lambda: [net.forward(U, phibar) for _ in range(reps)]) / reps
+        name = "tcgen05" if net.tensor_path() == 2 else "mma.sync"
+        out[name] = {"ms": ms, "tflops_useful": useful / ms / 1e9, "tflops_padded": padded / ms / 1e9}
+    net.status()
+    net.close()
+    return out
 
 
 def batch48_form(dev, timed, rank, world, steps):
@@ -475,7 +566,13 @@ def run_ours(a):
         torch.cuda.synchronize(dev)
         return max_over_ranks(e0.elapsed_time(e1))
 
+    alu = None
     if "fp64" in want:
+        # measured CUDA-core FMA peaks (the library's dscf_fma_peak), clocks sampled meanwhile
+        csamp = ClockSampler(local)
+        csamp.start()
+        alu = {"fp32_tflops": dscf.fma_peak(dscf.FP32), "fp64_tflops": dscf.fma_peak(dscf.FP64)}
+        alu["clocks"] = csamp.stop()
         k64 = max(2, min(10, a.steps // 10))
         c64 = dscf.Context(cfg, dscf.FP64, device=dev)
         c64.set(dscf.PHI, phi0.double())
@@ -492,6 +589,8 @@ def run_ours(a):
                          "hbm": {"alg_bytes_per_site": b64, "GBps": b64 * V / s64 / 1e9,
                                  "frac": b64 * V / s64 / 1e9 / peaks()[0]},
                          "fp64_alu": {"prop_flops_per_site": f64, "TFLOPs": f64 * V / s64 / 1e12,
+                                      "frac_of_measured": f64 * V / s64 / 1e12 / alu["fp64_tflops"],
+                                      "measured_peak_TFLOPs": alu["fp64_tflops"],
                                       "frac_of_nominal": f64 * V / s64 / 1e12 / FP64_NOMINAL_TFLOPS,
                                       "nominal_TFLOPs": FP64_NOMINAL_TFLOPS}}
         c64.close()
@@ -500,10 +599,16 @@ def run_ours(a):
         forms["fp32_noise"] = noise_form(cfg, dev, phi0, timed, world, max(10, min(a.steps, 20)))
     if "fp32_residual_stop" in want:
         forms["fp32_residual_stop"] = residual_stop_form(cfg, dev, phi0, timed, world, max(10, min(a.steps, 20)))
+    if "fp32_self_consistent" in want:
+        forms["fp32_self_consistent"] = self_consistent_form(cfg, dev, phi0, timed, world, max(10, min(a.steps, 20)))
+    if "solution128" in want:
+        forms["solution128"] = solution_form(dev, timed, rank, world, max(10, min(a.steps, 20)))
     if "fp32_learned" in want:
         forms["fp32_learned"] = learned_form(cfg, dev, phi0, timed, world, max(20, min(a.steps, 40)))
     if "batch48" in want:
         forms["batch48"] = batch48_form(dev, timed, rank, world, max(3, min(a.steps // 10, 10)))
+    if "net_forward" in want:
+        forms["net_forward"] = net_forward_form(dev, timed)
 
     hbm, peak_kind = peaks()
     # Dominant kernel: the propagator sweeps.  The unit is one contour step (the autotuner runs
@@ -533,7 +638,7 @@ def run_ours(a):
 
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
-        cpu = cpu_baseline_spawned(cfg, a.cpu_budget)
+        cpu = cpu_baseline_spawned(cfg)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
@@ -541,6 +646,7 @@ def run_ours(a):
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": workload_config(cfg), "e2e": e2e, "gpu_launches": int(launches * a.steps),
                 "roofline": roof, "cpu_baseline": cpu, "clocks": clk, "forms": forms, "kernels": kernels,
+                "alu_peaks": alu,
                 "ncg": {"iters": diag["ncg_iters"], "line_search_evals_per_iter": 1,
                         "gmax_start": diag["gmax_start"], "gmax_end": diag["gmax_end"]},
                 "umax": diag["umax"]}

@@ -165,9 +165,6 @@ int dscf_set_fields(dscf_ctx* ctx, int32_t which, const void* src, int32_t on_ho
  *  follow the inversion of the last step taken (a predictor step may use fewer iterations). */
 int dscf_diagnostics(dscf_ctx* ctx, int32_t replica, double* out);
 
-/* Synchronise the stream and return the device status word as an error code (DSCF_OK,
- * DSCF_ERR_TIMEOUT if a persistent sweep gave up a bounded wait, DSCF_ERR_NUMERIC) or
- * DSCF_ERR_CUDA if a kernel failed. */
 /* Observables of replica `replica` at the current state (Sec. 3; Eq. 1 restated in volume
  * fractions with constants dropped): out[0] free energy per site
  *   F = -(phi_p / N) ln Q - (1 - phi_p) ln <e^{-U_S}> - <sum_I U_I phi_I>
@@ -198,6 +195,9 @@ int dscf_minkowski(dscf_ctx* ctx, int32_t replica, int32_t species, double thres
  * settle within 64 (nx + ny + nz) + 1024 sweeps. */
 int dscf_trapped_solvent(dscf_ctx* ctx, int32_t replica, double threshold, double* out);
 
+/* Synchronise the stream and return the device status word as an error code (DSCF_OK,
+ * DSCF_ERR_TIMEOUT if a persistent sweep gave up a bounded wait, DSCF_ERR_NUMERIC) or
+ * DSCF_ERR_CUDA if a kernel failed. */
 int dscf_status(dscf_ctx* ctx);
 
 /* Release host-side state (graph, capture stream).  The workspace stays the caller's. */
@@ -261,6 +261,14 @@ int dscf_set_inversion_tol(dscf_ctx* ctx, double tol);
 int dscf_set_wait_limit(dscf_ctx* ctx, int32_t polls);
 int dscf_inject_lag(dscf_ctx* ctx, int32_t brick);
 
+/* Measured fused multiply-add throughput of the CUDA cores of the current device, in the given
+ * precision (a measurement helper for the arithmetic roofline of the kernels above; the paper has
+ * no counterpart): eight independent FMA chains per thread on 8 CTAs of 256 threads per SM, timed
+ * with CUDA events on `stream` (cudaStream_t or NULL), the best of three runs after a warm-up run
+ * (each a few tens of milliseconds).  *tflops receives 2 x FMAs / second / 1e12.  Synchronises the
+ * stream.  DSCF_ERR_ARG for a bad precision or NULL output, DSCF_ERR_CUDA if a launch fails. */
+int dscf_fma_peak(int32_t precision, void* stream, double* tflops);
+
 /* Timing probe.  enable != 0 makes the next dscf_step capture CUDA events (created by the
  * library) into the step graph: around the 2N contour-sweep launches of the first gradient
  * evaluation of the step, around the LB collide-stream launch, and around the whole step.
@@ -279,7 +287,8 @@ int dscf_probe_ms(dscf_ctx* ctx, float* ms);
  *
  * p: parameters of one replica (host memory; only the chain, stencil and composition fields
  * matter).  U_in, phi_out: device pointers, [ns][V] in the given precision; their device is the
- * one used.  stream: cudaStream_t or NULL.  Asynchronous on the stream.
+ * one used (the call switches to it and restores the calling thread's current device before it
+ * returns).  stream: cudaStream_t or NULL, a stream of that device.  Asynchronous on the stream.
  *
  * Neither the library nor the caller allocates anything: all scratch (propagator stack,
  * Boltzmann factors, quadratures, partial sums) lives in one file-scope device array of
@@ -342,8 +351,9 @@ int dscf_net_status(dscf_net* net);
 int dscf_net_free(dscf_net* net);
 
 /* Use a trained network (same grid as the context, batch 1) as the density map inside the
- * self-consistent inversion of dscf_step (the composition-to-potential solve of Eq. 6 with
- * phi[U] of Eqs. 8-10 replaced by the network): one FP32 melt replica only.
+ * self-consistent inversion of dscf_step (the determination of the potentials from the
+ * compositions, Sec. 2 after Eq. 17, with the density functional phi[U] of Eq. 2, evaluated by
+ * Eqs. 16-17, replaced by the network): one FP32 melt replica only.
  * Every corrector_every-th step (counted from this call, starting with the first) is exact and
  * judges the predictor (this synchronises): after a predictor step by that step's
  * self-consistency error ||phi[U] - phi*||_inf (exact densities at the potential the predictor

@@ -13,7 +13,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libdscf.so")
 BUILD = os.path.join(HERE, "_build")
-SOURCES = ["dscf_abi.cu", "dscf_prop.cu", "dscf_kern.cu", "dscf_static.cu", "dscf_pers.cu", "dscf_net.cu", "dscf_tc.cu"]
+SOURCES = ["dscf_abi.cu", "dscf_prop.cu", "dscf_kern.cu", "dscf_static.cu", "dscf_pers.cu", "dscf_net.cu", "dscf_tc.cu",
+           "dscf_peak.cu"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 FLAGS = ["-O3", "-std=c++17", "-gencode", "arch=compute_103a,code=sm_103a", "-lineinfo",
          "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]

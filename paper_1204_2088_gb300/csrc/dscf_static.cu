@@ -38,8 +38,29 @@ __global__ void k_put_rep(Rep* dst, Rep r) { *dst = r; }
 
 }  // namespace
 
+namespace {
+int densities_static_on(const dscf_params* p, int32_t precision, const void* U_in, void* phi_out, void* stream);
+}
+
+// Runs on the device that holds U_in and leaves the calling thread's current device as it found it.
 extern "C" int dscf_densities_static(const dscf_params* p, int32_t precision, const void* U_in, void* phi_out,
                                      void* stream) {
+    int prev = -1;
+    if (cudaGetDevice(&prev) != cudaSuccess) {
+        cudaGetLastError();
+        set_thread_error("dscf_densities_static: cudaGetDevice failed");
+        return DSCF_ERR_CUDA;
+    }
+    const int rc = densities_static_on(p, precision, U_in, phi_out, stream);
+    if (cudaSetDevice(prev) != cudaSuccess && rc == DSCF_OK) {
+        set_thread_error("dscf_densities_static: restoring the caller's device failed");
+        return DSCF_ERR_CUDA;
+    }
+    return rc;
+}
+
+namespace {
+int densities_static_on(const dscf_params* p, int32_t precision, const void* U_in, void* phi_out, void* stream) {
     if (!p || !U_in || !phi_out) {
         set_thread_error("dscf_densities_static: NULL argument");
         return DSCF_ERR_ARG;
@@ -171,3 +192,4 @@ extern "C" int dscf_densities_static(const dscf_params* p, int32_t precision, co
     }
     return DSCF_OK;
 }
+}  // namespace

@@ -98,6 +98,7 @@ def load():
         "dscf_net_tensor_path": (i32, [vp]),
         "dscf_net_status": (ctypes.c_int, [vp]),
         "dscf_inject_lag": (ctypes.c_int, [vp, i32]),
+        "dscf_fma_peak": (ctypes.c_int, [i32, vp, ctypes.POINTER(ctypes.c_double)]),
     }
     for name, (res, args) in sigs.items():
         fn = getattr(lib, name)
@@ -159,6 +160,17 @@ def densities_static(cfg: dict, U: torch.Tensor, out: torch.Tensor, precision=FP
     if rc != DSCF_OK:
         raise DSCFError(rc, lib.dscf_last_error(None).decode())
     return out
+
+
+def fma_peak(precision=FP32, stream=None) -> float:
+    """Measured FMA throughput of the current device's CUDA cores in TFLOP/s (dscf_fma_peak)."""
+    lib = load()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    out = ctypes.c_double()
+    rc = lib.dscf_fma_peak(int(precision), ctypes.c_void_p(s.cuda_stream), ctypes.byref(out))
+    if rc != DSCF_OK:
+        raise DSCFError(rc, lib.dscf_last_error(None).decode())
+    return out.value
 
 
 def _tuning_key(cfgs, precision, device) -> str:

@@ -8,7 +8,7 @@ diffusion-only model, u = 0), with the same seeds and noise.
 
 Systems (synthetic stand-ins for the paper's runs, Sec. 3):
   A8B8    symmetric melt, N = 16, f = 0.5, chi^0_AB = 1.0 (chi N = 16): lamellae
-  A5B11   asymmetric melt, N = 16, f = 5/16, chi^0_AB = 1.0: cylinders
+  A5B11   asymmetric melt, N = 16, f = 5/16, chi^0_AB = 1.3 (chi N = 20.8): cylinders (Fig. 2b)
   A2B8S   A2B8 in solvent, copolymer fraction 0.2, chi^0_AB = 2.3, chi^0_BS = 2.4, chi^0_AS = 0.25
 Protocol: 48^3 (the paper's Fig. 2 box), tau_s = tau_b = 1, six inversion iterations per step,
 dt = 0.1 tau, no thermal noise by default (--omega sets the noise parameter, --lb-noise adds the LB
@@ -43,7 +43,7 @@ def system_cfg(name: str, grid: int, seed: int, hydro: int) -> dict:
     if name == "A8B8":
         cfg = inputs.melt(g, 16, 0.5, 16.0, 1.0, 1.0, 0.01, seed, dt=0.1, hydro=hydro, ncg_iters=6, name=name)
     elif name == "A5B11":
-        cfg = inputs.melt(g, 16, 5 / 16, 16.0, 1.0, 1.0, 0.01, seed, dt=0.1, hydro=hydro, ncg_iters=6, name=name)
+        cfg = inputs.melt(g, 16, 5 / 16, 20.8, 1.0, 1.0, 0.01, seed, dt=0.1, hydro=hydro, ncg_iters=6, name=name)
     elif name == "A2B8S":
         cfg = inputs.solution(g, 10, 0.2, 0.2, 23.0, 24.0, 2.5, 1.0, 1.0, 0.01, seed, dt=0.1, hydro=hydro,
                               ncg_iters=6, name=name)

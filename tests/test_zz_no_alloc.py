@@ -1,12 +1,14 @@
 """The allocation-free density map (dscf_densities_static), called through the C ABI.
 
 It serves callers that cannot allocate device memory; it must give the same densities as the
-context-based dscf_densities on consecutive calls that reuse its fixed scratch array, and refuse
-problems larger than that array.  This file is collected last on purpose."""
+context-based dscf_densities (and as the FP64 oracle) on consecutive calls that reuse its fixed
+scratch array, leave the caller's current device alone, and refuse problems larger than that
+array.  This file is collected last on purpose."""
 import numpy as np
 import pytest
 import torch
 
+import oracle
 from paper_1204_2088_gb300 import build, dscf, inputs
 
 pytestmark = pytest.mark.gpu
@@ -37,11 +39,16 @@ def test_static_matches_context_entry_point_on_consecutive_calls(precision, tol)
         shape = (cfg["ns"], nz, ny, nx)
         U = torch.from_numpy(inputs.random_field(shape, seed=seed, scale=0.5)).to("cuda", dtype)
         out = torch.empty(shape, dtype=dtype, device="cuda")
+        dev_before = torch.cuda.current_device()
         dscf.densities_static(cfg, U, out, precision)
+        assert torch.cuda.current_device() == dev_before
         ref = dscf.Context(cfg, precision).densities(U)
         torch.cuda.synchronize()
         a, b = out.double().cpu().numpy(), ref.double().cpu().numpy()
         assert np.abs(a - b).max() <= tol * np.abs(b).max()
+        # and against the FP64 oracle on the same (rounded) potentials
+        o = oracle.densities(cfg, U.double().cpu().numpy())[0]
+        assert np.abs(a - o).max() <= tol * np.abs(o).max()
 
 
 def test_static_rejects_problems_beyond_its_scratch():
