@@ -17,7 +17,9 @@
 //   barrier, release store of the brick's step counter; then the forward interior stores and the
 //   x pass of the new values, in registers.
 // q is accumulated in registers over a whole block of beads and written once; nothing is
-// read-modify-written per step.  Every wait is bounded: on timeout the CTA sets a status bit and a
+// read-modify-written per step.  Each 1-D pass of the separable stencil is two packed-pair
+// operations per two sites (f32x2 add and fma), with the centre weight folded into the Boltzmann
+// factors.  Every wait is bounded: on timeout the CTA sets a status bit and a
 // global abort flag that makes every other CTA stop waiting, so the launch always finishes.
 #include "dscf_internal.cuh"
 
@@ -71,6 +73,37 @@ __device__ __forceinline__ bool bar_test(unsigned long long* bar, unsigned parit
         : "r"(saddr(bar)), "r"(parity)
         : "memory");
     return done != 0;
+}
+
+// Packed FP32 pairs (sm_100+ f32x2 arithmetic): two lanes of a float4 per instruction.
+__device__ __forceinline__ unsigned long long pk2(float a, float b) {
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void upk2(unsigned long long v, float& a, float& b) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+}
+__device__ __forceinline__ unsigned long long add2(unsigned long long a, unsigned long long b) {
+    unsigned long long r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ unsigned long long mul2(unsigned long long a, unsigned long long b) {
+    unsigned long long r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ unsigned long long fma2(unsigned long long a, unsigned long long b, unsigned long long c) {
+    unsigned long long r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
+__device__ __forceinline__ float4 f4(unsigned long long lo, unsigned long long hi) {
+    float4 o;
+    upk2(lo, o.x, o.y);
+    upk2(hi, o.z, o.w);
+    return o;
 }
 
 struct PersCtl {
@@ -154,7 +187,12 @@ __global__ void __launch_bounds__(32 * NW, 16 / NW) k_prop_pers(const Rep* __res
     const int by = b % nby, bz = b / nby;
     const int y0 = by * PBY, z0 = bz * BZ;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const float al = (float)R.alpha, be = (float)(1.0 - 2.0 * R.alpha);
+    // Each 1-D pass is applied as c + r (a + d) with r = alpha / (1 - 2 alpha), i.e. the
+    // stencil's pass divided by its centre weight be = 1 - 2 alpha; the three passes then give
+    // sigma / be^3, and be^3 is folded into the Boltzmann factors (and into q at its write-out).
+    const double be_d = 1.0 - 2.0 * R.alpha;
+    const float rr = (float)(R.alpha / be_d), be3 = (float)(be_d * be_d * be_d);
+    const unsigned long long rr2 = pk2(rr, rr), be32 = pk2(be3, be3);
     if (threadIdx.x < 8) {
         const int k = threadIdx.x < 4 ? threadIdx.x : threadIdx.x + 1;   // skip the centre
         const int dy = k % 3 - 1, dz = k / 3 - 1;
@@ -180,23 +218,17 @@ __global__ void __launch_bounds__(32 * NW, 16 / NW) k_prop_pers(const Rep* __res
     const int c0 = ctl.flags[(size_t)b * kFlagStride];   // step counters of all bricks are equal at launch
     bool aborted = ld_acquire(ctl.abort) != 0;
 
-    auto xpass = [&](VT v) -> VT {      // x pass of a periodic row held by the warp
+    auto xpass = [&](VT v) -> VT {      // x pass of a periodic row held by the warp: v + r (left + right)
         const float lv = __shfl_sync(0xffffffffu, v.w, (lane + 31) & 31);
         const float rv = __shfl_sync(0xffffffffu, v.x, (lane + 1) & 31);
-        VT o;
-        o.x = be * v.x + al * (lv + v.y);
-        o.y = be * v.y + al * (v.x + v.z);
-        o.z = be * v.z + al * (v.y + v.w);
-        o.w = be * v.w + al * (v.z + rv);
-        return o;
+        const unsigned long long mid = pk2(v.y, v.z);
+        const unsigned long long tlo = add2(pk2(lv, v.x), mid), thi = add2(mid, pk2(v.w, rv));
+        return f4(fma2(rr2, tlo, pk2(v.x, v.y)), fma2(rr2, thi, pk2(v.z, v.w)));
     };
-    auto mix = [&](VT a, VT c, VT d) -> VT {   // be c + al (a + d)
-        VT o;
-        o.x = be * c.x + al * (a.x + d.x);
-        o.y = be * c.y + al * (a.y + d.y);
-        o.z = be * c.z + al * (a.z + d.z);
-        o.w = be * c.w + al * (a.w + d.w);
-        return o;
+    auto mix = [&](VT a, VT c, VT d) -> VT {   // c + r (a + d)
+        const unsigned long long tlo = add2(pk2(a.x, a.y), pk2(d.x, d.y));
+        const unsigned long long thi = add2(pk2(a.z, a.w), pk2(d.z, d.w));
+        return f4(fma2(rr2, tlo, pk2(c.x, c.y)), fma2(rr2, thi, pk2(c.z, c.w)));
     };
     auto ys = [&](int pl, int r) { return YS + ((pl + 1) * PBY + r) * W + VEC * lane; };
     const bool face_plane = (w == 0 || w == BZ - 1);
@@ -208,8 +240,12 @@ __global__ void __launch_bounds__(32 * NW, 16 / NW) k_prop_pers(const Rep* __res
     auto load_e = [&](int species) {
         const float* E = (const float*)R.E + (size_t)species * V;
 #pragma unroll
-        for (int r = 0; r < PBY; ++r) e[r] = *(const VT*)(E + own0 + (size_t)r * W);
+        for (int r = 0; r < PBY; ++r) {
+            const VT v = *(const VT*)(E + own0 + (size_t)r * W);
+            e[r] = f4(mul2(be32, pk2(v.x, v.y)), mul2(be32, pk2(v.z, v.w)));
+        }
     };
+    auto q_out = [&](VT v) -> VT { return f4(mul2(be32, pk2(v.x, v.y)), mul2(be32, pk2(v.z, v.w))); };
     // backward: G_s of the brick into GS, issued by thread 0 as one bulk copy per plane (the
     // plane's PBY rows are contiguous in memory and in GS); the copies complete on gs_bar
     unsigned gs_phase = 0;
@@ -242,8 +278,8 @@ __global__ void __launch_bounds__(32 * NW, 16 / NW) k_prop_pers(const Rep* __res
         gs_pending = false;
     };
 
-    // the first input (G_0 = 1, or G+_{N+1} = 1): its x pass is be + 2 al everywhere
-    const float one = be + 2.0f * al;
+    // the first input (G_0 = 1, or G+_{N+1} = 1): its x pass is 1 + 2 r everywhere
+    const float one = 1.0f + 2.0f * rr;
     VT xf[PBY];
 #pragma unroll
     for (int r = 0; r < PBY; ++r) xf[r] = make_float4(one, one, one, one);
@@ -269,7 +305,7 @@ __global__ void __launch_bounds__(32 * NW, 16 / NW) k_prop_pers(const Rep* __res
                 float* q = (float*)R.q + (size_t)species * V;
 #pragma unroll
                 for (int r = 0; r < PBY; ++r) {
-                    *(VT*)(q + own0 + (size_t)r * W) = qacc[r];
+                    *(VT*)(q + own0 + (size_t)r * W) = q_out(qacc[r]);
                     qacc[r] = make_float4(0.f, 0.f, 0.f, 0.f);
                 }
             }
@@ -318,17 +354,14 @@ __global__ void __launch_bounds__(32 * NW, 16 / NW) k_prop_pers(const Rep* __res
         VT out[PBY];
 #pragma unroll
         for (int r = 0; r < PBY; ++r) {
-            const VT sg = mix(*(const VT*)ys(w - 1, r), xf[r], *(const VT*)ys(w + 1, r));
-            out[r].x = e[r].x * sg.x;
-            out[r].y = e[r].y * sg.y;
-            out[r].z = e[r].z * sg.z;
-            out[r].w = e[r].w * sg.w;
+            const VT a = *(const VT*)ys(w - 1, r), d = *(const VT*)ys(w + 1, r);
+            const unsigned long long sglo = fma2(rr2, add2(pk2(a.x, a.y), pk2(d.x, d.y)), pk2(xf[r].x, xf[r].y));
+            const unsigned long long sghi = fma2(rr2, add2(pk2(a.z, a.w), pk2(d.z, d.w)), pk2(xf[r].z, xf[r].w));
+            out[r] = f4(mul2(pk2(e[r].x, e[r].y), sglo), mul2(pk2(e[r].z, e[r].w), sghi));
             if (BWD) {
                 const VT g = *(const VT*)(GS + (w * PBY + r) * W + VEC * lane);
-                qacc[r].x += g.x * sg.x;
-                qacc[r].y += g.y * sg.y;
-                qacc[r].z += g.z * sg.z;
-                qacc[r].w += g.w * sg.w;
+                qacc[r] = f4(fma2(pk2(g.x, g.y), sglo, pk2(qacc[r].x, qacc[r].y)),
+                             fma2(pk2(g.z, g.w), sghi, pk2(qacc[r].z, qacc[r].w)));
             } else if (s == N) {
                 qsum += (out[r].x + out[r].y) + (out[r].z + out[r].w);
             }
@@ -354,7 +387,7 @@ __global__ void __launch_bounds__(32 * NW, 16 / NW) k_prop_pers(const Rep* __res
         }
         float* q = (float*)R.q + (size_t)species * V;
 #pragma unroll
-        for (int r = 0; r < PBY; ++r) *(VT*)(q + own0 + (size_t)r * W) = qacc[r];
+        for (int r = 0; r < PBY; ++r) *(VT*)(q + own0 + (size_t)r * W) = q_out(qacc[r]);
     } else {
         const double t = block_sum((double)qsum, sh);
         if (threadIdx.x == 0) slot(R, P_Q)[b] = t;
