@@ -355,9 +355,10 @@ def residual_stop_form(cfg, dev, phi0, timed, world, tuning, steps):
 
 def self_consistent_form(cfg, dev, phi0, timed, world, tuning, steps, tol=1e-5, cap=32):
     """The FP32 step with the inversion run to self-consistency: residual stop at the FP32
-    tolerance max|phi* - phi[U]| < 1e-5 with a cap of 32 iterations.  Measured early after the quench
-    (the first steps, from the cold start U = 0, need the cap) and from step 30 and step 300 on;
-    the iterations actually run and the largest residual at the end of a step are reported."""
+    tolerance max|phi* - phi[U]| < 1e-5 with a cap of 32 iterations, measured from step 30 and from
+    step 300 after the quench (the first steps, from the cold start U = 0, need the cap).  Reported:
+    the rate, the iterations actually run (mean and largest), the largest residual at the end of a
+    step, and the whole step against the HBM roofline with the bytes of the iterations run."""
     from paper_1204_2088_gb300 import dscf, replicas
     V = int(cfg["grid"][0] * cfg["grid"][1] * cfg["grid"][2])
     ctx = dscf.Context(dict(cfg, ncg_iters=cap), dscf.FP32, device=dev, tuning=tuning)
@@ -365,6 +366,7 @@ def self_consistent_form(cfg, dev, phi0, timed, world, tuning, steps, tol=1e-5, 
     ctx.set_inversion_tol(tol)
     out = {"unit": UNIT, "steps": steps, "tol": tol, "ncg_cap": cap, "tuning": list(tuning)}
     done = 0
+    hbm = peaks()[0]
     for start in (30, 300):
         ctx.step(start - done)
         ms = timed(lambda: ctx.step(steps))
@@ -376,9 +378,13 @@ def self_consistent_form(cfg, dev, phi0, timed, world, tuning, steps, tol=1e-5, 
             gend.append(d["gmax_end"])
         ctx.status()
         done = start + 2 * steps
+        mean_it = sum(its) / len(its)
+        b = step_bytes_per_site(cfg["N"], mean_it, cfg["cn_sweeps"], cfg["hydro"])
+        gbps = b * V / (ms / steps * 1e-3) / 1e9
         out[f"from_step_{start}"] = {"value": replicas.aggregate_rate([V * steps] * world, [ms]),
-                                     "ms_per_step": ms / steps, "mean_ncg_iters": sum(its) / len(its),
-                                     "max_ncg_iters": max(its), "max_gmax_end": max(gend)}
+                                     "ms_per_step": ms / steps, "mean_ncg_iters": mean_it,
+                                     "max_ncg_iters": max(its), "max_gmax_end": max(gend),
+                                     "hbm": {"alg_bytes_per_site": b, "GBps": gbps, "frac": gbps / hbm}}
     ctx.close()
     return out
 

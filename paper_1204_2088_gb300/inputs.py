@@ -8,7 +8,8 @@ Random numbers: a counter-based SplitMix64 stream (Steele, Lea, Flood, "Fast spl
 pseudorandom number generators", OOPSLA 2014) turned into normal deviates by the
 Box-Muller transform, so the same (seed, index) gives the same number on any machine.
 
-Workloads (synthetic stand-ins for the paper's quenched melts and solutions, Sec. 3):
+Workloads (synthetic stand-ins for the paper's quenched melts and solutions, Sec. 3), all at
+dt = 0.1 tau:
   melt32      AB melt f=0.5, chi N=20, 32^3, N=32, tau_s=tau_b=1, noise 0.01, 200 steps
   melt128     AB melt f=0.3, chi N=25, 128^3, N=64, noise 0.01 (tau_s, tau_b chosen from
               {0.6,1,2} x {0.8,1.5})
@@ -80,15 +81,19 @@ def solution(grid, N, f, phi_p, chiN_AB, chiN_BS, chiN_AS=0.0, tau_s=0.8, tau_b=
     }
 
 
+WORKLOAD_DT = 0.1   # tau: the coupled explicit scheme's velocity stays bounded over long runs
+
+
 def workload(name: str, **over):
+    dt = WORKLOAD_DT
     if name == "melt32":
-        cfg = melt((32, 32, 32), 32, 0.5, 20.0, 1.0, 1.0, 0.01, 1, name=name)
+        cfg = melt((32, 32, 32), 32, 0.5, 20.0, 1.0, 1.0, 0.01, 1, dt=dt, name=name)
     elif name == "melt128":
-        cfg = melt((128, 128, 128), 64, 0.3, 25.0, 1.0, 0.8, 0.01, 11, name=name)
+        cfg = melt((128, 128, 128), 64, 0.3, 25.0, 1.0, 0.8, 0.01, 11, dt=dt, name=name)
     elif name == "solution128":
-        cfg = solution((128, 128, 128), 48, 0.3, 0.12, 30.0, 35.0, 0.0, name=name)
+        cfg = solution((128, 128, 128), 48, 0.3, 0.12, 30.0, 35.0, 0.0, dt=dt, name=name)
     elif name == "melt256":
-        cfg = melt((256, 256, 256), 64, 0.5, 20.0, 1.0, 1.0, 0.01, 5, name=name)
+        cfg = melt((256, 256, 256), 64, 0.5, 20.0, 1.0, 1.0, 0.01, 5, dt=dt, name=name)
     else:
         raise KeyError(name)
     cfg.update(over)
@@ -105,7 +110,7 @@ def batch48(**over):
     reps = []
     for r, L in enumerate(sizes):
         cfg = melt((L, L, L), Ns[r % 3], fs[r % 3], chis[(r // 3) % 3], tss[r % 3], tbs[r % 2],
-                   0.01, 100 + r, name=f"batch48[{r}]")
+                   0.01, 100 + r, dt=WORKLOAD_DT, name=f"batch48[{r}]")
         cfg.update(over)
         reps.append(cfg)
     return reps
