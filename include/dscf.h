@@ -247,6 +247,16 @@ int dscf_set_noise(dscf_ctx* ctx, double omega, int32_t lb_noise, uint64_t seed)
  * negative or non-finite tol, DSCF_ERR_CUDA if the graph cannot be built. */
 int dscf_set_inversion_tol(dscf_ctx* ctx, double tol);
 
+/* Starting point of the inversion (step 1; the paper does not give it).  mode 0 (the default): the
+ * previous step's potentials U^{n-1}.  mode 1: their linear extrapolation in time,
+ * 2 U^{n-1} - U^{n-2}, once two steps since the last dscf_set_fields of PHI or U have produced
+ * potentials (before that, U^{n-1}); the densities at the starting point are evaluated first, one
+ * extra density evaluation per step.  The extrapolation makes the starting residual second order in
+ * dt instead of first, so with the residual stop (dscf_set_inversion_tol) fewer iterations are
+ * needed; the potentials the inversion converges to do not depend on the start.  Synchronises and
+ * re-captures the step graph.  DSCF_ERR_ARG for another mode. */
+int dscf_set_warm_start(dscf_ctx* ctx, int32_t mode);
+
 /* Failure detection of the persistent sweeps.  Every wait of a persistent sweep on a
  * neighbouring brick is bounded by `polls` polls (default 4194304, several seconds; each poll is
  * an acquire load of the neighbour's step counter followed by a short sleep).  A CTA that runs out

@@ -44,7 +44,7 @@ class Params(ctypes.Structure):
         ("tau_s", ctypes.c_double), ("tau_b", ctypes.c_double), ("rho0", ctypes.c_double),
         ("hydro", ctypes.c_int32), ("ncg_iters", ctypes.c_int32), ("cn_sweeps", ctypes.c_int32),
         ("phi_floor", ctypes.c_double), ("ncg_tol", ctypes.c_double),
-        ("omega", ctypes.c_double), ("lb_noise", ctypes.c_int32), ("pad_", ctypes.c_int32),
+        ("omega", ctypes.c_double), ("lb_noise", ctypes.c_int32), ("warm_extrap", ctypes.c_int32),
         ("seed", ctypes.c_uint64), ("step", ctypes.c_int64),
     ]
 
@@ -78,7 +78,8 @@ def lib():
             "or_lb_equilibrium": (None, [ctypes.c_double, D, D]),
             "or_lb_step": (None, [P, D, D, D, D]),
             "or_cd_step": (None, [P, D, D, D, D, D]),
-            "or_step": (None, [P, D, D, D, D, D, D, D, D]),
+            "or_step": (None, [P, D, D, D, D, D, D, D, D, D]),
+            "or_extrapolate": (None, [P, D, D]),
             "or_free_energy": (ctypes.c_double, [P, D, D]),
             "or_order_parameter": (ctypes.c_double, [P, D]),
             "or_segregation": (ctypes.c_double, [P, D]),
@@ -121,6 +122,7 @@ def make_params(cfg: dict) -> Params:
     p.omega = cfg.get("omega", 0.0)          # thermal noise (0: none)
     p.lb_noise = cfg.get("lb_noise", 0)
     p.seed = cfg.get("noise_seed", 0)
+    p.warm_extrap = cfg.get("warm_extrap", 0)
     p.step = cfg.get("noise_step", 0)
     return p
 
@@ -287,9 +289,14 @@ def cd_step(cfg: dict, phi: np.ndarray, mu_: np.ndarray, ulat: np.ndarray | None
     return out
 
 
-def step(cfg: dict, phi: np.ndarray, U: np.ndarray, pop: np.ndarray | None, mass0):
-    """One coupled time step.  Returns a dict with the new state and the step outputs."""
+def step(cfg: dict, phi: np.ndarray, U: np.ndarray, pop: np.ndarray | None, mass0, Uprev=None):
+    """One coupled time step.  Returns a dict with the new state and the step outputs; "Uprev"
+    holds a copy of the incoming U.  With cfg["warm_extrap"] and Uprev given (the incoming U of
+    the previous step, itself the result of an inversion) the inversion starts from
+    2 U - Uprev; without Uprev it starts from U."""
     p = make_params(cfg)
+    U_in = _f64(U).copy()
+    up = _f64(Uprev).copy() if (p.warm_extrap and Uprev is not None) else None
     phi = _f64(phi).copy()
     U = _f64(U).copy()
     shp = _shape(cfg)
@@ -303,8 +310,8 @@ def step(cfg: dict, phi: np.ndarray, U: np.ndarray, pop: np.ndarray | None, mass
     phim = np.empty_like(phi)
     info = np.zeros(2 + 4 * max(cfg.get("ncg_iters", 4), 0))
     lib().or_step(ctypes.byref(p), _ptr(phi), _ptr(U), _ptr(pop), _ptr(_f64(mass0)), _ptr(mu_),
-                  _ptr(ulat), _ptr(phim), _ptr(info))
-    return {"phi": phi, "U": U, "pop": pop, "mu": mu_, "ulat": ulat, "phim": phim, "info": info}
+                  _ptr(ulat), _ptr(phim), _ptr(info), _ptr(up) if up is not None else None)
+    return {"phi": phi, "U": U, "pop": pop, "mu": mu_, "ulat": ulat, "phim": phim, "info": info, "Uprev": U_in}
 
 
 def free_energy(cfg: dict, U: np.ndarray, phi: np.ndarray) -> float:

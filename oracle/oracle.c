@@ -46,7 +46,7 @@ typedef struct {
     double ncg_tol;      /* > 0: stop the inversion once max|phi* - phi[U]| < ncg_tol    */
     double omega;        /* > 0: thermal noise with noise parameter Omega = h^3/v0        */
     int32_t lb_noise;    /* with omega > 0: also the fluctuating LB modes (Eq. 13)       */
-    int32_t pad_;
+    int32_t warm_extrap; /* 1: start the inversion from 2 U^{n-1} - U^{n-2} (or_step)      */
     uint64_t seed;       /* key of the counter-based generator                           */
     int64_t step;        /* step index (counter word 1) of the noise of this call        */
 } or_params;
@@ -647,6 +647,21 @@ void or_cd_step(const or_params* p, const double* phi, const double* mu, const d
 }
 
 /* ------------------------------------------------------------------------------------ */
+/* Starting point of the inversion (the paper does not say where the Fletcher-Reeves      */
+/* iteration starts; reading: from the previous step's potentials, or with warm_extrap    */
+/* from their linear extrapolation in time, 2 U^{n-1} - U^{n-2}, once two steps have      */
+/* produced potentials).  Uprev holds U^{n-2} on entry and U^{n-1} on return.             */
+/* ------------------------------------------------------------------------------------ */
+void or_extrapolate(const or_params* p, double* U, double* Uprev) {
+    const int64_t n = (int64_t)p->ns * nsites(p);
+    for (int64_t i = 0; i < n; ++i) {
+        const double u = U[i];
+        U[i] = 2.0 * u - Uprev[i];
+        Uprev[i] = u;
+    }
+}
+
+/* ------------------------------------------------------------------------------------ */
 /* One coupled time step (Sec. 2, paragraph after Eq. 17: LB steps alternate with         */
 /* propagations of Eq. 3, each needing the self-consistent potentials).  Reading of the   */
 /* order within a step:                                                                   */
@@ -657,12 +672,14 @@ void or_cd_step(const or_params* p, const double* phi, const double* mu, const d
 /* State in/out: phi [ns][V] (replaced by phi^{n+1}), U [ns][V] (replaced by U^n),         */
 /* pop [19][V] (post-streaming populations, replaced by those of step n+1; unused if     */
 /* hydro == 0).  Outputs: mu [ns][V], ulat [3][V] (zero if hydro == 0), phim [ns][V] =    */
-/* phi[U^n], info as in or_ncg.                                                           */
+/* phi[U^n], info as in or_ncg.  With p->warm_extrap and Uprev != NULL the inversion starts */
+/* from the extrapolated potentials (or_extrapolate).                                     */
 /* ------------------------------------------------------------------------------------ */
 void or_step(const or_params* p, double* phi, double* U, double* pop, const double* mass0,
-             double* mu, double* ulat, double* phim, double* info) {
+             double* mu, double* ulat, double* phim, double* info, double* Uprev) {
     const int64_t V = nsites(p);
     const int ns = p->ns;
+    if (p->warm_extrap && Uprev) or_extrapolate(p, U, Uprev);
     or_ncg(p, phi, U, phim, info);
     or_mu(p, U, phi, mu);
     if (p->hydro) {

@@ -188,6 +188,7 @@ Layout make_layout(const dscf_params* p, int n, int prec, char* base) {
         R.del0 = take(ns * V * es);
         R.del1 = take(ns * V * es);
         R.rhs = take(ns * V * es);
+        R.Uprev = take(ns * V * es);
         R.part = (double*)take((size_t)NPART * R.part_stride * sizeof(double));
         R.scal = (double*)take((size_t)kScalStride * sizeof(double));
     }
@@ -243,6 +244,7 @@ struct dscf_ctx {
     bool pers_perm = false; // brick placement table in use
     int wait_limit = kPersSpinLimit;   // polls before a persistent sweep gives up on a neighbour
     double ncg_tol = 0.0;   // > 0: residual stop of the inversion (conditional graph nodes)
+    int warm = 0;           // 1: the inversion starts from the potentials extrapolated in time
     int noise = 0;          // thermal noise (dscf_set_noise): 1 compositions, 2 LB modes
     cudaError_t cap_err = cudaSuccess;   // first graph-construction error of a capture
     const char* cap_what = "";
@@ -426,6 +428,13 @@ int64_t enqueue_step(dscf_ctx* c, const Launch& L, bool pred = false) {
     };
     int64_t n = 0;
     mark(4);
+    if (!pred && c->warm && K > 0) {
+        // start from 2 U^{n-1} - U^{n-2} (once two steps have produced potentials) and evaluate
+        // phi there, the inversion's starting residual
+        launch_extrap<T>(L); ++n;
+        n += enqueue_eval<T>(c, L, 0, 0, nullptr);
+        launch_grad<T>(L, -1); ++n;
+    }
     if (K > 0) { launch_dir<T>(L, 0, 0); ++n; }
     for (int k = 0; k < K; ++k) {
         if (gate && c->cap_err == cudaSuccess) {
@@ -479,6 +488,16 @@ int64_t enqueue_step(dscf_ctx* c, const Launch& L, bool pred = false) {
     n += 3 + c->params[0].cn_sweeps;
     mark(5);
     return n;
+}
+
+// Forget the potentials' history (the extrapolated warm start restarts its count).
+int reset_warm(dscf_ctx* c) {
+    for (int r = 0; r < c->nrep; ++r) {
+        const Rep& R = c->L.reps[r];
+        if (int rc = cuda_check(c, cudaMemsetAsync(R.scal + S_WARM, 0, sizeof(double), c->stream), "warm-start reset"))
+            return rc;
+    }
+    return DSCF_OK;
 }
 
 template <typename T>
@@ -948,6 +967,7 @@ int dscf_set_fields(dscf_ctx* c, int32_t which, const void* src, int32_t on_host
     } else {
         c->phim_stale = true;
     }
+    if (int rc = reset_warm(c)) return rc;   // the history of the potentials no longer applies
     return cuda_check(c, cudaGetLastError(), "set field");
 }
 
@@ -1173,6 +1193,19 @@ int dscf_set_noise(dscf_ctx* c, double omega, int32_t lb_noise, uint64_t seed) {
         c->exec_pred = nullptr;
     }
     return DSCF_OK;
+}
+
+int dscf_set_warm_start(dscf_ctx* c, int32_t mode) {
+    if (!c) return DSCF_ERR_ARG;
+    if (mode != 0 && mode != 1) return fail(c, DSCF_ERR_ARG, "mode must be 0 (previous potentials) or 1 (extrapolated)");
+    if (int rc = set_dev(c)) return rc;
+    if (int rc = cuda_check(c, cudaStreamSynchronize(c->stream), "warm-start sync")) return rc;
+    if (c->exec) {
+        cudaGraphExecDestroy(c->exec);
+        c->exec = nullptr;
+    }
+    c->warm = mode;
+    return reset_warm(c);
 }
 
 int dscf_set_inversion_tol(dscf_ctx* c, double tol) {

@@ -45,6 +45,7 @@ enum ScalSlot {
     S_H0S, S_CDS, S_H1S,         // line search: <g,d>, <d, phi_m d>, h1
     S_GGS0, S_GGS1,              // <g,g> in the parity slots of the iterations
     S_TOT0, S_TOT1, S_TOT2,      // sum_r phi_I before the mass correction
+    S_WARM,                      // steps whose starting potentials Uprev holds (0, 1, 2 = enough)
     S_FIN = kScalStride - 1      // finished-block count (an unsigned in this slot's bytes)
 };
 
@@ -89,6 +90,7 @@ struct Rep {
     void* del0;  // [ns][V] Jacobi iterate ping
     void* del1;  // [ns][V] Jacobi iterate pong
     void* rhs;   // [ns][V] right-hand side of the Crank-Nicolson system
+    void* Uprev; // [ns][V] potentials the previous step's inversion started from
     // thermal noise (dscf_set_noise): composition flux variance 2 M dt / Omega per unit phi,
     // LB temperature dt^2 / Omega (0: off), generator key
     double noise_amp2, noise_kT;
@@ -368,6 +370,7 @@ template <typename T> void launch_cc_solvent(const Launch& L, int replica, const
 // mode 0: init (d = -g), mode 1: iteration k direction update
 template <typename T> void launch_dir(const Launch& L, int mode, int k);
 template <typename T> void launch_mu(const Launch& L, int K);   // K < 0: iterations from scal[S_NITER]
+template <typename T> void launch_extrap(const Launch& L);       // extrapolated start of the inversion
 template <typename T> void launch_lb(const Launch& L, const void* force_ext);
 template <typename T> void launch_cd(const Launch& L, int sweeps);
 template <typename T> void launch_dens_out(const Launch& L, void* phi_ext);

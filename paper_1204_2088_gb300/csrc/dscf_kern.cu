@@ -275,6 +275,27 @@ __global__ void __launch_bounds__(kFlatThreads) k_dir(const Rep* __restrict__ re
     }
 }
 
+// Starting point of the inversion from the potentials of the last two steps: once Uprev holds the
+// potentials a previous step started from (and they came out of an inversion: scal[S_WARM] = 2),
+// U <- 2 U - Uprev, the linear extrapolation in time; in every case Uprev <- the incoming U.  The
+// last block advances the history count.
+template <typename T>
+__global__ void __launch_bounds__(kFlatThreads) k_extrap(const Rep* __restrict__ reps, const int* __restrict__ blk2rep) {
+    FLAT_PROLOGUE
+    const bool go = R.scal[S_WARM] >= 2.0;
+    T* __restrict__ U = (T*)R.U;
+    T* __restrict__ Up = (T*)R.Uprev;
+    for (int I = 0; I < R.ns; ++I)
+        for (int i = i0 + threadIdx.x; i < i1; i += kFlatThreads) {
+            const size_t o = (size_t)I * V + i;
+            const T u = U[o];
+            if (go) U[o] = T(2) * u - Up[o];
+            Up[o] = u;
+        }
+    __shared__ int fin;
+    if (last_block_of(R, &fin) && threadIdx.x == 0) R.scal[S_WARM] = go ? 2.0 : R.scal[S_WARM] + 1.0;
+}
+
 // sigma[f] at one site, written as the x, y, z passes of the separable 27-point stencil.
 template <typename T>
 __device__ __forceinline__ T sigma_at(const T* __restrict__ f, int x, int y, int z, int nx, int ny, int nz, T al,
@@ -1497,6 +1518,10 @@ void launch_dir(const Launch& L, int mode, int k) {
     k_dir<T><<<L.nblk_total, kFlatThreads, 0, L.stream>>>(L.reps, L.blk2rep, mode, k, L.status);
 }
 template <typename T>
+void launch_extrap(const Launch& L) {
+    k_extrap<T><<<L.nblk_total, kFlatThreads, 0, L.stream>>>(L.reps, L.blk2rep);
+}
+template <typename T>
 void launch_mu(const Launch& L, int K) {
     k_mu<T><<<L.nblk_total, kFlatThreads, 0, L.stream>>>(L.reps, L.blk2rep, K);
 }
@@ -1538,6 +1563,7 @@ void launch_lb_diag(const Launch& L) {
     template void launch_grad<T>(const Launch&, int, int);             \
     template void launch_dir<T>(const Launch&, int, int);              \
     template void launch_mu<T>(const Launch&, int);                    \
+    template void launch_extrap<T>(const Launch&);                     \
     template void launch_lb<T>(const Launch&, const void*);            \
     template void launch_cd<T>(const Launch&, int);                    \
     template void launch_dens_out<T>(const Launch&, void*);            \

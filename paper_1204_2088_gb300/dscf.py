@@ -90,6 +90,7 @@ def load():
         "dscf_set_predictor": (ctypes.c_int, [vp, vp, i32, ctypes.c_double, i32]),
         "dscf_set_wait_limit": (ctypes.c_int, [vp, i32]),
         "dscf_set_inversion_tol": (ctypes.c_int, [vp, ctypes.c_double]),
+        "dscf_set_warm_start": (ctypes.c_int, [vp, i32]),
         "dscf_set_noise": (ctypes.c_int, [vp, ctypes.c_double, i32, ctypes.c_uint64]),
         "dscf_minkowski": (ctypes.c_int, [vp, i32, i32, ctypes.c_double, ctypes.POINTER(ctypes.c_int64)]),
         "dscf_trapped_solvent": (ctypes.c_int, [vp, i32, ctypes.c_double, ctypes.POINTER(ctypes.c_double)]),
@@ -357,6 +358,11 @@ class Context:
         """Residual stop of the inversion: at most ncg_iters iterations, fewer once max|phi* - phi[U]|
         < tol (0: fixed count)."""
         self._check(self.lib.dscf_set_inversion_tol(self.h, float(tol)))
+
+    def set_warm_start(self, mode):
+        """0: the inversion starts from the previous potentials; 1: from their linear
+        extrapolation in time (see dscf_set_warm_start)."""
+        self._check(self.lib.dscf_set_warm_start(self.h, int(mode)))
 
     def set_tuning(self, zc, kfuse):
         self._check(self.lib.dscf_set_tuning(self.h, int(zc), int(kfuse)))

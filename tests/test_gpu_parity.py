@@ -599,3 +599,36 @@ def test_error_codes():
     h = ctypes.c_void_p()
     rc = lib.dscf_init(ctypes.byref(p), 1, 0, ctypes.c_void_p(ws.data_ptr()), 1024, None, ctypes.byref(h))
     assert rc == -3 and not h.value
+
+
+@pytest.mark.parametrize("tol", [0.0, 1e-7], ids=["fixed_count", "residual_stop"])
+def test_extrapolated_warm_start_fp64_matches_oracle(tol):
+    """The inversion started from 2 U^{n-1} - U^{n-2} (dscf_set_warm_start(1)), against the oracle
+    step by step: the history starts after dscf_set_fields (the first two steps start from
+    U^{n-1}), the starting densities are evaluated at the extrapolated potentials."""
+    cfg = dict(STEP_CASES[0], ncg_iters=3 if tol == 0.0 else 12)
+    phi, U, dn = random_state(cfg, 71)
+    ctx = dscf.Context(cfg, dscf.FP64)
+    ctx.set(dscf.PHI, torch.from_numpy(phi).cuda())
+    ctx.set(dscf.U, torch.from_numpy(U).cuda())
+    ctx.set(dscf.POP, torch.from_numpy(dn).cuda())
+    ctx.set_warm_start(1)
+    if tol > 0:
+        ctx.set_inversion_tol(tol)
+    _, w, _, _ = oracle.lb_basis()
+    pop = dn + w[:, None, None, None]
+    m0 = phi.reshape(2, -1).sum(1)
+    ocfg = dict(cfg, warm_extrap=1, ncg_tol=tol)
+    Up = None
+    for k in range(5):
+        ctx.step(1)
+        ctx.status()
+        st = oracle.step(ocfg, phi, U, pop, m0, Uprev=Up if k >= 2 else None)
+        phi, U, pop, Up = st["phi"], st["U"], st["pop"], st["Uprev"]
+        for name, which, ref in (("phi", dscf.PHI, phi), ("U", dscf.U, U), ("mu", dscf.MU, st["mu"]),
+                                 ("phim", dscf.PHIM, st["phim"])):
+            assert rel(t2n(ctx.get(which)), ref) < 1e-10, (k, name)
+        if tol > 0:
+            its = sum(1 for j in range(12) if st["info"][2 + 4 * j + 3] != 0.0)
+            assert ctx.diagnostics()["ncg_iters"] == its, k
+    ctx.close()

@@ -1028,3 +1028,50 @@ def test_hydro_total_energy_is_non_increasing():
         phi, U, pop = o["phi"], o["U"], o["pop"]
     assert np.diff(E).max() < 0.0
     assert max(kin) > 1e-5          # the flow matters in this run
+
+
+# ---------------------------------------------------------------------------------------------
+# Starting point of the inversion (the paper does not give it): the previous step's potentials
+# or their linear extrapolation in time.  Neither changes what the inversion converges to; the
+# extrapolation makes the starting residual second order in the time step instead of first.
+# ---------------------------------------------------------------------------------------------
+def _run_start_residuals(cfg, steps, extrap):
+    phi = inputs.initial_fields(cfg)
+    U, Up, m0 = np.zeros_like(phi), None, phi.reshape(2, -1).sum(1)
+    c = dict(cfg, warm_extrap=1 if extrap else 0)
+    res, out = [], []
+    for k in range(steps):
+        # history: the incoming U of the previous step, once that step started from an inversion's
+        # result (from the third step on; the first starts from the cold U = 0)
+        st = oracle.step(c, phi, U, None, m0, Uprev=Up if k >= 2 else None)
+        res.append(st["info"][1])                 # max|phi* - phi[U]| where the inversion starts
+        phi, U, Up = st["phi"], st["U"], st["Uprev"]
+        out.append(phi)
+    return np.array(res), out
+
+
+def test_extrapolated_start_converges_to_the_same_state():
+    cfg = inputs.melt((10, 10, 10), 8, 0.5, 12.0, noise=0.05, seed=9, dt=0.02, hydro=0, ncg_iters=200)
+    cfg["ncg_tol"] = 1e-12
+    r0, plain = _run_start_residuals(cfg, 8, False)
+    r1, extr = _run_start_residuals(cfg, 8, True)
+    for a, b in zip(plain, extr):
+        assert np.abs(a - b).max() < 1e-10
+    assert (r1[:2] == r0[:2]).all()                # no history yet
+    assert (r1[3:] < 0.3 * r0[3:]).all()
+
+
+def test_extrapolated_start_residual_is_second_order_in_dt():
+    """Without extrapolation the starting residual is the composition change of one step, O(dt);
+    with it, O(dt^2): halving dt halves the first and quarters the second (after the quench
+    transient, at the same physical time)."""
+    res = {}
+    for dt in (0.02, 0.01):
+        n = int(round(0.2 / dt))
+        cfg = inputs.melt((10, 10, 10), 8, 0.5, 12.0, noise=0.05, seed=9, dt=dt, hydro=0, ncg_iters=200)
+        cfg["ncg_tol"] = 1e-12
+        res[dt] = (_run_start_residuals(cfg, n, False)[0][-1], _run_start_residuals(cfg, n, True)[0][-1])
+    plain = res[0.02][0] / res[0.01][0]
+    extr = res[0.02][1] / res[0.01][1]
+    assert 1.7 < plain < 2.3
+    assert 3.3 < extr < 4.9
