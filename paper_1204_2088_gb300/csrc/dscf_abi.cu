@@ -195,7 +195,7 @@ Layout make_layout(const dscf_params* p, int n, int prec, char* base) {
     L.off_reps = off; take(sizeof(Rep) * n);
     L.off_t2r = off; take(sizeof(int) * max_tiles_total);
     L.off_b2r = off; take(sizeof(int) * max_blk_total);
-    L.off_status = off; take(sizeof(int) * ((size_t)kFlagBase + (size_t)kMaxBricks * (kFlagStride + 1)));
+    L.off_status = off; take(sizeof(int) * kStatusInts);
     L.bytes = off;
     return L;
 }
@@ -241,7 +241,8 @@ struct dscf_ctx {
     int kfuse = 1;          // contour steps per propagator launch (1 = single-step kernels, 0 = persistent)
     int pers_bz = 0;        // brick depth of the persistent sweeps (0 = not available)
     int pers_nw = 16;       // warps per CTA of the persistent sweeps
-    bool pers_perm = false; // brick placement table in use
+    struct PersGroup { int width, first, nbricks; };   // one cooperative launch per sweep direction
+    std::vector<PersGroup> pgroups;                    // brick table entries [first, first + nbricks)
     int wait_limit = kPersSpinLimit;   // polls before a persistent sweep gives up on a neighbour
     double ncg_tol = 0.0;   // > 0: residual stop of the inversion (conditional graph nodes)
     int warm = 0;           // 1: the inversion starts from the potentials extrapolated in time
@@ -294,32 +295,85 @@ int reset_pers_flags(dscf_ctx* c) {
                       "re-arming the brick counters");
 }
 
-// Brick placement: the CTAs of a sweep-shaped cooperative launch land on SMs in a fixed pattern
-// that scatters consecutive CTA indices over the GPCs (and both dies).  Bricks are given to the
-// CTAs in the order of their SM ids instead, so that the bricks of one z slab (consecutive brick
-// indices, y fastest) share a GPC and neighbouring slabs sit on neighbouring GPCs.  The table is
-// a permutation: correctness does not depend on the placement actually repeating.
+int* pers_flags(dscf_ctx* c) { return c->d_status + kFlagBase; }
+int4* pers_table(dscf_ctx* c) { return (int4*)(c->d_status + kFlagBase + (size_t)kMaxBricks * kFlagStride); }
+int pers_total_bricks(const dscf_ctx* c) {
+    int t = 0;
+    for (const Rep& R : c->L.reps) t += pers_bricks(R, c->pers_bz);
+    return t;
+}
+
+// Launch groups and brick table of the persistent sweeps.  Replicas of one row width share a
+// launch while their bricks fit the co-resident CTAs (one per SM for bricks of 16 planes, two
+// for 8), taken in order of width and chain length so that the CTAs of a launch run about
+// equally long; every replica's bricks stay in one launch (they wait on one another).  Each
+// brick's step counter is at its replica's flag base (the replicas' bricks in index order).
+// Placement: the CTAs of a sweep-shaped cooperative launch land on SMs in a fixed pattern that
+// scatters consecutive CTA indices over the GPCs (and both dies); within a launch the bricks are
+// given to the CTAs in the order of their SM ids instead, so that the bricks of one z slab
+// (consecutive brick indices, y fastest) share a GPC and neighbouring slabs sit on neighbouring
+// GPCs.  The table is a permutation: correctness does not depend on the placement repeating.
 int place_bricks(dscf_ctx* c) {
-    c->pers_perm = false;
-    const int nb = pers_bricks(c->L.reps[0], c->pers_bz);
-    int* d_perm = c->d_status + kFlagBase + (size_t)kMaxBricks * kFlagStride;
-    int rc = cuda_check(c, (cudaError_t)pers_placement(c->pers_bz, c->pers_nw, nb, d_perm, c->stream), "placement probe");
-    std::vector<int> smid(nb), order(nb), perm(nb);
-    if (!rc) rc = cuda_check(c, cudaMemcpyAsync(smid.data(), d_perm, sizeof(int) * nb, cudaMemcpyDeviceToHost, c->stream),
-                             "placement probe");
-    if (!rc) rc = cuda_check(c, cudaStreamSynchronize(c->stream), "placement probe");
-    if (rc) return rc;
-    for (int i = 0; i < nb; ++i) order[i] = i;
-    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return smid[a] < smid[b]; });
-    for (int r = 0; r < nb; ++r) perm[order[r]] = r;
-    rc = cuda_check(c, cudaMemcpyAsync(d_perm, perm.data(), sizeof(int) * nb, cudaMemcpyHostToDevice, c->stream),
-                    "placement table");
-    if (!rc) rc = cuda_check(c, cudaStreamSynchronize(c->stream), "placement table");
-    if (!rc) c->pers_perm = true;
+    c->pgroups.clear();
+    const int n = c->nrep, bz = c->pers_bz;
+    const int cap = std::min(c->nsm * (c->pers_nw == 8 ? 2 : 1), kMaxBricks);
+    std::vector<int> fbase(n), order(n);
+    int tot = 0;
+    for (int r = 0; r < n; ++r) {
+        fbase[r] = tot;
+        tot += pers_bricks(c->L.reps[r], bz);
+        order[r] = r;
+    }
+    if (tot > kMaxBricks) return fail(c, DSCF_ERR_ARG, "persistent sweeps: %d bricks exceed %d", tot, kMaxBricks);
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+        const Rep &A = c->L.reps[a], &B = c->L.reps[b];
+        return A.nx != B.nx ? A.nx < B.nx : A.N < B.N;
+    });
+    std::vector<int4> table(tot);
+    int* d_smid = (int*)pers_table(c);   // probe scratch: the table is uploaded after the probes
+    std::vector<int4> ent;
+    int first = 0;
+    auto close = [&](int width) -> int {
+        const int nb = (int)ent.size();
+        if (!nb) return DSCF_OK;
+        std::vector<int> smid(nb), ord(nb);
+        int rc = cuda_check(c, (cudaError_t)pers_placement(bz, c->pers_nw, nb, d_smid, c->stream), "placement probe");
+        if (!rc) rc = cuda_check(c, cudaMemcpyAsync(smid.data(), d_smid, sizeof(int) * nb, cudaMemcpyDeviceToHost, c->stream),
+                                 "placement probe");
+        if (!rc) rc = cuda_check(c, cudaStreamSynchronize(c->stream), "placement probe");
+        if (rc) return rc;
+        for (int i = 0; i < nb; ++i) ord[i] = i;
+        std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return smid[a] < smid[b]; });
+        for (int k = 0; k < nb; ++k) table[first + ord[k]] = ent[k];
+        c->pgroups.push_back({width, first, nb});
+        first += nb;
+        ent.clear();
+        return DSCF_OK;
+    };
+    int width = 0;
+    for (int r : order) {
+        const Rep& R = c->L.reps[r];
+        const int nb = pers_bricks(R, bz);
+        if (nb > cap) return fail(c, DSCF_ERR_ARG, "persistent sweeps: replica %d has %d bricks, more than %d", r, nb, cap);
+        if (!ent.empty() && (R.nx != width || (int)ent.size() + nb > cap))
+            if (int rc = close(width)) return rc;
+        width = R.nx;
+        for (int b = 0; b < nb; ++b) ent.push_back(make_int4(r, b, fbase[r], 0));
+    }
+    if (int rc = close(width)) return rc;
+    int rc = cuda_check(c, cudaMemcpyAsync(pers_table(c), table.data(), sizeof(int4) * tot, cudaMemcpyHostToDevice, c->stream),
+                        "brick table");
+    if (!rc) rc = cuda_check(c, cudaStreamSynchronize(c->stream), "brick table");
+    if (rc) c->pgroups.clear();
     return rc;
 }
-const int* perm_of(const dscf_ctx* c) {
-    return c->pers_perm ? c->d_status + kFlagBase + (size_t)kMaxBricks * kFlagStride : nullptr;
+
+// One direction of the persistent sweeps of every replica: one cooperative launch per group.
+int64_t launch_pers_sweeps(dscf_ctx* c, const Launch& L, bool bwd, int limit) {
+    for (const auto& g : c->pgroups)
+        launch_prop_pers(L, bwd, g.width, c->pers_bz, c->pers_nw, g.nbricks, pers_table(c) + g.first, pers_flags(c),
+                         c->d_status + 2, limit);
+    return (int64_t)c->pgroups.size();
 }
 
 // Forward and backward contour sweeps of one gradient evaluation.
@@ -328,11 +382,9 @@ int64_t enqueue_sweeps(dscf_ctx* c, const Launch& L) {
     int64_t n = 0;
     const int K = c->kfuse;
     if (K == 0) {
-        const int nb = pers_bricks(c->L.reps[0], c->pers_bz);
-        int* flags = c->d_status + kFlagBase;
-        launch_prop_pers(L, false, c->pers_bz, c->pers_nw, nb, flags, c->d_status + 2, c->wait_limit, perm_of(c));
-        launch_prop_pers(L, true, c->pers_bz, c->pers_nw, nb, flags, c->d_status + 2, c->wait_limit, perm_of(c));
-        return 2;
+        n += launch_pers_sweeps(c, L, false, c->wait_limit);
+        n += launch_pers_sweeps(c, L, true, c->wait_limit);
+        return n;
     }
     if (K > 1) {
         int vmax = 0;
@@ -583,16 +635,31 @@ void set_zc(dscf_ctx* c, int zc) {
 // Persistent-sweep candidates (one warp per plane of the brick): bricks of 16 planes (one CTA per
 // SM) and bricks of 8 planes (two CTAs per SM).  The first becomes the context's persistent
 // configuration.
+bool pers_all_supported(const dscf_ctx* c, int bz, int nw) {
+    if (c->prec != DSCF_FP32) return false;
+    if (nw == 8 && c->nrep != 1) return false;   // bricks of 8 planes: one 128-wide replica
+    const int nsm = std::min(c->nsm, kMaxBricks / 2);
+    long long tot = 0;
+    for (const Rep& R : c->L.reps) {
+        if (!pers_supported(R, bz, nw, nsm)) return false;
+        tot += pers_bricks(R, bz);
+    }
+    return tot <= kMaxBricks;
+}
+
 int pers_select(dscf_ctx* c, std::vector<std::pair<int, int>>& pcand) {
     c->pers_bz = 0;
     pcand.clear();
-    if (c->nrep == 1 && c->prec == DSCF_FP32) {
-        const int nsm = std::min(c->nsm, kMaxBricks / 2);
-        if (pers_supported(c->L.reps[0], 16, 16, nsm)) pcand.push_back({16, 16});
-        if (pers_supported(c->L.reps[0], 8, 8, nsm)) pcand.push_back({8, 8});
-    }
+    if (pers_all_supported(c, 16, 16)) pcand.push_back({16, 16});
+    if (pers_all_supported(c, 8, 8)) pcand.push_back({8, 8});
     for (auto& pc : pcand)
-        if (int rc = cuda_check(c, (cudaError_t)pers_prepare(pc.first, pc.second), "persistent sweep set-up")) return rc;
+        for (int wdt : {32, 48, 64, 96, 128}) {
+            bool used = false;
+            for (const Rep& R : c->L.reps) used = used || R.nx == wdt;
+            if (used)
+                if (int rc = cuda_check(c, (cudaError_t)pers_prepare(wdt, pc.first, pc.second), "persistent sweep set-up"))
+                    return rc;
+        }
     if (!pcand.empty()) {
         c->pers_bz = pcand[0].first;
         c->pers_nw = pcand[0].second;
@@ -664,7 +731,7 @@ int autotune_zc(dscf_ctx* c) {
     if (!pcand.empty()) {
         c->pers_bz = pcand[0].first;
         c->pers_nw = pcand[0].second;
-        if (Vtot >= 32 * 32 * 32 && c->L.reps[0].N >= 2) {
+        if (Vtot >= 32 * 32 * 32 && Nmin >= 2) {
             // per contour step of the best multi-launch configuration, measured on a forward sweep
             auto sweep_ms = [&](int K, int zc) -> float {
                 c->kfuse = K;
@@ -676,8 +743,7 @@ int autotune_zc(dscf_ctx* c) {
                 cudaEventCreate(&e1);
                 auto run = [&]() {
                     if (K == 0) {
-                        launch_prop_pers(L, false, c->pers_bz, c->pers_nw, pers_bricks(c->L.reps[0], c->pers_bz),
-                                         c->d_status + kFlagBase, c->d_status + 2, kPersSpinLimit, perm_of(c));
+                        launch_pers_sweeps(c, L, false, kPersSpinLimit);
                     } else if (c->prec == DSCF_FP64) {
                         enqueue_sweeps<double>(c, L);
                     } else {
@@ -791,7 +857,7 @@ int dscf_init_tuned(const dscf_params* p, int32_t n, int32_t precision, void* wo
     rc = rc ? rc : chk(cudaMemcpyAsync(c->d_reps, c->L.reps.data(), sizeof(Rep) * n, cudaMemcpyHostToDevice, c->stream), "reps");
     rc = rc ? rc : chk(cudaMemcpyAsync(c->d_t2r, c->L.tile2rep.data(), sizeof(int) * c->L.ntiles, cudaMemcpyHostToDevice, c->stream), "t2r");
     rc = rc ? rc : chk(cudaMemcpyAsync(c->d_b2r, c->L.blk2rep.data(), sizeof(int) * c->L.nblk, cudaMemcpyHostToDevice, c->stream), "b2r");
-    rc = rc ? rc : chk(cudaMemsetAsync(c->d_status, 0, sizeof(int) * ((size_t)kFlagBase + (size_t)kMaxBricks * (kFlagStride + 1)), c->stream), "status");
+    rc = rc ? rc : chk(cudaMemsetAsync(c->d_status, 0, sizeof(int) * kStatusInts, c->stream), "status");
     const size_t es = precision == DSCF_FP64 ? 8 : 4;
     for (int r = 0; r < n && !rc; ++r) {
         const Rep& R = c->L.reps[r];
@@ -1241,7 +1307,7 @@ int dscf_set_wait_limit(dscf_ctx* c, int32_t polls) {
 int dscf_inject_lag(dscf_ctx* c, int32_t brick) {
     if (!c) return DSCF_ERR_ARG;
     if (!c->pers_bz || c->kfuse != 0) return fail(c, DSCF_ERR_STATE, "the context does not run persistent sweeps");
-    const int nb = pers_bricks(c->L.reps[0], c->pers_bz);
+    const int nb = pers_total_bricks(c);
     if (brick < 0 || brick >= nb) return fail(c, DSCF_ERR_ARG, "brick index out of range");
     if (int rc = set_dev(c)) return rc;
     // a counter far behind the others: the brick's neighbours wait for step values it never
@@ -1320,13 +1386,14 @@ int dscf_set_tuning(dscf_ctx* c, int32_t zc, int32_t kfuse) {
     if (zc < 1 || kfuse < 0 || kfuse > 4) return fail(c, DSCF_ERR_ARG, "need zc >= 1 and 0 <= kfuse <= 4");
     if (kfuse > 1 && !c->fusable) return fail(c, DSCF_ERR_ARG, "contour fusion needs FP32 and nx in {32, 64, 128}");
     if (kfuse == 0 && !c->pers_bz)
-        return fail(c, DSCF_ERR_ARG, "persistent sweeps need one FP32 replica with nx = 128, ny % 8 = 0, nz % 8 = 0");
+        return fail(c, DSCF_ERR_ARG,
+                    "persistent sweeps need FP32 replicas with nx in {32, 48, 64, 96, 128}, ny %% 8 = 0 and nz %% 16 = 0 "
+                    "(nz %% 8 = 0 for bricks of 8 planes: one 128-wide replica), at most one brick per SM each");
     int pbz = c->pers_bz, pnw = c->pers_nw;
     if (kfuse == 0 && (zc == 8 || zc == 16)) {   // brick depth requested
-        const int nsm = std::min(c->nsm, kMaxBricks / 2);
-        if (zc == 16 && pers_supported(c->L.reps[0], 16, 16, nsm)) { pbz = 16; pnw = 16; }
-        else if (zc == 8 && pers_supported(c->L.reps[0], 8, 8, nsm)) { pbz = 8; pnw = 8; }
-        else return fail(c, DSCF_ERR_ARG, "no persistent sweep with bricks of %d planes for this grid", zc);
+        if (zc == 16 && pers_all_supported(c, 16, 16)) { pbz = 16; pnw = 16; }
+        else if (zc == 8 && pers_all_supported(c, 8, 8)) { pbz = 8; pnw = 8; }
+        else return fail(c, DSCF_ERR_ARG, "no persistent sweep with bricks of %d planes for these grids", zc);
     }
     for (const Rep& R : c->L.reps)
         if (kfuse > R.N) return fail(c, DSCF_ERR_ARG, "kfuse exceeds a chain length");
@@ -1340,8 +1407,9 @@ int dscf_set_tuning(dscf_ctx* c, int32_t zc, int32_t kfuse) {
         cudaGraphExecDestroy(c->exec_pred);
         c->exec_pred = nullptr;
     }
-    if (kfuse == 0 && (pbz != c->pers_bz || pnw != c->pers_nw)) {
-        if (int rc = cuda_check(c, (cudaError_t)pers_prepare(pbz, pnw), "persistent sweep set-up")) return rc;
+    if (kfuse == 0 && (pbz != c->pers_bz || pnw != c->pers_nw || c->pgroups.empty())) {
+        for (const Rep& R : c->L.reps)
+            if (int rc = cuda_check(c, (cudaError_t)pers_prepare(R.nx, pbz, pnw), "persistent sweep set-up")) return rc;
         c->pers_bz = pbz;
         c->pers_nw = pnw;
         if (int rc = reset_pers_flags(c)) return rc;

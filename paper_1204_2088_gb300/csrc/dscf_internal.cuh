@@ -56,7 +56,9 @@ enum { ST_NONFINITE = 1, ST_TIMEOUT = 2 };
 // counter per persistent brick.
 constexpr int kFlagBase = 64;
 constexpr int kFlagStride = 32;   // ints between brick step counters: one 128-byte line each
-constexpr int kMaxBricks = 1024;
+constexpr int kMaxBricks = 2048;
+// status block: the words above, kMaxBricks counters, then the int4 brick table of the sweeps
+constexpr size_t kStatusInts = (size_t)kFlagBase + (size_t)kMaxBricks * kFlagStride + 4 * (size_t)kMaxBricks;
 
 // One replica as the kernels see it.  Pointers are into the caller's workspace; their element
 // type is the context precision (double or float) except part/scal (double).
@@ -378,13 +380,16 @@ template <typename T> void launch_pop_copy(const Launch& L, void* ext, int dir);
 template <typename T> void launch_mass_init(const Launch& L, int nrep);
 void launch_step_end(const Launch& L);
 template <typename T> void launch_lb_diag(const Launch& L);
-// persistent contour sweeps (FP32, nx = 128, one replica)
-size_t pers_smem_bytes(int vec, int bz);
+// persistent contour sweeps (FP32; row widths 32, 48, 64, 96, 128; several replicas of one width
+// per launch, each CTA taking its brick from an int4 table: replica, brick in the replica, flag
+// index of the replica's brick 0)
+size_t pers_smem_bytes(int width, int bz);
+bool pers_width_ok(int nx);
 bool pers_supported(const Rep& R, int bz, int nw, int nsm);   // nw: warps per CTA (16, or 8 with 2 CTAs per SM)
 int pers_bricks(const Rep& R, int bz);
-int pers_prepare(int bz, int nw);                                                                  // cudaError_t
-int launch_prop_pers(const Launch& L, bool bwd, int bz, int nw, int nbricks, int* flags, int* abortf, int limit,
-                     const int* perm);  // cudaError_t
+int pers_prepare(int width, int bz, int nw);                                                       // cudaError_t
+int launch_prop_pers(const Launch& L, bool bwd, int width, int bz, int nw, int nbricks, const int4* table, int* flags,
+                     int* abortf, int limit);  // cudaError_t
 // SM id of each CTA of a sweep-shaped cooperative launch (cudaError_t)
 int pers_placement(int bz, int nw, int nbricks, int* d_smid, cudaStream_t stream);
 

@@ -1,11 +1,16 @@
-// Persistent contour sweeps (Eq. 16-17) for one replica in the whole-row layout (FP32).
+// Persistent contour sweeps (Eq. 16-17) in the whole-row layout (FP32), for one replica or a
+// batch of replicas.
 //
 // One launch runs a whole forward (or backward) sweep of N contour steps.  The lattice is cut
 // into bricks of nx x 8 x BZ sites, one brick per CTA (one CTA per SM for BZ = 16, two for
 // BZ = 8; the launch is cooperative, so all CTAs are resident together), one warp per plane of
-// the brick.  A warp keeps its plane's x-filtered rows in registers from one contour step to the
-// next; per step the CTA only reads the halo rows and planes of its eight y/z neighbours from L2,
-// after checking with an acquire load that they have published that step.  Per step:
+// the brick.  Rows of 64, 96 or 128 sites are held by a whole warp (2, 3 or 4 sites per lane),
+// rows of 32 or 48 sites by half a warp, two rows side by side.  A CTA takes its brick from a
+// table (replica, brick, flag base), so replicas of one row width share a launch; a brick waits
+// only on the bricks of its own replica.  A warp keeps its plane's x-filtered rows in registers
+// from one contour step to the next; per step the CTA only reads the halo rows and planes of its
+// eight y/z neighbours from L2, after checking with an acquire load that they have published that
+// step.  Per step:
 //   halo rows of the previous step -> x pass -> shared XH (y-halo rows) and ZH (z-halo planes);
 //   barrier; each warp y-filters its plane in registers (two halo rows from XH) into shared YS,
 //   and one row of a z-halo plane;
@@ -17,10 +22,10 @@
 //   barrier, release store of the brick's step counter; then the forward interior stores and the
 //   x pass of the new values, in registers.
 // q is accumulated in registers over a whole block of beads and written once; nothing is
-// read-modify-written per step.  Each 1-D pass of the separable stencil is two packed-pair
-// operations per two sites (f32x2 add and fma), with the centre weight folded into the Boltzmann
-// factors.  Every wait is bounded: on timeout the CTA sets a status bit and a
-// global abort flag that makes every other CTA stop waiting, so the launch always finishes.
+// read-modify-written per step.  Each 1-D pass of the separable stencil is one add and one fma
+// per site, as packed f32x2 pairs (a scalar tail for three sites per lane), with the centre weight
+// folded into the Boltzmann factors.  Every wait is bounded: on timeout the CTA sets a status bit
+// and a global abort flag that makes every other CTA stop waiting, so the launch always finishes.
 #include "dscf_internal.cuh"
 
 namespace dscf {
@@ -99,19 +104,13 @@ __device__ __forceinline__ unsigned long long fma2(unsigned long long a, unsigne
     asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
     return r;
 }
-__device__ __forceinline__ float4 f4(unsigned long long lo, unsigned long long hi) {
-    float4 o;
-    upk2(lo, o.x, o.y);
-    upk2(hi, o.z, o.w);
-    return o;
-}
 
 struct PersCtl {
-    int* flags;        // one step counter per brick, kFlagStride ints apart
-    int* abort;        // set by a CTA that gave up waiting
-    int* status;       // device status word
-    const int* perm;   // brick of each CTA (NULL: brick = CTA index)
-    int limit;         // polls before giving up
+    int* flags;          // one step counter per brick, kFlagStride ints apart
+    int* abort;          // set by a CTA that gave up waiting
+    int* status;         // device status word
+    const int4* table;   // per CTA: replica, brick in the replica, flag index of the replica's brick 0
+    int limit;           // polls before giving up
 };
 
 // Wait until every neighbour brick has published `target`; threads 0..7 poll one neighbour each
@@ -145,30 +144,104 @@ struct PersGeom {
     static constexpr int NH = 2 * (BZ + 2) + 2 * PBY;   // halo rows per step
 };
 
+// Row geometry of a brick of width W: a row is held by LPR lanes, VEC consecutive sites each;
+// a warp holds HALVES rows side by side (lanes 0..LPR-1 the first, LPR..31 the second), so each
+// lane carries RPL of the plane's PBY rows (rows h RPL .. h RPL + RPL - 1 for lane half h).
+template <int W>
+struct PRow {
+    static constexpr int LPR = (W == 32 || W == 48) ? 16 : 32;
+    static constexpr int VEC = W / LPR;
+    static constexpr int HALVES = 32 / LPR;
+    static constexpr int RPL = PBY / HALVES;
+    static constexpr int CH = W / 4;   // 16-byte chunks per row
+    static_assert(LPR * VEC == W && VEC >= 2 && VEC <= 4, "row width");
+    static_assert(HALVES * CH <= 32, "one 16-byte chunk per lane for the rows a warp copies");
+};
+
+// VEC consecutive FP32 values: one vector access for 2 and 4, three scalar ones for 3
+template <int VEC>
+__device__ __forceinline__ void ldv(const float* p, float (&v)[VEC]) {
+    if constexpr (VEC == 4) {
+        const float4 t = *(const float4*)p;
+        v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+    } else if constexpr (VEC == 2) {
+        const float2 t = *(const float2*)p;
+        v[0] = t.x; v[1] = t.y;
+    } else {
+#pragma unroll
+        for (int k = 0; k < VEC; ++k) v[k] = p[k];
+    }
+}
+template <int VEC>
+__device__ __forceinline__ void stv(float* p, const float (&v)[VEC]) {
+    if constexpr (VEC == 4) {
+        *(float4*)p = make_float4(v[0], v[1], v[2], v[3]);
+    } else if constexpr (VEC == 2) {
+        *(float2*)p = make_float2(v[0], v[1]);
+    } else {
+#pragma unroll
+        for (int k = 0; k < VEC; ++k) p[k] = v[k];
+    }
+}
+// o = c + r (a + d) per site: packed pairs, a scalar tail for odd VEC (same rounding: one add, one
+// fma per site either way)
+template <int VEC>
+__device__ __forceinline__ void mixv(const float (&a)[VEC], const float (&c)[VEC], const float (&d)[VEC], float rr,
+                                     unsigned long long rr2, float (&o)[VEC]) {
+#pragma unroll
+    for (int k = 0; k + 1 < VEC; k += 2)
+        upk2(fma2(rr2, add2(pk2(a[k], a[k + 1]), pk2(d[k], d[k + 1])), pk2(c[k], c[k + 1])), o[k], o[k + 1]);
+    if constexpr (VEC & 1) o[VEC - 1] = __fmaf_rn(rr, __fadd_rn(a[VEC - 1], d[VEC - 1]), c[VEC - 1]);
+}
+// o = s * v per site
+template <int VEC>
+__device__ __forceinline__ void mulv(const float (&s)[VEC], const float (&v)[VEC], float (&o)[VEC]) {
+#pragma unroll
+    for (int k = 0; k + 1 < VEC; k += 2) upk2(mul2(pk2(s[k], s[k + 1]), pk2(v[k], v[k + 1])), o[k], o[k + 1]);
+    if constexpr (VEC & 1) o[VEC - 1] = __fmul_rn(s[VEC - 1], v[VEC - 1]);
+}
+// q += g * v per site
+template <int VEC>
+__device__ __forceinline__ void fmav(const float (&g)[VEC], const float (&v)[VEC], float (&q)[VEC]) {
+#pragma unroll
+    for (int k = 0; k + 1 < VEC; k += 2)
+        upk2(fma2(pk2(g[k], g[k + 1]), pk2(v[k], v[k + 1]), pk2(q[k], q[k + 1])), q[k], q[k + 1]);
+    if constexpr (VEC & 1) q[VEC - 1] = __fmaf_rn(g[VEC - 1], v[VEC - 1], q[VEC - 1]);
+}
+// scalar c times each site
+template <int VEC>
+__device__ __forceinline__ void scalev(float c, unsigned long long c2, float (&v)[VEC]) {
+#pragma unroll
+    for (int k = 0; k + 1 < VEC; k += 2) upk2(mul2(c2, pk2(v[k], v[k + 1])), v[k], v[k + 1]);
+    if constexpr (VEC & 1) v[VEC - 1] = __fmul_rn(c, v[VEC - 1]);
+}
+
 }  // namespace
 
-size_t pers_smem_bytes(int vec, int bz) {
-    const size_t W = 32 * (size_t)vec;
+size_t pers_smem_bytes(int width, int bz) {
     // YS (y-filtered level, planes -1..bz) + XH (x-filtered y-halo rows of the own planes) + ZH
     // (x-filtered z-halo planes, rows -1..8) + halo staging + backward G_s of the brick
     const size_t rows = (size_t)(bz + 2) * PBY + 2 * (size_t)bz + 2 * (PBY + 2) + (2 * (bz + 2) + 2 * PBY) +
                         (size_t)bz * PBY;
-    return rows * W * sizeof(float);
+    return rows * (size_t)width * sizeof(float);
 }
 
-// Warp w owns plane w of the brick, all PBY rows, four sites of each row per lane; the x-filtered
-// rows of the previous level stay in its registers, so the y pass runs in registers (only the two
-// y-halo rows of the plane come from shared memory) and only the y-filtered rows go through
-// shared memory, for the z pass of the neighbouring planes.  The z-halo planes are y-filtered one
-// row per warp.  Brick-boundary values are stored and published first; the rest of the forward
-// G_s follows without a fence (the backward G+ interior is never stored: it stays in registers).
-template <int BZ, bool BWD, int NW>
+// Warp w owns plane w of the brick, all PBY rows (HALVES rows side by side), VEC sites of each
+// row per lane; the x-filtered rows of the previous level stay in its registers, so the y pass
+// runs in registers (the rows across the lane halves by one shuffle, the two y-halo rows of the
+// plane from shared memory) and only the y-filtered rows go through shared memory, for the z pass
+// of the neighbouring planes.  The z-halo planes are y-filtered one row per lane half.  Brick-
+// boundary values are stored and published first; the rest of the forward G_s follows without a
+// fence (the backward G+ interior is never stored: it stays in registers).
+// Each CTA takes its brick from the table: several replicas of the same row width run in one
+// launch, each brick waiting only on the bricks of its own replica.
+template <int W, int BZ, bool BWD, int NW>
 __global__ void __launch_bounds__(32 * NW, 16 / NW) k_prop_pers(const Rep* __restrict__ reps, PersCtl ctl) {
     static_assert(NW == BZ, "one warp per plane");
-    constexpr int PWARPS = NW, PTHREADS = 32 * NW;
-    constexpr int VEC = 4, W = 128;
+    using RG = PRow<W>;
+    constexpr int VEC = RG::VEC, LPR = RG::LPR, HALVES = RG::HALVES, RPL = RG::RPL, CH = RG::CH;
+    constexpr int PWARPS = NW;
     using G = PersGeom<BZ, NW>;
-    using VT = float4;
     extern __shared__ __align__(16) unsigned char smem[];
     float* YS = (float*)smem;                                  // [BZ+2][PBY][W]
     float* XH = YS + (BZ + 2) * PBY * W;                       // [2][BZ][W]   rows -1 and PBY
@@ -178,15 +251,21 @@ __global__ void __launch_bounds__(32 * NW, 16 / NW) k_prop_pers(const Rep* __res
     __shared__ double sh[33];
     __shared__ int nbs[8];
     __shared__ __align__(8) unsigned long long gs_bar;   // backward: completion of the G_s prefetch
-    const Rep& R = reps[0];
+    const int4 tb = ctl.table[blockIdx.x];
+    const Rep& R = reps[tb.x];
+    const int b = tb.y;
+    const int fown = tb.z + tb.y;   // own step counter
     const int ny = R.ny, nz = R.nz, N = R.N, nA = R.nA;
     const int plane = W * ny;
     const size_t V = (size_t)R.V;
     const int nby = ny / PBY, nbz = nz / BZ;
-    const int b = ctl.perm ? ctl.perm[blockIdx.x] : (int)blockIdx.x;
     const int by = b % nby, bz = b / nby;
     const int y0 = by * PBY, z0 = bz * BZ;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int hf = lane / LPR, li = lane - hf * LPR;   // lane half (row group) and lane within the row
+    const int xo = VEC * li;
+    const int seg = lane - li;
+    const int lsrc = seg + ((li + LPR - 1) & (LPR - 1)), rsrc = seg + ((li + 1) & (LPR - 1));
     // Each 1-D pass is applied as c + r (a + d) with r = alpha / (1 - 2 alpha), i.e. the
     // stencil's pass divided by its centre weight be = 1 - 2 alpha; the three passes then give
     // sigma / be^3, and be^3 is folded into the Boltzmann factors (and into q at its write-out).
@@ -196,7 +275,7 @@ __global__ void __launch_bounds__(32 * NW, 16 / NW) k_prop_pers(const Rep* __res
     if (threadIdx.x < 8) {
         const int k = threadIdx.x < 4 ? threadIdx.x : threadIdx.x + 1;   // skip the centre
         const int dy = k % 3 - 1, dz = k / 3 - 1;
-        nbs[threadIdx.x] = (by + dy + nby) % nby + nby * ((bz + dz + nbz) % nbz);
+        nbs[threadIdx.x] = tb.z + (by + dy + nby) % nby + nby * ((bz + dz + nbz) % nbz);
     }
     // halo row h -> (row r, plane pl) of the brick's frame, r in -1..PBY, pl in -1..BZ
     auto halo_rp = [&](int h, int& r, int& pl) {
@@ -209,43 +288,42 @@ __global__ void __launch_bounds__(32 * NW, 16 / NW) k_prop_pers(const Rep* __res
         return ZH + ((pl < 0 ? 0 : 1) * (PBY + 2) + (r + 1)) * W;
     };
     __shared__ int hoff[2 * (BZ + 2) + 2 * PBY];   // global row offsets of the halo rows
-    for (int h = threadIdx.x; h < G::NH; h += PTHREADS) {
+    for (int h = threadIdx.x; h < G::NH; h += 32 * PWARPS) {
         int r, pl;
         halo_rp(h, r, pl);
         const int y = (y0 + r + ny) % ny, z = (z0 + pl + nz) % nz;
         hoff[h] = z * plane + y * W;
     }
-    const int c0 = ctl.flags[(size_t)b * kFlagStride];   // step counters of all bricks are equal at launch
+    const int c0 = ctl.flags[(size_t)fown * kFlagStride];   // step counters of a replica's bricks are equal at launch
     bool aborted = ld_acquire(ctl.abort) != 0;
 
-    auto xpass = [&](VT v) -> VT {      // x pass of a periodic row held by the warp: v + r (left + right)
-        const float lv = __shfl_sync(0xffffffffu, v.w, (lane + 31) & 31);
-        const float rv = __shfl_sync(0xffffffffu, v.x, (lane + 1) & 31);
-        const unsigned long long mid = pk2(v.y, v.z);
-        const unsigned long long tlo = add2(pk2(lv, v.x), mid), thi = add2(mid, pk2(v.w, rv));
-        return f4(fma2(rr2, tlo, pk2(v.x, v.y)), fma2(rr2, thi, pk2(v.z, v.w)));
+    auto xpass = [&](const float (&v)[VEC], float (&o)[VEC]) {   // x pass of a periodic row: v + r (left + right)
+        const float lv = __shfl_sync(0xffffffffu, v[VEC - 1], lsrc);
+        const float rv = __shfl_sync(0xffffffffu, v[0], rsrc);
+        float a[VEC], d[VEC];
+#pragma unroll
+        for (int k = 0; k < VEC; ++k) {
+            a[k] = k ? v[k - 1] : lv;
+            d[k] = (k + 1 < VEC) ? v[k + 1] : rv;
+        }
+        mixv<VEC>(a, v, d, rr, rr2, o);
     };
-    auto mix = [&](VT a, VT c, VT d) -> VT {   // c + r (a + d)
-        const unsigned long long tlo = add2(pk2(a.x, a.y), pk2(d.x, d.y));
-        const unsigned long long thi = add2(pk2(a.z, a.w), pk2(d.z, d.w));
-        return f4(fma2(rr2, tlo, pk2(c.x, c.y)), fma2(rr2, thi, pk2(c.z, c.w)));
-    };
-    auto ys = [&](int pl, int r) { return YS + ((pl + 1) * PBY + r) * W + VEC * lane; };
+    auto ys = [&](int pl, int r) { return YS + ((pl + 1) * PBY + r) * W + xo; };
     const bool face_plane = (w == 0 || w == BZ - 1);
     auto is_boundary = [&](int r) { return face_plane || r == 0 || r == PBY - 1; };
     // own plane never wraps: offset of (row r, plane w) is own0 + r * W
-    const size_t own0 = (size_t)(z0 + w) * plane + (size_t)y0 * W + VEC * lane;
+    const size_t own0 = (size_t)(z0 + w) * plane + (size_t)y0 * W + xo;
+    auto row_of = [&](int p) { return hf * RPL + p; };
 
-    VT e[PBY];
+    float e[RPL][VEC];
     auto load_e = [&](int species) {
         const float* E = (const float*)R.E + (size_t)species * V;
 #pragma unroll
-        for (int r = 0; r < PBY; ++r) {
-            const VT v = *(const VT*)(E + own0 + (size_t)r * W);
-            e[r] = f4(mul2(be32, pk2(v.x, v.y)), mul2(be32, pk2(v.z, v.w)));
+        for (int p = 0; p < RPL; ++p) {
+            ldv<VEC>(E + own0 + (size_t)row_of(p) * W, e[p]);
+            scalev<VEC>(be3, be32, e[p]);
         }
     };
-    auto q_out = [&](VT v) -> VT { return f4(mul2(be32, pk2(v.x, v.y)), mul2(be32, pk2(v.z, v.w))); };
     // backward: G_s of the brick into GS, issued by thread 0 as one bulk copy per plane (the
     // plane's PBY rows are contiguous in memory and in GS); the copies complete on gs_bar
     unsigned gs_phase = 0;
@@ -280,13 +358,17 @@ __global__ void __launch_bounds__(32 * NW, 16 / NW) k_prop_pers(const Rep* __res
 
     // the first input (G_0 = 1, or G+_{N+1} = 1): its x pass is 1 + 2 r everywhere
     const float one = 1.0f + 2.0f * rr;
-    VT xf[PBY];
+    float xf[RPL][VEC];
 #pragma unroll
-    for (int r = 0; r < PBY; ++r) xf[r] = make_float4(one, one, one, one);
-    for (int i = threadIdx.x; i < (2 * BZ + 2 * (PBY + 2)) * W; i += PTHREADS) XH[i] = one;   // XH and ZH
-    VT qacc[BWD ? PBY : 1];
+    for (int p = 0; p < RPL; ++p)
 #pragma unroll
-    for (int r = 0; r < (BWD ? PBY : 1); ++r) qacc[r] = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int k = 0; k < VEC; ++k) xf[p][k] = one;
+    for (int i = threadIdx.x; i < (2 * BZ + 2 * (PBY + 2)) * W; i += 32 * PWARPS) XH[i] = one;   // XH and ZH
+    float qacc[BWD ? RPL : 1][VEC];
+#pragma unroll
+    for (int p = 0; p < (BWD ? RPL : 1); ++p)
+#pragma unroll
+        for (int k = 0; k < VEC; ++k) qacc[p][k] = 0.f;
     float qsum = 0.f;
     int species = BWD ? (N <= nA ? 0 : 1) : (1 <= nA ? 0 : 1);
     load_e(species);
@@ -297,87 +379,135 @@ __global__ void __launch_bounds__(32 * NW, 16 / NW) k_prop_pers(const Rep* __res
     }
     __syncthreads();
 
+    auto write_q = [&](int sp) {   // a block's quadrature, scaled back by be^3
+        float* q = (float*)R.q + (size_t)sp * V;
+#pragma unroll
+        for (int p = 0; p < (BWD ? RPL : 1); ++p) {
+            float o[VEC];
+#pragma unroll
+            for (int k = 0; k < VEC; ++k) o[k] = qacc[p][k];
+            scalev<VEC>(be3, be32, o);
+            stv<VEC>(q + own0 + (size_t)row_of(p) * W, o);
+#pragma unroll
+            for (int k = 0; k < VEC; ++k) qacc[p][k] = 0.f;
+        }
+    };
+
     for (int j = 0; j < N; ++j) {
         const int s = BWD ? N - j : j + 1;
         const int sp = (s <= nA) ? 0 : 1;
         if (sp != species) {
-            if (BWD) {   // leaving the B block: its quadrature is complete
-                float* q = (float*)R.q + (size_t)species * V;
-#pragma unroll
-                for (int r = 0; r < PBY; ++r) {
-                    *(VT*)(q + own0 + (size_t)r * W) = q_out(qacc[r]);
-                    qacc[r] = make_float4(0.f, 0.f, 0.f, 0.f);
-                }
-            }
+            if (BWD) write_q(species);   // leaving the B block: its quadrature is complete
             species = sp;
             load_e(species);
         }
-        // halo of the previous step, x-filtered into XH / ZH
+        // halo of the previous step, x-filtered into XH / ZH; each warp copies and filters the
+        // rows of its own lane halves (a __syncwarp makes every lane's copied chunk visible)
         if (j > 0) {
             wait_nb(ctl, nbs, c0 + j, aborted);
             const float* src = BWD ? (const float*)(((j - 1) & 1) ? R.Gp1 : R.Gp0)
                                    : (const float*)R.G + (size_t)(s - 2) * V;
-            for (int h = w; h < G::NH; h += PWARPS) cp16(HS + h * W + VEC * lane, src + hoff[h] + VEC * lane);
+            {
+                const int i = lane / CH, ch = lane - i * CH;
+                for (int h0 = w * HALVES; h0 < G::NH; h0 += PWARPS * HALVES)
+                    if (i < HALVES) cp16(HS + (h0 + i) * W + 4 * ch, src + hoff[h0 + i] + 4 * ch);
+            }
             cpc();
             cpw0();
-            for (int h = w; h < G::NH; h += PWARPS) {
+            __syncwarp();
+            for (int h0 = w * HALVES; h0 < G::NH; h0 += PWARPS * HALVES) {
+                const int h = h0 + hf;
+                float v[VEC], o[VEC];
+                ldv<VEC>(HS + h * W + xo, v);
+                xpass(v, o);
                 int r, pl;
                 halo_rp(h, r, pl);
-                *(VT*)(halo_dst(r, pl) + VEC * lane) = xpass(*(const VT*)(HS + h * W + VEC * lane));
+                stv<VEC>(halo_dst(r, pl) + xo, o);
             }
         }
         __syncthreads();
         // y pass of the own plane in registers (its two y-halo rows from XH), into YS
         {
-            const VT top = *(const VT*)(XH + w * W + VEC * lane);          // row -1
-            const VT bot = *(const VT*)(XH + (BZ + w) * W + VEC * lane);   // row PBY
-            VT prev = top;
+            float up[VEC], dn[VEC];   // the row above the lane's first row, below its last
+            ldv<VEC>(XH + w * W + xo, up);           // row -1
+            ldv<VEC>(XH + (BZ + w) * W + xo, dn);    // row PBY
+            if constexpr (HALVES == 2) {   // rows across the two lane halves
 #pragma unroll
-            for (int r = 0; r < PBY; ++r) {
-                const VT nxt = (r + 1 < PBY) ? xf[r + 1] : bot;
-                const VT yv = mix(prev, xf[r], nxt);
-                prev = xf[r];
-                xf[r] = yv;   // xf now holds the y-filtered rows
-                *(VT*)ys(w, r) = yv;
+                for (int k = 0; k < VEC; ++k) {
+                    const float last = __shfl_xor_sync(0xffffffffu, xf[RPL - 1][k], LPR);
+                    const float first = __shfl_xor_sync(0xffffffffu, xf[0][k], LPR);
+                    if (hf == 1) up[k] = last;
+                    else dn[k] = first;
+                }
+            }
+            float prev[VEC];
+#pragma unroll
+            for (int k = 0; k < VEC; ++k) prev[k] = up[k];
+#pragma unroll
+            for (int p = 0; p < RPL; ++p) {
+                float yv[VEC], cur[VEC];
+#pragma unroll
+                for (int k = 0; k < VEC; ++k) cur[k] = xf[p][k];
+                if (p + 1 < RPL) mixv<VEC>(prev, cur, xf[p + 1 < RPL ? p + 1 : p], rr, rr2, yv);
+                else mixv<VEC>(prev, cur, dn, rr, rr2, yv);
+#pragma unroll
+                for (int k = 0; k < VEC; ++k) {
+                    prev[k] = cur[k];
+                    xf[p][k] = yv[k];   // xf now holds the y-filtered rows
+                }
+                stv<VEC>(ys(w, row_of(p)), yv);
             }
         }
-        // y pass of the z-halo planes, one row per warp (PBY rows of each of the two planes)
-        for (int t = w; t < 2 * PBY; t += PWARPS) {
+        // y pass of the z-halo planes, one row per lane half (PBY rows of each of the two planes)
+        for (int t0 = w * HALVES; t0 < 2 * PBY; t0 += PWARPS * HALVES) {
+            const int t = t0 + hf;
             const int side = t / PBY, r = t % PBY;
-            const float* zr = ZH + (side * (PBY + 2) + r + 1) * W + VEC * lane;
-            *(VT*)ys(side ? BZ : -1, r) = mix(*(const VT*)(zr - W), *(const VT*)zr, *(const VT*)(zr + W));
+            const float* zr = ZH + (side * (PBY + 2) + r + 1) * W + xo;
+            float a[VEC], c[VEC], d[VEC], o[VEC];
+            ldv<VEC>(zr - W, a);
+            ldv<VEC>(zr, c);
+            ldv<VEC>(zr + W, d);
+            mixv<VEC>(a, c, d, rr, rr2, o);
+            stv<VEC>(ys(side ? BZ : -1, r), o);
         }
         __syncthreads();
         // z pass and step output
         float* dst = BWD ? (float*)((j & 1) ? R.Gp1 : R.Gp0) : (float*)R.G + (size_t)(s - 1) * V;
         if (BWD) wait_gs();
-        VT out[PBY];
+        float out[RPL][VEC];
 #pragma unroll
-        for (int r = 0; r < PBY; ++r) {
-            const VT a = *(const VT*)ys(w - 1, r), d = *(const VT*)ys(w + 1, r);
-            const unsigned long long sglo = fma2(rr2, add2(pk2(a.x, a.y), pk2(d.x, d.y)), pk2(xf[r].x, xf[r].y));
-            const unsigned long long sghi = fma2(rr2, add2(pk2(a.z, a.w), pk2(d.z, d.w)), pk2(xf[r].z, xf[r].w));
-            out[r] = f4(mul2(pk2(e[r].x, e[r].y), sglo), mul2(pk2(e[r].z, e[r].w), sghi));
-            if (BWD) {
-                const VT g = *(const VT*)(GS + (w * PBY + r) * W + VEC * lane);
-                qacc[r] = f4(fma2(pk2(g.x, g.y), sglo, pk2(qacc[r].x, qacc[r].y)),
-                             fma2(pk2(g.z, g.w), sghi, pk2(qacc[r].z, qacc[r].w)));
-            } else if (s == N) {
-                qsum += (out[r].x + out[r].y) + (out[r].z + out[r].w);
+        for (int p = 0; p < RPL; ++p) {
+            const int r = row_of(p);
+            float a[VEC], d[VEC], sg[VEC];
+            ldv<VEC>(ys(w - 1, r), a);
+            ldv<VEC>(ys(w + 1, r), d);
+            mixv<VEC>(a, xf[p], d, rr, rr2, sg);
+            mulv<VEC>(e[p], sg, out[p]);
+            if constexpr (BWD) {
+                float g[VEC];
+                ldv<VEC>(GS + (w * PBY + r) * W + xo, g);
+                fmav<VEC>(g, sg, qacc[p]);
+            } else {
+                if (s == N) {
+                    float t = out[p][0] + out[p][1];
+                    if constexpr (VEC == 3) t = t + out[p][2];
+                    if constexpr (VEC == 4) t = t + (out[p][2] + out[p][3]);
+                    qsum += t;
+                }
             }
-            if (is_boundary(r) && (!BWD || s > 1)) *(VT*)(dst + own0 + (size_t)r * W) = out[r];
+            if (is_boundary(r) && (!BWD || s > 1)) stv<VEC>(dst + own0 + (size_t)r * W, out[p]);
         }
         // publish the boundary of this step: the CTA barrier orders every thread's boundary stores
         // before thread 0's release store, and release is cumulative, so a CTA whose acquire load
         // reads the new counter sees them.  The barrier also ends every warp's reads of YS, XH
         // and ZH for this step.
         __syncthreads();
-        if (threadIdx.x == 0) st_release(ctl.flags + (size_t)b * kFlagStride, c0 + j + 1);
+        if (threadIdx.x == 0) st_release(ctl.flags + (size_t)fown * kFlagStride, c0 + j + 1);
         if (BWD && s > 1) prefetch_gs(s - 1);   // GS slots of this thread were read above
 #pragma unroll
-        for (int r = 0; r < PBY; ++r) {
-            if (!BWD && !is_boundary(r)) *(VT*)(dst + own0 + (size_t)r * W) = out[r];
-            xf[r] = xpass(out[r]);
+        for (int p = 0; p < RPL; ++p) {
+            if (!BWD && !is_boundary(row_of(p))) stv<VEC>(dst + own0 + (size_t)row_of(p) * W, out[p]);
+            xpass(out[p], xf[p]);
         }
     }
     if (BWD) {   // the A block ends at s = 1
@@ -385,22 +515,25 @@ __global__ void __launch_bounds__(32 * NW, 16 / NW) k_prop_pers(const Rep* __res
             for (long long spins = 0; spins <= kGsSpinLimit && !bar_test(&gs_bar, gs_phase); ++spins) {
             }
         }
-        float* q = (float*)R.q + (size_t)species * V;
-#pragma unroll
-        for (int r = 0; r < PBY; ++r) *(VT*)(q + own0 + (size_t)r * W) = q_out(qacc[r]);
+        write_q(species);
     } else {
         const double t = block_sum((double)qsum, sh);
-        if (threadIdx.x == 0) slot(R, P_Q)[b] = t;
-        if (b == 0)
-            for (int i = threadIdx.x + gridDim.x; i < R.ntiles; i += PTHREADS) slot(R, P_Q)[i] = 0.0;
+        const int bl = ctl.table[blockIdx.x].y;   // reloaded: not kept live through the sweep
+        if (threadIdx.x == 0) slot(R, P_Q)[bl] = t;
+        if (bl == 0) {   // slots past the replica's bricks (the propagator tiling may have more)
+            const int nb = nby * nbz;
+            for (int i = threadIdx.x + nb; i < R.ntiles; i += 32 * PWARPS) slot(R, P_Q)[i] = 0.0;
+        }
     }
 }
 
 // Host side ---------------------------------------------------------------------------------
 
+bool pers_width_ok(int nx) { return nx == 32 || nx == 48 || nx == 64 || nx == 96 || nx == 128; }
+
 bool pers_supported(const Rep& R, int bz, int nw, int nsm) {
-    if (R.nx != 128 || R.ny % PBY || R.nz % bz) return false;
-    if (!((bz == 16 && nw == 16) || (bz == 8 && nw == 8))) return false;   // one warp per plane
+    if (!pers_width_ok(R.nx) || R.ny % PBY || R.nz % bz) return false;
+    if (!((bz == 16 && nw == 16) || (bz == 8 && nw == 8 && R.nx == 128))) return false;   // one warp per plane
     const int nb = (R.ny / PBY) * (R.nz / bz);
     return nb >= 1 && nb <= nsm * (nw == 8 ? 2 : 1);   // all bricks co-resident
 }
@@ -408,22 +541,31 @@ bool pers_supported(const Rep& R, int bz, int nw, int nsm) {
 int pers_bricks(const Rep& R, int bz) { return (R.ny / PBY) * (R.nz / bz); }
 
 namespace {
-template <int BZ, int NW>
+template <int W, int BZ, int NW>
 cudaError_t pers_attr() {
-    const int sm = (int)pers_smem_bytes(4, BZ);
-    cudaError_t e = cudaFuncSetAttribute(k_prop_pers<BZ, false, NW>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_prop_pers<BZ, true, NW>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    const int sm = (int)pers_smem_bytes(W, BZ);
+    cudaError_t e = cudaFuncSetAttribute(k_prop_pers<W, BZ, false, NW>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_prop_pers<W, BZ, true, NW>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_prop_pers<BZ, false, NW>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+        e = cudaFuncSetAttribute(k_prop_pers<W, BZ, false, NW>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_prop_pers<BZ, true, NW>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+        e = cudaFuncSetAttribute(k_prop_pers<W, BZ, true, NW>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     return e;
 }
 }  // namespace
 
-int pers_prepare(int bz, int nw) {
-    if (bz == 16 && nw == 16) return (int)pers_attr<16, 16>();
-    if (bz == 8 && nw == 8) return (int)pers_attr<8, 8>();
+int pers_prepare(int width, int bz, int nw) {
+    if (bz == 16 && nw == 16) {
+        switch (width) {
+            case 128: return (int)pers_attr<128, 16, 16>();
+            case 96: return (int)pers_attr<96, 16, 16>();
+            case 64: return (int)pers_attr<64, 16, 16>();
+            case 48: return (int)pers_attr<48, 16, 16>();
+            case 32: return (int)pers_attr<32, 16, 16>();
+            default: break;
+        }
+    }
+    if (bz == 8 && nw == 8 && width == 128) return (int)pers_attr<128, 8, 8>();
     return (int)cudaErrorInvalidValue;
 }
 
@@ -444,7 +586,7 @@ int pers_placement(int bz, int nw, int nbricks, int* d_smid, cudaStream_t stream
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(nbricks);
     cfg.blockDim = dim3(32 * nw);
-    cfg.dynamicSmemBytes = pers_smem_bytes(4, bz);
+    cfg.dynamicSmemBytes = pers_smem_bytes(128, bz);
     cfg.stream = stream;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeCooperative;
@@ -463,33 +605,41 @@ int pers_placement(int bz, int nw, int nbricks, int* d_smid, cudaStream_t stream
     return (int)e;
 }
 
-int launch_prop_pers(const Launch& L, bool bwd, int bz, int nw, int nbricks, int* flags, int* abortf, int limit,
-                     const int* perm) {
+int launch_prop_pers(const Launch& L, bool bwd, int width, int bz, int nw, int nbricks, const int4* table, int* flags,
+                     int* abortf, int limit) {
     PersCtl ctl;
     ctl.flags = flags;
     ctl.abort = abortf;
     ctl.status = L.status;
-    ctl.perm = perm;
+    ctl.table = table;
     ctl.limit = limit;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(nbricks);
     cfg.blockDim = dim3(32 * nw);
-    cfg.dynamicSmemBytes = pers_smem_bytes(4, bz);
+    cfg.dynamicSmemBytes = pers_smem_bytes(width, bz);
     cfg.stream = L.stream;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeCooperative;
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    cudaError_t e;
-    if (bz == 16 && nw == 16)
-        e = bwd ? cudaLaunchKernelEx(&cfg, k_prop_pers<16, true, 16>, L.reps, ctl)
-                : cudaLaunchKernelEx(&cfg, k_prop_pers<16, false, 16>, L.reps, ctl);
-    else if (bz == 8 && nw == 8)
-        e = bwd ? cudaLaunchKernelEx(&cfg, k_prop_pers<8, true, 8>, L.reps, ctl)
-                : cudaLaunchKernelEx(&cfg, k_prop_pers<8, false, 8>, L.reps, ctl);
-    else
-        e = cudaErrorInvalidValue;
+#define DSCF_PERS_LAUNCH(WW, BB, NN)                                                                     \
+    (bwd ? cudaLaunchKernelEx(&cfg, k_prop_pers<WW, BB, true, NN>, L.reps, ctl)                           \
+         : cudaLaunchKernelEx(&cfg, k_prop_pers<WW, BB, false, NN>, L.reps, ctl))
+    cudaError_t e = cudaErrorInvalidValue;
+    if (bz == 16 && nw == 16) {
+        switch (width) {
+            case 128: e = DSCF_PERS_LAUNCH(128, 16, 16); break;
+            case 96: e = DSCF_PERS_LAUNCH(96, 16, 16); break;
+            case 64: e = DSCF_PERS_LAUNCH(64, 16, 16); break;
+            case 48: e = DSCF_PERS_LAUNCH(48, 16, 16); break;
+            case 32: e = DSCF_PERS_LAUNCH(32, 16, 16); break;
+            default: break;
+        }
+    } else if (bz == 8 && nw == 8 && width == 128) {
+        e = DSCF_PERS_LAUNCH(128, 8, 8);
+    }
+#undef DSCF_PERS_LAUNCH
     return (int)e;
 }
 
