@@ -241,7 +241,7 @@ struct dscf_ctx {
     int kfuse = 1;          // contour steps per propagator launch (1 = single-step kernels, 0 = persistent)
     int pers_bz = 0;        // brick depth of the persistent sweeps (0 = not available)
     int pers_nw = 16;       // warps per CTA of the persistent sweeps
-    struct PersGroup { int width, first, nbricks; };   // one cooperative launch per sweep direction
+    struct PersGroup { int width, pby, first, nbricks; };   // one cooperative launch per sweep direction
     std::vector<PersGroup> pgroups;                    // brick table entries [first, first + nbricks)
     int wait_limit = kPersSpinLimit;   // polls before a persistent sweep gives up on a neighbour
     double ncg_tol = 0.0;   // > 0: residual stop of the inversion (conditional graph nodes)
@@ -327,13 +327,15 @@ int place_bricks(dscf_ctx* c) {
     if (tot > kMaxBricks) return fail(c, DSCF_ERR_ARG, "persistent sweeps: %d bricks exceed %d", tot, kMaxBricks);
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
         const Rep &A = c->L.reps[a], &B = c->L.reps[b];
-        return A.nx != B.nx ? A.nx < B.nx : A.N < B.N;
+        if (A.nx != B.nx) return A.nx < B.nx;
+        if (pers_pby(A) != pers_pby(B)) return pers_pby(A) < pers_pby(B);
+        return A.N < B.N;
     });
     std::vector<int4> table(tot);
     int* d_smid = (int*)pers_table(c);   // probe scratch: the table is uploaded after the probes
     std::vector<int4> ent;
     int first = 0;
-    auto close = [&](int width) -> int {
+    auto close = [&](int width, int pby) -> int {
         const int nb = (int)ent.size();
         if (!nb) return DSCF_OK;
         std::vector<int> smid(nb), ord(nb);
@@ -345,22 +347,23 @@ int place_bricks(dscf_ctx* c) {
         for (int i = 0; i < nb; ++i) ord[i] = i;
         std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return smid[a] < smid[b]; });
         for (int k = 0; k < nb; ++k) table[first + ord[k]] = ent[k];
-        c->pgroups.push_back({width, first, nb});
+        c->pgroups.push_back({width, pby, first, nb});
         first += nb;
         ent.clear();
         return DSCF_OK;
     };
-    int width = 0;
+    int width = 0, pby = 0;
     for (int r : order) {
         const Rep& R = c->L.reps[r];
         const int nb = pers_bricks(R, bz);
         if (nb > cap) return fail(c, DSCF_ERR_ARG, "persistent sweeps: replica %d has %d bricks, more than %d", r, nb, cap);
-        if (!ent.empty() && (R.nx != width || (int)ent.size() + nb > cap))
-            if (int rc = close(width)) return rc;
+        if (!ent.empty() && (R.nx != width || pers_pby(R) != pby || (int)ent.size() + nb > cap))
+            if (int rc = close(width, pby)) return rc;
         width = R.nx;
+        pby = pers_pby(R);
         for (int b = 0; b < nb; ++b) ent.push_back(make_int4(r, b, fbase[r], 0));
     }
-    if (int rc = close(width)) return rc;
+    if (int rc = close(width, pby)) return rc;
     int rc = cuda_check(c, cudaMemcpyAsync(pers_table(c), table.data(), sizeof(int4) * tot, cudaMemcpyHostToDevice, c->stream),
                         "brick table");
     if (!rc) rc = cuda_check(c, cudaStreamSynchronize(c->stream), "brick table");
@@ -371,8 +374,8 @@ int place_bricks(dscf_ctx* c) {
 // One direction of the persistent sweeps of every replica: one cooperative launch per group.
 int64_t launch_pers_sweeps(dscf_ctx* c, const Launch& L, bool bwd, int limit) {
     for (const auto& g : c->pgroups)
-        launch_prop_pers(L, bwd, g.width, c->pers_bz, c->pers_nw, g.nbricks, pers_table(c) + g.first, pers_flags(c),
-                         c->d_status + 2, limit);
+        launch_prop_pers(L, bwd, g.width, g.pby, c->pers_bz, c->pers_nw, g.nbricks, pers_table(c) + g.first,
+                         pers_flags(c), c->d_status + 2, limit);
     return (int64_t)c->pgroups.size();
 }
 
@@ -653,13 +656,10 @@ int pers_select(dscf_ctx* c, std::vector<std::pair<int, int>>& pcand) {
     if (pers_all_supported(c, 16, 16)) pcand.push_back({16, 16});
     if (pers_all_supported(c, 8, 8)) pcand.push_back({8, 8});
     for (auto& pc : pcand)
-        for (int wdt : {32, 48, 64, 96, 128}) {
-            bool used = false;
-            for (const Rep& R : c->L.reps) used = used || R.nx == wdt;
-            if (used)
-                if (int rc = cuda_check(c, (cudaError_t)pers_prepare(wdt, pc.first, pc.second), "persistent sweep set-up"))
-                    return rc;
-        }
+        for (const Rep& R : c->L.reps)
+            if (int rc = cuda_check(c, (cudaError_t)pers_prepare(R.nx, pers_pby(R), pc.first, pc.second),
+                                    "persistent sweep set-up"))
+                return rc;
     if (!pcand.empty()) {
         c->pers_bz = pcand[0].first;
         c->pers_nw = pcand[0].second;
@@ -1409,7 +1409,8 @@ int dscf_set_tuning(dscf_ctx* c, int32_t zc, int32_t kfuse) {
     }
     if (kfuse == 0 && (pbz != c->pers_bz || pnw != c->pers_nw || c->pgroups.empty())) {
         for (const Rep& R : c->L.reps)
-            if (int rc = cuda_check(c, (cudaError_t)pers_prepare(R.nx, pbz, pnw), "persistent sweep set-up")) return rc;
+            if (int rc = cuda_check(c, (cudaError_t)pers_prepare(R.nx, pers_pby(R), pbz, pnw), "persistent sweep set-up"))
+                return rc;
         c->pers_bz = pbz;
         c->pers_nw = pnw;
         if (int rc = reset_pers_flags(c)) return rc;

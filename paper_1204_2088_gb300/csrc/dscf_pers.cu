@@ -4,8 +4,9 @@
 // One launch runs a whole forward (or backward) sweep of N contour steps.  The lattice is cut
 // into bricks of nx x 8 x BZ sites, one brick per CTA (one CTA per SM for BZ = 16, two for
 // BZ = 8; the launch is cooperative, so all CTAs are resident together), one warp per plane of
-// the brick.  Rows of 64, 96 or 128 sites are held by a whole warp (2, 3 or 4 sites per lane),
-// rows of 32 or 48 sites by half a warp, two rows side by side.  A CTA takes its brick from a
+// the brick.  Rows of 96 or 128 sites are held by a whole warp (3 or 4 sites per lane), rows of
+// 32, 48 or 64 sites by half a warp (2, 3 or 4 sites per lane), two rows side by side; bricks of
+// these narrow rows have 16 rows instead of 8 where ny allows it.  A CTA takes its brick from a
 // table (replica, brick, flag base), so replicas of one row width share a launch; a brick waits
 // only on the bricks of its own replica.  A warp keeps its plane's x-filtered rows in registers
 // from one contour step to the next; per step the CTA only reads the halo rows and planes of its
@@ -32,7 +33,6 @@ namespace dscf {
 
 namespace {
 
-constexpr int PBY = 8;                 // brick rows
 // Polls of the backward G_s prefetch's mbarrier before giving up.  The copies depend on no other
 // CTA, so this bound is fixed and far above any real copy time (a shorter neighbour-wait limit set
 // for failure tests must not abandon a copy that is still landing in this CTA's shared memory).
@@ -139,17 +139,18 @@ __device__ __forceinline__ void wait_nb(const PersCtl& c, const int* nb, int tar
     __syncthreads();
 }
 
-template <int BZ, int NW>
+template <int BZ, int PBY>
 struct PersGeom {
     static constexpr int NH = 2 * (BZ + 2) + 2 * PBY;   // halo rows per step
 };
 
-// Row geometry of a brick of width W: a row is held by LPR lanes, VEC consecutive sites each;
-// a warp holds HALVES rows side by side (lanes 0..LPR-1 the first, LPR..31 the second), so each
-// lane carries RPL of the plane's PBY rows (rows h RPL .. h RPL + RPL - 1 for lane half h).
-template <int W>
+// Row geometry of a brick of width W and PBY rows: a row is held by LPR lanes, VEC consecutive
+// sites each; a warp holds HALVES rows side by side (lanes 0..LPR-1 the first, LPR..31 the
+// second), so each lane carries RPL of the plane's PBY rows (rows h RPL .. h RPL + RPL - 1 for
+// lane half h).
+template <int W, int PBY>
 struct PRow {
-    static constexpr int LPR = (W == 32 || W == 48) ? 16 : 32;
+    static constexpr int LPR = (W == 96 || W == 128) ? 32 : 16;
     static constexpr int VEC = W / LPR;
     static constexpr int HALVES = 32 / LPR;
     static constexpr int RPL = PBY / HALVES;
@@ -218,7 +219,8 @@ __device__ __forceinline__ void scalev(float c, unsigned long long c2, float (&v
 
 }  // namespace
 
-size_t pers_smem_bytes(int width, int bz) {
+size_t pers_smem_bytes(int width, int pby, int bz) {
+    const size_t PBY = (size_t)pby;
     // YS (y-filtered level, planes -1..bz) + XH (x-filtered y-halo rows of the own planes) + ZH
     // (x-filtered z-halo planes, rows -1..8) + halo staging + backward G_s of the brick
     const size_t rows = (size_t)(bz + 2) * PBY + 2 * (size_t)bz + 2 * (PBY + 2) + (2 * (bz + 2) + 2 * PBY) +
@@ -235,13 +237,13 @@ size_t pers_smem_bytes(int width, int bz) {
 // fence (the backward G+ interior is never stored: it stays in registers).
 // Each CTA takes its brick from the table: several replicas of the same row width run in one
 // launch, each brick waiting only on the bricks of its own replica.
-template <int W, int BZ, bool BWD, int NW>
+template <int W, int PBY, int BZ, bool BWD, int NW>
 __global__ void __launch_bounds__(32 * NW, 16 / NW) k_prop_pers(const Rep* __restrict__ reps, PersCtl ctl) {
     static_assert(NW == BZ, "one warp per plane");
-    using RG = PRow<W>;
+    using RG = PRow<W, PBY>;
     constexpr int VEC = RG::VEC, LPR = RG::LPR, HALVES = RG::HALVES, RPL = RG::RPL, CH = RG::CH;
     constexpr int PWARPS = NW;
-    using G = PersGeom<BZ, NW>;
+    using G = PersGeom<BZ, PBY>;
     extern __shared__ __align__(16) unsigned char smem[];
     float* YS = (float*)smem;                                  // [BZ+2][PBY][W]
     float* XH = YS + (BZ + 2) * PBY * W;                       // [2][BZ][W]   rows -1 and PBY
@@ -531,41 +533,55 @@ __global__ void __launch_bounds__(32 * NW, 16 / NW) k_prop_pers(const Rep* __res
 
 bool pers_width_ok(int nx) { return nx == 32 || nx == 48 || nx == 64 || nx == 96 || nx == 128; }
 
+// Brick rows: 16 for rows of at most 64 sites (so that a brick, and the co-resident launch, holds
+// as many sites as for the wider rows) where ny allows it, else 8.
+int pers_pby(const Rep& R) { return (R.nx <= 64 && R.ny % 16 == 0) ? 16 : 8; }
+
 bool pers_supported(const Rep& R, int bz, int nw, int nsm) {
-    if (!pers_width_ok(R.nx) || R.ny % PBY || R.nz % bz) return false;
+    if (!pers_width_ok(R.nx) || R.ny % 8 || R.nz % bz) return false;
     if (!((bz == 16 && nw == 16) || (bz == 8 && nw == 8 && R.nx == 128))) return false;   // one warp per plane
-    const int nb = (R.ny / PBY) * (R.nz / bz);
+    const int nb = pers_bricks(R, bz);
     return nb >= 1 && nb <= nsm * (nw == 8 ? 2 : 1);   // all bricks co-resident
 }
 
-int pers_bricks(const Rep& R, int bz) { return (R.ny / PBY) * (R.nz / bz); }
+int pers_bricks(const Rep& R, int bz) { return (R.ny / pers_pby(R)) * (R.nz / bz); }
 
 namespace {
-template <int W, int BZ, int NW>
+template <int W, int PBY, int BZ, int NW>
 cudaError_t pers_attr() {
-    const int sm = (int)pers_smem_bytes(W, BZ);
-    cudaError_t e = cudaFuncSetAttribute(k_prop_pers<W, BZ, false, NW>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_prop_pers<W, BZ, true, NW>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    const int sm = (int)pers_smem_bytes(W, PBY, BZ);
+    cudaError_t e = cudaFuncSetAttribute(k_prop_pers<W, PBY, BZ, false, NW>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_prop_pers<W, BZ, false, NW>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+        e = cudaFuncSetAttribute(k_prop_pers<W, PBY, BZ, true, NW>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_prop_pers<W, BZ, true, NW>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+        e = cudaFuncSetAttribute(k_prop_pers<W, PBY, BZ, false, NW>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_prop_pers<W, PBY, BZ, true, NW>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     return e;
 }
 }  // namespace
 
-int pers_prepare(int width, int bz, int nw) {
+int pers_prepare(int width, int pby, int bz, int nw) {
     if (bz == 16 && nw == 16) {
-        switch (width) {
-            case 128: return (int)pers_attr<128, 16, 16>();
-            case 96: return (int)pers_attr<96, 16, 16>();
-            case 64: return (int)pers_attr<64, 16, 16>();
-            case 48: return (int)pers_attr<48, 16, 16>();
-            case 32: return (int)pers_attr<32, 16, 16>();
-            default: break;
+        if (pby == 8) {
+            switch (width) {
+                case 128: return (int)pers_attr<128, 8, 16, 16>();
+                case 96: return (int)pers_attr<96, 8, 16, 16>();
+                case 64: return (int)pers_attr<64, 8, 16, 16>();
+                case 48: return (int)pers_attr<48, 8, 16, 16>();
+                case 32: return (int)pers_attr<32, 8, 16, 16>();
+                default: break;
+            }
+        } else if (pby == 16) {
+            switch (width) {
+                case 64: return (int)pers_attr<64, 16, 16, 16>();
+                case 48: return (int)pers_attr<48, 16, 16, 16>();
+                case 32: return (int)pers_attr<32, 16, 16, 16>();
+                default: break;
+            }
         }
     }
-    if (bz == 8 && nw == 8 && width == 128) return (int)pers_attr<128, 8, 8>();
+    if (bz == 8 && nw == 8 && width == 128 && pby == 8) return (int)pers_attr<128, 8, 8, 8>();
     return (int)cudaErrorInvalidValue;
 }
 
@@ -586,7 +602,7 @@ int pers_placement(int bz, int nw, int nbricks, int* d_smid, cudaStream_t stream
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(nbricks);
     cfg.blockDim = dim3(32 * nw);
-    cfg.dynamicSmemBytes = pers_smem_bytes(128, bz);
+    cfg.dynamicSmemBytes = pers_smem_bytes(128, 8, bz);
     cfg.stream = stream;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeCooperative;
@@ -605,8 +621,8 @@ int pers_placement(int bz, int nw, int nbricks, int* d_smid, cudaStream_t stream
     return (int)e;
 }
 
-int launch_prop_pers(const Launch& L, bool bwd, int width, int bz, int nw, int nbricks, const int4* table, int* flags,
-                     int* abortf, int limit) {
+int launch_prop_pers(const Launch& L, bool bwd, int width, int pby, int bz, int nw, int nbricks, const int4* table,
+                     int* flags, int* abortf, int limit) {
     PersCtl ctl;
     ctl.flags = flags;
     ctl.abort = abortf;
@@ -616,28 +632,35 @@ int launch_prop_pers(const Launch& L, bool bwd, int width, int bz, int nw, int n
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(nbricks);
     cfg.blockDim = dim3(32 * nw);
-    cfg.dynamicSmemBytes = pers_smem_bytes(width, bz);
+    cfg.dynamicSmemBytes = pers_smem_bytes(width, pby, bz);
     cfg.stream = L.stream;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeCooperative;
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-#define DSCF_PERS_LAUNCH(WW, BB, NN)                                                                     \
-    (bwd ? cudaLaunchKernelEx(&cfg, k_prop_pers<WW, BB, true, NN>, L.reps, ctl)                           \
-         : cudaLaunchKernelEx(&cfg, k_prop_pers<WW, BB, false, NN>, L.reps, ctl))
+#define DSCF_PERS_LAUNCH(WW, PP, BB, NN)                                                                 \
+    (bwd ? cudaLaunchKernelEx(&cfg, k_prop_pers<WW, PP, BB, true, NN>, L.reps, ctl)                       \
+         : cudaLaunchKernelEx(&cfg, k_prop_pers<WW, PP, BB, false, NN>, L.reps, ctl))
     cudaError_t e = cudaErrorInvalidValue;
-    if (bz == 16 && nw == 16) {
+    if (bz == 16 && nw == 16 && pby == 8) {
         switch (width) {
-            case 128: e = DSCF_PERS_LAUNCH(128, 16, 16); break;
-            case 96: e = DSCF_PERS_LAUNCH(96, 16, 16); break;
-            case 64: e = DSCF_PERS_LAUNCH(64, 16, 16); break;
-            case 48: e = DSCF_PERS_LAUNCH(48, 16, 16); break;
-            case 32: e = DSCF_PERS_LAUNCH(32, 16, 16); break;
+            case 128: e = DSCF_PERS_LAUNCH(128, 8, 16, 16); break;
+            case 96: e = DSCF_PERS_LAUNCH(96, 8, 16, 16); break;
+            case 64: e = DSCF_PERS_LAUNCH(64, 8, 16, 16); break;
+            case 48: e = DSCF_PERS_LAUNCH(48, 8, 16, 16); break;
+            case 32: e = DSCF_PERS_LAUNCH(32, 8, 16, 16); break;
             default: break;
         }
-    } else if (bz == 8 && nw == 8 && width == 128) {
-        e = DSCF_PERS_LAUNCH(128, 8, 8);
+    } else if (bz == 16 && nw == 16 && pby == 16) {
+        switch (width) {
+            case 64: e = DSCF_PERS_LAUNCH(64, 16, 16, 16); break;
+            case 48: e = DSCF_PERS_LAUNCH(48, 16, 16, 16); break;
+            case 32: e = DSCF_PERS_LAUNCH(32, 16, 16, 16); break;
+            default: break;
+        }
+    } else if (bz == 8 && nw == 8 && width == 128 && pby == 8) {
+        e = DSCF_PERS_LAUNCH(128, 8, 8, 8);
     }
 #undef DSCF_PERS_LAUNCH
     return (int)e;

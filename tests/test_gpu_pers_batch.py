@@ -1,5 +1,5 @@
 """Persistent contour sweeps over several replicas and row widths (Eq. 16-17), against the FP64
-oracle: every row width the sweep supports (32 and 48 sites: two rows per warp, 64, 96 and 128
+oracle: every row width the sweep supports (32, 48 and 64 sites: two rows per warp; 96 and 128
 sites: one), a batch of mixed widths, chain lengths and species counts in shared launches,
 bit-identity of a replica in the batch with its solo run, a race check, and the timeout of one
 brick inside a batch.  Tolerance: FP32 <= 1e-5 relative to the field's largest magnitude.
@@ -46,11 +46,13 @@ def ncomp_shape(cfg):
 
 
 @pytest.mark.parametrize("cfg", [melt((32, 16, 32), 7, 3), melt((48, 24, 16), 9, 4), solution((48, 8, 32), 6, 2),
-                                 melt((64, 16, 16), 5, 2), melt((96, 8, 32), 8, 5), solution((96, 16, 16), 7, 3)],
+                                 melt((48, 32, 16), 6, 2), melt((64, 16, 16), 5, 2), solution((64, 32, 16), 5, 2),
+                                 melt((64, 8, 32), 6, 4), melt((96, 8, 32), 8, 5), solution((96, 16, 16), 7, 3)],
                          ids=lambda c: "x".join(map(str, c["grid"])) + f"_ns{c['ns']}")
 def test_persistent_row_widths_fp32_within_1e5(cfg):
-    """One replica per width: the two-rows-per-warp layouts (32, 48), three sites per lane (48,
-    96) and the scalar tail of the packed pair arithmetic."""
+    """One replica per width: the two-rows-per-warp layouts (32, 48, 64), three sites per lane
+    (48, 96) with the scalar tail of the packed pair arithmetic, and bricks of 16 rows (narrow
+    rows with ny a multiple of 16) and of 8."""
     U = inputs.random_field(ncomp_shape(cfg), seed=21, scale=0.5)
     ref, _, _ = oracle.densities(cfg, U)
     ctx = dscf.Context(cfg, dscf.FP32)
@@ -125,7 +127,7 @@ def test_persistent_batch_timeout_is_reported_and_the_context_recovers():
     good = ctx.densities(flat)
     ctx.status()
     ctx.set_wait_limit(2000)
-    ctx.inject_lag(5)   # brick 0 of the third replica (flag indices follow the replicas in order)
+    ctx.inject_lag(0)   # brick 0 of the first replica, whose other brick then waits for it
     t0 = time.perf_counter()
     ctx.densities(flat)
     with pytest.raises(dscf.DSCFError) as err:
