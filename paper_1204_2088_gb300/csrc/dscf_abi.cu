@@ -303,11 +303,15 @@ int pers_total_bricks(const dscf_ctx* c) {
     return t;
 }
 
-// Launch groups and brick table of the persistent sweeps.  Replicas of one row width share a
-// launch while their bricks fit the co-resident CTAs (one per SM for bricks of 16 planes, two
-// for 8), taken in order of width and chain length so that the CTAs of a launch run about
-// equally long; every replica's bricks stay in one launch (they wait on one another).  Each
-// brick's step counter is at its replica's flag base (the replicas' bricks in index order).
+// Launch groups and brick table of the persistent sweeps.  The replicas are packed into
+// cooperative launches of at most as many bricks as can be co-resident (one per SM for bricks of
+// 16 planes, two for 8), every replica's bricks in one launch (they wait on one another): first
+// fit, replicas taken by decreasing chain length and then decreasing brick count, so that a launch
+// (which lasts as long as its longest chain) mostly holds chains of equal length.  A launch whose
+// replicas share one row width and brick height runs that width's kernel, any other the
+// mixed-width kernel (rows of 32 to 96 sites; 128-wide replicas share launches only with each
+// other).  Each brick's step counter is at its replica's flag base (the replicas'
+// bricks in index order).
 // Placement: the CTAs of a sweep-shaped cooperative launch land on SMs in a fixed pattern that
 // scatters consecutive CTA indices over the GPCs (and both dies); within a launch the bricks are
 // given to the CTAs in the order of their SM ids instead, so that the bricks of one z slab
@@ -317,53 +321,57 @@ int place_bricks(dscf_ctx* c) {
     c->pgroups.clear();
     const int n = c->nrep, bz = c->pers_bz;
     const int cap = std::min(c->nsm * (c->pers_nw == 8 ? 2 : 1), kMaxBricks);
-    std::vector<int> fbase(n), order(n);
+    std::vector<int> fbase(n), nbr(n), order(n);
     int tot = 0;
     for (int r = 0; r < n; ++r) {
         fbase[r] = tot;
-        tot += pers_bricks(c->L.reps[r], bz);
+        nbr[r] = pers_bricks(c->L.reps[r], bz);
+        tot += nbr[r];
         order[r] = r;
+        if (nbr[r] > cap)
+            return fail(c, DSCF_ERR_ARG, "persistent sweeps: replica %d has %d bricks, more than %d", r, nbr[r], cap);
     }
     if (tot > kMaxBricks) return fail(c, DSCF_ERR_ARG, "persistent sweeps: %d bricks exceed %d", tot, kMaxBricks);
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
         const Rep &A = c->L.reps[a], &B = c->L.reps[b];
-        if (A.nx != B.nx) return A.nx < B.nx;
-        if (pers_pby(A) != pers_pby(B)) return pers_pby(A) < pers_pby(B);
-        return A.N < B.N;
+        return A.N != B.N ? A.N > B.N : nbr[a] > nbr[b];
     });
+    std::vector<std::vector<int>> bins;
+    std::vector<int> load;
+    auto wide = [&](int r) { return c->L.reps[r].nx == 128; };   // 128-wide replicas share launches only with each other
+    for (int r : order) {
+        size_t k = 0;
+        while (k < bins.size() && (load[k] + nbr[r] > cap || wide(bins[k][0]) != wide(r))) ++k;
+        if (k == bins.size()) { bins.emplace_back(); load.push_back(0); }
+        bins[k].push_back(r);
+        load[k] += nbr[r];
+    }
     std::vector<int4> table(tot);
     int* d_smid = (int*)pers_table(c);   // probe scratch: the table is uploaded after the probes
-    std::vector<int4> ent;
     int first = 0;
-    auto close = [&](int width, int pby) -> int {
+    for (const auto& bin : bins) {
+        std::vector<int4> ent;
+        int width = c->L.reps[bin[0]].nx, pby = pers_pby(c->L.reps[bin[0]]);
+        for (int r : bin) {
+            const Rep& R = c->L.reps[r];
+            if (R.nx != width || pers_pby(R) != pby) width = pby = 0;   // mixed widths
+            for (int b = 0; b < nbr[r]; ++b) ent.push_back(make_int4(r, b, fbase[r], 0));
+        }
+        if (width == 0 && (bz != 16 || c->pers_nw != 16))
+            return fail(c, DSCF_ERR_ARG, "persistent sweeps: mixed row widths need bricks of 16 planes");
         const int nb = (int)ent.size();
-        if (!nb) return DSCF_OK;
         std::vector<int> smid(nb), ord(nb);
         int rc = cuda_check(c, (cudaError_t)pers_placement(bz, c->pers_nw, nb, d_smid, c->stream), "placement probe");
         if (!rc) rc = cuda_check(c, cudaMemcpyAsync(smid.data(), d_smid, sizeof(int) * nb, cudaMemcpyDeviceToHost, c->stream),
                                  "placement probe");
         if (!rc) rc = cuda_check(c, cudaStreamSynchronize(c->stream), "placement probe");
-        if (rc) return rc;
+        if (rc) { c->pgroups.clear(); return rc; }
         for (int i = 0; i < nb; ++i) ord[i] = i;
         std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return smid[a] < smid[b]; });
         for (int k = 0; k < nb; ++k) table[first + ord[k]] = ent[k];
         c->pgroups.push_back({width, pby, first, nb});
         first += nb;
-        ent.clear();
-        return DSCF_OK;
-    };
-    int width = 0, pby = 0;
-    for (int r : order) {
-        const Rep& R = c->L.reps[r];
-        const int nb = pers_bricks(R, bz);
-        if (nb > cap) return fail(c, DSCF_ERR_ARG, "persistent sweeps: replica %d has %d bricks, more than %d", r, nb, cap);
-        if (!ent.empty() && (R.nx != width || pers_pby(R) != pby || (int)ent.size() + nb > cap))
-            if (int rc = close(width, pby)) return rc;
-        width = R.nx;
-        pby = pers_pby(R);
-        for (int b = 0; b < nb; ++b) ent.push_back(make_int4(r, b, fbase[r], 0));
     }
-    if (int rc = close(width, pby)) return rc;
     int rc = cuda_check(c, cudaMemcpyAsync(pers_table(c), table.data(), sizeof(int4) * tot, cudaMemcpyHostToDevice, c->stream),
                         "brick table");
     if (!rc) rc = cuda_check(c, cudaStreamSynchronize(c->stream), "brick table");
@@ -655,11 +663,14 @@ int pers_select(dscf_ctx* c, std::vector<std::pair<int, int>>& pcand) {
     pcand.clear();
     if (pers_all_supported(c, 16, 16)) pcand.push_back({16, 16});
     if (pers_all_supported(c, 8, 8)) pcand.push_back({8, 8});
-    for (auto& pc : pcand)
+    for (auto& pc : pcand) {
         for (const Rep& R : c->L.reps)
             if (int rc = cuda_check(c, (cudaError_t)pers_prepare(R.nx, pers_pby(R), pc.first, pc.second),
                                     "persistent sweep set-up"))
                 return rc;
+        if (pc.first == 16)
+            if (int rc = cuda_check(c, (cudaError_t)pers_prepare(0, 0, 16, 16), "persistent sweep set-up")) return rc;
+    }
     if (!pcand.empty()) {
         c->pers_bz = pcand[0].first;
         c->pers_nw = pcand[0].second;
@@ -1411,6 +1422,8 @@ int dscf_set_tuning(dscf_ctx* c, int32_t zc, int32_t kfuse) {
         for (const Rep& R : c->L.reps)
             if (int rc = cuda_check(c, (cudaError_t)pers_prepare(R.nx, pers_pby(R), pbz, pnw), "persistent sweep set-up"))
                 return rc;
+        if (pbz == 16)
+            if (int rc = cuda_check(c, (cudaError_t)pers_prepare(0, 0, 16, 16), "persistent sweep set-up")) return rc;
         c->pers_bz = pbz;
         c->pers_nw = pnw;
         if (int rc = reset_pers_flags(c)) return rc;

@@ -383,12 +383,17 @@ template <typename T> void launch_lb_diag(const Launch& L);
 // persistent contour sweeps (FP32; row widths 32, 48, 64, 96, 128; several replicas of one width
 // per launch, each CTA taking its brick from an int4 table: replica, brick in the replica, flag
 // index of the replica's brick 0)
+// Brick rows: 16 for rows of at most 64 sites (so that a brick, and the co-resident launch, holds
+// as many sites as for the wider rows) where ny allows it, else 8.
+__host__ __device__ inline int pers_pby_of(int nx, int ny) { return (nx <= 64 && ny % 16 == 0) ? 16 : 8; }
 size_t pers_smem_bytes(int width, int pby, int bz);
+size_t pers_mix_smem_bytes();                                  // the mixed-width launches (width 0)
 bool pers_width_ok(int nx);
 int pers_pby(const Rep& R);                                    // brick rows of a replica (8 or 16)
 bool pers_supported(const Rep& R, int bz, int nw, int nsm);   // nw: warps per CTA (16, or 8 with 2 CTAs per SM)
 int pers_bricks(const Rep& R, int bz);
-int pers_prepare(int width, int pby, int bz, int nw);                                              // cudaError_t
+int pers_prepare(int width, int pby, int bz, int nw);   // cudaError_t; width 0: the mixed-width kernel
+// width 0: bricks of several widths in one launch (bricks of 16 planes)
 int launch_prop_pers(const Launch& L, bool bwd, int width, int pby, int bz, int nw, int nbricks, const int4* table,
                      int* flags, int* abortf, int limit);  // cudaError_t
 // SM id of each CTA of a sweep-shaped cooperative launch (cudaError_t)

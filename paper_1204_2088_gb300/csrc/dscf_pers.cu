@@ -29,6 +29,8 @@
 // and a global abort flag that makes every other CTA stop waiting, so the launch always finishes.
 #include "dscf_internal.cuh"
 
+#include <algorithm>
+
 namespace dscf {
 
 namespace {
@@ -238,7 +240,7 @@ size_t pers_smem_bytes(int width, int pby, int bz) {
 // Each CTA takes its brick from the table: several replicas of the same row width run in one
 // launch, each brick waiting only on the bricks of its own replica.
 template <int W, int PBY, int BZ, bool BWD, int NW>
-__global__ void __launch_bounds__(32 * NW, 16 / NW) k_prop_pers(const Rep* __restrict__ reps, PersCtl ctl) {
+__device__ __forceinline__ void pers_sweep(const Rep* __restrict__ reps, const PersCtl& ctl) {
     static_assert(NW == BZ, "one warp per plane");
     using RG = PRow<W, PBY>;
     constexpr int VEC = RG::VEC, LPR = RG::LPR, HALVES = RG::HALVES, RPL = RG::RPL, CH = RG::CH;
@@ -529,13 +531,43 @@ __global__ void __launch_bounds__(32 * NW, 16 / NW) k_prop_pers(const Rep* __res
     }
 }
 
+
+template <int W, int PBY, int BZ, bool BWD, int NW>
+__global__ void __launch_bounds__(32 * NW, 16 / NW) k_prop_pers(const Rep* __restrict__ reps, PersCtl ctl) {
+    pers_sweep<W, PBY, BZ, BWD, NW>(reps, ctl);
+}
+
+// Bricks of several row widths (32 to 96 sites) in one launch (batches): each CTA runs the sweep of
+// its replica's width; the launch's dynamic shared memory covers the largest.  128-wide replicas
+// keep launches of their own (with them in the same function the registers would spill).
+template <bool BWD>
+__global__ void __launch_bounds__(512, 1) k_prop_pers_mix(const Rep* __restrict__ reps, PersCtl ctl) {
+    const Rep& R = reps[ctl.table[blockIdx.x].x];
+    const int pby = pers_pby_of(R.nx, R.ny);
+    switch (R.nx * 32 + pby) {
+        case 32 * 32 + 8: pers_sweep<32, 8, 16, BWD, 16>(reps, ctl); break;
+        case 32 * 32 + 16: pers_sweep<32, 16, 16, BWD, 16>(reps, ctl); break;
+        case 48 * 32 + 8: pers_sweep<48, 8, 16, BWD, 16>(reps, ctl); break;
+        case 48 * 32 + 16: pers_sweep<48, 16, 16, BWD, 16>(reps, ctl); break;
+        case 64 * 32 + 8: pers_sweep<64, 8, 16, BWD, 16>(reps, ctl); break;
+        case 64 * 32 + 16: pers_sweep<64, 16, 16, BWD, 16>(reps, ctl); break;
+        case 96 * 32 + 8: pers_sweep<96, 8, 16, BWD, 16>(reps, ctl); break;
+        default: break;   // not reached: the host builds mixed launches of these widths only
+    }
+}
+
 // Host side ---------------------------------------------------------------------------------
 
 bool pers_width_ok(int nx) { return nx == 32 || nx == 48 || nx == 64 || nx == 96 || nx == 128; }
 
-// Brick rows: 16 for rows of at most 64 sites (so that a brick, and the co-resident launch, holds
-// as many sites as for the wider rows) where ny allows it, else 8.
-int pers_pby(const Rep& R) { return (R.nx <= 64 && R.ny % 16 == 0) ? 16 : 8; }
+int pers_pby(const Rep& R) { return pers_pby_of(R.nx, R.ny); }
+
+size_t pers_mix_smem_bytes() {
+    size_t m = 0;
+    for (int w : {32, 48, 64}) m = std::max(m, pers_smem_bytes(w, 16, 16));
+    for (int w : {32, 48, 64, 96}) m = std::max(m, pers_smem_bytes(w, 8, 16));
+    return m;
+}
 
 bool pers_supported(const Rep& R, int bz, int nw, int nsm) {
     if (!pers_width_ok(R.nx) || R.ny % 8 || R.nz % bz) return false;
@@ -562,6 +594,12 @@ cudaError_t pers_attr() {
 }  // namespace
 
 int pers_prepare(int width, int pby, int bz, int nw) {
+    if (width == 0) {
+        const int sm = (int)pers_mix_smem_bytes();
+        cudaError_t e = cudaFuncSetAttribute(k_prop_pers_mix<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_prop_pers_mix<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+        return (int)e;
+    }
     if (bz == 16 && nw == 16) {
         if (pby == 8) {
             switch (width) {
@@ -632,7 +670,7 @@ int launch_prop_pers(const Launch& L, bool bwd, int width, int pby, int bz, int 
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(nbricks);
     cfg.blockDim = dim3(32 * nw);
-    cfg.dynamicSmemBytes = pers_smem_bytes(width, pby, bz);
+    cfg.dynamicSmemBytes = width ? pers_smem_bytes(width, pby, bz) : pers_mix_smem_bytes();
     cfg.stream = L.stream;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeCooperative;
@@ -643,7 +681,10 @@ int launch_prop_pers(const Launch& L, bool bwd, int width, int pby, int bz, int 
     (bwd ? cudaLaunchKernelEx(&cfg, k_prop_pers<WW, PP, BB, true, NN>, L.reps, ctl)                       \
          : cudaLaunchKernelEx(&cfg, k_prop_pers<WW, PP, BB, false, NN>, L.reps, ctl))
     cudaError_t e = cudaErrorInvalidValue;
-    if (bz == 16 && nw == 16 && pby == 8) {
+    if (width == 0 && bz == 16 && nw == 16) {
+        e = bwd ? cudaLaunchKernelEx(&cfg, k_prop_pers_mix<true>, L.reps, ctl)
+                : cudaLaunchKernelEx(&cfg, k_prop_pers_mix<false>, L.reps, ctl);
+    } else if (bz == 16 && nw == 16 && pby == 8) {
         switch (width) {
             case 128: e = DSCF_PERS_LAUNCH(128, 8, 16, 16); break;
             case 96: e = DSCF_PERS_LAUNCH(96, 8, 16, 16); break;
