@@ -4,6 +4,8 @@ benchmark times, and over a long FP32 trajectory.
   - One coupled step of the 128^3 melt (N = 64, nA = 19, chi N = 25), FP32, in the tuning the
     autotuner picks for the benchmark (persistent contour sweeps: 128 bricks, one per SM), from a
     random state: every output field against the oracle's step from the same state.
+  - One coupled step of the 48 mixed replicas (24 x 48^3, 16 x 64^3, 8 x 96^3) in the tuning the
+    autotuner picks (persistent sweeps over the batch), three sampled replicas against the oracle.
   - 1000 FP32 steps of the 32^3 melt of the plain-method workload (N = 32, f = 0.5) at chi N = 8,
     below the spinodal, where rounding differences are damped instead of amplified: the
     compositions stay within 1e-5 of the FP64 oracle's trajectory (relative to their largest
@@ -64,6 +66,39 @@ def test_bench_configuration_one_step_fp32_matches_oracle():
     assert rel(got["ulat"], st["ulat"]) < 1e-4, rel(got["ulat"], st["ulat"])
     # population deviations (about 1e-3 w_i) carry the FP32 rounding of the full populations
     assert rel(got["pop"], st["pop"]) < 1e-4, rel(got["pop"], st["pop"])
+
+
+def test_batch48_configuration_one_step_fp32_matches_oracle_on_sampled_replicas():
+    """The 48 mixed replicas in the configuration the benchmark times (the autotuner's choice:
+    persistent sweeps over the batch, mixed-width launches), one coupled step from a random state;
+    three replicas, one of each size and chain length (48^3 N = 32, 64^3 N = 48, 96^3 N = 64),
+    against the oracle's step of that replica alone."""
+    cfgs = inputs.batch48()
+    _, w, _, _ = oracle.lb_basis()
+    states = []
+    for r, c in enumerate(cfgs):
+        nx, ny, nz = c["grid"]
+        phi = inputs.initial_fields(dict(c, noise=0.04, seed=300 + r))
+        U = inputs.random_field((2, nz, ny, nx), seed=400 + r, scale=0.2)
+        dn = 1e-3 * inputs.random_field((19, nz, ny, nx), seed=500 + r) * w[:, None, None, None]
+        states.append(tuple(a.astype(np.float32).astype(np.float64) for a in (phi, U, dn)))
+    ctx = dscf.Context(cfgs, dscf.FP32)
+    assert ctx.diagnostics()["kfuse"] == 0, "the benchmark configuration runs the persistent sweeps"
+    for k, f in ((0, dscf.PHI), (1, dscf.U), (2, dscf.POP)):
+        ctx.set(f, torch.cat([torch.from_numpy(st[k]).float().reshape(-1) for st in states]).cuda())
+    ctx.step(1)
+    ctx.status()
+    got = {k: t2n(ctx.get(f)) for k, f in (("phi", dscf.PHI), ("U", dscf.U), ("mu", dscf.MU))}
+    ctx.close()
+    offs = np.cumsum([0] + [2 * int(np.prod(c["grid"])) for c in cfgs])
+    for r in (0, 25, 41):
+        c = cfgs[r]
+        nx, ny, nz = c["grid"]
+        phi32, U32, dn32 = states[r]
+        st = oracle.step(c, phi32, U32, dn32 + w[:, None, None, None], phi32.reshape(2, -1).sum(1))
+        for k in ("phi", "U", "mu"):
+            mine = got[k][offs[r]:offs[r + 1]].reshape(2, nz, ny, nx)
+            assert rel(mine, st[k]) < 1e-5, (r, k, rel(mine, st[k]))
 
 
 def test_fp32_trajectory_of_1000_steps_stays_within_1e5_of_the_oracle():
