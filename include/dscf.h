@@ -212,13 +212,13 @@ int64_t dscf_launches_per_step(const dscf_ctx* ctx);
 /* Override the autotuner's choice (for instance with a value cached from an earlier run):
  * zc = z planes per propagator tile (>= 1), kfuse = contour steps per propagator launch (1..4;
  * > 1 needs FP32 and nx in {32, 64, 128} for every replica, and kfuse <= N), or kfuse = 0 for
- * persistent sweeps (FP32; every replica with nx in {32, 48, 64, 96, 128}, ny a multiple of 8 and
- * nz of 16, and at most one brick per SM; bricks of nx x 8 x 16 sites, one CTA of 16 warps per
- * SM, one warp per plane; replicas of one row width share a cooperative launch while their bricks
- * fit the SMs together, so a batch takes one launch per sweep direction and group; one 128-wide
- * replica may instead use bricks of 128 x 8 x 8 sites, two CTAs of 8 warps per SM, nz a multiple
- * of 8).  With kfuse = 0, zc = 16 or 8 selects the brick depth (DSCF_ERR_ARG if the grids do not
- * allow it), any other zc keeps the current depth.  Synchronises the stream; the
+ * persistent sweeps (FP32; every replica with nx in {32, 48, 64, 96, 128} and ny a multiple of 8;
+ * bricks of nx x 8 x 16 sites (nx x 16 x 16 for rows of at most 64 sites where ny allows), one
+ * CTA of 16 warps per SM, or of nx x 8 x 8 (nx x 16 x 8) sites, two CTAs of 8 warps per SM; nz a
+ * multiple of the brick depth; one warp per plane; replicas share cooperative launches while
+ * their bricks fit the SMs together, so a batch takes a few launches per sweep direction).  With
+ * kfuse = 0, zc = 16 or 8 selects the brick depth (DSCF_ERR_ARG if the grids do not allow it),
+ * any other zc keeps the current depth.  Synchronises the stream; the
  * next dscf_step re-captures its graph.  Results do not depend on either value beyond rounding. */
 int dscf_set_tuning(dscf_ctx* ctx, int32_t zc, int32_t kfuse);
 

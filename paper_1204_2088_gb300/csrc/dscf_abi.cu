@@ -357,8 +357,6 @@ int place_bricks(dscf_ctx* c) {
             if (R.nx != width || pers_pby(R) != pby) width = pby = 0;   // mixed widths
             for (int b = 0; b < nbr[r]; ++b) ent.push_back(make_int4(r, b, fbase[r], 0));
         }
-        if (width == 0 && (bz != 16 || c->pers_nw != 16))
-            return fail(c, DSCF_ERR_ARG, "persistent sweeps: mixed row widths need bricks of 16 planes");
         const int nb = (int)ent.size();
         std::vector<int> smid(nb), ord(nb);
         int rc = cuda_check(c, (cudaError_t)pers_placement(bz, c->pers_nw, nb, d_smid, c->stream), "placement probe");
@@ -648,7 +646,6 @@ void set_zc(dscf_ctx* c, int zc) {
 // configuration.
 bool pers_all_supported(const dscf_ctx* c, int bz, int nw) {
     if (c->prec != DSCF_FP32) return false;
-    if (nw == 8 && c->nrep != 1) return false;   // bricks of 8 planes: one 128-wide replica
     const int nsm = std::min(c->nsm, kMaxBricks / 2);
     long long tot = 0;
     for (const Rep& R : c->L.reps) {
@@ -668,8 +665,8 @@ int pers_select(dscf_ctx* c, std::vector<std::pair<int, int>>& pcand) {
             if (int rc = cuda_check(c, (cudaError_t)pers_prepare(R.nx, pers_pby(R), pc.first, pc.second),
                                     "persistent sweep set-up"))
                 return rc;
-        if (pc.first == 16)
-            if (int rc = cuda_check(c, (cudaError_t)pers_prepare(0, 0, 16, 16), "persistent sweep set-up")) return rc;
+        if (int rc = cuda_check(c, (cudaError_t)pers_prepare(0, 0, pc.first, pc.second), "persistent sweep set-up"))
+            return rc;
     }
     if (!pcand.empty()) {
         c->pers_bz = pcand[0].first;
@@ -1398,8 +1395,8 @@ int dscf_set_tuning(dscf_ctx* c, int32_t zc, int32_t kfuse) {
     if (kfuse > 1 && !c->fusable) return fail(c, DSCF_ERR_ARG, "contour fusion needs FP32 and nx in {32, 64, 128}");
     if (kfuse == 0 && !c->pers_bz)
         return fail(c, DSCF_ERR_ARG,
-                    "persistent sweeps need FP32 replicas with nx in {32, 48, 64, 96, 128}, ny %% 8 = 0 and nz %% 16 = 0 "
-                    "(nz %% 8 = 0 for bricks of 8 planes: one 128-wide replica), at most one brick per SM each");
+                    "persistent sweeps need FP32 replicas with nx in {32, 48, 64, 96, 128}, ny %% 8 = 0 and nz a "
+                    "multiple of the brick depth (16, or 8), and all bricks co-resident");
     int pbz = c->pers_bz, pnw = c->pers_nw;
     if (kfuse == 0 && (zc == 8 || zc == 16)) {   // brick depth requested
         if (zc == 16 && pers_all_supported(c, 16, 16)) { pbz = 16; pnw = 16; }
@@ -1422,8 +1419,7 @@ int dscf_set_tuning(dscf_ctx* c, int32_t zc, int32_t kfuse) {
         for (const Rep& R : c->L.reps)
             if (int rc = cuda_check(c, (cudaError_t)pers_prepare(R.nx, pers_pby(R), pbz, pnw), "persistent sweep set-up"))
                 return rc;
-        if (pbz == 16)
-            if (int rc = cuda_check(c, (cudaError_t)pers_prepare(0, 0, 16, 16), "persistent sweep set-up")) return rc;
+        if (int rc = cuda_check(c, (cudaError_t)pers_prepare(0, 0, pbz, pnw), "persistent sweep set-up")) return rc;
         c->pers_bz = pbz;
         c->pers_nw = pnw;
         if (int rc = reset_pers_flags(c)) return rc;

@@ -387,7 +387,7 @@ template <typename T> void launch_lb_diag(const Launch& L);
 // as many sites as for the wider rows) where ny allows it, else 8.
 __host__ __device__ inline int pers_pby_of(int nx, int ny) { return (nx <= 64 && ny % 16 == 0) ? 16 : 8; }
 size_t pers_smem_bytes(int width, int pby, int bz);
-size_t pers_mix_smem_bytes();                                  // the mixed-width launches (width 0)
+size_t pers_mix_smem_bytes(int bz);                            // the mixed-width launches (width 0)
 bool pers_width_ok(int nx);
 int pers_pby(const Rep& R);                                    // brick rows of a replica (8 or 16)
 bool pers_supported(const Rep& R, int bz, int nw, int nsm);   // nw: warps per CTA (16, or 8 with 2 CTAs per SM)

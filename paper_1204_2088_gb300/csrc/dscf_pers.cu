@@ -540,18 +540,18 @@ __global__ void __launch_bounds__(32 * NW, 16 / NW) k_prop_pers(const Rep* __res
 // Bricks of several row widths (32 to 96 sites) in one launch (batches): each CTA runs the sweep of
 // its replica's width; the launch's dynamic shared memory covers the largest.  128-wide replicas
 // keep launches of their own (with them in the same function the registers would spill).
-template <bool BWD>
-__global__ void __launch_bounds__(512, 1) k_prop_pers_mix(const Rep* __restrict__ reps, PersCtl ctl) {
+template <int BZ, bool BWD, int NW>
+__global__ void __launch_bounds__(32 * NW, 16 / NW) k_prop_pers_mix(const Rep* __restrict__ reps, PersCtl ctl) {
     const Rep& R = reps[ctl.table[blockIdx.x].x];
     const int pby = pers_pby_of(R.nx, R.ny);
     switch (R.nx * 32 + pby) {
-        case 32 * 32 + 8: pers_sweep<32, 8, 16, BWD, 16>(reps, ctl); break;
-        case 32 * 32 + 16: pers_sweep<32, 16, 16, BWD, 16>(reps, ctl); break;
-        case 48 * 32 + 8: pers_sweep<48, 8, 16, BWD, 16>(reps, ctl); break;
-        case 48 * 32 + 16: pers_sweep<48, 16, 16, BWD, 16>(reps, ctl); break;
-        case 64 * 32 + 8: pers_sweep<64, 8, 16, BWD, 16>(reps, ctl); break;
-        case 64 * 32 + 16: pers_sweep<64, 16, 16, BWD, 16>(reps, ctl); break;
-        case 96 * 32 + 8: pers_sweep<96, 8, 16, BWD, 16>(reps, ctl); break;
+        case 32 * 32 + 8: pers_sweep<32, 8, BZ, BWD, NW>(reps, ctl); break;
+        case 32 * 32 + 16: pers_sweep<32, 16, BZ, BWD, NW>(reps, ctl); break;
+        case 48 * 32 + 8: pers_sweep<48, 8, BZ, BWD, NW>(reps, ctl); break;
+        case 48 * 32 + 16: pers_sweep<48, 16, BZ, BWD, NW>(reps, ctl); break;
+        case 64 * 32 + 8: pers_sweep<64, 8, BZ, BWD, NW>(reps, ctl); break;
+        case 64 * 32 + 16: pers_sweep<64, 16, BZ, BWD, NW>(reps, ctl); break;
+        case 96 * 32 + 8: pers_sweep<96, 8, BZ, BWD, NW>(reps, ctl); break;
         default: break;   // not reached: the host builds mixed launches of these widths only
     }
 }
@@ -562,16 +562,17 @@ bool pers_width_ok(int nx) { return nx == 32 || nx == 48 || nx == 64 || nx == 96
 
 int pers_pby(const Rep& R) { return pers_pby_of(R.nx, R.ny); }
 
-size_t pers_mix_smem_bytes() {
+size_t pers_mix_smem_bytes(int bz) {
     size_t m = 0;
-    for (int w : {32, 48, 64}) m = std::max(m, pers_smem_bytes(w, 16, 16));
-    for (int w : {32, 48, 64, 96}) m = std::max(m, pers_smem_bytes(w, 8, 16));
+    for (int w : {32, 48, 64}) m = std::max(m, pers_smem_bytes(w, 16, bz));
+    for (int w : {32, 48, 64, 96}) m = std::max(m, pers_smem_bytes(w, 8, bz));
     return m;
 }
 
+// Brick depths: 16 planes on 16 warps (one CTA per SM) or 8 planes on 8 warps (two CTAs per SM).
 bool pers_supported(const Rep& R, int bz, int nw, int nsm) {
     if (!pers_width_ok(R.nx) || R.ny % 8 || R.nz % bz) return false;
-    if (!((bz == 16 && nw == 16) || (bz == 8 && nw == 8 && R.nx == 128))) return false;   // one warp per plane
+    if (!((bz == 16 && nw == 16) || (bz == 8 && nw == 8))) return false;   // one warp per plane
     const int nb = pers_bricks(R, bz);
     return nb >= 1 && nb <= nsm * (nw == 8 ? 2 : 1);   // all bricks co-resident
 }
@@ -591,36 +592,46 @@ cudaError_t pers_attr() {
         e = cudaFuncSetAttribute(k_prop_pers<W, PBY, BZ, true, NW>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     return e;
 }
+template <int BZ, int NW>
+cudaError_t pers_mix_attr() {
+    const int sm = (int)pers_mix_smem_bytes(BZ);
+    cudaError_t e = cudaFuncSetAttribute(k_prop_pers_mix<BZ, false, NW>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_prop_pers_mix<BZ, true, NW>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_prop_pers_mix<BZ, false, NW>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_prop_pers_mix<BZ, true, NW>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    return e;
+}
 }  // namespace
 
+// ACTION(W, PBY, BZ, NW) for the instantiated (width, rows) pairs of one brick depth
+#define DSCF_PERS_SWITCH(BB, NN, ACTION)                          \
+    switch (width * 32 + pby) {                                  \
+        case 128 * 32 + 8: ACTION(128, 8, BB, NN); break;        \
+        case 96 * 32 + 8: ACTION(96, 8, BB, NN); break;          \
+        case 64 * 32 + 8: ACTION(64, 8, BB, NN); break;          \
+        case 64 * 32 + 16: ACTION(64, 16, BB, NN); break;        \
+        case 48 * 32 + 8: ACTION(48, 8, BB, NN); break;          \
+        case 48 * 32 + 16: ACTION(48, 16, BB, NN); break;        \
+        case 32 * 32 + 8: ACTION(32, 8, BB, NN); break;          \
+        case 32 * 32 + 16: ACTION(32, 16, BB, NN); break;        \
+        default: break;                                          \
+    }
+
 int pers_prepare(int width, int pby, int bz, int nw) {
-    if (width == 0) {
-        const int sm = (int)pers_mix_smem_bytes();
-        cudaError_t e = cudaFuncSetAttribute(k_prop_pers_mix<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_prop_pers_mix<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-        return (int)e;
-    }
+    cudaError_t e = cudaErrorInvalidValue;
+#define DSCF_PERS_ATTR(WW, PP, BB, NN) e = pers_attr<WW, PP, BB, NN>()
     if (bz == 16 && nw == 16) {
-        if (pby == 8) {
-            switch (width) {
-                case 128: return (int)pers_attr<128, 8, 16, 16>();
-                case 96: return (int)pers_attr<96, 8, 16, 16>();
-                case 64: return (int)pers_attr<64, 8, 16, 16>();
-                case 48: return (int)pers_attr<48, 8, 16, 16>();
-                case 32: return (int)pers_attr<32, 8, 16, 16>();
-                default: break;
-            }
-        } else if (pby == 16) {
-            switch (width) {
-                case 64: return (int)pers_attr<64, 16, 16, 16>();
-                case 48: return (int)pers_attr<48, 16, 16, 16>();
-                case 32: return (int)pers_attr<32, 16, 16, 16>();
-                default: break;
-            }
-        }
+        if (width == 0) e = pers_mix_attr<16, 16>();
+        else DSCF_PERS_SWITCH(16, 16, DSCF_PERS_ATTR)
+    } else if (bz == 8 && nw == 8) {
+        if (width == 0) e = pers_mix_attr<8, 8>();
+        else DSCF_PERS_SWITCH(8, 8, DSCF_PERS_ATTR)
     }
-    if (bz == 8 && nw == 8 && width == 128 && pby == 8) return (int)pers_attr<128, 8, 8, 8>();
-    return (int)cudaErrorInvalidValue;
+#undef DSCF_PERS_ATTR
+    return (int)e;
 }
 
 namespace {
@@ -670,41 +681,31 @@ int launch_prop_pers(const Launch& L, bool bwd, int width, int pby, int bz, int 
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(nbricks);
     cfg.blockDim = dim3(32 * nw);
-    cfg.dynamicSmemBytes = width ? pers_smem_bytes(width, pby, bz) : pers_mix_smem_bytes();
+    cfg.dynamicSmemBytes = width ? pers_smem_bytes(width, pby, bz) : pers_mix_smem_bytes(bz);
     cfg.stream = L.stream;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeCooperative;
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-#define DSCF_PERS_LAUNCH(WW, PP, BB, NN)                                                                 \
-    (bwd ? cudaLaunchKernelEx(&cfg, k_prop_pers<WW, PP, BB, true, NN>, L.reps, ctl)                       \
-         : cudaLaunchKernelEx(&cfg, k_prop_pers<WW, PP, BB, false, NN>, L.reps, ctl))
     cudaError_t e = cudaErrorInvalidValue;
-    if (width == 0 && bz == 16 && nw == 16) {
-        e = bwd ? cudaLaunchKernelEx(&cfg, k_prop_pers_mix<true>, L.reps, ctl)
-                : cudaLaunchKernelEx(&cfg, k_prop_pers_mix<false>, L.reps, ctl);
-    } else if (bz == 16 && nw == 16 && pby == 8) {
-        switch (width) {
-            case 128: e = DSCF_PERS_LAUNCH(128, 8, 16, 16); break;
-            case 96: e = DSCF_PERS_LAUNCH(96, 8, 16, 16); break;
-            case 64: e = DSCF_PERS_LAUNCH(64, 8, 16, 16); break;
-            case 48: e = DSCF_PERS_LAUNCH(48, 8, 16, 16); break;
-            case 32: e = DSCF_PERS_LAUNCH(32, 8, 16, 16); break;
-            default: break;
-        }
-    } else if (bz == 16 && nw == 16 && pby == 16) {
-        switch (width) {
-            case 64: e = DSCF_PERS_LAUNCH(64, 16, 16, 16); break;
-            case 48: e = DSCF_PERS_LAUNCH(48, 16, 16, 16); break;
-            case 32: e = DSCF_PERS_LAUNCH(32, 16, 16, 16); break;
-            default: break;
-        }
-    } else if (bz == 8 && nw == 8 && width == 128 && pby == 8) {
-        e = DSCF_PERS_LAUNCH(128, 8, 8, 8);
+#define DSCF_PERS_LAUNCH(WW, PP, BB, NN)                                                                  \
+    e = bwd ? cudaLaunchKernelEx(&cfg, k_prop_pers<WW, PP, BB, true, NN>, L.reps, ctl)                    \
+            : cudaLaunchKernelEx(&cfg, k_prop_pers<WW, PP, BB, false, NN>, L.reps, ctl)
+    if (bz == 16 && nw == 16) {
+        if (width == 0)
+            e = bwd ? cudaLaunchKernelEx(&cfg, k_prop_pers_mix<16, true, 16>, L.reps, ctl)
+                    : cudaLaunchKernelEx(&cfg, k_prop_pers_mix<16, false, 16>, L.reps, ctl);
+        else DSCF_PERS_SWITCH(16, 16, DSCF_PERS_LAUNCH)
+    } else if (bz == 8 && nw == 8) {
+        if (width == 0)
+            e = bwd ? cudaLaunchKernelEx(&cfg, k_prop_pers_mix<8, true, 8>, L.reps, ctl)
+                    : cudaLaunchKernelEx(&cfg, k_prop_pers_mix<8, false, 8>, L.reps, ctl);
+        else DSCF_PERS_SWITCH(8, 8, DSCF_PERS_LAUNCH)
     }
 #undef DSCF_PERS_LAUNCH
     return (int)e;
 }
+#undef DSCF_PERS_SWITCH
 
 }  // namespace dscf

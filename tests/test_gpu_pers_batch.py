@@ -2,7 +2,8 @@
 oracle: every row width the sweep supports (32, 48 and 64 sites: two rows per warp; 96 and 128
 sites: one), a batch of mixed widths, chain lengths and species counts in shared launches,
 bit-identity of a replica in the batch with its solo run, a race check, and the timeout of one
-brick inside a batch.  Tolerance: FP32 <= 1e-5 relative to the field's largest magnitude.
+brick inside a batch, for bricks of 16 planes (one CTA per SM) and of 8 (two CTAs per SM).
+Tolerance: FP32 <= 1e-5 relative to the field's largest magnitude.
 """
 import numpy as np
 import pytest
@@ -49,14 +50,17 @@ def ncomp_shape(cfg):
                                  melt((48, 32, 16), 6, 2), melt((64, 16, 16), 5, 2), solution((64, 32, 16), 5, 2),
                                  melt((64, 8, 32), 6, 4), melt((96, 8, 32), 8, 5), solution((96, 16, 16), 7, 3)],
                          ids=lambda c: "x".join(map(str, c["grid"])) + f"_ns{c['ns']}")
-def test_persistent_row_widths_fp32_within_1e5(cfg):
+@pytest.mark.parametrize("depth", [16, 8])
+def test_persistent_row_widths_fp32_within_1e5(cfg, depth):
     """One replica per width: the two-rows-per-warp layouts (32, 48, 64), three sites per lane
     (48, 96) with the scalar tail of the packed pair arithmetic, and bricks of 16 rows (narrow
-    rows with ny a multiple of 16) and of 8."""
+    rows with ny a multiple of 16) and of 8; bricks of 16 planes (one CTA per SM) and of 8 (two)."""
+    if cfg["grid"][2] % depth:
+        pytest.skip("brick depth does not divide nz")
     U = inputs.random_field(ncomp_shape(cfg), seed=21, scale=0.5)
     ref, _, _ = oracle.densities(cfg, U)
     ctx = dscf.Context(cfg, dscf.FP32)
-    ctx.set_tuning(16, 0)
+    ctx.set_tuning(depth, 0)
     assert ctx.diagnostics()["kfuse"] == 0
     for _ in range(2):      # the brick step counters carry over between launches
         got = t2n(ctx.densities(torch.from_numpy(U)))
@@ -81,13 +85,14 @@ def _split(flat, cfgs):
     return out
 
 
-def test_persistent_batch_of_mixed_widths_matches_oracle_and_solo_runs():
+@pytest.mark.parametrize("depth", [16, 8])
+def test_persistent_batch_of_mixed_widths_matches_oracle_and_solo_runs(depth):
     """Seven replicas (widths 32 to 128, chain lengths 4 to 9, melts and a solution) in the
     persistent launches of one context: each against the oracle, and bit-identical to the same
     replica's own persistent sweep (a brick's arithmetic does not depend on the launch it is in)."""
     Us = _batch_U(BATCH, 30)
     ctx = dscf.Context(BATCH, dscf.FP32)
-    ctx.set_tuning(16, 0)
+    ctx.set_tuning(depth, 0)
     assert ctx.diagnostics()["kfuse"] == 0
     flat = torch.cat([torch.from_numpy(U).float().reshape(-1) for U in Us])
     got = _split(ctx.densities(flat).cpu(), BATCH)
@@ -96,18 +101,19 @@ def test_persistent_batch_of_mixed_widths_matches_oracle_and_solo_runs():
         ref, _, _ = oracle.densities(cfg, U)
         assert rel(got[r].numpy().astype(np.float64), ref) < 1e-5, r
         solo = dscf.Context(cfg, dscf.FP32)
-        solo.set_tuning(16, 0)
+        solo.set_tuning(depth, 0)
         one = solo.densities(torch.from_numpy(U)).cpu()
         solo.status()
         assert torch.equal(one, got[r]), r
 
 
-def test_persistent_batch_is_deterministic():
+@pytest.mark.parametrize("depth", [16, 8])
+def test_persistent_batch_is_deterministic(depth):
     """Race check of the handshake with several replicas per launch: repeated density maps are
     bitwise equal."""
     Us = _batch_U(BATCH, 40)
     ctx = dscf.Context(BATCH, dscf.FP32)
-    ctx.set_tuning(16, 0)
+    ctx.set_tuning(depth, 0)
     flat = torch.cat([torch.from_numpy(U).float().reshape(-1) for U in Us])
     first = ctx.densities(flat)
     for _ in range(10):
@@ -115,14 +121,15 @@ def test_persistent_batch_is_deterministic():
     ctx.status()
 
 
-def test_persistent_batch_timeout_is_reported_and_the_context_recovers():
+@pytest.mark.parametrize("depth", [16, 8])
+def test_persistent_batch_timeout_is_reported_and_the_context_recovers(depth):
     """A lagging brick of one replica (host-side counter set far behind): its neighbours' bounded
     waits run out, the abort flag releases every CTA of every launch, the host reads
     DSCF_ERR_TIMEOUT, and the context computes the same densities again afterwards."""
     import time
     Us = _batch_U(BATCH, 50)
     ctx = dscf.Context(BATCH, dscf.FP32)
-    ctx.set_tuning(16, 0)
+    ctx.set_tuning(depth, 0)
     flat = torch.cat([torch.from_numpy(U).float().reshape(-1) for U in Us])
     good = ctx.densities(flat)
     ctx.status()
@@ -140,14 +147,15 @@ def test_persistent_batch_timeout_is_reported_and_the_context_recovers():
     assert torch.equal(again, good)
 
 
-def test_persistent_batch_step_matches_multi_launch():
+@pytest.mark.parametrize("depth", [16, 8])
+def test_persistent_batch_step_matches_multi_launch(depth):
     """A whole time step (inversion, LB, convection-diffusion) of a mixed batch with persistent
     sweeps against the single-step contour kernels."""
     cfgs = [melt((48, 16, 16), 6, 3, hydro=1, ncg_iters=2, cn_sweeps=4, seed=3),
             melt((96, 8, 16), 8, 3, hydro=1, ncg_iters=2, cn_sweeps=4, seed=4)]
     phis = [inputs.initial_fields(c) for c in cfgs]
     outs = []
-    for kfuse, zc in ((1, 8), (0, 16)):
+    for kfuse, zc in ((1, 8), (0, depth)):
         ctx = dscf.Context(cfgs, dscf.FP32)
         ctx.set_tuning(zc, kfuse)
         ctx.set(dscf.PHI, torch.cat([torch.from_numpy(p).reshape(-1) for p in phis]).cuda())
