@@ -56,7 +56,7 @@ enum { ST_NONFINITE = 1, ST_TIMEOUT = 2 };
 // counter per persistent brick.
 constexpr int kFlagBase = 64;
 constexpr int kFlagStride = 32;   // ints between brick step counters: one 128-byte line each
-constexpr int kMaxBricks = 2048;
+constexpr int kMaxBricks = 4096;
 // status block: the words above, kMaxBricks counters, then the int4 brick table of the sweeps
 constexpr size_t kStatusInts = (size_t)kFlagBase + (size_t)kMaxBricks * kFlagStride + 4 * (size_t)kMaxBricks;
 
