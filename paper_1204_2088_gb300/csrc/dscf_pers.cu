@@ -224,7 +224,7 @@ __device__ __forceinline__ void scalev(float c, unsigned long long c2, float (&v
 size_t pers_smem_bytes(int width, int pby, int bz) {
     const size_t PBY = (size_t)pby;
     // YS (y-filtered level, planes -1..bz) + XH (x-filtered y-halo rows of the own planes) + ZH
-    // (x-filtered z-halo planes, rows -1..8) + halo staging + backward G_s of the brick
+    // (x-filtered z-halo planes, rows -1..pby) + halo staging + backward G_s of the brick
     const size_t rows = (size_t)(bz + 2) * PBY + 2 * (size_t)bz + 2 * (PBY + 2) + (2 * (bz + 2) + 2 * PBY) +
                         (size_t)bz * PBY;
     return rows * (size_t)width * sizeof(float);
@@ -237,8 +237,9 @@ size_t pers_smem_bytes(int width, int pby, int bz) {
 // of the neighbouring planes.  The z-halo planes are y-filtered one row per lane half.  Brick-
 // boundary values are stored and published first; the rest of the forward G_s follows without a
 // fence (the backward G+ interior is never stored: it stays in registers).
-// Each CTA takes its brick from the table: several replicas of the same row width run in one
-// launch, each brick waiting only on the bricks of its own replica.
+// Each CTA takes its brick from the table, so several replicas run in one launch (of one row
+// width here; the mixed-width kernel below calls this per CTA), each brick waiting only on the
+// bricks of its own replica.
 template <int W, int PBY, int BZ, bool BWD, int NW>
 __device__ __forceinline__ void pers_sweep(const Rep* __restrict__ reps, const PersCtl& ctl) {
     static_assert(NW == BZ, "one warp per plane");
