@@ -202,9 +202,9 @@ def test_cached_tuning_reproduces_the_autotuned_context(tmp_path):
     assert np.array_equal(outs[0], outs[1])
     with pytest.raises(dscf.DSCFError):
         dscf.Context(cfg, dscf.FP32, tuning=(4, 9))
-    bad = melt((64, 16, 16), 8, 3, hydro=1)
+    bad = melt((40, 16, 16), 8, 3, hydro=1)
     with pytest.raises(dscf.DSCFError):
-        dscf.Context(bad, dscf.FP32, tuning=(8, 0))   # persistent sweeps need nx = 128
+        dscf.Context(bad, dscf.FP32, tuning=(8, 0))   # persistent sweeps need nx in {32, 48, 64, 96, 128}
 
 
 def test_fused_step_fp32_matches_single_step():
