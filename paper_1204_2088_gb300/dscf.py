@@ -290,10 +290,16 @@ class Context:
         return out
 
     def set(self, which, t):
+        """Field from a device tensor, or from a host tensor: a pinned host tensor of the context's
+        dtype is copied asynchronously on the context's stream (the caller keeps it unchanged until
+        the next synchronising call), any other host tensor is staged and waited for."""
         if isinstance(t, torch.Tensor) and t.device.type == "cpu":
             src = t.to(self.dtype).contiguous()
             self._check(self.lib.dscf_set_fields(self.h, which, ctypes.c_void_p(src.data_ptr()), 1))
-            torch.cuda.current_stream(self.device).synchronize()
+            if src.data_ptr() == t.data_ptr() and t.is_pinned():
+                self._keep = src
+            else:
+                self.stream.synchronize()
             return
         src = self._as_field(t, which)
         self._check(self.lib.dscf_set_fields(self.h, which, ctypes.c_void_p(src.data_ptr()), 0))

@@ -632,3 +632,30 @@ def test_extrapolated_warm_start_fp64_matches_oracle(tol):
             its = sum(1 for j in range(12) if st["info"][2 + 4 * j + 3] != 0.0)
             assert ctx.diagnostics()["ncg_iters"] == its, k
     ctx.close()
+
+
+def test_host_buffers_round_trip_and_pinned_upload_is_ordered():
+    """Fields through host memory: a pinned host tensor is uploaded asynchronously on the
+    context's stream (no wait), then stepped and read back into the same pinned tensor; the result
+    equals the same step from a device-resident upload, and a pageable upload gives it too."""
+    cfg = melt((32, 16, 24), 10, 4, hydro=1, ncg_iters=2, cn_sweeps=4)
+    phi, U, dn = random_state(cfg, 95)
+    outs = []
+    for mode in ("device", "pinned", "pageable"):
+        ctx = dscf.Context(cfg, dscf.FP32)
+        ctx.set(dscf.U, torch.from_numpy(U).float().cuda())
+        ctx.set(dscf.POP, torch.from_numpy(dn).float().cuda())
+        host = torch.from_numpy(phi).float()
+        if mode == "device":
+            ctx.set(dscf.PHI, host.cuda())
+        elif mode == "pinned":
+            host = host.pin_memory()
+            ctx.set(dscf.PHI, host)
+        else:
+            ctx.set(dscf.PHI, host)
+        ctx.step(2)
+        out = torch.empty(host.shape, dtype=torch.float32).pin_memory()
+        ctx.get_host(dscf.PHI, out)
+        ctx.status()
+        outs.append(out.numpy().copy())
+    assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[0], outs[2])
