@@ -118,11 +118,11 @@ struct PersCtl {
 // Wait until every neighbour brick has published `target`; threads 0..7 poll one neighbour each
 // (each counter on its own cache line).  Only the pollers look at the shared abort flag, and only
 // every 32 polls, so that the waits of all CTAs do not contend on one line.
-__device__ __forceinline__ void wait_nb(const PersCtl& c, const int* nb, int target, bool& aborted) {
+__device__ __forceinline__ void wait_nb(const PersCtl& c, const int* nb, unsigned target, bool& aborted) {
     if (threadIdx.x < 8 && !aborted) {
         const int* f = c.flags + (size_t)nb[threadIdx.x] * kFlagStride;
         int spins = 0;
-        while (ld_acquire(f) < target) {
+        while ((int)((unsigned)ld_acquire(f) - target) < 0) {   // wrap-safe: counters only grow
             if ((++spins & 31) == 0) {
                 if (ld_acquire(c.abort) != 0) {
                     aborted = true;
@@ -299,7 +299,8 @@ __device__ __forceinline__ void pers_sweep(const Rep* __restrict__ reps, const P
         const int y = (y0 + r + ny) % ny, z = (z0 + pl + nz) % nz;
         hoff[h] = z * plane + y * W;
     }
-    const int c0 = ctl.flags[(size_t)fown * kFlagStride];   // step counters of a replica's bricks are equal at launch
+    // step counters of a replica's bricks are equal at launch (unsigned: they may wrap in long runs)
+    const unsigned c0 = (unsigned)ctl.flags[(size_t)fown * kFlagStride];
     bool aborted = ld_acquire(ctl.abort) != 0;
 
     auto xpass = [&](const float (&v)[VEC], float (&o)[VEC]) {   // x pass of a periodic row: v + r (left + right)
@@ -409,7 +410,7 @@ __device__ __forceinline__ void pers_sweep(const Rep* __restrict__ reps, const P
         // halo of the previous step, x-filtered into XH / ZH; each warp copies and filters the
         // rows of its own lane halves (a __syncwarp makes every lane's copied chunk visible)
         if (j > 0) {
-            wait_nb(ctl, nbs, c0 + j, aborted);
+            wait_nb(ctl, nbs, c0 + (unsigned)j, aborted);
             const float* src = BWD ? (const float*)(((j - 1) & 1) ? R.Gp1 : R.Gp0)
                                    : (const float*)R.G + (size_t)(s - 2) * V;
             {
@@ -507,7 +508,7 @@ __device__ __forceinline__ void pers_sweep(const Rep* __restrict__ reps, const P
         // reads the new counter sees them.  The barrier also ends every warp's reads of YS, XH
         // and ZH for this step.
         __syncthreads();
-        if (threadIdx.x == 0) st_release(ctl.flags + (size_t)fown * kFlagStride, c0 + j + 1);
+        if (threadIdx.x == 0) st_release(ctl.flags + (size_t)fown * kFlagStride, (int)(c0 + (unsigned)j + 1u));
         if (BWD && s > 1) prefetch_gs(s - 1);   // GS slots of this thread were read above
 #pragma unroll
         for (int p = 0; p < RPL; ++p) {
