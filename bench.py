@@ -345,6 +345,36 @@ def learned_form(cfg, dev, phi0, timed, world, tuning, steps):
     return out
 
 
+def learned256_form(dev, timed, rank, world, steps=40):
+    """The learned predictor on its own workload: the 256^3 symmetric melt (f = 0.5, chi N = 20,
+    N = 64), corrector every 10 steps; the exact FP32 step at the same size beside it (these rows
+    of 256 sites take the multi-launch contour kernels: a persistent sweep cannot hold 16.8 M sites).
+    The network is trained as in the 128^3 form, on 32^3 boxes of this physics, and fine-tuned on
+    ten exact steps of the run."""
+    import numpy as np
+    import torch
+
+    from paper_1204_2088_gb300 import dscf, inputs, replicas
+
+    cfg = inputs.workload("melt256", seed=replicas.rank_seed(5, rank))
+    V = int(np.prod(cfg["grid"]))
+    phi0 = torch.from_numpy(inputs.initial_fields(cfg)).float().to(dev)
+    c = dscf.Context(cfg, dscf.FP32, device=dev)
+    d = c.diagnostics()
+    tuning = (d["zc"], d["kfuse"])
+    c.set(dscf.PHI, phi0)
+    c.step(12)
+    k = 10
+    ms = timed(lambda: c.step(k))
+    c.status()
+    c.close()
+    out = learned_form(cfg, dev, phi0, timed, world, tuning, steps)
+    out["exact"] = {"value": replicas.aggregate_rate([V * k] * world, [ms]), "ms_per_step": ms / k, "steps": k,
+                    "tuning": list(tuning)}
+    out["workload"] = "melt256: AB diblock melt, 256^3, N=64, f=0.5, chi N=20, dt=0.1 tau"
+    return out
+
+
 def residual_stop_form(cfg, dev, phi0, timed, world, tuning, steps):
     """The FP32 step with the inversion stopped on its residual (at most ncg_iters iterations,
     fewer once max|phi* - phi[U]| < tol), measured early after the quench (from step 30) and later
@@ -664,6 +694,8 @@ def run_ours(a):
         forms["solution128"] = solution_form(dev, timed, rank, world, max(10, min(a.steps, 20)))
     if "fp32_learned" in want:
         forms["fp32_learned"] = learned_form(cfg, dev, phi0, timed, world, tuning, max(20, min(a.steps, 40)))
+    if "fp32_learned_256" in want:   # not in the default list: about four minutes
+        forms["fp32_learned_256"] = learned256_form(dev, timed, rank, world)
     if "batch48" in want:
         forms["batch48"] = batch48_form(dev, timed, rank, world, max(3, min(a.steps // 10, 10)))
     if "net_forward" in want:
