@@ -211,7 +211,8 @@ int64_t dscf_launches_per_step(const dscf_ctx* ctx);
 
 /* Override the autotuner's choice (for instance with a value cached from an earlier run):
  * zc = z planes per propagator tile (>= 1), kfuse = contour steps per propagator launch (1..4;
- * > 1 needs FP32 and nx in {32, 64, 128} for every replica, and kfuse <= N), or kfuse = 0 for
+ * > 1 needs FP32 and nx in {32, 64, 128} for every replica, or nx = 256 for every replica with
+ * kfuse <= 2 (rows of 256 sites have contour kernels of their own), and kfuse <= N), or kfuse = 0 for
  * persistent sweeps (FP32; every replica with nx in {32, 48, 64, 96, 128} and ny a multiple of 8;
  * bricks of nx x 8 x 16 sites (nx x 16 x 16 for rows of at most 64 sites where ny allows), one
  * CTA of 16 warps per SM, or of nx x 8 x 8 (nx x 16 x 8) sites, two CTAs of 8 warps per SM; nz a

@@ -28,6 +28,7 @@ struct Layout {
     std::vector<size_t> fwd_smem, bwd_smem;   // [s] dynamic shared memory of the contour launches
     size_t es = 8;
     int ntiles = 0, nblk = 0, nlb = 0, Nmax = 0;
+    bool w8 = false;                // every replica in whole rows of 256 sites
     size_t bytes = 0;
     // offsets of the shared blocks
     size_t off_reps = 0, off_t2r = 0, off_b2r = 0, off_status = 0;
@@ -133,6 +134,8 @@ Layout make_layout(const dscf_params* p, int n, int prec, char* base) {
     L.reps.resize(n);
     long long ext = 0, vb = 0;
     int max_tiles_total = 0, max_blk_total = 0;
+    L.w8 = true;
+    for (int r = 0; r < n; ++r) L.w8 = L.w8 && p[r].nx == 256;
     for (int r = 0; r < n; ++r) {
         Rep& R = L.reps[r];
         std::memset(&R, 0, sizeof(Rep));
@@ -140,12 +143,12 @@ Layout make_layout(const dscf_params* p, int n, int prec, char* base) {
         const dscf_params& q = p[r];
         R.nx = q.nx; R.ny = q.ny; R.nz = q.nz; R.ns = q.ns; R.N = q.N; R.nA = q.nA;
         R.V = (long long)q.nx * q.ny * q.nz;
-        tile_replica(R, kMinZc);
+        tile_replica(R, kMinZc, L.w8);
         const int max_tiles = R.ntiles;
         max_tiles_total += max_tiles;
         max_blk_total += R.nblk;
         R.part_stride = std::max(std::max(max_tiles, R.nblk), R.lb_nblk);
-        tile_replica(R, default_zc(q.nz));
+        tile_replica(R, default_zc(q.nz), L.w8);
         R.hydro = q.hydro;
         R.cn_sweeps = q.cn_sweeps;
         R.phi_p = q.phi_p; R.kappa = q.kappa; R.alpha = q.a * q.a / 6.0; R.dt = q.dt; R.M = q.M;
@@ -285,6 +288,7 @@ Launch launch_of(dscf_ctx* c, cudaStream_t s) {
     L.nrep = c->nrep;
     L.noise = c->noise;
     L.stream = s;
+    L.w8 = c->L.w8 ? 1 : 0;
     return L;
 }
 
@@ -637,7 +641,7 @@ int upload_tiles(dscf_ctx* c) {
 }
 
 void set_zc(dscf_ctx* c, int zc) {
-    for (int r = 0; r < c->nrep; ++r) tile_replica(c->L.reps[r], std::min(zc, c->L.reps[r].nz));
+    for (int r = 0; r < c->nrep; ++r) tile_replica(c->L.reps[r], std::min(zc, c->L.reps[r].nz), c->L.w8);
     assign_tiles(c->L, c->params.data(), c->nrep);
 }
 
@@ -701,7 +705,7 @@ int autotune_zc(dscf_ctx* c) {
         if (int rc = cuda_check(c, cudaEventCreate(&e1), "tune event")) { cudaEventDestroy(e0); return rc; }
         float best_ms = 1e30f;
         const int cands[] = {4, 5, 6, 8, 11, 16, 22, 32};
-        const int kmax = c->fusable ? std::min(4, Nmin) : 1;
+        const int kmax = c->fusable ? std::min(c->L.w8 ? 2 : 4, Nmin) : 1;   // rows of 256 sites: two steps
         for (int zc : cands) {
             set_zc(c, zc);
             if (int rc = upload_tiles(c)) { cudaEventDestroy(e0); cudaEventDestroy(e1); return rc; }
@@ -1394,7 +1398,9 @@ int dscf_set_predictor(dscf_ctx* c, dscf_net* net, int32_t corrector_every, doub
 int dscf_set_tuning(dscf_ctx* c, int32_t zc, int32_t kfuse) {
     if (!c) return DSCF_ERR_ARG;
     if (zc < 1 || kfuse < 0 || kfuse > 4) return fail(c, DSCF_ERR_ARG, "need zc >= 1 and 0 <= kfuse <= 4");
-    if (kfuse > 1 && !c->fusable) return fail(c, DSCF_ERR_ARG, "contour fusion needs FP32 and nx in {32, 64, 128}");
+    if (kfuse > 1 && !c->fusable)
+        return fail(c, DSCF_ERR_ARG, "contour fusion needs FP32 and nx in {32, 64, 128} (or 256 for every replica)");
+    if (kfuse > 2 && c->L.w8) return fail(c, DSCF_ERR_ARG, "rows of 256 sites fuse at most two contour steps");
     if (kfuse == 0 && !c->pers_bz)
         return fail(c, DSCF_ERR_ARG,
                     "persistent sweeps need FP32 replicas with nx in {32, 48, 64, 96, 128}, ny %% 8 = 0 and nz a "

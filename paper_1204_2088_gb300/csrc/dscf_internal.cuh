@@ -105,8 +105,10 @@ struct Rep {
 
 // Propagator and flat tiling of one replica for a given z-chunk; the context path and the
 // allocation-free path both use it.
-inline void tile_replica(Rep& R, int zc) {
-    R.vec = (R.nx == 32 || R.nx == 64 || R.nx == 128) ? R.nx / 32 : 0;
+// rows256: every replica of the launch has rows of 256 sites, which then take the whole-row
+// contour kernels of their own (8 sites per lane); otherwise such rows take the tiled layout.
+inline void tile_replica(Rep& R, int zc, bool rows256 = false) {
+    R.vec = (R.nx == 32 || R.nx == 64 || R.nx == 128) ? R.nx / 32 : ((rows256 && R.nx == 256) ? 8 : 0);
     R.tiles_x = R.vec ? 1 : (R.nx + kPropCols - 1) / kPropCols;
     R.tiles_y = (R.ny + kPropRows - 1) / kPropRows;
     R.zc = zc < 1 ? 1 : (zc > R.nz ? R.nz : zc);
@@ -134,6 +136,7 @@ struct Launch {
     int nrep;
     int noise;               // thermal noise: 1 compositions, 2 LB modes
     cudaStream_t stream;
+    int w8 = 0;              // every replica in whole rows of 256 sites (their own contour kernels)
 };
 
 // ---------------------------------------------------------------------------------------------

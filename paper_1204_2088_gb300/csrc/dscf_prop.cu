@@ -326,6 +326,23 @@ __global__ void __launch_bounds__(32 * NWARP) k_prop(const Rep* __restrict__ rep
     }
 }
 
+// Rows of 256 sites (8 per lane) in kernels of their own: in the kernels above they would raise
+// the register count, and so cut the occupancy, of every other row width.
+template <typename T, bool BWD>
+__global__ void __launch_bounds__(32 * NWARP) k_prop_w8(const Rep* __restrict__ reps, const int* __restrict__ tile2rep,
+                                                        int step) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ double sh[33];
+    const Rep& R = reps[tile2rep[blockIdx.x]];
+    const int lt = blockIdx.x - R.tile0;
+    const PropOps<T> o = prop_ops<T, BWD>(R, step);
+    const double qacc = prop_row<T, BWD, 8>(R, lt, o, smem);
+    if (!BWD && o.lastQ) {
+        const double t = block_sum(qacc, sh);
+        if (threadIdx.x == 0) slot(R, P_Q)[lt] = t;
+    }
+}
+
 // ---------------------------------------------------------------------------------------------
 // Contour-step fusion (whole-row layout, FP32): one launch advances a group of up to K contour
 // steps.  Warp w holds row y0 - K + w (ROWS output rows plus K halo rows on each side); level 0 is
@@ -517,6 +534,24 @@ __device__ __forceinline__ double prop_fused_row(const Rep& R, int lt, int g, un
     return qacc;
 }
 
+// Rows of 256 sites: two contour steps per launch (more would spill), in a kernel of their own.
+template <bool BWD>
+__global__ void __launch_bounds__(32 * (kPropRows + 4)) k_prop_fused_w8(const Rep* __restrict__ reps,
+                                                                       const int* __restrict__ tile2rep, int g) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ double sh[33];
+    const Rep& R = reps[tile2rep[blockIdx.x]];
+    const int lt = blockIdx.x - R.tile0;
+    const double qacc = prop_fused_row<BWD, 8, 2>(R, lt, g, smem);
+    if (!BWD) {
+        const bool lastQ = (g * 2 + 2 >= R.N);   // this group reaches s = N
+        if (lastQ) {
+            const double t = block_sum(qacc, sh);
+            if (threadIdx.x == 0) slot(R, P_Q)[lt] = t;
+        }
+    }
+}
+
 template <bool BWD, int K>
 __global__ void __launch_bounds__(32 * (kPropRows + 2 * K)) k_prop_fused(const Rep* __restrict__ reps,
                                                                         const int* __restrict__ tile2rep, int g) {
@@ -670,12 +705,14 @@ __global__ void __launch_bounds__(kFlatThreads) k_exp(const Rep* __restrict__ re
 template <typename T>
 void launch_prop_fwd(const Launch& L, int s, int grid, size_t smem) {
     if (grid <= 0) return;
-    k_prop<T, false><<<grid, 32 * NWARP, smem, L.stream>>>(L.reps, L.tile2rep, s);
+    if (L.w8) k_prop_w8<T, false><<<grid, 32 * NWARP, smem, L.stream>>>(L.reps, L.tile2rep, s);
+    else k_prop<T, false><<<grid, 32 * NWARP, smem, L.stream>>>(L.reps, L.tile2rep, s);
 }
 template <typename T>
 void launch_prop_bwd(const Launch& L, int j, int grid, size_t smem) {
     if (grid <= 0) return;
-    k_prop<T, true><<<grid, 32 * NWARP, smem, L.stream>>>(L.reps, L.tile2rep, j);
+    if (L.w8) k_prop_w8<T, true><<<grid, 32 * NWARP, smem, L.stream>>>(L.reps, L.tile2rep, j);
+    else k_prop<T, true><<<grid, 32 * NWARP, smem, L.stream>>>(L.reps, L.tile2rep, j);
 }
 size_t prop_fused_smem_bytes(int vec, int K) {
     return (size_t)(K * 2 + 4) * (kPropRows + 2 * K) * 32 * (vec > 0 ? vec : 1) * sizeof(float);
@@ -684,7 +721,11 @@ int prop_fused_threads(int K) { return 32 * (kPropRows + 2 * K); }
 void launch_prop_fused(const Launch& L, bool bwd, int K, int g, int grid, size_t smem) {
     if (grid <= 0) return;
     const int th = prop_fused_threads(K);
-    if (K == 2) {
+    if (L.w8) {   // two steps per launch only (the host never asks for more)
+        if (K != 2) return;
+        if (bwd) k_prop_fused_w8<true><<<grid, th, smem, L.stream>>>(L.reps, L.tile2rep, g);
+        else k_prop_fused_w8<false><<<grid, th, smem, L.stream>>>(L.reps, L.tile2rep, g);
+    } else if (K == 2) {
         if (bwd) k_prop_fused<true, 2><<<grid, th, smem, L.stream>>>(L.reps, L.tile2rep, g);
         else k_prop_fused<false, 2><<<grid, th, smem, L.stream>>>(L.reps, L.tile2rep, g);
     } else if (K == 3) {
@@ -704,6 +745,9 @@ int prop_fused_set_smem_limit(size_t bytes) {
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_prop_fused<true, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_prop_fused<false, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_prop_fused<true, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+    const int b8 = (int)prop_fused_smem_bytes(8, 2);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_prop_fused_w8<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, b8);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_prop_fused_w8<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, b8);
     return (int)e;
 }
 
@@ -712,6 +756,9 @@ int prop_set_smem_limit(size_t bytes) {
     cudaError_t e = cudaFuncSetAttribute(k_prop<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_prop<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    const int b8 = (int)prop_smem(8, true, sizeof(T));
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_prop_w8<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, b8);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_prop_w8<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, b8);
     return (int)e;
 }
 size_t prop_smem_bytes(int vec, bool bwd, size_t es) { return prop_smem(vec, bwd, es); }

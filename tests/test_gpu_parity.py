@@ -49,6 +49,7 @@ DENSITY_CASES = [
     melt((40, 20, 36), 8, 3),          # several tiles in x, y and z, ragged in each
     solution((33, 17, 9), 7, 4),       # solvent, odd sizes
     melt((1, 3, 70), 5, 2),            # degenerate x, z chunking with a ragged tail
+    melt((256, 9, 5), 6, 2),           # whole rows of 256 sites (8 per lane, kernels of their own), ragged y
 ]
 
 
@@ -80,6 +81,7 @@ FUSED_CASES = [
     (melt((32, 12, 10), 9, 4), 5),
     (melt((64, 9, 21), 11, 3), 8),
     (solution((128, 10, 6), 7, 5), 4),
+    (melt((256, 11, 9), 7, 3), 4),     # rows of 256 sites: at most two steps per launch
 ]
 
 
@@ -92,6 +94,10 @@ def test_fused_contour_groups_fp32_within_1e5(case, kfuse):
     U = inputs.random_field(ncomp_shape(cfg), seed=9, scale=0.5)
     ref, _, _ = oracle.densities(cfg, U)
     ctx = dscf.Context(cfg, dscf.FP32)
+    if cfg["grid"][0] == 256 and kfuse > 2:
+        with pytest.raises(dscf.DSCFError):
+            ctx.set_tuning(zc, kfuse)
+        return
     ctx.set_tuning(zc, kfuse)
     got = t2n(ctx.densities(torch.from_numpy(U)))
     assert ctx.diagnostics()["kfuse"] == kfuse
