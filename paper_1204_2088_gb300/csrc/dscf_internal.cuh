@@ -407,7 +407,7 @@ int pers_placement(int bz, int nw, int nbricks, int* d_smid, cudaStream_t stream
 namespace dscf {
 // tcgen05 forward convolution of the predictor network (dscf_tc.cu)
 bool tc_conv_supported(int nx, int ny);
-size_t tc_conv_smem(int ci, int co);
+size_t tc_conv_smem();
 int tc_conv_prepare();   // cudaError_t
 int tc_conv_blocks(int nx, int ny, int nz);   // CTAs per sample
 void launch_conv_tc(int layer, const void* in, const void* wt, const float* bias, int cout, void* out, int nx, int ny,

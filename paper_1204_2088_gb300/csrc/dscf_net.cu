@@ -254,7 +254,9 @@ __global__ void k_net_in(const float* __restrict__ U, const double* __restrict__
 }
 
 // Network input with the five x offsets folded into the channels (tcgen05 first layer):
-// xf[r][2 dx + c] = U_c[r + dx - 2 along x] - <U_c> for dx = 0..4, zero in channels 10..15.
+// xf[r][2 dx + c] = U_c[r + dx - 2 along x] - <U_c> for dx = 0..4, zero in channels 10..15, stored
+// by channel group within each x row, [B][nz][ny][2][nx][8], so that a group's part of a row is
+// contiguous.
 __global__ void k_net_in_fold(const float* __restrict__ U, const double* __restrict__ means, int nx, int V, int B,
                               bf16* __restrict__ xf) {
     const size_t r = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
@@ -275,9 +277,9 @@ __global__ void k_net_in_fold(const float* __restrict__ U, const double* __restr
     }
 #pragma unroll
     for (int c = 10; c < 16; ++c) v[c] = __float2bfloat16(0.f);
-    uint4* dst = (uint4*)(xf + r * 16);
-    dst[0] = *(const uint4*)&v[0];
-    dst[1] = *(const uint4*)&v[8];
+    bf16* dst = xf + ((size_t)b * V + row) * 16 + (size_t)x * 8;   // group 0; group 1 follows nx sites later
+    *(uint4*)dst = *(const uint4*)&v[0];
+    *(uint4*)(dst + (size_t)nx * 8) = *(const uint4*)&v[8];
 }
 
 // Network output: phi_c[r] = phibar_c + y[r][c] - <y_c>  ([B][2][V] float).

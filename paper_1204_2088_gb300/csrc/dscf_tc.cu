@@ -4,19 +4,21 @@
 //
 // GEMM view: for an output row of 128 sites along x, D[x][co] = sum over the 125 offsets
 // (dz, dy, dx) and input channels ci of A[x][ci] B[co][ci] with A the input row (y+dy, z+dz)
-// shifted by dx.  One CTA computes 4 output rows (y0..y0+3, z, x0..x0+127) into 4 TMEM
-// accumulators of 128 lanes x CO columns.  For each dz it stages the 8 input rows y0-2..y0+5 of
-// plane z+dz (periodic) in shared memory in the no-swizzle K-major operand layout
+// shifted by dx.  A CTA computes R output rows (y0..y0+R-1, z, x0..x0+127) into TMEM accumulators
+// of 128 lanes x CO columns.  For each dz the R + 4 input rows y0-2..y0+R+1 of plane z+dz
+// (periodic) sit in shared memory in the no-swizzle K-major operand layout
 //   [row][channel group of 8][x' = 0..131][8 channels]  (x' = x - x0 + 2),
 // in which 8 consecutive sites of one channel group form a contiguous 128-byte core matrix: the
 // descriptor has 128 B between core matrices along M (sites) and 132 x 16 B between channel
-// groups along K, and the shift by dx is just 16 dx bytes added to its start address.  The
-// weights of the (dy, dx) offsets of that dz are staged in two halves (dy 0..2, dy 3..4) as
-// [offset][channel group][co][8], the same layout for the N x K operand; the smaller footprint
-// lets two CTAs share an SM, one staging while the other's MMAs run.  One thread issues the M = 128, N = CO, K = 16 MMAs; a
-// tcgen05.commit on an mbarrier tells the CTA when the staged operands may be overwritten, and
-// after the last dz when the accumulators are complete.  The epilogue (bias, tanh, BF16 or FP32
+// groups along K, and the shift by dx is just 16 dx bytes added to its start address.  Weights
+// are staged as [offset][channel group][co][8], the same layout for the N x K operand.  One
+// thread issues the MMAs; tcgen05.commit on an mbarrier tells the CTA when staged operands may be
+// overwritten and when the accumulators are complete.  The epilogue (bias, tanh, BF16 or FP32
 // channel-last stores) reads each warp's quarter of the TMEM lanes with tcgen05.ld.
+//
+// The first layer (2 input channels, R = 4) folds the five x offsets into 16 channels and fills
+// its staged rows with bulk (TMA) copies, two planes in flight; the 32-channel layers stack the
+// five dy offsets along N (R = 8 and 4) and stage with per-thread 16-byte copies.
 //
 // Every wait is bounded; a CTA that gives up sets the error word, frees its tensor memory and
 // returns.
@@ -134,33 +136,47 @@ __device__ __forceinline__ int wrapi_(int v, int n) {
     return v < 0 ? v + n : v;
 }
 
-// EPI 0: tanh(acc + bias) -> BF16 [site][CO]; EPI 1: acc + bias -> FP32 [site][16] (CO = 16),
-// and the CTA's FP64 sums of channels 0 and 1 into part[(b * 2 + c) * nblk + i] (i: the CTA's
-// index within its sample, nblk: CTAs per sample), for the network's mean removal.
-// in: [B][V][CI] BF16 channel-last; wt: [125][CI/8][CO][8] BF16; bias: cout values.
-// FOLD: the input holds, in channels 2 dx + ci (dx = 0..4, ci = 0..1), the two real input channels
-// at x + dx - 2 (zero in channels 10..15), so one K = 16 step covers all five x offsets: the
-// offsets are (dz, dy) only, with weights [dz][dy][k / 8][co][k % 8].
-template <int CI, int CO, int EPI, bool FOLD>
+// Bulk (TMA) copies global -> shared completing on an mbarrier: both addresses 16-byte aligned,
+// bytes a multiple of 16.
+__device__ __forceinline__ void mbar_expect(uint64_t* mbar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(mbar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* mbar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(mbar))
+                 : "memory");
+}
+
+// First layer (2 -> 32 channels, tanh) on the folded input: channels 2 dx + ci (dx = 0..4,
+// ci = 0..1) hold the two real input channels at x + dx - 2 (zero in channels 10..15), so one
+// K = 16 step covers all five x offsets and the offsets left are the 25 (dz, dy).  The folded
+// input is stored row-major by channel group, in: [B][nz][ny][2][nx][8] BF16, so that each group's
+// part of an input row is one contiguous run of 16-byte sites and lands in the staged row by
+// bulk copies: the 128 sites of the tile and, periodic, the two on each side.
+// wt: [dz][dy][k / 8][co][k % 8] BF16, staged once per CTA together with the first plane.
+// Pipeline: the input rows of plane z + dz - 2 go to one of two buffers; warp 1 fills a buffer
+// (48 bulk copies on its `full` barrier) as soon as the MMAs that read it have completed (their
+// commit on its `freed` barrier), so the copies of plane dz + 1 are in flight while the MMAs of
+// plane dz run.  Thread 0 issues the 20 MMAs (M = 128, N = 32, K = 16) of each plane; a last commit
+// on `acc_done` releases the epilogue: tanh(acc + bias) -> BF16 [site][32].
+constexpr int L1_G = 2;                            // channel groups of the folded input
+constexpr int L1_CO = 32;
+constexpr int L1_ROWB = L1_G * TC_XP * 16;         // bytes of one staged row
+constexpr int L1_ABYTES = (TC_R + 4) * L1_ROWB;    // one plane's staged rows
+constexpr int L1_WBYTES = 25 * L1_G * L1_CO * 16;  // weights of the 25 (dz, dy)
+
 __global__ void __launch_bounds__(TC_THREADS, 2)
-    k_conv_tc(const bf16* __restrict__ in, const bf16* __restrict__ wt, const float* __restrict__ bias, int cout,
-              void* __restrict__ out, int nx, int ny, int nz, double* __restrict__ part, int* __restrict__ err) {
-    constexpr int G = CI / 8;                       // channel groups of 16 bytes
-    constexpr int ROWB = G * TC_XP * 16;            // bytes of one staged row
-    constexpr int ABYTES = (TC_R + 4) * ROWB;
-    constexpr int OFFB = G * CO * 16;               // bytes of the weights of one offset
-    constexpr int NDX = FOLD ? 1 : 5;               // x offsets per (dz, dy)
-    constexpr int DXS = FOLD ? 2 : 0;               // x' of the first x offset minus x - x0
+    k_conv_tc_l1(const bf16* __restrict__ in, const bf16* __restrict__ wt, const float* __restrict__ bias, int cout,
+                 bf16* __restrict__ out, int nx, int ny, int nz, int* __restrict__ err) {
+    constexpr int CO = L1_CO;
     constexpr uint32_t IDESC = idesc_bf16(128, CO);
     static_assert(TC_R * CO <= TC_TMEM_COLS, "accumulators exceed the tensor-memory allocation");
-    static_assert(CO == 16 || CO == 32, "CO");
-    static_assert(CI % 16 == 0, "CI");
     extern __shared__ __align__(1024) unsigned char smem[];
-    unsigned char* As = smem;
-    unsigned char* Ws = smem + ABYTES;
-    __shared__ __align__(8) uint64_t mbar;
+    unsigned char* Ws = smem + 2 * L1_ABYTES;
+    __shared__ __align__(8) uint64_t full[2], freed[2], acc_done;
     __shared__ uint32_t tmem_slot;
-    __shared__ float csum[TC_THREADS / 32][2];
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int nxt = nx / 128, nyb = ny / TC_R;
@@ -172,7 +188,8 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
     const int z = blk % nz, b = blk / nz;
     const int x0 = xt * 128, y0 = yb * TC_R;
     const size_t V = (size_t)nx * ny * nz;
-    const bf16* inb = in + (size_t)b * V * CI;
+    const bf16* inb = in + (size_t)b * V * 16;
+    const int xl = x0 == 0 ? nx - 2 : x0 - 2, xr = x0 + 128 == nx ? 0 : x0 + 128;
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(&tmem_slot)),
@@ -181,7 +198,11 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
     }
     if (tid == 0) {
-        mbar_init(&mbar, 1);
+        mbar_init(&full[0], 1);
+        mbar_init(&full[1], 1);
+        mbar_init(&freed[0], 1);
+        mbar_init(&freed[1], 1);
+        mbar_init(&acc_done, 1);
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
     fence_before_sync();
@@ -189,72 +210,70 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
     fence_after_sync();
     const uint32_t tmem = tmem_slot;
 
-    // this thread's staging slots within a row: chunk c = tid + k * TC_THREADS of the
-    // TC_XP * G chunks; consecutive threads read consecutive 16-byte channel groups of one site
-    constexpr int RCH = TC_XP * G;
-    constexpr int KCH = (RCH + TC_THREADS - 1) / TC_THREADS;
-    int soff[KCH], goff[KCH];
-#pragma unroll
-    for (int k = 0; k < KCH; ++k) {
-        const int c = tid + k * TC_THREADS;
-        const int g = c % G, xp = c / G;
-        int x = x0 - 2 + xp;
-        x = x < 0 ? x + nx : (x >= nx ? x - nx : x);
-        soff[k] = c < RCH ? (g * TC_XP + xp) * 16 : -1;
-        goff[k] = x * CI + g * 8;
-    }
+    // warp 1: the 8 input rows y0 - 2 .. y0 + 5 of plane z + dzi - 2 into buffer buf (and the
+    // weights with the first plane): per row and channel group the tile's 128 sites and the two
+    // periodic neighbours on each side
+    int nfill[2] = {0, 0};
+    auto fill = [&](int dzi, int buf) {
+        const int zin = wrapi_(z + dzi - 2, nz);
+        unsigned char* A = smem + buf * L1_ABYTES;
+        if (lane == 0) mbar_expect(&full[buf], L1_ABYTES + (dzi == 0 ? L1_WBYTES : 0));
+        __syncwarp();
+        if (dzi == 0 && lane == 0) bulk_g2s(Ws, wt, L1_WBYTES, &full[buf]);
+        for (int c = lane; c < (TC_R + 4) * L1_G * 3; c += 32) {
+            const int i = c / (L1_G * 3), g = (c / 3) % L1_G, p = c % 3;
+            const int yin = wrapi_(y0 - 2 + i, ny);
+            const bf16* src = inb + (((size_t)zin * ny + yin) * L1_G + g) * (size_t)nx * 8;
+            unsigned char* dst = A + (i * L1_G + g) * TC_XP * 16;
+            if (p == 0) bulk_g2s(dst + 2 * 16, src + (size_t)x0 * 8, 128 * 16, &full[buf]);
+            else if (p == 1) bulk_g2s(dst, src + (size_t)xl * 8, 2 * 16, &full[buf]);
+            else bulk_g2s(dst + 130 * 16, src + (size_t)xr * 8, 2 * 16, &full[buf]);
+        }
+        ++nfill[buf];
+    };
 
     bool ok = true;
-    int phase = 0;
-    for (int dzi = 0; dzi < 5 && ok; ++dzi) {
-        int zin = z + dzi - 2;
-        zin = zin < 0 ? zin + nz : (zin >= nz ? zin - nz : zin);
-        // the 8 input rows y0-2 .. y0+5 of plane zin
-#pragma unroll 1
-        for (int i = 0; i < TC_R + 4; ++i) {
-            const int yin = wrapi_(y0 - 2 + i, ny);
-            const bf16* src = inb + ((size_t)zin * ny + yin) * nx * CI;
-            unsigned char* dst = As + i * ROWB;
-#pragma unroll
-            for (int k = 0; k < KCH; ++k)
-                if (soff[k] >= 0) cp16(dst + soff[k], src + goff[k]);
+    if (tid == 0) {   // MMA issue
+        uint32_t fpar[2] = {0u, 0u};
+        for (int dzi = 0; dzi < 5 && ok; ++dzi) {
+            const int buf = dzi & 1;
+            ok = mbar_wait(&full[buf], fpar[buf]);
+            fpar[buf] ^= 1u;
+            if (!ok) break;
+            fence_after_sync();
+            const uint32_t a0 = smem_u32(smem + buf * L1_ABYTES);
+            const uint32_t w0 = smem_u32(Ws) + (uint32_t)(dzi * 5 * L1_G * CO * 16);
+            for (int r = 0; r < TC_R; ++r)
+                for (int dyi = 0; dyi < 5; ++dyi) {
+                    const uint32_t aaddr = a0 + (uint32_t)(((r + dyi) * L1_G) * TC_XP + 2) * 16u;
+                    const uint32_t baddr = w0 + (uint32_t)(dyi * L1_G * CO) * 16u;
+                    mma_bf16(tmem + (uint32_t)(r * CO), smem_desc(aaddr, TC_XP * 16, 128),
+                             smem_desc(baddr, CO * 16, 128), IDESC, (dzi | dyi) != 0);
+                }
+            mma_commit(&freed[buf]);               // buffer buf may be refilled
+            if (dzi == 4) mma_commit(&acc_done);   // every MMA of the CTA has completed
         }
-        // two halves of the 25 (dy, dx) offsets: dy 0..2, then dy 3..4
-#pragma unroll 1
-        for (int h = 0; h < 2 && ok; ++h) {
-            const int dy0 = h ? 3 : 0, dy1 = h ? 5 : 3;
-            const bf16* wsrc = wt + ((size_t)dzi * 5 + dy0) * NDX * G * CO * 8;
-            const int nbytes = (dy1 - dy0) * NDX * OFFB;
-            for (int c = tid; c < nbytes / 16; c += TC_THREADS) cp16(Ws + (size_t)c * 16, wsrc + (size_t)c * 8);
-            cp_commit();
-            cp_wait_all();
-            fence_proxy_async();   // the tensor cores read shared memory through the async proxy
-            __syncthreads();
-            if (tid == 0) {
-                fence_after_sync();
-                const uint32_t a0 = smem_u32(As), w0 = smem_u32(Ws);
-                for (int r = 0; r < TC_R; ++r)
-                    for (int dyi = dy0; dyi < dy1; ++dyi)
-                        for (int dxi = 0; dxi < NDX; ++dxi)
-#pragma unroll
-                            for (int kk = 0; kk < CI / 16; ++kk) {
-                                const uint32_t aaddr =
-                                    a0 + (uint32_t)(((r + dyi) * G + 2 * kk) * TC_XP + dxi + DXS) * 16u;
-                                const uint32_t baddr =
-                                    w0 + (uint32_t)((((dyi - dy0) * NDX + dxi) * G + 2 * kk) * CO) * 16u;
-                                mma_bf16(tmem + (uint32_t)(r * CO), smem_desc(aaddr, TC_XP * 16, 128),
-                                         smem_desc(baddr, CO * 16, 128), IDESC, (dzi | dyi | dxi | kk) != 0);
-                            }
-                mma_commit(&mbar);   // arrives once every MMA above has completed
-            }
-            const bool done = mbar_wait(&mbar, (uint32_t)(phase & 1));
-            ++phase;
-            if (!done) atomicOr(err, 1);
-            ok = __syncthreads_and(done ? 1 : 0) != 0;
+        if (!ok) atomicOr(err, 1);
+    } else if (warp == 1) {   // bulk copies
+        fill(0, 0);
+        fill(1, 1);
+        uint32_t mpar[2] = {0u, 0u};
+        for (int dzi = 0; dzi + 2 < 5 && ok; ++dzi) {
+            const int buf = dzi & 1;
+            ok = __all_sync(0xffffffffu, mbar_wait(&freed[buf], mpar[buf]));
+            mpar[buf] ^= 1u;
+            if (ok) fill(dzi + 2, buf);
         }
+        if (!ok && lane == 0) atomicOr(err, 1);
     }
+    __syncwarp();
+    const bool fin = ok && mbar_wait(&acc_done, 0u);
+    if (ok && !fin && lane == 0) atomicOr(err, 1);
+    ok = __syncthreads_and(fin ? 1 : 0) != 0;
+    if (!ok && warp == 1)   // let this CTA's copies in flight land before it exits
+        for (int k = 0; k < 2; ++k)
+            if (nfill[k]) mbar_wait(&full[k], (uint32_t)((nfill[k] - 1) & 1));
     fence_after_sync();
-    float s0 = 0.f, s1 = 0.f;
     if (ok) {
         // warps w and w + 4 share TMEM lane quarter w % 4 and take half of the rows each
         const int q = warp & 3;
@@ -263,43 +282,14 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
 #pragma unroll 1
         for (int r = (warp >> 2) * (TC_R / 2); r < ((warp >> 2) + 1) * (TC_R / 2); ++r) {
             float v[CO];
-            if (CO == 32) tmem_ld32(tq + (uint32_t)(r * CO), v);
-            else tmem_ld16(tq + (uint32_t)(r * CO), v);
+            tmem_ld32(tq + (uint32_t)(r * CO), v);
             const size_t site = (size_t)b * V + ((size_t)z * ny + (y0 + r)) * nx + x;
+            __align__(16) bf16 hv[CO];
 #pragma unroll
-            for (int co = 0; co < CO; ++co) v[co] += (co < cout) ? bias[co] : 0.f;
-            if (EPI == 0) {
-                __align__(16) bf16 hv[CO];
+            for (int co = 0; co < CO; ++co) hv[co] = __float2bfloat16(tanhf(v[co] + ((co < cout) ? bias[co] : 0.f)));
+            uint4* dst = (uint4*)(out + site * CO);
 #pragma unroll
-                for (int co = 0; co < CO; ++co) hv[co] = __float2bfloat16(tanhf(v[co]));
-                uint4* dst = (uint4*)((bf16*)out + site * CO);
-#pragma unroll
-                for (int k = 0; k < CO / 8; ++k) dst[k] = ((const uint4*)hv)[k];
-            } else {
-                float4* dst = (float4*)((float*)out + site * 16);
-#pragma unroll
-                for (int k = 0; k < 4; ++k) dst[k] = make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
-                s0 += v[0];
-                s1 += v[1];
-            }
-        }
-    }
-    if (EPI == 1) {   // fixed-order CTA sums of the two output channels
-#pragma unroll
-        for (int m = 16; m > 0; m >>= 1) {
-            s0 += __shfl_xor_sync(0xffffffffu, s0, m);
-            s1 += __shfl_xor_sync(0xffffffffu, s1, m);
-        }
-        if (lane == 0) {
-            csum[warp][0] = s0;
-            csum[warp][1] = s1;
-        }
-        __syncthreads();
-        if (tid < 2) {
-            double t = 0.0;
-            for (int w = 0; w < TC_THREADS / 32; ++w) t += (double)csum[w][tid];
-            const int nblk = nz * nyb * nxt;
-            part[((size_t)b * 2 + tid) * nblk + (blockIdx.x - (size_t)b * nblk)] = t;
+            for (int k = 0; k < CO / 8; ++k) dst[k] = ((const uint4*)hv)[k];
         }
     }
     fence_before_sync();
@@ -489,14 +479,10 @@ __global__ void __launch_bounds__(TC_THREADS, MINB)
 
 }  // namespace
 
-// Bytes of dynamic shared memory of the kernel for CI input and CO output channels: the staged
-// input rows and the staged weights of half a dz (every operand address the MMAs form lies inside
-// them: the A walk ends at the last staged row, the B walk at the last offset's weights).
-size_t tc_conv_smem(int ci, int co) {
-    const size_t a = (size_t)(TC_R + 4) * (ci / 8) * TC_XP * 16;
-    const size_t w = (size_t)15 * (ci / 8) * co * 16;   // the larger half (dy 0..2) of one dz
-    return a + w;
-}
+// Bytes of dynamic shared memory of the first layer: two buffers of staged input rows and the
+// weights of all 25 (dz, dy) offsets (every operand address its MMAs form lies inside them: the
+// A walk ends at the last staged row of a buffer, the B walk at the last offset's weights).
+size_t tc_conv_smem() { return (size_t)2 * L1_ABYTES + L1_WBYTES; }
 // the stacked variant: R + 4 staged rows and the weights of one whole dz
 constexpr size_t stk_smem(int ci, int co, int r) {
     return (size_t)(r + 4) * (ci / 8) * TC_XP * 16 + (size_t)25 * (ci / 8) * co * 16;
@@ -507,11 +493,11 @@ bool tc_conv_supported(int nx, int ny) { return nx % 128 == 0 && ny % kR2 == 0; 
 
 int tc_conv_prepare() {
     // the whole unified L1/shared array as shared memory, so that several CTAs fit per SM
-    cudaFuncSetAttribute(k_conv_tc<16, 32, 0, true>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    cudaFuncSetAttribute(k_conv_tc_l1, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     cudaFuncSetAttribute(k_conv_tc_stk<32, 32, 0, kR2, 512, 1>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     cudaFuncSetAttribute(k_conv_tc_stk<32, 16, 1, kR3, 256, 2>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-    cudaError_t e = cudaFuncSetAttribute(k_conv_tc<16, 32, 0, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)tc_conv_smem(16, 32));
+    cudaError_t e =
+        cudaFuncSetAttribute(k_conv_tc_l1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_conv_smem());
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_conv_tc_stk<32, 32, 0, kR2, 512, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)stk_smem(32, 32, kR2));
@@ -525,7 +511,7 @@ int tc_conv_prepare() {
 int tc_conv_blocks(int nx, int ny, int nz) { return nz * (ny / kR3) * (nx / 128); }
 
 // Layer l of the predictor network (0: 2 -> 32 tanh with the x offsets folded into 16 input
-// channels, weights [dz][dy][k / 8][co][k % 8]; 1: 32 -> 32 tanh and 2: 32 -> 16 linear FP32, both
+// channels, input [B][nz][ny][2][nx][8], weights [dz][dy][k / 8][co][k % 8]; 1: 32 -> 32 tanh and 2: 32 -> 16 linear FP32, both
 // stacked, weights [dz][dx][ci / 8][4 - dy][co][ci % 8]) over B samples of an nx x ny x nz grid
 // (tc_conv_supported must hold).
 void launch_conv_tc(int layer, const void* in, const void* wt, const float* bias, int cout, void* out, int nx, int ny,
@@ -533,8 +519,8 @@ void launch_conv_tc(int layer, const void* in, const void* wt, const float* bias
     const bf16* x = (const bf16*)in;
     const bf16* w = (const bf16*)wt;
     if (layer == 0)
-        k_conv_tc<16, 32, 0, true><<<B * nz * (ny / TC_R) * (nx / 128), TC_THREADS, tc_conv_smem(16, 32), s>>>(
-            x, w, bias, cout, out, nx, ny, nz, part, err);
+        k_conv_tc_l1<<<B * nz * (ny / TC_R) * (nx / 128), TC_THREADS, tc_conv_smem(), s>>>(x, w, bias, cout, (bf16*)out,
+                                                                                            nx, ny, nz, err);
     else if (layer == 1)
         k_conv_tc_stk<32, 32, 0, kR2, 512, 1><<<B * nz * (ny / kR2) * (nx / 128), TC_THREADS, stk_smem(32, 32, kR2), s>>>(
             x, w, bias, cout, out, nx, ny, nz, part, err);

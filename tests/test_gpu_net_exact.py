@@ -65,8 +65,8 @@ def paired_integers(n, lo, hi, seed):
     return v[np.argsort(inputs.uniform01(seed + 1, n))]
 
 
-def exact_problem():
-    nx, ny, nz = GRID
+def exact_problem(grid=GRID):
+    nx, ny, nz = grid
     V = nx * ny * nz
     U = np.stack([np.stack([paired_integers(V, -3, 3, 500 + 10 * b + c).reshape(nz, ny, nx) for c in range(2)])
                   for b in range(B)])
@@ -81,25 +81,28 @@ def flat(params):
     return np.concatenate([np.concatenate([W.ravel(), b]) for W, b in params])
 
 
-def emulate_forward(params, U, phibar):
+def emulate_forward(params, U, phibar, grid=GRID):
     (W1, b1), (W2, b2), (W3, b3) = params
     x = oracle.net_input(U)
-    h1 = bf16(np.tanh(oracle.conv3d(GRID, B, W1, b1, x)))
-    h2 = bf16(np.tanh(oracle.conv3d(GRID, B, W2, b2, h1)))
-    y = oracle.conv3d(GRID, B, W3, b3, h2)
+    h1 = bf16(np.tanh(oracle.conv3d(grid, B, W1, b1, x)))
+    h2 = bf16(np.tanh(oracle.conv3d(grid, B, W2, b2, h1)))
+    y = oracle.conv3d(grid, B, W3, b3, h2)
     phi = y - y.mean(axis=(2, 3, 4), keepdims=True) + np.asarray(phibar)[None, :, None, None, None]
     return phi, (x, h1, h2, y)
 
 
+@pytest.mark.parametrize("grid", [GRID, (256, 8, 4)], ids=["128x8x4", "256x8x4"])
 @pytest.mark.parametrize("path", [0, 1], ids=["tcgen05", "mma.sync"])
-def test_forward_is_exact(path):
-    U, params = exact_problem()
+def test_forward_is_exact(path, grid):
+    """Also at two 128-site x tiles per row (the first layer's periodic x neighbours come from the
+    other tile)."""
+    U, params = exact_problem(grid)
     phibar = [0.5, 0.5]
-    ref, (x, h1, h2, y) = emulate_forward(params, U, phibar)
+    ref, (x, h1, h2, y) = emulate_forward(params, U, phibar, grid)
     # the design: pre-activations are multiples of 16, activations exactly 0 or +-1
     assert set(np.unique(h1)) <= {-1.0, 0.0, 1.0} and set(np.unique(h2)) <= {-1.0, 0.0, 1.0}
     assert 0.05 < (h1 == 0).mean() < 0.95 and 0.05 < (h2 == 0).mean() < 0.95
-    net = dscf.Net(GRID, B, seed=1)
+    net = dscf.Net(grid, B, seed=1)
     net.set_params(torch.from_numpy(flat(params)).float())
     net.set_tensor_path(path)
     got = net.forward(torch.from_numpy(U).float(), phibar).cpu().numpy().astype(np.float64)
