@@ -255,8 +255,9 @@ __global__ void k_net_in(const float* __restrict__ U, const double* __restrict__
 
 // Network input with the five x offsets folded into the channels (tcgen05 first layer):
 // xf[r][2 dx + c] = U_c[r + dx - 2 along x] - <U_c> for dx = 0..4, zero in channels 10..15, stored
-// by channel group within each x row, [B][nz][ny][2][nx][8], so that a group's part of a row is
-// contiguous.
+// by channel group within each x row and with two periodic copies on each side of the row,
+// [B][nz][ny][2][nx + 4][8] (site x at x + 2), so that a group's part of a tile's staged row,
+// x0 - 2 .. x0 + 129, is one contiguous run.
 __global__ void k_net_in_fold(const float* __restrict__ U, const double* __restrict__ means, int nx, int V, int B,
                               bf16* __restrict__ xf) {
     const size_t r = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
@@ -277,9 +278,17 @@ __global__ void k_net_in_fold(const float* __restrict__ U, const double* __restr
     }
 #pragma unroll
     for (int c = 10; c < 16; ++c) v[c] = __float2bfloat16(0.f);
-    bf16* dst = xf + ((size_t)b * V + row) * 16 + (size_t)x * 8;   // group 0; group 1 follows nx sites later
-    *(uint4*)dst = *(const uint4*)&v[0];
-    *(uint4*)(dst + (size_t)nx * 8) = *(const uint4*)&v[8];
+    const size_t rowi = (size_t)b * (V / nx) + row / nx;
+    bf16* g0 = xf + rowi * 2 * (size_t)(nx + 4) * 8;   // group 0 of this row; group 1 follows
+    bf16* g1 = g0 + (size_t)(nx + 4) * 8;
+    const int xp = x + 2;
+    *(uint4*)(g0 + (size_t)xp * 8) = *(const uint4*)&v[0];
+    *(uint4*)(g1 + (size_t)xp * 8) = *(const uint4*)&v[8];
+    const int xh = x < 2 ? x + nx + 2 : (x >= nx - 2 ? x - nx + 2 : -1);   // periodic copy
+    if (xh >= 0) {
+        *(uint4*)(g0 + (size_t)xh * 8) = *(const uint4*)&v[0];
+        *(uint4*)(g1 + (size_t)xh * 8) = *(const uint4*)&v[8];
+    }
 }
 
 // Network output: phi_c[r] = phibar_c + y[r][c] - <y_c>  ([B][2][V] float).
@@ -434,7 +443,7 @@ NetLayout net_layout(int nx, int ny, int nz, int B) {
         L.wt[l] = take((size_t)KVOL * COUTP[l] * CINP[l] * 2);
     }
     L.x16 = take(S * 16 * 2);
-    L.x16f = tc_conv_supported(nx, ny) ? take(S * 16 * 2) : 0;
+    L.x16f = tc_conv_supported(nx, ny) ? take(S / nx * (nx + 4) * 16 * 2) : 0;
     L.h1 = take(S * 32 * 2);
     L.h2 = take(S * 32 * 2);
     L.y16 = take(S * 16 * 4);

@@ -16,9 +16,10 @@
 // overwritten and when the accumulators are complete.  The epilogue (bias, tanh, BF16 or FP32
 // channel-last stores) reads each warp's quarter of the TMEM lanes with tcgen05.ld.
 //
-// The first layer (2 input channels, R = 4) folds the five x offsets into 16 channels and fills
-// its staged rows with bulk (TMA) copies, two planes in flight; the 32-channel layers stack the
-// five dy offsets along N (R = 8 and 4) and stage with per-thread 16-byte copies.
+// The first layer (2 input channels, R = 4) folds the five x offsets into 16 channels and is a
+// persistent, warp-specialised kernel: bulk (TMA) copies, MMAs and epilogue of successive tiles
+// overlap.  The 32-channel layers stack the five dy offsets along N (R = 8 and 4) and stage with
+// per-thread 16-byte copies.
 //
 // Every wait is bounded; a CTA that gives up sets the error word, frees its tensor memory and
 // returns.
@@ -38,7 +39,6 @@ typedef __nv_bfloat16 bf16;
 constexpr int TC_R = 4;            // output rows per CTA
 constexpr int TC_XP = 132;         // staged row length (128 + 2 on each side)
 constexpr int TC_THREADS = 256;  // 8 warps: staging; epilogue pairs of warps per TMEM lane quarter
-constexpr int TC_TMEM_COLS = 128;  // >= TC_R * CO for CO <= 32
 constexpr long long kTcSpinLimit = 1ll << 20;   // try_wait polls (each may suspend ~1 us)
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -103,6 +103,10 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity) {
     return false;
 }
 
+__device__ __forceinline__ void mbar_arrive(uint64_t* mbar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(mbar)) : "memory");
+}
+
 // 32 consecutive FP32 columns of this warp's 32 TMEM lanes (one lane per thread).
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
     uint32_t r[32];
@@ -152,57 +156,71 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
 // First layer (2 -> 32 channels, tanh) on the folded input: channels 2 dx + ci (dx = 0..4,
 // ci = 0..1) hold the two real input channels at x + dx - 2 (zero in channels 10..15), so one
 // K = 16 step covers all five x offsets and the offsets left are the 25 (dz, dy).  The folded
-// input is stored row-major by channel group, in: [B][nz][ny][2][nx][8] BF16, so that each group's
-// part of an input row is one contiguous run of 16-byte sites and lands in the staged row by
-// bulk copies: the 128 sites of the tile and, periodic, the two on each side.
-// wt: [dz][dy][k / 8][co][k % 8] BF16, staged once per CTA together with the first plane.
-// Pipeline: the input rows of plane z + dz - 2 go to one of two buffers; warp 1 fills a buffer
-// (48 bulk copies on its `full` barrier) as soon as the MMAs that read it have completed (their
-// commit on its `freed` barrier), so the copies of plane dz + 1 are in flight while the MMAs of
-// plane dz run.  Thread 0 issues the 20 MMAs (M = 128, N = 32, K = 16) of each plane; a last commit
-// on `acc_done` releases the epilogue: tanh(acc + bias) -> BF16 [site][32].
+// input is stored by channel group within each x row, with two periodic copies on each side,
+// in: [B][nz][ny][2][nx + 4][8] BF16 (site x at x + 2), so that each group's part of a staged row
+// (the tile's 128 sites and two on each side) is one contiguous 2112-byte run: one bulk copy.
+// wt: [dz][dy][k / 8][co][k % 8] BF16, staged once per CTA.
+// Persistent: each CTA takes tiles (4 output rows of 128 sites) blockIdx.x, + gridDim.x, ... and
+// streams their planes (5 per tile) through two staging buffers, with warp-specialised roles
+// synchronised by mbarriers only:
+//   warp 1 (copies)   fills a buffer (16 bulk copies, `full`) as soon as the MMAs that read it
+//                     have completed (`freed`), so the next plane is in flight while one is used;
+//   thread 0 (MMAs)   issues the 20 MMAs (M = 128, N = 32, K = 16) of each plane into one of two
+//                     accumulator sets in TMEM (alternating by tile) and commits `tfull` after a
+//                     tile's last plane, once the epilogue has released that set (`tfree`);
+//   warps 2..5        (one TMEM lane quarter each) read a finished set, apply tanh(acc + bias),
+//                     store BF16 [site][32] and release the set,
+// so the copies, the MMAs and the epilogue of successive tiles overlap.
 constexpr int L1_G = 2;                            // channel groups of the folded input
 constexpr int L1_CO = 32;
 constexpr int L1_ROWB = L1_G * TC_XP * 16;         // bytes of one staged row
 constexpr int L1_ABYTES = (TC_R + 4) * L1_ROWB;    // one plane's staged rows
 constexpr int L1_WBYTES = 25 * L1_G * L1_CO * 16;  // weights of the 25 (dz, dy)
+constexpr int L1_THREADS = 192;                    // warps: MMA issue, copies, 4 epilogue
+constexpr int L1_TMEM_COLS = 256;                  // two accumulator sets of TC_R x 32 columns
+constexpr int L1_CTAS_PER_SM = 2;
 
-__global__ void __launch_bounds__(TC_THREADS, 2)
+__global__ void __launch_bounds__(L1_THREADS, L1_CTAS_PER_SM)
     k_conv_tc_l1(const bf16* __restrict__ in, const bf16* __restrict__ wt, const float* __restrict__ bias, int cout,
-                 bf16* __restrict__ out, int nx, int ny, int nz, int* __restrict__ err) {
+                 bf16* __restrict__ out, int nx, int ny, int nz, int B, int* __restrict__ err) {
     constexpr int CO = L1_CO;
     constexpr uint32_t IDESC = idesc_bf16(128, CO);
-    static_assert(TC_R * CO <= TC_TMEM_COLS, "accumulators exceed the tensor-memory allocation");
+    static_assert(2 * TC_R * CO <= L1_TMEM_COLS, "accumulators exceed the tensor-memory allocation");
     extern __shared__ __align__(1024) unsigned char smem[];
     unsigned char* Ws = smem + 2 * L1_ABYTES;
-    __shared__ __align__(8) uint64_t full[2], freed[2], acc_done;
+    __shared__ __align__(8) uint64_t full[2], freed[2], tfull[2], tfree[2], wbar;
     __shared__ uint32_t tmem_slot;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int nxt = nx / 128, nyb = ny / TC_R;
-    int blk = blockIdx.x;
-    const int xt = blk % nxt;
-    blk /= nxt;
-    const int yb = blk % nyb;
-    blk /= nyb;
-    const int z = blk % nz, b = blk / nz;
-    const int x0 = xt * 128, y0 = yb * TC_R;
+    const int ntile = B * nz * nyb * nxt;
+    const int nk = ntile > (int)blockIdx.x ? (ntile - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x : 0;
     const size_t V = (size_t)nx * ny * nz;
-    const bf16* inb = in + (size_t)b * V * 16;
-    const int xl = x0 == 0 ? nx - 2 : x0 - 2, xr = x0 + 128 == nx ? 0 : x0 + 128;
+    // tile t -> sample b, plane z, first row y0, first site x0
+    auto tile_of = [&](int k, int& b, int& z, int& y0, int& x0) {
+        int t = (int)blockIdx.x + k * (int)gridDim.x;
+        x0 = (t % nxt) * 128;
+        t /= nxt;
+        y0 = (t % nyb) * TC_R;
+        t /= nyb;
+        z = t % nz;
+        b = t / nz;
+    };
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(&tmem_slot)),
-                     "r"(TC_TMEM_COLS)
+                     "r"(L1_TMEM_COLS)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
     }
     if (tid == 0) {
-        mbar_init(&full[0], 1);
-        mbar_init(&full[1], 1);
-        mbar_init(&freed[0], 1);
-        mbar_init(&freed[1], 1);
-        mbar_init(&acc_done, 1);
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&full[i], 1);
+            mbar_init(&freed[i], 1);
+            mbar_init(&tfull[i], 1);
+            mbar_init(&tfree[i], 4);   // one arrival per epilogue warp
+        }
+        mbar_init(&wbar, 1);
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
     fence_before_sync();
@@ -210,93 +228,103 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
     fence_after_sync();
     const uint32_t tmem = tmem_slot;
 
-    // warp 1: the 8 input rows y0 - 2 .. y0 + 5 of plane z + dzi - 2 into buffer buf (and the
-    // weights with the first plane): per row and channel group the tile's 128 sites and the two
-    // periodic neighbours on each side
-    int nfill[2] = {0, 0};
-    auto fill = [&](int dzi, int buf) {
-        const int zin = wrapi_(z + dzi - 2, nz);
-        unsigned char* A = smem + buf * L1_ABYTES;
-        if (lane == 0) mbar_expect(&full[buf], L1_ABYTES + (dzi == 0 ? L1_WBYTES : 0));
-        __syncwarp();
-        if (dzi == 0 && lane == 0) bulk_g2s(Ws, wt, L1_WBYTES, &full[buf]);
-        for (int c = lane; c < (TC_R + 4) * L1_G * 3; c += 32) {
-            const int i = c / (L1_G * 3), g = (c / 3) % L1_G, p = c % 3;
-            const int yin = wrapi_(y0 - 2 + i, ny);
-            const bf16* src = inb + (((size_t)zin * ny + yin) * L1_G + g) * (size_t)nx * 8;
-            unsigned char* dst = A + (i * L1_G + g) * TC_XP * 16;
-            if (p == 0) bulk_g2s(dst + 2 * 16, src + (size_t)x0 * 8, 128 * 16, &full[buf]);
-            else if (p == 1) bulk_g2s(dst, src + (size_t)xl * 8, 2 * 16, &full[buf]);
-            else bulk_g2s(dst + 130 * 16, src + (size_t)xr * 8, 2 * 16, &full[buf]);
-        }
-        ++nfill[buf];
-    };
-
     bool ok = true;
-    if (tid == 0) {   // MMA issue
-        uint32_t fpar[2] = {0u, 0u};
-        for (int dzi = 0; dzi < 5 && ok; ++dzi) {
-            const int buf = dzi & 1;
-            ok = mbar_wait(&full[buf], fpar[buf]);
-            fpar[buf] ^= 1u;
-            if (!ok) break;
+    int nfill0 = 0, nfill1 = 0;   // fills issued per buffer
+    if (warp == 1) {   // bulk copies: the weights, then the 5 planes of each tile in order
+        if (lane == 0) {
+            mbar_expect(&wbar, L1_WBYTES);
+            bulk_g2s(Ws, wt, L1_WBYTES, &wbar);
+        }
+        for (int p = 0; p < 5 * nk && ok; ++p) {
+            const int buf = p & 1;
+            if (p >= 2) {
+                ok = __all_sync(0xffffffffu, mbar_wait(&freed[buf], (uint32_t)(((p >> 1) - 1) & 1)));
+                if (!ok) break;
+            }
+            int b, z, y0, x0;
+            tile_of(p / 5, b, z, y0, x0);
+            const int zin = wrapi_(z + p % 5 - 2, nz);
+            const bf16* inb = in + (size_t)b * (V / nx) * 2 * (nx + 4) * 8;
+            unsigned char* A = smem + buf * L1_ABYTES;
+            if (lane == 0) mbar_expect(&full[buf], L1_ABYTES);
+            __syncwarp();
+            if (lane < (TC_R + 4) * L1_G) {   // one staged row of one channel group per lane
+                const int i = lane / L1_G, g = lane % L1_G;
+                const int yin = wrapi_(y0 - 2 + i, ny);
+                const bf16* src = inb + ((((size_t)zin * ny + yin) * L1_G + g) * (nx + 4) + x0) * 8;
+                bulk_g2s(A + (i * L1_G + g) * TC_XP * 16, src, TC_XP * 16, &full[buf]);
+            }
+            if (buf) ++nfill1;
+            else ++nfill0;
+        }
+        if (!ok && lane == 0) atomicOr(err, 1);
+    } else if (tid == 0) {   // MMA issue
+        ok = mbar_wait(&wbar, 0u);
+        for (int k = 0; k < nk && ok; ++k) {
+            const int acc = k & 1;
+            if (k >= 2 && !(ok = mbar_wait(&tfree[acc], (uint32_t)(((k >> 1) - 1) & 1)))) break;
             fence_after_sync();
-            const uint32_t a0 = smem_u32(smem + buf * L1_ABYTES);
-            const uint32_t w0 = smem_u32(Ws) + (uint32_t)(dzi * 5 * L1_G * CO * 16);
-            for (int r = 0; r < TC_R; ++r)
-                for (int dyi = 0; dyi < 5; ++dyi) {
-                    const uint32_t aaddr = a0 + (uint32_t)(((r + dyi) * L1_G) * TC_XP + 2) * 16u;
-                    const uint32_t baddr = w0 + (uint32_t)(dyi * L1_G * CO) * 16u;
-                    mma_bf16(tmem + (uint32_t)(r * CO), smem_desc(aaddr, TC_XP * 16, 128),
-                             smem_desc(baddr, CO * 16, 128), IDESC, (dzi | dyi) != 0);
-                }
-            mma_commit(&freed[buf]);               // buffer buf may be refilled
-            if (dzi == 4) mma_commit(&acc_done);   // every MMA of the CTA has completed
+            const uint32_t t0 = tmem + (uint32_t)(acc * TC_R * CO);
+            for (int dzi = 0; dzi < 5; ++dzi) {
+                const int p = 5 * k + dzi, buf = p & 1;
+                if (!(ok = mbar_wait(&full[buf], (uint32_t)((p >> 1) & 1)))) break;
+                fence_after_sync();
+                const uint32_t a0 = smem_u32(smem + buf * L1_ABYTES);
+                const uint32_t w0 = smem_u32(Ws) + (uint32_t)(dzi * 5 * L1_G * CO * 16);
+                for (int r = 0; r < TC_R; ++r)
+                    for (int dyi = 0; dyi < 5; ++dyi) {
+                        const uint32_t aaddr = a0 + (uint32_t)(((r + dyi) * L1_G) * TC_XP + 2) * 16u;
+                        const uint32_t baddr = w0 + (uint32_t)(dyi * L1_G * CO) * 16u;
+                        mma_bf16(t0 + (uint32_t)(r * CO), smem_desc(aaddr, TC_XP * 16, 128),
+                                 smem_desc(baddr, CO * 16, 128), IDESC, (dzi | dyi) != 0);
+                    }
+                mma_commit(&freed[buf]);   // the buffer may be refilled
+            }
+            if (ok) mma_commit(&tfull[acc]);   // the tile's accumulators are complete
         }
         if (!ok) atomicOr(err, 1);
-    } else if (warp == 1) {   // bulk copies
-        fill(0, 0);
-        fill(1, 1);
-        uint32_t mpar[2] = {0u, 0u};
-        for (int dzi = 0; dzi + 2 < 5 && ok; ++dzi) {
-            const int buf = dzi & 1;
-            ok = __all_sync(0xffffffffu, mbar_wait(&freed[buf], mpar[buf]));
-            mpar[buf] ^= 1u;
-            if (ok) fill(dzi + 2, buf);
+    } else if (warp >= 2) {   // epilogue: warp w reads TMEM lane quarter w % 4
+        const int q = warp & 3;
+        float bs[CO];
+#pragma unroll
+        for (int co = 0; co < CO; ++co) bs[co] = co < cout ? bias[co] : 0.f;
+        for (int k = 0; k < nk && ok; ++k) {
+            const int acc = k & 1;
+            ok = __all_sync(0xffffffffu, mbar_wait(&tfull[acc], (uint32_t)((k >> 1) & 1)));
+            if (!ok) break;
+            fence_after_sync();
+            int b, z, y0, x0;
+            tile_of(k, b, z, y0, x0);
+            const uint32_t tq = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * TC_R * CO);
+#pragma unroll 1
+            for (int r = 0; r < TC_R; ++r) {
+                float v[CO];
+                tmem_ld32(tq + (uint32_t)(r * CO), v);
+                const size_t site = (size_t)b * V + ((size_t)z * ny + (y0 + r)) * nx + x0 + q * 32 + lane;
+                __align__(16) bf16 hv[CO];
+#pragma unroll
+                for (int co = 0; co < CO; ++co) hv[co] = __float2bfloat16(tanhf(v[co] + bs[co]));
+                uint4* dst = (uint4*)(out + site * CO);
+#pragma unroll
+                for (int j = 0; j < CO / 8; ++j) dst[j] = ((const uint4*)hv)[j];
+            }
+            fence_before_sync();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&tfree[acc]);
         }
         if (!ok && lane == 0) atomicOr(err, 1);
     }
-    __syncwarp();
-    const bool fin = ok && mbar_wait(&acc_done, 0u);
-    if (ok && !fin && lane == 0) atomicOr(err, 1);
-    ok = __syncthreads_and(fin ? 1 : 0) != 0;
-    if (!ok && warp == 1)   // let this CTA's copies in flight land before it exits
-        for (int k = 0; k < 2; ++k)
-            if (nfill[k]) mbar_wait(&full[k], (uint32_t)((nfill[k] - 1) & 1));
-    fence_after_sync();
-    if (ok) {
-        // warps w and w + 4 share TMEM lane quarter w % 4 and take half of the rows each
-        const int q = warp & 3;
-        const int x = x0 + q * 32 + lane;
-        const uint32_t tq = tmem + ((uint32_t)(q * 32) << 16);
-#pragma unroll 1
-        for (int r = (warp >> 2) * (TC_R / 2); r < ((warp >> 2) + 1) * (TC_R / 2); ++r) {
-            float v[CO];
-            tmem_ld32(tq + (uint32_t)(r * CO), v);
-            const size_t site = (size_t)b * V + ((size_t)z * ny + (y0 + r)) * nx + x;
-            __align__(16) bf16 hv[CO];
-#pragma unroll
-            for (int co = 0; co < CO; ++co) hv[co] = __float2bfloat16(tanhf(v[co] + ((co < cout) ? bias[co] : 0.f)));
-            uint4* dst = (uint4*)(out + site * CO);
-#pragma unroll
-            for (int k = 0; k < CO / 8; ++k) dst[k] = ((const uint4*)hv)[k];
-        }
+    __syncwarp();   // warp 0 reconverges after its MMA-issuing thread
+    ok = __syncthreads_and(ok ? 1 : 0) != 0;
+    if (!ok && warp == 1) {   // let this CTA's copies in flight land before it exits
+        if (nfill0) mbar_wait(&full[0], (uint32_t)((nfill0 - 1) & 1));
+        if (nfill1) mbar_wait(&full[1], (uint32_t)((nfill1 - 1) & 1));
     }
     fence_before_sync();
     __syncthreads();
     if (warp == 0) {
         fence_after_sync();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(TC_TMEM_COLS)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(L1_TMEM_COLS)
                      : "memory");
     }
 }
@@ -483,6 +511,14 @@ __global__ void __launch_bounds__(TC_THREADS, MINB)
 // weights of all 25 (dz, dy) offsets (every operand address its MMAs form lies inside them: the
 // A walk ends at the last staged row of a buffer, the B walk at the last offset's weights).
 size_t tc_conv_smem() { return (size_t)2 * L1_ABYTES + L1_WBYTES; }
+// CTAs of the persistent first layer: L1_CTAS_PER_SM per SM, at most one per tile
+int l1_grid(int ntile) {
+    int dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const int g = (nsm > 0 ? nsm : 1) * L1_CTAS_PER_SM;
+    return ntile < g ? ntile : g;
+}
 // the stacked variant: R + 4 staged rows and the weights of one whole dz
 constexpr size_t stk_smem(int ci, int co, int r) {
     return (size_t)(r + 4) * (ci / 8) * TC_XP * 16 + (size_t)25 * (ci / 8) * co * 16;
@@ -511,7 +547,7 @@ int tc_conv_prepare() {
 int tc_conv_blocks(int nx, int ny, int nz) { return nz * (ny / kR3) * (nx / 128); }
 
 // Layer l of the predictor network (0: 2 -> 32 tanh with the x offsets folded into 16 input
-// channels, input [B][nz][ny][2][nx][8], weights [dz][dy][k / 8][co][k % 8]; 1: 32 -> 32 tanh and 2: 32 -> 16 linear FP32, both
+// channels, input [B][nz][ny][2][nx + 4][8], weights [dz][dy][k / 8][co][k % 8]; 1: 32 -> 32 tanh and 2: 32 -> 16 linear FP32, both
 // stacked, weights [dz][dx][ci / 8][4 - dy][co][ci % 8]) over B samples of an nx x ny x nz grid
 // (tc_conv_supported must hold).
 void launch_conv_tc(int layer, const void* in, const void* wt, const float* bias, int cout, void* out, int nx, int ny,
@@ -519,8 +555,8 @@ void launch_conv_tc(int layer, const void* in, const void* wt, const float* bias
     const bf16* x = (const bf16*)in;
     const bf16* w = (const bf16*)wt;
     if (layer == 0)
-        k_conv_tc_l1<<<B * nz * (ny / TC_R) * (nx / 128), TC_THREADS, tc_conv_smem(), s>>>(x, w, bias, cout, (bf16*)out,
-                                                                                            nx, ny, nz, err);
+        k_conv_tc_l1<<<l1_grid(B * nz * (ny / TC_R) * (nx / 128)), L1_THREADS, tc_conv_smem(), s>>>(
+            x, w, bias, cout, (bf16*)out, nx, ny, nz, B, err);
     else if (layer == 1)
         k_conv_tc_stk<32, 32, 0, kR2, 512, 1><<<B * nz * (ny / kR2) * (nx / 128), TC_THREADS, stk_smem(32, 32, kR2), s>>>(
             x, w, bias, cout, out, nx, ny, nz, part, err);

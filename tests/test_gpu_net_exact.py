@@ -111,6 +111,25 @@ def test_forward_is_exact(path, grid):
     assert np.array_equal(got, ref), np.abs(got - ref).max()
 
 
+def test_forward_is_exact_when_ctas_take_several_tiles():
+    """At (128, 64, 48) x 2 samples (1536 tiles of 4 rows) the persistent first layer's CTAs take
+    several tiles each, alternating staging buffers and accumulator sets: on the exact problem
+    the tcgen05 forward equals the mma.sync forward (which the small grids pin to the oracle) bit
+    for bit."""
+    grid = (128, 64, 48)
+    U, params = exact_problem(grid)
+    phibar = [0.5, 0.5]
+    net = dscf.Net(grid, B, seed=1)
+    net.set_params(torch.from_numpy(flat(params)).float())
+    got = []
+    for path in (0, 1):
+        net.set_tensor_path(path)
+        got.append(net.forward(torch.from_numpy(U).float(), phibar).cpu().numpy().astype(np.float64))
+        net.status()
+    assert np.array_equal(got[0], got[1]), np.abs(got[0] - got[1]).max()
+    assert np.abs(got[0]).max() > 0.1
+
+
 @pytest.mark.parametrize("path", [0, 1], ids=["tcgen05", "mma.sync"])
 def test_parameter_gradients_elementwise(path):
     U, params = exact_problem()
