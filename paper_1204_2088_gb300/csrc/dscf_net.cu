@@ -291,6 +291,19 @@ __global__ void k_net_in_fold(const float* __restrict__ U, const double* __restr
     }
 }
 
+// Channel-last copy h[r][32] of an activation in the padded channel-group layout
+// hp[rows][4][nx + 4][8] (site x at x + 2) that the tcgen05 forward writes; for the backward pass.
+__global__ void k_unpad32(const bf16* __restrict__ hp, int nx, size_t S, bf16* __restrict__ h) {
+    const size_t r = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    if (r >= S) return;
+    const size_t rowi = r / nx;
+    const int x = (int)(r - rowi * nx);
+    const bf16* src = hp + (rowi * 4 * (size_t)(nx + 4) + (size_t)(x + 2)) * 8;
+    uint4* dst = (uint4*)(h + r * 32);
+#pragma unroll
+    for (int g = 0; g < 4; ++g) dst[g] = *(const uint4*)(src + (size_t)g * (nx + 4) * 8);
+}
+
 // Network output: phi_c[r] = phibar_c + y[r][c] - <y_c>  ([B][2][V] float).
 __global__ void k_net_out(const float* __restrict__ y, const double* __restrict__ means, int V, int B, double pb0,
                           double pb1, float* __restrict__ phi) {
@@ -423,8 +436,8 @@ __global__ void k_adam(float* __restrict__ p, const float* __restrict__ g, float
 size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct NetLayout {
-    size_t params, grads, m, v, wf[NL], wb[NL], wt[NL], x16, x16f, h1, h2, y16, dy16, dz2, dz1, gtmp, part, means, lpart,
-        err, bytes;
+    size_t params, grads, m, v, wf[NL], wb[NL], wt[NL], x16, x16f, h1, h2, h1p, h2p, y16, dy16, dz2, dz1, gtmp, part,
+        means, lpart, err, bytes;
 };
 constexpr int kPartBlocks = 512;   // partial sums per channel and sample
 
@@ -446,6 +459,9 @@ NetLayout net_layout(int nx, int ny, int nz, int B) {
     L.x16f = tc_conv_supported(nx, ny) ? take(S / nx * (nx + 4) * 16 * 2) : 0;
     L.h1 = take(S * 32 * 2);
     L.h2 = take(S * 32 * 2);
+    // the tcgen05 forward's activations, in the padded channel-group layout [rows][4][nx + 4][8]
+    L.h1p = tc_conv_supported(nx, ny) ? take(S / nx * (nx + 4) * 32 * 2) : 0;
+    L.h2p = tc_conv_supported(nx, ny) ? take(S / nx * (nx + 4) * 32 * 2) : 0;
     L.y16 = take(S * 16 * 4);
     L.dy16 = take(S * 16 * 2);
     L.dz2 = take(S * 32 * 2);
@@ -525,7 +541,7 @@ void forward(dscf_net* n, const float* U, double pb0, double pb1, float* phi) {
     k_net_in<<<eb, 256, 0, n->stream>>>(U, n->at<double>(n->L.means), V, B, n->at<bf16>(n->L.x16));
     if (n->use_tc()) {
         k_net_in_fold<<<eb, 256, 0, n->stream>>>(U, n->at<double>(n->L.means), n->nx, V, B, n->at<bf16>(n->L.x16f));
-        const size_t act[NL + 1] = {n->L.x16f, n->L.h1, n->L.h2, n->L.y16};
+        const size_t act[NL + 1] = {n->L.x16f, n->L.h1p, n->L.h2p, n->L.y16};
         for (int l = 0; l < NL; ++l)
             launch_conv_tc(l, n->ws + act[l], n->ws + n->L.wt[l], n->at<float>(n->L.params) + poff(l) + wcount(l),
                            COUT[l], n->ws + act[l + 1], n->nx, n->ny, n->nz, B, n->at<double>(n->L.part),
@@ -558,6 +574,10 @@ void backward(dscf_net* n, const float* phi, const float* tgt) {
     const int blocks = (ntiles + 3) / 4;
     const int eb = (int)((S + 255) / 256);
     float* grads = n->at<float>(n->L.grads);
+    if (n->use_tc()) {   // the forward pass left its activations in the padded layout
+        k_unpad32<<<eb, 256, 0, n->stream>>>(n->at<bf16>(n->L.h1p), n->nx, S, n->at<bf16>(n->L.h1));
+        k_unpad32<<<eb, 256, 0, n->stream>>>(n->at<bf16>(n->L.h2p), n->nx, S, n->at<bf16>(n->L.h2));
+    }
     cudaMemsetAsync(grads, 0, NPARAM * 4, n->stream);
     k_loss_g<<<1024, 256, 0, n->stream>>>(phi, tgt, S * 2, n->at<float>(n->L.gtmp), n->at<double>(n->L.lpart));
     chan_means(n, n->at<float>(n->L.gtmp), 2);

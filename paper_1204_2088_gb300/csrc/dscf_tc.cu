@@ -18,8 +18,10 @@
 //
 // The first layer (2 input channels, R = 4) folds the five x offsets into 16 channels and is a
 // persistent, warp-specialised kernel: bulk (TMA) copies, MMAs and epilogue of successive tiles
-// overlap.  The 32-channel layers stack the five dy offsets along N (R = 8 and 4) and stage with
-// per-thread 16-byte copies.
+// overlap.  The 32-channel layers stack the five dy offsets along N (R = 8 and 4) and stage each
+// plane's rows with one bulk copy per row and channel group.  Activations between layers are
+// stored in a padded channel-group layout (each row's channel groups contiguous, with periodic
+// copies of two sites at each end) so that every staged row is one contiguous run.
 //
 // Every wait is bounded; a CTA that gives up sets the error word, frees its tensor memory and
 // returns.
@@ -42,11 +44,6 @@ constexpr int TC_THREADS = 256;  // 8 warps: staging; epilogue pairs of warps pe
 constexpr long long kTcSpinLimit = 1ll << 20;   // try_wait polls (each may suspend ~1 us)
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-__device__ __forceinline__ void cp16(void* s, const void* g) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_u32(s)), "l"(g));
-}
-__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::); }
-__device__ __forceinline__ void cp_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
 // Shared-memory matrix descriptor (no swizzle): start address, leading-dimension byte offset
 // (between core matrices along K), stride-dimension byte offset (between 8-row core-matrix
@@ -80,7 +77,6 @@ __device__ __forceinline__ void mma_commit(uint64_t* mbar) {
 }
 __device__ __forceinline__ void fence_before_sync() { asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory"); }
 __device__ __forceinline__ void fence_after_sync() { asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory"); }
-__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
 
 __device__ __forceinline__ void mbar_init(uint64_t* mbar, int count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(mbar)), "r"(count) : "memory");
@@ -153,6 +149,20 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
                  : "memory");
 }
 
+// Store the 32 BF16 channels hv of site x of grid row rowi ((b nz + z) ny + y) in the padded
+// channel-group layout [rows][4][nx + 4][8] that the next layer stages from: site x at x + 2, and
+// the two sites at each end of the row also as the periodic copies beyond the other end.
+__device__ __forceinline__ void store_padded32(bf16* __restrict__ out, size_t rowi, int x, int nx, const bf16* hv) {
+    bf16* base = out + rowi * 4 * (size_t)(nx + 4) * 8;
+    const int xh = x < 2 ? x + nx + 2 : (x >= nx - 2 ? x - nx + 2 : -1);
+#pragma unroll
+    for (int g = 0; g < 4; ++g) {
+        bf16* row = base + (size_t)g * (nx + 4) * 8;
+        *(uint4*)(row + (size_t)(x + 2) * 8) = ((const uint4*)hv)[g];
+        if (xh >= 0) *(uint4*)(row + (size_t)xh * 8) = ((const uint4*)hv)[g];
+    }
+}
+
 // First layer (2 -> 32 channels, tanh) on the folded input: channels 2 dx + ci (dx = 0..4,
 // ci = 0..1) hold the two real input channels at x + dx - 2 (zero in channels 10..15), so one
 // K = 16 step covers all five x offsets and the offsets left are the 25 (dz, dy).  The folded
@@ -169,7 +179,8 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
 //                     accumulator sets in TMEM (alternating by tile) and commits `tfull` after a
 //                     tile's last plane, once the epilogue has released that set (`tfree`);
 //   warps 2..5        (one TMEM lane quarter each) read a finished set, apply tanh(acc + bias),
-//                     store BF16 [site][32] and release the set,
+//                     store BF16 in the padded channel-group layout of the next layer's input
+//                     ([B][nz][ny][4][nx + 4][8]) and release the set,
 // so the copies, the MMAs and the epilogue of successive tiles overlap.
 constexpr int L1_G = 2;                            // channel groups of the folded input
 constexpr int L1_CO = 32;
@@ -300,13 +311,10 @@ __global__ void __launch_bounds__(L1_THREADS, L1_CTAS_PER_SM)
             for (int r = 0; r < TC_R; ++r) {
                 float v[CO];
                 tmem_ld32(tq + (uint32_t)(r * CO), v);
-                const size_t site = (size_t)b * V + ((size_t)z * ny + (y0 + r)) * nx + x0 + q * 32 + lane;
                 __align__(16) bf16 hv[CO];
 #pragma unroll
                 for (int co = 0; co < CO; ++co) hv[co] = __float2bfloat16(tanhf(v[co] + bs[co]));
-                uint4* dst = (uint4*)(out + site * CO);
-#pragma unroll
-                for (int j = 0; j < CO / 8; ++j) dst[j] = ((const uint4*)hv)[j];
+                store_padded32(out, ((size_t)b * nz + z) * ny + y0 + r, x0 + q * 32 + lane, nx, hv);
             }
             fence_before_sync();
             __syncwarp();
@@ -347,7 +355,13 @@ __device__ __forceinline__ void tmem_zero(uint32_t taddr, int nc) {
 // accumulator of output row r starts at column (r + 4) CO.  Each staged A tile is read once for
 // five offsets instead of once per offset; the accumulators of the 8 halo rows (r < 0, r >= R)
 // collect unused sums.  TMEM is zeroed first so that every MMA accumulates.
+// in: [B][nz][ny][CI / 8][nx + 4][8] BF16, the padded channel-group layout (site x at x + 2, two
+// periodic copies at each end), so that each staged row and channel group is one 2112-byte bulk
+// (TMA) copy; a plane's rows and its weights complete on one mbarrier.
 // wt: [dz][dx][ci / 8][4 - dy][co][ci % 8].  R output rows per CTA, TMEM_COLS >= (R + 8) CO.
+// EPI 0: tanh(acc + bias) -> BF16 in the same padded layout (CO = 32); EPI 1: acc + bias -> FP32
+// [site][16] (CO = 16) and the CTA's FP64 sums of channels 0 and 1 into
+// part[(b * 2 + c) * nblk + i] (i: the CTA's index within its sample, nblk: CTAs per sample).
 template <int CI, int CO, int EPI, int R, int TMEM_COLS, int MINB>
 __global__ void __launch_bounds__(TC_THREADS, MINB)
     k_conv_tc_stk(const bf16* __restrict__ in, const bf16* __restrict__ wt, const float* __restrict__ bias, int cout,
@@ -364,9 +378,10 @@ __global__ void __launch_bounds__(TC_THREADS, MINB)
     extern __shared__ __align__(1024) unsigned char smem[];
     unsigned char* As = smem;
     unsigned char* Ws = smem + ABYTES;
-    __shared__ __align__(8) uint64_t mbar;
+    __shared__ __align__(8) uint64_t mbar, full;
     __shared__ uint32_t tmem_slot;
     __shared__ float csum[TC_THREADS / 32][2];
+    static_assert(ABYTES + WBYTES < (1 << 20), "transaction count of one plane");
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int nxt = nx / 128, nyb = ny / R;
@@ -378,7 +393,7 @@ __global__ void __launch_bounds__(TC_THREADS, MINB)
     const int z = blk % nz, b = blk / nz;
     const int x0 = xt * 128, y0 = yb * R;
     const size_t V = (size_t)nx * ny * nz;
-    const bf16* inb = in + (size_t)b * V * CI;
+    const bf16* inb = in + (size_t)b * (V / nx) * G * (nx + 4) * 8;
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(&tmem_slot)),
@@ -388,6 +403,7 @@ __global__ void __launch_bounds__(TC_THREADS, MINB)
     }
     if (tid == 0) {
         mbar_init(&mbar, 1);
+        mbar_init(&full, 1);
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
     fence_before_sync();
@@ -396,39 +412,30 @@ __global__ void __launch_bounds__(TC_THREADS, MINB)
     const uint32_t tmem = tmem_slot;
     if (warp < 4) tmem_zero(tmem + ((uint32_t)(warp * 32) << 16), (R + 8) * CO);
 
-    constexpr int RCH = TC_XP * G;
-    constexpr int KCH = (RCH + TC_THREADS - 1) / TC_THREADS;
-    int soff[KCH], goff[KCH];
-#pragma unroll
-    for (int k = 0; k < KCH; ++k) {
-        const int c = tid + k * TC_THREADS;
-        const int g = c % G, xp = c / G;
-        int x = x0 - 2 + xp;
-        x = x < 0 ? x + nx : (x >= nx ? x - nx : x);
-        soff[k] = c < RCH ? (g * TC_XP + xp) * 16 : -1;
-        goff[k] = x * CI + g * 8;
-    }
-
     bool ok = true;
+    int pending = -1;   // parity of a plane fill this CTA has not seen land
     for (int dzi = 0; dzi < 5 && ok; ++dzi) {
-        int zin = z + dzi - 2;
-        zin = zin < 0 ? zin + nz : (zin >= nz ? zin - nz : zin);
-#pragma unroll 1
-        for (int i = 0; i < R + 4; ++i) {
-            const int yin = wrapi_(y0 - 2 + i, ny);
-            const bf16* src = inb + ((size_t)zin * ny + yin) * nx * CI;
-            unsigned char* dst = As + i * ROWB;
-#pragma unroll
-            for (int k = 0; k < KCH; ++k)
-                if (soff[k] >= 0) cp16(dst + soff[k], src + goff[k]);
+        const int zin = wrapi_(z + dzi - 2, nz);
+        if (warp == 4) {   // the plane's R + 4 rows (one copy per row and channel group) and weights
+            if (lane == 0) mbar_expect(&full, ABYTES + WBYTES);
+            __syncwarp();
+            for (int c = lane; c < (R + 4) * G; c += 32) {
+                const int i = c / G, g = c % G;
+                const int yin = wrapi_(y0 - 2 + i, ny);
+                const bf16* src = inb + ((((size_t)zin * ny + yin) * G + g) * (nx + 4) + x0) * 8;
+                bulk_g2s(As + (i * G + g) * TC_XP * 16, src, TC_XP * 16, &full);
+            }
+            if (lane == 0) bulk_g2s(Ws, wt + (size_t)dzi * (WBYTES / 2), WBYTES, &full);
         }
-        const bf16* wsrc = wt + (size_t)dzi * (WBYTES / 2);
-        for (int c = tid; c < WBYTES / 16; c += TC_THREADS) cp16(Ws + (size_t)c * 16, wsrc + (size_t)c * 8);
-        cp_commit();
-        cp_wait_all();
-        fence_proxy_async();
+        pending = dzi & 1;
+        const bool landed = mbar_wait(&full, (uint32_t)(dzi & 1));
+        if (landed) pending = -1;
         fence_before_sync();   // orders the TMEM zeroing before the MMAs
-        __syncthreads();
+        ok = __syncthreads_and(landed ? 1 : 0) != 0;
+        if (!ok) {
+            if (tid == 0) atomicOr(err, 1);
+            break;
+        }
         if (tid == 0) {
             fence_after_sync();
             const uint32_t a0 = smem_u32(As), w0 = smem_u32(Ws);
@@ -443,10 +450,12 @@ __global__ void __launch_bounds__(TC_THREADS, MINB)
                     }
             mma_commit(&mbar);
         }
+        __syncwarp();
         const bool done = mbar_wait(&mbar, (uint32_t)(dzi & 1));
-        if (!done) atomicOr(err, 1);
+        if (!done && lane == 0) atomicOr(err, 1);
         ok = __syncthreads_and(done ? 1 : 0) != 0;
     }
+    if (pending >= 0 && warp == 4) mbar_wait(&full, (uint32_t)pending);   // copies in flight land first
     fence_after_sync();
     float s0 = 0.f, s1 = 0.f;
     if (ok) {
@@ -463,12 +472,11 @@ __global__ void __launch_bounds__(TC_THREADS, MINB)
 #pragma unroll
             for (int co = 0; co < CO; ++co) v[co] += (co < cout) ? bias[co] : 0.f;
             if (EPI == 0) {
+                static_assert(EPI != 0 || CO == 32, "the padded output layout holds 32 channels");
                 __align__(16) bf16 hv[CO];
 #pragma unroll
                 for (int co = 0; co < CO; ++co) hv[co] = __float2bfloat16(tanhf(v[co]));
-                uint4* dst = (uint4*)((bf16*)out + site * CO);
-#pragma unroll
-                for (int k = 0; k < CO / 8; ++k) dst[k] = ((const uint4*)hv)[k];
+                store_padded32((bf16*)out, ((size_t)b * nz + z) * ny + y0 + r, x, nx, hv);
             } else {
                 float4* dst = (float4*)((float*)out + site * 16);
 #pragma unroll
