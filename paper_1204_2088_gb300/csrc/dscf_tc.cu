@@ -357,12 +357,15 @@ __device__ __forceinline__ void tmem_zero(uint32_t taddr, int nc) {
 // collect unused sums.  TMEM is zeroed first so that every MMA accumulates.
 // in: [B][nz][ny][CI / 8][nx + 4][8] BF16, the padded channel-group layout (site x at x + 2, two
 // periodic copies at each end), so that each staged row and channel group is one 2112-byte bulk
-// (TMA) copy; a plane's rows and its weights complete on one mbarrier.
+// (TMA) copy.  The staged rows form NGRP groups that stream independently: warp 4 refills a
+// group with the next plane's rows as soon as the MMAs that read it have completed (`afree`), and
+// loads each plane's weights into one of NWB buffers (`wfull` / `wfree`), so the copies of plane
+// dz + 1 overlap the MMAs of plane dz; thread 0 issues the MMAs group by group.
 // wt: [dz][dx][ci / 8][4 - dy][co][ci % 8].  R output rows per CTA, TMEM_COLS >= (R + 8) CO.
 // EPI 0: tanh(acc + bias) -> BF16 in the same padded layout (CO = 32); EPI 1: acc + bias -> FP32
 // [site][16] (CO = 16) and the CTA's FP64 sums of channels 0 and 1 into
 // part[(b * 2 + c) * nblk + i] (i: the CTA's index within its sample, nblk: CTAs per sample).
-template <int CI, int CO, int EPI, int R, int TMEM_COLS, int MINB>
+template <int CI, int CO, int EPI, int R, int TMEM_COLS, int MINB, int NWB>
 __global__ void __launch_bounds__(TC_THREADS, MINB)
     k_conv_tc_stk(const bf16* __restrict__ in, const bf16* __restrict__ wt, const float* __restrict__ bias, int cout,
                   void* __restrict__ out, int nx, int ny, int nz, double* __restrict__ part, int* __restrict__ err) {
@@ -371,17 +374,19 @@ __global__ void __launch_bounds__(TC_THREADS, MINB)
     constexpr int ABYTES = (R + 4) * ROWB;
     constexpr int NS = 5 * CO;                      // stacked N
     constexpr int WBYTES = 5 * G * NS * 16;         // weights of one dz
+    constexpr int NGRP = 4;                         // row groups of a staged plane
+    constexpr int RG = (R + 4) / NGRP;              // rows per group
     constexpr uint32_t IDESC = idesc_bf16(128, NS);
     static_assert((R + 8) * CO <= TMEM_COLS, "accumulators exceed the tensor-memory allocation");
     static_assert(NS % 16 == 0 && NS <= 256, "stacked N");
-    static_assert(R % 2 == 0, "R");
+    static_assert(R % 2 == 0 && (R + 4) % NGRP == 0, "R");
+    static_assert(NWB == 1 || NWB == 2, "weight buffers");
     extern __shared__ __align__(1024) unsigned char smem[];
     unsigned char* As = smem;
     unsigned char* Ws = smem + ABYTES;
-    __shared__ __align__(8) uint64_t mbar, full;
+    __shared__ __align__(8) uint64_t afull[NGRP], afree[NGRP], wfull[NWB], wfree[NWB], done;
     __shared__ uint32_t tmem_slot;
     __shared__ float csum[TC_THREADS / 32][2];
-    static_assert(ABYTES + WBYTES < (1 << 20), "transaction count of one plane");
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int nxt = nx / 128, nyb = ny / R;
@@ -402,8 +407,15 @@ __global__ void __launch_bounds__(TC_THREADS, MINB)
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
     }
     if (tid == 0) {
-        mbar_init(&mbar, 1);
-        mbar_init(&full, 1);
+        for (int i = 0; i < NGRP; ++i) {
+            mbar_init(&afull[i], 1);
+            mbar_init(&afree[i], 1);
+        }
+        for (int i = 0; i < NWB; ++i) {
+            mbar_init(&wfull[i], 1);
+            mbar_init(&wfree[i], 1);
+        }
+        mbar_init(&done, 1);
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
     fence_before_sync();
@@ -411,51 +423,82 @@ __global__ void __launch_bounds__(TC_THREADS, MINB)
     fence_after_sync();
     const uint32_t tmem = tmem_slot;
     if (warp < 4) tmem_zero(tmem + ((uint32_t)(warp * 32) << 16), (R + 8) * CO);
+    fence_before_sync();   // orders the TMEM zeroing before the MMAs
+    __syncthreads();
+    fence_after_sync();
 
     bool ok = true;
-    int pending = -1;   // parity of a plane fill this CTA has not seen land
-    for (int dzi = 0; dzi < 5 && ok; ++dzi) {
-        const int zin = wrapi_(z + dzi - 2, nz);
-        if (warp == 4) {   // the plane's R + 4 rows (one copy per row and channel group) and weights
-            if (lane == 0) mbar_expect(&full, ABYTES + WBYTES);
-            __syncwarp();
-            for (int c = lane; c < (R + 4) * G; c += 32) {
-                const int i = c / G, g = c % G;
-                const int yin = wrapi_(y0 - 2 + i, ny);
-                const bf16* src = inb + ((((size_t)zin * ny + yin) * G + g) * (nx + 4) + x0) * 8;
-                bulk_g2s(As + (i * G + g) * TC_XP * 16, src, TC_XP * 16, &full);
+    // planes whose weights / rows warp 4 has issued, and groups issued of the next plane's rows
+    int nw_issued = 0, na_issued = 0, part_groups = 0;
+    if (warp == 4) {   // bulk copies
+        for (int p = 0; p < 5 && ok; ++p) {
+            const int zin = wrapi_(z + p - 2, nz);
+            const int wb = p % NWB;
+            if (p >= NWB && !(ok = __all_sync(0xffffffffu, mbar_wait(&wfree[wb], (uint32_t)((p / NWB - 1) & 1)))))
+                break;
+            if (lane == 0) {
+                mbar_expect(&wfull[wb], WBYTES);
+                bulk_g2s(Ws + wb * WBYTES, wt + (size_t)p * (WBYTES / 2), WBYTES, &wfull[wb]);
             }
-            if (lane == 0) bulk_g2s(Ws, wt + (size_t)dzi * (WBYTES / 2), WBYTES, &full);
+            nw_issued = p + 1;
+            for (int gi = 0; gi < NGRP && ok; ++gi) {
+                if (p >= 1 && !(ok = __all_sync(0xffffffffu, mbar_wait(&afree[gi], (uint32_t)((p - 1) & 1))))) break;
+                if (lane == 0) mbar_expect(&afull[gi], RG * ROWB);
+                __syncwarp();
+                for (int c = lane; c < RG * G; c += 32) {
+                    const int i = gi * RG + c / G, g = c % G;
+                    const int yin = wrapi_(y0 - 2 + i, ny);
+                    const bf16* src = inb + ((((size_t)zin * ny + yin) * G + g) * (nx + 4) + x0) * 8;
+                    bulk_g2s(As + (i * G + g) * TC_XP * 16, src, TC_XP * 16, &afull[gi]);
+                }
+                part_groups = gi + 1;
+            }
+            if (ok) {
+                na_issued = p + 1;
+                part_groups = 0;
+            }
         }
-        pending = dzi & 1;
-        const bool landed = mbar_wait(&full, (uint32_t)(dzi & 1));
-        if (landed) pending = -1;
-        fence_before_sync();   // orders the TMEM zeroing before the MMAs
-        ok = __syncthreads_and(landed ? 1 : 0) != 0;
-        if (!ok) {
-            if (tid == 0) atomicOr(err, 1);
-            break;
-        }
-        if (tid == 0) {
-            fence_after_sync();
-            const uint32_t a0 = smem_u32(As), w0 = smem_u32(Ws);
-            for (int j = 0; j < R + 4; ++j)
-                for (int dxi = 0; dxi < 5; ++dxi)
+        if (!ok && lane == 0) atomicOr(err, 1);
+    } else if (tid == 0) {   // MMA issue
+        for (int p = 0; p < 5 && ok; ++p) {
+            const int wb = p % NWB;
+            if (!(ok = mbar_wait(&wfull[wb], (uint32_t)((p / NWB) & 1)))) break;
+            const uint32_t w0 = smem_u32(Ws + wb * WBYTES);
+            for (int gi = 0; gi < NGRP; ++gi) {
+                if (!(ok = mbar_wait(&afull[gi], (uint32_t)(p & 1)))) break;
+                fence_after_sync();
+                const uint32_t a0 = smem_u32(As);
+                for (int j = gi * RG; j < (gi + 1) * RG; ++j)
+                    for (int dxi = 0; dxi < 5; ++dxi)
 #pragma unroll
-                    for (int kk = 0; kk < CI / 16; ++kk) {
-                        const uint32_t aaddr = a0 + (uint32_t)((j * G + 2 * kk) * TC_XP + dxi) * 16u;
-                        const uint32_t baddr = w0 + (uint32_t)((dxi * G + 2 * kk) * NS) * 16u;
-                        mma_bf16(tmem + (uint32_t)(j * CO), smem_desc(aaddr, TC_XP * 16, 128),
-                                 smem_desc(baddr, NS * 16, 128), IDESC, 1);
-                    }
-            mma_commit(&mbar);
+                        for (int kk = 0; kk < CI / 16; ++kk) {
+                            const uint32_t aaddr = a0 + (uint32_t)((j * G + 2 * kk) * TC_XP + dxi) * 16u;
+                            const uint32_t baddr = w0 + (uint32_t)((dxi * G + 2 * kk) * NS) * 16u;
+                            mma_bf16(tmem + (uint32_t)(j * CO), smem_desc(aaddr, TC_XP * 16, 128),
+                                     smem_desc(baddr, NS * 16, 128), IDESC, 1);
+                        }
+                mma_commit(&afree[gi]);   // the group's rows may be refilled
+            }
+            if (ok) mma_commit(&wfree[wb]);   // the plane's weights may be overwritten
         }
-        __syncwarp();
-        const bool done = mbar_wait(&mbar, (uint32_t)(dzi & 1));
-        if (!done && lane == 0) atomicOr(err, 1);
-        ok = __syncthreads_and(done ? 1 : 0) != 0;
+        if (ok) mma_commit(&done);
+        else atomicOr(err, 1);
     }
-    if (pending >= 0 && warp == 4) mbar_wait(&full, (uint32_t)pending);   // copies in flight land first
+    __syncwarp();   // warp 0 reconverges after its MMA-issuing thread
+    const bool fin = ok && mbar_wait(&done, 0u);
+    if (ok && !fin && lane == 0) atomicOr(err, 1);
+    ok = __syncthreads_and(fin ? 1 : 0) != 0;
+    if (!ok && warp == 4) {   // copies in flight land before the CTA exits
+        if (nw_issued)
+            for (int i = 0; i < NWB && i < nw_issued; ++i) {
+                const int last = nw_issued - 1 - ((nw_issued - 1 - i) % NWB);   // last plane loaded into buffer i
+                mbar_wait(&wfull[i], (uint32_t)((last / NWB) & 1));
+            }
+        for (int gi = 0; gi < NGRP; ++gi) {
+            const int n = na_issued + (gi < part_groups ? 1 : 0);
+            if (n) mbar_wait(&afull[gi], (uint32_t)((n - 1) & 1));
+        }
+    }
     fence_after_sync();
     float s0 = 0.f, s1 = 0.f;
     if (ok) {
@@ -527,27 +570,26 @@ int l1_grid(int ntile) {
     const int g = (nsm > 0 ? nsm : 1) * L1_CTAS_PER_SM;
     return ntile < g ? ntile : g;
 }
-// the stacked variant: R + 4 staged rows and the weights of one whole dz
-constexpr size_t stk_smem(int ci, int co, int r) {
-    return (size_t)(r + 4) * (ci / 8) * TC_XP * 16 + (size_t)25 * (ci / 8) * co * 16;
+// the stacked variant: R + 4 staged rows and NWB buffers of the weights of one whole dz
+constexpr size_t stk_smem(int ci, int co, int r, int nwb) {
+    return (size_t)(r + 4) * (ci / 8) * TC_XP * 16 + (size_t)nwb * 25 * (ci / 8) * co * 16;
 }
-constexpr int kR2 = 8, kR3 = 4;   // output rows per CTA of the second and third layer
-
+constexpr int kR2 = 8, kR3 = 8;   // output rows per CTA of the second and third layer
 bool tc_conv_supported(int nx, int ny) { return nx % 128 == 0 && ny % kR2 == 0; }
 
 int tc_conv_prepare() {
     // the whole unified L1/shared array as shared memory, so that several CTAs fit per SM
     cudaFuncSetAttribute(k_conv_tc_l1, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-    cudaFuncSetAttribute(k_conv_tc_stk<32, 32, 0, kR2, 512, 1>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-    cudaFuncSetAttribute(k_conv_tc_stk<32, 16, 1, kR3, 256, 2>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    cudaFuncSetAttribute(k_conv_tc_stk<32, 32, 0, kR2, 512, 1, 2>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    cudaFuncSetAttribute(k_conv_tc_stk<32, 16, 1, kR3, 256, 1, 2>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     cudaError_t e =
         cudaFuncSetAttribute(k_conv_tc_l1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_conv_smem());
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_conv_tc_stk<32, 32, 0, kR2, 512, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)stk_smem(32, 32, kR2));
+        e = cudaFuncSetAttribute(k_conv_tc_stk<32, 32, 0, kR2, 512, 1, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)stk_smem(32, 32, kR2, 2));
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_conv_tc_stk<32, 16, 1, kR3, 256, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)stk_smem(32, 16, kR3));
+        e = cudaFuncSetAttribute(k_conv_tc_stk<32, 16, 1, kR3, 256, 1, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)stk_smem(32, 16, kR3, 2));
     return (int)e;
 }
 
@@ -566,10 +608,10 @@ void launch_conv_tc(int layer, const void* in, const void* wt, const float* bias
         k_conv_tc_l1<<<l1_grid(B * nz * (ny / TC_R) * (nx / 128)), L1_THREADS, tc_conv_smem(), s>>>(
             x, w, bias, cout, (bf16*)out, nx, ny, nz, B, err);
     else if (layer == 1)
-        k_conv_tc_stk<32, 32, 0, kR2, 512, 1><<<B * nz * (ny / kR2) * (nx / 128), TC_THREADS, stk_smem(32, 32, kR2), s>>>(
+        k_conv_tc_stk<32, 32, 0, kR2, 512, 1, 2><<<B * nz * (ny / kR2) * (nx / 128), TC_THREADS, stk_smem(32, 32, kR2, 2), s>>>(
             x, w, bias, cout, out, nx, ny, nz, part, err);
     else
-        k_conv_tc_stk<32, 16, 1, kR3, 256, 2><<<B * nz * (ny / kR3) * (nx / 128), TC_THREADS, stk_smem(32, 16, kR3), s>>>(
+        k_conv_tc_stk<32, 16, 1, kR3, 256, 1, 2><<<B * nz * (ny / kR3) * (nx / 128), TC_THREADS, stk_smem(32, 16, kR3, 2), s>>>(
             x, w, bias, cout, out, nx, ny, nz, part, err);
 }
 
