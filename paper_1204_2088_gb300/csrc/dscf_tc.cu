@@ -12,14 +12,14 @@
 // descriptor has 128 B between core matrices along M (sites) and 132 x 16 B between channel
 // groups along K, and the shift by dx is just 16 dx bytes added to its start address.  Weights
 // are staged as [offset][channel group][co][8], the same layout for the N x K operand.  One
-// thread issues the MMAs; tcgen05.commit on an mbarrier tells the CTA when staged operands may be
-// overwritten and when the accumulators are complete.  The epilogue (bias, tanh, BF16 or FP32
-// channel-last stores) reads each warp's quarter of the TMEM lanes with tcgen05.ld.
+// thread issues the MMAs; tcgen05.commit on mbarriers tells the copying warp when staged operands
+// may be overwritten and the CTA when the accumulators are complete.  The epilogue (bias, then
+// tanh to BF16 or FP32 stores) reads each warp's quarter of the TMEM lanes with tcgen05.ld.
 //
 // The first layer (2 input channels, R = 4) folds the five x offsets into 16 channels and is a
 // persistent, warp-specialised kernel: bulk (TMA) copies, MMAs and epilogue of successive tiles
-// overlap.  The 32-channel layers stack the five dy offsets along N (R = 8 and 4) and stage each
-// plane's rows with one bulk copy per row and channel group.  Activations between layers are
+// overlap.  The 32-channel layers stack the five dy offsets along N (R = 8) and stream each
+// plane's rows in, one bulk copy per row and channel group.  Activations between layers are
 // stored in a padded channel-group layout (each row's channel groups contiguous, with periodic
 // copies of two sites at each end) so that every staged row is one contiguous run.
 //
@@ -38,9 +38,10 @@ namespace {
 
 typedef __nv_bfloat16 bf16;
 
-constexpr int TC_R = 4;            // output rows per CTA
+constexpr int TC_R = 4;            // output rows per tile of the first layer
 constexpr int TC_XP = 132;         // staged row length (128 + 2 on each side)
-constexpr int TC_THREADS = 256;  // 8 warps: staging; epilogue pairs of warps per TMEM lane quarter
+constexpr int TC_THREADS = 256;    // stacked layers: warp 4 copies, thread 0 issues MMAs, all 8
+                                   // warps run the epilogue (two per TMEM lane quarter)
 constexpr long long kTcSpinLimit = 1ll << 20;   // try_wait polls (each may suspend ~1 us)
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
