@@ -40,8 +40,6 @@ typedef __nv_bfloat16 bf16;
 
 constexpr int TC_R = 4;            // output rows per tile of the first layer
 constexpr int TC_XP = 132;         // staged row length (128 + 2 on each side)
-constexpr int TC_THREADS = 256;    // stacked layers: warp 4 copies, thread 0 issues MMAs, all 8
-                                   // warps run the epilogue (two per TMEM lane quarter)
 constexpr long long kTcSpinLimit = 1ll << 20;   // try_wait polls (each may suspend ~1 us)
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -355,21 +353,30 @@ __device__ __forceinline__ void tmem_zero(uint32_t taddr, int nc) {
 // columns land on the accumulators of output rows j - 4 .. j, which sit side by side when the
 // accumulator of output row r starts at column (r + 4) CO.  Each staged A tile is read once for
 // five offsets instead of once per offset; the accumulators of the 8 halo rows (r < 0, r >= R)
-// collect unused sums.  TMEM is zeroed first so that every MMA accumulates.
+// collect unused sums, so every MMA accumulates onto zeroed tensor memory.
 // in: [B][nz][ny][CI / 8][nx + 4][8] BF16, the padded channel-group layout (site x at x + 2, two
 // periodic copies at each end), so that each staged row and channel group is one 2112-byte bulk
-// (TMA) copy.  The staged rows form NGRP groups that stream independently: warp 4 refills a
-// group with the next plane's rows as soon as the MMAs that read it have completed (`afree`), and
-// loads each plane's weights into one of NWB buffers (`wfull` / `wfree`), so the copies of plane
-// dz + 1 overlap the MMAs of plane dz; thread 0 issues the MMAs group by group.
-// wt: [dz][dx][ci / 8][4 - dy][co][ci % 8].  R output rows per CTA, TMEM_COLS >= (R + 8) CO.
-// EPI 0: tanh(acc + bias) -> BF16 in the same padded layout (CO = 32); EPI 1: acc + bias -> FP32
-// [site][16] (CO = 16) and the CTA's FP64 sums of channels 0 and 1 into
-// part[(b * 2 + c) * nblk + i] (i: the CTA's index within its sample, nblk: CTAs per sample).
-template <int CI, int CO, int EPI, int R, int TMEM_COLS, int MINB, int NWB>
-__global__ void __launch_bounds__(TC_THREADS, MINB)
+// (TMA) copy.  wt: [dz][dx][ci / 8][4 - dy][co][ci % 8].
+// Persistent and warp-specialised: each CTA takes tiles (R output rows of 128 sites)
+// blockIdx.x, + gridDim.x, ... and streams their planes (5 per tile):
+//   warp 1 (copies)   loads each plane's weights into one of two buffers (`wfull` / `wfree`) and
+//                     its R + 4 staged rows in four groups, a group refilled with the next plane's
+//                     rows as soon as the MMAs that read it have completed (`afull` / `afree`);
+//   thread 0 (MMAs)   issues a plane's MMAs group by group into one of NACC accumulator sets
+//                     (alternating by tile) and commits `tfull` after a tile's last plane, once
+//                     the epilogue has released that set (`tfree`);
+//   warps 2..9        (two per TMEM lane quarter, half of the rows each) read a finished set,
+//                     store the outputs, zero the set again and release it.
+// EPI 0: tanh(acc + bias) -> BF16 in the padded layout (CO = 32); EPI 1: acc + bias -> FP32
+// [site][16] (CO = 16) and the tile's FP64 sums of channels 0 and 1, added in a fixed order, into
+// part[(b * 2 + c) * nblk + i] (i: the tile's index within its sample, nblk: tiles per sample).
+constexpr int STK_THREADS = 320;
+
+template <int CI, int CO, int EPI, int R, int NACC>
+__global__ void __launch_bounds__(STK_THREADS, 1)
     k_conv_tc_stk(const bf16* __restrict__ in, const bf16* __restrict__ wt, const float* __restrict__ bias, int cout,
-                  void* __restrict__ out, int nx, int ny, int nz, double* __restrict__ part, int* __restrict__ err) {
+                  void* __restrict__ out, int nx, int ny, int nz, int B, double* __restrict__ part,
+                  int* __restrict__ err) {
     constexpr int G = CI / 8;
     constexpr int ROWB = G * TC_XP * 16;
     constexpr int ABYTES = (R + 4) * ROWB;
@@ -377,29 +384,38 @@ __global__ void __launch_bounds__(TC_THREADS, MINB)
     constexpr int WBYTES = 5 * G * NS * 16;         // weights of one dz
     constexpr int NGRP = 4;                         // row groups of a staged plane
     constexpr int RG = (R + 4) / NGRP;              // rows per group
+    constexpr int NWB = 2;                          // weight buffers
+    constexpr int SETC = (R + 8) * CO;              // TMEM columns of one accumulator set
+    constexpr int TMEM_COLS = NACC * SETC;
     constexpr uint32_t IDESC = idesc_bf16(128, NS);
-    static_assert((R + 8) * CO <= TMEM_COLS, "accumulators exceed the tensor-memory allocation");
+    static_assert(TMEM_COLS == 256 || TMEM_COLS == 512, "tensor-memory allocation");
     static_assert(NS % 16 == 0 && NS <= 256, "stacked N");
-    static_assert(R % 2 == 0 && (R + 4) % NGRP == 0, "R");
-    static_assert(NWB == 1 || NWB == 2, "weight buffers");
+    static_assert(R % 2 == 0 && (R + 4) % NGRP == 0 && (SETC / 2) % 32 == 0, "R");
+    static_assert(EPI != 0 || CO == 32, "the padded output layout holds 32 channels");
     extern __shared__ __align__(1024) unsigned char smem[];
     unsigned char* As = smem;
     unsigned char* Ws = smem + ABYTES;
-    __shared__ __align__(8) uint64_t afull[NGRP], afree[NGRP], wfull[NWB], wfree[NWB], done;
+    __shared__ __align__(8) uint64_t afull[NGRP], afree[NGRP], wfull[NWB], wfree[NWB], tfull[NACC], tfree[NACC],
+        psum[NACC];
     __shared__ uint32_t tmem_slot;
-    __shared__ float csum[TC_THREADS / 32][2];
+    __shared__ float csum[NACC][8][2];
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int nxt = nx / 128, nyb = ny / R;
-    int blk = blockIdx.x;
-    const int xt = blk % nxt;
-    blk /= nxt;
-    const int yb = blk % nyb;
-    blk /= nyb;
-    const int z = blk % nz, b = blk / nz;
-    const int x0 = xt * 128, y0 = yb * R;
+    const int nblk = nz * nyb * nxt;   // tiles per sample
+    const int ntile = B * nblk;
+    const int nk = ntile > (int)blockIdx.x ? (ntile - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x : 0;
     const size_t V = (size_t)nx * ny * nz;
-    const bf16* inb = in + (size_t)b * (V / nx) * G * (nx + 4) * 8;
+    auto tile_of = [&](int k, int& t, int& b, int& z, int& y0, int& x0) {
+        t = (int)blockIdx.x + k * (int)gridDim.x;
+        int u = t;
+        x0 = (u % nxt) * 128;
+        u /= nxt;
+        y0 = (u % nyb) * R;
+        u /= nyb;
+        z = u % nz;
+        b = u / nz;
+    };
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(&tmem_slot)),
@@ -416,34 +432,44 @@ __global__ void __launch_bounds__(TC_THREADS, MINB)
             mbar_init(&wfull[i], 1);
             mbar_init(&wfree[i], 1);
         }
-        mbar_init(&done, 1);
+        for (int i = 0; i < NACC; ++i) {
+            mbar_init(&tfull[i], 1);
+            mbar_init(&tfree[i], 8);   // one arrival per epilogue warp
+            mbar_init(&psum[i], 8);
+        }
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
     fence_before_sync();
     __syncthreads();
     fence_after_sync();
     const uint32_t tmem = tmem_slot;
-    if (warp < 4) tmem_zero(tmem + ((uint32_t)(warp * 32) << 16), (R + 8) * CO);
-    fence_before_sync();   // orders the TMEM zeroing before the MMAs
+    const int q = warp & 3, half = (warp - 2) >> 2;   // epilogue warps: lane quarter, half of the rows
+    const uint32_t tq = tmem + ((uint32_t)(q * 32) << 16);
+    if (warp >= 2)
+        for (int a = 0; a < NACC; ++a) tmem_zero(tq + (uint32_t)(a * SETC + half * (SETC / 2)), SETC / 2);
+    fence_before_sync();   // the zeroing precedes the first MMAs
     __syncthreads();
     fence_after_sync();
 
     bool ok = true;
-    // planes whose weights / rows warp 4 has issued, and groups issued of the next plane's rows
+    // planes whose weights / rows warp 1 has issued, and groups issued of the next plane's rows
     int nw_issued = 0, na_issued = 0, part_groups = 0;
-    if (warp == 4) {   // bulk copies
-        for (int p = 0; p < 5 && ok; ++p) {
+    if (warp == 1) {   // bulk copies
+        for (int P = 0; P < 5 * nk && ok; ++P) {
+            int t, b, z, y0, x0;
+            tile_of(P / 5, t, b, z, y0, x0);
+            const int p = P % 5, wb = P % NWB;
             const int zin = wrapi_(z + p - 2, nz);
-            const int wb = p % NWB;
-            if (p >= NWB && !(ok = __all_sync(0xffffffffu, mbar_wait(&wfree[wb], (uint32_t)((p / NWB - 1) & 1)))))
+            const bf16* inb = in + (size_t)b * (V / nx) * G * (nx + 4) * 8;
+            if (P >= NWB && !(ok = __all_sync(0xffffffffu, mbar_wait(&wfree[wb], (uint32_t)((P / NWB - 1) & 1)))))
                 break;
             if (lane == 0) {
                 mbar_expect(&wfull[wb], WBYTES);
                 bulk_g2s(Ws + wb * WBYTES, wt + (size_t)p * (WBYTES / 2), WBYTES, &wfull[wb]);
             }
-            nw_issued = p + 1;
+            nw_issued = P + 1;
             for (int gi = 0; gi < NGRP && ok; ++gi) {
-                if (p >= 1 && !(ok = __all_sync(0xffffffffu, mbar_wait(&afree[gi], (uint32_t)((p - 1) & 1))))) break;
+                if (P >= 1 && !(ok = __all_sync(0xffffffffu, mbar_wait(&afree[gi], (uint32_t)((P - 1) & 1))))) break;
                 if (lane == 0) mbar_expect(&afull[gi], RG * ROWB);
                 __syncwarp();
                 for (int c = lane; c < RG * G; c += 32) {
@@ -455,97 +481,113 @@ __global__ void __launch_bounds__(TC_THREADS, MINB)
                 part_groups = gi + 1;
             }
             if (ok) {
-                na_issued = p + 1;
+                na_issued = P + 1;
                 part_groups = 0;
             }
         }
         if (!ok && lane == 0) atomicOr(err, 1);
     } else if (tid == 0) {   // MMA issue
-        for (int p = 0; p < 5 && ok; ++p) {
-            const int wb = p % NWB;
-            if (!(ok = mbar_wait(&wfull[wb], (uint32_t)((p / NWB) & 1)))) break;
-            const uint32_t w0 = smem_u32(Ws + wb * WBYTES);
-            for (int gi = 0; gi < NGRP; ++gi) {
-                if (!(ok = mbar_wait(&afull[gi], (uint32_t)(p & 1)))) break;
-                fence_after_sync();
-                const uint32_t a0 = smem_u32(As);
-                for (int j = gi * RG; j < (gi + 1) * RG; ++j)
-                    for (int dxi = 0; dxi < 5; ++dxi)
+        for (int k = 0; k < nk && ok; ++k) {
+            const int acc = k % NACC;
+            if (k >= NACC && !(ok = mbar_wait(&tfree[acc], (uint32_t)((k / NACC - 1) & 1)))) break;
+            fence_after_sync();
+            const uint32_t t0 = tmem + (uint32_t)(acc * SETC);
+            for (int p = 0; p < 5 && ok; ++p) {
+                const int P = 5 * k + p, wb = P % NWB;
+                if (!(ok = mbar_wait(&wfull[wb], (uint32_t)((P / NWB) & 1)))) break;
+                const uint32_t w0 = smem_u32(Ws + wb * WBYTES), a0 = smem_u32(As);
+                for (int gi = 0; gi < NGRP; ++gi) {
+                    if (!(ok = mbar_wait(&afull[gi], (uint32_t)(P & 1)))) break;
+                    fence_after_sync();
+                    for (int j = gi * RG; j < (gi + 1) * RG; ++j)
+                        for (int dxi = 0; dxi < 5; ++dxi)
 #pragma unroll
-                        for (int kk = 0; kk < CI / 16; ++kk) {
-                            const uint32_t aaddr = a0 + (uint32_t)((j * G + 2 * kk) * TC_XP + dxi) * 16u;
-                            const uint32_t baddr = w0 + (uint32_t)((dxi * G + 2 * kk) * NS) * 16u;
-                            mma_bf16(tmem + (uint32_t)(j * CO), smem_desc(aaddr, TC_XP * 16, 128),
-                                     smem_desc(baddr, NS * 16, 128), IDESC, 1);
-                        }
-                mma_commit(&afree[gi]);   // the group's rows may be refilled
+                            for (int kk = 0; kk < CI / 16; ++kk) {
+                                const uint32_t aaddr = a0 + (uint32_t)((j * G + 2 * kk) * TC_XP + dxi) * 16u;
+                                const uint32_t baddr = w0 + (uint32_t)((dxi * G + 2 * kk) * NS) * 16u;
+                                mma_bf16(t0 + (uint32_t)(j * CO), smem_desc(aaddr, TC_XP * 16, 128),
+                                         smem_desc(baddr, NS * 16, 128), IDESC, 1);
+                            }
+                    mma_commit(&afree[gi]);   // the group's rows may be refilled
+                }
+                if (ok) mma_commit(&wfree[wb]);   // the plane's weights may be overwritten
             }
-            if (ok) mma_commit(&wfree[wb]);   // the plane's weights may be overwritten
+            if (ok) mma_commit(&tfull[acc]);   // the tile's accumulators are complete
         }
-        if (ok) mma_commit(&done);
-        else atomicOr(err, 1);
+        if (!ok) atomicOr(err, 1);
+    } else if (warp >= 2) {   // epilogue
+        float bs[CO];
+#pragma unroll
+        for (int co = 0; co < CO; ++co) bs[co] = co < cout ? bias[co] : 0.f;
+        for (int k = 0; k < nk && ok; ++k) {
+            const int acc = k % NACC;
+            ok = __all_sync(0xffffffffu, mbar_wait(&tfull[acc], (uint32_t)((k / NACC) & 1)));
+            if (!ok) break;
+            fence_after_sync();
+            int t, b, z, y0, x0;
+            tile_of(k, t, b, z, y0, x0);
+            const int x = x0 + q * 32 + lane;
+            const uint32_t ts = tq + (uint32_t)(acc * SETC);
+            float s0 = 0.f, s1 = 0.f;
+#pragma unroll 1
+            for (int r = half * (R / 2); r < (half + 1) * (R / 2); ++r) {
+                float v[CO];
+                const uint32_t col = (uint32_t)((r + 4) * CO);
+                if (CO == 32) tmem_ld32(ts + col, v);
+                else tmem_ld16(ts + col, v);
+#pragma unroll
+                for (int co = 0; co < CO; ++co) v[co] += bs[co];
+                if (EPI == 0) {
+                    __align__(16) bf16 hv[CO];
+#pragma unroll
+                    for (int co = 0; co < CO; ++co) hv[co] = __float2bfloat16(tanhf(v[co]));
+                    store_padded32((bf16*)out, ((size_t)b * nz + z) * ny + y0 + r, x, nx, hv);
+                } else {
+                    const size_t site = (size_t)b * V + ((size_t)z * ny + (y0 + r)) * nx + x;
+                    float4* dst = (float4*)((float*)out + site * 16);
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) dst[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+                    s0 += v[0];
+                    s1 += v[1];
+                }
+            }
+            tmem_zero(ts + (uint32_t)(half * (SETC / 2)), SETC / 2);   // ready for the set's next tile
+            if (EPI == 1) {   // the tile's sums of the two output channels, in a fixed order
+#pragma unroll
+                for (int m = 16; m > 0; m >>= 1) {
+                    s0 += __shfl_xor_sync(0xffffffffu, s0, m);
+                    s1 += __shfl_xor_sync(0xffffffffu, s1, m);
+                }
+                if (lane == 0) {
+                    csum[acc][warp - 2][0] = s0;
+                    csum[acc][warp - 2][1] = s1;
+                    mbar_arrive(&psum[acc]);
+                }
+                if (warp == 2) {
+                    ok = __all_sync(0xffffffffu, mbar_wait(&psum[acc], (uint32_t)((k / NACC) & 1)));
+                    if (ok && lane < 2) {
+                        double sum = 0.0;
+                        for (int w = 0; w < 8; ++w) sum += (double)csum[acc][w][lane];
+                        part[((size_t)b * 2 + lane) * nblk + (t - b * nblk)] = sum;
+                    }
+                }
+            }
+            fence_before_sync();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&tfree[acc]);
+        }
+        if (!ok && lane == 0) atomicOr(err, 1);
     }
     __syncwarp();   // warp 0 reconverges after its MMA-issuing thread
-    const bool fin = ok && mbar_wait(&done, 0u);
-    if (ok && !fin && lane == 0) atomicOr(err, 1);
-    ok = __syncthreads_and(fin ? 1 : 0) != 0;
-    if (!ok && warp == 4) {   // copies in flight land before the CTA exits
-        if (nw_issued)
-            for (int i = 0; i < NWB && i < nw_issued; ++i) {
-                const int last = nw_issued - 1 - ((nw_issued - 1 - i) % NWB);   // last plane loaded into buffer i
-                mbar_wait(&wfull[i], (uint32_t)((last / NWB) & 1));
-            }
+    ok = __syncthreads_and(ok ? 1 : 0) != 0;
+    if (!ok && warp == 1) {   // copies in flight land before the CTA exits
+        for (int i = 0; i < NWB && i < nw_issued; ++i) {
+            const int last = nw_issued - 1 - ((nw_issued - 1 - i) % NWB);   // last plane loaded into buffer i
+            mbar_wait(&wfull[i], (uint32_t)((last / NWB) & 1));
+        }
         for (int gi = 0; gi < NGRP; ++gi) {
             const int n = na_issued + (gi < part_groups ? 1 : 0);
             if (n) mbar_wait(&afull[gi], (uint32_t)((n - 1) & 1));
-        }
-    }
-    fence_after_sync();
-    float s0 = 0.f, s1 = 0.f;
-    if (ok) {
-        const int q = warp & 3;
-        const int x = x0 + q * 32 + lane;
-        const uint32_t tq = tmem + ((uint32_t)(q * 32) << 16);
-#pragma unroll 1
-        for (int r = (warp >> 2) * (R / 2); r < ((warp >> 2) + 1) * (R / 2); ++r) {
-            float v[CO];
-            const uint32_t col = (uint32_t)((r + 4) * CO);
-            if (CO == 32) tmem_ld32(tq + col, v);
-            else tmem_ld16(tq + col, v);
-            const size_t site = (size_t)b * V + ((size_t)z * ny + (y0 + r)) * nx + x;
-#pragma unroll
-            for (int co = 0; co < CO; ++co) v[co] += (co < cout) ? bias[co] : 0.f;
-            if (EPI == 0) {
-                static_assert(EPI != 0 || CO == 32, "the padded output layout holds 32 channels");
-                __align__(16) bf16 hv[CO];
-#pragma unroll
-                for (int co = 0; co < CO; ++co) hv[co] = __float2bfloat16(tanhf(v[co]));
-                store_padded32((bf16*)out, ((size_t)b * nz + z) * ny + y0 + r, x, nx, hv);
-            } else {
-                float4* dst = (float4*)((float*)out + site * 16);
-#pragma unroll
-                for (int k = 0; k < 4; ++k) dst[k] = make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
-                s0 += v[0];
-                s1 += v[1];
-            }
-        }
-    }
-    if (EPI == 1) {
-#pragma unroll
-        for (int m = 16; m > 0; m >>= 1) {
-            s0 += __shfl_xor_sync(0xffffffffu, s0, m);
-            s1 += __shfl_xor_sync(0xffffffffu, s1, m);
-        }
-        if (lane == 0) {
-            csum[warp][0] = s0;
-            csum[warp][1] = s1;
-        }
-        __syncthreads();
-        if (tid < 2) {
-            double t = 0.0;
-            for (int w = 0; w < TC_THREADS / 32; ++w) t += (double)csum[w][tid];
-            const int nblk = nz * nyb * nxt;
-            part[((size_t)b * 2 + tid) * nblk + (blockIdx.x - (size_t)b * nblk)] = t;
         }
     }
     fence_before_sync();
@@ -563,33 +605,33 @@ __global__ void __launch_bounds__(TC_THREADS, MINB)
 // weights of all 25 (dz, dy) offsets (every operand address its MMAs form lies inside them: the
 // A walk ends at the last staged row of a buffer, the B walk at the last offset's weights).
 size_t tc_conv_smem() { return (size_t)2 * L1_ABYTES + L1_WBYTES; }
-// CTAs of the persistent first layer: L1_CTAS_PER_SM per SM, at most one per tile
-int l1_grid(int ntile) {
+// CTAs of a persistent layer: per_sm per SM, at most one per tile
+int persist_grid(int ntile, int per_sm) {
     int dev = 0, nsm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    const int g = (nsm > 0 ? nsm : 1) * L1_CTAS_PER_SM;
+    const int g = (nsm > 0 ? nsm : 1) * per_sm;
     return ntile < g ? ntile : g;
 }
 // the stacked variant: R + 4 staged rows and NWB buffers of the weights of one whole dz
 constexpr size_t stk_smem(int ci, int co, int r, int nwb) {
     return (size_t)(r + 4) * (ci / 8) * TC_XP * 16 + (size_t)nwb * 25 * (ci / 8) * co * 16;
 }
-constexpr int kR2 = 8, kR3 = 8;   // output rows per CTA of the second and third layer
+constexpr int kR2 = 8, kR3 = 8;   // output rows per tile of the second and third layer
 bool tc_conv_supported(int nx, int ny) { return nx % 128 == 0 && ny % kR2 == 0; }
 
 int tc_conv_prepare() {
     // the whole unified L1/shared array as shared memory, so that several CTAs fit per SM
     cudaFuncSetAttribute(k_conv_tc_l1, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-    cudaFuncSetAttribute(k_conv_tc_stk<32, 32, 0, kR2, 512, 1, 2>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-    cudaFuncSetAttribute(k_conv_tc_stk<32, 16, 1, kR3, 256, 1, 2>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    cudaFuncSetAttribute(k_conv_tc_stk<32, 32, 0, kR2, 1>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    cudaFuncSetAttribute(k_conv_tc_stk<32, 16, 1, kR3, 2>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     cudaError_t e =
         cudaFuncSetAttribute(k_conv_tc_l1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_conv_smem());
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_conv_tc_stk<32, 32, 0, kR2, 512, 1, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        e = cudaFuncSetAttribute(k_conv_tc_stk<32, 32, 0, kR2, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)stk_smem(32, 32, kR2, 2));
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_conv_tc_stk<32, 16, 1, kR3, 256, 1, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        e = cudaFuncSetAttribute(k_conv_tc_stk<32, 16, 1, kR3, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)stk_smem(32, 16, kR3, 2));
     return (int)e;
 }
@@ -598,22 +640,23 @@ int tc_conv_prepare() {
 int tc_conv_blocks(int nx, int ny, int nz) { return nz * (ny / kR3) * (nx / 128); }
 
 // Layer l of the predictor network (0: 2 -> 32 tanh with the x offsets folded into 16 input
-// channels, input [B][nz][ny][2][nx + 4][8], weights [dz][dy][k / 8][co][k % 8]; 1: 32 -> 32 tanh and 2: 32 -> 16 linear FP32, both
-// stacked, weights [dz][dx][ci / 8][4 - dy][co][ci % 8]) over B samples of an nx x ny x nz grid
-// (tc_conv_supported must hold).
+// channels, input [B][nz][ny][2][nx + 4][8], weights [dz][dy][k / 8][co][k % 8]; 1: 32 -> 32 tanh
+// and 2: 32 -> 16 linear FP32, both stacked, input [B][nz][ny][4][nx + 4][8], weights
+// [dz][dx][ci / 8][4 - dy][co][ci % 8]) over B samples of an nx x ny x nz grid
+// (tc_conv_supported must hold).  Persistent kernels: at most one CTA per tile.
 void launch_conv_tc(int layer, const void* in, const void* wt, const float* bias, int cout, void* out, int nx, int ny,
                     int nz, int B, double* part, int* err, cudaStream_t s) {
     const bf16* x = (const bf16*)in;
     const bf16* w = (const bf16*)wt;
     if (layer == 0)
-        k_conv_tc_l1<<<l1_grid(B * nz * (ny / TC_R) * (nx / 128)), L1_THREADS, tc_conv_smem(), s>>>(
-            x, w, bias, cout, (bf16*)out, nx, ny, nz, B, err);
+        k_conv_tc_l1<<<persist_grid(B * nz * (ny / TC_R) * (nx / 128), L1_CTAS_PER_SM), L1_THREADS, tc_conv_smem(),
+                       s>>>(x, w, bias, cout, (bf16*)out, nx, ny, nz, B, err);
     else if (layer == 1)
-        k_conv_tc_stk<32, 32, 0, kR2, 512, 1, 2><<<B * nz * (ny / kR2) * (nx / 128), TC_THREADS, stk_smem(32, 32, kR2, 2), s>>>(
-            x, w, bias, cout, out, nx, ny, nz, part, err);
+        k_conv_tc_stk<32, 32, 0, kR2, 1><<<persist_grid(B * nz * (ny / kR2) * (nx / 128), 1), STK_THREADS,
+                                           stk_smem(32, 32, kR2, 2), s>>>(x, w, bias, cout, out, nx, ny, nz, B, part, err);
     else
-        k_conv_tc_stk<32, 16, 1, kR3, 256, 1, 2><<<B * nz * (ny / kR3) * (nx / 128), TC_THREADS, stk_smem(32, 16, kR3, 2), s>>>(
-            x, w, bias, cout, out, nx, ny, nz, part, err);
+        k_conv_tc_stk<32, 16, 1, kR3, 2><<<persist_grid(B * nz * (ny / kR3) * (nx / 128), 1), STK_THREADS,
+                                           stk_smem(32, 16, kR3, 2), s>>>(x, w, bias, cout, out, nx, ny, nz, B, part, err);
 }
 
 }  // namespace dscf
