@@ -354,7 +354,7 @@ int64_t dscf_net_num_params(void);
 
 /* Tensor-core path of the network's forward convolutions.  path 0 (default): tcgen05 MMAs with
  * operands in shared memory and accumulators in tensor memory where the grid allows it (nx a
- * multiple of 128, ny of 4, sm_103 device), warp-level mma.sync otherwise; path 1: mma.sync
+ * multiple of 128, ny of 8, sm_103 device), warp-level mma.sync otherwise; path 1: mma.sync
  * always (the backward pass always uses mma.sync).  dscf_net_tensor_path returns 2 when the
  * forward runs on tcgen05, 1 for mma.sync.  dscf_net_status synchronises and returns
  * DSCF_ERR_TIMEOUT if a tcgen05 convolution gave up waiting for its MMAs (bounded wait; the

@@ -6,9 +6,11 @@
 // Tensor cores: every convolution (forward, and backward with respect to the input) is one
 // implicit GEMM over (offset, input channel) in BF16 with FP32 accumulation; weight gradients are
 // per-offset GEMMs over sites.  The forward convolutions run on tcgen05 (operands in shared
-// memory, accumulators in tensor memory; dscf_tc.cu) when nx is a multiple of 128 and ny of 4,
+// memory, accumulators in tensor memory; dscf_tc.cu) when nx is a multiple of 128 and ny of 8,
 // and with warp-level mma.sync m16n8k16 otherwise (and for the backward pass).  Activations are stored
-// channel-last in BF16 with channel counts padded to multiples of 16 (zero weights in the pad).
+// channel-last in BF16 with channel counts padded to multiples of 16 (zero weights in the pad);
+// the tcgen05 forward keeps its own copies in a padded channel-group layout (x16f, h1p, h2p) from
+// which it stages rows by bulk copies, and the backward pass reads channel-last copies of them.
 // Training keeps FP32 master weights and Adam moments.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>

@@ -27,7 +27,7 @@ from paper_1204_2088_gb300 import build, dscf, inputs
 
 pytestmark = pytest.mark.gpu
 
-GRID = (128, 8, 4)          # nx a multiple of 128 and ny of 4: the tcgen05 forward applies
+GRID = (128, 8, 4)          # nx a multiple of 128 and ny of 8: the tcgen05 forward applies
 B = 2
 
 
