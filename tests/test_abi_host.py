@@ -61,6 +61,22 @@ def test_workspace_scales_with_chain_and_grid(lib):
     assert c - a > 0.9 * (a - z)              # twice the sites: about twice the per-site part
 
 
+def test_net_workspace_validates_and_holds_the_padded_tcgen05_copies(lib):
+    """The network workspace: 0 for grids it cannot run (nx not a multiple of 16, empty extents,
+    no samples); on a grid the tcgen05 forward takes (nx a multiple of 128, ny of 8) it also
+    holds the padded channel-group copies of the layer inputs, rows x (nx + 4) sites of 16 (x16f)
+    and 32 (h1p, h2p) BF16 channels, and nothing else beyond a grid of as many sites that the
+    tcgen05 path does not take."""
+    f = lib.dscf_net_workspace_bytes
+    for bad in [(8, 8, 8, 1), (24, 8, 8, 1), (128, 0, 4, 1), (128, 8, 0, 1), (128, 8, 4, 0)]:
+        assert f(*bad) == 0, bad
+    for nx, ny, nz, B in [(128, 8, 4, 1), (128, 16, 8, 2), (256, 8, 4, 1)]:
+        rows = ny * nz * B
+        padded = rows * (nx + 4) * (16 + 32 + 32) * 2
+        other = f(16, ny * nx // 16, nz, B)     # same sites, rows of 16: mma.sync only
+        assert f(nx, ny, nz, B) - other == padded, (nx, ny, nz, B)
+
+
 def test_init_rejects_null_output(lib):
     p = dscf.make_params(inputs.melt((8, 8, 8), 4, 0.5, 10.0))
     rc = lib.dscf_init(ctypes.byref(p), 1, 0, None, 0, None, None)
