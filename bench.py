@@ -207,6 +207,16 @@ def peaks():
     return 6800.0, "fallback"
 
 
+def bf16_peak():
+    """Dense BF16 burst rate (TFLOP/s) of this GPU model: the measured one, else the fallback."""
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        if "bf16_tflops" in d:
+            return float(d["bf16_tflops"]), "measured burst"
+    return 1900.0, "fallback burst"
+
+
 FP64_NOMINAL_TFLOPS = 1.25   # GB300 FP64 (non-tensor), nominal
 
 
@@ -524,6 +534,12 @@ def net_forward_form(dev, timed, reps=10):
         ms = timed(lambda: [net.forward(U, phibar) for _ in range(reps)]) / reps
         name = "tcgen05" if net.tensor_path() == 2 else "mma.sync"
         out[name] = {"ms": ms, "tflops_useful": useful / ms / 1e9, "tflops_padded": padded / ms / 1e9}
+    peak, kind = bf16_peak()
+    out["bf16_peak"] = {"tflops": peak, "kind": kind}
+    for name in ("tcgen05", "mma.sync"):
+        if name in out:
+            out[name]["frac_useful"] = out[name]["tflops_useful"] / peak
+            out[name]["frac_padded"] = out[name]["tflops_padded"] / peak
     # one more forward on the default path inside a profiler range (a no-op unless a profiler runs
     # with profiling from start off), so that a capture can select exactly its launches
     net.set_tensor_path(0)
