@@ -357,8 +357,9 @@ int64_t dscf_net_num_params(void);
  * multiple of 128, ny of 8, sm_103 device), warp-level mma.sync otherwise; path 1: mma.sync
  * always (the backward pass always uses mma.sync).  dscf_net_tensor_path returns 2 when the
  * forward runs on tcgen05, 1 for mma.sync.  dscf_net_status synchronises and returns
- * DSCF_ERR_TIMEOUT if a tcgen05 convolution gave up waiting for its MMAs (bounded wait; the
- * output of that call is invalid), then clears the condition. */
+ * DSCF_ERR_TIMEOUT if a tcgen05 convolution gave up waiting for its operand copies, its MMAs or
+ * its epilogue (every wait is bounded; the output of that call is invalid), then clears the
+ * condition. */
 int dscf_net_set_tensor_path(dscf_net* net, int32_t path);
 int32_t dscf_net_tensor_path(const dscf_net* net);
 int dscf_net_status(dscf_net* net);
